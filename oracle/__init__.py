@@ -1,0 +1,253 @@
+"""Plain FP64 CPU oracle for the single-level comoving gas advance.
+
+TEST INFRASTRUCTURE, not product code.  Only ``tests/``,
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
+import this package.  It wraps ``nyx_oracle.c`` (built with gcc,
+``-O2 -ffp-contract=off``, OpenMP) through ctypes and shares no code with
+the CUDA path.
+
+What it computes follows the Nyx paper (Almgren et al. 2013): Sec. 2.2
+(comoving Euler + dual-energy equations, gamma-law EOS), Sec. 3.2 (unsplit
+PPM Godunov with characteristic tracing, reference states, two-shock Riemann
+solver, dual-energy switch, gravity predictor-corrector), Sec. 3.5 (CFL time
+step), Sec. 3.6 Steps 2 and 6.
+
+Arrays are per box, shape ``(ncomp, nz+2ng, ny+2ng, nx+2ng)`` float64, C
+order (x fastest).  A level is any object with numpy attributes ``lo``,
+``hi`` (nbox x 3, inclusive), ``dom`` (nbox), ``dx`` (nbox x 3), ``dom_lo``,
+``dom_hi`` (ndom x 3), ``dom_bc`` (ndom x 6: lo x,y,z then hi x,y,z; 0
+periodic, 1 outflow) and ``ng``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library with gcc (no FMA contraction)."""
+    src = os.path.join(_HERE, "nyx_oracle.c")
+    hdr = os.path.join(_HERE, "nyx_oracle.h")
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(src), os.path.getmtime(hdr))):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-fPIC", "-shared", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("small_dens", C.c_double),
+                ("small_pres", C.c_double), ("eta_de", C.c_double),
+                ("riemann_max_iter", C.c_int), ("riemann_tol", C.c_double),
+                ("grav_corrector", C.c_int), ("dual_energy_sync", C.c_int)]
+
+
+class _Level(C.Structure):
+    _fields_ = [("nbox", C.c_int), ("ng", C.c_int), ("lo", C.POINTER(C.c_int)),
+                ("hi", C.POINTER(C.c_int)), ("dom", C.POINTER(C.c_int)),
+                ("dx", C.POINTER(C.c_double)), ("ndom", C.c_int),
+                ("dom_lo", C.POINTER(C.c_int)), ("dom_hi", C.POINTER(C.c_int)),
+                ("dom_bc", C.POINTER(C.c_int))]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("floor_rho", C.c_longlong), ("floor_e", C.c_longlong),
+                ("use_e", C.c_longlong), ("bad", C.c_longlong)]
+
+
+@dataclass
+class OracleParams:
+    """Run-time parameters of the scheme (Sec. 3.2, 3.5, 3.6)."""
+    gamma: float = 5.0 / 3.0
+    cfl: float = 0.5
+    small_dens: float = 1e-10
+    small_pres: float = 1e-12
+    eta_de: float = 1e-4
+    riemann_max_iter: int = 12
+    riemann_tol: float = 1e-10
+    grav_corrector: int = 1
+    dual_energy_sync: int = 1
+
+    def _c(self) -> _Params:
+        return _Params(self.gamma, self.cfl, self.small_dens, self.small_pres, self.eta_de,
+                       self.riemann_max_iter, self.riemann_tol, self.grav_corrector,
+                       self.dual_energy_sync)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build()
+        L = C.CDLL(path)
+        dp = C.POINTER(C.c_double)
+        L.orc_fill_ghosts.argtypes = [C.POINTER(_Level), C.c_int, C.POINTER(dp)]
+        L.orc_fill_ghosts.restype = C.c_int
+        L.orc_advance.argtypes = [C.POINTER(_Level), C.POINTER(_Params), C.POINTER(dp),
+                                  C.POINTER(dp), C.POINTER(dp), C.c_double, C.c_double,
+                                  C.c_double, C.c_int, C.POINTER(dp), C.POINTER(_Stats)]
+        L.orc_advance.restype = C.c_int
+        L.orc_estdt.argtypes = [C.POINTER(_Level), C.POINTER(_Params), C.POINTER(dp), C.c_double]
+        L.orc_estdt.restype = C.c_double
+        L.orc_ppm_line.argtypes = [C.c_int, dp, dp, dp, dp]
+        L.orc_ppm_integrals.argtypes = [C.c_double] * 4 + [dp, dp]
+        L.orc_riemann.argtypes = [C.POINTER(_Params), dp, dp, dp, dp, dp]
+        L.orc_trace_line.argtypes = [C.POINTER(_Params), C.c_int, dp, dp, C.c_double,
+                                     C.c_double, C.c_double, C.c_int, dp, dp, dp, dp]
+        _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ptrs(arrs):
+    arr = (C.POINTER(C.c_double) * len(arrs))()
+    for i, a in enumerate(arrs):
+        arr[i] = _dp(a)
+    return arr
+
+
+def _level(lev):
+    keep = {}
+    for name in ("lo", "hi", "dom", "dom_lo", "dom_hi", "dom_bc"):
+        keep[name] = np.ascontiguousarray(getattr(lev, name), dtype=np.int32)
+    keep["dx"] = np.ascontiguousarray(lev.dx, dtype=np.float64)
+    ip = lambda n: keep[n].ctypes.data_as(C.POINTER(C.c_int))
+    cl = _Level(len(keep["lo"]), int(lev.ng), ip("lo"), ip("hi"), ip("dom"),
+                keep["dx"].ctypes.data_as(C.POINTER(C.c_double)), len(keep["dom_lo"]),
+                ip("dom_lo"), ip("dom_hi"), ip("dom_bc"))
+    return cl, keep
+
+
+def fill_ghosts(lev, arrays) -> None:
+    """Fill ghost cells of every box array in place (periodic / outflow / neighbour)."""
+    cl, keep = _level(lev)
+    ncomp = arrays[0].shape[0]
+    rc = lib().orc_fill_ghosts(C.byref(cl), ncomp, _ptrs(arrays))
+    if rc:
+        raise ValueError("oracle ghost fill: a ghost cell maps to no box of its domain")
+
+
+def advance(lev, params: OracleParams, states, grav=None, *, a_old=1.0, a_new=1.0, dt,
+            fill_ghosts=True, want_flux=False):
+    """One single-level advance (Steps 2 and 6).  Returns (new_states, stats, fluxes).
+
+    ``states`` (and ``grav``) are copied; ghost cells of the copies are filled
+    here unless ``fill_ghosts`` is False.  Fluxes (if asked) are per box a
+    list of three arrays of shape (6, nz', ny', nx') with n' = n + 1 along the
+    face direction: the raw final Godunov fluxes.
+    """
+    cl, keep = _level(lev)
+    sin = [np.array(s, dtype=np.float64, order="C", copy=True) for s in states]
+    sout = [s.copy() for s in sin]
+    g = None if grav is None else [np.array(x, dtype=np.float64, order="C", copy=True) for x in grav]
+    flux = None
+    fptr = None
+    if want_flux:
+        flux = []
+        flat = []
+        for b in range(len(sin)):
+            n = (lev.hi[b] - lev.lo[b] + 1).astype(int)
+            per = []
+            for d in range(3):
+                e = [int(n[0]), int(n[1]), int(n[2])]
+                e[d] += 1
+                arr = np.zeros((6, e[2], e[1], e[0]))
+                per.append(arr)
+                flat.append(arr)
+            flux.append(per)
+        fptr = _ptrs(flat)
+    st = _Stats()
+    p = params._c()
+    rc = lib().orc_advance(C.byref(cl), C.byref(p), _ptrs(sin), _ptrs(sout),
+                           None if g is None else _ptrs(g), a_old, a_new, dt,
+                           1 if fill_ghosts else 0, fptr, C.byref(st))
+    stats = dict(floor_e=st.floor_e, use_e=st.use_e, bad=st.bad, rc=rc)
+    if rc == -1:
+        raise ValueError("oracle advance: invalid level or ghost fill failure")
+    return sout, stats, flux
+
+
+def estdt(lev, params: OracleParams, states, a: float) -> float:
+    """CFL time step (Sec. 3.5) over the valid cells of every box."""
+    cl, keep = _level(lev)
+    sin = [np.ascontiguousarray(s, dtype=np.float64) for s in states]
+    p = params._c()
+    return float(lib().orc_estdt(C.byref(cl), C.byref(p), _ptrs(sin), a))
+
+
+def run(lev, params: OracleParams, states, grav=None, a_sched=None, nsteps=1):
+    """Advance ``nsteps`` steps; dt of each step is the CFL step of its input
+    state at a = a_sched[s] (a_sched defaults to a = 1).  Returns
+    (states, dts, stats_list)."""
+    if a_sched is None:
+        a_sched = np.ones(nsteps + 1)
+    cur = [np.array(s, dtype=np.float64, copy=True) for s in states]
+    dts, stats = [], []
+    for s in range(nsteps):
+        dt = estdt(lev, params, cur, float(a_sched[s]))
+        cur, st, _ = advance(lev, params, cur, grav, a_old=float(a_sched[s]),
+                             a_new=float(a_sched[s + 1]), dt=dt)
+        dts.append(dt)
+        stats.append(st)
+    return cur, dts, stats
+
+
+def ppm_line(s: np.ndarray):
+    """PPM edge values and curvature (sL, sR, s6) for cells 2..n-3 of a line."""
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    n = len(s)
+    sL, sR, s6 = np.zeros(n), np.zeros(n), np.zeros(n)
+    lib().orc_ppm_line(n, _dp(s), _dp(sL), _dp(sR), _dp(s6))
+    return sL, sR, s6
+
+
+def ppm_integrals(sL, sR, s6, sigma):
+    ip, im = C.c_double(), C.c_double()
+    lib().orc_ppm_integrals(sL, sR, s6, sigma, C.byref(ip), C.byref(im))
+    return ip.value, im.value
+
+
+def riemann(params: OracleParams, qL, qR):
+    """Two-shock solve of one face problem; states (rho, u_n, u_t1, u_t2, p).
+    Returns (flux8, pstar, ustar) with flux8 = (F_rho, F_mn, F_mt1, F_mt2,
+    F_rhoE, F_rhoe, u_g, p_g)."""
+    qL = np.ascontiguousarray(qL, dtype=np.float64)
+    qR = np.ascontiguousarray(qR, dtype=np.float64)
+    out = np.zeros(8)
+    ps, us = np.zeros(1), np.zeros(1)
+    p = params._c()
+    lib().orc_riemann(C.byref(p), _dp(qL), _dp(qR), _dp(out), _dp(ps), _dp(us))
+    return out, float(ps[0]), float(us[0])
+
+
+def trace_line(params: OracleParams, q5, g=None, *, dtp, dx, adot=0.0, direction=0):
+    """Trace a line of primitives (5 x n, rho,u_x,u_y,u_z,p) along
+    ``direction``.  Returns (qm, qp, beta_m, beta_p) for cells 2..n-3: the
+    low- and high-face edge states and the wave amplitudes (beta_-, beta_0,
+    beta_+) of each side."""
+    q5 = np.ascontiguousarray(q5, dtype=np.float64)
+    n = q5.shape[1]
+    gl = None if g is None else np.ascontiguousarray(g, dtype=np.float64)
+    qm, qp = np.zeros((5, n)), np.zeros((5, n))
+    bm, bp = np.zeros((3, n)), np.zeros((3, n))
+    p = params._c()
+    lib().orc_trace_line(C.byref(p), n, _dp(q5), None if gl is None else _dp(gl), dtp, dx, adot,
+                         direction, _dp(qm), _dp(qp), _dp(bm), _dp(bp))
+    return qm, qp, bm, bp

@@ -1,0 +1,88 @@
+/*
+ * nyx_oracle.h -- TEST INFRASTRUCTURE, not product code.
+ *
+ * Plain, slow FP64 CPU oracle for the single-level comoving gas advance of
+ * the Nyx paper (Almgren et al. 2013): Sec. 2.2 (comoving Euler and dual
+ * energy equations), Sec. 3.2 (unsplit PPM Godunov with characteristic
+ * tracing, reference states, two-shock Riemann solver, dual-energy switch,
+ * gravity predictor-corrector), Sec. 3.5 (CFL time step) and Sec. 3.6
+ * (Steps 2 and 6 of the single-level algorithm).
+ *
+ * Only the test suite, the package's smoke check and the benchmark's
+ * CPU-baseline leg may load this library.  It shares no code with the CUDA
+ * path and includes none of its headers.
+ *
+ * Layout of every box array: ncomp blocks of (nz+2ng)(ny+2ng)(nx+2ng)
+ * doubles, x fastest; cell (i,j,k) of the valid region [0,n) sits at
+ * ((c*Nz + k+ng)*Ny + j+ng)*Nx + i+ng.  State components: rho, m_x, m_y,
+ * m_z, rhoE, rhoe (m = rho U, unweighted by a).  Gravity: g_x, g_y, g_z.
+ */
+#ifndef NYX_ORACLE_H
+#define NYX_ORACLE_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_NCONS 6
+#define ORC_BC_PERIODIC 0
+#define ORC_BC_OUTFLOW 1
+
+typedef struct {
+  double gamma;          /* gamma-law EOS exponent (Sec. 2.2) */
+  double cfl;            /* hyperbolic CFL factor sigma (Sec. 3.5) */
+  double small_dens;     /* density floor */
+  double small_pres;     /* pressure floor */
+  double eta_de;         /* dual-energy threshold, 1e-4 (Sec. 3.2 / Step 6) */
+  int riemann_max_iter;  /* two-shock iteration cap */
+  double riemann_tol;    /* relative pressure convergence tolerance */
+  int grav_corrector;    /* 1: apply the Step 6 gravity corrector */
+  int dual_energy_sync;  /* 1: apply the Step 6 e/E synchronisation */
+} orc_params;
+
+typedef struct {
+  int nbox, ng;
+  const int *lo, *hi;     /* nbox*3 each; inclusive cell bounds in the domain index space */
+  const int *dom;         /* nbox: domain id of each box */
+  const double *dx;       /* nbox*3: cell widths */
+  int ndom;
+  const int *dom_lo, *dom_hi; /* ndom*3 each, inclusive */
+  const int *dom_bc;      /* ndom*6: bc of lo x,y,z then hi x,y,z */
+} orc_level;
+
+typedef struct {
+  long long floor_rho;    /* Godunov/edge states raised to small_dens */
+  long long floor_e;      /* cells whose rhoe was raised to the floor in the sync */
+  long long use_e;        /* cells where the sync kept e and re-derived E */
+  long long bad;          /* non-positive or non-finite density after the update */
+} orc_stats;
+
+/* Ghost fill (periodic copy / zero-gradient outflow / neighbour copy). */
+int orc_fill_ghosts(const orc_level *lev, int ncomp, double *const *f);
+
+/* One advance of every box: state_in (ghosts filled unless fill_ghosts=1,
+ * in which case they are filled in place) -> valid cells of state_out.
+ * grav may be NULL (zero gravity).  flux_out may be NULL; otherwise
+ * flux_out[b*3+d] receives box b's final direction-d fluxes, 6 components
+ * each laid out as ((c*nz + k)*ny + j)*(nx+1 on d==0 ...) -- see
+ * orc_flux_count. */
+int orc_advance(const orc_level *lev, const orc_params *p, double *const *state_in,
+                double *const *state_out, double *const *grav, double a_old,
+                double a_new, double dt, int fill_ghosts, double *const *flux_out,
+                orc_stats *stats);
+
+/* CFL time step over valid cells at scale factor a (Sec. 3.5). */
+double orc_estdt(const orc_level *lev, const orc_params *p, double *const *state, double a);
+
+/* Unit-level entry points used by the pin tests. */
+void orc_ppm_line(int n, const double *s, double *sL, double *sR, double *s6);
+void orc_ppm_integrals(double sL, double sR, double s6, double sigma, double *ip, double *im);
+int orc_riemann(const orc_params *p, const double *qL, const double *qR, double *flux8,
+                double *pstar, double *ustar);
+void orc_trace_line(const orc_params *p, int n, const double *q5, const double *gline,
+                    double dtp, double dx, double adot, int dir, double *qm, double *qp,
+                    double *beta_m, double *beta_p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
