@@ -1,0 +1,371 @@
+#!/usr/bin/env python3
+"""Benchmark of the single-level comoving gas advance on GB300.
+
+One step = ghost fill + fused advance + CFL dt of the whole level (every
+box), i.e. one pass of the hot path over one synthetic level.  Default
+workload: the large batched mixed-precision level, a periodic 512^3 domain
+cut into 4096 boxes of 32^3 plus 410 independent 64^3 boxes at half the
+cell width (2.42e8 valid cells), lognormal comoving field with sigma = 1.0,
+a from 1/51 to 1/31.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle, as it stands, on a bounded sample of the same workload.
+N > 1 (torchrun): every rank advances its own replica of the level on its
+own GPU (replicas, weak scaling); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1301_4498_gb300 import workloads as W  # noqa: E402
+
+METRIC = "zone-updates/s per level step on 1 GB300 + HBM-roofline fraction, FP32-batched vs FP64"
+ALG_BYTES_PER_ZONE = 120  # read S (6 x 8 B) + g (3 x 8 B), write S (6 x 8 B)
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def make_workload(name: str, nsteps: int, sample_only: bool = False):
+    if name == "large":
+        if sample_only:  # the independent 64^3 boxes only: what the CPU sample uses
+            return W.large_level(nsteps=max(nsteps, 1), coarse_select=[], fine_select=range(16))
+        return W.large_level(nsteps=max(nsteps, 1))
+    if name == "comoving128":
+        return W.comoving_box(n=128, sigma=0.5, seed=1, nsteps=max(nsteps, 10))
+    if name == "uneven512":
+        return W.uneven_boxes(nbox=512, nsteps=max(nsteps, 10))
+    if name == "mixed256":
+        return W.comoving_box(n=256, sigma=1.0, seed=4, nsteps=max(nsteps, 50), mixed=True)
+    if name == "sod":
+        return W.sod()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def a_schedule_for(w, nsteps):
+    """a_0..a_nsteps from the workload's schedule (cycled if longer)."""
+    a = np.asarray(w.a_sched, dtype=np.float64)
+    if len(a) >= nsteps + 1:
+        return a[: nsteps + 1].copy()
+    reps = (nsteps + 1 + len(a) - 1) // len(a)
+    return np.tile(a, reps)[: nsteps + 1]
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    """Max of a host scalar over all ranks (timing only; no data-path exchange)."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if (torch.cuda.is_available() and dist.get_backend() == "nccl") else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------- CPU oracle timing
+
+def oracle_sample(workload_name, w, budget_s=12.0, max_boxes=None):
+    """Time the FP64 CPU oracle on a bounded sample of the workload: whole
+    independent boxes (periodic domains of their own) advanced one step,
+    added one at a time until ``budget_s`` of CPU time is spent."""
+    import oracle
+    P = oracle.OracleParams(gamma=w.gamma, cfl=w.cfl)
+    lev = w.level
+    # boxes that are their own domain (all of them for single-box levels)
+    dom_count = np.bincount(lev.dom)
+    own = [b for b in range(lev.nbox) if dom_count[lev.dom[b]] == 1]
+    if not own:
+        own = list(range(lev.nbox))
+    cells = 0
+    elapsed = 0.0
+    used = 0
+    a0, a1 = float(w.a_sched[0]), float(w.a_sched[1])
+    for b in own:
+        sub = lev.subset([b])
+        st = [w.state[b]]
+        gr = None if w.grav is None else [w.grav[b]]
+        t0 = time.perf_counter()
+        dt = oracle.estdt(sub, P, st, a0)
+        oracle.advance(sub, P, st, gr, a_old=a0, a_new=a1, dt=dt)
+        elapsed += time.perf_counter() - t0
+        cells += int(np.prod(sub.hi[0] - sub.lo[0] + 1))
+        used += 1
+        if elapsed >= budget_s or (max_boxes and used >= max_boxes):
+            break
+    return {"value": cells / elapsed, "unit": "zone-updates/s", "cores": os.cpu_count(),
+            "kind": "oracle", "elapsed_s": elapsed,
+            "sample": f"{used} whole box(es) of the '{workload_name}' workload ({cells} cells), "
+                      f"1 step each, FP64 oracle, OpenMP on all host cores; {elapsed:.1f} s"}
+
+
+def run_reference(args, w):
+    ws, rank, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    # each step: one oracle step on a bounded sample of the workload
+    per_step = []
+    info = None
+    for s in range(args.warmup + args.steps):
+        r = oracle_sample(args.workload, w, budget_s=args.ref_budget, max_boxes=args.ref_boxes)
+        if s >= args.warmup:
+            per_step.append(r)
+        info = r
+    value = statistics.median(x["value"] for x in per_step)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "zone-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.median(x["elapsed_s"] for x in per_step) * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "level": w.name, "sample": info["sample"]},
+        "cpu_baseline": {"value": value, "unit": "zone-updates/s", "cores": info["cores"],
+                         "kind": "oracle", "sample": info["sample"]},
+        "e2e": {"value": value, "unit": "zone-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------- GPU path
+
+def run_ours(args, w):
+    import torch
+    from paper_1301_4498_gb300 import hydro as H
+    ws, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    peaks, peak_src = load_peaks()
+    K, Wm = args.steps, args.warmup
+    cells = w.level.valid_cells()
+
+    plan = H.Plan(w.level, gamma=w.gamma, cfl=w.cfl, precision=args.precision,
+                  batching="persistent", autotune=1 if args.autotune else 0)
+    lev = H.make_level(plan, w.state, w.grav)
+    a_host = a_schedule_for(w, max(K, Wm) + 1)
+    a = torch.tensor(a_host, dtype=torch.float64, device="cuda")
+    dt = torch.zeros(len(a_host), dtype=torch.float64, device="cuda")
+    stream = plan.torch_stream
+
+    # warm-up: W eager steps (the first one also runs the tile autotuner)
+    plan.run(lev, a, dt, Wm, compute_dt0=True, use_graph=False)
+    # capture the K-step graph (first launch also warms it)
+    plan.run(lev, a, dt, K, compute_dt0=True, use_graph=True)
+    torch.cuda.synchronize()
+    rc, flags = plan.status()
+    if rc != H.NYX_OK:
+        raise SystemExit(f"device status after warm-up: {rc} flags {flags}")
+    plan.counters(reset=True)
+
+    # timed: K steps (one graph replay), inputs (>= 20 GB) far larger than L2
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.run(lev, a, dt, K, compute_dt0=True, use_graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    launches = plan.counters(reset=True)["launches"]
+    ms_max = max_over_ranks(ms, ws)
+    value = ws * cells * K / (ms_max / 1e3)
+
+    # dominant kernel: the fused advance, timed with events on its own stream
+    plan.profile(True)
+    plan.run(lev, a, dt, K, compute_dt0=True, use_graph=False)
+    prof = plan.counters(reset=True)
+    plan.profile(False)
+    adv_ms = prof["advance_ms"] / max(1, prof["timed_advances"])
+    fill_ms = prof["fill_ms"] / max(1, prof["timed_fills"])
+    achieved = ALG_BYTES_PER_ZONE * cells / (adv_ms / 1e3) / 1e9
+    shape, (tx, ty) = plan.tile_shape()
+
+    # end to end through the C ABI with pinned host buffers
+    host_in = torch.from_numpy(plan.pack_host(w.state, 6)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    e2e_steps = max(1, min(3, K))
+    d = plan.step_host(lev, host_in, host_out, float(a_host[0]), float(a_host[1]), 0.0)
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for s in range(e2e_steps):
+        d = plan.step_host(lev, host_in, host_out, float(a_host[s]), float(a_host[s + 1]), d)
+    t_e2e = max_over_ranks(time.perf_counter() - t0, ws)
+    e2e_value = ws * cells * e2e_steps / t_e2e
+    state_bytes = host_in.numel() * 8
+
+    # FP64 forms on the same workload (one step each), for the FP32-vs-FP64 comparison
+    side = {}
+    if not args.no_fp64:
+        for label, batching in (("fp64_persistent", "persistent"), ("fp64_per_box", "per_box")):
+            p64 = H.Plan(w.level, gamma=w.gamma, cfl=w.cfl, precision="fp64", batching=batching)
+            l64 = H.Level(lev.state[0], lev.state[1], lev.grav, lev.cur)
+            p64.run(l64, a, dt, 1, compute_dt0=True, use_graph=False)
+            torch.cuda.synchronize()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(p64.torch_stream)
+            p64.run(l64, a, dt, 1, compute_dt0=True, use_graph=False)
+            f1.record(p64.torch_stream)
+            torch.cuda.synchronize()
+            side[label] = {"value": cells / (f0.elapsed_time(f1) / 1e3), "unit": "zone-updates/s",
+                           "steps": 1}
+            p64.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = oracle_sample(args.workload, w, budget_s=args.cpu_budget)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "zone-updates/s", "n_gpus": ws,
+            "steps": K, "warmup": Wm, "ms_per_step": ms_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "level": w.name, "valid_cells": cells,
+                       "boxes": w.level.nbox, "precision": args.precision,
+                       "batching": "persistent + CUDA graph", "tile": [tx, ty],
+                       "l2": "inputs larger than L2 (state + gravity > 20 GB)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                         "kernel": "k_fused<float>", "kernel_ms": adv_ms,
+                         "alg_bytes_per_zone": ALG_BYTES_PER_ZONE,
+                         "peak_source": f"hbm_gbs {peak_src}"},
+            "kernel_ms": {"advance": adv_ms, "ghost_fill": fill_ms},
+            "fp64_comparison": side,
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": "zone-updates/s", "h2d_bytes_per_step": state_bytes,
+                    "d2h_bytes_per_step": state_bytes + 8, "steps": e2e_steps},
+            "gpu_launches": launches,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out), flush=True)
+    plan.close()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="large",
+                    choices=["large", "comoving128", "uneven512", "mixed256", "sod"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--autotune", type=int, default=1)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--ref-budget", type=float, default=6.0)
+    ap.add_argument("--ref-boxes", type=int, default=0)
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    w = make_workload(args.workload, args.steps, sample_only=args.impl == "reference")
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

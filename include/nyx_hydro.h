@@ -1,0 +1,211 @@
+/*
+ * nyx_hydro.h -- C ABI of libnyxhydro.so, the GB300 (sm_103a) single-level
+ * comoving gas advance of Nyx (Almgren et al. 2013).
+ *
+ * The operation is Step 2 (hydro advance) and the hydro part of Step 6
+ * (gravity corrector, dual-energy sync) of the single-level algorithm
+ * (Sec. 3.6), for the comoving Euler + dual-energy equations of Sec. 2.2 in
+ * the discretisation of Sec. 3.2 (unsplit PPM Godunov with characteristic
+ * tracing, reference states, full corner coupling, two-shock Riemann
+ * solver), over every box of one AMR level (Sec. 4.1), plus the CFL time
+ * step of Sec. 3.5.
+ *
+ * Conventions for every entry point:
+ *  - Return 0 (NYX_OK) on success or a negative NYX_E* code; the text of
+ *    the last error of the calling thread is returned by nyx_last_error().
+ *  - Device pointers are plain CUDA device addresses of the current device;
+ *    the caller owns every buffer it passes and the library never frees one.
+ *  - Work is enqueued on the stream given to nyx_hydro_plan() and is
+ *    asynchronous; device-side failures (negative density, non-finite
+ *    values) raise a status word that nyx_hydro_status() reads.
+ *  - A plan is not thread-safe: one host thread at a time per plan.
+ *
+ * Level buffers.  A "field" of ncomp components over a level is one device
+ * buffer of doubles.  Box b occupies [off[b], off[b+1]) with off from
+ * nyx_hydro_layout(); inside it component c is a contiguous array of
+ * (nz+2ng)(ny+2ng)(nx+2ng) doubles (x fastest, ghost cells included),
+ * starting at off[b] + c*stride[b] (stride[b] is the padded component
+ * volume, a multiple of 32 doubles).  The conserved state has 6
+ * components (rho, m_x, m_y, m_z, rhoE, rhoe) with m = rho U, not weighted
+ * by a (the a, a^2 weights of the paper's U are applied inside the update);
+ * gravity has 3 (g_x, g_y, g_z).
+ */
+#ifndef NYX_HYDRO_H
+#define NYX_HYDRO_H
+#include <stddef.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NYX_OK 0
+#define NYX_EINVAL (-1)    /* bad descriptor, parameter or pointer */
+#define NYX_ECUDA (-2)     /* a CUDA call failed */
+#define NYX_ENEGATIVE (-3) /* device flag: density <= 0 after an update */
+#define NYX_ENONFINITE (-4) /* device flag: NaN/Inf in an updated state */
+#define NYX_ETIMEOUT (-5)  /* device flag: a bounded device wait gave up */
+#define NYX_ENOMEM (-6)    /* device allocation failed */
+
+#define NYX_BC_PERIODIC 0
+#define NYX_BC_OUTFLOW 1   /* zero-gradient extrapolation */
+
+#define NYX_FP64 0         /* all arithmetic FP64 */
+#define NYX_MIXED 1        /* FP32 reconstruction/tracing/Riemann; FP64 state,
+                              flux-divergence accumulation and dual-energy sync */
+
+#define NYX_PERSISTENT 0   /* one persistent fused launch over all (box, tile) items */
+#define NYX_PER_BOX 1      /* plain FP64 stage-by-stage kernels, one box at a time */
+
+/* One grid of the level (Sec. 4.1): inclusive cell bounds lo..hi in the
+ * index space of its domain, even cell counts, cell widths dx. */
+typedef struct {
+  int lo[3], hi[3];
+  int domain;
+  double dx[3];
+} nyx_box;
+
+/* A domain: the region the boxes of one index space tile, with the kind of
+ * boundary on its lo x,y,z and hi x,y,z faces.  Boxes of one domain must
+ * not overlap; every ghost cell must map (after periodic wrap or outflow
+ * clamp) to a valid cell of some box of the same domain. */
+typedef struct {
+  int lo[3], hi[3];
+  int bc[6];
+} nyx_domain;
+
+typedef struct {
+  int nboxes;
+  int ng;                  /* ghost width: must be 4 (PPM stencil + corner coupling) */
+  const nyx_box *boxes;    /* host array, copied by nyx_hydro_plan */
+  int ndomains;
+  const nyx_domain *domains;
+} nyx_level_desc;
+
+typedef struct {
+  double gamma;            /* gamma-law EOS exponent, p = (gamma-1) rho e (Sec. 2.2) */
+  double cfl;              /* CFL factor sigma of Sec. 3.5, 0 < cfl < 1 */
+  double small_dens;       /* density floor of edge and Godunov states */
+  double small_pres;       /* pressure floor */
+  double eta_de;           /* dual-energy threshold (1e-4 in Sec. 3.2 / Step 6) */
+  int riemann_max_iter;    /* two-shock iteration cap */
+  double riemann_tol;      /* relative pressure tolerance (1e-10 FP64, 1e-6 mixed) */
+  int precision;           /* NYX_FP64 or NYX_MIXED */
+  int grav_corrector;      /* 1: Step 6 gravity corrector */
+  int batching;            /* NYX_PERSISTENT or NYX_PER_BOX */
+  int autotune;            /* 1: time the tile shapes once and keep the fastest */
+  int keep_fluxes;         /* 1: keep the final fluxes of the last advance */
+} nyx_hydro_params;
+
+typedef struct nyx_plan nyx_plan;
+
+/* Caller-owned device buffers of one level: two state versions (a stencil
+ * cannot update in place), gravity (may be NULL for g = 0), and which
+ * state version is current.  nyx_hydro_advance flips cur. */
+typedef struct {
+  double *state[2];
+  const double *grav;
+  int cur;
+} nyx_level;
+
+/* Fill *params with the defaults (gamma 5/3, cfl 0.5, small_dens 1e-10,
+ * small_pres 1e-12, eta_de 1e-4, 12 iterations, tol 1e-10, FP64,
+ * corrector on, persistent, autotune off, keep_fluxes off). */
+void nyx_hydro_default_params(nyx_hydro_params *params);
+
+/* Validate the level (Sec. 4.1: even positive extents, ng == 4, boxes of a
+ * domain disjoint and covering every ghost cell's image), copy it to the
+ * device, build the ghost-fill copy list and the batched work list, and
+ * allocate the plan's scratch.  stream: a cudaStream_t (NULL = legacy
+ * default stream).  *out receives the plan; NYX_EINVAL / NYX_ENOMEM /
+ * NYX_ECUDA on failure (no plan is returned). */
+int nyx_hydro_plan(const nyx_level_desc *level, const nyx_hydro_params *params,
+                   void *stream, nyx_plan **out);
+
+/* Offsets (in doubles) of each box's block in a field of ncomp components:
+ * off has nboxes+1 entries, off[nboxes] = total doubles to allocate.
+ * stride (nboxes entries, may be NULL) receives the component stride. */
+int nyx_hydro_layout(const nyx_plan *plan, int ncomp, size_t *off, size_t *stride);
+
+/* Fill the ghost cells of every box of a level field in place (ghost
+ * exchange of Sec. 4.1): copy from the box covering the same point after
+ * periodic wrap; zero-gradient copy across outflow faces.  Used by the
+ * advance on the state; callers use it once on gravity. */
+int nyx_hydro_fill(nyx_plan *plan, double *field, int ncomp);
+
+/* CFL time step of Sec. 3.5 for state[cur]:
+ *   *dt_dev = cfl * min over valid cells and d of a dx_d / (|U_d| + c)
+ * a_dev and dt_dev are device scalars (so the call can be graph captured). */
+int nyx_hydro_estdt(nyx_plan *plan, const nyx_level *level, const double *a_dev, double *dt_dev);
+
+/* One single-level hydro advance (Sec. 3.6 Steps 2 and 6, hydro part):
+ * ghost fill of state[cur], then state[1-cur] (valid cells) =
+ * advance(state[cur], g) from a_old to a_new over dt, then cur flips.
+ * a_old_dev, a_new_dev, dt_dev: device scalars.  grav_dev: device field of
+ * 3 components with ghosts filled; when NULL, level->grav is used, and
+ * when that is NULL too, g = 0.  dt_next_dev (may be NULL): receives the
+ * CFL step of the new state at a_new, computed in the same pass. */
+int nyx_hydro_advance(nyx_plan *plan, nyx_level *level, const double *a_old_dev,
+                      const double *a_new_dev, const double *dt_dev, const double *grav_dev,
+                      double *dt_next_dev);
+
+/* nsteps advances back to back.  a_dev holds a_0..a_nsteps; dt_dev holds
+ * nsteps+1 scalars: dt_dev[0] is the first step's dt (computed here by
+ * nyx_hydro_estdt if compute_dt0 != 0) and step s writes dt_dev[s+1].
+ * use_graph != 0 captures the sequence once into a CUDA graph (kept in the
+ * plan, keyed by the pointers and nsteps) and replays it. */
+int nyx_hydro_run(nyx_plan *plan, nyx_level *level, const double *a_dev, double *dt_dev,
+                  int nsteps, int compute_dt0, int use_graph);
+
+/* Final Godunov fluxes of the last advance through box `box` in direction
+ * dir (0,1,2): raw fluxes F (per unit area and time, not scaled by a or
+ * dt; reflux of Sec. 4.3 Step 8 scales them), components (rho, m_x, m_y,
+ * m_z, rhoE, rhoe), each an (n_d+1) x (other extents) array, x fastest,
+ * in out (device, 6 * (n_x+(d==0)) (n_y+(d==1)) (n_z+(d==2)) doubles).
+ * Needs keep_fluxes = 1 in the plan's parameters. */
+int nyx_hydro_fluxes(nyx_plan *plan, const nyx_level *level, int box, int dir, double *out);
+
+/* End-to-end step with HOST buffers: copy host_state_in (a whole level
+ * field of 6 components, layout as above, ghosts need not be filled) to
+ * state[cur], advance one step (dt from *dt_inout when > 0, else the CFL
+ * step of the input at a_old), copy the new state to host_state_out and the
+ * next step's CFL dt to *dt_inout.  Gravity is level->grav, resident on
+ * the device.  Synchronous.  Pinned host buffers give the full copy rate. */
+int nyx_hydro_step_host(nyx_plan *plan, nyx_level *level, const double *host_state_in,
+                        double *host_state_out, double a_old, double a_new, double *dt_inout);
+
+/* Tile shapes of the fused persistent kernel: shape index -> columns per
+ * work item (tx, ty).  nyx_hydro_tile_shape returns NYX_EINVAL for an index
+ * out of range; nyx_hydro_set_tile_shape fixes the plan's shape (and turns
+ * its autotuner off); nyx_hydro_get_tile_shape reports the shape in use. */
+int nyx_hydro_tile_shape(int shape, int *tx, int *ty);
+int nyx_hydro_set_tile_shape(nyx_plan *plan, int shape);
+int nyx_hydro_get_tile_shape(const nyx_plan *plan, int *shape);
+
+/* Counters of the plan: kernel launches it enqueued (graph replays count
+ * the kernels of the graph), and, while profiling is on, the summed CUDA
+ * event durations of its ghost fills and of its advance kernels (eager
+ * calls only; graph replays are not split by kernel).  read synchronises
+ * the stream; reset != 0 zeroes the counters after reading. */
+typedef struct {
+  long long launches;
+  long long timed_fills, timed_advances;
+  double fill_ms, advance_ms;
+} nyx_hydro_counters;
+int nyx_hydro_profile(nyx_plan *plan, int enable);
+int nyx_hydro_counters_read(nyx_plan *plan, int reset, nyx_hydro_counters *out);
+
+/* Synchronise the plan's stream, read and clear the device status word.
+ * *flags (may be NULL) receives its bits (1 negative density, 2 non-finite,
+ * 4 queue overrun, 8 timeout).  Returns NYX_OK, or the NYX_E* code of the
+ * most severe raised bit. */
+int nyx_hydro_status(nyx_plan *plan, int *flags);
+
+/* Release the plan's device and host resources (not the caller's buffers). */
+int nyx_plan_destroy(nyx_plan *plan);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *nyx_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

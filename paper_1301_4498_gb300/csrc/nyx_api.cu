@@ -1,0 +1,910 @@
+// nyx_api.cu -- host side of libnyxhydro.so: level validation, the ghost-fill
+// copy list, the batched work list (largest boxes first, as a knapsack-style
+// balance of the paper's Sec. 5.1 distribution), CUDA-graph capture, status
+// and the C ABI of include/nyx_hydro.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "nyx_hydro.h"
+#include "nyx_internal.cuh"
+#include "nyx_kernels.h"
+
+using namespace nyx;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  return fail(NYX_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                    \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+struct FillPass {
+  FillRect *d_rects = nullptr;
+  long long *d_pref = nullptr;
+  int n = 0;
+  long long total = 0;
+};
+
+using GraphKey = std::tuple<const void *, const void *, const void *, int, const void *, const void *,
+                            int, int>;
+
+}  // namespace
+
+struct nyx_plan {
+  int nbox = 0;
+  std::vector<nyx_box> boxes;
+  std::vector<nyx_domain> doms;
+  nyx_hydro_params prm{};
+  cudaStream_t stream = nullptr;
+  std::vector<BoxDev> hbox;
+  std::vector<long long> cell_pref;
+  long long total_cells = 0;
+  long long total_stride = 0;
+  BoxDev *d_boxes = nullptr;
+  long long *d_cell_pref = nullptr;
+  SchemeConsts hK{};
+  SchemeConsts *d_K = nullptr;
+  StepConsts *d_SC = nullptr;
+  BoxStep *d_BS = nullptr;
+  unsigned long long *d_dtacc = nullptr;
+  unsigned *d_status = nullptr;
+  double *d_scal = nullptr;  // host-call scalars: a_old, a_new, dt, dt_next
+  FillPass pass[4];
+  // per-box FP64 form
+  double *d_scratch = nullptr;
+  long long Vmax = 0;
+  // final-flux store
+  double *d_flux = nullptr;
+  std::vector<long long> flux_off;
+  long long *d_flux_off = nullptr;
+  bool flux_valid = false;
+  // fused persistent form
+  WorkItem *d_items[8] = {nullptr};
+  int nitems[8] = {0};
+  int *d_queue = nullptr;
+  int shape = 0;
+  bool tuned = false;
+  int max_grid[8] = {0};
+  std::map<GraphKey, std::pair<cudaGraphExec_t, long long>> graphs;  // graph, kernels in it
+  // counters and profiling
+  long long launches = 0;
+  bool profiling = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_fill, ev_adv;
+};
+
+namespace {
+
+long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
+
+bool intersect(const int alo[3], const int ahi[3], const int blo[3], const int bhi[3], int olo[3],
+               int ohi[3]) {
+  for (int d = 0; d < 3; ++d) {
+    olo[d] = std::max(alo[d], blo[d]);
+    ohi[d] = std::min(ahi[d], bhi[d]);
+    if (olo[d] > ohi[d]) return false;
+  }
+  return true;
+}
+
+// Build the ghost-fill rectangles of every box: pass 0 = copies from boxes
+// of the same domain (with periodic images), passes 1..3 = zero-gradient
+// outflow along x, y, z.  Returns false (with g_err set) if the ghost cells
+// of some box are not covered exactly once.
+bool build_fill(const nyx_plan &P, std::vector<FillRect> out[4]) {
+  const int ng = 4;
+  const int nd = (int)P.doms.size();
+  // boxes of each domain and a uniform bin grid per domain
+  std::vector<std::vector<int>> dboxes(nd);
+  for (int b = 0; b < P.nbox; ++b) dboxes[P.boxes[b].domain].push_back(b);
+  struct Bins {
+    int bs = 1, nb[3] = {1, 1, 1};
+    std::vector<std::vector<int>> cell;
+  };
+  std::vector<Bins> bins(nd);
+  for (int d = 0; d < nd; ++d) {
+    const nyx_domain &D = P.doms[d];
+    int bs = 1;
+    for (int b : dboxes[d])
+      for (int a = 0; a < 3; ++a) bs = std::max(bs, P.boxes[b].hi[a] - P.boxes[b].lo[a] + 1);
+    Bins &B = bins[d];
+    B.bs = bs;
+    for (int a = 0; a < 3; ++a) B.nb[a] = (D.hi[a] - D.lo[a] + 1 + bs - 1) / bs;
+    B.cell.assign((size_t)B.nb[0] * B.nb[1] * B.nb[2], {});
+    for (int b : dboxes[d]) {
+      int l[3], h[3];
+      for (int a = 0; a < 3; ++a) {
+        l[a] = (P.boxes[b].lo[a] - D.lo[a]) / bs;
+        h[a] = (P.boxes[b].hi[a] - D.lo[a]) / bs;
+      }
+      for (int k = l[2]; k <= h[2]; ++k)
+        for (int j = l[1]; j <= h[1]; ++j)
+          for (int i = l[0]; i <= h[0]; ++i)
+            B.cell[((size_t)k * B.nb[1] + j) * B.nb[0] + i].push_back(b);
+    }
+  }
+  std::vector<int> stamp(P.nbox, -1);
+  int stamp_id = 0;
+  for (int b = 0; b < P.nbox; ++b) {
+    const nyx_box &X = P.boxes[b];
+    const nyx_domain &D = P.doms[X.domain];
+    const Bins &B = bins[X.domain];
+    int glo[3], ghi[3], L[3];
+    long long ghost = 1, valid = 1;
+    for (int a = 0; a < 3; ++a) {
+      glo[a] = X.lo[a] - ng;
+      ghi[a] = X.hi[a] + ng;
+      L[a] = D.hi[a] - D.lo[a] + 1;
+      ghost *= (ghi[a] - glo[a] + 1);
+      valid *= (X.hi[a] - X.lo[a] + 1);
+    }
+    ghost -= valid;
+    long long covered = 0;
+    int smin[3], smax[3];
+    for (int a = 0; a < 3; ++a) {
+      bool per = D.bc[a] == NYX_BC_PERIODIC;
+      smin[a] = per ? -1 : 0;
+      smax[a] = per ? 1 : 0;
+    }
+    for (int sz = smin[2]; sz <= smax[2]; ++sz)
+      for (int sy = smin[1]; sy <= smax[1]; ++sy)
+        for (int sx = smin[0]; sx <= smax[0]; ++sx) {
+          int sh[3] = {sx * L[0], sy * L[1], sz * L[2]};
+          // candidate boxes: bins overlapping the grown box shifted back
+          int ql[3], qh[3];
+          bool any = true;
+          for (int a = 0; a < 3; ++a) {
+            int lo = std::max(glo[a] - sh[a], D.lo[a]);
+            int hi = std::min(ghi[a] - sh[a], D.hi[a]);
+            if (lo > hi) any = false;
+            ql[a] = (lo - D.lo[a]) / B.bs;
+            qh[a] = (hi - D.lo[a]) / B.bs;
+          }
+          if (!any) continue;
+          ++stamp_id;
+          for (int k = ql[2]; k <= qh[2]; ++k)
+            for (int j = ql[1]; j <= qh[1]; ++j)
+              for (int i = ql[0]; i <= qh[0]; ++i)
+                for (int c : B.cell[((size_t)k * B.nb[1] + j) * B.nb[0] + i]) {
+                  if (stamp[c] == stamp_id) continue;
+                  stamp[c] = stamp_id;
+                  if (c == b && sx == 0 && sy == 0 && sz == 0) continue;
+                  const nyx_box &Y = P.boxes[c];
+                  int rlo[3], rhi[3], olo[3], ohi[3];
+                  for (int a = 0; a < 3; ++a) {
+                    rlo[a] = Y.lo[a] + sh[a];
+                    rhi[a] = Y.hi[a] + sh[a];
+                  }
+                  if (!intersect(glo, ghi, rlo, rhi, olo, ohi)) continue;
+                  FillRect R;
+                  R.dst_box = b;
+                  R.src_box = c;
+                  for (int a = 0; a < 3; ++a) {
+                    R.dlo[a] = olo[a] - X.lo[a];
+                    R.ext[a] = ohi[a] - olo[a] + 1;
+                    R.slo[a] = olo[a] - sh[a] - Y.lo[a];
+                    R.sstep[a] = 1;
+                  }
+                  // a copy into the box's own valid cells means overlapping boxes
+                  int vlo[3], vhi[3];
+                  int xl[3] = {X.lo[0], X.lo[1], X.lo[2]}, xh[3] = {X.hi[0], X.hi[1], X.hi[2]};
+                  if (intersect(olo, ohi, xl, xh, vlo, vhi)) {
+                    g_err = "boxes " + std::to_string(b) + " and " + std::to_string(c) +
+                            " overlap (or a periodic domain is narrower than the ghost width)";
+                    return false;
+                  }
+                  covered += (long long)R.ext[0] * R.ext[1] * R.ext[2];
+                  out[0].push_back(R);
+                }
+        }
+    // outflow passes: axis a, low and high sides touching the domain boundary
+    for (int a = 0; a < 3; ++a) {
+      for (int side = 0; side < 2; ++side) {
+        int bc = D.bc[side ? 3 + a : a];
+        bool touch = side ? (X.hi[a] == D.hi[a]) : (X.lo[a] == D.lo[a]);
+        if (bc != NYX_BC_OUTFLOW || !touch) continue;
+        FillRect R;
+        R.dst_box = b;
+        R.src_box = b;
+        int n[3] = {X.hi[0] - X.lo[0] + 1, X.hi[1] - X.lo[1] + 1, X.hi[2] - X.lo[2] + 1};
+        for (int e = 0; e < 3; ++e) {
+          if (e == a) {
+            R.dlo[e] = side ? n[e] : -ng;
+            R.ext[e] = ng;
+            R.slo[e] = side ? n[e] - 1 : 0;
+            R.sstep[e] = 0;
+          } else {
+            // axes handled by a later pass stay inside the domain here
+            int lo = -ng, hi = n[e] + ng - 1;
+            if (e > a) {
+              if (D.bc[e] == NYX_BC_OUTFLOW && X.lo[e] == D.lo[e]) lo = 0;
+              if (D.bc[3 + e] == NYX_BC_OUTFLOW && X.hi[e] == D.hi[e]) hi = n[e] - 1;
+            }
+            R.dlo[e] = lo;
+            R.ext[e] = hi - lo + 1;
+            R.slo[e] = lo;
+            R.sstep[e] = 1;
+          }
+        }
+        covered += (long long)R.ext[0] * R.ext[1] * R.ext[2];
+        out[1 + a].push_back(R);
+      }
+    }
+    if (covered != ghost) {
+      g_err = "ghost cells of box " + std::to_string(b) + " covered " + std::to_string(covered) +
+              " times in total, expected " + std::to_string(ghost) +
+              " (gap, overlap or unsupported boundary)";
+      return false;
+    }
+  }
+  return true;
+}
+
+int upload_pass(FillPass &p, const std::vector<FillRect> &rects) {
+  p.n = (int)rects.size();
+  if (!p.n) return NYX_OK;
+  std::vector<long long> pref(p.n);
+  long long acc = 0;
+  for (int i = 0; i < p.n; ++i) {
+    pref[i] = acc;
+    acc += (long long)rects[i].ext[0] * rects[i].ext[1] * rects[i].ext[2];
+  }
+  p.total = acc;
+  CK(cudaMalloc(&p.d_rects, sizeof(FillRect) * p.n));
+  CK(cudaMalloc(&p.d_pref, sizeof(long long) * p.n));
+  CK(cudaMemcpy(p.d_rects, rects.data(), sizeof(FillRect) * p.n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p.d_pref, pref.data(), sizeof(long long) * p.n, cudaMemcpyHostToDevice));
+  return NYX_OK;
+}
+
+// Work list of the fused kernel for one tile shape: every box cut into
+// tx x ty column tiles, ordered largest work first (LPT).
+std::vector<WorkItem> build_items(const nyx_plan &P, int tx, int ty) {
+  std::vector<WorkItem> items;
+  for (int b = 0; b < P.nbox; ++b) {
+    const BoxDev &X = P.hbox[b];
+    for (int y0 = 0; y0 < X.n[1]; y0 += ty)
+      for (int x0 = 0; x0 < X.n[0]; x0 += tx) {
+        WorkItem w;
+        w.box = b;
+        w.x0 = x0;
+        w.y0 = y0;
+        w.nx = std::min(tx, X.n[0] - x0);
+        w.ny = std::min(ty, X.n[1] - y0);
+        w.pad = 0;
+        items.push_back(w);
+      }
+  }
+  std::stable_sort(items.begin(), items.end(), [&](const WorkItem &a, const WorkItem &b) {
+    long long wa = (long long)(a.nx + 2) * (a.ny + 2) * (P.hbox[a.box].n[2] + 2);
+    long long wb = (long long)(b.nx + 2) * (b.ny + 2) * (P.hbox[b.box].n[2] + 2);
+    return wa > wb;
+  });
+  return items;
+}
+
+void free_plan(nyx_plan *P) {
+  if (!P) return;
+  for (auto &kv : P->graphs) cudaGraphExecDestroy(kv.second.first);
+  for (auto &e : P->ev_fill) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  for (auto &e : P->ev_adv) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  cudaFree(P->d_boxes);
+  cudaFree(P->d_cell_pref);
+  cudaFree(P->d_K);
+  cudaFree(P->d_SC);
+  cudaFree(P->d_BS);
+  cudaFree(P->d_dtacc);
+  cudaFree(P->d_status);
+  cudaFree(P->d_scal);
+  for (auto &p : P->pass) {
+    cudaFree(p.d_rects);
+    cudaFree(p.d_pref);
+  }
+  cudaFree(P->d_scratch);
+  cudaFree(P->d_flux);
+  cudaFree(P->d_flux_off);
+  for (auto &it : P->d_items) cudaFree(it);
+  cudaFree(P->d_queue);
+  delete P;
+}
+
+bool capturing(nyx_plan *P) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(P->stream, &cs);
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+// Event pair around a span of launches when profiling an eager call.
+struct Span {
+  nyx_plan *P;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *list;
+  cudaEvent_t e0 = nullptr;
+  Span(nyx_plan *P_, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *l) : P(P_), list(l) {
+    if (P->profiling && !capturing(P)) {
+      cudaEventCreate(&e0);
+      cudaEventRecord(e0, P->stream);
+    }
+  }
+  ~Span() {
+    if (e0) {
+      cudaEvent_t e1;
+      cudaEventCreate(&e1);
+      cudaEventRecord(e1, P->stream);
+      list->emplace_back(e0, e1);
+    }
+  }
+};
+
+int do_fill(nyx_plan *P, double *field, int ncomp) {
+  Span sp(P, &P->ev_fill);
+  for (int p = 0; p < 4; ++p) {
+    launch_fill(field, ncomp, P->d_boxes, P->pass[p].d_rects, P->pass[p].d_pref, P->pass[p].n,
+                P->pass[p].total, P->stream);
+    if (P->pass[p].n > 0 && P->pass[p].total > 0) P->launches += 1;
+  }
+  return NYX_OK;
+}
+
+int do_estdt(nyx_plan *P, const double *state, const double *a_dev, double *dt_dev) {
+  launch_estdt(P->d_boxes, P->d_cell_pref, P->nbox, P->total_cells, state, P->d_K, a_dev,
+               P->d_dtacc, P->stream);
+  launch_dt_finalize(P->d_K, P->d_dtacc, dt_dev, P->stream);
+  P->launches += 2;
+  return NYX_OK;
+}
+
+int tune_shape(nyx_plan *P, const FusedArgs &base);
+
+int do_advance(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_new,
+               const double *dt, const double *grav, double *dt_next) {
+  double *S = L->state[L->cur];
+  double *Sn = L->state[1 - L->cur];
+  const double *G = grav ? grav : L->grav;
+  do_fill(P, S, NCONS);
+  launch_step_setup(P->d_K, a_old, a_new, dt, P->d_SC, P->d_boxes, P->nbox, P->d_BS, P->stream);
+  P->launches += 1;
+  unsigned long long *acc = dt_next ? P->d_dtacc : nullptr;
+  {
+  Span sp(P, &P->ev_adv);
+  if (P->prm.batching == NYX_PER_BOX) {
+    for (int b = 0; b < P->nbox; ++b) {
+      const BoxDev &X = P->hbox[b];
+      launch_staged_box(X, P->d_boxes + b, P->d_K, P->d_SC, P->d_BS + b, S + NCONS * X.pref,
+                        G ? G + NGRAV * X.pref : nullptr, Sn + NCONS * X.pref, P->d_scratch,
+                        P->Vmax, acc, P->d_status,
+                        P->d_flux ? P->d_flux + P->flux_off[b] : nullptr, P->stream);
+      P->launches += P->d_flux ? 29 : 26;
+    }
+  } else {
+    FusedArgs a;
+    a.boxes = P->d_boxes;
+    a.queue = P->d_queue;
+    a.K = P->d_K;
+    a.SC = P->d_SC;
+    a.BS = P->d_BS;
+    a.S = S;
+    a.G = G;
+    a.Sn = Sn;
+    a.dtacc = acc;
+    a.status = P->d_status;
+    a.flux_keep = P->d_flux;
+    a.flux_off = P->d_flux_off;
+    if (P->prm.autotune && !P->tuned) {
+      int rc = tune_shape(P, a);
+      if (rc) return rc;
+    }
+    a.items = P->d_items[P->shape];
+    a.nitems = P->nitems[P->shape];
+    int grid = std::min(P->max_grid[P->shape], a.nitems);
+    int e = launch_fused(P->prm.precision, P->shape, a, grid, P->stream);
+    if (e) return cuda_fail((cudaError_t)e, "fused advance launch");
+    P->launches += 1;
+  }
+  }
+  if (dt_next) {
+    launch_dt_finalize(P->d_K, P->d_dtacc, dt_next, P->stream);
+    P->launches += 1;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "advance launch");
+  P->flux_valid = P->d_flux != nullptr;
+  L->cur = 1 - L->cur;
+  return NYX_OK;
+}
+
+// Time every tile shape on the plan's level once (state is only read;
+// the output buffer is overwritten) and keep the fastest.
+int tune_shape(nyx_plan *P, const FusedArgs &base) {
+  P->tuned = true;
+  cudaStreamCaptureStatus cs;
+  CK(cudaStreamIsCapturing(P->stream, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return NYX_OK;  // keep the current shape under capture
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_s = P->shape;
+  for (int s = 0; s < fused_num_shapes(); ++s) {
+    FusedArgs a = base;
+    a.items = P->d_items[s];
+    a.nitems = P->nitems[s];
+    a.dtacc = nullptr;
+    a.flux_keep = nullptr;
+    int grid = std::min(P->max_grid[s], a.nitems);
+    float tot = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {
+      CK(cudaEventRecord(e0, P->stream));
+      int e = launch_fused(P->prm.precision, s, a, grid, P->stream);
+      if (e) return cuda_fail((cudaError_t)e, "autotune launch");
+      P->launches += 1;
+      CK(cudaEventRecord(e1, P->stream));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep > 0) tot += ms;
+    }
+    if (tot < best) {
+      best = tot;
+      best_s = s;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  P->shape = best_s;
+  return NYX_OK;
+}
+
+int enqueue_run(nyx_plan *P, nyx_level *L, const double *a_dev, double *dt_dev, int nsteps,
+                int compute_dt0) {
+  if (compute_dt0) do_estdt(P, L->state[L->cur], a_dev, dt_dev);
+  for (int s = 0; s < nsteps; ++s) {
+    int rc = do_advance(P, L, a_dev + s, a_dev + s + 1, dt_dev + s, nullptr, dt_dev + s + 1);
+    if (rc) return rc;
+  }
+  return NYX_OK;
+}
+
+}  // namespace
+
+// ====================================================================== fused dispatch
+namespace nyx {
+
+static const TileShape kShapes[] = {{16, 16}, {32, 8}, {16, 8}};
+
+int fused_num_shapes() { return 3; }
+TileShape fused_shape(int idx) { return kShapes[idx]; }
+
+int launch_fused(int precision, int shape, const FusedArgs &a, int grid, cudaStream_t st) {
+  if (grid < 1) grid = 1;
+  return precision == NYX_MIXED ? launch_fused_mixed(shape, a, grid, st)
+                                : launch_fused_f64(shape, a, grid, st);
+}
+
+int fused_max_grid(int precision, int shape) {
+  return precision == NYX_MIXED ? max_grid_mixed(shape) : max_grid_f64(shape);
+}
+
+}  // namespace nyx
+
+// ====================================================================== C ABI
+extern "C" {
+
+void nyx_hydro_default_params(nyx_hydro_params *p) {
+  if (!p) return;
+  p->gamma = 5.0 / 3.0;
+  p->cfl = 0.5;
+  p->small_dens = 1e-10;
+  p->small_pres = 1e-12;
+  p->eta_de = 1e-4;
+  p->riemann_max_iter = 12;
+  p->riemann_tol = 1e-10;
+  p->precision = NYX_FP64;
+  p->grav_corrector = 1;
+  p->batching = NYX_PERSISTENT;
+  p->autotune = 0;
+  p->keep_fluxes = 0;
+}
+
+const char *nyx_last_error(void) { return g_err.c_str(); }
+
+int nyx_hydro_plan(const nyx_level_desc *lev, const nyx_hydro_params *prm, void *stream,
+                   nyx_plan **out) {
+  g_err.clear();
+  if (!lev || !prm || !out) return fail(NYX_EINVAL, "null argument");
+  *out = nullptr;
+  if (lev->nboxes <= 0 || !lev->boxes) return fail(NYX_EINVAL, "level has no boxes");
+  if (lev->ndomains <= 0 || !lev->domains) return fail(NYX_EINVAL, "level has no domains");
+  if (lev->ng != 4) return fail(NYX_EINVAL, "ghost width must be 4");
+  if (!(prm->gamma > 1.0) || !(prm->cfl > 0.0 && prm->cfl <= 1.0) || !(prm->small_dens > 0.0) ||
+      !(prm->small_pres > 0.0) || !(prm->eta_de >= 0.0) || prm->riemann_max_iter < 1 ||
+      !(prm->riemann_tol > 0.0))
+    return fail(NYX_EINVAL, "invalid scheme parameters");
+  if (prm->precision != NYX_FP64 && prm->precision != NYX_MIXED)
+    return fail(NYX_EINVAL, "precision must be NYX_FP64 or NYX_MIXED");
+  if (prm->batching != NYX_PERSISTENT && prm->batching != NYX_PER_BOX)
+    return fail(NYX_EINVAL, "batching must be NYX_PERSISTENT or NYX_PER_BOX");
+  if (prm->batching == NYX_PER_BOX && prm->precision != NYX_FP64)
+    return fail(NYX_EINVAL, "the per-box form is FP64 only");
+  for (int d = 0; d < lev->ndomains; ++d) {
+    const nyx_domain &D = lev->domains[d];
+    for (int a = 0; a < 3; ++a) {
+      if (D.hi[a] < D.lo[a]) return fail(NYX_EINVAL, "empty domain " + std::to_string(d));
+      for (int s = 0; s < 2; ++s) {
+        int bc = D.bc[s * 3 + a];
+        if (bc != NYX_BC_PERIODIC && bc != NYX_BC_OUTFLOW)
+          return fail(NYX_EINVAL, "unknown boundary kind in domain " + std::to_string(d));
+      }
+      if ((D.bc[a] == NYX_BC_PERIODIC) != (D.bc[3 + a] == NYX_BC_PERIODIC))
+        return fail(NYX_EINVAL, "periodic boundaries must come in pairs");
+      if (D.bc[a] == NYX_BC_PERIODIC && D.hi[a] - D.lo[a] + 1 < 4)
+        return fail(NYX_EINVAL, "periodic domain narrower than the ghost width");
+    }
+  }
+  for (int b = 0; b < lev->nboxes; ++b) {
+    const nyx_box &X = lev->boxes[b];
+    if (X.domain < 0 || X.domain >= lev->ndomains)
+      return fail(NYX_EINVAL, "box " + std::to_string(b) + " has an invalid domain");
+    const nyx_domain &D = lev->domains[X.domain];
+    for (int a = 0; a < 3; ++a) {
+      int n = X.hi[a] - X.lo[a] + 1;
+      if (n <= 0 || (n & 1))
+        return fail(NYX_EINVAL, "box " + std::to_string(b) + " extent must be even and positive");
+      if (X.lo[a] < D.lo[a] || X.hi[a] > D.hi[a])
+        return fail(NYX_EINVAL, "box " + std::to_string(b) + " lies outside its domain");
+      if (!(X.dx[a] > 0.0) || !std::isfinite(X.dx[a]))
+        return fail(NYX_EINVAL, "box " + std::to_string(b) + " has a non-positive dx");
+    }
+  }
+  nyx_plan *P = new nyx_plan();
+  P->nbox = lev->nboxes;
+  P->boxes.assign(lev->boxes, lev->boxes + lev->nboxes);
+  P->doms.assign(lev->domains, lev->domains + lev->ndomains);
+  P->prm = *prm;
+  P->stream = (cudaStream_t)stream;
+  // layout
+  long long pref = 0, cells = 0;
+  P->hbox.resize(P->nbox);
+  P->cell_pref.resize(P->nbox);
+  for (int b = 0; b < P->nbox; ++b) {
+    BoxDev &X = P->hbox[b];
+    for (int a = 0; a < 3; ++a) {
+      X.n[a] = P->boxes[b].hi[a] - P->boxes[b].lo[a] + 1;
+      X.N[a] = X.n[a] + 8;
+      X.dx[a] = P->boxes[b].dx[a];
+      X.idx[a] = 1.0 / X.dx[a];
+    }
+    X.stride = round_up((long long)X.N[0] * X.N[1] * X.N[2], 32);
+    X.pref = pref;
+    pref += X.stride;
+    P->cell_pref[b] = cells;
+    cells += (long long)X.n[0] * X.n[1] * X.n[2];
+    P->Vmax = std::max(P->Vmax, X.stride);
+  }
+  P->total_cells = cells;
+  P->total_stride = pref;
+  std::vector<FillRect> rects[4];
+  if (!build_fill(*P, rects)) {
+    std::string m = g_err;
+    free_plan(P);
+    return fail(NYX_EINVAL, m);
+  }
+  int rc = NYX_OK;
+#define TRY(x)              \
+  do {                      \
+    rc = (x);               \
+    if (rc) goto fail_out;  \
+  } while (0)
+#define TRYC(x)                                                  \
+  do {                                                           \
+    cudaError_t e_ = (x);                                        \
+    if (e_ != cudaSuccess) {                                     \
+      rc = (e_ == cudaErrorMemoryAllocation)                     \
+               ? fail(NYX_ENOMEM, std::string("device allocation failed: ") + #x) \
+               : cuda_fail(e_, #x);                              \
+      goto fail_out;                                             \
+    }                                                            \
+  } while (0)
+  {
+    for (int p = 0; p < 4; ++p) TRY(upload_pass(P->pass[p], rects[p]));
+    TRYC(cudaMalloc(&P->d_boxes, sizeof(BoxDev) * P->nbox));
+    TRYC(cudaMemcpy(P->d_boxes, P->hbox.data(), sizeof(BoxDev) * P->nbox, cudaMemcpyHostToDevice));
+    TRYC(cudaMalloc(&P->d_cell_pref, sizeof(long long) * P->nbox));
+    TRYC(cudaMemcpy(P->d_cell_pref, P->cell_pref.data(), sizeof(long long) * P->nbox,
+                    cudaMemcpyHostToDevice));
+    SchemeConsts &K = P->hK;
+    K.gamma = prm->gamma;
+    K.gm1 = prm->gamma - 1.0;
+    K.igm1 = 1.0 / K.gm1;
+    K.kshock = (prm->gamma + 1.0) / (2.0 * prm->gamma);
+    K.small_dens = prm->small_dens;
+    K.small_pres = prm->small_pres;
+    K.tol = prm->riemann_tol;
+    K.tol_mixed = std::max(prm->riemann_tol, 1e-6);  // FP32 cannot resolve tighter
+    K.eta_de = prm->eta_de;
+    K.cfl = prm->cfl;
+    K.kappa = 2.0 - 3.0 * K.gm1;
+    K.efloor = prm->small_pres * K.igm1;
+    K.max_iter = prm->riemann_max_iter;
+    K.grav_corrector = prm->grav_corrector;
+    TRYC(cudaMalloc(&P->d_K, sizeof(SchemeConsts)));
+    TRYC(cudaMemcpy(P->d_K, &K, sizeof(SchemeConsts), cudaMemcpyHostToDevice));
+    TRYC(cudaMalloc(&P->d_SC, sizeof(StepConsts)));
+    TRYC(cudaMalloc(&P->d_BS, sizeof(BoxStep) * P->nbox));
+    TRYC(cudaMalloc(&P->d_dtacc, sizeof(unsigned long long)));
+    unsigned long long inf = 0x7ff0000000000000ULL;
+    TRYC(cudaMemcpy(P->d_dtacc, &inf, sizeof(inf), cudaMemcpyHostToDevice));
+    TRYC(cudaMalloc(&P->d_status, sizeof(unsigned)));
+    TRYC(cudaMemset(P->d_status, 0, sizeof(unsigned)));
+    TRYC(cudaMalloc(&P->d_scal, 4 * sizeof(double)));
+    if (prm->batching == NYX_PER_BOX) {
+      TRYC(cudaMalloc(&P->d_scratch, sizeof(double) * staged_scratch_doubles(P->Vmax)));
+    } else {
+      for (int s = 0; s < fused_num_shapes(); ++s) {
+        TileShape ts = fused_shape(s);
+        std::vector<WorkItem> it = build_items(*P, ts.tx, ts.ty);
+        P->nitems[s] = (int)it.size();
+        TRYC(cudaMalloc(&P->d_items[s], sizeof(WorkItem) * it.size()));
+        TRYC(cudaMemcpy(P->d_items[s], it.data(), sizeof(WorkItem) * it.size(),
+                        cudaMemcpyHostToDevice));
+      }
+      TRYC(cudaMalloc(&P->d_queue, sizeof(int)));
+      TRYC(cudaMemset(P->d_queue, 0, sizeof(int)));
+      for (int sh = 0; sh < fused_num_shapes(); ++sh)
+        P->max_grid[sh] = fused_max_grid(prm->precision, sh);
+      TRYC(cudaGetLastError());
+    }
+    if (prm->keep_fluxes) {
+      long long acc = 0;
+      P->flux_off.resize(P->nbox);
+      for (int b = 0; b < P->nbox; ++b) {
+        P->flux_off[b] = acc;
+        const BoxDev &X = P->hbox[b];
+        for (int d = 0; d < 3; ++d)
+          acc += 6LL * (X.n[0] + (d == 0)) * (X.n[1] + (d == 1)) * (X.n[2] + (d == 2));
+      }
+      TRYC(cudaMalloc(&P->d_flux, sizeof(double) * acc));
+      TRYC(cudaMalloc(&P->d_flux_off, sizeof(long long) * P->nbox));
+      TRYC(cudaMemcpy(P->d_flux_off, P->flux_off.data(), sizeof(long long) * P->nbox,
+                      cudaMemcpyHostToDevice));
+    }
+  }
+  *out = P;
+  return NYX_OK;
+fail_out:
+  free_plan(P);
+  return rc;
+#undef TRY
+#undef TRYC
+}
+
+int nyx_hydro_layout(const nyx_plan *P, int ncomp, size_t *off, size_t *stride) {
+  if (!P || !off || ncomp <= 0) return fail(NYX_EINVAL, "null argument or ncomp <= 0");
+  for (int b = 0; b < P->nbox; ++b) {
+    off[b] = (size_t)ncomp * (size_t)P->hbox[b].pref;
+    if (stride) stride[b] = (size_t)P->hbox[b].stride;
+  }
+  off[P->nbox] = (size_t)ncomp * (size_t)P->total_stride;
+  return NYX_OK;
+}
+
+int nyx_hydro_fill(nyx_plan *P, double *field, int ncomp) {
+  if (!P || !field || ncomp <= 0) return fail(NYX_EINVAL, "null argument or ncomp <= 0");
+  do_fill(P, field, ncomp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "ghost fill launch");
+  return NYX_OK;
+}
+
+int nyx_hydro_estdt(nyx_plan *P, const nyx_level *L, const double *a_dev, double *dt_dev) {
+  if (!P || !L || !a_dev || !dt_dev || !L->state[L->cur & 1])
+    return fail(NYX_EINVAL, "null argument");
+  do_estdt(P, L->state[L->cur & 1], a_dev, dt_dev);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "estdt launch");
+  return NYX_OK;
+}
+
+int nyx_hydro_advance(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_new,
+                      const double *dt, const double *grav, double *dt_next) {
+  if (!P || !L || !a_old || !a_new || !dt) return fail(NYX_EINVAL, "null argument");
+  if ((L->cur != 0 && L->cur != 1) || !L->state[0] || !L->state[1] || L->state[0] == L->state[1])
+    return fail(NYX_EINVAL, "level needs two distinct state buffers and cur in {0,1}");
+  return do_advance(P, L, a_old, a_new, dt, grav, dt_next);
+}
+
+int nyx_hydro_run(nyx_plan *P, nyx_level *L, const double *a_dev, double *dt_dev, int nsteps,
+                  int compute_dt0, int use_graph) {
+  if (!P || !L || !a_dev || !dt_dev || nsteps < 0) return fail(NYX_EINVAL, "null argument");
+  if ((L->cur != 0 && L->cur != 1) || !L->state[0] || !L->state[1] || L->state[0] == L->state[1])
+    return fail(NYX_EINVAL, "level needs two distinct state buffers and cur in {0,1}");
+  if (!use_graph) return enqueue_run(P, L, a_dev, dt_dev, nsteps, compute_dt0);
+  if (P->prm.batching == NYX_PERSISTENT && P->prm.autotune && !P->tuned) {
+    // tune outside the capture: one eager step on scratch copies is not
+    // possible without the caller's buffers, so tune on the real ones and
+    // redo the work below (the tuning launches only write state[1-cur]).
+    FusedArgs a{};
+    a.boxes = P->d_boxes;
+    a.queue = P->d_queue;
+    a.K = P->d_K;
+    a.SC = P->d_SC;
+    a.BS = P->d_BS;
+    a.S = L->state[L->cur];
+    a.G = L->grav;
+    a.Sn = L->state[1 - L->cur];
+    a.status = P->d_status;
+    do_fill(P, L->state[L->cur], NCONS);
+    launch_step_setup(P->d_K, a_dev, a_dev + 1, a_dev, P->d_SC, P->d_boxes, P->nbox, P->d_BS,
+                      P->stream);
+    int rc = tune_shape(P, a);
+    if (rc) return rc;
+  }
+  GraphKey key(L->state[0], L->state[1], L->grav, L->cur, a_dev, dt_dev, nsteps, compute_dt0);
+  auto it = P->graphs.find(key);
+  if (it == P->graphs.end()) {
+    nyx_level tmp = *L;
+    long long before = P->launches;
+    CK(cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_run(P, &tmp, a_dev, dt_dev, nsteps, compute_dt0);
+    long long in_graph = P->launches - before;
+    P->launches = before;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(P->stream, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+    cudaGraphExec_t ge = nullptr;
+    e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    it = P->graphs.emplace(key, std::make_pair(ge, in_graph)).first;
+  }
+  CK(cudaGraphLaunch(it->second.first, P->stream));
+  P->launches += it->second.second;
+  L->cur = (L->cur + nsteps) & 1;
+  P->flux_valid = P->d_flux != nullptr;
+  return NYX_OK;
+}
+
+int nyx_hydro_fluxes(nyx_plan *P, const nyx_level *L, int box, int dir, double *out) {
+  (void)L;
+  if (!P || !out) return fail(NYX_EINVAL, "null argument");
+  if (box < 0 || box >= P->nbox || dir < 0 || dir > 2) return fail(NYX_EINVAL, "box or dir out of range");
+  if (!P->d_flux) return fail(NYX_EINVAL, "plan was made without keep_fluxes");
+  if (!P->flux_valid) return fail(NYX_EINVAL, "no advance has run yet");
+  const BoxDev &X = P->hbox[box];
+  long long off = P->flux_off[box];
+  for (int d = 0; d < dir; ++d)
+    off += 6LL * (X.n[0] + (d == 0)) * (X.n[1] + (d == 1)) * (X.n[2] + (d == 2));
+  long long n = 6LL * (X.n[0] + (dir == 0)) * (X.n[1] + (dir == 1)) * (X.n[2] + (dir == 2));
+  CK(cudaMemcpyAsync(out, P->d_flux + off, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                     P->stream));
+  return NYX_OK;
+}
+
+int nyx_hydro_step_host(nyx_plan *P, nyx_level *L, const double *host_in, double *host_out,
+                        double a_old, double a_new, double *dt_inout) {
+  if (!P || !L || !host_in || !host_out || !dt_inout) return fail(NYX_EINVAL, "null argument");
+  if ((L->cur != 0 && L->cur != 1) || !L->state[0] || !L->state[1] || L->state[0] == L->state[1])
+    return fail(NYX_EINVAL, "level needs two distinct state buffers and cur in {0,1}");
+  size_t bytes = sizeof(double) * (size_t)NCONS * (size_t)P->total_stride;
+  double h[3] = {a_old, a_new, *dt_inout};
+  CK(cudaMemcpyAsync(L->state[L->cur], host_in, bytes, cudaMemcpyHostToDevice, P->stream));
+  CK(cudaMemcpyAsync(P->d_scal, h, 3 * sizeof(double), cudaMemcpyHostToDevice, P->stream));
+  if (!(*dt_inout > 0.0)) do_estdt(P, L->state[L->cur], P->d_scal, P->d_scal + 2);
+  int rc = do_advance(P, L, P->d_scal, P->d_scal + 1, P->d_scal + 2, nullptr, P->d_scal + 3);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(host_out, L->state[L->cur], bytes, cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaMemcpyAsync(dt_inout, P->d_scal + 3, sizeof(double), cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  return NYX_OK;
+}
+
+int nyx_hydro_tile_shape(int shape, int *tx, int *ty) {
+  if (shape < 0 || shape >= fused_num_shapes()) return fail(NYX_EINVAL, "tile shape out of range");
+  TileShape t = fused_shape(shape);
+  if (tx) *tx = t.tx;
+  if (ty) *ty = t.ty;
+  return NYX_OK;
+}
+
+int nyx_hydro_set_tile_shape(nyx_plan *P, int shape) {
+  if (!P) return fail(NYX_EINVAL, "null plan");
+  if (P->prm.batching != NYX_PERSISTENT) return fail(NYX_EINVAL, "plan is not persistent");
+  if (shape < 0 || shape >= fused_num_shapes()) return fail(NYX_EINVAL, "tile shape out of range");
+  P->shape = shape;
+  P->tuned = true;
+  return NYX_OK;
+}
+
+int nyx_hydro_get_tile_shape(const nyx_plan *P, int *shape) {
+  if (!P || !shape) return fail(NYX_EINVAL, "null argument");
+  *shape = P->shape;
+  return NYX_OK;
+}
+
+int nyx_hydro_profile(nyx_plan *P, int enable) {
+  if (!P) return fail(NYX_EINVAL, "null plan");
+  P->profiling = enable != 0;
+  return NYX_OK;
+}
+
+int nyx_hydro_counters_read(nyx_plan *P, int reset, nyx_hydro_counters *out) {
+  if (!P || !out) return fail(NYX_EINVAL, "null argument");
+  CK(cudaStreamSynchronize(P->stream));
+  auto sum = [](std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &v, double &ms, long long &n) {
+    ms = 0.0;
+    n = (long long)v.size();
+    for (auto &e : v) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, e.first, e.second) == cudaSuccess) ms += t;
+    }
+  };
+  sum(P->ev_fill, out->fill_ms, out->timed_fills);
+  sum(P->ev_adv, out->advance_ms, out->timed_advances);
+  out->launches = P->launches;
+  if (reset) {
+    for (auto &e : P->ev_fill) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+    for (auto &e : P->ev_adv) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+    P->ev_fill.clear();
+    P->ev_adv.clear();
+    P->launches = 0;
+  }
+  return NYX_OK;
+}
+
+int nyx_hydro_status(nyx_plan *P, int *flags) {
+  if (!P) return fail(NYX_EINVAL, "null plan");
+  CK(cudaStreamSynchronize(P->stream));
+  unsigned st = 0;
+  CK(cudaMemcpy(&st, P->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  CK(cudaMemset(P->d_status, 0, sizeof(unsigned)));
+  if (flags) *flags = (int)st;
+  if (st & ST_NONFINITE) return fail(NYX_ENONFINITE, "non-finite value in an updated state");
+  if (st & ST_NEGATIVE) return fail(NYX_ENEGATIVE, "density <= 0 after an update");
+  if (st & ST_TIMEOUT) return fail(NYX_ETIMEOUT, "a bounded device wait gave up");
+  if (st & ST_OVERRUN) return fail(NYX_ECUDA, "work queue overrun");
+  return NYX_OK;
+}
+
+int nyx_plan_destroy(nyx_plan *P) {
+  if (!P) return fail(NYX_EINVAL, "null plan");
+  cudaStreamSynchronize(P->stream);
+  free_plan(P);
+  return NYX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,66 @@
+// nyx_kernels.h -- host launchers of the kernels of libnyxhydro.so.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "nyx_internal.cuh"
+
+namespace nyx {
+
+void launch_fill(double *field, int ncomp, const BoxDev *boxes, const FillRect *rects,
+                 const long long *rect_pref, int nrect, long long total, cudaStream_t st);
+
+void launch_step_setup(const SchemeConsts *K, const double *a_old, const double *a_new,
+                       const double *dt, StepConsts *SC, const BoxDev *boxes, int nbox,
+                       BoxStep *BS, cudaStream_t st);
+
+void launch_estdt(const BoxDev *boxes, const long long *cell_pref, int nbox, long long total,
+                  const double *state, const SchemeConsts *K, const double *a_dev,
+                  unsigned long long *dtacc, cudaStream_t st);
+
+void launch_dt_finalize(const SchemeConsts *K, unsigned long long *dtacc, double *dt_out,
+                        cudaStream_t st);
+
+size_t staged_scratch_doubles(long long V);
+
+void launch_staged_box(const BoxDev &b, const BoxDev *b_dev, const SchemeConsts *K,
+                       const StepConsts *SC, const BoxStep *BSb, const double *Sbox,
+                       const double *Gbox, double *Snbox, double *scratch, long long V,
+                       unsigned long long *dtacc, unsigned *status, double *flux_keep,
+                       cudaStream_t st);
+
+// Arguments of one launch of the fused persistent advance.
+struct FusedArgs {
+  const BoxDev *boxes;
+  const WorkItem *items;
+  int nitems;
+  int *queue;                     // work-queue counter (zeroed by the launcher)
+  const SchemeConsts *K;
+  const StepConsts *SC;
+  const BoxStep *BS;
+  const double *S;                // state field (6 comps), ghosts filled
+  const double *G;                // gravity field (3 comps) or null
+  double *Sn;                     // new state field
+  unsigned long long *dtacc;      // CFL min accumulator, or null
+  unsigned *status;
+  double *flux_keep;              // final-flux store, or null
+  const long long *flux_off;      // per-box offsets into flux_keep
+};
+
+// Tile shapes of the fused kernel (columns per CTA in x and y).
+struct TileShape {
+  int tx, ty;
+};
+int fused_num_shapes();
+TileShape fused_shape(int idx);
+
+// Launch the fused advance over all items with the given shape index.
+// precision: NYX_FP64 or NYX_MIXED.  Returns a cudaError_t.
+int launch_fused(int precision, int shape, const FusedArgs &a, int grid, cudaStream_t st);
+int fused_max_grid(int precision, int shape);
+
+int launch_fused_f64(int shape, const FusedArgs &a, int grid, cudaStream_t st);
+int launch_fused_mixed(int shape, const FusedArgs &a, int grid, cudaStream_t st);
+int max_grid_f64(int shape);
+int max_grid_mixed(int shape);
+
+}  // namespace nyx

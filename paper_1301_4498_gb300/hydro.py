@@ -1,0 +1,363 @@
+"""Thin ctypes binding of libnyxhydro.so (include/nyx_hydro.h).
+
+Argument marshalling only: every step of the advance runs in the CUDA
+library.  PyTorch provides device memory and the stream.  There is no CPU
+fallback: if the library is missing or cannot load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnyxhydro.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "nyx_hydro.h")
+
+NYX_OK = 0
+NYX_EINVAL = -1
+NYX_ECUDA = -2
+NYX_ENEGATIVE = -3
+NYX_ENONFINITE = -4
+NYX_ETIMEOUT = -5
+NYX_ENOMEM = -6
+NYX_FP64 = 0
+NYX_MIXED = 1
+NYX_PERSISTENT = 0
+NYX_PER_BOX = 1
+
+_lib = None
+
+
+class NyxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"nyx error {code}: {msg}")
+        self.code = code
+
+
+class NyxBox(C.Structure):
+    _fields_ = [("lo", C.c_int * 3), ("hi", C.c_int * 3), ("domain", C.c_int),
+                ("dx", C.c_double * 3)]
+
+
+class NyxDomain(C.Structure):
+    _fields_ = [("lo", C.c_int * 3), ("hi", C.c_int * 3), ("bc", C.c_int * 6)]
+
+
+class NyxLevelDesc(C.Structure):
+    _fields_ = [("nboxes", C.c_int), ("ng", C.c_int), ("boxes", C.POINTER(NyxBox)),
+                ("ndomains", C.c_int), ("domains", C.POINTER(NyxDomain))]
+
+
+class NyxParams(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("small_dens", C.c_double),
+                ("small_pres", C.c_double), ("eta_de", C.c_double),
+                ("riemann_max_iter", C.c_int), ("riemann_tol", C.c_double),
+                ("precision", C.c_int), ("grav_corrector", C.c_int), ("batching", C.c_int),
+                ("autotune", C.c_int), ("keep_fluxes", C.c_int)]
+
+
+class NyxLevel(C.Structure):
+    _fields_ = [("state", C.c_void_p * 2), ("grav", C.c_void_p), ("cur", C.c_int)]
+
+
+class NyxCounters(C.Structure):
+    _fields_ = [("launches", C.c_longlong), ("timed_fills", C.c_longlong),
+                ("timed_advances", C.c_longlong), ("fill_ms", C.c_double),
+                ("advance_ms", C.c_double)]
+
+
+def header_functions():
+    """Names of the functions include/nyx_hydro.h declares."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(nyx_\w+)\s*\(", txt, flags=re.M)))
+
+
+def load_library(path: str | None = None):
+    """Load libnyxhydro.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise NyxError(NYX_ECUDA, f"{p} is not built; run __graft_entry__.build() first")
+    L = C.CDLL(p)
+    vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
+    L.nyx_hydro_default_params.argtypes = [C.POINTER(NyxParams)]
+    L.nyx_hydro_default_params.restype = None
+    L.nyx_last_error.restype = C.c_char_p
+    L.nyx_hydro_plan.argtypes = [C.POINTER(NyxLevelDesc), C.POINTER(NyxParams), vp, C.POINTER(vp)]
+    L.nyx_hydro_layout.argtypes = [vp, C.c_int, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
+    L.nyx_hydro_fill.argtypes = [vp, vp, C.c_int]
+    L.nyx_hydro_estdt.argtypes = [vp, C.POINTER(NyxLevel), vp, vp]
+    L.nyx_hydro_advance.argtypes = [vp, C.POINTER(NyxLevel), vp, vp, vp, vp, vp]
+    L.nyx_hydro_run.argtypes = [vp, C.POINTER(NyxLevel), vp, vp, C.c_int, C.c_int, C.c_int]
+    L.nyx_hydro_fluxes.argtypes = [vp, C.POINTER(NyxLevel), C.c_int, C.c_int, vp]
+    L.nyx_hydro_step_host.argtypes = [vp, C.POINTER(NyxLevel), vp, vp, C.c_double, C.c_double,
+                                      dp]
+    L.nyx_hydro_status.argtypes = [vp, ip]
+    L.nyx_plan_destroy.argtypes = [vp]
+    L.nyx_hydro_tile_shape.argtypes = [C.c_int, ip, ip]
+    L.nyx_hydro_set_tile_shape.argtypes = [vp, C.c_int]
+    L.nyx_hydro_get_tile_shape.argtypes = [vp, ip]
+    L.nyx_hydro_profile.argtypes = [vp, C.c_int]
+    L.nyx_hydro_counters_read.argtypes = [vp, C.c_int, C.POINTER(NyxCounters)]
+    for name in ("nyx_hydro_plan", "nyx_hydro_layout", "nyx_hydro_fill", "nyx_hydro_estdt",
+                 "nyx_hydro_advance", "nyx_hydro_run", "nyx_hydro_fluxes", "nyx_hydro_step_host",
+                 "nyx_hydro_status", "nyx_plan_destroy", "nyx_hydro_tile_shape",
+                 "nyx_hydro_set_tile_shape", "nyx_hydro_get_tile_shape", "nyx_hydro_profile",
+                 "nyx_hydro_counters_read"):
+        getattr(L, name).restype = C.c_int
+    if path is None:
+        _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != NYX_OK:
+        raise NyxError(rc, load_library().nyx_last_error().decode())
+    return rc
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def level_desc(spec):
+    """C level descriptor from a LevelSpec-like object (see workloads.LevelSpec)."""
+    nb = len(spec.lo)
+    boxes = (NyxBox * nb)()
+    for b in range(nb):
+        for a in range(3):
+            boxes[b].lo[a] = int(spec.lo[b][a])
+            boxes[b].hi[a] = int(spec.hi[b][a])
+            boxes[b].dx[a] = float(spec.dx[b][a])
+        boxes[b].domain = int(spec.dom[b])
+    nd = len(spec.dom_lo)
+    doms = (NyxDomain * nd)()
+    for d in range(nd):
+        for a in range(3):
+            doms[d].lo[a] = int(spec.dom_lo[d][a])
+            doms[d].hi[a] = int(spec.dom_hi[d][a])
+        for a in range(6):
+            doms[d].bc[a] = int(spec.dom_bc[d][a])
+    desc = NyxLevelDesc(nb, int(spec.ng), boxes, nd, doms)
+    return desc, (boxes, doms)
+
+
+def make_params(**kw) -> NyxParams:
+    p = NyxParams()
+    load_library().nyx_hydro_default_params(C.byref(p))
+    prec = kw.pop("precision", None)
+    if prec is not None:
+        p.precision = {"fp64": NYX_FP64, "mixed": NYX_MIXED}.get(prec, prec)
+    bat = kw.pop("batching", None)
+    if bat is not None:
+        p.batching = {"persistent": NYX_PERSISTENT, "per_box": NYX_PER_BOX}.get(bat, bat)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+class Level:
+    """Two state fields, gravity and the current-version index of one level
+    (caller-owned torch tensors)."""
+
+    def __init__(self, state0, state1, grav=None, cur=0):
+        self.state = [state0, state1]
+        self.grav = grav
+        self.cur = cur
+        self._c = NyxLevel()
+
+    def c(self):
+        self._c.state[0] = self.state[0].data_ptr()
+        self._c.state[1] = self.state[1].data_ptr()
+        self._c.grav = None if self.grav is None else self.grav.data_ptr()
+        self._c.cur = self.cur
+        return self._c
+
+    def sync_from_c(self):
+        self.cur = self._c.cur
+
+    @property
+    def current(self):
+        return self.state[self.cur]
+
+
+class _Ordered:
+    """Order library work after the caller's torch stream and torch work
+    after the library's stream (the plan runs on its own non-default stream,
+    which CUDA-graph capture requires)."""
+
+    def __init__(self, plan):
+        self.plan = plan
+
+    def __enter__(self):
+        import torch
+        self.plan.torch_stream.wait_stream(torch.cuda.current_stream())
+        return self
+
+    def __exit__(self, *exc):
+        import torch
+        torch.cuda.current_stream().wait_stream(self.plan.torch_stream)
+        return False
+
+
+class Plan:
+    """A plan of libnyxhydro.so over one level (see nyx_hydro_plan)."""
+
+    def __init__(self, spec, stream=None, **params):
+        import torch
+        self.lib = load_library()
+        self.spec = spec
+        self.params = make_params(**params)
+        desc, self._keep = level_desc(spec)
+        if stream is None:
+            stream = torch.cuda.Stream()
+        self.torch_stream = stream
+        self.stream = stream.cuda_stream
+        h = C.c_void_p()
+        _check(self.lib.nyx_hydro_plan(C.byref(desc), C.byref(self.params),
+                                       C.c_void_p(self.stream), C.byref(h)))
+        self.h = h
+        self.nbox = len(spec.lo)
+
+    def ordered(self):
+        return _Ordered(self)
+
+    # ---------------------------------------------------------- layout
+    def layout(self, ncomp):
+        off = (C.c_size_t * (self.nbox + 1))()
+        st = (C.c_size_t * self.nbox)()
+        _check(self.lib.nyx_hydro_layout(self.h, ncomp, off, st))
+        return np.frombuffer(off, dtype=np.uint64).astype(np.int64), \
+            np.frombuffer(st, dtype=np.uint64).astype(np.int64)
+
+    def pack_host(self, arrays, ncomp, out=None):
+        """Pack per-box arrays (ncomp, Nz, Ny, Nx) into one flat host array."""
+        off, st = self.layout(ncomp)
+        if out is None:
+            out = np.zeros(int(off[-1]), dtype=np.float64)
+        for b, a in enumerate(arrays):
+            vol = a.shape[1] * a.shape[2] * a.shape[3]
+            blk = out[off[b]:off[b + 1]].reshape(ncomp, st[b])
+            blk[:, :vol] = a.reshape(ncomp, vol)
+        return out
+
+    def unpack_host(self, flat, ncomp):
+        off, st = self.layout(ncomp)
+        res = []
+        for b in range(self.nbox):
+            shp = self.spec.shape(b, ncomp)
+            vol = shp[1] * shp[2] * shp[3]
+            blk = flat[off[b]:off[b + 1]].reshape(ncomp, st[b])
+            res.append(blk[:, :vol].reshape(shp).copy())
+        return res
+
+    def to_device(self, arrays, ncomp):
+        import torch
+        return torch.from_numpy(self.pack_host(arrays, ncomp)).cuda()
+
+    def from_device(self, t, ncomp):
+        return self.unpack_host(t.detach().cpu().numpy(), ncomp)
+
+    def empty_field(self, ncomp):
+        import torch
+        off, _ = self.layout(ncomp)
+        return torch.zeros(int(off[-1]), dtype=torch.float64, device="cuda")
+
+    # ---------------------------------------------------------- calls
+    def fill(self, field, ncomp):
+        with self.ordered():
+            _check(self.lib.nyx_hydro_fill(self.h, _ptr(field), ncomp))
+
+    def estdt(self, level, a_dev, dt_dev):
+        with self.ordered():
+            _check(self.lib.nyx_hydro_estdt(self.h, C.byref(level.c()), _ptr(a_dev),
+                                            _ptr(dt_dev)))
+
+    def advance(self, level, a_old, a_new, dt, grav=None, dt_next=None):
+        cl = level.c()
+        with self.ordered():
+            _check(self.lib.nyx_hydro_advance(self.h, C.byref(cl), _ptr(a_old), _ptr(a_new),
+                                              _ptr(dt), _ptr(grav), _ptr(dt_next)))
+        level.sync_from_c()
+
+    def run(self, level, a_dev, dt_dev, nsteps, compute_dt0=True, use_graph=True):
+        cl = level.c()
+        with self.ordered():
+            _check(self.lib.nyx_hydro_run(self.h, C.byref(cl), _ptr(a_dev), _ptr(dt_dev), nsteps,
+                                          1 if compute_dt0 else 0, 1 if use_graph else 0))
+        level.sync_from_c()
+
+    def fluxes(self, level, box, direction):
+        import torch
+        n = list(self.spec.extent(box))
+        n[direction] += 1
+        out = torch.empty((6, n[2], n[1], n[0]), dtype=torch.float64, device="cuda")
+        with self.ordered():
+            _check(self.lib.nyx_hydro_fluxes(self.h, C.byref(level.c()), box, direction,
+                                             _ptr(out)))
+        return out
+
+    def set_tile_shape(self, shape):
+        _check(self.lib.nyx_hydro_set_tile_shape(self.h, shape))
+
+    def tile_shape(self):
+        s = C.c_int()
+        _check(self.lib.nyx_hydro_get_tile_shape(self.h, C.byref(s)))
+        tx, ty = C.c_int(), C.c_int()
+        _check(self.lib.nyx_hydro_tile_shape(s.value, C.byref(tx), C.byref(ty)))
+        return s.value, (tx.value, ty.value)
+
+    def profile(self, enable=True):
+        _check(self.lib.nyx_hydro_profile(self.h, 1 if enable else 0))
+
+    def counters(self, reset=True):
+        c = NyxCounters()
+        _check(self.lib.nyx_hydro_counters_read(self.h, 1 if reset else 0, C.byref(c)))
+        return dict(launches=c.launches, timed_fills=c.timed_fills,
+                    timed_advances=c.timed_advances, fill_ms=c.fill_ms, advance_ms=c.advance_ms)
+
+    def step_host(self, level, host_in, host_out, a_old, a_new, dt=0.0):
+        """End-to-end step through host buffers (torch CPU tensors, ideally
+        pinned).  Returns the next step's CFL dt."""
+        d = C.c_double(dt)
+        cl = level.c()
+        import torch
+        self.torch_stream.wait_stream(torch.cuda.current_stream())
+        _check(self.lib.nyx_hydro_step_host(self.h, C.byref(cl), C.c_void_p(host_in.data_ptr()),
+                                            C.c_void_p(host_out.data_ptr()), a_old, a_new,
+                                            C.byref(d)))
+        level.sync_from_c()
+        return d.value
+
+    def status(self):
+        f = C.c_int()
+        rc = self.lib.nyx_hydro_status(self.h, C.byref(f))
+        return rc, f.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.nyx_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_level(plan, states, grav=None):
+    """Device level from per-box host arrays (ghost cells need not be valid)."""
+    s0 = plan.to_device(states, 6)
+    s1 = plan.empty_field(6)
+    g = None
+    if grav is not None:
+        g = plan.to_device(grav, 3)
+        plan.fill(g, 3)
+    return Level(s0, s1, g)

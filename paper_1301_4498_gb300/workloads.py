@@ -319,8 +319,8 @@ def large_level(n=512, box=32, nfine=410, fine_n=64, sigma=1.0, seed=5, nsteps=1
     ``coarse_select`` / ``fine_select`` keep only some boxes (their fields are
     still cut from the same full-size draws)."""
     coarse = tiled_level(n, box, name="coarse")
-    f = comoving_fields((n, n, n), sigma, seed, 1.0 / n)
     csel = range(coarse.nbox) if coarse_select is None else coarse_select
+    f = comoving_fields((n, n, n), sigma, seed, 1.0 / n) if len(csel) else None
     fsel = range(nfine) if fine_select is None else fine_select
     S, G = [], []
     clev = coarse.subset(list(csel)) if coarse_select is not None else coarse
@@ -340,7 +340,10 @@ def large_level(n=512, box=32, nfine=410, fine_n=64, sigma=1.0, seed=5, nsteps=1
         s, g = _patch_state(fine, i, fb)
         S.append(s)
         G.append(g)
-    lev = merge_levels(clev, fine, name="large") if len(fsel) else clev
+    if not len(csel):
+        lev = fine
+    else:
+        lev = merge_levels(clev, fine, name="large") if len(fsel) else clev
     return Workload(f"{n}^3 level as {coarse.nbox} boxes of {box}^3 + {nfine} boxes of {fine_n}^3",
                     lev, S, G, a_schedule(1.0 / 51, 1.0 / 31, nsteps), 5.0 / 3.0, 0.5, nsteps, True)
 
