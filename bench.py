@@ -34,6 +34,17 @@ from paper_1301_4498_gb300 import workloads as W  # noqa: E402
 
 METRIC = "zone-updates/s per level step on 1 GB300 + HBM-roofline fraction, FP32-batched vs FP64"
 ALG_BYTES_PER_ZONE = 120  # read S (6 x 8 B) + g (3 x 8 B), write S (6 x 8 B)
+# Algorithmic floating-point operations per zone-update (+ - * / sqrt counted
+# once each, comparisons not counted): 3196 for primitives, PPM + tracing in 3
+# directions, 12 Riemann set-ups/samplings, 18 corner-coupling corrections and
+# the update, plus 480 per mean Newton iteration of the 12 two-shock solves.
+# The FP64 oracle on the large level's 64^3 boxes averages 3.05 iterations at
+# the mixed path's tolerance (1e-6) and 3.73 at the FP64 one (1e-10).
+ALG_FLOPS_PER_ZONE = {"mixed": 3196 + 480 * 3.05, "fp64": 3196 + 480 * 3.73}
+# Peaks from unit counts and the maximum SM clock (2070 MHz): 152 SMs x 128
+# FP32 lanes x 2 (FMA) = 80.5 TFLOP/s; 152 SMs x 2 FP64 FMA/clk x 2 = 1.26 TFLOP/s.
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 
 def load_peaks():
@@ -55,6 +66,8 @@ def make_workload(name: str, nsteps: int, sample_only: bool = False):
         return W.comoving_box(n=128, sigma=0.5, seed=1, nsteps=max(nsteps, 10))
     if name == "uneven512":
         return W.uneven_boxes(nbox=512, nsteps=max(nsteps, 10))
+    if name == "uneven64":  # the first 64 boxes of the 512-box level (profiling case)
+        return W.uneven_boxes(nbox=512, boxes=list(range(64)), nsteps=max(nsteps, 10))
     if name == "mixed256":
         return W.comoving_box(n=256, sigma=1.0, seed=4, nsteps=max(nsteps, 50), mixed=True)
     if name == "sod":
@@ -275,22 +288,30 @@ def run_ours(args, w):
     plan.profile(False)
     adv_ms = prof["advance_ms"] / max(1, prof["timed_advances"])
     fill_ms = prof["fill_ms"] / max(1, prof["timed_fills"])
-    achieved = ALG_BYTES_PER_ZONE * cells / (adv_ms / 1e3) / 1e9
+    achieved_gbs = ALG_BYTES_PER_ZONE * cells / (adv_ms / 1e3) / 1e9
+    flops = ALG_FLOPS_PER_ZONE[args.precision]
+    peak_tf = PEAK_FP32_TFLOPS if args.precision == "mixed" else PEAK_FP64_TFLOPS
+    achieved_tf = flops * cells / (adv_ms / 1e3) / 1e12
     shape, (tx, ty) = plan.tile_shape()
 
     # end to end through the C ABI with pinned host buffers
-    host_in = torch.from_numpy(plan.pack_host(w.state, 6)).pin_memory()
-    host_out = torch.empty_like(host_in).pin_memory()
-    e2e_steps = max(1, min(3, K))
-    d = plan.step_host(lev, host_in, host_out, float(a_host[0]), float(a_host[1]), 0.0)
-    torch.cuda.synchronize()
-    barrier(ws)
-    t0 = time.perf_counter()
-    for s in range(e2e_steps):
-        d = plan.step_host(lev, host_in, host_out, float(a_host[s]), float(a_host[s + 1]), d)
-    t_e2e = max_over_ranks(time.perf_counter() - t0, ws)
-    e2e_value = ws * cells * e2e_steps / t_e2e
-    state_bytes = host_in.numel() * 8
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.from_numpy(plan.pack_host(w.state, 6)).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        e2e_steps = max(1, min(3, K))
+        d = plan.step_host(lev, host_in, host_out, float(a_host[0]), float(a_host[1]), 0.0)
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        for s in range(e2e_steps):
+            d = plan.step_host(lev, host_in, host_out, float(a_host[s]), float(a_host[s + 1]), d)
+        t_e2e = max_over_ranks(time.perf_counter() - t0, ws)
+        state_bytes = host_in.numel() * 8
+        e2e = {"value": ws * cells * e2e_steps / t_e2e, "unit": "zone-updates/s",
+               "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes + 8,
+               "steps": e2e_steps}
+        del host_in, host_out
 
     # FP64 forms on the same workload (one step each), for the FP32-vs-FP64 comparison
     side = {}
@@ -325,16 +346,21 @@ def run_ours(args, w):
                        "batching": "persistent + CUDA graph", "tile": [tx, ty],
                        "l2": "inputs larger than L2 (state + gravity > 20 GB)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                         "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                         "kernel": "k_fused<float>", "kernel_ms": adv_ms,
-                         "alg_bytes_per_zone": ALG_BYTES_PER_ZONE,
-                         "peak_source": f"hbm_gbs {peak_src}"},
+            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf,
+                         "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
+                         "traffic": args.traffic_per_zone * cells if args.traffic_per_zone else None,
+                         "kernel": f"k_fused<{'float' if args.precision == 'mixed' else 'double'}>",
+                         "kernel_ms": adv_ms, "alg_flops_per_zone": flops,
+                         "pipe": "fp32" if args.precision == "mixed" else "fp64",
+                         "peak_source": "unit counts x 2070 MHz"},
+            "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"],
+                             "unit": "GB/s", "frac": achieved_gbs / peaks["hbm_gbs"],
+                             "alg_bytes_per_zone": ALG_BYTES_PER_ZONE,
+                             "peak_source": f"hbm_gbs {peak_src}"},
             "kernel_ms": {"advance": adv_ms, "ghost_fill": fill_ms},
             "fp64_comparison": side,
             "clocks": clk,
-            "e2e": {"value": e2e_value, "unit": "zone-updates/s", "h2d_bytes_per_step": state_bytes,
-                    "d2h_bytes_per_step": state_bytes + 8, "steps": e2e_steps},
+            "e2e": e2e,
             "gpu_launches": launches,
             "cpu_baseline": cpu,
         }
@@ -349,11 +375,14 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="large",
-                    choices=["large", "comoving128", "uneven512", "mixed256", "sod"])
+                    choices=["large", "comoving128", "uneven512", "uneven64", "mixed256", "sod"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--traffic-per-zone", type=float, default=0.0,
+                    help="DRAM bytes per zone of the advance kernel from an ncu capture")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-budget", type=float, default=6.0)
     ap.add_argument("--ref-boxes", type=int, default=0)

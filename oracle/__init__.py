@@ -105,6 +105,8 @@ def lib():
         L.orc_ppm_line.argtypes = [C.c_int, dp, dp, dp, dp]
         L.orc_ppm_integrals.argtypes = [C.c_double] * 4 + [dp, dp]
         L.orc_riemann.argtypes = [C.POINTER(_Params), dp, dp, dp, dp, dp]
+        L.orc_riemann_counts.argtypes = [C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.c_int]
+        L.orc_riemann_counts.restype = None
         L.orc_trace_line.argtypes = [C.POINTER(_Params), C.c_int, dp, dp, C.c_double,
                                      C.c_double, C.c_double, C.c_int, dp, dp, dp, dp]
         _lib = L
@@ -207,6 +209,13 @@ def run(lev, params: OracleParams, states, grav=None, a_sched=None, nsteps=1):
         dts.append(dt)
         stats.append(st)
     return cur, dts, stats
+
+
+def riemann_counts(reset: bool = True):
+    """(two-shock solves, Newton iterations) since the last reset."""
+    c, n = C.c_longlong(), C.c_longlong()
+    lib().orc_riemann_counts(C.byref(c), C.byref(n), 1 if reset else 0)
+    return c.value, n.value
 
 
 def ppm_line(s: np.ndarray):

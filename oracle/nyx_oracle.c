@@ -18,8 +18,14 @@
 #include "nyx_oracle.h"
 
 #include <math.h>
+#include <omp.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* Two-shock solve statistics (calls, Newton iterations), one cache-line
+ * slot per OpenMP thread; read by orc_riemann_counts. */
+#define ORC_MAX_THREADS 512
+static long long orc_rcount[ORC_MAX_THREADS * 8][2];
 
 #define SIXTH (1.0 / 6.0)
 #define TWO_THIRDS (2.0 / 3.0)
@@ -249,6 +255,7 @@ static void riemann_solve(const eos_t *E, const double *qL, const double *qR, do
   const double pL = qL[4], pR = qR[4], uL = qL[1], uR = qR[1];
   double p = (CR * pL + CL * pR + CL * CR * (uL - uR)) / (CL + CR);
   if (p < E->small_pres) p = E->small_pres;
+  long long nit = 0;
   for (int it = 0; it < E->max_iter; ++it) {
     double WL = shock_w(E, CL, pL, p);
     double WR = shock_w(E, CR, pR, p);
@@ -260,7 +267,15 @@ static void riemann_solve(const eos_t *E, const double *qL, const double *qR, do
     if (pn < E->small_pres) pn = E->small_pres;
     int conv = fabs(pn - p) <= E->tol * pn;
     p = pn;
+    nit++;
     if (conv) break;
+  }
+  {
+    int t = omp_get_thread_num();
+    if (t < ORC_MAX_THREADS) {
+      orc_rcount[t * 8][0] += 1;
+      orc_rcount[t * 8][1] += nit;
+    }
   }
   const double WL = shock_w(E, CL, pL, p);
   const double WR = shock_w(E, CR, pR, p);
@@ -822,6 +837,17 @@ double orc_estdt(const orc_level *L, const orc_params *P, double *const *state, 
     if (bmin < best) best = bmin;
   }
   return P->cfl * best;
+}
+
+void orc_riemann_counts(long long *calls, long long *iters, int reset) {
+  long long c = 0, n = 0;
+  for (int t = 0; t < ORC_MAX_THREADS; ++t) {
+    c += orc_rcount[t * 8][0];
+    n += orc_rcount[t * 8][1];
+    if (reset) orc_rcount[t * 8][0] = orc_rcount[t * 8][1] = 0;
+  }
+  *calls = c;
+  *iters = n;
 }
 
 /* ------------------------------------------------------------------ */

@@ -73,6 +73,9 @@ int orc_advance(const orc_level *lev, const orc_params *p, double *const *state_
 /* CFL time step over valid cells at scale factor a (Sec. 3.5). */
 double orc_estdt(const orc_level *lev, const orc_params *p, double *const *state, double a);
 
+/* Two-shock solves and Newton iterations since the last reset (all threads). */
+void orc_riemann_counts(long long *calls, long long *iters, int reset);
+
 /* Unit-level entry points used by the pin tests. */
 void orc_ppm_line(int n, const double *s, double *sL, double *sR, double *s6);
 void orc_ppm_integrals(double sL, double sR, double s6, double sigma, double *ip, double *im);

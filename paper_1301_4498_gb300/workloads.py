@@ -76,7 +76,7 @@ class LevelSpec:
 
     def subset(self, boxes) -> "LevelSpec":
         """Level made of some boxes only (their domains kept whole)."""
-        boxes = np.asarray(boxes)
+        boxes = np.asarray(boxes, dtype=np.int64)
         return LevelSpec(self.lo[boxes].copy(), self.hi[boxes].copy(), self.dom[boxes].copy(),
                          self.dx[boxes].copy(), self.dom_lo, self.dom_hi, self.dom_bc, self.ng,
                          self.name + "-subset", dict(self.meta))
