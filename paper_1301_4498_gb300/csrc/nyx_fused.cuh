@@ -59,9 +59,16 @@ __device__ __forceinline__ void prims_of(const double *S, long long bs, long lon
                                          R (&q)[5]) {
   const R rho = (R)S[id];
   q[0] = rho;
-  q[1] = (R)S[bs + id] / rho;
-  q[2] = (R)S[2 * bs + id] / rho;
-  q[3] = (R)S[3 * bs + id] / rho;
+  if constexpr (sizeof(R) == 4) {
+    const R ir = R(1) / rho;
+    q[1] = (R)S[bs + id] * ir;
+    q[2] = (R)S[2 * bs + id] * ir;
+    q[3] = (R)S[3 * bs + id] * ir;
+  } else {
+    q[1] = (R)S[bs + id] / rho;
+    q[2] = (R)S[2 * bs + id] / rho;
+    q[3] = (R)S[3 * bs + id] / rho;
+  }
   R p = E.gm1 * (R)S[5 * bs + id];
   if (p < E.small_pres) p = E.small_pres;
   q[4] = p;
@@ -182,6 +189,112 @@ __device__ __forceinline__ void update_cell(const nyx::SchemeConsts &k, const ny
     if ((double)t0 < dtmin) dtmin = (double)t0;
     if ((double)t1 < dtmin) dtmin = (double)t1;
     if ((double)t2 < dtmin) dtmin = (double)t2;
+  }
+}
+
+// Exact float -> double conversion on the integer pipe (FP32 results are
+// never subnormal here: the mixed unit is built with flush-to-zero).  The
+// FP64 pipe of this part runs at 1/64 of the FP32 rate and also executes the
+// F2F conversion, so keeping conversions off it matters.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xffu;
+  const unsigned bias = (e == 0u) ? 0u : ((e == 0xffu) ? 0x70000000u : 0x38000000u);
+  const unsigned hi = (b & 0x80000000u) | (((b & 0x7fffffffu) >> 3) + bias);
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+
+// finite test on the high word (integer pipe)
+__device__ __forceinline__ bool finite_hi(double x) {
+  return ((unsigned)__double2hiint(x) & 0x7ff00000u) != 0x7ff00000u;
+}
+
+// Mixed-precision update of one cell: the same FP64 update (flux divergence
+// accumulated in FP64 from exactly converted FP32 fluxes, comoving weights,
+// gravity predictor-corrector, FP64 kinetic-energy subtraction), arranged so
+// that the FP64 pipe does as little as possible: the p div U source term is
+// formed in FP32, 1/rho is an FP32 reciprocal refined by one FP64 Newton step.
+__device__ __forceinline__ void update_cell_mixed(
+    const nyx::SchemeConsts &k, const nyx::StepConsts &sc, const nyx::BoxDev &b, const double *S,
+    const double *G, double *Sn, long long id, const float (&Fxm)[8], const float (&Fxp)[8],
+    const float (&Fym)[8], const float (&Fyp)[8], const float (&Fzm)[8], const float (&Fzp)[8],
+    double &dtmin, unsigned &flags, bool want_dt) {
+  const long long bs = b.stride;
+  double div[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const double dx_ = f2d_exact(Fxp[c]) - f2d_exact(Fxm[c]);
+    const double dy_ = f2d_exact(Fyp[c]) - f2d_exact(Fym[c]);
+    const double dz_ = f2d_exact(Fzp[c]) - f2d_exact(Fzm[c]);
+    div[c] = dx_ * b.idx[0] + dy_ * b.idx[1] + dz_ * b.idx[2];
+  }
+  const float pdivu_f = 0.5f * (Fxp[7] + Fxm[7]) * (Fxp[6] - Fxm[6]) * (float)b.idx[0] +
+                        0.5f * (Fyp[7] + Fym[7]) * (Fyp[6] - Fym[6]) * (float)b.idx[1] +
+                        0.5f * (Fzp[7] + Fzm[7]) * (Fzp[6] - Fzm[6]) * (float)b.idx[2];
+  const double pdivu = f2d_exact(pdivu_f);
+  const double rho = S[id];
+  const double m0 = S[bs + id], m1 = S[2 * bs + id], m2 = S[3 * bs + id];
+  const double rE = S[4 * bs + id], re = S[5 * bs + id];
+  double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+  if (G) {
+    g0 = G[id];
+    g1 = G[bs + id];
+    g2 = G[2 * bs + id];
+  }
+  const double rho_s = rho - sc.dtp * div[0];
+  const double dtrho = sc.dt * rho;
+  const double ms0 = (sc.a_old * m0 - sc.dt * div[1] + dtrho * g0) * sc.ian;
+  const double ms1 = (sc.a_old * m1 - sc.dt * div[2] + dtrho * g1) * sc.ian;
+  const double ms2 = (sc.a_old * m2 - sc.dt * div[3] + dtrho * g2) * sc.ian;
+  const double mg = m0 * g0 + m1 * g1 + m2 * g2;
+  const double rE_s = (sc.ao2 * rE - sc.ahdt * div[4] + sc.dta * mg + sc.expn * re) * sc.ian2;
+  const double re_s = (sc.ao2 * re - sc.ahdt * (div[5] + pdivu) + sc.expn * re) * sc.ian2;
+  double mn0 = ms0, mn1 = ms1, mn2 = ms2, rEn = rE_s;
+  if (k.grav_corrector) {
+    const double cr = sc.hdt * (rho_s - rho) * sc.ian;
+    mn0 = ms0 + cr * g0;
+    mn1 = ms1 + cr * g1;
+    mn2 = ms2 + cr * g2;
+    const double msg = ms0 * g0 + ms1 * g1 + ms2 * g2;
+    rEn = rE_s + sc.hdt * (sc.a_new * msg - sc.a_old * mg) * sc.ian2;
+  }
+  // 1/rho: FP32 reciprocal, one Newton step in FP64 (relative error ~1e-14)
+  const float rho_f = (float)rho_s;
+  double ir = f2d_exact(1.0f / rho_f);
+  ir = ir * (2.0 - rho_s * ir);
+  const double ke = 0.5 * (mn0 * mn0 + mn1 * mn1 + mn2 * mn2) * ir;
+  double ren = re_s;
+  if (rEn - ke > k.eta_de * rEn) {
+    ren = rEn - ke;
+  } else {
+    rEn = ren + ke;
+  }
+  if (ren < k.efloor) {
+    ren = k.efloor;
+    rEn = ren + ke;
+  }
+  if (!(rho_f > 0.0f)) flags |= nyx::ST_NEGATIVE;
+  if (!finite_hi(rho_s) || !finite_hi(rEn) || !finite_hi(ren) || !finite_hi(mn0) ||
+      !finite_hi(mn1) || !finite_hi(mn2))
+    flags |= nyx::ST_NONFINITE;
+  Sn[id] = rho_s;
+  Sn[bs + id] = mn0;
+  Sn[2 * bs + id] = mn1;
+  Sn[3 * bs + id] = mn2;
+  Sn[4 * bs + id] = rEn;
+  Sn[5 * bs + id] = ren;
+  if (want_dt) {
+    const float irf = 1.0f / rho_f;
+    float p = (float)k.gm1 * (float)ren;
+    if (p < (float)k.small_pres) p = (float)k.small_pres;
+    const float c2 = (float)k.gamma * p * irf;
+    const float c = c2 * rsqrtf(c2);
+    const float an = (float)sc.a_new;
+    const float t0 = an * (float)b.dx[0] / (fabsf((float)mn0 * irf) + c);
+    const float t1 = an * (float)b.dx[1] / (fabsf((float)mn1 * irf) + c);
+    const float t2 = an * (float)b.dx[2] / (fabsf((float)mn2 * irf) + c);
+    const float tm = fminf(t0, fminf(t1, t2));
+    if ((double)tm < dtmin) dtmin = (double)tm;
   }
 }
 
@@ -470,8 +583,12 @@ __global__ void __launch_bounds__(FusedGeom<R, TX, TY>::NT, 1) k_fused(nyx::Fuse
           Fyp[k] = B[(8 + k) * NC + me + W];
         }
         const long long id = col + (long long)(c - 1 + 4) * ps;
-        update_cell<R>(KK, sc, b, S, G, Sn, id, Fxm, Fxp, Fym, Fyp, Ffz_prev, Ffz, dtmin, flags,
-                       a.dtacc != nullptr);
+        if constexpr (sizeof(R) == 4)
+          update_cell_mixed(KK, sc, b, S, G, Sn, id, Fxm, Fxp, Fym, Fyp, Ffz_prev, Ffz, dtmin,
+                            flags, a.dtacc != nullptr);
+        else
+          update_cell<R>(KK, sc, b, S, G, Sn, id, Fxm, Fxp, Fym, Fyp, Ffz_prev, Ffz, dtmin, flags,
+                         a.dtacc != nullptr);
         if (a.flux_keep) {
           double *fk = a.flux_keep + a.flux_off[w.box];
           const int nx = b.n[0], ny = b.n[1];

@@ -130,41 +130,61 @@ __device__ __forceinline__ void trace_cell(const Eos<R> &E, const R (&s)[5][5], 
   const R rc = rho * c;
   const R cor = c / rho;
 
+  // The fastest wave toward a face is the reference itself, so its own
+  // amplitude is identically zero (beta_+ on the high face, beta_- on the
+  // low face) and is not formed.  Each remaining wave needs the parabola
+  // integral only of the variables its projection uses: (p, u_n) for the
+  // acoustic waves, (rho, p, u_t1, u_t2) for the entropy/shear wave.
+  constexpr int T1 = (DIR == 0) ? 1 : 0;
+  constexpr int T2 = (DIR == 2) ? 1 : 2;
+  constexpr int TV1 = 1 + T1, TV2 = 1 + T2;
   // ---- high face i+1/2: waves with lam > 0
   {
-    R ref[5], d0[5], d1[5], d2[5];
+    R ref[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      ref[v] = (lam2 > R(0)) ? ppm_ip(sL[v], sR[v], s6[v], sig2) : sR[v];
-      d0[v] = (lam0 > R(0)) ? ref[v] - ppm_ip(sL[v], sR[v], s6[v], sig0) : R(0);
-      d1[v] = (lam1 > R(0)) ? ref[v] - ppm_ip(sL[v], sR[v], s6[v], sig1) : R(0);
-      d2[v] = (lam2 > R(0)) ? ref[v] - ppm_ip(sL[v], sR[v], s6[v], sig2) : R(0);
+    for (int v = 0; v < 5; ++v) ref[v] = (lam2 > R(0)) ? ppm_ip(sL[v], sR[v], s6[v], sig2) : sR[v];
+    R d0p = R(0), d0n = R(0), d1r = R(0), d1p = R(0), d1a = R(0), d1b = R(0);
+    if (lam0 > R(0)) {
+      d0p = ref[4] - ppm_ip(sL[4], sR[4], s6[4], sig0);
+      d0n = ref[NV] - ppm_ip(sL[NV], sR[NV], s6[NV], sig0);
     }
-    R bm = (d0[4] - rc * d0[NV]) * hc2;
-    R bp = (d2[4] + rc * d2[NV]) * hc2;
-    R b0 = d1[0] - d1[4] * ic2;
-    qp[0] = ref[0] - bm - b0 - bp;
-#pragma unroll
-    for (int v = 1; v <= 3; ++v) qp[v] = (v == NV) ? ref[v] - cor * (bp - bm) : ref[v] - d1[v];
-    qp[4] = ref[4] - c2 * (bm + bp);
+    if (lam1 > R(0)) {
+      d1r = ref[0] - ppm_ip(sL[0], sR[0], s6[0], sig1);
+      d1p = ref[4] - ppm_ip(sL[4], sR[4], s6[4], sig1);
+      d1a = ref[TV1] - ppm_ip(sL[TV1], sR[TV1], s6[TV1], sig1);
+      d1b = ref[TV2] - ppm_ip(sL[TV2], sR[TV2], s6[TV2], sig1);
+    }
+    const R bm = (d0p - rc * d0n) * hc2;
+    const R b0 = d1r - d1p * ic2;
+    qp[0] = ref[0] - bm - b0;
+    qp[NV] = ref[NV] - cor * (R(0) - bm);
+    qp[TV1] = ref[TV1] - d1a;
+    qp[TV2] = ref[TV2] - d1b;
+    qp[4] = ref[4] - c2 * bm;
   }
   // ---- low face i-1/2: waves with lam < 0
   {
-    R ref[5], d0[5], d1[5], d2[5];
+    R ref[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      ref[v] = (lam0 < R(0)) ? ppm_im(sL[v], sR[v], s6[v], sig0) : sL[v];
-      d0[v] = (lam0 < R(0)) ? ref[v] - ppm_im(sL[v], sR[v], s6[v], sig0) : R(0);
-      d1[v] = (lam1 < R(0)) ? ref[v] - ppm_im(sL[v], sR[v], s6[v], sig1) : R(0);
-      d2[v] = (lam2 < R(0)) ? ref[v] - ppm_im(sL[v], sR[v], s6[v], sig2) : R(0);
+    for (int v = 0; v < 5; ++v) ref[v] = (lam0 < R(0)) ? ppm_im(sL[v], sR[v], s6[v], sig0) : sL[v];
+    R d2p = R(0), d2n = R(0), d1r = R(0), d1p = R(0), d1a = R(0), d1b = R(0);
+    if (lam2 < R(0)) {
+      d2p = ref[4] - ppm_im(sL[4], sR[4], s6[4], sig2);
+      d2n = ref[NV] - ppm_im(sL[NV], sR[NV], s6[NV], sig2);
     }
-    R bm = (d0[4] - rc * d0[NV]) * hc2;
-    R bp = (d2[4] + rc * d2[NV]) * hc2;
-    R b0 = d1[0] - d1[4] * ic2;
-    qm[0] = ref[0] - bm - b0 - bp;
-#pragma unroll
-    for (int v = 1; v <= 3; ++v) qm[v] = (v == NV) ? ref[v] - cor * (bp - bm) : ref[v] - d1[v];
-    qm[4] = ref[4] - c2 * (bm + bp);
+    if (lam1 < R(0)) {
+      d1r = ref[0] - ppm_im(sL[0], sR[0], s6[0], sig1);
+      d1p = ref[4] - ppm_im(sL[4], sR[4], s6[4], sig1);
+      d1a = ref[TV1] - ppm_im(sL[TV1], sR[TV1], s6[TV1], sig1);
+      d1b = ref[TV2] - ppm_im(sL[TV2], sR[TV2], s6[TV2], sig1);
+    }
+    const R bp = (d2p + rc * d2n) * hc2;
+    const R b0 = d1r - d1p * ic2;
+    qm[0] = ref[0] - b0 - bp;
+    qm[NV] = ref[NV] - cor * bp;
+    qm[TV1] = ref[TV1] - d1a;
+    qm[TV2] = ref[TV2] - d1b;
+    qm[4] = ref[4] - c2 * bp;
   }
   // ---- half-step sources from cell-centre values, then floors
 #pragma unroll
@@ -289,6 +309,120 @@ __device__ __forceinline__ void riemann(const Eos<R> &E, const R (&qL)[5], const
   out[7] = pg;
 }
 
+// The same two-shock solve for the FP32 path, written with reciprocals and
+// reciprocal square roots (MUFU) instead of divisions and square roots.  With
+// x = max(1 + K (p - p_s)/p_s, 1e-10) and r = x^{-1/2}: W = C x r, 1/W = r/C,
+// and the Newton slope 1/Z = (W^2 + C^2)/(2 W^3) = (x + 1) r^3 / (2 C).
+__device__ __forceinline__ void sample_side_fast(const Eos<float> &E, float ro, float iro, float uo,
+                                                 float t1o, float t2o, float po, float Wo, float iWo,
+                                                 float co, float s, float pstar, float ustar,
+                                                 float (&g)[5]) {
+  float d = iro - (pstar - po) * (iWo * iWo);  // 1/rho*
+  float rhos = 1.0f / d;
+  float ird = d;
+  if (!(rhos >= E.small_dens)) {
+    rhos = E.small_dens;
+    ird = 1.0f / E.small_dens;
+  }
+  const float cs2 = E.gamma * pstar * ird;
+  const float cs = cs2 * rsqrtf(cs2);
+  int star;
+  float w = -1.0f;
+  if (pstar > po) {
+    const float S = uo - s * (Wo * iro);
+    star = (s * S < 0.0f) ? 1 : 0;
+  } else {
+    const float H = uo - s * co;
+    const float T = ustar - s * cs;
+    if (s * H >= 0.0f) {
+      star = 0;
+    } else if (s * T < 0.0f) {
+      star = 1;
+    } else {
+      star = 2;
+      w = H / (H - T);
+    }
+  }
+  if (star == 0) {
+    g[0] = ro;
+    g[1] = uo;
+    g[4] = po;
+  } else if (star == 1) {
+    g[0] = rhos;
+    g[1] = ustar;
+    g[4] = pstar;
+  } else {
+    g[0] = (1.0f - w) * ro + w * rhos;
+    g[1] = (1.0f - w) * uo + w * ustar;
+    g[4] = (1.0f - w) * po + w * pstar;
+  }
+  g[2] = t1o;
+  g[3] = t2o;
+}
+
+__device__ __forceinline__ void riemann_fast(const Eos<float> &E, const float (&qL)[5],
+                                             const float (&qR)[5], float (&out)[8]) {
+  const float iRL = 1.0f / qL[0], iRR = 1.0f / qR[0];
+  const float c2L = E.gamma * qL[4] * iRL, c2R = E.gamma * qR[4] * iRR;
+  const float cL = c2L * rsqrtf(c2L), cR = c2R * rsqrtf(c2R);
+  const float CL = qL[0] * cL, CR = qR[0] * cR;
+  const float iCL = 1.0f / CL, iCR = 1.0f / CR;
+  const float pL = qL[4], pR = qR[4], uL = qL[1], uR = qR[1];
+  const float kL = E.kshock / pL, kR = E.kshock / pR;
+  float p = (CR * pL + CL * pR + CL * CR * (uL - uR)) / (CL + CR);
+  if (p < E.small_pres) p = E.small_pres;
+  for (int it = 0; it < E.max_iter; ++it) {
+    const float xL = fmaxf(1.0f + (p - pL) * kL, 1e-10f);
+    const float xR = fmaxf(1.0f + (p - pR) * kR, 1e-10f);
+    const float rL = rsqrtf(xL), rR = rsqrtf(xR);
+    const float usL = uL - (p - pL) * (rL * iCL);
+    const float usR = uR + (p - pR) * (rR * iCR);
+    const float izL = (xL + 1.0f) * (rL * rL * rL) * (0.5f * iCL);
+    const float izR = (xR + 1.0f) * (rR * rR * rR) * (0.5f * iCR);
+    float pn = p - (usR - usL) / (izL + izR);
+    if (pn < E.small_pres) pn = E.small_pres;
+    const bool conv = fabsf(pn - p) <= E.tol * pn;
+    p = pn;
+    if (conv) break;
+  }
+  const float xL = fmaxf(1.0f + (p - pL) * kL, 1e-10f);
+  const float xR = fmaxf(1.0f + (p - pR) * kR, 1e-10f);
+  const float rL = rsqrtf(xL), rR = rsqrtf(xR);
+  const float WL = CL * xL * rL, WR = CR * xR * rR;
+  const float ustar = (pL - pR + WL * uL + WR * uR) / (WL + WR);
+  const float pstar = p;
+  float g[5];
+  if (ustar > 0.0f) {
+    sample_side_fast(E, qL[0], iRL, qL[1], qL[2], qL[3], qL[4], WL, rL * iCL, cL, 1.0f, pstar,
+                     ustar, g);
+  } else if (ustar < 0.0f) {
+    sample_side_fast(E, qR[0], iRR, qR[1], qR[2], qR[3], qR[4], WR, rR * iCR, cR, -1.0f, pstar,
+                     ustar, g);
+  } else {
+    float gl[5], gr[5];
+    sample_side_fast(E, qL[0], iRL, qL[1], qL[2], qL[3], qL[4], WL, rL * iCL, cL, 1.0f, pstar,
+                     ustar, gl);
+    sample_side_fast(E, qR[0], iRR, qR[1], qR[2], qR[3], qR[4], WR, rR * iCR, cR, -1.0f, pstar,
+                     ustar, gr);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) g[v] = 0.5f * (gl[v] + gr[v]);
+  }
+  if (g[0] < E.small_dens) g[0] = E.small_dens;
+  if (g[4] < E.small_pres) g[4] = E.small_pres;
+  const float rg = g[0], ug = g[1], t1 = g[2], t2 = g[3], pg = g[4];
+  const float frho = rg * ug;
+  const float rhoeg = pg * E.igm1;
+  const float ke = 0.5f * rg * (ug * ug + t1 * t1 + t2 * t2);
+  out[0] = frho;
+  out[1] = frho * ug + pg;
+  out[2] = frho * t1;
+  out[3] = frho * t2;
+  out[4] = ug * (rhoeg + ke + pg);
+  out[5] = ug * rhoeg;
+  out[6] = ug;
+  out[7] = pg;
+}
+
 // Tangential axes of face direction DIR, increasing order.
 template <int DIR>
 struct Tan {
@@ -304,7 +438,10 @@ __device__ __forceinline__ void face_flux(const Eos<R> &E, const R (&qLl)[5], co
   R qL[5] = {qLl[0], qLl[1 + DIR], qLl[1 + T1], qLl[1 + T2], qLl[4]};
   R qR[5] = {qRl[0], qRl[1 + DIR], qRl[1 + T1], qRl[1 + T2], qRl[4]};
   R o[8];
-  riemann(E, qL, qR, o);
+  if constexpr (sizeof(R) == 4)
+    riemann_fast(E, qL, qR, o);
+  else
+    riemann(E, qL, qR, o);
   F[0] = o[0];
   F[1 + DIR] = o[1];
   F[1 + T1] = o[2];
@@ -361,9 +498,16 @@ __device__ __forceinline__ void transverse1(const Eos<R> &E, const R (&q)[5], R 
     return;
   }
   out[0] = rn;
-  out[1] = m0 / rn;
-  out[2] = m1 / rn;
-  out[3] = m2 / rn;
+  if constexpr (sizeof(R) == 4) {
+    const R irn = R(1) / rn;
+    out[1] = m0 * irn;
+    out[2] = m1 * irn;
+    out[3] = m2 * irn;
+  } else {
+    out[1] = m0 / rn;
+    out[2] = m1 / rn;
+    out[3] = m2 / rn;
+  }
   R p = E.gm1 * en;
   if (p < E.small_pres) p = E.small_pres;
   out[4] = p;
@@ -392,9 +536,16 @@ __device__ __forceinline__ void transverse2(const Eos<R> &E, const R (&q)[5], R 
     return;
   }
   out[0] = rn;
-  out[1] = m0 / rn;
-  out[2] = m1 / rn;
-  out[3] = m2 / rn;
+  if constexpr (sizeof(R) == 4) {
+    const R irn = R(1) / rn;
+    out[1] = m0 * irn;
+    out[2] = m1 * irn;
+    out[3] = m2 * irn;
+  } else {
+    out[1] = m0 / rn;
+    out[2] = m1 / rn;
+    out[3] = m2 / rn;
+  }
   R p = E.gm1 * en;
   if (p < E.small_pres) p = E.small_pres;
   out[4] = p;
