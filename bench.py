@@ -246,6 +246,8 @@ def run_ours(args, w):
 
     plan = H.Plan(w.level, gamma=w.gamma, cfl=w.cfl, precision=args.precision,
                   batching="persistent", autotune=1 if args.autotune else 0)
+    if args.tile_shape >= 0:
+        plan.set_tile_shape(args.tile_shape)
     lev = H.make_level(plan, w.state, w.grav)
     a_host = a_schedule_for(w, max(K, Wm) + 1)
     a = torch.tensor(a_host, dtype=torch.float64, device="cuda")
@@ -349,7 +351,8 @@ def run_ours(args, w):
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf,
                          "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
                          "traffic": args.traffic_per_zone * cells if args.traffic_per_zone else None,
-                         "kernel": f"k_fused<{'float' if args.precision == 'mixed' else 'double'}>",
+                         "kernel": ("k_fused2 (task form)" if shape >= 3 else
+                                    f"k_fused<{'float' if args.precision == 'mixed' else 'double'}>"),
                          "kernel_ms": adv_ms, "alg_flops_per_zone": flops,
                          "pipe": "fp32" if args.precision == "mixed" else "fp64",
                          "peak_source": "unit counts x 2070 MHz"},
@@ -378,6 +381,8 @@ def main(argv=None):
                     choices=["large", "comoving128", "uneven512", "uneven64", "mixed256", "sod"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--autotune", type=int, default=1)
+    ap.add_argument("--tile-shape", type=int, default=-1,
+                    help="fix the fused kernel's tile shape (see nyx_hydro_tile_shape)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -173,9 +173,12 @@ int nyx_hydro_step_host(nyx_plan *plan, nyx_level *level, const double *host_sta
                         double *host_state_out, double a_old, double a_new, double *dt_inout);
 
 /* Tile shapes of the fused persistent kernel: shape index -> columns per
- * work item (tx, ty).  nyx_hydro_tile_shape returns NYX_EINVAL for an index
- * out of range; nyx_hydro_set_tile_shape fixes the plan's shape (and turns
- * its autotuner off); nyx_hydro_get_tile_shape reports the shape in use. */
+ * work item (tx, ty).  Shapes 0-2 are the column-owning form (FP64 and
+ * mixed), 3-5 the task form (mixed only).  nyx_hydro_tile_shape returns
+ * NYX_EINVAL for an index out of range; nyx_hydro_set_tile_shape fixes the
+ * plan's shape (and turns its autotuner off; NYX_EINVAL if the shape does
+ * not exist for the plan's precision); nyx_hydro_get_tile_shape reports the
+ * shape in use. */
 int nyx_hydro_tile_shape(int shape, int *tx, int *ty);
 int nyx_hydro_set_tile_shape(nyx_plan *plan, int shape);
 int nyx_hydro_get_tile_shape(const nyx_plan *plan, int *shape);

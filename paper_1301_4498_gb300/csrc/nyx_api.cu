@@ -450,7 +450,7 @@ int tune_shape(nyx_plan *P, const FusedArgs &base) {
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
   int best_s = P->shape;
-  for (int s = 0; s < fused_num_shapes(); ++s) {
+  for (int s = 0; s < fused_num_shapes(P->prm.precision); ++s) {
     FusedArgs a = base;
     a.items = P->d_items[s];
     a.nitems = P->nitems[s];
@@ -495,9 +495,10 @@ int enqueue_run(nyx_plan *P, nyx_level *L, const double *a_dev, double *dt_dev, 
 // ====================================================================== fused dispatch
 namespace nyx {
 
-static const TileShape kShapes[] = {{16, 16}, {32, 8}, {16, 8}};
+// 0-2: column-owning form (FP64 and mixed); 3-5: task form (mixed only)
+static const TileShape kShapes[] = {{16, 16}, {32, 8}, {16, 8}, {16, 8}, {8, 8}, {32, 4}};
 
-int fused_num_shapes() { return 3; }
+int fused_num_shapes(int precision) { return precision == NYX_MIXED ? 6 : 3; }
 TileShape fused_shape(int idx) { return kShapes[idx]; }
 
 int launch_fused(int precision, int shape, const FusedArgs &a, int grid, cudaStream_t st) {
@@ -665,7 +666,7 @@ int nyx_hydro_plan(const nyx_level_desc *lev, const nyx_hydro_params *prm, void 
     if (prm->batching == NYX_PER_BOX) {
       TRYC(cudaMalloc(&P->d_scratch, sizeof(double) * staged_scratch_doubles(P->Vmax)));
     } else {
-      for (int s = 0; s < fused_num_shapes(); ++s) {
+      for (int s = 0; s < fused_num_shapes(prm->precision); ++s) {
         TileShape ts = fused_shape(s);
         std::vector<WorkItem> it = build_items(*P, ts.tx, ts.ty);
         P->nitems[s] = (int)it.size();
@@ -675,8 +676,13 @@ int nyx_hydro_plan(const nyx_level_desc *lev, const nyx_hydro_params *prm, void 
       }
       TRYC(cudaMalloc(&P->d_queue, sizeof(int)));
       TRYC(cudaMemset(P->d_queue, 0, sizeof(int)));
-      for (int sh = 0; sh < fused_num_shapes(); ++sh)
+      for (int sh = 0; sh < fused_num_shapes(prm->precision); ++sh) {
         P->max_grid[sh] = fused_max_grid(prm->precision, sh);
+        if (P->max_grid[sh] < 1) {
+          rc = fail(NYX_ECUDA, "tile shape " + std::to_string(sh) + " cannot be launched");
+          goto fail_out;
+        }
+      }
       TRYC(cudaGetLastError());
     }
     if (prm->keep_fluxes) {
@@ -828,7 +834,7 @@ int nyx_hydro_step_host(nyx_plan *P, nyx_level *L, const double *host_in, double
 }
 
 int nyx_hydro_tile_shape(int shape, int *tx, int *ty) {
-  if (shape < 0 || shape >= fused_num_shapes()) return fail(NYX_EINVAL, "tile shape out of range");
+  if (shape < 0 || shape >= fused_num_shapes(NYX_MIXED)) return fail(NYX_EINVAL, "tile shape out of range");
   TileShape t = fused_shape(shape);
   if (tx) *tx = t.tx;
   if (ty) *ty = t.ty;
@@ -838,7 +844,7 @@ int nyx_hydro_tile_shape(int shape, int *tx, int *ty) {
 int nyx_hydro_set_tile_shape(nyx_plan *P, int shape) {
   if (!P) return fail(NYX_EINVAL, "null plan");
   if (P->prm.batching != NYX_PERSISTENT) return fail(NYX_EINVAL, "plan is not persistent");
-  if (shape < 0 || shape >= fused_num_shapes()) return fail(NYX_EINVAL, "tile shape out of range");
+  if (shape < 0 || shape >= fused_num_shapes(P->prm.precision)) return fail(NYX_EINVAL, "tile shape out of range");
   P->shape = shape;
   P->tuned = true;
   return NYX_OK;

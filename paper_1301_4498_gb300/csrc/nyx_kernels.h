@@ -50,7 +50,7 @@ struct FusedArgs {
 struct TileShape {
   int tx, ty;
 };
-int fused_num_shapes();
+int fused_num_shapes(int precision);
 TileShape fused_shape(int idx);
 
 // Launch the fused advance over all items with the given shape index.

@@ -191,6 +191,33 @@ def test_mixed_within_gates(oracle_results, name):
         assert linf <= MIXED_GATES["linf"] and l1 <= MIXED_GATES["l1"], (k, err)
 
 
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("name", ["sod", "tiled64x8", "uneven6"])
+def test_mixed_every_tile_shape_within_gates(oracle_results, name, shape):
+    """Both forms of the mixed kernel (column-owning shapes 0-2, task form
+    3-5), including ragged tiles of the uneven boxes."""
+    w, ref, dts, n = oracle_results(name)
+    plan = H.Plan(w.level, gamma=w.gamma, cfl=w.cfl, precision="mixed")
+    plan.set_tile_shape(shape)
+    lev = H.make_level(plan, w.state, w.grav)
+    a = torch.tensor(np.asarray(w.a_sched[:n + 1], dtype=np.float64), device="cuda")
+    dt = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+    plan.run(lev, a, dt, n, compute_dt0=True, use_graph=False)
+    torch.cuda.synchronize()
+    rc, flags = plan.status()
+    assert rc == H.NYX_OK, (rc, flags)
+    err = field_errors(plan.from_device(lev.current, 6), ref)
+    for k, (linf, l1) in err.items():
+        assert linf <= MIXED_GATES["linf"] and l1 <= MIXED_GATES["l1"], (shape, k, err)
+
+
+def test_fp64_rejects_task_form_shapes():
+    w = W.comoving_box(n=16, nsteps=1)
+    plan = H.Plan(w.level, gamma=w.gamma, precision="fp64")
+    with pytest.raises(H.NyxError):
+        plan.set_tile_shape(3)
+
+
 # ------------------------------------------------------------------ fluxes, host step, status
 
 def test_flux_export_matches_oracle():
@@ -201,6 +228,8 @@ def test_flux_export_matches_oracle():
                                 a_new=w.a_sched[1], dt=dt, want_flux=True)
     for batching in ("per_box", "persistent"):
         plan = H.Plan(w.level, gamma=w.gamma, cfl=w.cfl, batching=batching, keep_fluxes=1)
+        if batching == "persistent":
+            plan.set_tile_shape(2)  # ragged 16 x 8 tiles on these boxes
         lev = H.make_level(plan, w.state, w.grav)
         a = torch.tensor(w.a_sched[:2], dtype=torch.float64, device="cuda")
         d = torch.tensor([dt], dtype=torch.float64, device="cuda")
@@ -241,3 +270,27 @@ def test_negative_density_raises_status_without_fault():
     # the context is still usable
     x = torch.ones(4, device="cuda") * 2
     assert x.sum().item() == 8.0
+
+
+@pytest.mark.parametrize("shape", [0, 3])
+def test_mixed_flux_export_close_to_oracle(shape):
+    """Flux export of the mixed path (both kernel forms) against the FP64
+    oracle's fluxes: FP32 accuracy, normwise per component."""
+    w = W.uneven_boxes(nbox=512, boxes=[0, 1], nsteps=1)
+    P = oracle_params(w)
+    dt = oracle.estdt(w.level, P, w.state, w.a_sched[0])
+    _, _, flux = oracle.advance(w.level, P, w.state, w.grav, a_old=w.a_sched[0],
+                                a_new=w.a_sched[1], dt=dt, want_flux=True)
+    plan = H.Plan(w.level, gamma=w.gamma, cfl=w.cfl, precision="mixed", keep_fluxes=1)
+    plan.set_tile_shape(shape)
+    lev = H.make_level(plan, w.state, w.grav)
+    a = torch.tensor(w.a_sched[:2], dtype=torch.float64, device="cuda")
+    d = torch.tensor([dt], dtype=torch.float64, device="cuda")
+    plan.advance(lev, a[0:1], a[1:2], d)
+    for b in range(2):
+        for di in range(3):
+            f = plan.fluxes(lev, b, di).cpu().numpy()
+            r = flux[b][di]
+            for c in range(6):
+                scale = np.abs(r[c]).max()
+                assert np.abs(f[c] - r[c]).max() <= 2e-3 * scale, (shape, b, di, c)
