@@ -41,7 +41,8 @@ struct G2 {
   static constexpr int FFZ = QZFP + 10 * NC;         // [2 faces][8][NC] final z fluxes
   static constexpr int P1 = FFZ + 16 * NC;           // [28][NC] pool: FX,FY | Fxy,Fyx,Fxz,Fyz | Ffx,Ffy
   static constexpr int P2 = P1 + 28 * NC;            // [40][NC] pool: qxy,qyx,qxz,qyz | qxf,qyf
-  static constexpr int TOTAL = P2 + 40 * NC;
+  static constexpr int GR = P2 + 40 * NC;            // [3][NC] gravity of plane c
+  static constexpr int TOTAL = GR + 3 * NC;
   static constexpr size_t SMEM = sizeof(float) * (size_t)TOTAL;
 };
 
@@ -80,6 +81,42 @@ __device__ __forceinline__ void ld8(const float *b, int nc, int cell, float (&F)
   for (int k = 0; k < 8; ++k) F[k] = b[k * nc + cell];
 }
 
+// Lab frame (rho, u_x, u_y, u_z, p) <-> the normal frame of face direction
+// dir (rho, u_n, u_t1, u_t2, p), with dir warp-uniform: selects, no local
+// memory.  Tangential axes in increasing order, as everywhere else.
+__device__ __forceinline__ void to_normal(int dir, const float (&q)[5], float (&n)[5]) {
+  n[0] = q[0];
+  n[1] = (dir == 0) ? q[1] : ((dir == 1) ? q[2] : q[3]);
+  n[2] = (dir == 0) ? q[2] : q[1];
+  n[3] = (dir == 2) ? q[2] : q[3];
+  n[4] = q[4];
+}
+__device__ __forceinline__ void to_lab(int dir, const float (&n)[5], float (&q)[5]) {
+  q[0] = n[0];
+  q[1] = (dir == 0) ? n[1] : n[2];
+  q[2] = (dir == 0) ? n[2] : ((dir == 1) ? n[1] : n[3]);
+  q[3] = (dir == 2) ? n[1] : n[3];
+  q[4] = n[4];
+}
+
+// One Riemann problem on a direction-dir face; lab-frame states in and
+// F = (F_rho, F_mx, F_my, F_mz, F_rhoE, F_rhoe, u_g, p_g) out.
+__device__ __forceinline__ void face_flux_dir(const Eos<float> &E, int dir, const float (&ql)[5],
+                                              const float (&qr)[5], float (&F)[8]) {
+  float nl[5], nr[5], o[8];
+  to_normal(dir, ql, nl);
+  to_normal(dir, qr, nr);
+  riemann_fast(E, nl, nr, o);
+  F[0] = o[0];
+  F[1] = (dir == 0) ? o[1] : o[2];
+  F[2] = (dir == 0) ? o[2] : ((dir == 1) ? o[1] : o[3]);
+  F[3] = (dir == 2) ? o[1] : o[3];
+  F[4] = o[4];
+  F[5] = o[5];
+  F[6] = o[6];
+  F[7] = o[7];
+}
+
 template <int TX, int TY, int MB>
 __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a) {
   using G = G2<TX, TY>;
@@ -113,11 +150,10 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
     const double *S = a.S + nyx::NCONS * b.pref;
     const double *Gv = a.G ? a.G + nyx::NGRAV * b.pref : nullptr;
     double *Sn = a.Sn + nyx::NCONS * b.pref;
-    const float dtdx[3] = {(float)bst.dtdx[0], (float)bst.dtdx[1], (float)bst.dtdx[2]};
+    const float dtdx0 = (float)bst.dtdx[0], dtdx1 = (float)bst.dtdx[1], dtdx2 = (float)bst.dtdx[2];
     const float c30 = (float)bst.cdt3[0], c31 = (float)bst.cdt3[1], c32 = (float)bst.cdt3[2];
     const float ch0 = (float)bst.chalf[0], ch1 = (float)bst.chalf[1], ch2 = (float)bst.chalf[2];
     const int nstrip = 4 * (nxt + 2) + 4 * (nyt + 2);
-    // column geometry of owned column e
     auto col_i = [&](int e) { return e % W - 1; };
     auto col_j = [&](int e) { return e / W - 1; };
     auto active = [&](int e) { return e < NC && (e % W - 1) <= nxt && (e / W - 1) <= nyt; };
@@ -129,6 +165,55 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
       prims_of<float>(S, bs, id, E, q);
 #pragma unroll
       for (int v = 0; v < 5; ++v) sm[G::PR + (slot * 5 + v) * NE + ecell] = q[v];
+    };
+    // FP64 update of plane p from the final fluxes in the shared buffers:
+    // x, y faces in P1 (written by the last final-solve stage), z faces in
+    // the FFZ ring slots sm_lo (face p-1/2) and sm_hi (face p+1/2).
+    auto update = [&](int e, int p, int slot_lo, int slot_hi) {
+      const int i = col_i(e), j = col_j(e);
+      float Fxm[8], Fxp[8], Fym[8], Fyp[8], Fzm[8], Fzp[8];
+      ld8(sm + G::P1, NC, e, Fxm);
+      ld8(sm + G::P1, NC, e + 1, Fxp);
+      ld8(sm + G::P1 + 8 * NC, NC, e, Fym);
+      ld8(sm + G::P1 + 8 * NC, NC, e + W, Fyp);
+      ld8(sm + G::FFZ + slot_lo * 8 * NC, NC, e, Fzm);
+      ld8(sm + G::FFZ + slot_hi * 8 * NC, NC, e, Fzp);
+      const long long id = gcol(i, j) + (long long)(p + 4) * ps;
+      update_cell_mixed(KK, sc, b, S, Gv, Sn, id, Fxm, Fxp, Fym, Fyp, Fzm, Fzp, dtmin, flags,
+                        a.dtacc != nullptr);
+      if (a.flux_keep) {
+        double *fk = a.flux_keep + a.flux_off[w.box];
+        const int nx = b.n[0], ny = b.n[1];
+        const int gx = w.x0 + i, gy = w.y0 + j;
+        long long fx = (long long)(nx + 1) * ny * nz;
+        long long ix = ((long long)p * ny + gy) * (nx + 1) + gx;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) fk[k * fx + ix] = (double)Fxm[k];
+        if (gx == nx - 1)
+#pragma unroll
+          for (int k = 0; k < 6; ++k) fk[k * fx + ix + 1] = (double)Fxp[k];
+        fk += 6 * fx;
+        long long fy = (long long)nx * (ny + 1) * nz;
+        long long iy = ((long long)p * (ny + 1) + gy) * nx + gx;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) fk[k * fy + iy] = (double)Fym[k];
+        if (gy == ny - 1)
+#pragma unroll
+          for (int k = 0; k < 6; ++k) fk[k * fy + iy + nx] = (double)Fyp[k];
+        fk += 6 * fy;
+        long long fz = (long long)nx * ny * (nz + 1);
+        long long iz = ((long long)p * ny + gy) * nx + gx;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) fk[k * fz + iz] = (double)Fzm[k];
+        if (p == nz - 1)
+#pragma unroll
+          for (int k = 0; k < 6; ++k) fk[k * fz + iz + (long long)nx * ny] = (double)Fzp[k];
+      }
+    };
+    auto is_out = [&](int e) {
+      if (!active(e)) return false;
+      const int i = col_i(e), j = col_j(e);
+      return i >= 0 && i < nxt && j >= 0 && j < nyt;
     };
 
     // prologue: planes -3 .. 0 of every owned column
@@ -142,75 +227,87 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
     for (int c = -1; c <= nz; ++c) {
       const int pc = par2(c), pm = par2(c - 1);
       const bool zc = c >= 1;
-      // ------------------------------------------------ S0: primitives
+      // ------------------------------------------------ S0: primitives (+ gravity of plane c)
       for (int t = tid; t < NCP + nstrip; t += NT) {
         if (t < NCP) {
           if (!active(t)) continue;
           const int i = col_i(t), j = col_j(t);
-          load_prims(gcol(i, j) + (long long)(c + 2 + 4) * ps, ring5(c + 2), (j + 3) * WE + (i + 3));
+          const long long cc = gcol(i, j);
+          load_prims(cc + (long long)(c + 2 + 4) * ps, ring5(c + 2), (j + 3) * WE + (i + 3));
+          float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+          if (Gv) {
+            const long long id = cc + (long long)(c + 4) * ps;
+            g0 = (float)Gv[id];
+            g1 = (float)Gv[bs + id];
+            g2 = (float)Gv[2 * bs + id];
+          }
+          sm[G::GR + t] = g0;
+          sm[G::GR + NC + t] = g1;
+          sm[G::GR + 2 * NC + t] = g2;
         } else {
           const int u = t - NCP;
           int x, y;
           if (u < 4 * (nyt + 2)) {
-            const int r = u % (nyt + 2), s = u / (nyt + 2);
+            const int r = u % (nyt + 2), s2 = u / (nyt + 2);
             y = r - 1;
-            x = (s < 2) ? (-3 + s) : (nxt + 1 + (s - 2));
+            x = (s2 < 2) ? (-3 + s2) : (nxt + 1 + (s2 - 2));
           } else {
             const int v = u - 4 * (nyt + 2);
-            const int r = v % (nxt + 2), s = v / (nxt + 2);
+            const int r = v % (nxt + 2), s2 = v / (nxt + 2);
             x = r - 1;
-            y = (s < 2) ? (-3 + s) : (nyt + 1 + (s - 2));
+            y = (s2 < 2) ? (-3 + s2) : (nyt + 1 + (s2 - 2));
           }
           load_prims(gcol(x, y) + (long long)(c + 4) * ps, ring5(c), (y + 3) * WE + (x + 3));
         }
       }
       __syncthreads();
 
-      // ------------------------------------------------ S1: tracing at plane c
-      for (int t = tid; t < 3 * NCP; t += NT) {
-        const int kind = t / NCP, e = t - kind * NCP;
-        if (!active(e)) continue;
-        const int i = col_i(e), j = col_j(e);
-        const int ee = (j + 3) * WE + (i + 3);
-        const float *P0 = sm + G::PR + ring5(c) * 5 * NE;
-        const float rho = P0[ee], p = P0[4 * NE + ee];
-        const float cs2 = E.gamma * p / rho;
-        const float cs = cs2 * rsqrtf(cs2);
-        float g3[3] = {0.f, 0.f, 0.f};
-        if (Gv) {
-          const long long id = gcol(i, j) + (long long)(c + 4) * ps;
-          g3[0] = (float)Gv[id];
-          g3[1] = (float)Gv[bs + id];
-          g3[2] = (float)Gv[2 * bs + id];
-        }
-        float s[5][5], qm[5], qp[5];
-        if (kind == 0) {
-#pragma unroll
-          for (int v = 0; v < 5; ++v)
-#pragma unroll
-            for (int o = 0; o < 5; ++o) s[v][o] = P0[v * NE + ee + (o - 2)];
-          trace_cell<float, 0>(E, s, cs, g3, dtdx[0], src, qm, qp);
-          float *dst = sm + G::QXY + (pc * 2 + 0) * 10 * NC;
-          st5(dst, NC, e, qm);
-          st5(dst + 5 * NC, NC, e, qp);
-        } else if (kind == 1) {
-#pragma unroll
-          for (int v = 0; v < 5; ++v)
-#pragma unroll
-            for (int o = 0; o < 5; ++o) s[v][o] = P0[v * NE + ee + (o - 2) * WE];
-          trace_cell<float, 1>(E, s, cs, g3, dtdx[1], src, qm, qp);
-          float *dst = sm + G::QXY + (pc * 2 + 1) * 10 * NC;
-          st5(dst, NC, e, qm);
-          st5(dst + 5 * NC, NC, e, qp);
-        } else {
+      // ------------------------------------------------ S1: update of plane c-2, tracing at plane c
+      // The update (FP64 pipe) goes first so that it overlaps the FP32 tracing
+      // of the other warps.  Its fluxes stay untouched until the S2 barrier.
+      if (c >= 2 && tid < NCP && is_out(tid)) update(tid, c - 2, pc, pm);
+      {
+        const int dir = tid / NCP, e = tid - dir * NCP;
+        if (active(e)) {
+          const int i = col_i(e), j = col_j(e);
+          const int ee = (j + 3) * WE + (i + 3);
+          const float *P0 = sm + G::PR + ring5(c) * 5 * NE;
+          const float rho = P0[ee], p = P0[4 * NE + ee];
+          const float cs2 = E.gamma * p / rho;
+          const float cs = cs2 * rsqrtf(cs2);
+          float gl[3] = {sm[G::GR + e], sm[G::GR + NC + e], sm[G::GR + 2 * NC + e]};
+          float gn[3];
+          gn[0] = (dir == 0) ? gl[0] : ((dir == 1) ? gl[1] : gl[2]);
+          gn[1] = (dir == 0) ? gl[1] : gl[0];
+          gn[2] = (dir == 2) ? gl[1] : gl[2];
+          float s5[5][5];
 #pragma unroll
           for (int o = 0; o < 5; ++o) {
-            const float *Po = sm + G::PR + ring5(c - 2 + o) * 5 * NE;
+            const float *Po;
+            int cell;
+            if (dir == 0) {
+              Po = P0;
+              cell = ee + (o - 2);
+            } else if (dir == 1) {
+              Po = P0;
+              cell = ee + (o - 2) * WE;
+            } else {
+              Po = sm + G::PR + ring5(c - 2 + o) * 5 * NE;
+              cell = ee;
+            }
+            float ql[5], qn[5];
 #pragma unroll
-            for (int v = 0; v < 5; ++v) s[v][o] = Po[v * NE + ee];
+            for (int v = 0; v < 5; ++v) ql[v] = Po[v * NE + cell];
+            to_normal(dir, ql, qn);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) s5[v][o] = qn[v];
           }
-          trace_cell<float, 2>(E, s, cs, g3, dtdx[2], src, qm, qp);
-          float *dst = sm + G::QZ + pc * 10 * NC;
+          const float dtdx = (dir == 0) ? dtdx0 : ((dir == 1) ? dtdx1 : dtdx2);
+          float qmn[5], qpn[5], qm[5], qp[5];
+          trace_cell<float, 0>(E, s5, cs, gn, dtdx, src, qmn, qpn);
+          to_lab(dir, qmn, qm);
+          to_lab(dir, qpn, qp);
+          float *dst = (dir == 2) ? sm + G::QZ + pc * 10 * NC : sm + G::QXY + (pc * 2 + dir) * 10 * NC;
           st5(dst, NC, e, qm);
           st5(dst + 5 * NC, NC, e, qp);
         }
@@ -218,31 +315,40 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
       __syncthreads();
 
       // ------------------------------------------------ S2: normal solves
-      for (int t = tid; t < 3 * NCP; t += NT) {
-        const int kind = t / NCP, e = t - kind * NCP;
-        if (!active(e)) continue;
-        const int i = col_i(e), j = col_j(e);
-        float l[5], r[5], F[8];
-        if (kind == 0) {
-          if (i < 0) continue;
-          const float *q = sm + G::QXY + (pc * 2 + 0) * 10 * NC;
-          ld5(q + 5 * NC, NC, e - 1, l);
-          ld5(q, NC, e, r);
-          face_flux<float, 0>(E, l, r, F);
-          st7(sm + G::P1, NC, e, F);
-        } else if (kind == 1) {
-          if (j < 0) continue;
-          const float *q = sm + G::QXY + (pc * 2 + 1) * 10 * NC;
-          ld5(q + 5 * NC, NC, e - W, l);
-          ld5(q, NC, e, r);
-          face_flux<float, 1>(E, l, r, F);
-          st7(sm + G::P1 + 7 * NC, NC, e, F);
-        } else {
-          if (c < 0) continue;
-          ld5(sm + G::QZ + pm * 10 * NC + 5 * NC, NC, e, l);
-          ld5(sm + G::QZ + pc * 10 * NC, NC, e, r);
-          face_flux<float, 2>(E, l, r, F);
-          st7(sm + G::FZ + pc * 7 * NC, NC, e, F);
+      {
+        const int kind = tid / NCP, e = tid - kind * NCP;
+        if (active(e)) {
+          const int i = col_i(e), j = col_j(e);
+          const float *L, *Rr;
+          float *O;
+          int lc;
+          bool go;
+          if (kind == 0) {
+            go = i >= 0;
+            L = sm + G::QXY + (pc * 2 + 0) * 10 * NC + 5 * NC;
+            lc = e - 1;
+            Rr = sm + G::QXY + (pc * 2 + 0) * 10 * NC;
+            O = sm + G::P1;
+          } else if (kind == 1) {
+            go = j >= 0;
+            L = sm + G::QXY + (pc * 2 + 1) * 10 * NC + 5 * NC;
+            lc = e - W;
+            Rr = sm + G::QXY + (pc * 2 + 1) * 10 * NC;
+            O = sm + G::P1 + 7 * NC;
+          } else {
+            go = c >= 0;
+            L = sm + G::QZ + pm * 10 * NC + 5 * NC;
+            lc = e;
+            Rr = sm + G::QZ + pc * 10 * NC;
+            O = sm + G::FZ + pc * 7 * NC;
+          }
+          if (go) {
+            float l[5], r[5], F[8];
+            ld5(L, NC, lc, l);
+            ld5(Rr, NC, e, r);
+            face_flux_dir(E, kind, l, r, F);
+            st7(O, NC, e, F);
+          }
         }
       }
       __syncthreads();
@@ -253,52 +359,48 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
         if (!active(e)) continue;
         const int i = col_i(e), j = col_j(e);
         const bool inX = i >= 0 && i < nxt, inY = j >= 0 && j < nyt;
-        float qa[5], qb[5], oa[5], ob[5];
-        if (kind == 0 || kind == 3) {  // by normal y fluxes: q_{x|y} (0), q_{z|y} (3)
-          if (!inY) continue;
-          const TFlux<float> Fm = ld7(sm + G::P1 + 7 * NC, NC, e);
-          const TFlux<float> Fp = ld7(sm + G::P1 + 7 * NC, NC, e + W);
-          const float *q = (kind == 0) ? sm + G::QXY + (pc * 2 + 0) * 10 * NC : sm + G::QZ + pc * 10 * NC;
-          ld5(q, NC, e, qa);
-          ld5(q + 5 * NC, NC, e, qb);
-          transverse1(E, qa, c31, Fp, Fm, oa);
-          transverse1(E, qb, c31, Fp, Fm, ob);
-          if (kind == 0) {
-            st5(sm + G::P2, NC, e, oa);
-            st5(sm + G::P2 + 5 * NC, NC, e, ob);
-          } else {
-            st5(sm + G::QZYM, NC, e, oa);
-            st5(sm + G::QZYP + pc * 5 * NC, NC, e, ob);
-          }
-        } else if (kind == 1 || kind == 2) {  // by normal x fluxes: q_{y|x} (1), q_{z|x} (2)
-          if (!inX) continue;
-          const TFlux<float> Fm = ld7(sm + G::P1, NC, e);
-          const TFlux<float> Fp = ld7(sm + G::P1, NC, e + 1);
-          const float *q = (kind == 1) ? sm + G::QXY + (pc * 2 + 1) * 10 * NC : sm + G::QZ + pc * 10 * NC;
-          ld5(q, NC, e, qa);
-          ld5(q + 5 * NC, NC, e, qb);
-          transverse1(E, qa, c30, Fp, Fm, oa);
-          transverse1(E, qb, c30, Fp, Fm, ob);
-          if (kind == 1) {
-            st5(sm + G::P2 + 10 * NC, NC, e, oa);
-            st5(sm + G::P2 + 15 * NC, NC, e, ob);
-          } else {
-            st5(sm + G::QZXM, NC, e, oa);
-            st5(sm + G::QZXP + pc * 5 * NC, NC, e, ob);
-          }
-        } else {  // by normal z fluxes at plane c-1: q_{x|z} (4), q_{y|z} (5)
-          if (!zc) continue;
-          const TFlux<float> Fm = ld7(sm + G::FZ + pm * 7 * NC, NC, e);
-          const TFlux<float> Fp = ld7(sm + G::FZ + pc * 7 * NC, NC, e);
-          const float *q = sm + G::QXY + (pm * 2 + (kind - 4)) * 10 * NC;
-          ld5(q, NC, e, qa);
-          ld5(q + 5 * NC, NC, e, qb);
-          transverse1(E, qa, c32, Fp, Fm, oa);
-          transverse1(E, qb, c32, Fp, Fm, ob);
-          float *dst = sm + G::P2 + (20 + 10 * (kind - 4)) * NC;
-          st5(dst, NC, e, oa);
-          st5(dst + 5 * NC, NC, e, ob);
+        const float *Q, *Fmb, *Fpb;
+        float *Om, *Op;
+        int fpc;
+        float coef;
+        bool go;
+        switch (kind) {
+          case 0:  // q_{x|y} at c
+            go = inY; Q = sm + G::QXY + (pc * 2 + 0) * 10 * NC; Fmb = Fpb = sm + G::P1 + 7 * NC;
+            fpc = e + W; coef = c31; Om = sm + G::P2; Op = sm + G::P2 + 5 * NC;
+            break;
+          case 1:  // q_{y|x} at c
+            go = inX; Q = sm + G::QXY + (pc * 2 + 1) * 10 * NC; Fmb = Fpb = sm + G::P1;
+            fpc = e + 1; coef = c30; Om = sm + G::P2 + 10 * NC; Op = sm + G::P2 + 15 * NC;
+            break;
+          case 2:  // q_{z|x} at c
+            go = inX; Q = sm + G::QZ + pc * 10 * NC; Fmb = Fpb = sm + G::P1;
+            fpc = e + 1; coef = c30; Om = sm + G::QZXM; Op = sm + G::QZXP + pc * 5 * NC;
+            break;
+          case 3:  // q_{z|y} at c
+            go = inY; Q = sm + G::QZ + pc * 10 * NC; Fmb = Fpb = sm + G::P1 + 7 * NC;
+            fpc = e + W; coef = c31; Om = sm + G::QZYM; Op = sm + G::QZYP + pc * 5 * NC;
+            break;
+          case 4:  // q_{x|z} at c-1
+            go = zc; Q = sm + G::QXY + (pm * 2 + 0) * 10 * NC; Fmb = sm + G::FZ + pm * 7 * NC;
+            Fpb = sm + G::FZ + pc * 7 * NC; fpc = e; coef = c32;
+            Om = sm + G::P2 + 20 * NC; Op = sm + G::P2 + 25 * NC;
+            break;
+          default:  // q_{y|z} at c-1
+            go = zc; Q = sm + G::QXY + (pm * 2 + 1) * 10 * NC; Fmb = sm + G::FZ + pm * 7 * NC;
+            Fpb = sm + G::FZ + pc * 7 * NC; fpc = e; coef = c32;
+            Om = sm + G::P2 + 30 * NC; Op = sm + G::P2 + 35 * NC;
+            break;
         }
+        if (!go) continue;
+        const TFlux<float> Fm = ld7(Fmb, NC, e), Fp = ld7(Fpb, NC, fpc);
+        float qa[5], qb[5], oa[5], ob[5];
+        ld5(Q, NC, e, qa);
+        ld5(Q + 5 * NC, NC, e, qb);
+        transverse1(E, qa, coef, Fp, Fm, oa);
+        transverse1(E, qb, coef, Fp, Fm, ob);
+        st5(Om, NC, e, oa);
+        st5(Op, NC, e, ob);
       }
       __syncthreads();
 
@@ -308,172 +410,123 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
         if (!active(e)) continue;
         const int i = col_i(e), j = col_j(e);
         const bool inX = i >= 0 && i < nxt, inY = j >= 0 && j < nyt;
-        float l[5], r[5], F[8];
-        if (kind == 0) {  // F^{x|y} at plane c
-          if (!(i >= 0 && inY)) continue;
-          ld5(sm + G::P2 + 5 * NC, NC, e - 1, l);
-          ld5(sm + G::P2, NC, e, r);
-          face_flux<float, 0>(E, l, r, F);
-          st7(sm + G::P1, NC, e, F);
-        } else if (kind == 1) {  // F^{y|x} at plane c
-          if (!(j >= 0 && inX)) continue;
-          ld5(sm + G::P2 + 15 * NC, NC, e - W, l);
-          ld5(sm + G::P2 + 10 * NC, NC, e, r);
-          face_flux<float, 1>(E, l, r, F);
-          st7(sm + G::P1 + 7 * NC, NC, e, F);
-        } else if (kind == 2) {  // F^{x|z} at plane c-1
-          if (!(zc && i >= 0)) continue;
-          ld5(sm + G::P2 + 25 * NC, NC, e - 1, l);
-          ld5(sm + G::P2 + 20 * NC, NC, e, r);
-          face_flux<float, 0>(E, l, r, F);
-          st7(sm + G::P1 + 14 * NC, NC, e, F);
-        } else if (kind == 3) {  // F^{y|z} at plane c-1
-          if (!(zc && j >= 0)) continue;
-          ld5(sm + G::P2 + 35 * NC, NC, e - W, l);
-          ld5(sm + G::P2 + 30 * NC, NC, e, r);
-          face_flux<float, 1>(E, l, r, F);
-          st7(sm + G::P1 + 21 * NC, NC, e, F);
-        } else if (kind == 4) {  // F^{z|x} at face c-1/2
-          if (!(c >= 0 && inX)) continue;
-          ld5(sm + G::QZXP + pm * 5 * NC, NC, e, l);
-          ld5(sm + G::QZXM, NC, e, r);
-          face_flux<float, 2>(E, l, r, F);
-          st7(sm + G::FZXY + (pc * 2 + 0) * 7 * NC, NC, e, F);
-        } else {  // F^{z|y} at face c-1/2
-          if (!(c >= 0 && inY)) continue;
-          ld5(sm + G::QZYP + pm * 5 * NC, NC, e, l);
-          ld5(sm + G::QZYM, NC, e, r);
-          face_flux<float, 2>(E, l, r, F);
-          st7(sm + G::FZXY + (pc * 2 + 1) * 7 * NC, NC, e, F);
+        const float *L, *Rr;
+        float *O;
+        int lc, dir;
+        bool go;
+        switch (kind) {
+          case 0:  // F^{x|y} at c
+            go = i >= 0 && inY; dir = 0; L = sm + G::P2 + 5 * NC; lc = e - 1; Rr = sm + G::P2;
+            O = sm + G::P1;
+            break;
+          case 1:  // F^{y|x} at c
+            go = j >= 0 && inX; dir = 1; L = sm + G::P2 + 15 * NC; lc = e - W;
+            Rr = sm + G::P2 + 10 * NC; O = sm + G::P1 + 7 * NC;
+            break;
+          case 2:  // F^{x|z} at c-1
+            go = zc && i >= 0; dir = 0; L = sm + G::P2 + 25 * NC; lc = e - 1;
+            Rr = sm + G::P2 + 20 * NC; O = sm + G::P1 + 14 * NC;
+            break;
+          case 3:  // F^{y|z} at c-1
+            go = zc && j >= 0; dir = 1; L = sm + G::P2 + 35 * NC; lc = e - W;
+            Rr = sm + G::P2 + 30 * NC; O = sm + G::P1 + 21 * NC;
+            break;
+          case 4:  // F^{z|x} at face c-1/2
+            go = c >= 0 && inX; dir = 2; L = sm + G::QZXP + pm * 5 * NC; lc = e;
+            Rr = sm + G::QZXM; O = sm + G::FZXY + (pc * 2 + 0) * 7 * NC;
+            break;
+          default:  // F^{z|y} at face c-1/2
+            go = c >= 0 && inY; dir = 2; L = sm + G::QZYP + pm * 5 * NC; lc = e;
+            Rr = sm + G::QZYM; O = sm + G::FZXY + (pc * 2 + 1) * 7 * NC;
+            break;
         }
+        if (!go) continue;
+        float l[5], r[5], F[8];
+        ld5(L, NC, lc, l);
+        ld5(Rr, NC, e, r);
+        face_flux_dir(E, dir, l, r, F);
+        st7(O, NC, e, F);
       }
       __syncthreads();
 
       // ------------------------------------------------ S5: final states, theta = 1/2
-      for (int t = tid; t < 3 * NCP; t += NT) {
-        const int kind = t / NCP, e = t - kind * NCP;
-        if (!active(e)) continue;
-        const int i = col_i(e), j = col_j(e);
-        const bool inX = i >= 0 && i < nxt, inY = j >= 0 && j < nyt;
-        float qa[5], qb[5], oa[5], ob[5];
-        if (kind == 0) {  // z at plane c: by F^{x|y} in x, F^{y|x} in y
-          if (!(inX && inY)) continue;
-          const TFlux<float> Am = ld7(sm + G::P1, NC, e), Ap = ld7(sm + G::P1, NC, e + 1);
-          const TFlux<float> Bm = ld7(sm + G::P1 + 7 * NC, NC, e), Bp = ld7(sm + G::P1 + 7 * NC, NC, e + W);
-          const float *q = sm + G::QZ + pc * 10 * NC;
-          ld5(q, NC, e, qa);
-          ld5(q + 5 * NC, NC, e, qb);
-          transverse2(E, qa, ch0, Ap, Am, ch1, Bp, Bm, oa);
-          transverse2(E, qb, ch0, Ap, Am, ch1, Bp, Bm, ob);
-          st5(sm + G::QZFM, NC, e, oa);
-          st5(sm + G::QZFP + pc * 5 * NC, NC, e, ob);
-        } else if (kind == 1) {  // x at plane c-1: by F^{y|z} in y, F^{z|y} in z
-          if (!(zc && inY)) continue;
-          const TFlux<float> Am = ld7(sm + G::P1 + 21 * NC, NC, e);
-          const TFlux<float> Ap = ld7(sm + G::P1 + 21 * NC, NC, e + W);
-          const TFlux<float> Bm = ld7(sm + G::FZXY + (pm * 2 + 1) * 7 * NC, NC, e);
-          const TFlux<float> Bp = ld7(sm + G::FZXY + (pc * 2 + 1) * 7 * NC, NC, e);
-          const float *q = sm + G::QXY + (pm * 2 + 0) * 10 * NC;
-          ld5(q, NC, e, qa);
-          ld5(q + 5 * NC, NC, e, qb);
-          transverse2(E, qa, ch1, Ap, Am, ch2, Bp, Bm, oa);
-          transverse2(E, qb, ch1, Ap, Am, ch2, Bp, Bm, ob);
-          st5(sm + G::P2, NC, e, oa);
-          st5(sm + G::P2 + 5 * NC, NC, e, ob);
-        } else {  // y at plane c-1: by F^{x|z} in x, F^{z|x} in z
-          if (!(zc && inX)) continue;
-          const TFlux<float> Am = ld7(sm + G::P1 + 14 * NC, NC, e);
-          const TFlux<float> Ap = ld7(sm + G::P1 + 14 * NC, NC, e + 1);
-          const TFlux<float> Bm = ld7(sm + G::FZXY + (pm * 2 + 0) * 7 * NC, NC, e);
-          const TFlux<float> Bp = ld7(sm + G::FZXY + (pc * 2 + 0) * 7 * NC, NC, e);
-          const float *q = sm + G::QXY + (pm * 2 + 1) * 10 * NC;
-          ld5(q, NC, e, qa);
-          ld5(q + 5 * NC, NC, e, qb);
-          transverse2(E, qa, ch0, Ap, Am, ch2, Bp, Bm, oa);
-          transverse2(E, qb, ch0, Ap, Am, ch2, Bp, Bm, ob);
-          st5(sm + G::P2 + 10 * NC, NC, e, oa);
-          st5(sm + G::P2 + 15 * NC, NC, e, ob);
+      {
+        const int kind = tid / NCP, e = tid - kind * NCP;
+        if (active(e)) {
+          const int i = col_i(e), j = col_j(e);
+          const bool inX = i >= 0 && i < nxt, inY = j >= 0 && j < nyt;
+          const float *Q, *Ab, *Bmb, *Bpb;
+          float *Om, *Op;
+          int apc, bpc;
+          float k1c, k2c;
+          bool go;
+          if (kind == 0) {  // z at plane c: F^{x|y} in x, F^{y|x} in y
+            go = inX && inY; Q = sm + G::QZ + pc * 10 * NC;
+            Ab = sm + G::P1; apc = e + 1; k1c = ch0;
+            Bmb = Bpb = sm + G::P1 + 7 * NC; bpc = e + W; k2c = ch1;
+            Om = sm + G::QZFM; Op = sm + G::QZFP + pc * 5 * NC;
+          } else if (kind == 1) {  // x at plane c-1: F^{y|z} in y, F^{z|y} in z
+            go = zc && inY; Q = sm + G::QXY + (pm * 2 + 0) * 10 * NC;
+            Ab = sm + G::P1 + 21 * NC; apc = e + W; k1c = ch1;
+            Bmb = sm + G::FZXY + (pm * 2 + 1) * 7 * NC; Bpb = sm + G::FZXY + (pc * 2 + 1) * 7 * NC;
+            bpc = e; k2c = ch2;
+            Om = sm + G::P2; Op = sm + G::P2 + 5 * NC;
+          } else {  // y at plane c-1: F^{x|z} in x, F^{z|x} in z
+            go = zc && inX; Q = sm + G::QXY + (pm * 2 + 1) * 10 * NC;
+            Ab = sm + G::P1 + 14 * NC; apc = e + 1; k1c = ch0;
+            Bmb = sm + G::FZXY + (pm * 2 + 0) * 7 * NC; Bpb = sm + G::FZXY + (pc * 2 + 0) * 7 * NC;
+            bpc = e; k2c = ch2;
+            Om = sm + G::P2 + 10 * NC; Op = sm + G::P2 + 15 * NC;
+          }
+          if (go) {
+            const TFlux<float> Am = ld7(Ab, NC, e), Ap = ld7(Ab, NC, apc);
+            const TFlux<float> Bm = ld7(Bmb, NC, e), Bp = ld7(Bpb, NC, bpc);
+            float qa[5], qb[5], oa[5], ob[5];
+            ld5(Q, NC, e, qa);
+            ld5(Q + 5 * NC, NC, e, qb);
+            transverse2(E, qa, k1c, Ap, Am, k2c, Bp, Bm, oa);
+            transverse2(E, qb, k1c, Ap, Am, k2c, Bp, Bm, ob);
+            st5(Om, NC, e, oa);
+            st5(Op, NC, e, ob);
+          }
         }
       }
       __syncthreads();
 
       // ------------------------------------------------ S6: final solves
-      for (int t = tid; t < 3 * NCP; t += NT) {
-        const int kind = t / NCP, e = t - kind * NCP;
-        if (!active(e)) continue;
-        const int i = col_i(e), j = col_j(e);
-        const bool inX = i >= 0 && i < nxt, inY = j >= 0 && j < nyt;
-        float l[5], r[5], F[8];
-        if (kind == 0) {
-          if (!(zc && i >= 0 && inY)) continue;
-          ld5(sm + G::P2 + 5 * NC, NC, e - 1, l);
-          ld5(sm + G::P2, NC, e, r);
-          face_flux<float, 0>(E, l, r, F);
-          st8(sm + G::P1, NC, e, F);
-        } else if (kind == 1) {
-          if (!(zc && j >= 0 && inX)) continue;
-          ld5(sm + G::P2 + 15 * NC, NC, e - W, l);
-          ld5(sm + G::P2 + 10 * NC, NC, e, r);
-          face_flux<float, 1>(E, l, r, F);
-          st8(sm + G::P1 + 8 * NC, NC, e, F);
-        } else {
-          if (!(c >= 0 && inX && inY)) continue;
-          ld5(sm + G::QZFP + pm * 5 * NC, NC, e, l);
-          ld5(sm + G::QZFM, NC, e, r);
-          face_flux<float, 2>(E, l, r, F);
-          st8(sm + G::FFZ + pc * 8 * NC, NC, e, F);
-        }
-      }
-      __syncthreads();
-
-      // ------------------------------------------------ S7: update of plane c-1
-      if (zc) {
-        for (int t = tid; t < NCP; t += NT) {
-          if (!active(t)) continue;
-          const int i = col_i(t), j = col_j(t);
-          if (!(i >= 0 && i < nxt && j >= 0 && j < nyt)) continue;
-          float Fxm[8], Fxp[8], Fym[8], Fyp[8], Fzm[8], Fzp[8];
-          ld8(sm + G::P1, NC, t, Fxm);
-          ld8(sm + G::P1, NC, t + 1, Fxp);
-          ld8(sm + G::P1 + 8 * NC, NC, t, Fym);
-          ld8(sm + G::P1 + 8 * NC, NC, t + W, Fyp);
-          ld8(sm + G::FFZ + pm * 8 * NC, NC, t, Fzm);
-          ld8(sm + G::FFZ + pc * 8 * NC, NC, t, Fzp);
-          const long long id = gcol(i, j) + (long long)(c - 1 + 4) * ps;
-          update_cell_mixed(KK, sc, b, S, Gv, Sn, id, Fxm, Fxp, Fym, Fyp, Fzm, Fzp, dtmin, flags,
-                            a.dtacc != nullptr);
-          if (a.flux_keep) {
-            double *fk = a.flux_keep + a.flux_off[w.box];
-            const int nx = b.n[0], ny = b.n[1];
-            const int gx = w.x0 + i, gy = w.y0 + j, p = c - 1;
-            long long fx = (long long)(nx + 1) * ny * nz;
-            long long ix = ((long long)p * ny + gy) * (nx + 1) + gx;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) fk[k * fx + ix] = (double)Fxm[k];
-            if (gx == nx - 1)
-#pragma unroll
-              for (int k = 0; k < 6; ++k) fk[k * fx + ix + 1] = (double)Fxp[k];
-            fk += 6 * fx;
-            long long fy = (long long)nx * (ny + 1) * nz;
-            long long iy = ((long long)p * (ny + 1) + gy) * nx + gx;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) fk[k * fy + iy] = (double)Fym[k];
-            if (gy == ny - 1)
-#pragma unroll
-              for (int k = 0; k < 6; ++k) fk[k * fy + iy + nx] = (double)Fyp[k];
-            fk += 6 * fy;
-            long long fz = (long long)nx * ny * (nz + 1);
-            long long iz = ((long long)p * ny + gy) * nx + gx;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) fk[k * fz + iz] = (double)Fzm[k];
-            if (p == nz - 1)
-#pragma unroll
-              for (int k = 0; k < 6; ++k) fk[k * fz + iz + (long long)nx * ny] = (double)Fzp[k];
+      {
+        const int kind = tid / NCP, e = tid - kind * NCP;
+        if (active(e)) {
+          const int i = col_i(e), j = col_j(e);
+          const bool inX = i >= 0 && i < nxt, inY = j >= 0 && j < nyt;
+          const float *L, *Rr;
+          float *O;
+          int lc;
+          bool go;
+          if (kind == 0) {
+            go = zc && i >= 0 && inY; L = sm + G::P2 + 5 * NC; lc = e - 1; Rr = sm + G::P2;
+            O = sm + G::P1;
+          } else if (kind == 1) {
+            go = zc && j >= 0 && inX; L = sm + G::P2 + 15 * NC; lc = e - W; Rr = sm + G::P2 + 10 * NC;
+            O = sm + G::P1 + 8 * NC;
+          } else {
+            go = c >= 0 && inX && inY; L = sm + G::QZFP + pm * 5 * NC; lc = e; Rr = sm + G::QZFM;
+            O = sm + G::FFZ + pc * 8 * NC;
+          }
+          if (go) {
+            float l[5], r[5], F[8];
+            ld5(L, NC, lc, l);
+            ld5(Rr, NC, e, r);
+            face_flux_dir(E, kind, l, r, F);
+            st8(O, NC, e, F);
           }
         }
       }
-      // no barrier: the next plane's S0 writes only the primitive ring
+      __syncthreads();
+      // the update of plane c-1 runs in the next plane's S1 (or below for the last plane)
     }
+    // update of the last plane: fluxes of faces nz-3/2 (slot par(nz-1)) and nz-1/2 (par(nz))
+    if (tid < NCP && is_out(tid)) update(tid, nz - 1, par2(nz - 1), par2(nz));
     __syncthreads();
   }
 
