@@ -53,23 +53,49 @@ __device__ __forceinline__ Eos<R> make_eos(const nyx::SchemeConsts &k, bool mixe
   return e;
 }
 
+// double -> float, round to nearest even, flushing results below the
+// smallest normal float to zero (the mixed unit runs with flush-to-zero),
+// computed on the integer pipe: the FP64 pipe of this part is 1/64 of the
+// FP32 rate and also executes the F2F conversion.
+__device__ __forceinline__ float d2f_rn(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned sign = hi & 0x80000000u;
+  const int E = (int)((hi >> 20) & 0x7ffu);
+  const int e = E - 896;
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu;
+  unsigned bits = ((unsigned)e << 23) + m;
+  bits += (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  if (e <= 0) bits = 0u;
+  if (e >= 255) bits = (E == 0x7ff && ((hi & 0xfffffu) | lo)) ? 0x7fc00000u : 0x7f800000u;
+  return __uint_as_float(bits | sign);
+}
+
+template <class R>
+__device__ __forceinline__ R to_r(double x) {
+  if constexpr (sizeof(R) == 4)
+    return d2f_rn(x);
+  else
+    return x;
+}
+
 // primitives (rho, u, v, w, p) of one cell of the state
 template <class R>
 __device__ __forceinline__ void prims_of(const double *S, long long bs, long long id, const Eos<R> &E,
                                          R (&q)[5]) {
-  const R rho = (R)S[id];
+  const R rho = to_r<R>(S[id]);
   q[0] = rho;
   if constexpr (sizeof(R) == 4) {
     const R ir = R(1) / rho;
-    q[1] = (R)S[bs + id] * ir;
-    q[2] = (R)S[2 * bs + id] * ir;
-    q[3] = (R)S[3 * bs + id] * ir;
+    q[1] = to_r<R>(S[bs + id]) * ir;
+    q[2] = to_r<R>(S[2 * bs + id]) * ir;
+    q[3] = to_r<R>(S[3 * bs + id]) * ir;
   } else {
     q[1] = (R)S[bs + id] / rho;
     q[2] = (R)S[2 * bs + id] / rho;
     q[3] = (R)S[3 * bs + id] / rho;
   }
-  R p = E.gm1 * (R)S[5 * bs + id];
+  R p = E.gm1 * to_r<R>(S[5 * bs + id]);
   if (p < E.small_pres) p = E.small_pres;
   q[4] = p;
 }
@@ -214,11 +240,31 @@ __device__ __forceinline__ bool finite_hi(double x) {
 // gravity predictor-corrector, FP64 kinetic-energy subtraction), arranged so
 // that the FP64 pipe does as little as possible: the p div U source term is
 // formed in FP32, 1/rho is an FP32 reciprocal refined by one FP64 Newton step.
+// FP32 constants of the mixed update (converted once per work item).
+struct MixK {
+  float idx0, idx1, idx2, gm1, gamma, small_pres, an_dx0, an_dx1, an_dx2;
+};
+
+__device__ __forceinline__ MixK make_mixk(const nyx::SchemeConsts &k, const nyx::StepConsts &sc,
+                                          const nyx::BoxDev &b) {
+  MixK m;
+  m.idx0 = d2f_rn(b.idx[0]);
+  m.idx1 = d2f_rn(b.idx[1]);
+  m.idx2 = d2f_rn(b.idx[2]);
+  m.gm1 = d2f_rn(k.gm1);
+  m.gamma = d2f_rn(k.gamma);
+  m.small_pres = d2f_rn(k.small_pres);
+  m.an_dx0 = d2f_rn(sc.a_new * b.dx[0]);
+  m.an_dx1 = d2f_rn(sc.a_new * b.dx[1]);
+  m.an_dx2 = d2f_rn(sc.a_new * b.dx[2]);
+  return m;
+}
+
 __device__ __forceinline__ void update_cell_mixed(
-    const nyx::SchemeConsts &k, const nyx::StepConsts &sc, const nyx::BoxDev &b, const double *S,
-    const double *G, double *Sn, long long id, const float (&Fxm)[8], const float (&Fxp)[8],
-    const float (&Fym)[8], const float (&Fyp)[8], const float (&Fzm)[8], const float (&Fzp)[8],
-    double &dtmin, unsigned &flags, bool want_dt) {
+    const nyx::SchemeConsts &k, const nyx::StepConsts &sc, const nyx::BoxDev &b, const MixK &mk,
+    const double *S, const double *G, double *Sn, long long id, const float (&Fxm)[8],
+    const float (&Fxp)[8], const float (&Fym)[8], const float (&Fyp)[8], const float (&Fzm)[8],
+    const float (&Fzp)[8], float &dtmin, unsigned &flags, bool want_dt) {
   const long long bs = b.stride;
   double div[6];
 #pragma unroll
@@ -228,9 +274,9 @@ __device__ __forceinline__ void update_cell_mixed(
     const double dz_ = f2d_exact(Fzp[c]) - f2d_exact(Fzm[c]);
     div[c] = dx_ * b.idx[0] + dy_ * b.idx[1] + dz_ * b.idx[2];
   }
-  const float pdivu_f = 0.5f * (Fxp[7] + Fxm[7]) * (Fxp[6] - Fxm[6]) * (float)b.idx[0] +
-                        0.5f * (Fyp[7] + Fym[7]) * (Fyp[6] - Fym[6]) * (float)b.idx[1] +
-                        0.5f * (Fzp[7] + Fzm[7]) * (Fzp[6] - Fzm[6]) * (float)b.idx[2];
+  const float pdivu_f = 0.5f * (Fxp[7] + Fxm[7]) * (Fxp[6] - Fxm[6]) * mk.idx0 +
+                        0.5f * (Fyp[7] + Fym[7]) * (Fyp[6] - Fym[6]) * mk.idx1 +
+                        0.5f * (Fzp[7] + Fzm[7]) * (Fzp[6] - Fzm[6]) * mk.idx2;
   const double pdivu = f2d_exact(pdivu_f);
   const double rho = S[id];
   const double m0 = S[bs + id], m1 = S[2 * bs + id], m2 = S[3 * bs + id];
@@ -259,7 +305,7 @@ __device__ __forceinline__ void update_cell_mixed(
     rEn = rE_s + sc.hdt * (sc.a_new * msg - sc.a_old * mg) * sc.ian2;
   }
   // 1/rho: FP32 reciprocal, one Newton step in FP64 (relative error ~1e-14)
-  const float rho_f = (float)rho_s;
+  const float rho_f = d2f_rn(rho_s);
   double ir = f2d_exact(1.0f / rho_f);
   ir = ir * (2.0 - rho_s * ir);
   const double ke = 0.5 * (mn0 * mn0 + mn1 * mn1 + mn2 * mn2) * ir;
@@ -285,16 +331,14 @@ __device__ __forceinline__ void update_cell_mixed(
   Sn[5 * bs + id] = ren;
   if (want_dt) {
     const float irf = 1.0f / rho_f;
-    float p = (float)k.gm1 * (float)ren;
-    if (p < (float)k.small_pres) p = (float)k.small_pres;
-    const float c2 = (float)k.gamma * p * irf;
+    float p = mk.gm1 * d2f_rn(ren);
+    if (p < mk.small_pres) p = mk.small_pres;
+    const float c2 = mk.gamma * p * irf;
     const float c = c2 * rsqrtf(c2);
-    const float an = (float)sc.a_new;
-    const float t0 = an * (float)b.dx[0] / (fabsf((float)mn0 * irf) + c);
-    const float t1 = an * (float)b.dx[1] / (fabsf((float)mn1 * irf) + c);
-    const float t2 = an * (float)b.dx[2] / (fabsf((float)mn2 * irf) + c);
-    const float tm = fminf(t0, fminf(t1, t2));
-    if ((double)tm < dtmin) dtmin = (double)tm;
+    const float t0 = mk.an_dx0 / (fabsf(d2f_rn(mn0) * irf) + c);
+    const float t1 = mk.an_dx1 / (fabsf(d2f_rn(mn1) * irf) + c);
+    const float t2 = mk.an_dx2 / (fabsf(d2f_rn(mn2) * irf) + c);
+    dtmin = fminf(dtmin, fminf(t0, fminf(t1, t2)));
   }
 }
 
@@ -347,6 +391,7 @@ __global__ void __launch_bounds__(FusedGeom<R, TX, TY>::NT, 1) k_fused(nyx::Fuse
     const R dtdx0 = (R)bst.dtdx[0], dtdx1 = (R)bst.dtdx[1], dtdx2 = (R)bst.dtdx[2];
     const R c30 = (R)bst.cdt3[0], c31 = (R)bst.cdt3[1], c32 = (R)bst.cdt3[2];
     const R ch0 = (R)bst.chalf[0], ch1 = (R)bst.chalf[1], ch2 = (R)bst.chalf[2];
+    const MixK mixk = make_mixk(KK, sc, b);
 
     // own-column z window: planes c-2 .. c+2
     R win[5][5];
@@ -415,9 +460,9 @@ __global__ void __launch_bounds__(FusedGeom<R, TX, TY>::NT, 1) k_fused(nyx::Fuse
         R g3[3] = {R(0), R(0), R(0)};
         if (G) {
           const long long id = col + (long long)(c + 4) * ps;
-          g3[0] = (R)G[id];
-          g3[1] = (R)G[bs + id];
-          g3[2] = (R)G[2 * bs + id];
+          g3[0] = to_r<R>(G[id]);
+          g3[1] = to_r<R>(G[bs + id]);
+          g3[2] = to_r<R>(G[2 * bs + id]);
         }
         R s[5][5];
 #pragma unroll
@@ -583,10 +628,12 @@ __global__ void __launch_bounds__(FusedGeom<R, TX, TY>::NT, 1) k_fused(nyx::Fuse
           Fyp[k] = B[(8 + k) * NC + me + W];
         }
         const long long id = col + (long long)(c - 1 + 4) * ps;
-        if constexpr (sizeof(R) == 4)
-          update_cell_mixed(KK, sc, b, S, G, Sn, id, Fxm, Fxp, Fym, Fyp, Ffz_prev, Ffz, dtmin,
+        if constexpr (sizeof(R) == 4) {
+          float dtf = __int_as_float(0x7f800000);
+          update_cell_mixed(KK, sc, b, mixk, S, G, Sn, id, Fxm, Fxp, Fym, Fyp, Ffz_prev, Ffz, dtf,
                             flags, a.dtacc != nullptr);
-        else
+          if ((double)dtf < dtmin) dtmin = (double)dtf;
+        } else
           update_cell<R>(KK, sc, b, S, G, Sn, id, Fxm, Fxp, Fym, Fyp, Ffz_prev, Ffz, dtmin, flags,
                          a.dtacc != nullptr);
         if (a.flux_keep) {

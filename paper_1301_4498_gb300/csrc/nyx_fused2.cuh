@@ -81,6 +81,38 @@ __device__ __forceinline__ void ld8(const float *b, int nc, int cell, float (&F)
   for (int k = 0; k < 8; ++k) F[k] = b[k * nc + cell];
 }
 
+// Copy one cell's final fluxes (low faces, and the high faces on the box's
+// last column/row/plane) into the flux store of its box: x block (6, nz, ny,
+// nx+1), then y block (6, nz, ny+1, nx), then z block (6, nz+1, ny, nx).
+__device__ __forceinline__ void keep_fluxes(double *fk, int nx, int ny, int nz, int gx, int gy,
+                                            int p, const float (&Fxm)[8], const float (&Fxp)[8],
+                                            const float (&Fym)[8], const float (&Fyp)[8],
+                                            const float (&Fzm)[8], const float (&Fzp)[8]) {
+  const long long fx = (long long)(nx + 1) * ny * nz;
+  const long long ix = ((long long)p * ny + gy) * (nx + 1) + gx;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) fk[k * fx + ix] = (double)Fxm[k];
+  if (gx == nx - 1)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) fk[k * fx + ix + 1] = (double)Fxp[k];
+  fk += 6 * fx;
+  const long long fy = (long long)nx * (ny + 1) * nz;
+  const long long iy = ((long long)p * (ny + 1) + gy) * nx + gx;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) fk[k * fy + iy] = (double)Fym[k];
+  if (gy == ny - 1)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) fk[k * fy + iy + nx] = (double)Fyp[k];
+  fk += 6 * fy;
+  const long long fz = (long long)nx * ny * (nz + 1);
+  const long long iz = ((long long)p * ny + gy) * nx + gx;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) fk[k * fz + iz] = (double)Fzm[k];
+  if (p == nz - 1)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) fk[k * fz + iz + (long long)nx * ny] = (double)Fzp[k];
+}
+
 // Lab frame (rho, u_x, u_y, u_z, p) <-> the normal frame of face direction
 // dir (rho, u_n, u_t1, u_t2, p), with dir warp-uniform: selects, no local
 // memory.  Tangential axes in increasing order, as everywhere else.
@@ -129,11 +161,17 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
   const nyx::StepConsts sc = *a.SC;
   const Eos<float> E = make_eos<float>(KK, true);
   TraceSrc<float> src;
-  src.hdtp = (float)sc.hdtp;
-  src.src_u = (float)sc.src_u;
-  src.src_p = (float)sc.src_p;
+  src.hdtp = d2f_rn(sc.hdtp);
+  src.src_u = d2f_rn(sc.src_u);
+  src.src_p = d2f_rn(sc.src_p);
   const int tid = threadIdx.x;
-  double dtmin = __longlong_as_double(0x7ff0000000000000LL);
+  // Every task of this thread is on one owned column: kind kq (and kq+3 in
+  // the six-kind stages) of column me.
+  const int kq = tid / NCP;
+  const int me = tid - kq * NCP;
+  const int mi = me % W - 1, mj = me / W - 1;
+  const int mee = (mj + 3) * WE + (mi + 3);
+  float dtmin = __int_as_float(0x7f800000);
   unsigned flags = 0;
 
   for (;;) {
@@ -150,102 +188,72 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
     const double *S = a.S + nyx::NCONS * b.pref;
     const double *Gv = a.G ? a.G + nyx::NGRAV * b.pref : nullptr;
     double *Sn = a.Sn + nyx::NCONS * b.pref;
-    const float dtdx0 = (float)bst.dtdx[0], dtdx1 = (float)bst.dtdx[1], dtdx2 = (float)bst.dtdx[2];
-    const float c30 = (float)bst.cdt3[0], c31 = (float)bst.cdt3[1], c32 = (float)bst.cdt3[2];
-    const float ch0 = (float)bst.chalf[0], ch1 = (float)bst.chalf[1], ch2 = (float)bst.chalf[2];
+    const MixK mk = make_mixk(KK, sc, b);
+    const float dtdx0 = d2f_rn(bst.dtdx[0]), dtdx1 = d2f_rn(bst.dtdx[1]), dtdx2 = d2f_rn(bst.dtdx[2]);
+    const float c30 = d2f_rn(bst.cdt3[0]), c31 = d2f_rn(bst.cdt3[1]), c32 = d2f_rn(bst.cdt3[2]);
+    const float ch0 = d2f_rn(bst.chalf[0]), ch1 = d2f_rn(bst.chalf[1]), ch2 = d2f_rn(bst.chalf[2]);
     const int nstrip = 4 * (nxt + 2) + 4 * (nyt + 2);
-    auto col_i = [&](int e) { return e % W - 1; };
-    auto col_j = [&](int e) { return e / W - 1; };
-    auto active = [&](int e) { return e < NC && (e % W - 1) <= nxt && (e / W - 1) <= nyt; };
-    auto gcol = [&](int i, int j) {
-      return (long long)(w.y0 + j + 4) * b.N[0] + (w.x0 + i + 4);
-    };
+    // geometry of this thread's column for this tile
+    const bool act = me < NC && mi <= nxt && mj <= nyt;
+    const bool inX = mi >= 0 && mi < nxt, inY = mj >= 0 && mj < nyt;
+    const long long mycol = (long long)(w.y0 + mj + 4) * b.N[0] + (w.x0 + mi + 4);
+    // this thread's update cell (updates are packed onto whole warps)
+    const int nout = nxt * nyt;
+    const bool upd = tid < nout;
+    const int ui = upd ? tid % nxt : 0, uj = upd ? tid / nxt : 0;
+    const int ue = (uj + 1) * W + (ui + 1);
+    const long long ucol = (long long)(w.y0 + uj + 4) * b.N[0] + (w.x0 + ui + 4);
+
     auto load_prims = [&](long long id, int slot, int ecell) {
       float q[5];
       prims_of<float>(S, bs, id, E, q);
 #pragma unroll
       for (int v = 0; v < 5; ++v) sm[G::PR + (slot * 5 + v) * NE + ecell] = q[v];
     };
-    // FP64 update of plane p from the final fluxes in the shared buffers:
-    // x, y faces in P1 (written by the last final-solve stage), z faces in
-    // the FFZ ring slots sm_lo (face p-1/2) and sm_hi (face p+1/2).
-    auto update = [&](int e, int p, int slot_lo, int slot_hi) {
-      const int i = col_i(e), j = col_j(e);
+    // FP64 update of plane p: x, y faces from P1 (the last final-solve
+    // stage), z faces from FFZ ring slots slot_lo (face p-1/2) and slot_hi.
+    auto update = [&](int p, int slot_lo, int slot_hi) {
       float Fxm[8], Fxp[8], Fym[8], Fyp[8], Fzm[8], Fzp[8];
-      ld8(sm + G::P1, NC, e, Fxm);
-      ld8(sm + G::P1, NC, e + 1, Fxp);
-      ld8(sm + G::P1 + 8 * NC, NC, e, Fym);
-      ld8(sm + G::P1 + 8 * NC, NC, e + W, Fyp);
-      ld8(sm + G::FFZ + slot_lo * 8 * NC, NC, e, Fzm);
-      ld8(sm + G::FFZ + slot_hi * 8 * NC, NC, e, Fzp);
-      const long long id = gcol(i, j) + (long long)(p + 4) * ps;
-      update_cell_mixed(KK, sc, b, S, Gv, Sn, id, Fxm, Fxp, Fym, Fyp, Fzm, Fzp, dtmin, flags,
+      ld8(sm + G::P1, NC, ue, Fxm);
+      ld8(sm + G::P1, NC, ue + 1, Fxp);
+      ld8(sm + G::P1 + 8 * NC, NC, ue, Fym);
+      ld8(sm + G::P1 + 8 * NC, NC, ue + W, Fyp);
+      ld8(sm + G::FFZ + slot_lo * 8 * NC, NC, ue, Fzm);
+      ld8(sm + G::FFZ + slot_hi * 8 * NC, NC, ue, Fzp);
+      const long long id = ucol + (long long)(p + 4) * ps;
+      update_cell_mixed(KK, sc, b, mk, S, Gv, Sn, id, Fxm, Fxp, Fym, Fyp, Fzm, Fzp, dtmin, flags,
                         a.dtacc != nullptr);
-      if (a.flux_keep) {
-        double *fk = a.flux_keep + a.flux_off[w.box];
-        const int nx = b.n[0], ny = b.n[1];
-        const int gx = w.x0 + i, gy = w.y0 + j;
-        long long fx = (long long)(nx + 1) * ny * nz;
-        long long ix = ((long long)p * ny + gy) * (nx + 1) + gx;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) fk[k * fx + ix] = (double)Fxm[k];
-        if (gx == nx - 1)
-#pragma unroll
-          for (int k = 0; k < 6; ++k) fk[k * fx + ix + 1] = (double)Fxp[k];
-        fk += 6 * fx;
-        long long fy = (long long)nx * (ny + 1) * nz;
-        long long iy = ((long long)p * (ny + 1) + gy) * nx + gx;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) fk[k * fy + iy] = (double)Fym[k];
-        if (gy == ny - 1)
-#pragma unroll
-          for (int k = 0; k < 6; ++k) fk[k * fy + iy + nx] = (double)Fyp[k];
-        fk += 6 * fy;
-        long long fz = (long long)nx * ny * (nz + 1);
-        long long iz = ((long long)p * ny + gy) * nx + gx;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) fk[k * fz + iz] = (double)Fzm[k];
-        if (p == nz - 1)
-#pragma unroll
-          for (int k = 0; k < 6; ++k) fk[k * fz + iz + (long long)nx * ny] = (double)Fzp[k];
-      }
-    };
-    auto is_out = [&](int e) {
-      if (!active(e)) return false;
-      const int i = col_i(e), j = col_j(e);
-      return i >= 0 && i < nxt && j >= 0 && j < nyt;
+      if (a.flux_keep)
+        keep_fluxes(a.flux_keep + a.flux_off[w.box], b.n[0], b.n[1], nz, w.x0 + ui, w.y0 + uj, p,
+                    Fxm, Fxp, Fym, Fyp, Fzm, Fzp);
     };
 
     // prologue: planes -3 .. 0 of every owned column
     for (int t = tid; t < 4 * NCP; t += NT) {
-      const int o = t / NCP, e = t - o * NCP;
-      if (!active(e)) continue;
-      const int i = col_i(e), j = col_j(e), p = o - 3;
-      load_prims(gcol(i, j) + (long long)(p + 4) * ps, ring5(p), (j + 3) * WE + (i + 3));
+      const int p = t / NCP - 3;
+      if (act) load_prims(mycol + (long long)(p + 4) * ps, ring5(p), mee);
     }
 
     for (int c = -1; c <= nz; ++c) {
       const int pc = par2(c), pm = par2(c - 1);
       const bool zc = c >= 1;
       // ------------------------------------------------ S0: primitives (+ gravity of plane c)
-      for (int t = tid; t < NCP + nstrip; t += NT) {
-        if (t < NCP) {
-          if (!active(t)) continue;
-          const int i = col_i(t), j = col_j(t);
-          const long long cc = gcol(i, j);
-          load_prims(cc + (long long)(c + 2 + 4) * ps, ring5(c + 2), (j + 3) * WE + (i + 3));
+      if (tid < NCP) {
+        if (act) {
+          load_prims(mycol + (long long)(c + 2 + 4) * ps, ring5(c + 2), mee);
           float g0 = 0.f, g1 = 0.f, g2 = 0.f;
           if (Gv) {
-            const long long id = cc + (long long)(c + 4) * ps;
-            g0 = (float)Gv[id];
-            g1 = (float)Gv[bs + id];
-            g2 = (float)Gv[2 * bs + id];
+            const long long id = mycol + (long long)(c + 4) * ps;
+            g0 = d2f_rn(Gv[id]);
+            g1 = d2f_rn(Gv[bs + id]);
+            g2 = d2f_rn(Gv[2 * bs + id]);
           }
-          sm[G::GR + t] = g0;
-          sm[G::GR + NC + t] = g1;
-          sm[G::GR + 2 * NC + t] = g2;
-        } else {
-          const int u = t - NCP;
+          sm[G::GR + me] = g0;
+          sm[G::GR + NC + me] = g1;
+          sm[G::GR + 2 * NC + me] = g2;
+        }
+      } else {
+        for (int u = tid - NCP; u < nstrip; u += NT - NCP) {
           int x, y;
           if (u < 4 * (nyt + 2)) {
             const int r = u % (nyt + 2), s2 = u / (nyt + 2);
@@ -257,7 +265,9 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
             x = r - 1;
             y = (s2 < 2) ? (-3 + s2) : (nyt + 1 + (s2 - 2));
           }
-          load_prims(gcol(x, y) + (long long)(c + 4) * ps, ring5(c), (y + 3) * WE + (x + 3));
+          const long long id =
+              ((long long)(c + 4) * b.N[1] + (w.y0 + y + 4)) * b.N[0] + (w.x0 + x + 4);
+          load_prims(id, ring5(c), (y + 3) * WE + (x + 3));
         }
       }
       __syncthreads();
@@ -265,278 +275,249 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
       // ------------------------------------------------ S1: update of plane c-2, tracing at plane c
       // The update (FP64 pipe) goes first so that it overlaps the FP32 tracing
       // of the other warps.  Its fluxes stay untouched until the S2 barrier.
-      if (c >= 2 && tid < NCP && is_out(tid)) update(tid, c - 2, pc, pm);
-      {
-        const int dir = tid / NCP, e = tid - dir * NCP;
-        if (active(e)) {
-          const int i = col_i(e), j = col_j(e);
-          const int ee = (j + 3) * WE + (i + 3);
-          const float *P0 = sm + G::PR + ring5(c) * 5 * NE;
-          const float rho = P0[ee], p = P0[4 * NE + ee];
-          const float cs2 = E.gamma * p / rho;
-          const float cs = cs2 * rsqrtf(cs2);
-          float gl[3] = {sm[G::GR + e], sm[G::GR + NC + e], sm[G::GR + 2 * NC + e]};
-          float gn[3];
-          gn[0] = (dir == 0) ? gl[0] : ((dir == 1) ? gl[1] : gl[2]);
-          gn[1] = (dir == 0) ? gl[1] : gl[0];
-          gn[2] = (dir == 2) ? gl[1] : gl[2];
-          float s5[5][5];
+      if (c >= 2 && upd) update(c - 2, pc, pm);
+      if (act) {
+        const int dir = kq;
+        const float *P0 = sm + G::PR + ring5(c) * 5 * NE;
+        const float rho = P0[mee], p = P0[4 * NE + mee];
+        const float cs2 = E.gamma * p / rho;
+        const float cs = cs2 * rsqrtf(cs2);
+        const float gl0 = sm[G::GR + me], gl1 = sm[G::GR + NC + me], gl2 = sm[G::GR + 2 * NC + me];
+        float gn[3];
+        gn[0] = (dir == 0) ? gl0 : ((dir == 1) ? gl1 : gl2);
+        gn[1] = (dir == 0) ? gl1 : gl0;
+        gn[2] = (dir == 2) ? gl1 : gl2;
+        float s5[5][5];
 #pragma unroll
-          for (int o = 0; o < 5; ++o) {
-            const float *Po;
-            int cell;
-            if (dir == 0) {
-              Po = P0;
-              cell = ee + (o - 2);
-            } else if (dir == 1) {
-              Po = P0;
-              cell = ee + (o - 2) * WE;
-            } else {
-              Po = sm + G::PR + ring5(c - 2 + o) * 5 * NE;
-              cell = ee;
-            }
-            float ql[5], qn[5];
+        for (int o = 0; o < 5; ++o) {
+          const float *Po = (dir == 2) ? sm + G::PR + ring5(c - 2 + o) * 5 * NE : P0;
+          const int cell = (dir == 0) ? mee + (o - 2) : ((dir == 1) ? mee + (o - 2) * WE : mee);
+          float ql[5], qn[5];
 #pragma unroll
-            for (int v = 0; v < 5; ++v) ql[v] = Po[v * NE + cell];
-            to_normal(dir, ql, qn);
+          for (int v = 0; v < 5; ++v) ql[v] = Po[v * NE + cell];
+          to_normal(dir, ql, qn);
 #pragma unroll
-            for (int v = 0; v < 5; ++v) s5[v][o] = qn[v];
-          }
-          const float dtdx = (dir == 0) ? dtdx0 : ((dir == 1) ? dtdx1 : dtdx2);
-          float qmn[5], qpn[5], qm[5], qp[5];
-          trace_cell<float, 0>(E, s5, cs, gn, dtdx, src, qmn, qpn);
-          to_lab(dir, qmn, qm);
-          to_lab(dir, qpn, qp);
-          float *dst = (dir == 2) ? sm + G::QZ + pc * 10 * NC : sm + G::QXY + (pc * 2 + dir) * 10 * NC;
-          st5(dst, NC, e, qm);
-          st5(dst + 5 * NC, NC, e, qp);
+          for (int v = 0; v < 5; ++v) s5[v][o] = qn[v];
         }
+        const float dtdx = (dir == 0) ? dtdx0 : ((dir == 1) ? dtdx1 : dtdx2);
+        float qmn[5], qpn[5], qm[5], qp[5];
+        trace_cell<float, 0>(E, s5, cs, gn, dtdx, src, qmn, qpn);
+        to_lab(dir, qmn, qm);
+        to_lab(dir, qpn, qp);
+        float *dst = (dir == 2) ? sm + G::QZ + pc * 10 * NC : sm + G::QXY + (pc * 2 + dir) * 10 * NC;
+        st5(dst, NC, me, qm);
+        st5(dst + 5 * NC, NC, me, qp);
       }
       __syncthreads();
 
       // ------------------------------------------------ S2: normal solves
-      {
-        const int kind = tid / NCP, e = tid - kind * NCP;
-        if (active(e)) {
-          const int i = col_i(e), j = col_j(e);
-          const float *L, *Rr;
-          float *O;
-          int lc;
-          bool go;
-          if (kind == 0) {
-            go = i >= 0;
-            L = sm + G::QXY + (pc * 2 + 0) * 10 * NC + 5 * NC;
-            lc = e - 1;
-            Rr = sm + G::QXY + (pc * 2 + 0) * 10 * NC;
-            O = sm + G::P1;
-          } else if (kind == 1) {
-            go = j >= 0;
-            L = sm + G::QXY + (pc * 2 + 1) * 10 * NC + 5 * NC;
-            lc = e - W;
-            Rr = sm + G::QXY + (pc * 2 + 1) * 10 * NC;
-            O = sm + G::P1 + 7 * NC;
-          } else {
-            go = c >= 0;
-            L = sm + G::QZ + pm * 10 * NC + 5 * NC;
-            lc = e;
-            Rr = sm + G::QZ + pc * 10 * NC;
-            O = sm + G::FZ + pc * 7 * NC;
-          }
-          if (go) {
-            float l[5], r[5], F[8];
-            ld5(L, NC, lc, l);
-            ld5(Rr, NC, e, r);
-            face_flux_dir(E, kind, l, r, F);
-            st7(O, NC, e, F);
-          }
+      if (act) {
+        const float *L, *Rr;
+        float *O;
+        int lc;
+        bool go;
+        if (kq == 0) {
+          go = mi >= 0;
+          L = sm + G::QXY + (pc * 2 + 0) * 10 * NC + 5 * NC;
+          lc = me - 1;
+          Rr = sm + G::QXY + (pc * 2 + 0) * 10 * NC;
+          O = sm + G::P1;
+        } else if (kq == 1) {
+          go = mj >= 0;
+          L = sm + G::QXY + (pc * 2 + 1) * 10 * NC + 5 * NC;
+          lc = me - W;
+          Rr = sm + G::QXY + (pc * 2 + 1) * 10 * NC;
+          O = sm + G::P1 + 7 * NC;
+        } else {
+          go = c >= 0;
+          L = sm + G::QZ + pm * 10 * NC + 5 * NC;
+          lc = me;
+          Rr = sm + G::QZ + pc * 10 * NC;
+          O = sm + G::FZ + pc * 7 * NC;
+        }
+        if (go) {
+          float l[5], r[5], F[8];
+          ld5(L, NC, lc, l);
+          ld5(Rr, NC, me, r);
+          face_flux_dir(E, kq, l, r, F);
+          st7(O, NC, me, F);
         }
       }
       __syncthreads();
 
       // ------------------------------------------------ S3: corner coupling, theta = 1/3
-      for (int t = tid; t < 6 * NCP; t += NT) {
-        const int kind = t / NCP, e = t - kind * NCP;
-        if (!active(e)) continue;
-        const int i = col_i(e), j = col_j(e);
-        const bool inX = i >= 0 && i < nxt, inY = j >= 0 && j < nyt;
-        const float *Q, *Fmb, *Fpb;
-        float *Om, *Op;
-        int fpc;
-        float coef;
-        bool go;
-        switch (kind) {
-          case 0:  // q_{x|y} at c
-            go = inY; Q = sm + G::QXY + (pc * 2 + 0) * 10 * NC; Fmb = Fpb = sm + G::P1 + 7 * NC;
-            fpc = e + W; coef = c31; Om = sm + G::P2; Op = sm + G::P2 + 5 * NC;
-            break;
-          case 1:  // q_{y|x} at c
-            go = inX; Q = sm + G::QXY + (pc * 2 + 1) * 10 * NC; Fmb = Fpb = sm + G::P1;
-            fpc = e + 1; coef = c30; Om = sm + G::P2 + 10 * NC; Op = sm + G::P2 + 15 * NC;
-            break;
-          case 2:  // q_{z|x} at c
-            go = inX; Q = sm + G::QZ + pc * 10 * NC; Fmb = Fpb = sm + G::P1;
-            fpc = e + 1; coef = c30; Om = sm + G::QZXM; Op = sm + G::QZXP + pc * 5 * NC;
-            break;
-          case 3:  // q_{z|y} at c
-            go = inY; Q = sm + G::QZ + pc * 10 * NC; Fmb = Fpb = sm + G::P1 + 7 * NC;
-            fpc = e + W; coef = c31; Om = sm + G::QZYM; Op = sm + G::QZYP + pc * 5 * NC;
-            break;
-          case 4:  // q_{x|z} at c-1
-            go = zc; Q = sm + G::QXY + (pm * 2 + 0) * 10 * NC; Fmb = sm + G::FZ + pm * 7 * NC;
-            Fpb = sm + G::FZ + pc * 7 * NC; fpc = e; coef = c32;
-            Om = sm + G::P2 + 20 * NC; Op = sm + G::P2 + 25 * NC;
-            break;
-          default:  // q_{y|z} at c-1
-            go = zc; Q = sm + G::QXY + (pm * 2 + 1) * 10 * NC; Fmb = sm + G::FZ + pm * 7 * NC;
-            Fpb = sm + G::FZ + pc * 7 * NC; fpc = e; coef = c32;
-            Om = sm + G::P2 + 30 * NC; Op = sm + G::P2 + 35 * NC;
-            break;
+      if (act) {
+#pragma unroll 1
+        for (int rep = 0; rep < 2; ++rep) {
+          const int kind = kq + 3 * rep;
+          const float *Q, *Fmb, *Fpb;
+          float *Om, *Op;
+          int fpc;
+          float coef;
+          bool go;
+          switch (kind) {
+            case 0:  // q_{x|y} at c
+              go = inY; Q = sm + G::QXY + (pc * 2 + 0) * 10 * NC; Fmb = Fpb = sm + G::P1 + 7 * NC;
+              fpc = me + W; coef = c31; Om = sm + G::P2; Op = sm + G::P2 + 5 * NC;
+              break;
+            case 1:  // q_{y|x} at c
+              go = inX; Q = sm + G::QXY + (pc * 2 + 1) * 10 * NC; Fmb = Fpb = sm + G::P1;
+              fpc = me + 1; coef = c30; Om = sm + G::P2 + 10 * NC; Op = sm + G::P2 + 15 * NC;
+              break;
+            case 2:  // q_{z|x} at c
+              go = inX; Q = sm + G::QZ + pc * 10 * NC; Fmb = Fpb = sm + G::P1;
+              fpc = me + 1; coef = c30; Om = sm + G::QZXM; Op = sm + G::QZXP + pc * 5 * NC;
+              break;
+            case 3:  // q_{z|y} at c
+              go = inY; Q = sm + G::QZ + pc * 10 * NC; Fmb = Fpb = sm + G::P1 + 7 * NC;
+              fpc = me + W; coef = c31; Om = sm + G::QZYM; Op = sm + G::QZYP + pc * 5 * NC;
+              break;
+            case 4:  // q_{x|z} at c-1
+              go = zc; Q = sm + G::QXY + (pm * 2 + 0) * 10 * NC; Fmb = sm + G::FZ + pm * 7 * NC;
+              Fpb = sm + G::FZ + pc * 7 * NC; fpc = me; coef = c32;
+              Om = sm + G::P2 + 20 * NC; Op = sm + G::P2 + 25 * NC;
+              break;
+            default:  // q_{y|z} at c-1
+              go = zc; Q = sm + G::QXY + (pm * 2 + 1) * 10 * NC; Fmb = sm + G::FZ + pm * 7 * NC;
+              Fpb = sm + G::FZ + pc * 7 * NC; fpc = me; coef = c32;
+              Om = sm + G::P2 + 30 * NC; Op = sm + G::P2 + 35 * NC;
+              break;
+          }
+          if (go) {
+            const TFlux<float> Fm = ld7(Fmb, NC, me), Fp = ld7(Fpb, NC, fpc);
+            float qa[5], qb[5], oa[5], ob[5];
+            ld5(Q, NC, me, qa);
+            ld5(Q + 5 * NC, NC, me, qb);
+            transverse1(E, qa, coef, Fp, Fm, oa);
+            transverse1(E, qb, coef, Fp, Fm, ob);
+            st5(Om, NC, me, oa);
+            st5(Op, NC, me, ob);
+          }
         }
-        if (!go) continue;
-        const TFlux<float> Fm = ld7(Fmb, NC, e), Fp = ld7(Fpb, NC, fpc);
-        float qa[5], qb[5], oa[5], ob[5];
-        ld5(Q, NC, e, qa);
-        ld5(Q + 5 * NC, NC, e, qb);
-        transverse1(E, qa, coef, Fp, Fm, oa);
-        transverse1(E, qb, coef, Fp, Fm, ob);
-        st5(Om, NC, e, oa);
-        st5(Op, NC, e, ob);
       }
       __syncthreads();
 
       // ------------------------------------------------ S4: intermediate solves
-      for (int t = tid; t < 6 * NCP; t += NT) {
-        const int kind = t / NCP, e = t - kind * NCP;
-        if (!active(e)) continue;
-        const int i = col_i(e), j = col_j(e);
-        const bool inX = i >= 0 && i < nxt, inY = j >= 0 && j < nyt;
-        const float *L, *Rr;
-        float *O;
-        int lc, dir;
-        bool go;
-        switch (kind) {
-          case 0:  // F^{x|y} at c
-            go = i >= 0 && inY; dir = 0; L = sm + G::P2 + 5 * NC; lc = e - 1; Rr = sm + G::P2;
-            O = sm + G::P1;
-            break;
-          case 1:  // F^{y|x} at c
-            go = j >= 0 && inX; dir = 1; L = sm + G::P2 + 15 * NC; lc = e - W;
-            Rr = sm + G::P2 + 10 * NC; O = sm + G::P1 + 7 * NC;
-            break;
-          case 2:  // F^{x|z} at c-1
-            go = zc && i >= 0; dir = 0; L = sm + G::P2 + 25 * NC; lc = e - 1;
-            Rr = sm + G::P2 + 20 * NC; O = sm + G::P1 + 14 * NC;
-            break;
-          case 3:  // F^{y|z} at c-1
-            go = zc && j >= 0; dir = 1; L = sm + G::P2 + 35 * NC; lc = e - W;
-            Rr = sm + G::P2 + 30 * NC; O = sm + G::P1 + 21 * NC;
-            break;
-          case 4:  // F^{z|x} at face c-1/2
-            go = c >= 0 && inX; dir = 2; L = sm + G::QZXP + pm * 5 * NC; lc = e;
-            Rr = sm + G::QZXM; O = sm + G::FZXY + (pc * 2 + 0) * 7 * NC;
-            break;
-          default:  // F^{z|y} at face c-1/2
-            go = c >= 0 && inY; dir = 2; L = sm + G::QZYP + pm * 5 * NC; lc = e;
-            Rr = sm + G::QZYM; O = sm + G::FZXY + (pc * 2 + 1) * 7 * NC;
-            break;
+      if (act) {
+#pragma unroll 1
+        for (int rep = 0; rep < 2; ++rep) {
+          const int kind = kq + 3 * rep;
+          const float *L, *Rr;
+          float *O;
+          int lc, dir;
+          bool go;
+          switch (kind) {
+            case 0:  // F^{x|y} at c
+              go = mi >= 0 && inY; dir = 0; L = sm + G::P2 + 5 * NC; lc = me - 1; Rr = sm + G::P2;
+              O = sm + G::P1;
+              break;
+            case 1:  // F^{y|x} at c
+              go = mj >= 0 && inX; dir = 1; L = sm + G::P2 + 15 * NC; lc = me - W;
+              Rr = sm + G::P2 + 10 * NC; O = sm + G::P1 + 7 * NC;
+              break;
+            case 2:  // F^{x|z} at c-1
+              go = zc && mi >= 0; dir = 0; L = sm + G::P2 + 25 * NC; lc = me - 1;
+              Rr = sm + G::P2 + 20 * NC; O = sm + G::P1 + 14 * NC;
+              break;
+            case 3:  // F^{y|z} at c-1
+              go = zc && mj >= 0; dir = 1; L = sm + G::P2 + 35 * NC; lc = me - W;
+              Rr = sm + G::P2 + 30 * NC; O = sm + G::P1 + 21 * NC;
+              break;
+            case 4:  // F^{z|x} at face c-1/2
+              go = c >= 0 && inX; dir = 2; L = sm + G::QZXP + pm * 5 * NC; lc = me;
+              Rr = sm + G::QZXM; O = sm + G::FZXY + (pc * 2 + 0) * 7 * NC;
+              break;
+            default:  // F^{z|y} at face c-1/2
+              go = c >= 0 && inY; dir = 2; L = sm + G::QZYP + pm * 5 * NC; lc = me;
+              Rr = sm + G::QZYM; O = sm + G::FZXY + (pc * 2 + 1) * 7 * NC;
+              break;
+          }
+          if (go) {
+            float l[5], r[5], F[8];
+            ld5(L, NC, lc, l);
+            ld5(Rr, NC, me, r);
+            face_flux_dir(E, dir, l, r, F);
+            st7(O, NC, me, F);
+          }
         }
-        if (!go) continue;
-        float l[5], r[5], F[8];
-        ld5(L, NC, lc, l);
-        ld5(Rr, NC, e, r);
-        face_flux_dir(E, dir, l, r, F);
-        st7(O, NC, e, F);
       }
       __syncthreads();
 
       // ------------------------------------------------ S5: final states, theta = 1/2
-      {
-        const int kind = tid / NCP, e = tid - kind * NCP;
-        if (active(e)) {
-          const int i = col_i(e), j = col_j(e);
-          const bool inX = i >= 0 && i < nxt, inY = j >= 0 && j < nyt;
-          const float *Q, *Ab, *Bmb, *Bpb;
-          float *Om, *Op;
-          int apc, bpc;
-          float k1c, k2c;
-          bool go;
-          if (kind == 0) {  // z at plane c: F^{x|y} in x, F^{y|x} in y
-            go = inX && inY; Q = sm + G::QZ + pc * 10 * NC;
-            Ab = sm + G::P1; apc = e + 1; k1c = ch0;
-            Bmb = Bpb = sm + G::P1 + 7 * NC; bpc = e + W; k2c = ch1;
-            Om = sm + G::QZFM; Op = sm + G::QZFP + pc * 5 * NC;
-          } else if (kind == 1) {  // x at plane c-1: F^{y|z} in y, F^{z|y} in z
-            go = zc && inY; Q = sm + G::QXY + (pm * 2 + 0) * 10 * NC;
-            Ab = sm + G::P1 + 21 * NC; apc = e + W; k1c = ch1;
-            Bmb = sm + G::FZXY + (pm * 2 + 1) * 7 * NC; Bpb = sm + G::FZXY + (pc * 2 + 1) * 7 * NC;
-            bpc = e; k2c = ch2;
-            Om = sm + G::P2; Op = sm + G::P2 + 5 * NC;
-          } else {  // y at plane c-1: F^{x|z} in x, F^{z|x} in z
-            go = zc && inX; Q = sm + G::QXY + (pm * 2 + 1) * 10 * NC;
-            Ab = sm + G::P1 + 14 * NC; apc = e + 1; k1c = ch0;
-            Bmb = sm + G::FZXY + (pm * 2 + 0) * 7 * NC; Bpb = sm + G::FZXY + (pc * 2 + 0) * 7 * NC;
-            bpc = e; k2c = ch2;
-            Om = sm + G::P2 + 10 * NC; Op = sm + G::P2 + 15 * NC;
-          }
-          if (go) {
-            const TFlux<float> Am = ld7(Ab, NC, e), Ap = ld7(Ab, NC, apc);
-            const TFlux<float> Bm = ld7(Bmb, NC, e), Bp = ld7(Bpb, NC, bpc);
-            float qa[5], qb[5], oa[5], ob[5];
-            ld5(Q, NC, e, qa);
-            ld5(Q + 5 * NC, NC, e, qb);
-            transverse2(E, qa, k1c, Ap, Am, k2c, Bp, Bm, oa);
-            transverse2(E, qb, k1c, Ap, Am, k2c, Bp, Bm, ob);
-            st5(Om, NC, e, oa);
-            st5(Op, NC, e, ob);
-          }
+      if (act) {
+        const float *Q, *Ab, *Bmb, *Bpb;
+        float *Om, *Op;
+        int apc, bpc;
+        float k1c, k2c;
+        bool go;
+        if (kq == 0) {  // z at plane c: F^{x|y} in x, F^{y|x} in y
+          go = inX && inY; Q = sm + G::QZ + pc * 10 * NC;
+          Ab = sm + G::P1; apc = me + 1; k1c = ch0;
+          Bmb = Bpb = sm + G::P1 + 7 * NC; bpc = me + W; k2c = ch1;
+          Om = sm + G::QZFM; Op = sm + G::QZFP + pc * 5 * NC;
+        } else if (kq == 1) {  // x at plane c-1: F^{y|z} in y, F^{z|y} in z
+          go = zc && inY; Q = sm + G::QXY + (pm * 2 + 0) * 10 * NC;
+          Ab = sm + G::P1 + 21 * NC; apc = me + W; k1c = ch1;
+          Bmb = sm + G::FZXY + (pm * 2 + 1) * 7 * NC; Bpb = sm + G::FZXY + (pc * 2 + 1) * 7 * NC;
+          bpc = me; k2c = ch2;
+          Om = sm + G::P2; Op = sm + G::P2 + 5 * NC;
+        } else {  // y at plane c-1: F^{x|z} in x, F^{z|x} in z
+          go = zc && inX; Q = sm + G::QXY + (pm * 2 + 1) * 10 * NC;
+          Ab = sm + G::P1 + 14 * NC; apc = me + 1; k1c = ch0;
+          Bmb = sm + G::FZXY + (pm * 2 + 0) * 7 * NC; Bpb = sm + G::FZXY + (pc * 2 + 0) * 7 * NC;
+          bpc = me; k2c = ch2;
+          Om = sm + G::P2 + 10 * NC; Op = sm + G::P2 + 15 * NC;
+        }
+        if (go) {
+          const TFlux<float> Am = ld7(Ab, NC, me), Ap = ld7(Ab, NC, apc);
+          const TFlux<float> Bm = ld7(Bmb, NC, me), Bp = ld7(Bpb, NC, bpc);
+          float qa[5], qb[5], oa[5], ob[5];
+          ld5(Q, NC, me, qa);
+          ld5(Q + 5 * NC, NC, me, qb);
+          transverse2(E, qa, k1c, Ap, Am, k2c, Bp, Bm, oa);
+          transverse2(E, qb, k1c, Ap, Am, k2c, Bp, Bm, ob);
+          st5(Om, NC, me, oa);
+          st5(Op, NC, me, ob);
         }
       }
       __syncthreads();
 
       // ------------------------------------------------ S6: final solves
-      {
-        const int kind = tid / NCP, e = tid - kind * NCP;
-        if (active(e)) {
-          const int i = col_i(e), j = col_j(e);
-          const bool inX = i >= 0 && i < nxt, inY = j >= 0 && j < nyt;
-          const float *L, *Rr;
-          float *O;
-          int lc;
-          bool go;
-          if (kind == 0) {
-            go = zc && i >= 0 && inY; L = sm + G::P2 + 5 * NC; lc = e - 1; Rr = sm + G::P2;
-            O = sm + G::P1;
-          } else if (kind == 1) {
-            go = zc && j >= 0 && inX; L = sm + G::P2 + 15 * NC; lc = e - W; Rr = sm + G::P2 + 10 * NC;
-            O = sm + G::P1 + 8 * NC;
-          } else {
-            go = c >= 0 && inX && inY; L = sm + G::QZFP + pm * 5 * NC; lc = e; Rr = sm + G::QZFM;
-            O = sm + G::FFZ + pc * 8 * NC;
-          }
-          if (go) {
-            float l[5], r[5], F[8];
-            ld5(L, NC, lc, l);
-            ld5(Rr, NC, e, r);
-            face_flux_dir(E, kind, l, r, F);
-            st8(O, NC, e, F);
-          }
+      if (act) {
+        const float *L, *Rr;
+        float *O;
+        int lc;
+        bool go;
+        if (kq == 0) {
+          go = zc && mi >= 0 && inY; L = sm + G::P2 + 5 * NC; lc = me - 1; Rr = sm + G::P2;
+          O = sm + G::P1;
+        } else if (kq == 1) {
+          go = zc && mj >= 0 && inX; L = sm + G::P2 + 15 * NC; lc = me - W; Rr = sm + G::P2 + 10 * NC;
+          O = sm + G::P1 + 8 * NC;
+        } else {
+          go = c >= 0 && inX && inY; L = sm + G::QZFP + pm * 5 * NC; lc = me; Rr = sm + G::QZFM;
+          O = sm + G::FFZ + pc * 8 * NC;
+        }
+        if (go) {
+          float l[5], r[5], F[8];
+          ld5(L, NC, lc, l);
+          ld5(Rr, NC, me, r);
+          face_flux_dir(E, kq, l, r, F);
+          st8(O, NC, me, F);
         }
       }
       __syncthreads();
       // the update of plane c-1 runs in the next plane's S1 (or below for the last plane)
     }
-    // update of the last plane: fluxes of faces nz-3/2 (slot par(nz-1)) and nz-1/2 (par(nz))
-    if (tid < NCP && is_out(tid)) update(tid, nz - 1, par2(nz - 1), par2(nz));
+    // update of the last plane: z faces nz-3/2 (slot par(nz-1)) and nz-1/2 (par(nz))
+    if (upd) update(nz - 1, par2(nz - 1), par2(nz));
     __syncthreads();
   }
 
   if (a.dtacc) {
-    for (int o = 16; o > 0; o >>= 1) {
-      double v = __shfl_xor_sync(0xffffffffu, dtmin, o);
-      if (v < dtmin) dtmin = v;
-    }
-    if ((tid & 31) == 0 && dtmin < __longlong_as_double(0x7ff0000000000000LL))
-      nyx::atomic_min_pos(a.dtacc, dtmin);
+    for (int o = 16; o > 0; o >>= 1) dtmin = fminf(dtmin, __shfl_xor_sync(0xffffffffu, dtmin, o));
+    if ((tid & 31) == 0 && dtmin < __int_as_float(0x7f800000))
+      nyx::atomic_min_pos(a.dtacc, (double)dtmin);
   }
   if (flags) atomicOr(a.status, flags);
 }
