@@ -25,7 +25,9 @@ struct G2 {
   static constexpr int W = TX + 2, H = TY + 2, NC = W * H;
   static constexpr int NCP = (NC + 31) / 32 * 32;  // task stride of one kind
   static constexpr int WE = TX + 6, HE = TY + 6, NE = WE * HE;
-  static constexpr int NT = 3 * NCP;
+  static constexpr int NTC = 3 * NCP;                     // column-task threads
+  static constexpr int NU = (TX * TY + 31) / 32 * 32;     // update threads
+  static constexpr int NT = NTC + NU;
   // shared layout, in floats
   static constexpr int PR = 0;                       // [5 planes][5 vars][NE] primitives
   static constexpr int QXY = PR + 25 * NE;           // [2 planes][2 dirs x,y][10][NC] traced x, y
@@ -153,6 +155,7 @@ template <int TX, int TY, int MB>
 __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a) {
   using G = G2<TX, TY>;
   constexpr int NC = G::NC, NCP = G::NCP, NE = G::NE, W = G::W, WE = G::WE, NT = G::NT;
+  constexpr int NTC = G::NTC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float *sm = reinterpret_cast<float *>(smem_raw);
   __shared__ int s_item;
@@ -165,10 +168,13 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
   src.src_u = d2f_rn(sc.src_u);
   src.src_p = d2f_rn(sc.src_p);
   const int tid = threadIdx.x;
-  // Every task of this thread is on one owned column: kind kq (and kq+3 in
-  // the six-kind stages) of column me.
-  const int kq = tid / NCP;
-  const int me = tid - kq * NCP;
+  // Threads [0, NTC) take column tasks: every task of such a thread is on one
+  // owned column, kind kq (and kq+3 in the six-kind stages) of column me.
+  // Threads [NTC, NT) are the update warps: the FP64 update of one output
+  // cell each, overlapped with the tracing of the column threads.
+  const bool colthr = tid < NTC;
+  const int kq = colthr ? tid / NCP : 3;
+  const int me = colthr ? tid - kq * NCP : NCP;
   const int mi = me % W - 1, mj = me / W - 1;
   const int mee = (mj + 3) * WE + (mi + 3);
   float dtmin = __int_as_float(0x7f800000);
@@ -194,13 +200,14 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
     const float ch0 = d2f_rn(bst.chalf[0]), ch1 = d2f_rn(bst.chalf[1]), ch2 = d2f_rn(bst.chalf[2]);
     const int nstrip = 4 * (nxt + 2) + 4 * (nyt + 2);
     // geometry of this thread's column for this tile
-    const bool act = me < NC && mi <= nxt && mj <= nyt;
+    const bool act = colthr && me < NC && mi <= nxt && mj <= nyt;
     const bool inX = mi >= 0 && mi < nxt, inY = mj >= 0 && mj < nyt;
     const long long mycol = (long long)(w.y0 + mj + 4) * b.N[0] + (w.x0 + mi + 4);
-    // this thread's update cell (updates are packed onto whole warps)
+    // this thread's update cell (update threads only, packed on whole warps)
     const int nout = nxt * nyt;
-    const bool upd = tid < nout;
-    const int ui = upd ? tid % nxt : 0, uj = upd ? tid / nxt : 0;
+    const int uthr = tid - NTC;
+    const bool upd = !colthr && uthr < nout;
+    const int ui = upd ? uthr % nxt : 0, uj = upd ? uthr / nxt : 0;
     const int ue = (uj + 1) * W + (ui + 1);
     const long long ucol = (long long)(w.y0 + uj + 4) * b.N[0] + (w.x0 + ui + 4);
 
@@ -228,10 +235,11 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
                     Fxm, Fxp, Fym, Fyp, Fzm, Fzp);
     };
 
-    // prologue: planes -3 .. 0 of every owned column
-    for (int t = tid; t < 4 * NCP; t += NT) {
-      const int p = t / NCP - 3;
-      if (act) load_prims(mycol + (long long)(p + 4) * ps, ring5(p), mee);
+    // prologue: planes -3 .. -1 of every owned column (column threads of
+    // kinds 0, 1, 2) and plane 0 (kind 0 again)
+    if (act) {
+      load_prims(mycol + (long long)(kq - 3 + 4) * ps, ring5(kq - 3), mee);
+      if (kq == 0) load_prims(mycol + (long long)(0 + 4) * ps, ring5(0), mee);
     }
 
     for (int c = -1; c <= nz; ++c) {
@@ -253,6 +261,7 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
           sm[G::GR + 2 * NC + me] = g2;
         }
       } else {
+        // the halo strips: every thread that is not a kind-0 column thread
         for (int u = tid - NCP; u < nstrip; u += NT - NCP) {
           int x, y;
           if (u < 4 * (nyt + 2)) {
