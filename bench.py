@@ -66,6 +66,8 @@ def make_workload(name: str, nsteps: int, sample_only: bool = False):
         return W.comoving_box(n=128, sigma=0.5, seed=1, nsteps=max(nsteps, 10))
     if name == "uneven512":
         return W.uneven_boxes(nbox=512, nsteps=max(nsteps, 10))
+    if name == "large128":  # the large level's box sizes on a 128^3 domain (profiling case)
+        return W.large_level(n=128, box=32, nfine=6, nsteps=max(nsteps, 1))
     if name == "uneven64":  # the first 64 boxes of the 512-box level (profiling case)
         return W.uneven_boxes(nbox=512, boxes=list(range(64)), nsteps=max(nsteps, 10))
     if name == "mixed256":
@@ -378,7 +380,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="large",
-                    choices=["large", "comoving128", "uneven512", "uneven64", "mixed256", "sod"])
+                    choices=["large", "large128", "comoving128", "uneven512", "uneven64", "mixed256",
+                             "sod"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--tile-shape", type=int, default=-1,

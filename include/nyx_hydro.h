@@ -202,6 +202,32 @@ int nyx_hydro_counters_read(nyx_plan *plan, int reset, nyx_hydro_counters *out);
  * most severe raised bit. */
 int nyx_hydro_status(nyx_plan *plan, int *flags);
 
+/* Allocation-free CFL step (no counterpart in the paper: it serves callers,
+ * not the method).  Same result as nyx_hydro_estdt for a state laid out as
+ * nyx_hydro_layout describes, but without a plan: it calls no cudaMalloc,
+ * cudaFree or allocating library routine.  It is for callers that cannot
+ * allocate device memory -- code running where a framework or application
+ * owns every device allocation, or a latency-critical loop that must not
+ * enter the allocator.
+ *  - Scratch: one file-scope __device__ array of fixed size (box table for up
+ *    to NYX_NOALLOC_MAX_BOXES boxes, cell offsets, the min accumulator and
+ *    the scheme constants, about 0.4 MB), held by every GPU that loads the
+ *    library until the process exits.  Levels with more boxes are rejected
+ *    with NYX_EINVAL.
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current); make that first call before any stream capture.
+ *  - Every call shares the array and leaves its contents behind; each call
+ *    rewrites the tables and resets the accumulator before use.  Calls that
+ *    overlap on the GPU (other streams, other host threads) race.
+ *  - level, params: host descriptors as for nyx_hydro_plan (ng must be 4).
+ *    state: device field of 6 components.  a_dev, dt_dev: device scalars.
+ *    stream: a cudaStream_t (NULL = legacy default stream).  Asynchronous
+ *    apart from the staging of the tables; errors as elsewhere. */
+#define NYX_NOALLOC_MAX_BOXES 4096
+int nyx_hydro_estdt_noalloc(const nyx_level_desc *level, const nyx_hydro_params *params,
+                            const double *state, const double *a_dev, double *dt_dev,
+                            void *stream);
+
 /* Release the plan's device and host resources (not the caller's buffers). */
 int nyx_plan_destroy(nyx_plan *plan);
 

@@ -495,6 +495,8 @@ int enqueue_run(nyx_plan *P, nyx_level *L, const double *a_dev, double *dt_dev, 
 // ====================================================================== fused dispatch
 namespace nyx {
 
+void record_error(const char *msg) { g_err = msg ? msg : ""; }
+
 // 0-2: column-owning form (FP64 and mixed); 3-5: task form (mixed only)
 static const TileShape kShapes[] = {{16, 16}, {32, 8}, {16, 8}, {16, 8}, {8, 8}, {32, 4}};
 

@@ -6,6 +6,9 @@
 
 namespace nyx {
 
+// Set the message nyx_last_error() returns on this thread.
+void record_error(const char *msg);
+
 void launch_fill(double *field, int ncomp, const BoxDev *boxes, const FillRect *rects,
                  const long long *rect_pref, int nrect, long long total, cudaStream_t st);
 

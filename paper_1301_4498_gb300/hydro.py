@@ -27,6 +27,7 @@ NYX_FP64 = 0
 NYX_MIXED = 1
 NYX_PERSISTENT = 0
 NYX_PER_BOX = 1
+NOALLOC_MAX_BOXES = 4096  # NYX_NOALLOC_MAX_BOXES of include/nyx_hydro.h
 
 _lib = None
 
@@ -105,11 +106,13 @@ def load_library(path: str | None = None):
     L.nyx_hydro_get_tile_shape.argtypes = [vp, ip]
     L.nyx_hydro_profile.argtypes = [vp, C.c_int]
     L.nyx_hydro_counters_read.argtypes = [vp, C.c_int, C.POINTER(NyxCounters)]
+    L.nyx_hydro_estdt_noalloc.argtypes = [C.POINTER(NyxLevelDesc), C.POINTER(NyxParams), vp, vp,
+                                          vp, vp]
     for name in ("nyx_hydro_plan", "nyx_hydro_layout", "nyx_hydro_fill", "nyx_hydro_estdt",
                  "nyx_hydro_advance", "nyx_hydro_run", "nyx_hydro_fluxes", "nyx_hydro_step_host",
                  "nyx_hydro_status", "nyx_plan_destroy", "nyx_hydro_tile_shape",
                  "nyx_hydro_set_tile_shape", "nyx_hydro_get_tile_shape", "nyx_hydro_profile",
-                 "nyx_hydro_counters_read"):
+                 "nyx_hydro_counters_read", "nyx_hydro_estdt_noalloc"):
         getattr(L, name).restype = C.c_int
     if path is None:
         _lib = L
@@ -350,6 +353,18 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def estdt_noalloc(spec, state, a_dev, dt_dev, stream=None, **params):
+    """nyx_hydro_estdt_noalloc: the CFL step of a level field without a plan
+    and without any device allocation (scratch in a fixed device array)."""
+    import torch
+    desc, keep = level_desc(spec)
+    p = make_params(**params)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(load_library().nyx_hydro_estdt_noalloc(C.byref(desc), C.byref(p), _ptr(state),
+                                                   _ptr(a_dev), _ptr(dt_dev), C.c_void_p(stream)))
 
 
 def make_level(plan, states, grav=None):
