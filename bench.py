@@ -57,33 +57,37 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def make_workload(name: str, nsteps: int, sample_only: bool = False):
-    if name == "large":
+def make_workload(name: str, sample_only: bool = False):
+    """The named workload with its prescribed scale-factor schedule (the
+    bench takes the first K+1 values of it)."""
+    if name == "large":  # a from 1/51 to 1/31 over 100 steps
         if sample_only:  # the independent 64^3 boxes only: what the CPU sample uses
-            return W.large_level(nsteps=max(nsteps, 1), coarse_select=[], fine_select=range(16))
-        return W.large_level(nsteps=max(nsteps, 1))
-    if name == "comoving128":
-        return W.comoving_box(n=128, sigma=0.5, seed=1, nsteps=max(nsteps, 10))
-    if name == "uneven512":
-        return W.uneven_boxes(nbox=512, nsteps=max(nsteps, 10))
+            return W.large_level(nsteps=100, coarse_select=[], fine_select=range(16))
+        return W.large_level(nsteps=100)
     if name == "large128":  # the large level's box sizes on a 128^3 domain (profiling case)
-        return W.large_level(n=128, box=32, nfine=6, nsteps=max(nsteps, 1))
+        return W.large_level(n=128, box=32, nfine=6, nsteps=100)
+    if name == "comoving128":
+        return W.comoving_box(n=128, sigma=0.5, seed=1, nsteps=10)
+    if name == "uneven512":
+        return W.uneven_boxes(nbox=512, nsteps=10)
     if name == "uneven64":  # the first 64 boxes of the 512-box level (profiling case)
-        return W.uneven_boxes(nbox=512, boxes=list(range(64)), nsteps=max(nsteps, 10))
+        return W.uneven_boxes(nbox=512, boxes=list(range(64)), nsteps=10)
     if name == "mixed256":
-        return W.comoving_box(n=256, sigma=1.0, seed=4, nsteps=max(nsteps, 50), mixed=True)
+        return W.comoving_box(n=256, sigma=1.0, seed=4, nsteps=50, mixed=True)
     if name == "sod":
         return W.sod()
     raise SystemExit(f"unknown workload {name}")
 
 
 def a_schedule_for(w, nsteps):
-    """a_0..a_nsteps from the workload's schedule (cycled if longer)."""
+    """a_0..a_nsteps: the workload's schedule, continued linearly (never
+    cycled back) if more steps are asked for than it prescribes."""
     a = np.asarray(w.a_sched, dtype=np.float64)
     if len(a) >= nsteps + 1:
         return a[: nsteps + 1].copy()
-    reps = (nsteps + 1 + len(a) - 1) // len(a)
-    return np.tile(a, reps)[: nsteps + 1]
+    step = (a[-1] - a[0]) / max(1, len(a) - 1)
+    extra = a[-1] + step * np.arange(1, nsteps + 2 - len(a))
+    return np.concatenate([a, extra])
 
 
 class ClockSampler:
@@ -397,7 +401,7 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
-    w = make_workload(args.workload, args.steps, sample_only=args.impl == "reference")
+    w = make_workload(args.workload, sample_only=args.impl == "reference")
     if args.impl == "reference":
         run_reference(args, w)
     else:
