@@ -311,7 +311,8 @@ def tiled_box(n=64, box=32, sigma=0.5, seed=1, nsteps=2, a0=1.0 / 51, aN=1.0 / 4
 
 
 def large_level(n=512, box=32, nfine=410, fine_n=64, sigma=1.0, seed=5, nsteps=100,
-                fine_seed0=50000, fine_select=None, coarse_select=None) -> Workload:
+                fine_seed0=50000, fine_select=None, coarse_select=None,
+                keep_fields=False) -> Workload:
     """A periodic n^3 level cut into (n/box)^3 boxes of box^3 plus ``nfine``
     independent periodic fine_n^3 boxes at half the cell width (a seeded 10%
     refined subset; no coarse-fine coupling).  a from 1/51 to 1/31.
@@ -332,6 +333,7 @@ def large_level(n=512, box=32, nfine=410, fine_n=64, sigma=1.0, seed=5, nsteps=1
         s, g = _patch_state(clev, i, fb)
         S.append(s)
         G.append(g)
+    coarse_fields = f if keep_fields else None
     del f
     fsel = list(fsel)
     fine = independent_boxes_level([(fine_n,) * 3] * len(fsel), 0.5 / n, name="fine")
@@ -344,8 +346,26 @@ def large_level(n=512, box=32, nfine=410, fine_n=64, sigma=1.0, seed=5, nsteps=1
         lev = fine
     else:
         lev = merge_levels(clev, fine, name="large") if len(fsel) else clev
-    return Workload(f"{n}^3 level as {coarse.nbox} boxes of {box}^3 + {nfine} boxes of {fine_n}^3",
-                    lev, S, G, a_schedule(1.0 / 51, 1.0 / 31, nsteps), 5.0 / 3.0, 0.5, nsteps, True)
+    w = Workload(f"{n}^3 level as {coarse.nbox} boxes of {box}^3 + {nfine} boxes of {fine_n}^3",
+                 lev, S, G, a_schedule(1.0 / 51, 1.0 / 31, nsteps), 5.0 / 3.0, 0.5, nsteps, True)
+    if keep_fields:
+        w.level.meta["coarse_fields"] = coarse_fields
+        w.level.meta["coarse_n"] = n
+        w.level.meta["coarse_boxes"] = len(list(csel))
+    return w
+
+
+def ghosted_patch(fields: Fields, lo, hi, ng=NG):
+    """State and gravity of the box [lo, hi] of a periodic patch with its
+    ghost cells taken from the same patch (periodic wrap): the input a
+    single box needs to be advanced one step on its own."""
+    nz, ny, nx = fields.rho.shape
+    idx = [np.arange(lo[d] - ng, hi[d] + ng + 1) % n for d, n in enumerate((nx, ny, nz))]
+    sl = np.ix_(idx[2], idx[1], idx[0])
+    rho = fields.rho[sl]
+    u = np.stack([fields.u[c][sl] for c in range(3)])
+    g = np.stack([fields.g[c][sl] for c in range(3)])
+    return conserved_from_primitive(rho, u, rho * E0), g
 
 
 def sound_wave(n, amp=1e-5, direction=(1, 0, 0), nz=8, gamma=5.0 / 3.0) -> Workload:

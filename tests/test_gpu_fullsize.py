@@ -1,0 +1,161 @@
+"""Parity at the full sizes of the named workloads, in the launch
+configuration bench.py times (persistent fused kernel, tile shape chosen by
+the autotuner, CUDA graph), against the FP64 oracle:
+
+* 128^3 comoving box, 10 steps: FP64 within 1e-12, mixed within the gates;
+* 512 uneven boxes: every box one step; 16 boxes (independent periodic
+  domains) for all 10 steps;
+* 256^3 box with sigma = 1.0: mixed path against the oracle over 2 steps, and
+  its per-field L1/L-inf error against the FP64 GPU path (itself pinned to
+  the oracle) over 50 steps, printed;
+* the large level (512^3 as 4096 boxes of 32^3 + 410 boxes of 64^3): one
+  step of each precision; sampled boxes recomputed by the oracle one by one
+  (coarse boxes from ghost regions cut out of the generator's full field,
+  fine boxes whole).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1301_4498_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1301_4498_gb300 import hydro as H  # noqa: E402
+from test_gpu_parity import FP64_TOL, MIXED_GATES, field_errors  # noqa: E402
+
+
+def run_gpu(w, nsteps, precision, use_graph=True, autotune=1, a_sched=None):
+    plan = H.Plan(w.level, gamma=w.gamma, cfl=w.cfl, precision=precision, autotune=autotune)
+    lev = H.make_level(plan, w.state, w.grav)
+    a_host = np.asarray(w.a_sched if a_sched is None else a_sched, dtype=np.float64)[:nsteps + 1]
+    a = torch.tensor(a_host, device="cuda")
+    dt = torch.zeros(nsteps + 1, dtype=torch.float64, device="cuda")
+    plan.run(lev, a, dt, nsteps, compute_dt0=True, use_graph=use_graph)
+    torch.cuda.synchronize()
+    rc, flags = plan.status()
+    assert rc == H.NYX_OK, (rc, flags)
+    return plan.from_device(lev.current, 6), dt.cpu().numpy()
+
+
+def check(err, precision):
+    for k, (linf, l1) in err.items():
+        if precision == "fp64":
+            assert linf <= FP64_TOL, (k, err)
+        else:
+            assert linf <= MIXED_GATES["linf"] and l1 <= MIXED_GATES["l1"], (k, err)
+
+
+def test_comoving_128_ten_steps():
+    w = W.comoving_box(n=128, sigma=0.5, seed=1, nsteps=10)
+    ref, dts, _ = oracle.run(w.level, oracle.OracleParams(gamma=w.gamma, cfl=w.cfl), w.state,
+                             w.grav, w.a_sched, 10)
+    for precision in ("fp64", "mixed"):
+        S, dt = run_gpu(w, 10, precision)
+        err = field_errors(S, ref)
+        print(f"comoving128 10 steps {precision}:", err)
+        check(err, precision)
+        if precision == "fp64":
+            assert np.array_equal(dt[:10], np.asarray(dts))
+
+
+def test_uneven_512_boxes():
+    w = W.uneven_boxes(nbox=512, nsteps=10)
+    P = oracle.OracleParams(gamma=w.gamma, cfl=w.cfl)
+    ref, dts, _ = oracle.run(w.level, P, w.state, w.grav, w.a_sched, 1)
+    for precision in ("fp64", "mixed"):
+        S, dt = run_gpu(w, 1, precision)
+        err = field_errors(S, ref)
+        print(f"uneven512 1 step {precision}:", err)
+        check(err, precision)
+    S1, _ = run_gpu(w, 1, "fp64", use_graph=False, autotune=0)
+    plan = H.Plan(w.level, gamma=w.gamma, cfl=w.cfl, batching="per_box")
+    lev = H.make_level(plan, w.state, w.grav)
+    a = torch.tensor(w.a_sched[:2], dtype=torch.float64, device="cuda")
+    d = torch.zeros(2, dtype=torch.float64, device="cuda")
+    plan.run(lev, a, d, 1, compute_dt0=True, use_graph=False)
+    S2 = plan.from_device(lev.current, 6)
+    for x, y in zip(S1, S2):
+        assert np.array_equal(W.valid(x), W.valid(y))
+    # 16 whole boxes (independent periodic domains) for all 10 steps
+    sub = W.uneven_boxes(nbox=512, boxes=list(range(0, 512, 32)), nsteps=10)
+    ref10, _, _ = oracle.run(sub.level, P, sub.state, sub.grav, sub.a_sched, 10)
+    for precision in ("fp64", "mixed"):
+        S, _ = run_gpu(sub, 10, precision)
+        err = field_errors(S, ref10)
+        print(f"uneven512 subset 10 steps {precision}:", err)
+        check(err, precision)
+
+
+def test_mixed_256_sigma1():
+    w = W.comoving_box(n=256, sigma=1.0, seed=4, nsteps=50, mixed=True)
+    ref2, _, _ = oracle.run(w.level, oracle.OracleParams(gamma=w.gamma, cfl=w.cfl), w.state,
+                            w.grav, w.a_sched, 2)
+    S2, _ = run_gpu(w, 2, "mixed")
+    err2 = field_errors(S2, ref2)
+    print("mixed256 2 steps mixed vs oracle:", err2)
+    check(err2, "mixed")
+    S64, _ = run_gpu(w, 50, "fp64")
+    S32, _ = run_gpu(w, 50, "mixed")
+    err50 = field_errors(S32, S64)
+    print("mixed256 50 steps mixed vs FP64 GPU (L-inf, L1):", err50)
+    for k, (linf, l1) in err50.items():
+        assert l1 <= 1e-3 and linf <= 0.1, (k, err50)
+
+
+def test_large_level_sampled_boxes():
+    w = W.large_level(nsteps=100, keep_fields=True)
+    f = w.level.meta.pop("coarse_fields")
+    ncoarse = w.level.meta["coarse_boxes"]
+    P = oracle.OracleParams(gamma=w.gamma, cfl=w.cfl)
+    a0, a1 = float(w.a_sched[0]), float(w.a_sched[1])
+    dt_or = oracle.estdt(w.level, P, w.state, a0)
+    rng = np.random.default_rng(11)
+    coarse = sorted(rng.choice(ncoarse, 6, replace=False).tolist()) + [0, ncoarse - 1]
+    fine = sorted(rng.choice(np.arange(ncoarse, w.level.nbox), 3, replace=False).tolist())
+    # oracle, box by box, with the same dt
+    ref = {}
+    for b in coarse:
+        S0, G0 = W.ghosted_patch(f, w.level.lo[b], w.level.hi[b])
+        sub = w.level.subset([b])
+        out, _, _ = oracle.advance(sub, P, [S0], [G0], a_old=a0, a_new=a1, dt=dt_or,
+                                   fill_ghosts=False)
+        ref[b] = out[0]
+    for b in fine:
+        sub = w.level.subset([b])
+        out, _, _ = oracle.advance(sub, P, [w.state[b]], [w.grav[b]], a_old=a0, a_new=a1,
+                                   dt=dt_or)
+        ref[b] = out[0]
+    del f
+    for precision in ("fp64", "mixed"):
+        plan = H.Plan(w.level, gamma=w.gamma, cfl=w.cfl, precision=precision, autotune=1)
+        lev = H.make_level(plan, w.state, w.grav)
+        a = torch.tensor([a0, a1], dtype=torch.float64, device="cuda")
+        dt = torch.tensor([dt_or, 0.0], dtype=torch.float64, device="cuda")
+        plan.run(lev, a, dt, 1, compute_dt0=False, use_graph=True)
+        est = torch.zeros(1, dtype=torch.float64, device="cuda")
+        lev0 = H.Level(lev.state[1 - lev.cur], lev.state[lev.cur], lev.grav, 0)
+        plan.estdt(lev0, a[0:1], est)  # the GPU's own CFL step of the input state
+        torch.cuda.synchronize()
+        rc, flags = plan.status()
+        assert rc == H.NYX_OK, (rc, flags)
+        if precision == "fp64":
+            assert est.item() == dt_or
+        off, st = plan.layout(6)
+        cur = lev.current.cpu().numpy()
+        got, exp = [], []
+        for b in coarse + fine:
+            shp = w.level.shape(b, 6)
+            vol = shp[1] * shp[2] * shp[3]
+            got.append(cur[off[b]:off[b + 1]].reshape(6, st[b])[:, :vol].reshape(shp))
+            exp.append(ref[b])
+        err = field_errors(got, exp)
+        print(f"large level, {len(got)} sampled boxes, 1 step {precision}:", err)
+        check(err, precision)
+        plan.close()
+        del lev
+        torch.cuda.empty_cache()
