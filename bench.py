@@ -43,6 +43,11 @@ ALG_BYTES_PER_ZONE = 120  # read S (6 x 8 B) + g (3 x 8 B), write S (6 x 8 B)
 ALG_FLOPS_PER_ZONE = {"mixed": 3196 + 480 * 3.05, "fp64": 3196 + 480 * 3.73}
 # Peaks from unit counts and the maximum SM clock (2070 MHz): 152 SMs x 128
 # FP32 lanes x 2 (FMA) = 80.5 TFLOP/s; 152 SMs x 2 FP64 FMA/clk x 2 = 1.26 TFLOP/s.
+# DRAM bytes per zone of the task-form kernel at 16 x 8 tiles on the large
+# level's box sizes (ncu capture of the large128 workload, profiles/
+# k_fused2_mixed_large128.md); traffic scales with the cells of boxes of the
+# same sizes.  Reported only for that kernel, workload and shape.
+TRAFFIC_BYTES_PER_ZONE = {("large", 3): 155.5, ("large128", 3): 155.5}
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
@@ -356,7 +361,11 @@ def run_ours(args, w):
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf,
                          "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
-                         "traffic": args.traffic_per_zone * cells if args.traffic_per_zone else None,
+                         "traffic": (args.traffic_per_zone * cells if args.traffic_per_zone else
+                                     (TRAFFIC_BYTES_PER_ZONE[(args.workload, shape)] * cells
+                                      if args.precision == "mixed" and
+                                      (args.workload, shape) in TRAFFIC_BYTES_PER_ZONE else None)),
+                         "traffic_unit": "bytes per launch",
                          "kernel": ("k_fused2 (task form)" if shape >= 3 else
                                     f"k_fused<{'float' if args.precision == 'mixed' else 'double'}>"),
                          "kernel_ms": adv_ms, "alg_flops_per_zone": flops,

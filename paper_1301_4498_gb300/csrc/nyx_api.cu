@@ -69,6 +69,7 @@ struct nyx_plan {
   BoxStep *d_BS = nullptr;
   unsigned long long *d_dtacc = nullptr;
   unsigned *d_status = nullptr;
+  unsigned *d_status_tune = nullptr;  // status of autotuner launches (never reported)
   double *d_scal = nullptr;  // host-call scalars: a_old, a_new, dt, dt_next
   FillPass pass[4];
   // per-box FP64 form
@@ -321,6 +322,7 @@ void free_plan(nyx_plan *P) {
   cudaFree(P->d_BS);
   cudaFree(P->d_dtacc);
   cudaFree(P->d_status);
+  cudaFree(P->d_status_tune);
   cudaFree(P->d_scal);
   for (auto &p : P->pass) {
     cudaFree(p.d_rects);
@@ -456,6 +458,7 @@ int tune_shape(nyx_plan *P, const FusedArgs &base) {
     a.nitems = P->nitems[s];
     a.dtacc = nullptr;
     a.flux_keep = nullptr;
+    a.status = P->d_status_tune;
     int grid = std::min(P->max_grid[s], a.nitems);
     float tot = 0.f;
     for (int rep = 0; rep < 3; ++rep) {
@@ -664,6 +667,8 @@ int nyx_hydro_plan(const nyx_level_desc *lev, const nyx_hydro_params *prm, void 
     TRYC(cudaMemcpy(P->d_dtacc, &inf, sizeof(inf), cudaMemcpyHostToDevice));
     TRYC(cudaMalloc(&P->d_status, sizeof(unsigned)));
     TRYC(cudaMemset(P->d_status, 0, sizeof(unsigned)));
+    TRYC(cudaMalloc(&P->d_status_tune, sizeof(unsigned)));
+    TRYC(cudaMemset(P->d_status_tune, 0, sizeof(unsigned)));
     TRYC(cudaMalloc(&P->d_scal, 4 * sizeof(double)));
     if (prm->batching == NYX_PER_BOX) {
       TRYC(cudaMalloc(&P->d_scratch, sizeof(double) * staged_scratch_doubles(P->Vmax)));
@@ -765,9 +770,11 @@ int nyx_hydro_run(nyx_plan *P, nyx_level *L, const double *a_dev, double *dt_dev
     a.S = L->state[L->cur];
     a.G = L->grav;
     a.Sn = L->state[1 - L->cur];
-    a.status = P->d_status;
+    a.status = P->d_status_tune;
+    // time the shapes on the first step as it will run: its own dt
+    if (compute_dt0) do_estdt(P, L->state[L->cur], a_dev, dt_dev);
     do_fill(P, L->state[L->cur], NCONS);
-    launch_step_setup(P->d_K, a_dev, a_dev + 1, a_dev, P->d_SC, P->d_boxes, P->nbox, P->d_BS,
+    launch_step_setup(P->d_K, a_dev, a_dev + 1, dt_dev, P->d_SC, P->d_boxes, P->nbox, P->d_BS,
                       P->stream);
     int rc = tune_shape(P, a);
     if (rc) return rc;

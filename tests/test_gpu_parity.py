@@ -294,3 +294,27 @@ def test_mixed_flux_export_close_to_oracle(shape):
             for c in range(6):
                 scale = np.abs(r[c]).max()
                 assert np.abs(f[c] - r[c]).max() <= 2e-3 * scale, (shape, b, di, c)
+
+
+def test_autotuned_graph_run_reports_clean_status():
+    """The autotuner times its shapes on the real first step before a graph
+    capture; its timing launches must leave the plan's status clean and the
+    result equal to an untuned eager run with the chosen shape."""
+    w = W.tiled_box(n=64, box=32, nsteps=2)
+    plan = H.Plan(w.level, gamma=w.gamma, cfl=w.cfl, precision="mixed", autotune=1)
+    lev = H.make_level(plan, w.state, w.grav)
+    a = torch.tensor(w.a_sched[:3], dtype=torch.float64, device="cuda")
+    dt = torch.zeros(3, dtype=torch.float64, device="cuda")
+    plan.run(lev, a, dt, 2, compute_dt0=True, use_graph=True)
+    torch.cuda.synchronize()
+    assert plan.status() == (H.NYX_OK, 0)
+    shape = plan.tile_shape()[0]
+    got = plan.from_device(lev.current, 6)
+    plan2 = H.Plan(w.level, gamma=w.gamma, cfl=w.cfl, precision="mixed")
+    plan2.set_tile_shape(shape)
+    lev2 = H.make_level(plan2, w.state, w.grav)
+    dt2 = torch.zeros(3, dtype=torch.float64, device="cuda")
+    plan2.run(lev2, a, dt2, 2, compute_dt0=True, use_graph=False)
+    ref = plan2.from_device(lev2.current, 6)
+    for x, y in zip(got, ref):
+        assert np.array_equal(W.valid(x), W.valid(y))
