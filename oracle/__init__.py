@@ -88,11 +88,10 @@ class OracleParams:
                        self.dual_energy_sync)
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        path = build()
-        L = C.CDLL(path)
+def load(path: str):
+    """Load an oracle library file and declare its entry points."""
+    L = C.CDLL(path)
+    if True:
         dp = C.POINTER(C.c_double)
         L.orc_fill_ghosts.argtypes = [C.POINTER(_Level), C.c_int, C.POINTER(dp)]
         L.orc_fill_ghosts.restype = C.c_int
@@ -109,8 +108,33 @@ def lib():
         L.orc_riemann_counts.restype = None
         L.orc_trace_line.argtypes = [C.POINTER(_Params), C.c_int, dp, dp, C.c_double,
                                      C.c_double, C.c_double, C.c_int, dp, dp, dp, dp]
-        _lib = L
+    return L
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = load(build())
     return _lib
+
+
+class use_library:
+    """Context manager: route every oracle call through another build of
+    nyx_oracle.c (the mutation tests use it to plant mistakes)."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self.saved = _lib
+        _lib = load(self.path)
+        return _lib
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
 
 
 def _dp(a: np.ndarray):

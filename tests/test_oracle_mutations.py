@@ -1,0 +1,102 @@
+"""The pins are strong enough: each plausible mistake planted in a copy of
+the oracle (a dropped term, a wrong sign, index or coefficient, a transposed
+operand) is compiled on the CPU and must make a named pin fail.
+
+The mistakes live only in temporary copies of nyx_oracle.c; the oracle in
+the tree is never modified."""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import test_oracle_ppm as tp
+import test_oracle_riemann as tr
+import test_oracle_step as ts
+import test_oracle_trace as tt
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(os.path.dirname(HERE), "oracle", "nyx_oracle.c")
+
+# name: (text in nyx_oracle.c, replacement, pin that must fail, pin arguments)
+MUTANTS = {
+    "pdV term dropped from rho e": ("- ahdt * pdivu", "- 0.0 * pdivu",
+                                    ts.test_internal_energy_tracks_total_minus_kinetic, ()),
+    "gravity source sign in tracing": ("src->hdtp * g3[d]", "src->hdtp * (-g3[d])",
+                                       tt.test_gravity_shifts_edge_velocity_by_half_step, ()),
+    "corrector without the 1/2": ("rEn = rE_s + hdt *", "rEn = rE_s + dt *",
+                                  ts.test_uniform_gravity_at_rest, ()),
+    "PPM interface coefficient": ("(d1 - d0) * SIXTH", "(d1 - d0) * 0.2",
+                                  tp.test_unlimited_interface_exact_for_cubic_averages, ()),
+    "PPM extremum not flattened": ("if ((sR - si) * (si - sL) <= 0.0)",
+                                   "if ((sR - si) * (si - sL) < -1e300)",
+                                   tp.test_local_extremum_is_flattened, ()),
+    "PPM integral curvature term": ("(1.0 - TWO_THIRDS * sig)", "(1.0 - 0.5 * sig)",
+                                    tp.test_integrals_are_averages_of_the_parabola, ()),
+    "shock sampled on the wrong side": ("star = (s * S < 0.0);", "star = (s * S > 0.0);",
+                                        tr.test_supersonic_upwinding, ()),
+    "tangential velocity from the other slot": ("  g[2] = qo[2];", "  g[2] = qo[3];",
+                                                tr.test_contact_only, ()),
+    "energy flux without p u": ("out[4] = ug * (rhoeg + ke + pg);", "out[4] = ug * (rhoeg + ke);",
+                                tr.test_supersonic_upwinding, ()),
+    "Newton step sign": ("double pn = p - ZL * ZR", "double pn = p + ZL * ZR",
+                         tr.test_symmetric_collision_closed_form, (1.4, 1.0)),
+    "shock curve constant (gamma+1 -> gamma-1)": (
+        "e.kshock = (p->gamma + 1.0) / (2.0 * p->gamma);",
+        "e.kshock = (p->gamma - 1.0) / (2.0 * p->gamma);",
+        tr.test_symmetric_collision_closed_form, (1.4, 1.0)),
+    "expansion drag sign": ("0.5 * adot;", "-0.5 * adot;",
+                            tt.test_expansion_sources_on_uniform_state, ()),
+    "entropy-wave amplitude sign": ("double b0 = dq[1][0] - dq[1][4] * ic2;",
+                                    "double b0 = dq[1][0] + dq[1][4] * ic2;",
+                                    tt.test_acoustic_simple_wave_linear_limit, ()),
+    "acoustic velocity term sign": ("q[v] = ref[v] - cor * (bp - bm);",
+                                    "q[v] = ref[v] - cor * (bp + bm);",
+                                    tt.test_acoustic_wave_in_supersonic_flow, ()),
+    "corner coupling theta 1/3 -> 1/2": ("cdt = dtp / (3.0 * dx[t])", "cdt = dtp / (2.0 * dx[t])",
+                                         ts.test_trilinear_advection_exact, ()),
+    "final-state theta 1/2 -> 1/4": ("c1 = 0.5 * dtp / dx[t1], c2 = 0.5 * dtp / dx[t2]",
+                                     "c1 = 0.25 * dtp / dx[t1], c2 = 0.25 * dtp / dx[t2]",
+                                     ts.test_trilinear_advection_exact, ()),
+    "momentum weighted by a_new": ("(a_old * m[c] - dt * div[1 + c]",
+                                   "(a_new * m[c] - dt * div[1 + c]",
+                                   ts.test_uniform_state_under_expansion, ()),
+    "divergence reads the x neighbour": ("(Ff[d][c * V + id + g.st[d]] - Ff[d][c * V + id])",
+                                         "(Ff[d][c * V + id + g.st[0]] - Ff[d][c * V + id])",
+                                         ts.test_flux_export_reproduces_density_update, ()),
+    "dual-energy switch reversed": ("if (rEn - ke > P->eta_de * rEn)",
+                                    "if (rEn - ke < P->eta_de * rEn)",
+                                    ts.test_dual_energy_switch_direction, (5e-5, True)),
+    "pressure from rho E instead of rho e": ("double p = E->gm1 * S[5 * vol + id];",
+                                             "double p = E->gm1 * S[4 * vol + id];",
+                                             ts.test_dt_closed_form_uniform, ()),
+    "CFL step without a": ("double t = a * dx[d] / (fabs(q6[1 + d]) + q6[5]);",
+                           "double t = dx[d] / (fabs(q6[1 + d]) + q6[5]);",
+                           ts.test_dt_closed_form_uniform, ()),
+    "periodic wrap off by one": ("x = dlo[d] + ((x - dlo[d]) % len + len) % len;",
+                                 "x = dlo[d] + ((x - dlo[d] + 1) % len + len) % len;",
+                                 ts.test_ghost_fill_periodic_outflow_and_tiles, ()),
+}
+
+
+@pytest.fixture(scope="module")
+def mutant_dir(tmp_path_factory):
+    return tmp_path_factory.mktemp("oracle_mutants")
+
+
+@pytest.mark.parametrize("name", list(MUTANTS))
+def test_planted_mistake_is_caught(name, mutant_dir):
+    old, new, pin, args = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation site not found: {old}"
+    tag = str(abs(hash(name)))
+    c = os.path.join(mutant_dir, f"m{tag}.c")
+    so = os.path.join(mutant_dir, f"m{tag}.so")
+    with open(c, "w") as f:
+        f.write(src.replace(old, new))
+    subprocess.run(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                    "-I", os.path.dirname(SRC), "-o", so, c, "-lm"], check=True)
+    pin(*args)  # the pin passes on the oracle itself
+    with oracle.use_library(so):
+        with pytest.raises(AssertionError):
+            pin(*args)

@@ -327,3 +327,55 @@ def test_internal_energy_tracks_total_minus_kinetic():
     # p div U term removed from the rho e update the drift is ~53%
     assert change > 0.2
     assert drift < 0.05
+
+
+@pytest.mark.parametrize("frac,keeps_e", [(5e-5, True), (0.5, False)])
+def test_dual_energy_switch_direction(frac, keeps_e):
+    """Step 6 sync on a uniform moving state (no fluxes act): where
+    rhoE - KE > 1e-4 rhoE the internal energy is re-derived from E, else E is
+    re-derived from the evolved e.  rho e is deliberately inconsistent with
+    rho E - KE on input, so the branch taken shows in the output."""
+    rho, u = 1.0, np.array([2.0, 0.0, 0.0])
+    ke = 0.5 * rho * (u @ u)
+    rhoE = ke / (1.0 - frac)          # (rhoE - KE)/rhoE = frac
+    rhoe = 0.3 * (rhoE - ke)          # evolved e, not equal to E - KE
+    S0 = np.array([rho, rho * u[0], 0.0, 0.0, rhoE, rhoe])
+    w = W.uniform_level(S0, n=(8, 8, 8), dx=1 / 8)
+    P = oracle.OracleParams(gamma=G53)
+    S, st, _ = _one_step(w, P, dt=1e-3)
+    v = W.valid(S[0])
+    if keeps_e:
+        assert np.allclose(v[5], rhoe, rtol=1e-12)
+        assert np.allclose(v[4], rhoe + ke, rtol=1e-12)
+    else:
+        assert np.allclose(v[4], rhoE, rtol=1e-12)
+        assert np.allclose(v[5], rhoE - ke, rtol=1e-9)
+
+
+def test_trilinear_advection_exact():
+    """Uniform velocity and pressure: the Euler equations reduce to linear
+    advection of rho.  For a trilinear density field the fully corner-coupled
+    scheme (theta = 1/3 for the singly corrected states, 1/2 for the final
+    ones) transports it exactly: cells beyond the stencil's reach of the
+    outflow boundary match rho(x - U dt) to round-off."""
+    n = 16
+    lev = W.single_box_level(n, n, n, 1.0 / n, bc=(1, 1, 1, 1, 1, 1))
+    x = (np.arange(n) + 0.5) / n
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    U = np.array([0.3, 0.2, 0.1])
+    p0 = 1.0
+
+    def rho_of(X, Y, Z):
+        return 1.0 + 0.5 * (X - 0.5) * (Y - 0.5) * (Z - 0.5) + 0.1 * (X - 0.5) - 0.05 * (Y - 0.5)
+
+    rho = rho_of(X, Y, Z)
+    u = np.stack([np.full_like(rho, U[0]), np.full_like(rho, U[1]), np.full_like(rho, U[2])])
+    S = W.empty_box(lev, 0, 6)
+    W.put_valid(S, W.conserved_from_primitive(rho, u, np.full_like(rho, p0 / (G53 - 1))))
+    P = oracle.OracleParams(gamma=G53)
+    dt = 0.5 * (1.0 / n) / (U.max() + np.sqrt(G53 * p0 / rho.min()))
+    out, _, _ = oracle.advance(lev, P, [S], None, dt=dt)
+    got = W.valid(out[0])[0]
+    exact = rho_of(X - U[0] * dt, Y - U[1] * dt, Z - U[2] * dt)
+    inner = (slice(4, n - 4),) * 3
+    assert np.abs(got[inner] - exact[inner]).max() <= 1e-13

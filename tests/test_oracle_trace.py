@@ -115,3 +115,27 @@ def test_acoustic_simple_wave_linear_limit():
         assert qp[0, i] - 1.0 == pytest.approx(foot, abs=1e-11)
         assert qp[1, i] == pytest.approx(foot, abs=1e-11)
         assert qp[4, i] - p0 == pytest.approx(foot, abs=1e-11)
+
+
+def test_acoustic_wave_in_supersonic_flow():
+    """Supersonic flow (u = 3c) carrying a small u-c acoustic wave: both
+    acoustic families move toward the high face, the u+c one is the
+    reference and the u-c one is projected with the eigenvectors, so the
+    high-face state is the wave at the foot of the u-c characteristic."""
+    P = oracle.OracleParams(gamma=G53)
+    n = 16
+    eps = 1e-6
+    x = np.arange(n, dtype=float)
+    p0, c, U = 1.0 / G53, 1.0, 3.0
+    f = eps * (x - 8.0)
+    q = np.zeros((5, n))
+    q[0] = 1.0 - f      # (rho, u, p) = (1, U, p0) - f (1, -c, c^2): the u-c family
+    q[1] = U + f
+    q[4] = p0 - f
+    dtp, dx = 0.1, 1.0
+    qm, qp, _, _ = oracle.trace_line(P, q, dtp=dtp, dx=dx, direction=0)
+    for i in range(3, n - 3):
+        foot = eps * (i + 0.5 - (U - c) * dtp / dx / 2 - 8.0)
+        assert qp[0, i] - 1.0 == pytest.approx(-foot, abs=1e-11)
+        assert qp[1, i] - U == pytest.approx(foot, abs=1e-11)
+        assert qp[4, i] - p0 == pytest.approx(-foot, abs=1e-11)
