@@ -133,7 +133,8 @@ int nyx_hydro_fill(nyx_plan *plan, double *field, int ncomp);
 
 /* CFL time step of Sec. 3.5 for state[cur]:
  *   *dt_dev = cfl * min over valid cells and d of a dx_d / (|U_d| + c)
- * a_dev and dt_dev are device scalars (so the call can be graph captured). */
+ * a_dev and dt_dev are device scalars (so the call can be graph captured).
+ * FP64 plans evaluate it in FP64, mixed plans in FP32. */
 int nyx_hydro_estdt(nyx_plan *plan, const nyx_level *level, const double *a_dev, double *dt_dev);
 
 /* One single-level hydro advance (Sec. 3.6 Steps 2 and 6, hydro part):
@@ -203,8 +204,8 @@ int nyx_hydro_counters_read(nyx_plan *plan, int reset, nyx_hydro_counters *out);
 int nyx_hydro_status(nyx_plan *plan, int *flags);
 
 /* Allocation-free CFL step (no counterpart in the paper: it serves callers,
- * not the method).  Same result as nyx_hydro_estdt for a state laid out as
- * nyx_hydro_layout describes, but without a plan: it calls no cudaMalloc,
+ * not the method).  Same result as nyx_hydro_estdt of an FP64 plan, for a state
+ * laid out as nyx_hydro_layout describes, but without a plan: it calls no cudaMalloc,
  * cudaFree or allocating library routine.  It is for callers that cannot
  * allocate device memory -- code running where a framework or application
  * owns every device allocation, or a latency-critical loop that must not

@@ -374,8 +374,12 @@ int do_fill(nyx_plan *P, double *field, int ncomp) {
 }
 
 int do_estdt(nyx_plan *P, const double *state, const double *a_dev, double *dt_dev) {
-  launch_estdt(P->d_boxes, P->d_cell_pref, P->nbox, P->total_cells, state, P->d_K, a_dev,
-               P->d_dtacc, P->stream);
+  if (P->prm.precision == NYX_MIXED)
+    launch_estdt_mixed(P->d_boxes, P->d_cell_pref, P->nbox, P->total_cells, state, P->d_K, a_dev,
+                       P->d_dtacc, P->stream);
+  else
+    launch_estdt(P->d_boxes, P->d_cell_pref, P->nbox, P->total_cells, state, P->d_K, a_dev,
+                 P->d_dtacc, P->stream);
   launch_dt_finalize(P->d_K, P->d_dtacc, dt_dev, P->stream);
   P->launches += 2;
   return NYX_OK;

@@ -8,30 +8,28 @@
 namespace nyx {
 namespace {
 
-// One thread per (cell of a rectangle); rect_pref[r] = cells before rect r.
-__global__ void k_fill(double *field, int ncomp, const BoxDev *boxes, const FillRect *rects,
-                       const long long *rect_pref, int nrect, long long total) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    int lo = 0, hi = nrect - 1;
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (rect_pref[mid] <= t) lo = mid; else hi = mid - 1;
-    }
-    const FillRect R = rects[lo];
-    long long f = t - rect_pref[lo];
-    int i = (int)(f % R.ext[0]);
-    long long u = f / R.ext[0];
-    int j = (int)(u % R.ext[1]);
-    int k = (int)(u / R.ext[1]);
+// One CTA per rectangle (grid-strided): consecutive threads copy
+// consecutive x cells of a row, so both sides are read and written in
+// coalesced runs, and no thread searches the rectangle list.
+__global__ void k_fill_rects(double *field, int ncomp, const BoxDev *boxes, const FillRect *rects,
+                             int nrect) {
+  for (int r = blockIdx.x; r < nrect; r += gridDim.x) {
+    const FillRect R = rects[r];
     const BoxDev bd = boxes[R.dst_box];
     const BoxDev bs = boxes[R.src_box];
-    long long di = cell_index(bd, R.dlo[0] + i, R.dlo[1] + j, R.dlo[2] + k);
-    long long si = cell_index(bs, R.slo[0] + R.sstep[0] * i, R.slo[1] + R.sstep[1] * j,
-                              R.slo[2] + R.sstep[2] * k);
     double *D = field + (long long)ncomp * bd.pref;
     const double *S = field + (long long)ncomp * bs.pref;
-    for (int c = 0; c < ncomp; ++c) D[c * bd.stride + di] = S[c * bs.stride + si];
+    const int n = R.ext[0] * R.ext[1] * R.ext[2];
+    for (int f = threadIdx.x; f < n; f += blockDim.x) {
+      const int i = f % R.ext[0];
+      const int u = f / R.ext[0];
+      const int j = u % R.ext[1];
+      const int k = u / R.ext[1];
+      const long long di = cell_index(bd, R.dlo[0] + i, R.dlo[1] + j, R.dlo[2] + k);
+      const long long si = cell_index(bs, R.slo[0] + R.sstep[0] * i, R.slo[1] + R.sstep[1] * j,
+                                      R.slo[2] + R.sstep[2] * k);
+      for (int c = 0; c < ncomp; ++c) D[c * bd.stride + di] = S[c * bs.stride + si];
+    }
   }
 }
 
@@ -39,10 +37,10 @@ __global__ void k_fill(double *field, int ncomp, const BoxDev *boxes, const Fill
 
 void launch_fill(double *field, int ncomp, const BoxDev *boxes, const FillRect *rects,
                  const long long *rect_pref, int nrect, long long total, cudaStream_t st) {
+  (void)rect_pref;
   if (nrect <= 0 || total <= 0) return;
-  long long g = (total + 255) / 256;
-  if (g > 152 * 32) g = 152 * 32;
-  k_fill<<<(int)g, 256, 0, st>>>(field, ncomp, boxes, rects, rect_pref, nrect, total);
+  const int grid = nrect < 152 * 16 ? nrect : 152 * 16;
+  k_fill_rects<<<grid, 256, 0, st>>>(field, ncomp, boxes, rects, nrect);
 }
 
 }  // namespace nyx

@@ -34,3 +34,61 @@ int max_grid_mixed(int shape) {
 }
 
 }  // namespace nyx
+
+namespace nyx {
+namespace {
+
+// CFL step of a state in FP32 (mixed plans): the same minimum as the FP64
+// reduction, with the primitives and the ratios formed in FP32.
+__global__ void k_estdt_mixed(const BoxDev *boxes, const long long *cell_pref, int nbox,
+                              long long total, const double *state, const SchemeConsts *K,
+                              const double *a_dev, unsigned long long *dtacc) {
+  const float gm1 = nyx_mixed::d2f_rn(K->gm1), gamma = nyx_mixed::d2f_rn(K->gamma);
+  const float small_pres = nyx_mixed::d2f_rn(K->small_pres);
+  const double a = *a_dev;
+  float local_min = __int_as_float(0x7f800000);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nbox - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (cell_pref[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const BoxDev b = boxes[lo];
+    const long long f = t - cell_pref[lo];
+    const int i = (int)(f % b.n[0]);
+    const long long u = f / b.n[0];
+    const int j = (int)(u % b.n[1]);
+    const int kk = (int)(u / b.n[1]);
+    const double *S = state + NCONS * b.pref;
+    const long long id = cell_index(b, i, j, kk);
+    const float rho = nyx_mixed::d2f_rn(S[id]);
+    const float ir = 1.0f / rho;
+    float p = gm1 * nyx_mixed::d2f_rn(S[5 * b.stride + id]);
+    if (p < small_pres) p = small_pres;
+    const float c2 = gamma * p * ir;
+    const float c = c2 * rsqrtf(c2);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float adx = nyx_mixed::d2f_rn(a * b.dx[d]);
+      const float tt = adx / (fabsf(nyx_mixed::d2f_rn(S[(1 + d) * b.stride + id]) * ir) + c);
+      local_min = fminf(local_min, tt);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) local_min = fminf(local_min, __shfl_xor_sync(0xffffffffu, local_min, o));
+  if ((threadIdx.x & 31) == 0 && local_min < __int_as_float(0x7f800000))
+    atomic_min_pos(dtacc, (double)local_min);
+}
+
+}  // namespace
+
+void launch_estdt_mixed(const BoxDev *boxes, const long long *cell_pref, int nbox, long long total,
+                        const double *state, const SchemeConsts *K, const double *a_dev,
+                        unsigned long long *dtacc, cudaStream_t st) {
+  long long g = (total + 255) / 256;
+  if (g > 152 * 64) g = 152 * 64;
+  if (g < 1) g = 1;
+  k_estdt_mixed<<<(int)g, 256, 0, st>>>(boxes, cell_pref, nbox, total, state, K, a_dev, dtacc);
+}
+
+}  // namespace nyx

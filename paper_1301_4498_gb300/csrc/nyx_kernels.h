@@ -20,6 +20,10 @@ void launch_estdt(const BoxDev *boxes, const long long *cell_pref, int nbox, lon
                   const double *state, const SchemeConsts *K, const double *a_dev,
                   unsigned long long *dtacc, cudaStream_t st);
 
+void launch_estdt_mixed(const BoxDev *boxes, const long long *cell_pref, int nbox, long long total,
+                        const double *state, const SchemeConsts *K, const double *a_dev,
+                        unsigned long long *dtacc, cudaStream_t st);
+
 void launch_dt_finalize(const SchemeConsts *K, unsigned long long *dtacc, double *dt_out,
                         cudaStream_t st);
 
