@@ -133,19 +133,6 @@ __device__ __forceinline__ void to_lab(int dir, const float (&n)[5], float (&q)[
   q[4] = n[4];
 }
 
-// Normal-frame Riemann output of a direction-dir face -> lab-frame flux
-// F = (F_rho, F_mx, F_my, F_mz, F_rhoE, F_rhoe, u_g, p_g).
-__device__ __forceinline__ void from_normal_flux(int dir, const float (&o)[8], float (&F)[8]) {
-  F[0] = o[0];
-  F[1] = (dir == 0) ? o[1] : o[2];
-  F[2] = (dir == 0) ? o[2] : ((dir == 1) ? o[1] : o[3]);
-  F[3] = (dir == 2) ? o[1] : o[3];
-  F[4] = o[4];
-  F[5] = o[5];
-  F[6] = o[6];
-  F[7] = o[7];
-}
-
 // One Riemann problem on a direction-dir face; lab-frame states in and
 // F = (F_rho, F_mx, F_my, F_mz, F_rhoE, F_rhoe, u_g, p_g) out.
 __device__ __forceinline__ void face_flux_dir(const Eos<float> &E, int dir, const float (&ql)[5],
@@ -420,64 +407,46 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
       __syncthreads();
 
       // ------------------------------------------------ S4: intermediate solves
-      // A thread's two problems (kinds kq and kq+3) are solved together.
       if (act) {
-        const float *L[2], *Rr[2];
-        float *O[2];
-        int lc[2], dir[2];
-        bool go[2];
-#pragma unroll
+#pragma unroll 1
         for (int rep = 0; rep < 2; ++rep) {
           const int kind = kq + 3 * rep;
+          const float *L, *Rr;
+          float *O;
+          int lc, dir;
+          bool go;
           switch (kind) {
             case 0:  // F^{x|y} at c
-              go[rep] = mi >= 0 && inY; dir[rep] = 0; L[rep] = sm + G::P2 + 5 * NC; lc[rep] = me - 1;
-              Rr[rep] = sm + G::P2; O[rep] = sm + G::P1;
+              go = mi >= 0 && inY; dir = 0; L = sm + G::P2 + 5 * NC; lc = me - 1; Rr = sm + G::P2;
+              O = sm + G::P1;
               break;
             case 1:  // F^{y|x} at c
-              go[rep] = mj >= 0 && inX; dir[rep] = 1; L[rep] = sm + G::P2 + 15 * NC; lc[rep] = me - W;
-              Rr[rep] = sm + G::P2 + 10 * NC; O[rep] = sm + G::P1 + 7 * NC;
+              go = mj >= 0 && inX; dir = 1; L = sm + G::P2 + 15 * NC; lc = me - W;
+              Rr = sm + G::P2 + 10 * NC; O = sm + G::P1 + 7 * NC;
               break;
             case 2:  // F^{x|z} at c-1
-              go[rep] = zc && mi >= 0; dir[rep] = 0; L[rep] = sm + G::P2 + 25 * NC; lc[rep] = me - 1;
-              Rr[rep] = sm + G::P2 + 20 * NC; O[rep] = sm + G::P1 + 14 * NC;
+              go = zc && mi >= 0; dir = 0; L = sm + G::P2 + 25 * NC; lc = me - 1;
+              Rr = sm + G::P2 + 20 * NC; O = sm + G::P1 + 14 * NC;
               break;
             case 3:  // F^{y|z} at c-1
-              go[rep] = zc && mj >= 0; dir[rep] = 1; L[rep] = sm + G::P2 + 35 * NC; lc[rep] = me - W;
-              Rr[rep] = sm + G::P2 + 30 * NC; O[rep] = sm + G::P1 + 21 * NC;
+              go = zc && mj >= 0; dir = 1; L = sm + G::P2 + 35 * NC; lc = me - W;
+              Rr = sm + G::P2 + 30 * NC; O = sm + G::P1 + 21 * NC;
               break;
             case 4:  // F^{z|x} at face c-1/2
-              go[rep] = c >= 0 && inX; dir[rep] = 2; L[rep] = sm + G::QZXP + pm * 5 * NC; lc[rep] = me;
-              Rr[rep] = sm + G::QZXM; O[rep] = sm + G::FZXY + (pc * 2 + 0) * 7 * NC;
+              go = c >= 0 && inX; dir = 2; L = sm + G::QZXP + pm * 5 * NC; lc = me;
+              Rr = sm + G::QZXM; O = sm + G::FZXY + (pc * 2 + 0) * 7 * NC;
               break;
             default:  // F^{z|y} at face c-1/2
-              go[rep] = c >= 0 && inY; dir[rep] = 2; L[rep] = sm + G::QZYP + pm * 5 * NC; lc[rep] = me;
-              Rr[rep] = sm + G::QZYM; O[rep] = sm + G::FZXY + (pc * 2 + 1) * 7 * NC;
+              go = c >= 0 && inY; dir = 2; L = sm + G::QZYP + pm * 5 * NC; lc = me;
+              Rr = sm + G::QZYM; O = sm + G::FZXY + (pc * 2 + 1) * 7 * NC;
               break;
           }
-        }
-        if (go[0] || go[1]) {
-          // an inactive problem is replaced by the active one's inputs and discarded
-          const int a0 = go[0] ? 0 : 1, a1 = go[1] ? 1 : 0;
-          float l0[5], r0[5], l1[5], r1[5], n_l0[5], n_r0[5], n_l1[5], n_r1[5], o0[8], o1[8];
-          ld5(L[a0], NC, lc[a0], l0);
-          ld5(Rr[a0], NC, me, r0);
-          ld5(L[a1], NC, lc[a1], l1);
-          ld5(Rr[a1], NC, me, r1);
-          to_normal(dir[a0], l0, n_l0);
-          to_normal(dir[a0], r0, n_r0);
-          to_normal(dir[a1], l1, n_l1);
-          to_normal(dir[a1], r1, n_r1);
-          riemann_fast2(E, n_l0, n_r0, o0, n_l1, n_r1, o1);
-          if (go[0]) {
-            float F[8];
-            from_normal_flux(dir[0], o0, F);
-            st7(O[0], NC, me, F);
-          }
-          if (go[1]) {
-            float F[8];
-            from_normal_flux(dir[1], o1, F);
-            st7(O[1], NC, me, F);
+          if (go) {
+            float l[5], r[5], F[8];
+            ld5(L, NC, lc, l);
+            ld5(Rr, NC, me, r);
+            face_flux_dir(E, dir, l, r, F);
+            st7(O, NC, me, F);
           }
         }
       }

@@ -423,104 +423,6 @@ __device__ __forceinline__ void riemann_fast(const Eos<float> &E, const float (&
   out[7] = pg;
 }
 
-// Two independent FP32 two-shock solves in one Newton loop: the same
-// arithmetic as riemann_fast for each problem, interleaved so that the two
-// serial iteration chains hide each other's latency.  Each problem keeps
-// its own convergence test; a converged one is frozen.
-__device__ __forceinline__ void riemann_fast2(const Eos<float> &E, const float (&qL)[5],
-                                              const float (&qR)[5], float (&out)[8],
-                                              const float (&qL2)[5], const float (&qR2)[5],
-                                              float (&out2)[8]) {
-  struct Side {
-    float iR, c, C, iC, k;
-  };
-  auto side = [&](const float (&q)[5]) {
-    Side s;
-    s.iR = 1.0f / q[0];
-    const float c2 = E.gamma * q[4] * s.iR;
-    s.c = c2 * rsqrtf(c2);
-    s.C = q[0] * s.c;
-    s.iC = 1.0f / s.C;
-    s.k = E.kshock / q[4];
-    return s;
-  };
-  const Side a = side(qL), b = side(qR), a2 = side(qL2), b2 = side(qR2);
-  float p = (b.C * qL[4] + a.C * qR[4] + a.C * b.C * (qL[1] - qR[1])) / (a.C + b.C);
-  float p2 = (b2.C * qL2[4] + a2.C * qR2[4] + a2.C * b2.C * (qL2[1] - qR2[1])) / (a2.C + b2.C);
-  if (p < E.small_pres) p = E.small_pres;
-  if (p2 < E.small_pres) p2 = E.small_pres;
-  bool done = false, done2 = false;
-  for (int it = 0; it < E.max_iter && !(done && done2); ++it) {
-    const float xL = fmaxf(1.0f + (p - qL[4]) * a.k, 1e-10f);
-    const float xR = fmaxf(1.0f + (p - qR[4]) * b.k, 1e-10f);
-    const float xL2 = fmaxf(1.0f + (p2 - qL2[4]) * a2.k, 1e-10f);
-    const float xR2 = fmaxf(1.0f + (p2 - qR2[4]) * b2.k, 1e-10f);
-    const float rL = rsqrtf(xL), rR = rsqrtf(xR), rL2 = rsqrtf(xL2), rR2 = rsqrtf(xR2);
-    const float usL = qL[1] - (p - qL[4]) * (rL * a.iC);
-    const float usR = qR[1] + (p - qR[4]) * (rR * b.iC);
-    const float usL2 = qL2[1] - (p2 - qL2[4]) * (rL2 * a2.iC);
-    const float usR2 = qR2[1] + (p2 - qR2[4]) * (rR2 * b2.iC);
-    const float izL = (xL + 1.0f) * (rL * rL * rL) * (0.5f * a.iC);
-    const float izR = (xR + 1.0f) * (rR * rR * rR) * (0.5f * b.iC);
-    const float izL2 = (xL2 + 1.0f) * (rL2 * rL2 * rL2) * (0.5f * a2.iC);
-    const float izR2 = (xR2 + 1.0f) * (rR2 * rR2 * rR2) * (0.5f * b2.iC);
-    float pn = p - (usR - usL) / (izL + izR);
-    float pn2 = p2 - (usR2 - usL2) / (izL2 + izR2);
-    if (pn < E.small_pres) pn = E.small_pres;
-    if (pn2 < E.small_pres) pn2 = E.small_pres;
-    if (!done) {
-      const bool conv = fabsf(pn - p) <= E.tol * pn;
-      p = pn;
-      done = conv;
-    }
-    if (!done2) {
-      const bool conv2 = fabsf(pn2 - p2) <= E.tol * pn2;
-      p2 = pn2;
-      done2 = conv2;
-    }
-  }
-  auto finish = [&](const float (&ql)[5], const float (&qr)[5], const Side &l, const Side &r,
-                    float pstar, float (&o)[8]) {
-    const float xL = fmaxf(1.0f + (pstar - ql[4]) * l.k, 1e-10f);
-    const float xR = fmaxf(1.0f + (pstar - qr[4]) * r.k, 1e-10f);
-    const float rL = rsqrtf(xL), rR = rsqrtf(xR);
-    const float WL = l.C * xL * rL, WR = r.C * xR * rR;
-    const float ustar = (ql[4] - qr[4] + WL * ql[1] + WR * qr[1]) / (WL + WR);
-    float g[5];
-    if (ustar > 0.0f) {
-      sample_side_fast(E, ql[0], l.iR, ql[1], ql[2], ql[3], ql[4], WL, rL * l.iC, l.c, 1.0f,
-                       pstar, ustar, g);
-    } else if (ustar < 0.0f) {
-      sample_side_fast(E, qr[0], r.iR, qr[1], qr[2], qr[3], qr[4], WR, rR * r.iC, r.c, -1.0f,
-                       pstar, ustar, g);
-    } else {
-      float gl[5], gr[5];
-      sample_side_fast(E, ql[0], l.iR, ql[1], ql[2], ql[3], ql[4], WL, rL * l.iC, l.c, 1.0f,
-                       pstar, ustar, gl);
-      sample_side_fast(E, qr[0], r.iR, qr[1], qr[2], qr[3], qr[4], WR, rR * r.iC, r.c, -1.0f,
-                       pstar, ustar, gr);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) g[v] = 0.5f * (gl[v] + gr[v]);
-    }
-    if (g[0] < E.small_dens) g[0] = E.small_dens;
-    if (g[4] < E.small_pres) g[4] = E.small_pres;
-    const float rg = g[0], ug = g[1], t1 = g[2], t2 = g[3], pg = g[4];
-    const float frho = rg * ug;
-    const float rhoeg = pg * E.igm1;
-    const float ke = 0.5f * rg * (ug * ug + t1 * t1 + t2 * t2);
-    o[0] = frho;
-    o[1] = frho * ug + pg;
-    o[2] = frho * t1;
-    o[3] = frho * t2;
-    o[4] = ug * (rhoeg + ke + pg);
-    o[5] = ug * rhoeg;
-    o[6] = ug;
-    o[7] = pg;
-  };
-  finish(qL, qR, a, b, p, out);
-  finish(qL2, qR2, a2, b2, p2, out2);
-}
-
 // Tangential axes of face direction DIR, increasing order.
 template <int DIR>
 struct Tan {
