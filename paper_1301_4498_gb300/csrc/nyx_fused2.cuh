@@ -28,8 +28,6 @@ struct G2 {
   static constexpr int NTC = 3 * NCP;                     // column-task threads
   static constexpr int NU = (TX * TY + 31) / 32 * 32;     // update threads
   static constexpr int NT = NTC + NU;
-  // registers per thread that still fit the CTAs wanted per SM (granule 8)
-  static constexpr int regs_for(int mb) { return (65536 / (NT * mb)) / 8 * 8; }
   // shared layout, in floats
   static constexpr int PR = 0;                       // [5 planes][5 vars][NE] primitives
   static constexpr int QXY = PR + 25 * NE;           // [2 planes][2 dirs x,y][10][NC] traced x, y
@@ -154,12 +152,7 @@ __device__ __forceinline__ void face_flux_dir(const Eos<float> &E, int dir, cons
 }
 
 template <int TX, int TY, int MB>
-struct RegBudget {
-  static constexpr int value = G2<TX, TY>::regs_for(MB);
-};
-
-template <int TX, int TY, int MB>
-__global__ void __maxnreg__((RegBudget<TX, TY, MB>::value)) k_fused2(nyx::FusedArgs a) {
+__global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a) {
   using G = G2<TX, TY>;
   constexpr int NC = G::NC, NCP = G::NCP, NE = G::NE, W = G::W, WE = G::WE, NT = G::NT;
   constexpr int NTC = G::NTC;
