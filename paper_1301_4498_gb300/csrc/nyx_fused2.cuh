@@ -4,14 +4,19 @@
 // different mapping onto the SM: every per-column value lives in shared
 // memory (structure-of-arrays, [field][column]) and each stage is a list of
 // independent tasks -- one trace direction of one column, one Riemann
-// problem on one face, one corner-coupling correction, one update -- that
-// the CTA's threads take in order.  Tasks of one kind are padded to a whole
-// number of warps, so a warp runs one kind at a time.  With three threads per
-// column a 16 x 8 tile runs 18 warps per SM at <= 113 registers per thread
-// (the column-owning form runs 11 warps at 168 with spills), which is what
-// the latency-bound Riemann and tracing arithmetic needs.  The FP64 update of
-// plane c-1 (stage 7) has no barrier behind it, so it overlaps the loads of
-// the next plane.
+// problem on one face, one corner-coupling correction -- that the column
+// threads take in order (three threads per column).  Tasks of one kind are
+// padded to a whole number of warps, so a warp runs one kind at a time.
+//
+// The FP64 update (stage 7) runs on its own warps, one output cell per
+// thread, decoupled from the column threads' stage barriers: the column
+// threads hand over the final fluxes of plane c-1 through named barriers
+// (READY after they are stored, FREE before the buffer is overwritten), so
+// the update of one plane, bound by the FP64 pipe and the state loads,
+// overlaps all stages of the next plane instead of lengthening one of them.
+// The update of plane p may run until the final fluxes of plane p+1 are
+// stored, so the x/y flux buffer is single and the z-face buffer holds two
+// faces.
 //
 // Rings over planes: slot = (plane + 2) & 1 for the two-plane rings, and
 // (plane + 8) % 5 for the five-plane primitive ring.
@@ -28,9 +33,13 @@ struct G2 {
   static constexpr int NTC = 3 * NCP;                     // column-task threads
   static constexpr int NU = (TX * TY + 31) / 32 * 32;     // update threads
   static constexpr int NT = NTC + NU;
+  // final fluxes of one plane, compact over the output cells: x faces
+  // [(TX+1) x TY], then y faces [TX x (TY+1)]; z faces [TX x TY]
+  static constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1), NUF = NXF + NYF, NZF = TX * TY;
   // shared layout, in floats
-  static constexpr int PR = 0;                       // [5 planes][5 vars][NE] primitives
-  static constexpr int QXY = PR + 25 * NE;           // [2 planes][2 dirs x,y][10][NC] traced x, y
+  static constexpr int PR = 0;                       // [5 planes][5 vars][NC] primitives ring
+  static constexpr int PE = PR + 25 * NC;            // [5 vars][NE] plane c with its 3-cell frame
+  static constexpr int QXY = PE + 5 * NE;            // [2 planes][2 dirs x,y][10][NC] traced x, y
   static constexpr int QZ = QXY + 40 * NC;           // [2 planes][10][NC] traced z
   static constexpr int FZ = QZ + 20 * NC;            // [2 faces][7][NC] normal z fluxes
   static constexpr int QZXM = FZ + 14 * NC;          // [5][NC] q_{z|x} low side, plane c
@@ -40,13 +49,25 @@ struct G2 {
   static constexpr int FZXY = QZYP + 10 * NC;        // [2 faces][2 kinds z|x, z|y][7][NC]
   static constexpr int QZFM = FZXY + 28 * NC;        // [5][NC] final z state, low side
   static constexpr int QZFP = QZFM + 5 * NC;         // [2 planes][5][NC] final z, high side
-  static constexpr int FFZ = QZFP + 10 * NC;         // [2 faces][8][NC] final z fluxes
-  static constexpr int P1 = FFZ + 16 * NC;           // [28][NC] pool: FX,FY | Fxy,Fyx,Fxz,Fyz | Ffx,Ffy
+  static constexpr int P1 = QZFP + 10 * NC;          // [28][NC] pool: FX,FY | Fxy,Fyx,Fxz,Fyz
   static constexpr int P2 = P1 + 28 * NC;            // [40][NC] pool: qxy,qyx,qxz,qyz | qxf,qyf
   static constexpr int GR = P2 + 40 * NC;            // [3][NC] gravity of plane c
-  static constexpr int TOTAL = GR + 3 * NC;
+  static constexpr int UF = GR + 3 * NC;             // [8][NUF] final x, y fluxes of plane c-1
+  static constexpr int FFZ = UF + 8 * NUF;           // [2 faces][8][NZF] final z fluxes
+  static constexpr int TOTAL = FFZ + 16 * NZF;
   static constexpr size_t SMEM = sizeof(float) * (size_t)TOTAL;
+  static_assert(SMEM <= 227 * 1024, "task-form tile does not fit in shared memory");
 };
+
+// Named barriers: 0 is __syncthreads (all threads, item fetch and tile end);
+// the column threads' stage barrier; the update hand-over pair.
+constexpr int BAR_COL = 1, BAR_READY = 2, BAR_FREE = 3;
+__device__ __forceinline__ void bar_sync_n(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_arrive_n(int id, int n) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
 
 __device__ __forceinline__ int par2(int plane) { return (plane + 2) & 1; }
 __device__ __forceinline__ int ring5(int plane) { return (plane + 8) % 5; }
@@ -155,7 +176,7 @@ template <int TX, int TY, int MB>
 __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a) {
   using G = G2<TX, TY>;
   constexpr int NC = G::NC, NCP = G::NCP, NE = G::NE, W = G::W, WE = G::WE, NT = G::NT;
-  constexpr int NTC = G::NTC;
+  constexpr int NTC = G::NTC, NUF = G::NUF, NXF = G::NXF, NZF = G::NZF;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float *sm = reinterpret_cast<float *>(smem_raw);
   __shared__ int s_item;
@@ -171,7 +192,7 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
   // Threads [0, NTC) take column tasks: every task of such a thread is on one
   // owned column, kind kq (and kq+3 in the six-kind stages) of column me.
   // Threads [NTC, NT) are the update warps: the FP64 update of one output
-  // cell each, overlapped with the tracing of the column threads.
+  // cell each, one plane behind the column threads.
   const bool colthr = tid < NTC;
   const int kq = colthr ? tid / NCP : 3;
   const int me = colthr ? tid - kq * NCP : NCP;
@@ -187,339 +208,368 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
     if (item >= a.nitems) break;
     const nyx::WorkItem w = a.items[item];
     const nyx::BoxDev b = a.boxes[w.box];
-    const nyx::BoxStep bst = a.BS[w.box];
     const int nxt = w.nx, nyt = w.ny, nz = b.n[2];
     const long long bs = b.stride;
     const long long ps = (long long)b.N[0] * b.N[1];
     const double *S = a.S + nyx::NCONS * b.pref;
-    const double *Gv = a.G ? a.G + nyx::NGRAV * b.pref : nullptr;
-    double *Sn = a.Sn + nyx::NCONS * b.pref;
-    const MixK mk = make_mixk(KK, sc, b);
-    const float dtdx0 = d2f_rn(bst.dtdx[0]), dtdx1 = d2f_rn(bst.dtdx[1]), dtdx2 = d2f_rn(bst.dtdx[2]);
-    const float c30 = d2f_rn(bst.cdt3[0]), c31 = d2f_rn(bst.cdt3[1]), c32 = d2f_rn(bst.cdt3[2]);
-    const float ch0 = d2f_rn(bst.chalf[0]), ch1 = d2f_rn(bst.chalf[1]), ch2 = d2f_rn(bst.chalf[2]);
-    const int nstrip = 4 * (nxt + 2) + 4 * (nyt + 2);
-    // geometry of this thread's column for this tile
-    const bool act = colthr && me < NC && mi <= nxt && mj <= nyt;
-    const bool inX = mi >= 0 && mi < nxt, inY = mj >= 0 && mj < nyt;
-    const long long mycol = (long long)(w.y0 + mj + 4) * b.N[0] + (w.x0 + mi + 4);
-    // this thread's update cell (update threads only, packed on whole warps)
-    const int nout = nxt * nyt;
-    const int uthr = tid - NTC;
-    const bool upd = !colthr && uthr < nout;
-    const int ui = upd ? uthr % nxt : 0, uj = upd ? uthr / nxt : 0;
-    const int ue = (uj + 1) * W + (ui + 1);
-    const long long ucol = (long long)(w.y0 + uj + 4) * b.N[0] + (w.x0 + ui + 4);
 
-    auto load_prims = [&](long long id, int slot, int ecell) {
-      float q[5];
-      prims_of<float>(S, bs, id, E, q);
+    if (colthr) {
+      const nyx::BoxStep bst = a.BS[w.box];
+      const double *Gv = a.G ? a.G + nyx::NGRAV * b.pref : nullptr;
+      const float dtdx0 = d2f_rn(bst.dtdx[0]), dtdx1 = d2f_rn(bst.dtdx[1]), dtdx2 = d2f_rn(bst.dtdx[2]);
+      const float c30 = d2f_rn(bst.cdt3[0]), c31 = d2f_rn(bst.cdt3[1]), c32 = d2f_rn(bst.cdt3[2]);
+      const float ch0 = d2f_rn(bst.chalf[0]), ch1 = d2f_rn(bst.chalf[1]), ch2 = d2f_rn(bst.chalf[2]);
+      const int nstrip = 4 * (nxt + 2) + 4 * (nyt + 2);
+      // geometry of this thread's column for this tile
+      const bool act = me < NC && mi <= nxt && mj <= nyt;
+      const bool inX = mi >= 0 && mi < nxt, inY = mj >= 0 && mj < nyt;
+      const long long mycol = (long long)(w.y0 + mj + 4) * b.N[0] + (w.x0 + mi + 4);
+
+      auto load_prims = [&](long long id, float *dst, int stride) {
+        float q[5];
+        prims_of<float>(S, bs, id, E, q);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) sm[G::PR + (slot * 5 + v) * NE + ecell] = q[v];
-    };
-    // FP64 update of plane p: x, y faces from P1 (the last final-solve
-    // stage), z faces from FFZ ring slots slot_lo (face p-1/2) and slot_hi.
-    auto update = [&](int p, int slot_lo, int slot_hi) {
-      float Fxm[8], Fxp[8], Fym[8], Fyp[8], Fzm[8], Fzp[8];
-      ld8(sm + G::P1, NC, ue, Fxm);
-      ld8(sm + G::P1, NC, ue + 1, Fxp);
-      ld8(sm + G::P1 + 8 * NC, NC, ue, Fym);
-      ld8(sm + G::P1 + 8 * NC, NC, ue + W, Fyp);
-      ld8(sm + G::FFZ + slot_lo * 8 * NC, NC, ue, Fzm);
-      ld8(sm + G::FFZ + slot_hi * 8 * NC, NC, ue, Fzp);
-      const long long id = ucol + (long long)(p + 4) * ps;
-      update_cell_mixed(KK, sc, b, mk, S, Gv, Sn, id, Fxm, Fxp, Fym, Fyp, Fzm, Fzp, dtmin, flags,
-                        a.dtacc != nullptr);
-      if (a.flux_keep)
-        keep_fluxes(a.flux_keep + a.flux_off[w.box], b.n[0], b.n[1], nz, w.x0 + ui, w.y0 + uj, p,
-                    Fxm, Fxp, Fym, Fyp, Fzm, Fzp);
-    };
+        for (int v = 0; v < 5; ++v) dst[v * stride] = q[v];
+      };
+      auto ring = [&](int plane) { return sm + G::PR + ring5(plane) * 5 * NC + me; };
 
-    // prologue: planes -3 .. -1 of every owned column (column threads of
-    // kinds 0, 1, 2) and plane 0 (kind 0 again)
-    if (act) {
-      load_prims(mycol + (long long)(kq - 3 + 4) * ps, ring5(kq - 3), mee);
-      if (kq == 0) load_prims(mycol + (long long)(0 + 4) * ps, ring5(0), mee);
-    }
-
-    for (int c = -1; c <= nz; ++c) {
-      const int pc = par2(c), pm = par2(c - 1);
-      const bool zc = c >= 1;
-      // ------------------------------------------------ S0: primitives (+ gravity of plane c)
-      if (tid < NCP) {
-        if (act) {
-          load_prims(mycol + (long long)(c + 2 + 4) * ps, ring5(c + 2), mee);
-          float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-          if (Gv) {
-            const long long id = mycol + (long long)(c + 4) * ps;
-            g0 = d2f_rn(Gv[id]);
-            g1 = d2f_rn(Gv[bs + id]);
-            g2 = d2f_rn(Gv[2 * bs + id]);
-          }
-          sm[G::GR + me] = g0;
-          sm[G::GR + NC + me] = g1;
-          sm[G::GR + 2 * NC + me] = g2;
-        }
-      } else {
-        // the halo strips: every thread that is not a kind-0 column thread
-        for (int u = tid - NCP; u < nstrip; u += NT - NCP) {
-          int x, y;
-          if (u < 4 * (nyt + 2)) {
-            const int r = u % (nyt + 2), s2 = u / (nyt + 2);
-            y = r - 1;
-            x = (s2 < 2) ? (-3 + s2) : (nxt + 1 + (s2 - 2));
-          } else {
-            const int v = u - 4 * (nyt + 2);
-            const int r = v % (nxt + 2), s2 = v / (nxt + 2);
-            x = r - 1;
-            y = (s2 < 2) ? (-3 + s2) : (nyt + 1 + (s2 - 2));
-          }
-          const long long id =
-              ((long long)(c + 4) * b.N[1] + (w.y0 + y + 4)) * b.N[0] + (w.x0 + x + 4);
-          load_prims(id, ring5(c), (y + 3) * WE + (x + 3));
-        }
-      }
-      __syncthreads();
-
-      // ------------------------------------------------ S1: update of plane c-2, tracing at plane c
-      // The update (FP64 pipe) goes first so that it overlaps the FP32 tracing
-      // of the other warps.  Its fluxes stay untouched until the S2 barrier.
-      if (c >= 2 && upd) update(c - 2, pc, pm);
+      // prologue: planes -1 and 0 by kind 0 (which copies plane c into the
+      // framed buffer), planes -3 and -2 by kinds 1 and 2
       if (act) {
-        const int dir = kq;
-        const float *P0 = sm + G::PR + ring5(c) * 5 * NE;
-        const float rho = P0[mee], p = P0[4 * NE + mee];
-        const float cs2 = E.gamma * p / rho;
-        const float cs = cs2 * rsqrtf(cs2);
-        const float gl0 = sm[G::GR + me], gl1 = sm[G::GR + NC + me], gl2 = sm[G::GR + 2 * NC + me];
-        float gn[3];
-        gn[0] = (dir == 0) ? gl0 : ((dir == 1) ? gl1 : gl2);
-        gn[1] = (dir == 0) ? gl1 : gl0;
-        gn[2] = (dir == 2) ? gl1 : gl2;
-        float s5[5][5];
-#pragma unroll
-        for (int o = 0; o < 5; ++o) {
-          const float *Po = (dir == 2) ? sm + G::PR + ring5(c - 2 + o) * 5 * NE : P0;
-          const int cell = (dir == 0) ? mee + (o - 2) : ((dir == 1) ? mee + (o - 2) * WE : mee);
-          float ql[5], qn[5];
-#pragma unroll
-          for (int v = 0; v < 5; ++v) ql[v] = Po[v * NE + cell];
-          to_normal(dir, ql, qn);
-#pragma unroll
-          for (int v = 0; v < 5; ++v) s5[v][o] = qn[v];
-        }
-        const float dtdx = (dir == 0) ? dtdx0 : ((dir == 1) ? dtdx1 : dtdx2);
-        float qmn[5], qpn[5], qm[5], qp[5];
-        trace_cell<float, 0>(E, s5, cs, gn, dtdx, src, qmn, qpn);
-        to_lab(dir, qmn, qm);
-        to_lab(dir, qpn, qp);
-        float *dst = (dir == 2) ? sm + G::QZ + pc * 10 * NC : sm + G::QXY + (pc * 2 + dir) * 10 * NC;
-        st5(dst, NC, me, qm);
-        st5(dst + 5 * NC, NC, me, qp);
-      }
-      __syncthreads();
-
-      // ------------------------------------------------ S2: normal solves
-      if (act) {
-        const float *L, *Rr;
-        float *O;
-        int lc;
-        bool go;
         if (kq == 0) {
-          go = mi >= 0;
-          L = sm + G::QXY + (pc * 2 + 0) * 10 * NC + 5 * NC;
-          lc = me - 1;
-          Rr = sm + G::QXY + (pc * 2 + 0) * 10 * NC;
-          O = sm + G::P1;
-        } else if (kq == 1) {
-          go = mj >= 0;
-          L = sm + G::QXY + (pc * 2 + 1) * 10 * NC + 5 * NC;
-          lc = me - W;
-          Rr = sm + G::QXY + (pc * 2 + 1) * 10 * NC;
-          O = sm + G::P1 + 7 * NC;
+          load_prims(mycol + (long long)(-1 + 4) * ps, ring(-1), NC);
+          load_prims(mycol + (long long)(0 + 4) * ps, ring(0), NC);
         } else {
-          go = c >= 0;
-          L = sm + G::QZ + pm * 10 * NC + 5 * NC;
-          lc = me;
-          Rr = sm + G::QZ + pc * 10 * NC;
-          O = sm + G::FZ + pc * 7 * NC;
-        }
-        if (go) {
-          float l[5], r[5], F[8];
-          ld5(L, NC, lc, l);
-          ld5(Rr, NC, me, r);
-          face_flux_dir(E, kq, l, r, F);
-          st7(O, NC, me, F);
+          load_prims(mycol + (long long)(kq - 4 + 4) * ps, ring(kq - 4), NC);
         }
       }
-      __syncthreads();
 
-      // ------------------------------------------------ S3: corner coupling, theta = 1/3
-      if (act) {
-#pragma unroll 1
-        for (int rep = 0; rep < 2; ++rep) {
-          const int kind = kq + 3 * rep;
-          const float *Q, *Fmb, *Fpb;
-          float *Om, *Op;
-          int fpc;
-          float coef;
-          bool go;
-          switch (kind) {
-            case 0:  // q_{x|y} at c
-              go = inY; Q = sm + G::QXY + (pc * 2 + 0) * 10 * NC; Fmb = Fpb = sm + G::P1 + 7 * NC;
-              fpc = me + W; coef = c31; Om = sm + G::P2; Op = sm + G::P2 + 5 * NC;
-              break;
-            case 1:  // q_{y|x} at c
-              go = inX; Q = sm + G::QXY + (pc * 2 + 1) * 10 * NC; Fmb = Fpb = sm + G::P1;
-              fpc = me + 1; coef = c30; Om = sm + G::P2 + 10 * NC; Op = sm + G::P2 + 15 * NC;
-              break;
-            case 2:  // q_{z|x} at c
-              go = inX; Q = sm + G::QZ + pc * 10 * NC; Fmb = Fpb = sm + G::P1;
-              fpc = me + 1; coef = c30; Om = sm + G::QZXM; Op = sm + G::QZXP + pc * 5 * NC;
-              break;
-            case 3:  // q_{z|y} at c
-              go = inY; Q = sm + G::QZ + pc * 10 * NC; Fmb = Fpb = sm + G::P1 + 7 * NC;
-              fpc = me + W; coef = c31; Om = sm + G::QZYM; Op = sm + G::QZYP + pc * 5 * NC;
-              break;
-            case 4:  // q_{x|z} at c-1
-              go = zc; Q = sm + G::QXY + (pm * 2 + 0) * 10 * NC; Fmb = sm + G::FZ + pm * 7 * NC;
-              Fpb = sm + G::FZ + pc * 7 * NC; fpc = me; coef = c32;
-              Om = sm + G::P2 + 20 * NC; Op = sm + G::P2 + 25 * NC;
-              break;
-            default:  // q_{y|z} at c-1
-              go = zc; Q = sm + G::QXY + (pm * 2 + 1) * 10 * NC; Fmb = sm + G::FZ + pm * 7 * NC;
-              Fpb = sm + G::FZ + pc * 7 * NC; fpc = me; coef = c32;
-              Om = sm + G::P2 + 30 * NC; Op = sm + G::P2 + 35 * NC;
-              break;
+      for (int c = -1; c <= nz; ++c) {
+        const int pc = par2(c), pm = par2(c - 1);
+        const bool zc = c >= 1;
+        // ---------------------------------------------- S0: primitives (+ gravity of plane c)
+        if (tid < NCP) {
+          if (act) {
+            load_prims(mycol + (long long)(c + 2 + 4) * ps, ring(c + 2), NC);
+            float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+            if (Gv) {
+              const long long id = mycol + (long long)(c + 4) * ps;
+              g0 = d2f_rn(Gv[id]);
+              g1 = d2f_rn(Gv[bs + id]);
+              g2 = d2f_rn(Gv[2 * bs + id]);
+            }
+            sm[G::GR + me] = g0;
+            sm[G::GR + NC + me] = g1;
+            sm[G::GR + 2 * NC + me] = g2;
+            // plane c of the own column into the framed buffer
+            const float *rc = ring(c);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) sm[G::PE + v * NE + mee] = rc[v * NC];
           }
-          if (go) {
-            const TFlux<float> Fm = ld7(Fmb, NC, me), Fp = ld7(Fpb, NC, fpc);
-            float qa[5], qb[5], oa[5], ob[5];
-            ld5(Q, NC, me, qa);
-            ld5(Q + 5 * NC, NC, me, qb);
-            transverse1(E, qa, coef, Fp, Fm, oa);
-            transverse1(E, qb, coef, Fp, Fm, ob);
-            st5(Om, NC, me, oa);
-            st5(Op, NC, me, ob);
+        } else {
+          // the frame strips of plane c: column threads of kinds 1 and 2
+          for (int u = tid - NCP; u < nstrip; u += NTC - NCP) {
+            int x, y;
+            if (u < 4 * (nyt + 2)) {
+              const int r = u % (nyt + 2), s2 = u / (nyt + 2);
+              y = r - 1;
+              x = (s2 < 2) ? (-3 + s2) : (nxt + 1 + (s2 - 2));
+            } else {
+              const int v = u - 4 * (nyt + 2);
+              const int r = v % (nxt + 2), s2 = v / (nxt + 2);
+              x = r - 1;
+              y = (s2 < 2) ? (-3 + s2) : (nyt + 1 + (s2 - 2));
+            }
+            const long long id =
+                ((long long)(c + 4) * b.N[1] + (w.y0 + y + 4)) * b.N[0] + (w.x0 + x + 4);
+            load_prims(id, sm + G::PE + (y + 3) * WE + (x + 3), NE);
           }
         }
-      }
-      __syncthreads();
+        bar_sync_n(BAR_COL, NTC);
 
-      // ------------------------------------------------ S4: intermediate solves
-      if (act) {
-#pragma unroll 1
-        for (int rep = 0; rep < 2; ++rep) {
-          const int kind = kq + 3 * rep;
+        // ---------------------------------------------- S1: tracing at plane c
+        if (act) {
+          const int dir = kq;
+          const float *P0 = sm + G::PE;
+          const float rho = P0[mee], p = P0[4 * NE + mee];
+          const float cs2 = E.gamma * p / rho;
+          const float cs = cs2 * rsqrtf(cs2);
+          const float gl0 = sm[G::GR + me], gl1 = sm[G::GR + NC + me], gl2 = sm[G::GR + 2 * NC + me];
+          float gn[3];
+          gn[0] = (dir == 0) ? gl0 : ((dir == 1) ? gl1 : gl2);
+          gn[1] = (dir == 0) ? gl1 : gl0;
+          gn[2] = (dir == 2) ? gl1 : gl2;
+          float s5[5][5];
+#pragma unroll
+          for (int o = 0; o < 5; ++o) {
+            const float *Po = (dir == 2) ? ring(c - 2 + o) : P0 + ((dir == 0) ? mee + (o - 2) : mee + (o - 2) * WE);
+            const int st = (dir == 2) ? NC : NE;
+            float ql[5], qn[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) ql[v] = Po[v * st];
+            to_normal(dir, ql, qn);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) s5[v][o] = qn[v];
+          }
+          const float dtdx = (dir == 0) ? dtdx0 : ((dir == 1) ? dtdx1 : dtdx2);
+          float qmn[5], qpn[5], qm[5], qp[5];
+          trace_cell<float, 0>(E, s5, cs, gn, dtdx, src, qmn, qpn);
+          to_lab(dir, qmn, qm);
+          to_lab(dir, qpn, qp);
+          float *dst = (dir == 2) ? sm + G::QZ + pc * 10 * NC : sm + G::QXY + (pc * 2 + dir) * 10 * NC;
+          st5(dst, NC, me, qm);
+          st5(dst + 5 * NC, NC, me, qp);
+        }
+        bar_sync_n(BAR_COL, NTC);
+
+        // ---------------------------------------------- S2: normal solves
+        if (act) {
           const float *L, *Rr;
           float *O;
-          int lc, dir;
+          int lc;
           bool go;
-          switch (kind) {
-            case 0:  // F^{x|y} at c
-              go = mi >= 0 && inY; dir = 0; L = sm + G::P2 + 5 * NC; lc = me - 1; Rr = sm + G::P2;
-              O = sm + G::P1;
-              break;
-            case 1:  // F^{y|x} at c
-              go = mj >= 0 && inX; dir = 1; L = sm + G::P2 + 15 * NC; lc = me - W;
-              Rr = sm + G::P2 + 10 * NC; O = sm + G::P1 + 7 * NC;
-              break;
-            case 2:  // F^{x|z} at c-1
-              go = zc && mi >= 0; dir = 0; L = sm + G::P2 + 25 * NC; lc = me - 1;
-              Rr = sm + G::P2 + 20 * NC; O = sm + G::P1 + 14 * NC;
-              break;
-            case 3:  // F^{y|z} at c-1
-              go = zc && mj >= 0; dir = 1; L = sm + G::P2 + 35 * NC; lc = me - W;
-              Rr = sm + G::P2 + 30 * NC; O = sm + G::P1 + 21 * NC;
-              break;
-            case 4:  // F^{z|x} at face c-1/2
-              go = c >= 0 && inX; dir = 2; L = sm + G::QZXP + pm * 5 * NC; lc = me;
-              Rr = sm + G::QZXM; O = sm + G::FZXY + (pc * 2 + 0) * 7 * NC;
-              break;
-            default:  // F^{z|y} at face c-1/2
-              go = c >= 0 && inY; dir = 2; L = sm + G::QZYP + pm * 5 * NC; lc = me;
-              Rr = sm + G::QZYM; O = sm + G::FZXY + (pc * 2 + 1) * 7 * NC;
-              break;
+          if (kq == 0) {
+            go = mi >= 0;
+            L = sm + G::QXY + (pc * 2 + 0) * 10 * NC + 5 * NC;
+            lc = me - 1;
+            Rr = sm + G::QXY + (pc * 2 + 0) * 10 * NC;
+            O = sm + G::P1;
+          } else if (kq == 1) {
+            go = mj >= 0;
+            L = sm + G::QXY + (pc * 2 + 1) * 10 * NC + 5 * NC;
+            lc = me - W;
+            Rr = sm + G::QXY + (pc * 2 + 1) * 10 * NC;
+            O = sm + G::P1 + 7 * NC;
+          } else {
+            go = c >= 0;
+            L = sm + G::QZ + pm * 10 * NC + 5 * NC;
+            lc = me;
+            Rr = sm + G::QZ + pc * 10 * NC;
+            O = sm + G::FZ + pc * 7 * NC;
           }
           if (go) {
             float l[5], r[5], F[8];
             ld5(L, NC, lc, l);
             ld5(Rr, NC, me, r);
-            face_flux_dir(E, dir, l, r, F);
+            face_flux_dir(E, kq, l, r, F);
             st7(O, NC, me, F);
           }
         }
-      }
-      __syncthreads();
+        bar_sync_n(BAR_COL, NTC);
 
-      // ------------------------------------------------ S5: final states, theta = 1/2
-      if (act) {
-        const float *Q, *Ab, *Bmb, *Bpb;
-        float *Om, *Op;
-        int apc, bpc;
-        float k1c, k2c;
-        bool go;
-        if (kq == 0) {  // z at plane c: F^{x|y} in x, F^{y|x} in y
-          go = inX && inY; Q = sm + G::QZ + pc * 10 * NC;
-          Ab = sm + G::P1; apc = me + 1; k1c = ch0;
-          Bmb = Bpb = sm + G::P1 + 7 * NC; bpc = me + W; k2c = ch1;
-          Om = sm + G::QZFM; Op = sm + G::QZFP + pc * 5 * NC;
-        } else if (kq == 1) {  // x at plane c-1: F^{y|z} in y, F^{z|y} in z
-          go = zc && inY; Q = sm + G::QXY + (pm * 2 + 0) * 10 * NC;
-          Ab = sm + G::P1 + 21 * NC; apc = me + W; k1c = ch1;
-          Bmb = sm + G::FZXY + (pm * 2 + 1) * 7 * NC; Bpb = sm + G::FZXY + (pc * 2 + 1) * 7 * NC;
-          bpc = me; k2c = ch2;
-          Om = sm + G::P2; Op = sm + G::P2 + 5 * NC;
-        } else {  // y at plane c-1: F^{x|z} in x, F^{z|x} in z
-          go = zc && inX; Q = sm + G::QXY + (pm * 2 + 1) * 10 * NC;
-          Ab = sm + G::P1 + 14 * NC; apc = me + 1; k1c = ch0;
-          Bmb = sm + G::FZXY + (pm * 2 + 0) * 7 * NC; Bpb = sm + G::FZXY + (pc * 2 + 0) * 7 * NC;
-          bpc = me; k2c = ch2;
-          Om = sm + G::P2 + 10 * NC; Op = sm + G::P2 + 15 * NC;
+        // ---------------------------------------------- S3: corner coupling, theta = 1/3
+        if (act) {
+  #pragma unroll 1
+          for (int rep = 0; rep < 2; ++rep) {
+            const int kind = kq + 3 * rep;
+            const float *Q, *Fmb, *Fpb;
+            float *Om, *Op;
+            int fpc;
+            float coef;
+            bool go;
+            switch (kind) {
+              case 0:  // q_{x|y} at c
+                go = inY; Q = sm + G::QXY + (pc * 2 + 0) * 10 * NC; Fmb = Fpb = sm + G::P1 + 7 * NC;
+                fpc = me + W; coef = c31; Om = sm + G::P2; Op = sm + G::P2 + 5 * NC;
+                break;
+              case 1:  // q_{y|x} at c
+                go = inX; Q = sm + G::QXY + (pc * 2 + 1) * 10 * NC; Fmb = Fpb = sm + G::P1;
+                fpc = me + 1; coef = c30; Om = sm + G::P2 + 10 * NC; Op = sm + G::P2 + 15 * NC;
+                break;
+              case 2:  // q_{z|x} at c
+                go = inX; Q = sm + G::QZ + pc * 10 * NC; Fmb = Fpb = sm + G::P1;
+                fpc = me + 1; coef = c30; Om = sm + G::QZXM; Op = sm + G::QZXP + pc * 5 * NC;
+                break;
+              case 3:  // q_{z|y} at c
+                go = inY; Q = sm + G::QZ + pc * 10 * NC; Fmb = Fpb = sm + G::P1 + 7 * NC;
+                fpc = me + W; coef = c31; Om = sm + G::QZYM; Op = sm + G::QZYP + pc * 5 * NC;
+                break;
+              case 4:  // q_{x|z} at c-1
+                go = zc; Q = sm + G::QXY + (pm * 2 + 0) * 10 * NC; Fmb = sm + G::FZ + pm * 7 * NC;
+                Fpb = sm + G::FZ + pc * 7 * NC; fpc = me; coef = c32;
+                Om = sm + G::P2 + 20 * NC; Op = sm + G::P2 + 25 * NC;
+                break;
+              default:  // q_{y|z} at c-1
+                go = zc; Q = sm + G::QXY + (pm * 2 + 1) * 10 * NC; Fmb = sm + G::FZ + pm * 7 * NC;
+                Fpb = sm + G::FZ + pc * 7 * NC; fpc = me; coef = c32;
+                Om = sm + G::P2 + 30 * NC; Op = sm + G::P2 + 35 * NC;
+                break;
+            }
+            if (go) {
+              const TFlux<float> Fm = ld7(Fmb, NC, me), Fp = ld7(Fpb, NC, fpc);
+              float qa[5], qb[5], oa[5], ob[5];
+              ld5(Q, NC, me, qa);
+              ld5(Q + 5 * NC, NC, me, qb);
+              transverse1(E, qa, coef, Fp, Fm, oa);
+              transverse1(E, qb, coef, Fp, Fm, ob);
+              st5(Om, NC, me, oa);
+              st5(Op, NC, me, ob);
+            }
+          }
         }
-        if (go) {
-          const TFlux<float> Am = ld7(Ab, NC, me), Ap = ld7(Ab, NC, apc);
-          const TFlux<float> Bm = ld7(Bmb, NC, me), Bp = ld7(Bpb, NC, bpc);
-          float qa[5], qb[5], oa[5], ob[5];
-          ld5(Q, NC, me, qa);
-          ld5(Q + 5 * NC, NC, me, qb);
-          transverse2(E, qa, k1c, Ap, Am, k2c, Bp, Bm, oa);
-          transverse2(E, qb, k1c, Ap, Am, k2c, Bp, Bm, ob);
-          st5(Om, NC, me, oa);
-          st5(Op, NC, me, ob);
-        }
-      }
-      __syncthreads();
+        bar_sync_n(BAR_COL, NTC);
 
-      // ------------------------------------------------ S6: final solves
-      if (act) {
-        const float *L, *Rr;
-        float *O;
-        int lc;
-        bool go;
-        if (kq == 0) {
-          go = zc && mi >= 0 && inY; L = sm + G::P2 + 5 * NC; lc = me - 1; Rr = sm + G::P2;
-          O = sm + G::P1;
-        } else if (kq == 1) {
-          go = zc && mj >= 0 && inX; L = sm + G::P2 + 15 * NC; lc = me - W; Rr = sm + G::P2 + 10 * NC;
-          O = sm + G::P1 + 8 * NC;
-        } else {
-          go = c >= 0 && inX && inY; L = sm + G::QZFP + pm * 5 * NC; lc = me; Rr = sm + G::QZFM;
-          O = sm + G::FFZ + pc * 8 * NC;
+        // ---------------------------------------------- S4: intermediate solves
+        if (act) {
+  #pragma unroll 1
+          for (int rep = 0; rep < 2; ++rep) {
+            const int kind = kq + 3 * rep;
+            const float *L, *Rr;
+            float *O;
+            int lc, dir;
+            bool go;
+            switch (kind) {
+              case 0:  // F^{x|y} at c
+                go = mi >= 0 && inY; dir = 0; L = sm + G::P2 + 5 * NC; lc = me - 1; Rr = sm + G::P2;
+                O = sm + G::P1;
+                break;
+              case 1:  // F^{y|x} at c
+                go = mj >= 0 && inX; dir = 1; L = sm + G::P2 + 15 * NC; lc = me - W;
+                Rr = sm + G::P2 + 10 * NC; O = sm + G::P1 + 7 * NC;
+                break;
+              case 2:  // F^{x|z} at c-1
+                go = zc && mi >= 0; dir = 0; L = sm + G::P2 + 25 * NC; lc = me - 1;
+                Rr = sm + G::P2 + 20 * NC; O = sm + G::P1 + 14 * NC;
+                break;
+              case 3:  // F^{y|z} at c-1
+                go = zc && mj >= 0; dir = 1; L = sm + G::P2 + 35 * NC; lc = me - W;
+                Rr = sm + G::P2 + 30 * NC; O = sm + G::P1 + 21 * NC;
+                break;
+              case 4:  // F^{z|x} at face c-1/2
+                go = c >= 0 && inX; dir = 2; L = sm + G::QZXP + pm * 5 * NC; lc = me;
+                Rr = sm + G::QZXM; O = sm + G::FZXY + (pc * 2 + 0) * 7 * NC;
+                break;
+              default:  // F^{z|y} at face c-1/2
+                go = c >= 0 && inY; dir = 2; L = sm + G::QZYP + pm * 5 * NC; lc = me;
+                Rr = sm + G::QZYM; O = sm + G::FZXY + (pc * 2 + 1) * 7 * NC;
+                break;
+            }
+            if (go) {
+              float l[5], r[5], F[8];
+              ld5(L, NC, lc, l);
+              ld5(Rr, NC, me, r);
+              face_flux_dir(E, dir, l, r, F);
+              st7(O, NC, me, F);
+            }
+          }
         }
-        if (go) {
-          float l[5], r[5], F[8];
-          ld5(L, NC, lc, l);
-          ld5(Rr, NC, me, r);
-          face_flux_dir(E, kq, l, r, F);
-          st8(O, NC, me, F);
+        bar_sync_n(BAR_COL, NTC);
+
+        // ---------------------------------------------- S5: final states, theta = 1/2
+        if (act) {
+          const float *Q, *Ab, *Bmb, *Bpb;
+          float *Om, *Op;
+          int apc, bpc;
+          float k1c, k2c;
+          bool go;
+          if (kq == 0) {  // z at plane c: F^{x|y} in x, F^{y|x} in y
+            go = inX && inY; Q = sm + G::QZ + pc * 10 * NC;
+            Ab = sm + G::P1; apc = me + 1; k1c = ch0;
+            Bmb = Bpb = sm + G::P1 + 7 * NC; bpc = me + W; k2c = ch1;
+            Om = sm + G::QZFM; Op = sm + G::QZFP + pc * 5 * NC;
+          } else if (kq == 1) {  // x at plane c-1: F^{y|z} in y, F^{z|y} in z
+            go = zc && inY; Q = sm + G::QXY + (pm * 2 + 0) * 10 * NC;
+            Ab = sm + G::P1 + 21 * NC; apc = me + W; k1c = ch1;
+            Bmb = sm + G::FZXY + (pm * 2 + 1) * 7 * NC; Bpb = sm + G::FZXY + (pc * 2 + 1) * 7 * NC;
+            bpc = me; k2c = ch2;
+            Om = sm + G::P2; Op = sm + G::P2 + 5 * NC;
+          } else {  // y at plane c-1: F^{x|z} in x, F^{z|x} in z
+            go = zc && inX; Q = sm + G::QXY + (pm * 2 + 1) * 10 * NC;
+            Ab = sm + G::P1 + 14 * NC; apc = me + 1; k1c = ch0;
+            Bmb = sm + G::FZXY + (pm * 2 + 0) * 7 * NC; Bpb = sm + G::FZXY + (pc * 2 + 0) * 7 * NC;
+            bpc = me; k2c = ch2;
+            Om = sm + G::P2 + 10 * NC; Op = sm + G::P2 + 15 * NC;
+          }
+          if (go) {
+            const TFlux<float> Am = ld7(Ab, NC, me), Ap = ld7(Ab, NC, apc);
+            const TFlux<float> Bm = ld7(Bmb, NC, me), Bp = ld7(Bpb, NC, bpc);
+            float qa[5], qb[5], oa[5], ob[5];
+            ld5(Q, NC, me, qa);
+            ld5(Q + 5 * NC, NC, me, qb);
+            transverse2(E, qa, k1c, Ap, Am, k2c, Bp, Bm, oa);
+            transverse2(E, qb, k1c, Ap, Am, k2c, Bp, Bm, ob);
+            st5(Om, NC, me, oa);
+            st5(Op, NC, me, ob);
+          }
         }
+        bar_sync_n(BAR_COL, NTC);
+
+        // ---------------------------------------------- S6: final solves
+        // The fluxes go to the update warps' buffers: x and y faces of plane
+        // c-1, z face c-1/2 (slot c & 1).  The buffers are written once the
+        // update of plane c-2 has released them, and handed over after.
+        {
+          bool go = false;
+          float F[8];
+          if (act) {
+            const float *L, *Rr;
+            int lc;
+            if (kq == 0) {
+              go = zc && mi >= 0 && inY; L = sm + G::P2 + 5 * NC; lc = me - 1; Rr = sm + G::P2;
+            } else if (kq == 1) {
+              go = zc && mj >= 0 && inX; L = sm + G::P2 + 15 * NC; lc = me - W; Rr = sm + G::P2 + 10 * NC;
+            } else {
+              go = c >= 0 && inX && inY; L = sm + G::QZFP + pm * 5 * NC; lc = me; Rr = sm + G::QZFM;
+            }
+            if (go) {
+              float l[5], r[5];
+              ld5(L, NC, lc, l);
+              ld5(Rr, NC, me, r);
+              face_flux_dir(E, kq, l, r, F);
+            }
+          }
+          if (c >= 2) bar_sync_n(BAR_FREE, NT);
+          if (go) {
+            float *O = (kq == 0)   ? sm + G::UF + mj * (TX + 1) + mi
+                       : (kq == 1) ? sm + G::UF + NXF + mj * TX + mi
+                                   : sm + G::FFZ + (c & 1) * 8 * NZF + mj * TX + mi;
+            st8(O, (kq == 2) ? NZF : NUF, 0, F);
+          }
+          if (c >= 1) {
+            __threadfence_block();
+            bar_arrive_n(BAR_READY, NT);
+          }
+        }
+        // no barrier here: the next plane's S0 touches nothing S6 reads or writes
       }
-      __syncthreads();
-      // the update of plane c-1 runs in the next plane's S1 (or below for the last plane)
+    } else {
+      // ------------------------------------------------ update warps (stage 7)
+      const int nout = nxt * nyt;
+      const int uthr = tid - NTC;
+      const bool upd = uthr < nout;
+      const int ui = upd ? uthr % nxt : 0, uj = upd ? uthr / nxt : 0;
+      const long long ucol = (long long)(w.y0 + uj + 4) * b.N[0] + (w.x0 + ui + 4);
+      const double *Gv = a.G ? a.G + nyx::NGRAV * b.pref : nullptr;
+      double *Sn = a.Sn + nyx::NCONS * b.pref;
+      const MixK mk = make_mixk(KK, sc, b);
+      const int ux = uj * (TX + 1) + ui, uy = NXF + uj * TX + ui, uz = uj * TX + ui;
+      for (int p = 0; p < nz; ++p) {
+        // the final fluxes of plane p (x, y faces; z faces p-1/2 and p+1/2)
+        bar_sync_n(BAR_READY, NT);
+        if (upd) {
+          float Fxm[8], Fxp[8], Fym[8], Fyp[8], Fzm[8], Fzp[8];
+          const float *U = sm + G::UF;
+          const float *Zm = sm + G::FFZ + (p & 1) * 8 * NZF, *Zp = sm + G::FFZ + ((p + 1) & 1) * 8 * NZF;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            Fxm[k] = U[k * NUF + ux];
+            Fxp[k] = U[k * NUF + ux + 1];
+            Fym[k] = U[k * NUF + uy];
+            Fyp[k] = U[k * NUF + uy + TX];
+            Fzm[k] = Zm[k * NZF + uz];
+            Fzp[k] = Zp[k * NZF + uz];
+          }
+          const long long id = ucol + (long long)(p + 4) * ps;
+          update_cell_mixed(KK, sc, b, mk, S, Gv, Sn, id, Fxm, Fxp, Fym, Fyp, Fzm, Fzp, dtmin,
+                            flags, a.dtacc != nullptr);
+          if (a.flux_keep)
+            keep_fluxes(a.flux_keep + a.flux_off[w.box], b.n[0], b.n[1], nz, w.x0 + ui,
+                        w.y0 + uj, p, Fxm, Fxp, Fym, Fyp, Fzm, Fzp);
+        }
+        // plane p's buffers may be overwritten (by the fluxes of plane p+1)
+        if (p + 2 <= nz) bar_arrive_n(BAR_FREE, NT);
+      }
     }
-    // update of the last plane: z faces nz-3/2 (slot par(nz-1)) and nz-1/2 (par(nz))
-    if (upd) update(nz - 1, par2(nz - 1), par2(nz));
     __syncthreads();
   }
 
