@@ -108,6 +108,18 @@ def load(path: str):
         L.orc_riemann_counts.restype = None
         L.orc_trace_line.argtypes = [C.POINTER(_Params), C.c_int, dp, dp, C.c_double,
                                      C.c_double, C.c_double, C.c_int, dp, dp, dp, dp]
+        L.orc_amr_check.argtypes = [C.POINTER(_Level), C.POINTER(_Level)]
+        L.orc_amr_check.restype = C.c_int
+        L.orc_amr_interp.argtypes = [C.POINTER(_Level), C.c_int, C.POINTER(dp), C.POINTER(_Level),
+                                     C.POINTER(dp), C.c_int]
+        L.orc_amr_interp.restype = C.c_int
+        L.orc_amr_reflux.argtypes = [C.POINTER(_Level), C.POINTER(dp), C.POINTER(dp),
+                                     C.POINTER(_Level), C.POINTER(dp), C.c_double, C.c_double,
+                                     C.c_double]
+        L.orc_amr_reflux.restype = C.c_int
+        L.orc_amr_average_down.argtypes = [C.POINTER(_Level), C.c_int, C.POINTER(dp),
+                                           C.POINTER(_Level), C.POINTER(dp)]
+        L.orc_amr_average_down.restype = C.c_int
     return L
 
 
@@ -284,3 +296,89 @@ def trace_line(params: OracleParams, q5, g=None, *, dtp, dx, adot=0.0, direction
     lib().orc_trace_line(C.byref(p), n, _dp(q5), None if gl is None else _dp(gl), dtp, dx, adot,
                          direction, _dp(qm), _dp(qp), _dp(bm), _dp(bp))
     return qm, qp, bm, bp
+
+
+# ---------------------------------------------------------------------------
+# Coarse-fine coupling, refinement ratio 2, no subcycling (Sec. 4.1-4.3).
+# A fine level refines the coarse level's domain k as its own domain k
+# (lo_f = 2 lo_c, hi_f = 2 hi_c + 1, periodic); fine boxes start and end on
+# coarse cell boundaries.
+
+def amr_check(coarse, fine) -> bool:
+    """True if ``fine`` refines ``coarse`` as the coupling functions require."""
+    cc, kc = _level(coarse)
+    cf, kf = _level(fine)
+    return lib().orc_amr_check(C.byref(cc), C.byref(cf)) == 0
+
+
+def amr_interp(coarse, cfield, fine, ffield, region: str = "ghosts"):
+    """Conservative limited linear interpolation (Sec. 4.1) of the coarse
+    field (ghosts filled) into a copy of the fine field.  region "all": every
+    cell of every fine box; "ghosts": the fine ghost cells, a ghost cell in
+    the valid region of a fine box taking that cell's value.  Returns the
+    new fine arrays."""
+    cc, kc = _level(coarse)
+    cf, kf = _level(fine)
+    src = [np.ascontiguousarray(a, dtype=np.float64) for a in cfield]
+    out = [np.array(a, dtype=np.float64, order="C", copy=True) for a in ffield]
+    rc = lib().orc_amr_interp(C.byref(cc), src[0].shape[0], _ptrs(src), C.byref(cf), _ptrs(out),
+                              0 if region == "all" else 1)
+    if rc:
+        raise ValueError("oracle interpolation: not a ratio-2 hierarchy or a cell maps to no box")
+    return out
+
+
+def amr_reflux(coarse, cstate, cflux, fine, fflux, *, a_old, a_new, dt):
+    """Reflux (Sec. 4.3, Steps 2 and 8) of a copy of the coarse state.
+    ``cflux`` / ``fflux`` are the per-box flux lists returned by advance()."""
+    cc, kc = _level(coarse)
+    cf, kf = _level(fine)
+    out = [np.array(a, dtype=np.float64, order="C", copy=True) for a in cstate]
+    cfl = [np.ascontiguousarray(a) for per in cflux for a in per]
+    ffl = [np.ascontiguousarray(a) for per in fflux for a in per]
+    rc = lib().orc_amr_reflux(C.byref(cc), _ptrs(out), _ptrs(cfl), C.byref(cf), _ptrs(ffl),
+                              a_old, a_new, dt)
+    if rc:
+        raise ValueError("oracle reflux: not a ratio-2 hierarchy")
+    return out
+
+
+def amr_average_down(coarse, cstate, fine, fstate):
+    """Average down (Sec. 4.3, Step 8): a copy of the coarse field whose
+    cells under the fine level hold the mean of their 8 fine cells."""
+    cc, kc = _level(coarse)
+    cf, kf = _level(fine)
+    out = [np.array(a, dtype=np.float64, order="C", copy=True) for a in cstate]
+    src = [np.ascontiguousarray(a, dtype=np.float64) for a in fstate]
+    rc = lib().orc_amr_average_down(C.byref(cc), out[0].shape[0], _ptrs(out), C.byref(cf),
+                                    _ptrs(src))
+    if rc:
+        raise ValueError("oracle average down: not a ratio-2 hierarchy")
+    return out
+
+
+def amr_estdt(coarse, fine, params: OracleParams, cstate, fstate, a: float) -> float:
+    """Shared time step of both levels (no subcycling, Sec. 4.2-4.3)."""
+    return min(estdt(coarse, params, cstate, a), estdt(fine, params, fstate, a))
+
+
+def amr_step(coarse, fine, params: OracleParams, cstate, fstate, cgrav=None, fgrav=None, *,
+             a_old, a_new, dt, reflux=True, average_down=True):
+    """One two-level advance with no subcycling (Sec. 4.3 Advance(0) with
+    l_a = l_finest): coarse ghost fill; fine ghost fill (fine neighbours,
+    else interpolation from the coarse level); both levels advanced by dt
+    (Steps 2 and 6); reflux of the coarse cells next to the fine level and
+    average down (Step 8).  Gravity arrays must have their ghosts filled.
+    Returns (coarse_new, fine_new, stats_coarse, stats_fine)."""
+    cs = [np.array(a, dtype=np.float64, order="C", copy=True) for a in cstate]
+    fill_ghosts(coarse, cs)
+    fs = amr_interp(coarse, cs, fine, fstate, "ghosts")
+    cn, stc, cfx = advance(coarse, params, cs, cgrav, a_old=a_old, a_new=a_new, dt=dt,
+                           fill_ghosts=False, want_flux=True)
+    fn, stf, ffx = advance(fine, params, fs, fgrav, a_old=a_old, a_new=a_new, dt=dt,
+                           fill_ghosts=False, want_flux=True)
+    if reflux:
+        cn = amr_reflux(coarse, cn, cfx, fine, ffx, a_old=a_old, a_new=a_new, dt=dt)
+    if average_down:
+        cn = amr_average_down(coarse, cn, fine, fn)
+    return cn, fn, stc, stf

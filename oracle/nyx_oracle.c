@@ -899,3 +899,246 @@ void orc_trace_line(const orc_params *p, int n, const double *q5, const double *
       for (int w = 0; w < 3; ++w) beta_p[w * n + i] = bp[w];
   }
 }
+
+/* ------------------------------------------------------------------ */
+/* Coarse-fine coupling, refinement ratio 2, no subcycling.
+ *
+ * Sec. 4.1: grids are refined by 2 and properly nested; data of a newly
+ * refined region comes from a piecewise linear profile in each coarse cell,
+ * built from its nearest neighbours and limited so that it makes no new
+ * maxima or minima, evaluated at the fine cell centres (so the mean of the
+ * 8 fine cells is the coarse value).  Sec. 4.2: no subcycling, both levels
+ * take the same dt.  Sec. 4.3, Step 2: the fine ghost cells take coarse
+ * (Dirichlet) data where no fine grid covers them; Step 8: reflux the
+ * coarse cells next to the fine level, then average the fine solution down.
+ *
+ * Readings (the paper names the operations without their formulas):
+ *  - the slope of the linear profile along d is the MC-limited slope of the
+ *    coarse cell and its two neighbours along d (the PPM slope of O2);
+ *  - "no new extrema": the three slopes are scaled by one factor alpha so
+ *    that the largest and smallest fine values stay inside the range of the
+ *    coarse cell and its six face neighbours;
+ *  - each conserved component (rho, m, rhoE, rhoe) and each gravity
+ *    component is interpolated on its own;
+ *  - reflux corrects the flux-divergence terms of the update only, with the
+ *    update's coefficients (dt' for rho, dt/a_new for m, a_h dt/a_new^2 for
+ *    rhoE and rhoe); the gravity corrector, the pdV term and the dual-energy
+ *    switch are not redone, and averaging down does not re-sync e and E.
+ */
+static int floor_div2(int x) { return (x >= 0) ? x / 2 : -((-x + 1) / 2); }
+
+static int wrap_into(int x, int lo, int hi) {
+  int len = hi - lo + 1;
+  return lo + ((x - lo) % len + len) % len;
+}
+
+int orc_amr_check(const orc_level *C, const orc_level *F) {
+  if (C->ng < 4 || F->ng < 4 || F->ndom != C->ndom) return -1;
+  for (int d = 0; d < C->ndom; ++d)
+    for (int a = 0; a < 3; ++a) {
+      if (F->dom_lo[3 * d + a] != 2 * C->dom_lo[3 * d + a]) return -1;
+      if (F->dom_hi[3 * d + a] != 2 * C->dom_hi[3 * d + a] + 1) return -1;
+      if (C->dom_bc[6 * d + a] != ORC_BC_PERIODIC || C->dom_bc[6 * d + 3 + a] != ORC_BC_PERIODIC)
+        return -1;
+      if (F->dom_bc[6 * d + a] != ORC_BC_PERIODIC || F->dom_bc[6 * d + 3 + a] != ORC_BC_PERIODIC)
+        return -1;
+    }
+  for (int b = 0; b < F->nbox; ++b)
+    for (int a = 0; a < 3; ++a) {
+      if (F->lo[3 * b + a] % 2 != 0 || (F->hi[3 * b + a] + 1) % 2 != 0) return -1;
+    }
+  return 0;
+}
+
+/* Interpolated value of one fine cell: coarse cell (I,J,K) (local indices of
+ * coarse box geometry g, its ghosts filled), fine offsets o in {0,1}^3. */
+static double prolong_value(const double *u, const geom_t *g, int I, int J, int K, const int o[3]) {
+  const size_t id = gidx(g, I, J, K);
+  const double uc = u[id];
+  double s[3], umin = uc, umax = uc;
+  for (int d = 0; d < 3; ++d) {
+    const double um = u[id - g->st[d]], up = u[id + g->st[d]];
+    s[d] = mc_slope(um, uc, up);
+    if (um < umin) umin = um;
+    if (up < umin) umin = up;
+    if (um > umax) umax = um;
+    if (up > umax) umax = up;
+  }
+  const double dev = 0.25 * (fabs(s[0]) + fabs(s[1]) + fabs(s[2]));
+  double alpha = 1.0;
+  if (dev > 0.0) {
+    if (uc + dev > umax) alpha = fmin(alpha, (umax - uc) / dev);
+    if (uc - dev < umin) alpha = fmin(alpha, (uc - umin) / dev);
+  }
+  const double xo = o[0] ? 0.25 : -0.25, yo = o[1] ? 0.25 : -0.25, zo = o[2] ? 0.25 : -0.25;
+  return uc + alpha * (s[0] * xo + s[1] * yo + s[2] * zo);
+}
+
+int orc_amr_interp(const orc_level *C, int ncomp, double *const *cf, const orc_level *F,
+                   double *const *ff, int region) {
+  if (orc_amr_check(C, F)) return -1;
+  int err = 0;
+  for (int b = 0; b < F->nbox; ++b) {
+    geom_t g = make_geom(F->lo + 3 * b, F->hi + 3 * b, F->ng);
+    const int dom = F->dom[b];
+    const int *flo = F->dom_lo + 3 * dom, *fhi = F->dom_hi + 3 * dom;
+    const int *clo = C->dom_lo + 3 * dom;
+#pragma omp parallel for schedule(static) reduction(| : err)
+    for (int k = -g.ng; k < g.n[2] + g.ng; ++k) {
+      int hint = -1, chint = -1;
+      for (int j = -g.ng; j < g.n[1] + g.ng; ++j)
+        for (int i = -g.ng; i < g.n[0] + g.ng; ++i) {
+          const int loc[3] = {i, j, k};
+          int inside = 1;
+          for (int d = 0; d < 3; ++d)
+            if (loc[d] < 0 || loc[d] >= g.n[d]) inside = 0;
+          if (region == 1 && inside) continue;
+          int gi[3];
+          for (int d = 0; d < 3; ++d) gi[d] = wrap_into(F->lo[3 * b + d] + loc[d], flo[d], fhi[d]);
+          const size_t dst = gidx(&g, i, j, k);
+          if (region == 1) {
+            const int sb = find_box(F, dom, gi, hint);
+            if (sb >= 0) {
+              hint = sb;
+              geom_t gs = make_geom(F->lo + 3 * sb, F->hi + 3 * sb, F->ng);
+              const size_t src = gidx(&gs, gi[0] - F->lo[3 * sb], gi[1] - F->lo[3 * sb + 1],
+                                      gi[2] - F->lo[3 * sb + 2]);
+              for (int c = 0; c < ncomp; ++c) ff[b][c * g.vol + dst] = ff[sb][c * gs.vol + src];
+              continue;
+            }
+          }
+          int ci[3], o[3];
+          for (int d = 0; d < 3; ++d) {
+            const int rel = gi[d] - flo[d];
+            ci[d] = clo[d] + floor_div2(rel);
+            o[d] = rel - 2 * floor_div2(rel);
+          }
+          const int cb = find_box(C, dom, ci, chint);
+          if (cb < 0) {
+            err = 1;
+            continue;
+          }
+          chint = cb;
+          geom_t gc = make_geom(C->lo + 3 * cb, C->hi + 3 * cb, C->ng);
+          for (int c = 0; c < ncomp; ++c)
+            ff[b][c * g.vol + dst] =
+                prolong_value(cf[cb] + c * gc.vol, &gc, ci[0] - C->lo[3 * cb],
+                              ci[1] - C->lo[3 * cb + 1], ci[2] - C->lo[3 * cb + 2], o);
+        }
+    }
+  }
+  return err ? -1 : 0;
+}
+
+/* Coarse cell ci (domain index, wrapped) is under the fine level if a fine
+ * box holds its first fine cell. */
+static int coarse_covered(const orc_level *C, const orc_level *F, int dom, const int ci[3]) {
+  int fi[3];
+  for (int d = 0; d < 3; ++d) fi[d] = F->dom_lo[3 * dom + d] + 2 * (ci[d] - C->dom_lo[3 * dom + d]);
+  return find_box(F, dom, fi, -1) >= 0;
+}
+
+int orc_amr_reflux(const orc_level *C, double *const *cstate, double *const *cflux,
+                   const orc_level *F, double *const *fflux, double a_old, double a_new,
+                   double dt) {
+  if (orc_amr_check(C, F)) return -1;
+  const double a_half = 0.5 * (a_old + a_new);
+  const double dtp = dt / a_half;
+  const double ian = 1.0 / a_new;
+  const double ian2 = 1.0 / (a_new * a_new);
+  const double ahdt = a_half * dt;
+  const double coef[6] = {dtp, dt * ian, dt * ian, dt * ian, ahdt * ian2, ahdt * ian2};
+  /* six orientations in a fixed order (x low, x high, y low, ...); within
+   * one orientation no coarse cell is met twice */
+  for (int orient = 0; orient < 6; ++orient) {
+    const int d = orient / 2, high = orient % 2;
+    const int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;
+    for (int fb = 0; fb < F->nbox; ++fb) {
+      const int dom = F->dom[fb];
+      const int *clo = C->dom_lo + 3 * dom, *chi = C->dom_hi + 3 * dom;
+      const int *flo = F->dom_lo + 3 * dom;
+      int fl[3], fn[3], cl[3], ch[3];
+      for (int a = 0; a < 3; ++a) {
+        fl[a] = F->lo[3 * fb + a];
+        fn[a] = F->hi[3 * fb + a] - fl[a] + 1;
+        cl[a] = clo[a] + (fl[a] - flo[a]) / 2;
+        ch[a] = cl[a] + fn[a] / 2 - 1;
+      }
+      int fe[3] = {fn[0], fn[1], fn[2]};
+      fe[d] += 1;
+      const size_t fv = (size_t)fe[0] * fe[1] * fe[2];
+      const double *Ff = fflux[3 * fb + d];
+      const int ffi = high ? fn[d] : 0; /* fine face index along d */
+      for (int q2 = cl[t2]; q2 <= ch[t2]; ++q2)
+        for (int q1 = cl[t1]; q1 <= ch[t1]; ++q1) {
+          int P[3];
+          P[d] = high ? ch[d] + 1 : cl[d] - 1;
+          P[t1] = q1;
+          P[t2] = q2;
+          for (int a = 0; a < 3; ++a) P[a] = wrap_into(P[a], clo[a], chi[a]);
+          if (coarse_covered(C, F, dom, P)) continue;
+          const int cb = find_box(C, dom, P, -1);
+          if (cb < 0) return -1;
+          geom_t gc = make_geom(C->lo + 3 * cb, C->hi + 3 * cb, C->ng);
+          int pl[3];
+          for (int a = 0; a < 3; ++a) pl[a] = P[a] - C->lo[3 * cb + a];
+          int ce[3] = {gc.n[0], gc.n[1], gc.n[2]};
+          ce[d] += 1;
+          const size_t cv = (size_t)ce[0] * ce[1] * ce[2];
+          int cf[3] = {pl[0], pl[1], pl[2]};
+          if (!high) cf[d] += 1; /* the outside cell's high face */
+          const size_t cid = ((size_t)cf[2] * ce[1] + cf[1]) * ce[0] + cf[0];
+          const double *Fc = cflux[3 * cb + d];
+          const double idx = 1.0 / C->dx[3 * cb + d];
+          const size_t sid = gidx(&gc, pl[0], pl[1], pl[2]);
+          for (int c = 0; c < 6; ++c) {
+            double fsum = 0.0;
+            for (int s = 0; s < 4; ++s) {
+              int fi[3];
+              fi[d] = ffi;
+              fi[t1] = 2 * (q1 - cl[t1]) + (s & 1);
+              fi[t2] = 2 * (q2 - cl[t2]) + (s >> 1);
+              const double v = Ff[c * fv + ((size_t)fi[2] * fe[1] + fi[1]) * fe[0] + fi[0]];
+              fsum = (s == 0) ? v : fsum + v;
+            }
+            const double favg = 0.25 * fsum;
+            const double corr = coef[c] * ((favg - Fc[c * cv + cid]) * idx);
+            double *U = cstate[cb] + c * gc.vol + sid;
+            *U = high ? *U + corr : *U - corr;
+          }
+        }
+    }
+  }
+  return 0;
+}
+
+int orc_amr_average_down(const orc_level *C, int ncomp, double *const *cstate,
+                         const orc_level *F, double *const *fstate) {
+  if (orc_amr_check(C, F)) return -1;
+  for (int fb = 0; fb < F->nbox; ++fb) {
+    const int dom = F->dom[fb];
+    geom_t g = make_geom(F->lo + 3 * fb, F->hi + 3 * fb, F->ng);
+    const int *clo = C->dom_lo + 3 * dom, *flo = F->dom_lo + 3 * dom;
+    for (int K = 0; K < g.n[2] / 2; ++K)
+      for (int J = 0; J < g.n[1] / 2; ++J)
+        for (int I = 0; I < g.n[0] / 2; ++I) {
+          int ci[3] = {I, J, K};
+          for (int a = 0; a < 3; ++a) ci[a] += clo[a] + (F->lo[3 * fb + a] - flo[a]) / 2;
+          const int cb = find_box(C, dom, ci, -1);
+          if (cb < 0) return -1;
+          geom_t gc = make_geom(C->lo + 3 * cb, C->hi + 3 * cb, C->ng);
+          const size_t cid = gidx(&gc, ci[0] - C->lo[3 * cb], ci[1] - C->lo[3 * cb + 1],
+                                  ci[2] - C->lo[3 * cb + 2]);
+          for (int c = 0; c < ncomp; ++c) {
+            double s = 0.0;
+            for (int o = 0; o < 8; ++o) {
+              const double v = fstate[fb][c * g.vol + gidx(&g, 2 * I + (o & 1), 2 * J + ((o >> 1) & 1),
+                                                           2 * K + (o >> 2))];
+              s = (o == 0) ? v : s + v;
+            }
+            cstate[cb][c * gc.vol + cid] = 0.125 * s;
+          }
+        }
+  }
+  return 0;
+}

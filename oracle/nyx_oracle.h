@@ -12,6 +12,11 @@
  * CPU-baseline leg may load this library.  It shares no code with the CUDA
  * path and includes none of its headers.
  *
+ * Coarse-fine coupling (orc_amr_*): a fine level refines a coarse level by
+ * 2 in every direction with no subcycling (Sec. 4.2; Sec. 4.3: Step 2 with
+ * coarse Dirichlet data for the fine ghosts, Step 8 reflux and average
+ * down; Sec. 4.1 for the conservative limited linear interpolation).
+ *
  * Layout of every box array: ncomp blocks of (nz+2ng)(ny+2ng)(nx+2ng)
  * doubles, x fastest; cell (i,j,k) of the valid region [0,n) sits at
  * ((c*Nz + k+ng)*Ny + j+ng)*Nx + i+ng.  State components: rho, m_x, m_y,
@@ -75,6 +80,35 @@ double orc_estdt(const orc_level *lev, const orc_params *p, double *const *state
 
 /* Two-shock solves and Newton iterations since the last reset (all threads). */
 void orc_riemann_counts(long long *calls, long long *iters, int reset);
+
+/* ---- coarse-fine coupling, refinement ratio 2 (Sec. 4.1-4.3) ----------
+ * Fine domain k refines coarse domain k: dom_lo_f = 2 dom_lo_c, dom_hi_f =
+ * 2 dom_hi_c + 1, every face periodic.  Fine boxes start and end on coarse
+ * cell boundaries (even lo, odd hi).  Returns 0, or -1 if the pair is not
+ * such a hierarchy. */
+int orc_amr_check(const orc_level *C, const orc_level *F);
+
+/* Conservative limited linear interpolation (Sec. 4.1) of the coarse field
+ * cf (ghosts filled) into the fine field ff.  region 0: every cell of every
+ * fine box, valid and ghost; region 1: the fine ghost cells only -- a ghost
+ * cell that lies in the valid region of a fine box (after periodic wrap)
+ * takes that cell's value, every other one is interpolated. */
+int orc_amr_interp(const orc_level *C, int ncomp, double *const *cf, const orc_level *F,
+                   double *const *ff, int region);
+
+/* Reflux (Sec. 4.3, Steps 2 and 8): every coarse cell outside the fine level that
+ * shares a face with it gets the difference between the area average of the
+ * fine fluxes on that face and its own coarse flux, with the coefficients
+ * of the update (a_old, a_new, dt as given to orc_advance).  cflux / fflux
+ * are the flux_out arrays of the two advances (box*3 + dir). */
+int orc_amr_reflux(const orc_level *C, double *const *cstate, double *const *cflux,
+                   const orc_level *F, double *const *fflux, double a_old, double a_new,
+                   double dt);
+
+/* Average down (Sec. 4.3, Step 8): every coarse cell under the fine level
+ * takes the mean of its 8 fine cells, all ncomp components. */
+int orc_amr_average_down(const orc_level *C, int ncomp, double *const *cstate,
+                         const orc_level *F, double *const *fstate);
 
 /* Unit-level entry points used by the pin tests. */
 void orc_ppm_line(int n, const double *s, double *sL, double *sR, double *s6);

@@ -416,3 +416,81 @@ def uniform_level(state6, n=(16, 16, 16), dx=1.0 / 16, grav=None) -> Workload:
                                      (3, n[2], n[1], n[0])))
         G = [g]
     return Workload("uniform", lev, [S], G, np.ones(2), 5.0 / 3.0, 0.5, 1)
+
+
+# ---------------------------------------------------------------------------
+# two-level hierarchies (a fine level refining coarse regions by 2)
+
+def refined_level(coarse: LevelSpec, regions, name="fine") -> LevelSpec:
+    """The ratio-2 refinement of coarse regions.  Region (d, lo, hi), in
+    coarse cells of domain d, becomes the fine box of fine cells
+    2(lo - dom_lo) + dom_lo_f .. 2(hi - dom_lo) + 1 + dom_lo_f with half the
+    cell width.  Fine domain k refines coarse domain k (dom_lo_f = 2 dom_lo,
+    dom_hi_f = 2 dom_hi + 1) with the same boundary kinds."""
+    dlo_f = 2 * coarse.dom_lo
+    dhi_f = 2 * coarse.dom_hi + 1
+    lo, hi, dom, dx = [], [], [], []
+    for (d, rlo, rhi) in regions:
+        rlo, rhi = np.asarray(rlo), np.asarray(rhi)
+        lo.append(2 * (rlo - coarse.dom_lo[d]) + dlo_f[d])
+        hi.append(2 * (rhi - coarse.dom_lo[d]) + 1 + dlo_f[d])
+        dom.append(d)
+        # cell width of the coarse box holding the region's first cell
+        inside = np.all((coarse.lo <= rlo) & (rlo <= coarse.hi), axis=1) & (coarse.dom == d)
+        dx.append(coarse.dx[int(np.argmax(inside))] / 2)
+    return _mk(lo, hi, dom, dx, dlo_f, dhi_f, coarse.dom_bc, name)
+
+
+def refine_boxes(coarse: LevelSpec, boxes, name="fine") -> LevelSpec:
+    """The ratio-2 refinement of whole coarse boxes."""
+    return refined_level(coarse, [(int(coarse.dom[b]), coarse.lo[b], coarse.hi[b]) for b in boxes],
+                         name)
+
+
+@dataclass
+class AmrWorkload:
+    """A coarse workload and a fine level refining part of it.  The fine
+    initial data and gravity are not generated here: each path makes them by
+    its own interpolation from the coarse level (Sec. 4.1: newly refined
+    regions take interpolated coarse data)."""
+    name: str
+    coarse: Workload
+    fine: LevelSpec
+    refined: list
+
+
+def amr_level(n=128, box=32, nfine=6, sigma=1.0, seed=5, select_seed=11, nsteps=10,
+              a0=1.0 / 51, aN=1.0 / 49, refined=None) -> AmrWorkload:
+    """A periodic n^3 comoving level cut into box^3 boxes, with ``nfine``
+    seeded boxes refined by 2 (or the given coarse box indices)."""
+    w = tiled_box(n=n, box=box, sigma=sigma, seed=seed, nsteps=nsteps, a0=a0, aN=aN)
+    if refined is None:
+        rng = np.random.default_rng(select_seed)
+        refined = sorted(int(b) for b in rng.choice(w.level.nbox, size=nfine, replace=False))
+    fine = refine_boxes(w.level, refined)
+    w.name = f"{w.name}, {len(refined)} refined by 2"
+    return AmrWorkload(w.name, w, fine, list(refined))
+
+
+def amr_large(n=512, box=32, nfine=410, sigma=1.0, seed=5, select_seed=11, nsteps=100,
+              coarse_only=False) -> AmrWorkload:
+    """The large level's box structure with its refined 10% coupled: a
+    periodic 512^3 level as 4096 boxes of 32^3, 410 seeded boxes refined by 2
+    (64^3 fine boxes at half the cell width over them).  a from 1/51 to 1/31."""
+    coarse = tiled_level(n, box, name="coarse")
+    f = comoving_fields((n, n, n), sigma, seed, 1.0 / n)
+    S, G = [], []
+    for b in range(coarse.nbox):
+        i0, j0, k0 = (int(v) for v in coarse.lo[b])
+        sl = (slice(k0, k0 + box), slice(j0, j0 + box), slice(i0, i0 + box))
+        fb = Fields(np.ascontiguousarray(f.rho[sl]), np.ascontiguousarray(f.u[(slice(None),) + sl]),
+                    np.ascontiguousarray(f.g[(slice(None),) + sl]))
+        s, g = _patch_state(coarse, b, fb)
+        S.append(s)
+        G.append(g)
+    del f
+    rng = np.random.default_rng(select_seed)
+    refined = sorted(int(b) for b in rng.choice(coarse.nbox, size=nfine, replace=False))
+    w = Workload(f"{n}^3 level as {coarse.nbox} boxes of {box}^3, {nfine} refined by 2",
+                 coarse, S, G, a_schedule(1.0 / 51, 1.0 / 31, nsteps), 5.0 / 3.0, 0.5, nsteps, True)
+    return AmrWorkload(w.name, w, refine_boxes(coarse, refined), refined)

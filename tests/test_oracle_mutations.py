@@ -10,6 +10,7 @@ import subprocess
 import pytest
 
 import oracle
+import test_oracle_amr as ta
 import test_oracle_ppm as tp
 import test_oracle_riemann as tr
 import test_oracle_step as ts
@@ -76,6 +77,31 @@ MUTANTS = {
     "periodic wrap off by one": ("x = dlo[d] + ((x - dlo[d]) % len + len) % len;",
                                  "x = dlo[d] + ((x - dlo[d] + 1) % len + len) % len;",
                                  ts.test_ghost_fill_periodic_outflow_and_tiles, ()),
+    # coarse-fine coupling
+    "reflux sign flipped": ("*U = high ? *U + corr : *U - corr;",
+                            "*U = high ? *U - corr : *U + corr;",
+                            ta.test_two_level_step_conserves_only_with_reflux, (True,)),
+    "reflux against the covered cell's face": ("if (!high) cf[d] += 1;", "if (high) cf[d] += 1;",
+                                               ta.test_two_level_step_conserves_only_with_reflux,
+                                               (True,)),
+    "fine fluxes from the opposite face": ("const int ffi = high ? fn[d] : 0;",
+                                           "const int ffi = high ? 0 : fn[d];",
+                                           ta.test_two_level_step_conserves_only_with_reflux,
+                                           (True,)),
+    "interpolation offset 1/2": ("const double xo = o[0] ? 0.25 : -0.25",
+                                 "const double xo = o[0] ? 0.5 : -0.5",
+                                 ta.test_interp_reproduces_linear_data, ()),
+    "one-sided interpolation slope": ("s[d] = mc_slope(um, uc, up);", "s[d] = mc_slope(uc, uc, up);",
+                                      ta.test_interp_reproduces_linear_data, ()),
+    "extrema limiter off": ("  double alpha = 1.0;\n  if (dev > 0.0) {",
+                            "  double alpha = 1.0;\n  if (dev < 0.0) {",
+                            ta.test_interp_is_conservative_and_makes_no_new_extrema, ()),
+    "average down over 4 cells": ("cstate[cb][c * gc.vol + cid] = 0.125 * s;",
+                                  "cstate[cb][c * gc.vol + cid] = 0.25 * s;",
+                                  ta.test_average_down_undoes_interpolation, ()),
+    "fine ghosts never copied from fine neighbours": ("          if (region == 1) {\n            const int sb",
+                                                      "          if (region == 2) {\n            const int sb",
+                                                      ta.test_fine_ghosts_take_fine_neighbours_first, ()),
 }
 
 
