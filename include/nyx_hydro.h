@@ -8,7 +8,10 @@
  * the discretisation of Sec. 3.2 (unsplit PPM Godunov with characteristic
  * tracing, reference states, full corner coupling, two-shock Riemann
  * solver), over every box of one AMR level (Sec. 4.1), plus the CFL time
- * step of Sec. 3.5.
+ * step of Sec. 3.5.  The nyx_amr_* calls couple two such levels, a fine
+ * level refining a coarse one by 2 with no subcycling (Sec. 4.1-4.3):
+ * coarse-to-fine interpolation of the fine ghost cells, reflux and average
+ * down.
  *
  * Conventions for every entry point:
  *  - Return 0 (NYX_OK) on success or a negative NYX_E* code; the text of
@@ -93,6 +96,10 @@ typedef struct {
   int batching;            /* NYX_PERSISTENT or NYX_PER_BOX */
   int autotune;            /* 1: time the tile shapes once and keep the fastest */
   int keep_fluxes;         /* 1: keep the final fluxes of the last advance */
+  int coarse_fine;         /* 1: the level is the fine level of a nyx_amr pair: ghost
+                              cells that no box of the level covers are left to
+                              nyx_amr_interp (coarse data, Sec. 4.3 Step 2) instead
+                              of being an error */
 } nyx_hydro_params;
 
 typedef struct nyx_plan nyx_plan;
@@ -108,7 +115,7 @@ typedef struct {
 
 /* Fill *params with the defaults (gamma 5/3, cfl 0.5, small_dens 1e-10,
  * small_pres 1e-12, eta_de 1e-4, 12 iterations, tol 1e-10, FP64,
- * corrector on, persistent, autotune off, keep_fluxes off). */
+ * corrector on, persistent, autotune off, keep_fluxes off, coarse_fine off). */
 void nyx_hydro_default_params(nyx_hydro_params *params);
 
 /* Validate the level (Sec. 4.1: even positive extents, ng == 4, boxes of a
@@ -231,6 +238,80 @@ int nyx_hydro_estdt_noalloc(const nyx_level_desc *level, const nyx_hydro_params 
 
 /* Release the plan's device and host resources (not the caller's buffers). */
 int nyx_plan_destroy(nyx_plan *plan);
+
+/* ---------------------------------------------------------------- two levels
+ * Coarse-fine coupling of Sec. 4.1-4.3 for a refinement ratio of 2 and no
+ * subcycling (both levels take the same dt, Sec. 4.2).
+ *  - Hierarchy: the fine plan's domain k refines the coarse plan's domain k
+ *    (fine lo = 2 coarse lo, fine hi = 2 coarse hi + 1), every domain face
+ *    periodic; fine boxes start and end on coarse cell boundaries (even lo,
+ *    odd hi).  The coarse level must cover its domains (a plain plan), the
+ *    fine plan is made with coarse_fine = 1; both with keep_fluxes = 1, the
+ *    same precision and the same stream.
+ *  - Interpolation (Sec. 4.1): in each coarse cell a linear profile with the
+ *    MC-limited slope along each axis (from the two face neighbours), all
+ *    three slopes scaled by one factor so that no fine value leaves the
+ *    range of the coarse cell and its six face neighbours; the fine value is
+ *    the profile at the fine cell centre (the 8 fine cells average to the
+ *    coarse value).  Each component separately.
+ *  - Reflux (Sec. 4.3 Steps 2 and 8): a coarse cell outside the fine level
+ *    that shares a face with it has that face's coarse flux replaced by the
+ *    mean of the 4 fine fluxes, with the update's coefficients (dt/a_h for
+ *    rho, dt/a_new for m, a_h dt/a_new^2 for rhoE and rhoe).  The gravity
+ *    corrector, pdV and dual-energy terms are not redone.
+ *  - Average down (Sec. 4.3 Step 8): a coarse cell under the fine level
+ *    takes the mean of its 8 fine cells (every component).
+ * The amr object keeps both plans (which the caller still owns and must
+ * destroy after it) and its own device tables. */
+typedef struct nyx_amr nyx_amr;
+
+#define NYX_AMR_GHOSTS 0   /* fine ghost cells that no fine box covers */
+#define NYX_AMR_ALL 1      /* every cell of every fine box (initial data) */
+
+/* Check the pair and build the interpolation, reflux and average-down
+ * tables.  NYX_EINVAL if the plans do not form such a hierarchy. */
+int nyx_amr_create(nyx_plan *coarse, nyx_plan *fine, nyx_amr **out);
+
+/* Interpolate a coarse field (device, ncomp components, coarse layout, its
+ * ghost cells filled) into a fine field (fine layout).  region
+ * NYX_AMR_GHOSTS writes the fine ghost cells -- all of them; the fine
+ * plan's nyx_hydro_fill (or its advance) then overwrites those another fine
+ * box covers; NYX_AMR_ALL writes every cell of every fine box. */
+int nyx_amr_interp(nyx_amr *amr, const double *coarse_field, double *fine_field, int ncomp,
+                   int region);
+
+/* Reflux the coarse state coarse_new (device, 6 components) with the
+ * fluxes and step scalars of the last advance of each plan. */
+int nyx_amr_reflux(nyx_amr *amr, double *coarse_new);
+
+/* Average the fine field (ncomp components) down onto the coarse field. */
+int nyx_amr_average_down(nyx_amr *amr, const double *fine_field, double *coarse_field,
+                         int ncomp);
+
+/* Shared CFL step of both levels: *dt_dev = min of nyx_hydro_estdt over the
+ * coarse and the fine state[cur] at a. */
+int nyx_amr_estdt(nyx_amr *amr, const nyx_level *coarse, const nyx_level *fine,
+                  const double *a_dev, double *dt_dev);
+
+/* One two-level step (Sec. 4.3 Advance(0) with no subcycling): advance the
+ * coarse level (Steps 2 and 6, its own ghost fill first); interpolate the
+ * fine ghost cells from the coarse state at t^n; advance the fine level (its
+ * fine-fine ghost copies first); reflux and average down into the new
+ * coarse state.  Both levels' cur flip.  Gravity: each level's grav (ghosts
+ * filled; the fine one e.g. by nyx_amr_interp with NYX_AMR_ALL).
+ * dt_next_dev (may be NULL) receives nyx_amr_estdt of the new states at
+ * a_new.  Scalars are device pointers. */
+int nyx_amr_step(nyx_amr *amr, nyx_level *coarse, nyx_level *fine, const double *a_old_dev,
+                 const double *a_new_dev, const double *dt_dev, double *dt_next_dev);
+
+/* nsteps two-level steps, like nyx_hydro_run (a_dev: nsteps+1 scale
+ * factors; dt_dev: nsteps+1 scalars, dt_dev[0] computed here when
+ * compute_dt0 != 0); use_graph != 0 captures them once into a CUDA graph. */
+int nyx_amr_run(nyx_amr *amr, nyx_level *coarse, nyx_level *fine, const double *a_dev,
+                double *dt_dev, int nsteps, int compute_dt0, int use_graph);
+
+/* Release the amr object (not the plans or the caller's buffers). */
+int nyx_amr_destroy(nyx_amr *amr);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *nyx_last_error(void);

@@ -17,12 +17,16 @@
 #include "nyx_hydro.h"
 #include "nyx_internal.cuh"
 #include "nyx_kernels.h"
+#include "nyx_plan.h"
 
 using namespace nyx;
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
+
+namespace nyx {
+namespace host {
 
 int fail(int code, const std::string &msg) {
   g_err = msg;
@@ -33,66 +37,10 @@ int cuda_fail(cudaError_t e, const char *what) {
   return fail(NYX_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-#define CK(call)                                    \
-  do {                                              \
-    cudaError_t e_ = (call);                        \
-    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
-  } while (0)
+}  // namespace host
+}  // namespace nyx
 
-struct FillPass {
-  FillRect *d_rects = nullptr;
-  long long *d_pref = nullptr;
-  int n = 0;
-  long long total = 0;
-};
-
-using GraphKey = std::tuple<const void *, const void *, const void *, int, const void *, const void *,
-                            int, int>;
-
-}  // namespace
-
-struct nyx_plan {
-  int nbox = 0;
-  std::vector<nyx_box> boxes;
-  std::vector<nyx_domain> doms;
-  nyx_hydro_params prm{};
-  cudaStream_t stream = nullptr;
-  std::vector<BoxDev> hbox;
-  std::vector<long long> cell_pref;
-  long long total_cells = 0;
-  long long total_stride = 0;
-  BoxDev *d_boxes = nullptr;
-  long long *d_cell_pref = nullptr;
-  SchemeConsts hK{};
-  SchemeConsts *d_K = nullptr;
-  StepConsts *d_SC = nullptr;
-  BoxStep *d_BS = nullptr;
-  unsigned long long *d_dtacc = nullptr;
-  unsigned *d_status = nullptr;
-  unsigned *d_status_tune = nullptr;  // status of autotuner launches (never reported)
-  double *d_scal = nullptr;  // host-call scalars: a_old, a_new, dt, dt_next
-  FillPass pass[4];
-  // per-box FP64 form
-  double *d_scratch = nullptr;
-  long long Vmax = 0;
-  // final-flux store
-  double *d_flux = nullptr;
-  std::vector<long long> flux_off;
-  long long *d_flux_off = nullptr;
-  bool flux_valid = false;
-  // fused persistent form
-  WorkItem *d_items[8] = {nullptr};
-  int nitems[8] = {0};
-  int *d_queue = nullptr;
-  int shape = 0;
-  bool tuned = false;
-  int max_grid[8] = {0};
-  std::map<GraphKey, std::pair<cudaGraphExec_t, long long>> graphs;  // graph, kernels in it
-  // counters and profiling
-  long long launches = 0;
-  bool profiling = false;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_fill, ev_adv;
-};
+using namespace nyx::host;
 
 namespace {
 
@@ -251,7 +199,9 @@ bool build_fill(const nyx_plan &P, std::vector<FillRect> out[4]) {
         out[1 + a].push_back(R);
       }
     }
-    if (covered != ghost) {
+    // the fine level of a coarse-fine pair may leave ghost cells to the
+    // coarse interpolation; every other level covers each exactly once
+    if (P.prm.coarse_fine ? covered > ghost : covered != ghost) {
       g_err = "ghost cells of box " + std::to_string(b) + " covered " + std::to_string(covered) +
               " times in total, expected " + std::to_string(ghost) +
               " (gap, overlap or unsupported boundary)";
@@ -499,6 +449,50 @@ int enqueue_run(nyx_plan *P, nyx_level *L, const double *a_dev, double *dt_dev, 
 
 }  // namespace
 
+namespace nyx {
+namespace host {
+
+int plan_fill(nyx_plan *P, double *field, int ncomp) { return do_fill(P, field, ncomp); }
+
+int plan_advance(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_new,
+                 const double *dt, const double *grav, double *dt_next) {
+  return do_advance(P, L, a_old, a_new, dt, grav, dt_next);
+}
+
+void plan_estdt_accumulate(nyx_plan *P, const double *state, const double *a_dev,
+                           unsigned long long *acc) {
+  if (P->prm.precision == NYX_MIXED)
+    launch_estdt_mixed(P->d_boxes, P->d_cell_pref, P->nbox, P->total_cells, state, P->d_K, a_dev,
+                       acc, P->stream);
+  else
+    launch_estdt(P->d_boxes, P->d_cell_pref, P->nbox, P->total_cells, state, P->d_K, a_dev, acc,
+                 P->stream);
+  P->launches += 1;
+}
+
+bool plan_capturing(nyx_plan *P) { return capturing(P); }
+
+int plan_tune(nyx_plan *P, nyx_level *L, const double *a_dev, const double *dt_dev) {
+  if (!(P->prm.batching == NYX_PERSISTENT && P->prm.autotune && !P->tuned)) return NYX_OK;
+  FusedArgs a{};
+  a.boxes = P->d_boxes;
+  a.queue = P->d_queue;
+  a.K = P->d_K;
+  a.SC = P->d_SC;
+  a.BS = P->d_BS;
+  a.S = L->state[L->cur];
+  a.G = L->grav;
+  a.Sn = L->state[1 - L->cur];
+  a.status = P->d_status_tune;
+  do_fill(P, L->state[L->cur], NCONS);
+  launch_step_setup(P->d_K, a_dev, a_dev + 1, dt_dev, P->d_SC, P->d_boxes, P->nbox, P->d_BS,
+                    P->stream);
+  return tune_shape(P, a);
+}
+
+}  // namespace host
+}  // namespace nyx
+
 // ====================================================================== fused dispatch
 namespace nyx {
 
@@ -539,6 +533,7 @@ void nyx_hydro_default_params(nyx_hydro_params *p) {
   p->batching = NYX_PERSISTENT;
   p->autotune = 0;
   p->keep_fluxes = 0;
+  p->coarse_fine = 0;
 }
 
 const char *nyx_last_error(void) { return g_err.c_str(); }

@@ -1,0 +1,102 @@
+// nyx_plan.h -- the plan object of libnyxhydro.so and the host helpers the
+// translation units share (level advance, ghost fill, CFL reduction).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <tuple>
+#include <utility>
+#include <vector>
+
+#include "nyx_hydro.h"
+#include "nyx_internal.cuh"
+
+namespace nyx {
+namespace host {
+
+struct FillPass {
+  FillRect *d_rects = nullptr;
+  long long *d_pref = nullptr;
+  int n = 0;
+  long long total = 0;
+};
+
+using GraphKey = std::tuple<const void *, const void *, const void *, int, const void *, const void *,
+                            int, int>;
+
+// Set the thread's last error and return code.
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+}  // namespace host
+}  // namespace nyx
+
+#define CK(call)                                                       \
+  do {                                                                 \
+    cudaError_t e_ = (call);                                           \
+    if (e_ != cudaSuccess) return nyx::host::cuda_fail(e_, #call);     \
+  } while (0)
+
+struct nyx_plan {
+  int nbox = 0;
+  std::vector<nyx_box> boxes;
+  std::vector<nyx_domain> doms;
+  nyx_hydro_params prm{};
+  cudaStream_t stream = nullptr;
+  std::vector<nyx::BoxDev> hbox;
+  std::vector<long long> cell_pref;
+  long long total_cells = 0;
+  long long total_stride = 0;
+  nyx::BoxDev *d_boxes = nullptr;
+  long long *d_cell_pref = nullptr;
+  nyx::SchemeConsts hK{};
+  nyx::SchemeConsts *d_K = nullptr;
+  nyx::StepConsts *d_SC = nullptr;
+  nyx::BoxStep *d_BS = nullptr;
+  unsigned long long *d_dtacc = nullptr;
+  unsigned *d_status = nullptr;
+  unsigned *d_status_tune = nullptr;  // status of autotuner launches (never reported)
+  double *d_scal = nullptr;  // host-call scalars: a_old, a_new, dt, dt_next
+  nyx::host::FillPass pass[4];
+  // per-box FP64 form
+  double *d_scratch = nullptr;
+  long long Vmax = 0;
+  // final-flux store
+  double *d_flux = nullptr;
+  std::vector<long long> flux_off;
+  long long *d_flux_off = nullptr;
+  bool flux_valid = false;
+  // fused persistent form
+  nyx::WorkItem *d_items[8] = {nullptr};
+  int nitems[8] = {0};
+  int *d_queue = nullptr;
+  int shape = 0;
+  bool tuned = false;
+  int max_grid[8] = {0};
+  std::map<nyx::host::GraphKey, std::pair<cudaGraphExec_t, long long>> graphs;  // graph, kernels in it
+  // counters and profiling
+  long long launches = 0;
+  bool profiling = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_fill, ev_adv;
+};
+
+
+namespace nyx {
+namespace host {
+
+// Ghost fill of a level field, one advance, and the CFL reduction of one
+// plan (all enqueued on the plan's stream; see nyx_api.cu).
+int plan_fill(nyx_plan *P, double *field, int ncomp);
+int plan_advance(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_new,
+                 const double *dt, const double *grav, double *dt_next);
+// Fold the CFL minimum of a state into the plan's accumulator (no finalise).
+void plan_estdt_accumulate(nyx_plan *P, const double *state, const double *a_dev,
+                           unsigned long long *acc);
+bool plan_capturing(nyx_plan *P);
+// Time the tile shapes once (autotuning plans only) on state[cur] of L, its
+// ghost cells filled here, with the step scalars a_dev[0], a_dev[1], *dt_dev.
+int plan_tune(nyx_plan *P, nyx_level *L, const double *a_dev, const double *dt_dev);
+
+}  // namespace host
+}  // namespace nyx

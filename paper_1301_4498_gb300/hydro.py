@@ -28,6 +28,8 @@ NYX_MIXED = 1
 NYX_PERSISTENT = 0
 NYX_PER_BOX = 1
 NOALLOC_MAX_BOXES = 4096  # NYX_NOALLOC_MAX_BOXES of include/nyx_hydro.h
+NYX_AMR_GHOSTS = 0
+NYX_AMR_ALL = 1
 
 _lib = None
 
@@ -57,7 +59,7 @@ class NyxParams(C.Structure):
                 ("small_pres", C.c_double), ("eta_de", C.c_double),
                 ("riemann_max_iter", C.c_int), ("riemann_tol", C.c_double),
                 ("precision", C.c_int), ("grav_corrector", C.c_int), ("batching", C.c_int),
-                ("autotune", C.c_int), ("keep_fluxes", C.c_int)]
+                ("autotune", C.c_int), ("keep_fluxes", C.c_int), ("coarse_fine", C.c_int)]
 
 
 class NyxLevel(C.Structure):
@@ -108,6 +110,18 @@ def load_library(path: str | None = None):
     L.nyx_hydro_counters_read.argtypes = [vp, C.c_int, C.POINTER(NyxCounters)]
     L.nyx_hydro_estdt_noalloc.argtypes = [C.POINTER(NyxLevelDesc), C.POINTER(NyxParams), vp, vp,
                                           vp, vp]
+    L.nyx_amr_create.argtypes = [vp, vp, C.POINTER(vp)]
+    L.nyx_amr_interp.argtypes = [vp, vp, vp, C.c_int, C.c_int]
+    L.nyx_amr_reflux.argtypes = [vp, vp]
+    L.nyx_amr_average_down.argtypes = [vp, vp, vp, C.c_int]
+    L.nyx_amr_estdt.argtypes = [vp, C.POINTER(NyxLevel), C.POINTER(NyxLevel), vp, vp]
+    L.nyx_amr_step.argtypes = [vp, C.POINTER(NyxLevel), C.POINTER(NyxLevel), vp, vp, vp, vp]
+    L.nyx_amr_run.argtypes = [vp, C.POINTER(NyxLevel), C.POINTER(NyxLevel), vp, vp, C.c_int,
+                              C.c_int, C.c_int]
+    L.nyx_amr_destroy.argtypes = [vp]
+    for name in ("nyx_amr_create", "nyx_amr_interp", "nyx_amr_reflux", "nyx_amr_average_down",
+                 "nyx_amr_estdt", "nyx_amr_step", "nyx_amr_run", "nyx_amr_destroy"):
+        getattr(L, name).restype = C.c_int
     for name in ("nyx_hydro_plan", "nyx_hydro_layout", "nyx_hydro_fill", "nyx_hydro_estdt",
                  "nyx_hydro_advance", "nyx_hydro_run", "nyx_hydro_fluxes", "nyx_hydro_step_host",
                  "nyx_hydro_status", "nyx_plan_destroy", "nyx_hydro_tile_shape",
@@ -365,6 +379,72 @@ def estdt_noalloc(spec, state, a_dev, dt_dev, stream=None, **params):
         stream = torch.cuda.current_stream().cuda_stream
     _check(load_library().nyx_hydro_estdt_noalloc(C.byref(desc), C.byref(p), _ptr(state),
                                                    _ptr(a_dev), _ptr(dt_dev), C.c_void_p(stream)))
+
+
+class Amr:
+    """A fine plan coupled to the coarse plan it refines by 2 (nyx_amr_*):
+    fine ghost cells from the coarse level, reflux, average down, the
+    shared CFL step and the two-level step.  Both plans must share a stream
+    (pass the coarse plan's ``torch_stream`` to the fine Plan), keep fluxes,
+    and the fine plan must be made with coarse_fine=1."""
+
+    def __init__(self, coarse: "Plan", fine: "Plan"):
+        self.lib = load_library()
+        self.coarse, self.fine = coarse, fine
+        h = C.c_void_p()
+        _check(self.lib.nyx_amr_create(coarse.h, fine.h, C.byref(h)))
+        self.h = h
+
+    def ordered(self):
+        return _Ordered(self.coarse)
+
+    def interp(self, coarse_field, fine_field, ncomp, region="ghosts"):
+        r = NYX_AMR_ALL if region == "all" else NYX_AMR_GHOSTS
+        with self.ordered():
+            _check(self.lib.nyx_amr_interp(self.h, _ptr(coarse_field), _ptr(fine_field), ncomp, r))
+
+    def reflux(self, coarse_new):
+        with self.ordered():
+            _check(self.lib.nyx_amr_reflux(self.h, _ptr(coarse_new)))
+
+    def average_down(self, fine_field, coarse_field, ncomp):
+        with self.ordered():
+            _check(self.lib.nyx_amr_average_down(self.h, _ptr(fine_field), _ptr(coarse_field),
+                                                 ncomp))
+
+    def estdt(self, coarse_level, fine_level, a_dev, dt_dev):
+        with self.ordered():
+            _check(self.lib.nyx_amr_estdt(self.h, C.byref(coarse_level.c()),
+                                          C.byref(fine_level.c()), _ptr(a_dev), _ptr(dt_dev)))
+
+    def step(self, coarse_level, fine_level, a_old, a_new, dt, dt_next=None):
+        cc, cf = coarse_level.c(), fine_level.c()
+        with self.ordered():
+            _check(self.lib.nyx_amr_step(self.h, C.byref(cc), C.byref(cf), _ptr(a_old),
+                                         _ptr(a_new), _ptr(dt), _ptr(dt_next)))
+        coarse_level.sync_from_c()
+        fine_level.sync_from_c()
+
+    def run(self, coarse_level, fine_level, a_dev, dt_dev, nsteps, compute_dt0=True,
+            use_graph=True):
+        cc, cf = coarse_level.c(), fine_level.c()
+        with self.ordered():
+            _check(self.lib.nyx_amr_run(self.h, C.byref(cc), C.byref(cf), _ptr(a_dev),
+                                        _ptr(dt_dev), nsteps, 1 if compute_dt0 else 0,
+                                        1 if use_graph else 0))
+        coarse_level.sync_from_c()
+        fine_level.sync_from_c()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.nyx_amr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def make_level(plan, states, grav=None):
