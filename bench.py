@@ -81,6 +81,12 @@ def make_workload(name: str, sample_only: bool = False):
         return W.comoving_box(n=256, sigma=1.0, seed=4, nsteps=50, mixed=True)
     if name == "sod":
         return W.sod()
+    if name == "amr":  # the large level with its 10% refined boxes coupled (ratio 2)
+        if sample_only:
+            return W.amr_level(n=64, box=32, nfine=1, nsteps=100, a0=1.0 / 51, aN=1.0 / 31)
+        return W.amr_large(nsteps=100)
+    if name == "amr128":  # the same structure on a 128^3 domain (profiling case)
+        return W.amr_large(n=128, box=32, nfine=6, nsteps=100)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -386,6 +392,253 @@ def run_ours(args, w):
     plan.close()
 
 
+# ---------------------------------------------------------------------- two levels
+
+# Algorithmic bytes of the coupling kernels: interpolation writes the 6
+# doubles of a fine ghost cell (the coarse cells it reads are shared by 8 fine
+# cells: 6 more bytes); reflux reads 4 fine and 1 coarse flux of 6 doubles and
+# reads and writes the coarse cell (336 B per coarse face); average down reads
+# 8 fine cells and writes one coarse cell (432 B per coarse cell).
+AMR_BYTES = {"interp": 54, "reflux": 336, "avgdown": 432}
+
+
+def oracle_amr_sample(w, budget_s=12.0):
+    """Time the FP64 CPU oracle's two-level step on a bounded sample: a
+    64^3 periodic coarse level (8 boxes of 32^3) with one of them refined by
+    2 (the large coupled level's box sizes), steps until the budget."""
+    import oracle
+    cw = w.coarse
+    P = oracle.OracleParams(gamma=cw.gamma, cfl=cw.cfl)
+    cs = [s.copy() for s in cw.state]
+    oracle.fill_ghosts(cw.level, cs)
+    fs = oracle.amr_interp(cw.level, cs, w.fine,
+                           [np.zeros(w.fine.shape(b, 6)) for b in range(w.fine.nbox)], "all")
+    cg = [g.copy() for g in cw.grav]
+    oracle.fill_ghosts(cw.level, cg)
+    fg = oracle.amr_interp(cw.level, cg, w.fine,
+                           [np.zeros(w.fine.shape(b, 3)) for b in range(w.fine.nbox)], "all")
+    cells = cw.level.valid_cells() + w.fine.valid_cells()
+    a0, a1 = float(cw.a_sched[0]), float(cw.a_sched[1])
+    elapsed, steps = 0.0, 0
+    while elapsed < budget_s:
+        t0 = time.perf_counter()
+        dt = oracle.amr_estdt(cw.level, w.fine, P, cs, fs, a0)
+        cs, fs, _, _ = oracle.amr_step(cw.level, w.fine, P, cs, fs, cg, fg, a_old=a0, a_new=a1,
+                                       dt=dt)
+        elapsed += time.perf_counter() - t0
+        steps += 1
+    return {"value": cells * steps / elapsed, "unit": "zone-updates/s", "cores": os.cpu_count(),
+            "kind": "oracle", "elapsed_s": elapsed / steps,
+            "sample": f"{steps} two-level step(s) of a 64^3 coarse level (8 boxes of 32^3) with one "
+                      f"box refined by 2 ({cells} cells), FP64 oracle, OpenMP on all host cores; "
+                      f"{elapsed:.1f} s"}
+
+
+def run_reference_amr(args, w):
+    ws, rank, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    per = []
+    info = None
+    for s in range(args.warmup + args.steps):
+        r = oracle_amr_sample(w, budget_s=args.ref_budget)
+        if s >= args.warmup:
+            per.append(r)
+        info = r
+    value = statistics.median(x["value"] for x in per)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "zone-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.median(x["elapsed_s"] for x in per) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "level": w.name, "sample": info["sample"]},
+        "cpu_baseline": {"value": value, "unit": "zone-updates/s", "cores": info["cores"],
+                         "kind": "oracle", "sample": info["sample"]},
+        "e2e": {"value": value, "unit": "zone-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def run_amr(args, aw):
+    """Two-level steps (coarse advance, fine ghosts from the coarse level,
+    fine advance, reflux, average down, shared CFL dt) of a coupled
+    hierarchy; zone-updates count the valid cells of both levels."""
+    import torch
+    from paper_1301_4498_gb300 import hydro as H
+    ws, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    peaks, peak_src = load_peaks()
+    K, Wm = args.steps, args.warmup
+    cw = aw.coarse
+    cells_c, cells_f = cw.level.valid_cells(), aw.fine.valid_cells()
+    cells = cells_c + cells_f
+    kw = dict(gamma=cw.gamma, cfl=cw.cfl, precision=args.precision, batching="persistent",
+              autotune=1 if args.autotune else 0, keep_fluxes=args.keep_fluxes)
+    cp = H.Plan(cw.level, **kw)
+    fp = H.Plan(aw.fine, stream=cp.torch_stream, coarse_fine=1, **kw)
+    if args.tile_shape >= 0:
+        cp.set_tile_shape(args.tile_shape)
+        fp.set_tile_shape(args.tile_shape)
+    amr = H.Amr(cp, fp)
+    lc = H.make_level(cp, cw.state, cw.grav)
+    cp.fill(lc.current, 6)
+    fs0 = fp.empty_field(6)
+    amr.interp(lc.current, fs0, 6, "all")       # newly refined data: interpolated (Sec. 4.1)
+    fg = fp.empty_field(3)
+    amr.interp(lc.grav, fg, 3, "all")
+    lf = H.Level(fs0, fp.empty_field(6), fg)
+    a_host = a_schedule_for(cw, max(K, Wm) + 1)
+    a = torch.tensor(a_host, dtype=torch.float64, device="cuda")
+    dt = torch.zeros(len(a_host), dtype=torch.float64, device="cuda")
+    stream = cp.torch_stream
+
+    amr.run(lc, lf, a, dt, Wm, compute_dt0=True, use_graph=False)
+    amr.run(lc, lf, a, dt, K, compute_dt0=True, use_graph=True)
+    torch.cuda.synchronize()
+    for p in (cp, fp):
+        rc, flags = p.status()
+        if rc != H.NYX_OK:
+            raise SystemExit(f"device status after warm-up: {rc} flags {flags}")
+    cp.counters(reset=True)
+    fp.counters(reset=True)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    amr.run(lc, lf, a, dt, K, compute_dt0=True, use_graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    launches = cp.counters(reset=True)["launches"] + fp.counters(reset=True)["launches"]
+    ms_max = max_over_ranks(ms, ws)
+    value = ws * cells * K / (ms_max / 1e3)
+
+    # the fused advances (both levels) and the coupling kernels, each timed
+    # with events on the plans' stream in eager steps
+    cp.profile(True)
+    fp.profile(True)
+    amr.run(lc, lf, a, dt, K, compute_dt0=True, use_graph=False)
+    pc, pf = cp.counters(reset=True), fp.counters(reset=True)
+    cp.profile(False)
+    fp.profile(False)
+    adv_c = pc["advance_ms"] / max(1, pc["timed_advances"])
+    adv_f = pf["advance_ms"] / max(1, pf["timed_advances"])
+
+    def timed(fn, reps=5):
+        fn()
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for _ in range(reps):
+            fn()
+        q1.record(stream)
+        torch.cuda.synchronize()
+        return q0.elapsed_time(q1) / reps
+
+    scratch_c = lc.state[1 - lc.cur].clone()
+    scratch_f = lf.current.clone()
+    t_interp = timed(lambda: amr.interp(lc.current, scratch_f, 6, "ghosts"))
+    t_reflux = timed(lambda: amr.reflux(scratch_c))
+    t_avg = timed(lambda: amr.average_down(lf.current, scratch_c, 6))
+    del scratch_c, scratch_f
+    nghost = sum(int(np.prod(np.array(aw.fine.shape(b, 1)[1:]))) - int(np.prod(aw.fine.extent(b)))
+                 for b in range(aw.fine.nbox))
+    nface = 0
+    for b in range(aw.fine.nbox):
+        hx, hy, hz = (e // 2 for e in aw.fine.extent(b))
+        nface += 2 * (hy * hz + hx * hz + hx * hy)   # coarse faces around the fine box
+    ncov = cells_f // 8
+    coupling = {}
+    for name, ms_k, units in (("interp", t_interp, nghost), ("reflux", t_reflux, nface),
+                              ("avgdown", t_avg, ncov)):
+        gbs = AMR_BYTES[name] * units / (ms_k / 1e3) / 1e9
+        coupling[name] = {"ms": ms_k, "units": units, "alg_bytes_per_unit": AMR_BYTES[name],
+                          "achieved_gbs": gbs, "frac_hbm": gbs / peaks["hbm_gbs"]}
+    adv_ms = adv_c + adv_f
+    flops = ALG_FLOPS_PER_ZONE[args.precision]
+    peak_tf = PEAK_FP32_TFLOPS if args.precision == "mixed" else PEAK_FP64_TFLOPS
+    achieved_tf = flops * cells / (adv_ms / 1e3) / 1e12
+    achieved_gbs = ALG_BYTES_PER_ZONE * cells / (adv_ms / 1e3) / 1e9
+    shape, (tx, ty) = cp.tile_shape()
+
+    e2e = None
+    if not args.no_e2e:
+        hc_in = lc.current.cpu().pin_memory()
+        hf_in = lf.current.cpu().pin_memory()
+        hc_out = torch.empty_like(hc_in).pin_memory()
+        hf_out = torch.empty_like(hf_in).pin_memory()
+        e2e_steps = max(1, min(3, K))
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for s in range(e2e_steps):
+                lc.current.copy_(hc_in, non_blocking=True)
+                lf.current.copy_(hf_in, non_blocking=True)
+                amr.step(lc, lf, a[s:s + 1], a[s + 1:s + 2], dt[s:s + 1], dt[s + 1:s + 2])
+                hc_out.copy_(lc.current, non_blocking=True)
+                hf_out.copy_(lf.current, non_blocking=True)
+            stream.synchronize()
+        t_e2e = max_over_ranks(time.perf_counter() - t0, ws)
+        nbytes = (hc_in.numel() + hf_in.numel()) * 8
+        e2e = {"value": ws * cells * e2e_steps / t_e2e, "unit": "zone-updates/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": e2e_steps}
+        del hc_in, hf_in, hc_out, hf_out
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = oracle_amr_sample(make_workload(args.workload, sample_only=True),
+                                budget_s=args.cpu_budget)
+        cpu.pop("elapsed_s", None)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "zone-updates/s", "n_gpus": ws,
+            "steps": K, "warmup": Wm, "ms_per_step": ms_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "level": aw.name, "valid_cells": cells,
+                       "coarse_cells": cells_c, "fine_cells": cells_f,
+                       "boxes": [cw.level.nbox, aw.fine.nbox], "precision": args.precision,
+                       "batching": "persistent + CUDA graph, two levels, no subcycling",
+                       "keep_fluxes": args.keep_fluxes, "tile": [tx, ty],
+                       "l2": "inputs larger than L2 (state + gravity > 20 GB)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf,
+                         "unit": "TFLOP/s", "frac": achieved_tf / peak_tf, "traffic": None,
+                         "traffic_unit": "bytes per launch",
+                         "kernel": "fused advance of both levels", "kernel_ms": adv_ms,
+                         "alg_flops_per_zone": flops,
+                         "pipe": "fp32" if args.precision == "mixed" else "fp64",
+                         "peak_source": "unit counts x 2070 MHz"},
+            "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"],
+                             "unit": "GB/s", "frac": achieved_gbs / peaks["hbm_gbs"],
+                             "alg_bytes_per_zone": ALG_BYTES_PER_ZONE,
+                             "peak_source": f"hbm_gbs {peak_src}"},
+            "kernel_ms": {"advance_coarse": adv_c, "advance_fine": adv_f,
+                          "ghost_fill_coarse": pc["fill_ms"] / max(1, pc["timed_fills"]),
+                          "ghost_fill_fine": pf["fill_ms"] / max(1, pf["timed_fills"])},
+            "coupling": coupling,
+            "clocks": clk,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out), flush=True)
+    amr.close()
+    fp.close()
+    cp.close()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -394,7 +647,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="large",
                     choices=["large", "large128", "comoving128", "uneven512", "uneven64", "mixed256",
-                             "sod"])
+                             "sod", "amr", "amr128"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--tile-shape", type=int, default=-1,
@@ -404,6 +657,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--traffic-per-zone", type=float, default=0.0,
                     help="DRAM bytes per zone of the advance kernel from an ncu capture")
+    ap.add_argument("--keep-fluxes", type=int, default=1,
+                    help="two-level workloads: 1 keep every face's flux, 2 box faces only")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-budget", type=float, default=6.0)
     ap.add_argument("--ref-boxes", type=int, default=0)
@@ -411,7 +666,12 @@ def main(argv=None):
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     w = make_workload(args.workload, sample_only=args.impl == "reference")
-    if args.impl == "reference":
+    if isinstance(w, W.AmrWorkload):
+        if args.impl == "reference":
+            run_reference_amr(args, w)
+        else:
+            run_amr(args, w)
+    elif args.impl == "reference":
         run_reference(args, w)
     else:
         run_ours(args, w)

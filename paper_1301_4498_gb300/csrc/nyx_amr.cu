@@ -85,6 +85,9 @@ __device__ __forceinline__ double mc_slope_d(double sm, double s0, double sp) {
   return 0.0;
 }
 
+// One thread per coarse cell of the rectangle's footprint: the slopes and the
+// limiter factor of a coarse cell are formed once and give its (up to 8)
+// fine cells, each evaluated with the same expression as cell by cell.
 __global__ void k_amr_interp(const double *cf, double *ff, int ncomp, const BoxDev *cboxes,
                              const BoxDev *fboxes, const InterpRect *rects, int nrect) {
   for (int r = blockIdx.x; r < nrect; r += gridDim.x) {
@@ -94,24 +97,17 @@ __global__ void k_amr_interp(const double *cf, double *ff, int ncomp, const BoxD
     const double *C = cf + (long long)ncomp * bc.pref;
     double *F = ff + (long long)ncomp * bf.pref;
     const long long s1 = bc.N[0], s2 = (long long)bc.N[0] * bc.N[1];
-    const int n = R.ext[0] * R.ext[1] * R.ext[2];
-    for (int q = threadIdx.x; q < n; q += blockDim.x) {
-      const int i = q % R.ext[0];
-      const int u = q / R.ext[0];
-      const int j = u % R.ext[1];
-      const int k = u / R.ext[1];
-      const int f[3] = {R.flo[0] + i, R.flo[1] + j, R.flo[2] + k};
-      int ci[3], o[3];
+    int c0[3], ne[3];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const int rel = f[d] + R.base[d];
-        ci[d] = (rel >> 1) + R.coff[d];
-        o[d] = rel & 1;
-      }
-      const long long cid = cell_index(bc, ci[0], ci[1], ci[2]);
-      const long long fid = cell_index(bf, f[0], f[1], f[2]);
+    for (int d = 0; d < 3; ++d) {
+      c0[d] = (R.flo[d] + R.base[d]) >> 1;
+      ne[d] = ((R.flo[d] + R.ext[d] - 1 + R.base[d]) >> 1) - c0[d] + 1;
+    }
+    const int n = ne[0] * ne[1] * ne[2];
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+      const int cr[3] = {c0[0] + q % ne[0], c0[1] + (q / ne[0]) % ne[1], c0[2] + q / (ne[0] * ne[1])};
+      const long long cid = cell_index(bc, cr[0] + R.coff[0], cr[1] + R.coff[1], cr[2] + R.coff[2]);
       const long long st[3] = {1, s1, s2};
-      const double xo = o[0] ? 0.25 : -0.25, yo = o[1] ? 0.25 : -0.25, zo = o[2] ? 0.25 : -0.25;
       for (int c = 0; c < ncomp; ++c) {
         const double *u_ = C + c * bc.stride;
         const double uc = u_[cid];
@@ -131,7 +127,19 @@ __global__ void k_amr_interp(const double *cf, double *ff, int ncomp, const BoxD
           if (uc + dev > umax) alpha = fmin(alpha, (umax - uc) / dev);
           if (uc - dev < umin) alpha = fmin(alpha, (uc - umin) / dev);
         }
-        F[c * bf.stride + fid] = uc + alpha * (s[0] * xo + s[1] * yo + s[2] * zo);
+        double *o_ = F + c * bf.stride;
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+          const int f0 = 2 * cr[0] + (o & 1) - R.base[0];
+          const int f1 = 2 * cr[1] + ((o >> 1) & 1) - R.base[1];
+          const int f2 = 2 * cr[2] + (o >> 2) - R.base[2];
+          if (f0 < R.flo[0] || f0 >= R.flo[0] + R.ext[0] || f1 < R.flo[1] ||
+              f1 >= R.flo[1] + R.ext[1] || f2 < R.flo[2] || f2 >= R.flo[2] + R.ext[2])
+            continue;
+          const double xo = (o & 1) ? 0.25 : -0.25, yo = ((o >> 1) & 1) ? 0.25 : -0.25,
+                       zo = (o >> 2) ? 0.25 : -0.25;
+          o_[cell_index(bf, f0, f1, f2)] = uc + alpha * (s[0] * xo + s[1] * yo + s[2] * zo);
+        }
       }
     }
   }
