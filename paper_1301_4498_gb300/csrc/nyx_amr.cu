@@ -410,6 +410,52 @@ struct Builder {
   }
 };
 
+// Rectangles of at most about kChunk cells, so that small hierarchies still
+// give every SM work: interpolation rectangles are cut along z at coarse
+// cell boundaries (each coarse cell stays in one piece), face and average
+// rectangles along their slowest axis.
+constexpr int kChunk = 4096;
+
+void split_interp(const InterpRect &R, std::vector<InterpRect> &out) {
+  const long long plane = (long long)R.ext[0] * R.ext[1];
+  int step = (int)std::max<long long>(2, kChunk / std::max<long long>(1, plane)) & ~1;
+  int z = R.flo[2];
+  const int zend = R.flo[2] + R.ext[2];
+  while (z < zend) {
+    // the first piece ends on a coarse boundary: (z + base) even after it
+    int e = std::min(zend, z + step);
+    if (e < zend && ((e + R.base[2]) & 1)) ++e;
+    InterpRect P = R;
+    P.flo[2] = z;
+    P.ext[2] = e - z;
+    out.push_back(P);
+    z = e;
+  }
+}
+
+void split_face(const FaceRect &R, std::vector<FaceRect> &out) {
+  const int t2 = (R.d == 2) ? 1 : 2;
+  const int step = std::max(1, kChunk / std::max(1, R.ext[0]));
+  for (int a = 0; a < R.ext[1]; a += step) {
+    FaceRect P = R;
+    P.plo[t2] = R.plo[t2] + a;
+    P.ext[1] = std::min(step, R.ext[1] - a);
+    P.ft0[1] = R.ft0[1] + 2 * a;
+    out.push_back(P);
+  }
+}
+
+void split_avg(const AvgRect &R, std::vector<AvgRect> &out) {
+  const int step = std::max(1, kChunk / std::max(1, R.ext[0] * R.ext[1]));
+  for (int a = 0; a < R.ext[2]; a += step) {
+    AvgRect P = R;
+    P.clo[2] = R.clo[2] + a;
+    P.ext[2] = std::min(step, R.ext[2] - a);
+    P.flo[2] = R.flo[2] + 2 * a;
+    out.push_back(P);
+  }
+}
+
 int build_tables(nyx_amr *A) {
   const nyx_plan &C = *A->C, &F = *A->F;
   Builder B(C, F);
@@ -499,6 +545,19 @@ int build_tables(nyx_amr *A) {
       }
     }
   }
+  std::vector<InterpRect> ig2, ia2;
+  for (const InterpRect &R : ig) split_interp(R, ig2);
+  for (const InterpRect &R : ia) split_interp(R, ia2);
+  ig.swap(ig2);
+  ia.swap(ia2);
+  for (int o = 0; o < 6; ++o) {
+    std::vector<FaceRect> f2;
+    for (const FaceRect &R : face[o]) split_face(R, f2);
+    face[o].swap(f2);
+  }
+  std::vector<AvgRect> avg2;
+  for (const AvgRect &R : avg) split_avg(R, avg2);
+  avg.swap(avg2);
   int rc;
   if ((rc = upload(ig, &A->d_ig))) return rc;
   if ((rc = upload(ia, &A->d_ia))) return rc;
