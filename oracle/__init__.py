@@ -53,7 +53,8 @@ class _Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("small_dens", C.c_double),
                 ("small_pres", C.c_double), ("eta_de", C.c_double),
                 ("riemann_max_iter", C.c_int), ("riemann_tol", C.c_double),
-                ("grav_corrector", C.c_int), ("dual_energy_sync", C.c_int)]
+                ("grav_corrector", C.c_int), ("dual_energy_sync", C.c_int),
+                ("grav_energy", C.c_int)]
 
 
 class _Level(C.Structure):
@@ -81,11 +82,12 @@ class OracleParams:
     riemann_tol: float = 1e-10
     grav_corrector: int = 1
     dual_energy_sync: int = 1
+    grav_energy: int = 0       # Sec. 3.2: 0 rho U . g in the energy; 1 the kinetic-energy change
 
     def _c(self) -> _Params:
         return _Params(self.gamma, self.cfl, self.small_dens, self.small_pres, self.eta_de,
                        self.riemann_max_iter, self.riemann_tol, self.grav_corrector,
-                       self.dual_energy_sync)
+                       self.dual_energy_sync, self.grav_energy)
 
 
 def load(path: str):
@@ -108,6 +110,10 @@ def load(path: str):
         L.orc_riemann_counts.restype = None
         L.orc_trace_line.argtypes = [C.POINTER(_Params), C.c_int, dp, dp, C.c_double,
                                      C.c_double, C.c_double, C.c_int, dp, dp, dp, dp]
+        L.orc_correct.argtypes = [C.POINTER(_Level), C.POINTER(_Params), C.POINTER(dp),
+                                  C.POINTER(dp), C.POINTER(dp), C.POINTER(dp), C.c_double,
+                                  C.c_double, C.c_double, C.POINTER(_Stats)]
+        L.orc_correct.restype = C.c_int
         L.orc_amr_check.argtypes = [C.POINTER(_Level), C.POINTER(_Level)]
         L.orc_amr_check.restype = C.c_int
         L.orc_amr_interp.argtypes = [C.POINTER(_Level), C.c_int, C.POINTER(dp), C.POINTER(_Level),
@@ -220,6 +226,33 @@ def advance(lev, params: OracleParams, states, grav=None, *, a_old=1.0, a_new=1.
     if rc == -1:
         raise ValueError("oracle advance: invalid level or ghost fill failure")
     return sout, stats, flux
+
+
+def predict(lev, params: OracleParams, states, grav=None, *, a_old, a_new, dt, fill_ghosts=True):
+    """Step 2 alone: the advance without the gravity corrector and without
+    the dual-energy sync (the predictor U^{n+1,*})."""
+    import dataclasses
+    p = dataclasses.replace(params, grav_corrector=0, dual_energy_sync=0)
+    out, st, _ = advance(lev, p, states, grav, a_old=a_old, a_new=a_new, dt=dt,
+                         fill_ghosts=fill_ghosts)
+    return out, st
+
+
+def correct(lev, params: OracleParams, old, pred, g_old=None, g_new=None, *, a_old, a_new, dt):
+    """Step 6 alone (Sec. 3.6): gravity corrector with g^n and g^{n+1}, then
+    the dual-energy sync (if params.dual_energy_sync), applied to a copy of
+    the predictor.  Returns (new_states, stats)."""
+    cl, keep = _level(lev)
+    o = [np.ascontiguousarray(a, dtype=np.float64) for a in old]
+    out = [np.array(a, dtype=np.float64, order="C", copy=True) for a in pred]
+    go = None if g_old is None else [np.ascontiguousarray(a, dtype=np.float64) for a in g_old]
+    gn = None if g_new is None else [np.ascontiguousarray(a, dtype=np.float64) for a in g_new]
+    st = _Stats()
+    p = params._c()
+    rc = lib().orc_correct(C.byref(cl), C.byref(p), _ptrs(o), _ptrs(out),
+                           None if go is None else _ptrs(go), None if gn is None else _ptrs(gn),
+                           a_old, a_new, dt, C.byref(st))
+    return out, dict(floor_e=st.floor_e, use_e=st.use_e, bad=st.bad, rc=rc)
 
 
 def estdt(lev, params: OracleParams, states, a: float) -> float:

@@ -492,6 +492,57 @@ static void primitives(const eos_t *E, const double *S, size_t vol, size_t id, d
 static double *alloc_arr(size_t n) { return (double *)calloc(n, sizeof(double)); }
 
 /* One box, Steps 2 and 6 of the single-level algorithm (Sec. 3.6). */
+/* Scalars of one step (Sec. 2.2, 3.6) used by the corrector. */
+typedef struct {
+  double a_old, a_new, dt, hdt, ian, ian2, eta_de, efloor;
+} step_k;
+
+/* Step 6 for one cell: the gravity corrector U^{n+1} = U^{n+1,*} + dt/2
+ * (S_g^{n+1,*} - S_g^n) with g_old at t^n and g_new at t^{n+1} (when
+ * P->grav_corrector), then the dual-energy synchronisation (when
+ * P->dual_energy_sync).  rho, m: state at t^n; rho_s, ms, rE_s, re_s: the
+ * predictor.  out = (rho, m_x, m_y, m_z, rhoE, rhoe) at t^{n+1}. */
+static void finish_cell(const orc_params *P, const step_k *s, double rho, const double m[3],
+                        const double go[3], const double gn[3], double rho_s, const double ms[3],
+                        double rE_s, double re_s, double out[6], long long *n_use_e,
+                        long long *n_floor) {
+  double mn[3];
+  double rEn = rE_s;
+  if (P->grav_corrector) {
+    for (int c = 0; c < 3; ++c) mn[c] = ms[c] + s->hdt * (rho_s * gn[c] - rho * go[c]) * s->ian;
+    if (P->grav_energy) {
+      double ks = ms[0] * ms[0] + ms[1] * ms[1] + ms[2] * ms[2];
+      double kn = mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2];
+      rEn = rE_s + 0.5 * (kn - ks) / rho_s;
+    } else {
+      double mg = m[0] * go[0] + m[1] * go[1] + m[2] * go[2];
+      double msg = ms[0] * gn[0] + ms[1] * gn[1] + ms[2] * gn[2];
+      rEn = rE_s + s->hdt * (s->a_new * msg - s->a_old * mg) * s->ian2;
+    }
+  } else {
+    for (int c = 0; c < 3; ++c) mn[c] = ms[c];
+  }
+  double ren = re_s;
+  if (P->dual_energy_sync) {
+    double ke = 0.5 * (mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]) / rho_s;
+    if (rEn - ke > s->eta_de * rEn) {
+      ren = rEn - ke;
+    } else {
+      rEn = ren + ke;
+      (*n_use_e)++;
+    }
+    if (ren < s->efloor) {
+      ren = s->efloor;
+      rEn = ren + ke;
+      (*n_floor)++;
+    }
+  }
+  out[0] = rho_s;
+  for (int c = 0; c < 3; ++c) out[1 + c] = mn[c];
+  out[4] = rEn;
+  out[5] = ren;
+}
+
 static int advance_box(const eos_t *E, const orc_params *P, const int lo_[3], const int hi_[3],
                        int ng, const double dx[3], const double *S, double *Sn, const double *G,
                        double a_old, double a_new, double dt, double *flux_out[3],
@@ -700,6 +751,7 @@ static int advance_box(const eos_t *E, const orc_params *P, const int lo_[3], co
   const double expn = a_half * (a_new - a_old) * kappa;
   const double hdt = 0.5 * dt;
   const double efloor = P->small_pres * E->igm1;
+  const step_k sk = {a_old, a_new, dt, hdt, ian, ian2, P->eta_de, efloor};
   int vlo[3] = {0, 0, 0}, vhi[3] = {g.n[0] - 1, g.n[1] - 1, g.n[2] - 1};
   long long n_use_e = 0, n_floor = 0, n_bad = 0;
 #pragma omp parallel for collapse(2) schedule(static) reduction(+ : n_use_e, n_floor, n_bad)
@@ -732,35 +784,26 @@ static int advance_box(const eos_t *E, const orc_params *P, const int lo_[3], co
         double rho_s = rho - dtp * div[0];
         double ms[3];
         for (int c = 0; c < 3; ++c) ms[c] = (a_old * m[c] - dt * div[1 + c] + dt * rho * gv[c]) * ian;
-        double mg = m[0] * gv[0] + m[1] * gv[1] + m[2] * gv[2];
-        double rE_s = (ao2 * rE - ahdt * div[4] + dta * mg + expn * re) * ian2;
-        double re_s = (ao2 * re - ahdt * div[5] - ahdt * pdivu + expn * re) * ian2;
-        /* corrector: U^{n+1} = U^{n+1,*} + dt/2 (S_g^{n+1,*} - S_g^n) */
-        double mn[3];
-        double rEn = rE_s;
-        if (P->grav_corrector) {
-          for (int c = 0; c < 3; ++c) mn[c] = ms[c] + hdt * (rho_s * gv[c] - rho * gv[c]) * ian;
-          double msg = ms[0] * gv[0] + ms[1] * gv[1] + ms[2] * gv[2];
-          rEn = rE_s + hdt * (a_new * msg - a_old * mg) * ian2;
+        double rE_s;
+        if (P->grav_energy) {
+          /* Sec. 3.2, second alternative: the gravity part of the energy
+           * update is the change of the kinetic energy that the gravity part
+           * of the momentum update makes (at the new density) */
+          double mh[3];
+          for (int c = 0; c < 3; ++c) mh[c] = (a_old * m[c] - dt * div[1 + c]) * ian;
+          double kh = mh[0] * mh[0] + mh[1] * mh[1] + mh[2] * mh[2];
+          double ks = ms[0] * ms[0] + ms[1] * ms[1] + ms[2] * ms[2];
+          rE_s = (ao2 * rE - ahdt * div[4] + expn * re) * ian2 + 0.5 * (ks - kh) / rho_s;
         } else {
-          for (int c = 0; c < 3; ++c) mn[c] = ms[c];
+          double mg = m[0] * gv[0] + m[1] * gv[1] + m[2] * gv[2];
+          rE_s = (ao2 * rE - ahdt * div[4] + dta * mg + expn * re) * ian2;
         }
-        double ren = re_s;
-        /* dual-energy synchronisation */
-        if (P->dual_energy_sync) {
-          double ke = 0.5 * (mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]) / rho_s;
-          if (rEn - ke > P->eta_de * rEn) {
-            ren = rEn - ke;
-          } else {
-            rEn = ren + ke;
-            n_use_e++;
-          }
-          if (ren < efloor) {
-            ren = efloor;
-            rEn = ren + ke;
-            n_floor++;
-          }
-        }
+        double re_s = (ao2 * re - ahdt * div[5] - ahdt * pdivu + expn * re) * ian2;
+        /* corrector (Step 6) and dual-energy synchronisation */
+        double out[6];
+        finish_cell(P, &sk, rho, m, gv, gv, rho_s, ms, rE_s, re_s, out, &n_use_e, &n_floor);
+        const double rEn = out[4], ren = out[5];
+        double mn[3] = {out[1], out[2], out[3]};
         if (!(rho_s > 0.0) || !isfinite(rho_s) || !isfinite(rEn) || !isfinite(ren)) n_bad++;
         Sn[id] = rho_s;
         for (int c = 0; c < 3; ++c) Sn[(1 + c) * V + id] = mn[c];
@@ -811,6 +854,51 @@ int orc_advance(const orc_level *L, const orc_params *P, double *const *state_in
     if (r) rc = r;
   }
   return rc;
+}
+
+/* Step 6 alone (corrector with g^{n+1}, then the sync), see the header. */
+int orc_correct(const orc_level *L, const orc_params *P, double *const *old,
+                double *const *pred, double *const *g_old, double *const *g_new, double a_old,
+                double a_new, double dt, orc_stats *st) {
+  eos_t E = make_eos(P);
+  orc_params Pc = *P;
+  Pc.grav_corrector = 1;
+  const double an2 = a_new * a_new;
+  const step_k sk = {a_old, a_new, dt, 0.5 * dt, 1.0 / a_new, 1.0 / an2, P->eta_de,
+                     P->small_pres * E.igm1};
+  long long n_use_e = 0, n_floor = 0, n_bad = 0;
+  for (int b = 0; b < L->nbox; ++b) {
+    geom_t g = make_geom(L->lo + 3 * b, L->hi + 3 * b, L->ng);
+    const size_t V = g.vol;
+    const double *S = old[b];
+    double *Sp = pred[b];
+    const double *Go = g_old ? g_old[b] : NULL, *Gn = g_new ? g_new[b] : NULL;
+#pragma omp parallel for collapse(2) schedule(static) reduction(+ : n_use_e, n_floor, n_bad)
+    for (int k = 0; k < g.n[2]; ++k)
+      for (int j = 0; j < g.n[1]; ++j)
+        for (int i = 0; i < g.n[0]; ++i) {
+          size_t id = gidx(&g, i, j, k);
+          double m[3] = {S[V + id], S[2 * V + id], S[3 * V + id]};
+          double ms[3] = {Sp[V + id], Sp[2 * V + id], Sp[3 * V + id]};
+          double go[3] = {0.0, 0.0, 0.0}, gn[3] = {0.0, 0.0, 0.0};
+          for (int c = 0; c < 3; ++c) {
+            if (Go) go[c] = Go[c * V + id];
+            if (Gn) gn[c] = Gn[c * V + id];
+          }
+          double out[6];
+          finish_cell(&Pc, &sk, S[id], m, go, gn, Sp[id], ms, Sp[4 * V + id], Sp[5 * V + id], out,
+                      &n_use_e, &n_floor);
+          if (!(out[0] > 0.0) || !isfinite(out[0]) || !isfinite(out[4]) || !isfinite(out[5]))
+            n_bad++;
+          for (int c = 0; c < 6; ++c) Sp[c * V + id] = out[c];
+        }
+  }
+  if (st) {
+    st->use_e += n_use_e;
+    st->floor_e += n_floor;
+    st->bad += n_bad;
+  }
+  return n_bad ? -3 : 0;
 }
 
 /* CFL time step, Sec. 3.5: sigma * min over cells and directions of

@@ -42,6 +42,9 @@ typedef struct {
   double riemann_tol;    /* relative pressure convergence tolerance */
   int grav_corrector;    /* 1: apply the Step 6 gravity corrector */
   int dual_energy_sync;  /* 1: apply the Step 6 e/E synchronisation */
+  int grav_energy;       /* S_g in the total energy (Sec. 3.2): 0 the product of the
+                            cell-centred momentum and g; 1 the change of the kinetic
+                            energy that the momentum's gravity update makes */
 } orc_params;
 
 typedef struct {
@@ -74,6 +77,17 @@ int orc_advance(const orc_level *lev, const orc_params *p, double *const *state_
                 double *const *state_out, double *const *grav, double a_old,
                 double a_new, double dt, int fill_ghosts, double *const *flux_out,
                 orc_stats *stats);
+
+/* Step 6 on its own, for a gravity field recomputed at t^{n+1} (Sec. 3.6:
+ * Step 4 solves for g^{n+1} from the predicted density): pred holds the
+ * predictor of orc_advance run with grav_corrector = 0 and
+ * dual_energy_sync = 0 (valid cells); old the state at t^n.  The corrector
+ * with g_old at t^n and g_new at t^{n+1}, then the dual-energy sync (when
+ * p->dual_energy_sync), is applied to pred in place.  g_old / g_new may be
+ * NULL (zero).  With g_new = g_old this is the corrector of orc_advance. */
+int orc_correct(const orc_level *lev, const orc_params *p, double *const *old,
+                double *const *pred, double *const *g_old, double *const *g_new, double a_old,
+                double a_new, double dt, orc_stats *stats);
 
 /* CFL time step over valid cells at scale factor a (Sec. 3.5). */
 double orc_estdt(const orc_level *lev, const orc_params *p, double *const *state, double a);

@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 import test_oracle_amr as ta
+import test_oracle_gravity as tg
 import test_oracle_ppm as tp
 import test_oracle_riemann as tr
 import test_oracle_step as ts
@@ -25,7 +26,7 @@ MUTANTS = {
                                     ts.test_internal_energy_tracks_total_minus_kinetic, ()),
     "gravity source sign in tracing": ("src->hdtp * g3[d]", "src->hdtp * (-g3[d])",
                                        tt.test_gravity_shifts_edge_velocity_by_half_step, ()),
-    "corrector without the 1/2": ("rEn = rE_s + hdt *", "rEn = rE_s + dt *",
+    "corrector without the 1/2": ("rEn = rE_s + s->hdt *", "rEn = rE_s + s->dt *",
                                   ts.test_uniform_gravity_at_rest, ()),
     "PPM interface coefficient": ("(d1 - d0) * SIXTH", "(d1 - d0) * 0.2",
                                   tp.test_unlimited_interface_exact_for_cubic_averages, ()),
@@ -65,8 +66,8 @@ MUTANTS = {
     "divergence reads the x neighbour": ("(Ff[d][c * V + id + g.st[d]] - Ff[d][c * V + id])",
                                          "(Ff[d][c * V + id + g.st[0]] - Ff[d][c * V + id])",
                                          ts.test_flux_export_reproduces_density_update, ()),
-    "dual-energy switch reversed": ("if (rEn - ke > P->eta_de * rEn)",
-                                    "if (rEn - ke < P->eta_de * rEn)",
+    "dual-energy switch reversed": ("if (rEn - ke > s->eta_de * rEn)",
+                                    "if (rEn - ke < s->eta_de * rEn)",
                                     ts.test_dual_energy_switch_direction, (5e-5, True)),
     "pressure from rho E instead of rho e": ("double p = E->gm1 * S[5 * vol + id];",
                                              "double p = E->gm1 * S[4 * vol + id];",
@@ -77,6 +78,16 @@ MUTANTS = {
     "periodic wrap off by one": ("x = dlo[d] + ((x - dlo[d]) % len + len) % len;",
                                  "x = dlo[d] + ((x - dlo[d] + 1) % len + len) % len;",
                                  ts.test_ghost_fill_periodic_outflow_and_tiles, ()),
+    # gravity source variants
+    "corrector uses g^n for the new density": ("(rho_s * gn[c] - rho * go[c])",
+                                                "(rho_s * go[c] - rho * go[c])",
+                                                tg.test_uniform_gas_at_rest_with_new_gravity, (0,)),
+    "option (ii) predictor sign": ("0.5 * (ks - kh) / rho_s", "0.5 * (kh - ks) / rho_s",
+                                   tg.test_option_two_leaves_internal_energy_to_the_hydro, ()),
+    "option (ii) corrector adds the whole kinetic energy": ("rEn = rE_s + 0.5 * (kn - ks) / rho_s;",
+                                                            "rEn = rE_s + 0.5 * kn / rho_s;",
+                                                            tg.test_uniform_gas_at_rest_with_new_gravity,
+                                                            (1,)),
     # coarse-fine coupling
     "reflux sign flipped": ("*U = high ? *U + corr : *U - corr;",
                             "*U = high ? *U - corr : *U + corr;",
