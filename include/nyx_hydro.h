@@ -100,6 +100,10 @@ typedef struct {
                               cells that no box of the level covers are left to
                               nyx_amr_interp (coarse data, Sec. 4.3 Step 2) instead
                               of being an error */
+  int grav_energy;         /* gravity source of the total energy (Sec. 3.2): 0 the
+                              product of the cell-centred momentum and g; 1 the change
+                              of the kinetic energy that the momentum's gravity update
+                              makes (leaves e = E - U^2/2 to the hydro update) */
 } nyx_hydro_params;
 
 typedef struct nyx_plan nyx_plan;
@@ -115,7 +119,8 @@ typedef struct {
 
 /* Fill *params with the defaults (gamma 5/3, cfl 0.5, small_dens 1e-10,
  * small_pres 1e-12, eta_de 1e-4, 12 iterations, tol 1e-10, FP64,
- * corrector on, persistent, autotune off, keep_fluxes off, coarse_fine off). */
+ * corrector on, persistent, autotune off, keep_fluxes off, coarse_fine off,
+ * grav_energy 0). */
 void nyx_hydro_default_params(nyx_hydro_params *params);
 
 /* Validate the level (Sec. 4.1: even positive extents, ng == 4, boxes of a
@@ -154,6 +159,27 @@ int nyx_hydro_estdt(nyx_plan *plan, const nyx_level *level, const double *a_dev,
 int nyx_hydro_advance(nyx_plan *plan, nyx_level *level, const double *a_old_dev,
                       const double *a_new_dev, const double *dt_dev, const double *grav_dev,
                       double *dt_next_dev);
+
+/* Step 2 alone (Sec. 3.6), for a caller that recomputes gravity at t^{n+1}
+ * (Step 4) before the corrector: ghost fill of state[cur], then
+ * state[1-cur] (valid cells) = the predictor U^{n+1,*} of state[cur] with
+ * grav_old (g^n; NULL: level->grav, NULL again: g = 0) -- the advance without
+ * the gravity corrector and without the dual-energy sync.  cur does not
+ * flip.  Scalars are device pointers. */
+int nyx_hydro_predict(nyx_plan *plan, nyx_level *level, const double *a_old_dev,
+                      const double *a_new_dev, const double *dt_dev, const double *grav_old_dev);
+
+/* Step 6 alone (Sec. 3.6): state[1-cur], a predictor from nyx_hydro_predict
+ * with the same scalars, gets the gravity corrector with g^n (grav_old_dev)
+ * and g^{n+1} (grav_new_dev) -- in the energy discretisation of the plan's
+ * grav_energy -- then the dual-energy sync, in place (FP64 for every plan);
+ * cur flips.  Gravity fields are device fields of 3 components (valid cells
+ * read; NULL = zero).  dt_next_dev (may be NULL) receives the CFL step of
+ * the new state at a_new.  With grav_new = grav_old the pair gives the
+ * result of nyx_hydro_advance (bitwise for FP64 plans). */
+int nyx_hydro_correct(nyx_plan *plan, nyx_level *level, const double *a_old_dev,
+                      const double *a_new_dev, const double *dt_dev, const double *grav_old_dev,
+                      const double *grav_new_dev, double *dt_next_dev);
 
 /* nsteps advances back to back.  a_dev holds a_0..a_nsteps; dt_dev holds
  * nsteps+1 scalars: dt_dev[0] is the first step's dt (computed here by

@@ -338,7 +338,7 @@ int do_estdt(nyx_plan *P, const double *state, const double *a_dev, double *dt_d
 int tune_shape(nyx_plan *P, const FusedArgs &base);
 
 int do_advance(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_new,
-               const double *dt, const double *grav, double *dt_next) {
+               const double *dt, const double *grav, double *dt_next, bool predict_only = false) {
   double *S = L->state[L->cur];
   double *Sn = L->state[1 - L->cur];
   const double *G = grav ? grav : L->grav;
@@ -354,7 +354,8 @@ int do_advance(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_n
       launch_staged_box(X, P->d_boxes + b, P->d_K, P->d_SC, P->d_BS + b, S + NCONS * X.pref,
                         G ? G + NGRAV * X.pref : nullptr, Sn + NCONS * X.pref, P->d_scratch,
                         P->Vmax, acc, P->d_status,
-                        P->d_flux ? P->d_flux + P->flux_off[b] : nullptr, P->stream);
+                        P->d_flux ? P->d_flux + P->flux_off[b] : nullptr, predict_only ? 1 : 0,
+                        P->stream);
       P->launches += P->d_flux ? 29 : 26;
     }
   } else {
@@ -371,6 +372,7 @@ int do_advance(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_n
     a.status = P->d_status;
     a.flux_keep = P->d_flux;
     a.flux_off = P->d_flux_off;
+    a.predict_only = predict_only ? 1 : 0;
     if (P->prm.autotune && !P->tuned) {
       int rc = tune_shape(P, a);
       if (rc) return rc;
@@ -390,6 +392,25 @@ int do_advance(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_n
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "advance launch");
   P->flux_valid = P->d_flux != nullptr;
+  if (!predict_only) L->cur = 1 - L->cur;
+  return NYX_OK;
+}
+
+// Step 6 alone: state[1-cur] (a predictor) corrected with g^n / g^{n+1},
+// synchronised; cur flips.
+int do_correct(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_new,
+               const double *dt, const double *g_old, const double *g_new, double *dt_next) {
+  launch_step_setup(P->d_K, a_old, a_new, dt, P->d_SC, P->d_boxes, P->nbox, P->d_BS, P->stream);
+  launch_correct(P->d_boxes, P->d_cell_pref, P->nbox, P->total_cells, P->d_K, P->d_SC,
+                 L->state[L->cur], L->state[1 - L->cur], g_old, g_new,
+                 dt_next ? P->d_dtacc : nullptr, P->d_status, P->stream);
+  P->launches += 2;
+  if (dt_next) {
+    launch_dt_finalize(P->d_K, P->d_dtacc, dt_next, P->stream);
+    P->launches += 1;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "corrector launch");
   L->cur = 1 - L->cur;
   return NYX_OK;
 }
@@ -534,6 +555,7 @@ void nyx_hydro_default_params(nyx_hydro_params *p) {
   p->autotune = 0;
   p->keep_fluxes = 0;
   p->coarse_fine = 0;
+  p->grav_energy = 0;
 }
 
 const char *nyx_last_error(void) { return g_err.c_str(); }
@@ -657,6 +679,7 @@ int nyx_hydro_plan(const nyx_level_desc *lev, const nyx_hydro_params *prm, void 
     K.efloor = prm->small_pres * K.igm1;
     K.max_iter = prm->riemann_max_iter;
     K.grav_corrector = prm->grav_corrector;
+    K.grav_energy = prm->grav_energy;
     TRYC(cudaMalloc(&P->d_K, sizeof(SchemeConsts)));
     TRYC(cudaMemcpy(P->d_K, &K, sizeof(SchemeConsts), cudaMemcpyHostToDevice));
     TRYC(cudaMalloc(&P->d_SC, sizeof(StepConsts)));
@@ -748,6 +771,23 @@ int nyx_hydro_advance(nyx_plan *P, nyx_level *L, const double *a_old, const doub
   if ((L->cur != 0 && L->cur != 1) || !L->state[0] || !L->state[1] || L->state[0] == L->state[1])
     return fail(NYX_EINVAL, "level needs two distinct state buffers and cur in {0,1}");
   return do_advance(P, L, a_old, a_new, dt, grav, dt_next);
+}
+
+int nyx_hydro_predict(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_new,
+                      const double *dt, const double *grav_old) {
+  if (!P || !L || !a_old || !a_new || !dt) return fail(NYX_EINVAL, "null argument");
+  if ((L->cur != 0 && L->cur != 1) || !L->state[0] || !L->state[1] || L->state[0] == L->state[1])
+    return fail(NYX_EINVAL, "level needs two distinct state buffers and cur in {0,1}");
+  return do_advance(P, L, a_old, a_new, dt, grav_old, nullptr, true);
+}
+
+int nyx_hydro_correct(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_new,
+                      const double *dt, const double *grav_old, const double *grav_new,
+                      double *dt_next) {
+  if (!P || !L || !a_old || !a_new || !dt) return fail(NYX_EINVAL, "null argument");
+  if ((L->cur != 0 && L->cur != 1) || !L->state[0] || !L->state[1] || L->state[0] == L->state[1])
+    return fail(NYX_EINVAL, "level needs two distinct state buffers and cur in {0,1}");
+  return do_correct(P, L, a_old, a_new, dt, grav_old, grav_new, dt_next);
 }
 
 int nyx_hydro_run(nyx_plan *P, nyx_level *L, const double *a_dev, double *dt_dev, int nsteps,

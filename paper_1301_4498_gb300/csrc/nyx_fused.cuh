@@ -27,6 +27,7 @@
 #include "nyx_internal.cuh"
 #include "nyx_kernels.h"
 #include "nyx_scheme.cuh"
+#include "nyx_finish.cuh"
 
 namespace NYX_NS {
 
@@ -144,7 +145,7 @@ __device__ __forceinline__ void update_cell(const nyx::SchemeConsts &k, const ny
                                             const R (&Fxp)[8], const R (&Fym)[8],
                                             const R (&Fyp)[8], const R (&Fzm)[8],
                                             const R (&Fzp)[8], double &dtmin, unsigned &flags,
-                                            bool want_dt) {
+                                            bool want_dt, bool full) {
   const long long bs = b.stride;
   double div[6];
 #pragma unroll
@@ -170,28 +171,13 @@ __device__ __forceinline__ void update_cell(const nyx::SchemeConsts &k, const ny
   const double ms0 = (sc.a_old * m0 - sc.dt * div[1] + sc.dt * rho * g0) * sc.ian;
   const double ms1 = (sc.a_old * m1 - sc.dt * div[2] + sc.dt * rho * g1) * sc.ian;
   const double ms2 = (sc.a_old * m2 - sc.dt * div[3] + sc.dt * rho * g2) * sc.ian;
-  const double mg = m0 * g0 + m1 * g1 + m2 * g2;
-  const double rE_s = (sc.ao2 * rE - sc.ahdt * div[4] + sc.dta * mg + sc.expn * re) * sc.ian2;
+  const double rE_s = nyx::predictor_energy(k, sc, rE, re, div[4], m0, m1, m2, g0, g1, g2, div[1],
+                                              div[2], div[3], rho_s, ms0, ms1, ms2);
   const double re_s = (sc.ao2 * re - sc.ahdt * div[5] - sc.ahdt * pdivu + sc.expn * re) * sc.ian2;
-  double mn0 = ms0, mn1 = ms1, mn2 = ms2, rEn = rE_s;
-  if (k.grav_corrector) {
-    mn0 = ms0 + sc.hdt * (rho_s * g0 - rho * g0) * sc.ian;
-    mn1 = ms1 + sc.hdt * (rho_s * g1 - rho * g1) * sc.ian;
-    mn2 = ms2 + sc.hdt * (rho_s * g2 - rho * g2) * sc.ian;
-    const double msg = ms0 * g0 + ms1 * g1 + ms2 * g2;
-    rEn = rE_s + sc.hdt * (sc.a_new * msg - sc.a_old * mg) * sc.ian2;
-  }
-  double ren = re_s;
-  const double ke = 0.5 * (mn0 * mn0 + mn1 * mn1 + mn2 * mn2) / rho_s;
-  if (rEn - ke > k.eta_de * rEn) {
-    ren = rEn - ke;
-  } else {
-    rEn = ren + ke;
-  }
-  if (ren < k.efloor) {
-    ren = k.efloor;
-    rEn = ren + ke;
-  }
+  double o6[6];
+  nyx::finish_cell(k, sc, rho, m0, m1, m2, g0, g1, g2, g0, g1, g2, rho_s, ms0, ms1, ms2, rE_s, re_s,
+                   k.grav_corrector && full, full, o6);
+  const double mn0 = o6[1], mn1 = o6[2], mn2 = o6[3], rEn = o6[4], ren = o6[5];
   if (!(rho_s > 0.0)) flags |= nyx::ST_NEGATIVE;
   if (!isfinite(rho_s) || !isfinite(rEn) || !isfinite(ren) || !isfinite(mn0) || !isfinite(mn1) ||
       !isfinite(mn2))
@@ -202,7 +188,7 @@ __device__ __forceinline__ void update_cell(const nyx::SchemeConsts &k, const ny
   Sn[3 * bs + id] = mn2;
   Sn[4 * bs + id] = rEn;
   Sn[5 * bs + id] = ren;
-  if (want_dt) {
+  if (want_dt && full) {
     // CFL step of the new state at a_new (Sec. 3.5), in the path's precision
     const R r = (R)rho_s;
     R p = (R)k.gm1 * (R)ren;
@@ -264,7 +250,7 @@ __device__ __forceinline__ void update_cell_mixed(
     const nyx::SchemeConsts &k, const nyx::StepConsts &sc, const nyx::BoxDev &b, const MixK &mk,
     const double *S, const double *G, double *Sn, long long id, const float (&Fxm)[8],
     const float (&Fxp)[8], const float (&Fym)[8], const float (&Fyp)[8], const float (&Fzm)[8],
-    const float (&Fzp)[8], float &dtmin, unsigned &flags, bool want_dt) {
+    const float (&Fzp)[8], float &dtmin, unsigned &flags, bool want_dt, bool full) {
   const long long bs = b.stride;
   double div[6];
 #pragma unroll
@@ -292,32 +278,51 @@ __device__ __forceinline__ void update_cell_mixed(
   const double ms0 = (sc.a_old * m0 - sc.dt * div[1] + dtrho * g0) * sc.ian;
   const double ms1 = (sc.a_old * m1 - sc.dt * div[2] + dtrho * g1) * sc.ian;
   const double ms2 = (sc.a_old * m2 - sc.dt * div[3] + dtrho * g2) * sc.ian;
-  const double mg = m0 * g0 + m1 * g1 + m2 * g2;
-  const double rE_s = (sc.ao2 * rE - sc.ahdt * div[4] + sc.dta * mg + sc.expn * re) * sc.ian2;
-  const double re_s = (sc.ao2 * re - sc.ahdt * (div[5] + pdivu) + sc.expn * re) * sc.ian2;
-  double mn0 = ms0, mn1 = ms1, mn2 = ms2, rEn = rE_s;
-  if (k.grav_corrector) {
-    const double cr = sc.hdt * (rho_s - rho) * sc.ian;
-    mn0 = ms0 + cr * g0;
-    mn1 = ms1 + cr * g1;
-    mn2 = ms2 + cr * g2;
-    const double msg = ms0 * g0 + ms1 * g1 + ms2 * g2;
-    rEn = rE_s + sc.hdt * (sc.a_new * msg - sc.a_old * mg) * sc.ian2;
-  }
   // 1/rho: FP32 reciprocal, one Newton step in FP64 (relative error ~1e-14)
   const float rho_f = d2f_rn(rho_s);
   double ir = f2d_exact(1.0f / rho_f);
   ir = ir * (2.0 - rho_s * ir);
-  const double ke = 0.5 * (mn0 * mn0 + mn1 * mn1 + mn2 * mn2) * ir;
-  double ren = re_s;
-  if (rEn - ke > k.eta_de * rEn) {
-    ren = rEn - ke;
+  const double mg = m0 * g0 + m1 * g1 + m2 * g2;
+  double rE_s;
+  if (k.grav_energy) {
+    // Sec. 3.2, second alternative: the kinetic-energy change of the gravity update
+    const double mh0 = (sc.a_old * m0 - sc.dt * div[1]) * sc.ian;
+    const double mh1 = (sc.a_old * m1 - sc.dt * div[2]) * sc.ian;
+    const double mh2 = (sc.a_old * m2 - sc.dt * div[3]) * sc.ian;
+    const double kh = mh0 * mh0 + mh1 * mh1 + mh2 * mh2;
+    const double ks = ms0 * ms0 + ms1 * ms1 + ms2 * ms2;
+    rE_s = (sc.ao2 * rE - sc.ahdt * div[4] + sc.expn * re) * sc.ian2 + 0.5 * (ks - kh) * ir;
   } else {
-    rEn = ren + ke;
+    rE_s = (sc.ao2 * rE - sc.ahdt * div[4] + sc.dta * mg + sc.expn * re) * sc.ian2;
   }
-  if (ren < k.efloor) {
-    ren = k.efloor;
-    rEn = ren + ke;
+  const double re_s = (sc.ao2 * re - sc.ahdt * (div[5] + pdivu) + sc.expn * re) * sc.ian2;
+  double mn0 = ms0, mn1 = ms1, mn2 = ms2, rEn = rE_s;
+  if (k.grav_corrector && full) {
+    const double cr = sc.hdt * (rho_s - rho) * sc.ian;
+    mn0 = ms0 + cr * g0;
+    mn1 = ms1 + cr * g1;
+    mn2 = ms2 + cr * g2;
+    if (k.grav_energy) {
+      const double ks = ms0 * ms0 + ms1 * ms1 + ms2 * ms2;
+      const double kn = mn0 * mn0 + mn1 * mn1 + mn2 * mn2;
+      rEn = rE_s + 0.5 * (kn - ks) * ir;
+    } else {
+      const double msg = ms0 * g0 + ms1 * g1 + ms2 * g2;
+      rEn = rE_s + sc.hdt * (sc.a_new * msg - sc.a_old * mg) * sc.ian2;
+    }
+  }
+  double ren = re_s;
+  if (full) {
+    const double ke = 0.5 * (mn0 * mn0 + mn1 * mn1 + mn2 * mn2) * ir;
+    if (rEn - ke > k.eta_de * rEn) {
+      ren = rEn - ke;
+    } else {
+      rEn = ren + ke;
+    }
+    if (ren < k.efloor) {
+      ren = k.efloor;
+      rEn = ren + ke;
+    }
   }
   if (!(rho_f > 0.0f)) flags |= nyx::ST_NEGATIVE;
   if (!finite_hi(rho_s) || !finite_hi(rEn) || !finite_hi(ren) || !finite_hi(mn0) ||
@@ -329,7 +334,7 @@ __device__ __forceinline__ void update_cell_mixed(
   Sn[3 * bs + id] = mn2;
   Sn[4 * bs + id] = rEn;
   Sn[5 * bs + id] = ren;
-  if (want_dt) {
+  if (want_dt && full) {
     const float irf = 1.0f / rho_f;
     float p = mk.gm1 * d2f_rn(ren);
     if (p < mk.small_pres) p = mk.small_pres;
@@ -631,11 +636,11 @@ __global__ void __launch_bounds__(FusedGeom<R, TX, TY>::NT, 1) k_fused(nyx::Fuse
         if constexpr (sizeof(R) == 4) {
           float dtf = __int_as_float(0x7f800000);
           update_cell_mixed(KK, sc, b, mixk, S, G, Sn, id, Fxm, Fxp, Fym, Fyp, Ffz_prev, Ffz, dtf,
-                            flags, a.dtacc != nullptr);
+                            flags, a.dtacc != nullptr, !a.predict_only);
           if ((double)dtf < dtmin) dtmin = (double)dtf;
         } else
           update_cell<R>(KK, sc, b, S, G, Sn, id, Fxm, Fxp, Fym, Fyp, Ffz_prev, Ffz, dtmin, flags,
-                         a.dtacc != nullptr);
+                         a.dtacc != nullptr, !a.predict_only);
         if (a.flux_keep) {
           double *fk = a.flux_keep + a.flux_off[w.box];
           const int nx = b.n[0], ny = b.n[1];

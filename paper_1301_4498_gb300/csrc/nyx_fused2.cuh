@@ -561,7 +561,7 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
           }
           const long long id = ucol + (long long)(p + 4) * ps;
           update_cell_mixed(KK, sc, b, mk, S, Gv, Sn, id, Fxm, Fxp, Fym, Fyp, Fzm, Fzp, dtmin,
-                            flags, a.dtacc != nullptr);
+                            flags, a.dtacc != nullptr, !a.predict_only);
           if (a.flux_keep)
             keep_fluxes(a.flux_keep + a.flux_off[w.box], b.n[0], b.n[1], nz, w.x0 + ui,
                         w.y0 + uj, p, Fxm, Fxp, Fym, Fyp, Fzm, Fzp);

@@ -33,6 +33,7 @@ struct SchemeConsts {
   double gamma, gm1, igm1, kshock, small_dens, small_pres, tol, eta_de, cfl, kappa, efloor;
   double tol_mixed;
   int max_iter, grav_corrector;
+  int grav_energy;  // S_g in the total energy: 0 rho U . g, 1 kinetic-energy change (Sec. 3.2)
 };
 
 // Scalars of one step, derived on the device from a_old, a_new, dt so that

@@ -33,7 +33,7 @@ void launch_staged_box(const BoxDev &b, const BoxDev *b_dev, const SchemeConsts 
                        const StepConsts *SC, const BoxStep *BSb, const double *Sbox,
                        const double *Gbox, double *Snbox, double *scratch, long long V,
                        unsigned long long *dtacc, unsigned *status, double *flux_keep,
-                       cudaStream_t st);
+                       int predict_only, cudaStream_t st);
 
 // Arguments of one launch of the fused persistent advance.
 struct FusedArgs {
@@ -51,6 +51,7 @@ struct FusedArgs {
   unsigned *status;
   double *flux_keep;              // final-flux store, or null
   const long long *flux_off;      // per-box offsets into flux_keep
+  int predict_only;               // 1: Step 2 only (no corrector, no dual-energy sync, no dt)
 };
 
 // Tile shapes of the fused kernel (columns per CTA in x and y).
@@ -66,6 +67,15 @@ int launch_fused(int precision, int shape, const FusedArgs &a, int grid, cudaStr
 int fused_max_grid(int precision, int shape);
 
 int launch_fused_f64(int shape, const FusedArgs &a, int grid, cudaStream_t st);
+
+// Step 6 alone over every valid cell of a level (FP64): the predictor in
+// Sp (6 components) is corrected in place with the state at t^n in S, g^n in
+// Go and g^{n+1} in Gn (either may be null: zero), then synchronised; the CFL
+// minimum of the result goes to dtacc (may be null).
+void launch_correct(const BoxDev *boxes, const long long *cell_pref, int nbox, long long total,
+                    const SchemeConsts *K, const StepConsts *SC, const double *S, double *Sp,
+                    const double *Go, const double *Gn, unsigned long long *dtacc,
+                    unsigned *status, cudaStream_t st);
 int launch_fused_mixed(int shape, const FusedArgs &a, int grid, cudaStream_t st);
 int max_grid_f64(int shape);
 int max_grid_mixed(int shape);

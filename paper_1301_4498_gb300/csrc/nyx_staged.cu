@@ -8,6 +8,7 @@
 #define NYX_NS nyx_f64
 #include "nyx_scheme.cuh"
 #include "nyx_internal.cuh"
+#include "nyx_finish.cuh"
 #include "nyx_kernels.h"
 
 namespace nyx {
@@ -216,7 +217,7 @@ __global__ void k_final(BoxDev b, const SchemeConsts *K, const BoxStep *BS, cons
 __global__ void k_update(BoxDev b, const SchemeConsts *K, const StepConsts *SC, const double *S,
                          const double *G, const double *F0, const double *F1, const double *F2,
                          double *Sn, long long V, Range r, unsigned long long *dtacc,
-                         unsigned *status, double *flux_keep) {
+                         unsigned *status, double *flux_keep, int predict_only) {
   const SchemeConsts k = *K;
   const StepConsts sc = *SC;
   const long long s0 = 1, s1 = b.N[0], s2 = (long long)b.N[0] * b.N[1];
@@ -255,31 +256,15 @@ __global__ void k_update(BoxDev b, const SchemeConsts *K, const StepConsts *SC, 
     const double ms0 = (sc.a_old * m0 - sc.dt * div[1] + sc.dt * rho * g0) * sc.ian;
     const double ms1 = (sc.a_old * m1 - sc.dt * div[2] + sc.dt * rho * g1) * sc.ian;
     const double ms2 = (sc.a_old * m2 - sc.dt * div[3] + sc.dt * rho * g2) * sc.ian;
-    const double mg = m0 * g0 + m1 * g1 + m2 * g2;
-    const double rE_s = (sc.ao2 * rE - sc.ahdt * div[4] + sc.dta * mg + sc.expn * re) * sc.ian2;
+    const double rE_s = predictor_energy(k, sc, rE, re, div[4], m0, m1, m2, g0, g1, g2, div[1],
+                                         div[2], div[3], rho_s, ms0, ms1, ms2);
     const double re_s =
         (sc.ao2 * re - sc.ahdt * div[5] - sc.ahdt * pdivu + sc.expn * re) * sc.ian2;
-    // corrector (Step 6): + dt/2 (S_g^{n+1,*} - S_g^n)
-    double mn0 = ms0, mn1 = ms1, mn2 = ms2, rEn = rE_s;
-    if (k.grav_corrector) {
-      mn0 = ms0 + sc.hdt * (rho_s * g0 - rho * g0) * sc.ian;
-      mn1 = ms1 + sc.hdt * (rho_s * g1 - rho * g1) * sc.ian;
-      mn2 = ms2 + sc.hdt * (rho_s * g2 - rho * g2) * sc.ian;
-      const double msg = ms0 * g0 + ms1 * g1 + ms2 * g2;
-      rEn = rE_s + sc.hdt * (sc.a_new * msg - sc.a_old * mg) * sc.ian2;
-    }
-    double ren = re_s;
-    // dual-energy synchronisation (Step 6)
-    const double ke = 0.5 * (mn0 * mn0 + mn1 * mn1 + mn2 * mn2) / rho_s;
-    if (rEn - ke > k.eta_de * rEn) {
-      ren = rEn - ke;
-    } else {
-      rEn = ren + ke;
-    }
-    if (ren < k.efloor) {
-      ren = k.efloor;
-      rEn = ren + ke;
-    }
+    // corrector (Step 6): + dt/2 (S_g^{n+1,*} - S_g^n), then the dual-energy sync
+    double o6[6];
+    finish_cell(k, sc, rho, m0, m1, m2, g0, g1, g2, g0, g1, g2, rho_s, ms0, ms1, ms2, rE_s, re_s,
+                k.grav_corrector && !predict_only, !predict_only, o6);
+    const double mn0 = o6[1], mn1 = o6[2], mn2 = o6[3], rEn = o6[4], ren = o6[5];
     if (!(rho_s > 0.0)) flags |= ST_NEGATIVE;
     if (!isfinite(rho_s) || !isfinite(rEn) || !isfinite(ren) || !isfinite(mn0) ||
         !isfinite(mn1) || !isfinite(mn2))
@@ -291,7 +276,7 @@ __global__ void k_update(BoxDev b, const SchemeConsts *K, const StepConsts *SC, 
     Sn[4 * bs + id] = rEn;
     Sn[5 * bs + id] = ren;
     // CFL step of the new state at a_new (Sec. 3.5)
-    if (dtacc) {
+    if (dtacc && !predict_only) {
       double p = k.gm1 * ren;
       if (p < k.small_pres) p = k.small_pres;
       const double c = sqrt(k.gamma * p / rho_s);
@@ -309,6 +294,80 @@ __global__ void k_update(BoxDev b, const SchemeConsts *K, const StepConsts *SC, 
       if (v < local_min) local_min = v;
     }
     if ((threadIdx.x & 31) == 0) atomic_min_pos(dtacc, local_min);
+  }
+  if (flags) atomicOr(status, flags);
+}
+
+// ------------------------------------------------------------ Step 6 alone
+// The corrector with g^n and g^{n+1} and the dual-energy sync over every
+// valid cell of the level, in place on the predictor; one thread per cell,
+// cells of a box in x-fastest order (coalesced), the box found by a binary
+// search of the cell offsets.  CFL minimum of the result as in k_update.
+__global__ void k_correct(const BoxDev *boxes, const long long *cell_pref, int nbox,
+                          long long total, const SchemeConsts *K, const StepConsts *SC,
+                          const double *S, double *Sp, const double *Go, const double *Gn,
+                          unsigned long long *dtacc, unsigned *status) {
+  const SchemeConsts k = *K;
+  const StepConsts sc = *SC;
+  double local_min = __longlong_as_double(0x7ff0000000000000LL);
+  unsigned flags = 0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nbox - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (cell_pref[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const BoxDev b = boxes[lo];
+    const long long f = t - cell_pref[lo];
+    const int i = (int)(f % b.n[0]);
+    const long long u = f / b.n[0];
+    const int j = (int)(u % b.n[1]);
+    const int kk = (int)(u / b.n[1]);
+    const long long bs = b.stride;
+    const long long id = NCONS * b.pref + cell_index(b, i, j, kk);
+    const long long ig = NGRAV * b.pref + cell_index(b, i, j, kk);
+    double go0 = 0.0, go1 = 0.0, go2 = 0.0, gn0 = 0.0, gn1 = 0.0, gn2 = 0.0;
+    if (Go) {
+      go0 = Go[ig];
+      go1 = Go[bs + ig];
+      go2 = Go[2 * bs + ig];
+    }
+    if (Gn) {
+      gn0 = Gn[ig];
+      gn1 = Gn[bs + ig];
+      gn2 = Gn[2 * bs + ig];
+    }
+    double o6[6];
+    finish_cell(k, sc, S[id], S[bs + id], S[2 * bs + id], S[3 * bs + id], go0, go1, go2, gn0, gn1,
+                gn2, Sp[id], Sp[bs + id], Sp[2 * bs + id], Sp[3 * bs + id], Sp[4 * bs + id],
+                Sp[5 * bs + id], true, true, o6);
+    const double rho_s = o6[0];
+    if (!(rho_s > 0.0)) flags |= ST_NEGATIVE;
+    if (!isfinite(rho_s) || !isfinite(o6[4]) || !isfinite(o6[5]) || !isfinite(o6[1]) ||
+        !isfinite(o6[2]) || !isfinite(o6[3]))
+      flags |= ST_NONFINITE;
+#pragma unroll
+    for (int c = 1; c < 6; ++c) Sp[c * bs + id] = o6[c];
+    if (dtacc) {
+      double p = k.gm1 * o6[5];
+      if (p < k.small_pres) p = k.small_pres;
+      const double c = sqrt(k.gamma * p / rho_s);
+      double t0 = sc.a_new * b.dx[0] / (fabs(o6[1] / rho_s) + c);
+      double t1 = sc.a_new * b.dx[1] / (fabs(o6[2] / rho_s) + c);
+      double t2 = sc.a_new * b.dx[2] / (fabs(o6[3] / rho_s) + c);
+      if (t0 < local_min) local_min = t0;
+      if (t1 < local_min) local_min = t1;
+      if (t2 < local_min) local_min = t2;
+    }
+  }
+  if (dtacc) {
+    for (int o = 16; o > 0; o >>= 1) {
+      double v = __shfl_xor_sync(0xffffffffu, local_min, o);
+      if (v < local_min) local_min = v;
+    }
+    if ((threadIdx.x & 31) == 0 && local_min < __longlong_as_double(0x7ff0000000000000LL))
+      atomic_min_pos(dtacc, local_min);
   }
   if (flags) atomicOr(status, flags);
 }
@@ -438,6 +497,15 @@ void launch_estdt(const BoxDev *boxes, const long long *cell_pref, int nbox, lon
                                                  dtacc);
 }
 
+void launch_correct(const BoxDev *boxes, const long long *cell_pref, int nbox, long long total,
+                    const SchemeConsts *K, const StepConsts *SC, const double *S, double *Sp,
+                    const double *Go, const double *Gn, unsigned long long *dtacc,
+                    unsigned *status, cudaStream_t st) {
+  if (total <= 0) return;
+  k_correct<<<grid_for(total, 256), 256, 0, st>>>(boxes, cell_pref, nbox, total, K, SC, S, Sp, Go,
+                                                   Gn, dtacc, status);
+}
+
 void launch_dt_finalize(const SchemeConsts *K, unsigned long long *dtacc, double *dt_out,
                         cudaStream_t st) {
   k_dt_finalize<<<1, 1, 0, st>>>(K, dtacc, dt_out);
@@ -450,7 +518,7 @@ void launch_staged_box(const BoxDev &b, const BoxDev *b_dev, const SchemeConsts 
                        const StepConsts *SC, const BoxStep *BSb, const double *Sbox,
                        const double *Gbox, double *Snbox, double *scratch, long long V,
                        unsigned long long *dtacc, unsigned *status, double *flux_keep,
-                       cudaStream_t st) {
+                       int predict_only, cudaStream_t st) {
   (void)b_dev;
   const int BLK = 256;
   double *q = scratch;
@@ -548,7 +616,8 @@ void launch_staged_box(const BoxDev &b, const BoxDev *b_dev, const SchemeConsts 
     int lo[3] = {0, 0, 0}, hi[3] = {b.n[0] - 1, b.n[1] - 1, b.n[2] - 1};
     Range r = make_range(lo, hi);
     k_update<<<grid_for(r.count, BLK), BLK, 0, st>>>(b, K, SC, Sbox, Gbox, Ff[0], Ff[1], Ff[2],
-                                                     Snbox, V, r, dtacc, status, flux_keep);
+                                                     Snbox, V, r, dtacc, status, flux_keep,
+                                                     predict_only);
   }
   if (flux_keep) {
     double *o = flux_keep;

@@ -59,7 +59,8 @@ class NyxParams(C.Structure):
                 ("small_pres", C.c_double), ("eta_de", C.c_double),
                 ("riemann_max_iter", C.c_int), ("riemann_tol", C.c_double),
                 ("precision", C.c_int), ("grav_corrector", C.c_int), ("batching", C.c_int),
-                ("autotune", C.c_int), ("keep_fluxes", C.c_int), ("coarse_fine", C.c_int)]
+                ("autotune", C.c_int), ("keep_fluxes", C.c_int), ("coarse_fine", C.c_int),
+                ("grav_energy", C.c_int)]
 
 
 class NyxLevel(C.Structure):
@@ -98,6 +99,8 @@ def load_library(path: str | None = None):
     L.nyx_hydro_estdt.argtypes = [vp, C.POINTER(NyxLevel), vp, vp]
     L.nyx_hydro_advance.argtypes = [vp, C.POINTER(NyxLevel), vp, vp, vp, vp, vp]
     L.nyx_hydro_run.argtypes = [vp, C.POINTER(NyxLevel), vp, vp, C.c_int, C.c_int, C.c_int]
+    L.nyx_hydro_predict.argtypes = [vp, C.POINTER(NyxLevel), vp, vp, vp, vp]
+    L.nyx_hydro_correct.argtypes = [vp, C.POINTER(NyxLevel), vp, vp, vp, vp, vp, vp]
     L.nyx_hydro_fluxes.argtypes = [vp, C.POINTER(NyxLevel), C.c_int, C.c_int, vp]
     L.nyx_hydro_step_host.argtypes = [vp, C.POINTER(NyxLevel), vp, vp, C.c_double, C.c_double,
                                       dp]
@@ -126,7 +129,8 @@ def load_library(path: str | None = None):
                  "nyx_hydro_advance", "nyx_hydro_run", "nyx_hydro_fluxes", "nyx_hydro_step_host",
                  "nyx_hydro_status", "nyx_plan_destroy", "nyx_hydro_tile_shape",
                  "nyx_hydro_set_tile_shape", "nyx_hydro_get_tile_shape", "nyx_hydro_profile",
-                 "nyx_hydro_counters_read", "nyx_hydro_estdt_noalloc"):
+                 "nyx_hydro_counters_read", "nyx_hydro_estdt_noalloc", "nyx_hydro_predict",
+                 "nyx_hydro_correct"):
         getattr(L, name).restype = C.c_int
     if path is None:
         _lib = L
@@ -301,6 +305,23 @@ class Plan:
         with self.ordered():
             _check(self.lib.nyx_hydro_advance(self.h, C.byref(cl), _ptr(a_old), _ptr(a_new),
                                               _ptr(dt), _ptr(grav), _ptr(dt_next)))
+        level.sync_from_c()
+
+    def predict(self, level, a_old, a_new, dt, grav_old=None):
+        """Step 2 alone: state[1-cur] = predictor (cur unchanged)."""
+        cl = level.c()
+        with self.ordered():
+            _check(self.lib.nyx_hydro_predict(self.h, C.byref(cl), _ptr(a_old), _ptr(a_new),
+                                              _ptr(dt), _ptr(grav_old)))
+        level.sync_from_c()
+
+    def correct(self, level, a_old, a_new, dt, grav_old=None, grav_new=None, dt_next=None):
+        """Step 6 alone on the predictor in state[1-cur] (g^n, g^{n+1}); cur flips."""
+        cl = level.c()
+        with self.ordered():
+            _check(self.lib.nyx_hydro_correct(self.h, C.byref(cl), _ptr(a_old), _ptr(a_new),
+                                              _ptr(dt), _ptr(grav_old), _ptr(grav_new),
+                                              _ptr(dt_next)))
         level.sync_from_c()
 
     def run(self, level, a_dev, dt_dev, nsteps, compute_dt0=True, use_graph=True):

@@ -494,3 +494,27 @@ def amr_large(n=512, box=32, nfine=410, sigma=1.0, seed=5, select_seed=11, nstep
     w = Workload(f"{n}^3 level as {coarse.nbox} boxes of {box}^3, {nfine} refined by 2",
                  coarse, S, G, a_schedule(1.0 / 51, 1.0 / 31, nsteps), 5.0 / 3.0, 0.5, nsteps, True)
     return AmrWorkload(w.name, w, refine_boxes(coarse, refined), refined)
+
+
+def cell_factors(lev: LevelSpec, seed, amp) -> list:
+    """Seeded per-cell factors 1 + amp N(0, 1) over the valid cells of every
+    box (shape (nz, ny, nx) each).  Multiplying all six conserved components
+    of a cell by its factor perturbs the density and keeps the velocity and
+    the specific energies."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(lev.nbox):
+        nx, ny, nz = lev.extent(b)
+        out.append(1.0 + amp * rng.standard_normal((nz, ny, nx)))
+    return out
+
+
+def scale_valid(arrays, factors, ng: int = NG) -> list:
+    """Copies of per-box arrays with every component of each valid cell
+    multiplied by that cell's factor."""
+    out = []
+    for a, f in zip(arrays, factors):
+        a = np.array(a, dtype=np.float64, copy=True)
+        valid(a, ng)[...] *= f[None]
+        out.append(a)
+    return out

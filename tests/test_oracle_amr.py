@@ -186,16 +186,14 @@ def test_fine_ghosts_take_fine_neighbours_first():
 
 
 def _two_level_state(w, fine, pert=0.02, seed=9):
+    """Coarse state of the workload, fine state interpolated from it and
+    perturbed cell by cell (seeded factors), coarse cells under the fine
+    level averaged down: a composite state whose coarse level holds its
+    totals."""
     lev = w.level
     cs = _filled(lev, w.state)
     fs = oracle.amr_interp(lev, cs, fine, _fine_empty(fine, 6), "all")
-    rng = np.random.default_rng(seed)
-    for b in range(fine.nbox):
-        v = W.valid(fs[b])
-        v[0] *= 1.0 + pert * rng.standard_normal(v[0].shape)
-        v[1:4] *= 1.0 + pert * rng.standard_normal(v[1:4].shape)
-        ke = 0.5 * (v[1] ** 2 + v[2] ** 2 + v[3] ** 2) / v[0]
-        v[4] = v[5] + ke
+    fs = W.scale_valid(fs, W.cell_factors(fine, seed, pert))
     cs = oracle.amr_average_down(lev, cs, fine, fs)
     return cs, fs
 
