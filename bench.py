@@ -34,6 +34,16 @@ from paper_1301_4498_gb300 import workloads as W  # noqa: E402
 
 METRIC = "zone-updates/s per level step on 1 GB300 + HBM-roofline fraction, FP32-batched vs FP64"
 ALG_BYTES_PER_ZONE = 120  # read S (6 x 8 B) + g (3 x 8 B), write S (6 x 8 B)
+# Standalone corrector (Step 6 with g^{n+1}): read rho, m at t^n (4 x 8 B), the
+# predictor (6 x 8 B), g^n and g^{n+1} (2 x 3 x 8 B); write m, rhoE, rhoe (5 x 8 B).
+CORRECT_BYTES_PER_ZONE = 168
+# Its FP64 operations per zone (option (i)): momentum corrector 3 x 6, energy
+# corrector 16 (two dot products and the weighted difference), dual-energy
+# sync 10 (kinetic energy with its division, the switch test, the
+# subtraction).  FP64 division and square root run at a small fraction of the
+# FP32 rate here; measured FP64 instruction rate: 0.506e12 per second.
+CORRECT_FP64_FLOPS_PER_ZONE = 44
+FP64_INSTR_TPS = 0.506
 # Algorithmic floating-point operations per zone-update (+ - * / sqrt counted
 # once each, comparisons not counted): 3196 for primitives, PPM + tracing in 3
 # directions, 12 Riemann set-ups/samplings, 18 corner-coupling corrections and
@@ -332,6 +342,63 @@ def run_ours(args, w):
                "steps": e2e_steps}
         del host_in, host_out
 
+    # scheme variants on the same level: the standalone corrector with a second
+    # gravity field (Step 6 with g^{n+1}) and the fused advance with energy
+    # option (ii) (Sec. 3.2), each timed with events on its plan's stream
+    variants = {}
+    if not args.no_variants:
+        g_new = lev.grav.clone()
+        a1 = a[:2]
+        dtv = dt[:1]
+        plan.predict(lev, a1[:1], a1[1:], dtv, lev.grav)
+        torch.cuda.synchronize()
+        snap = lev.state[1 - lev.cur].clone()
+        reps = 3
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        tot = 0.0
+        for r in range(reps):
+            lev.state[1 - lev.cur].copy_(snap)
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            plan.correct(lev, a1[:1], a1[1:], dtv, lev.grav, g_new)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            tot += ev[0].elapsed_time(ev[1])
+            lev.cur = 1 - lev.cur          # keep the state at t^n current
+        c_ms = tot / reps
+        gbs = CORRECT_BYTES_PER_ZONE * cells / (c_ms / 1e3) / 1e9
+        f64 = CORRECT_FP64_FLOPS_PER_ZONE * cells / (c_ms / 1e3) / 1e12
+        variants["corrector"] = {"ms": c_ms, "bound": "fp64",
+                                 "alg_fp64_flops_per_zone": CORRECT_FP64_FLOPS_PER_ZONE,
+                                 "achieved": f64, "peak": FP64_INSTR_TPS, "unit": "TFLOP/s",
+                                 "frac": f64 / FP64_INSTR_TPS,
+                                 "peak_source": "measured FP64 instruction rate (one flop per "
+                                                "non-FMA instruction)",
+                                 "hbm": {"alg_bytes_per_zone": CORRECT_BYTES_PER_ZONE,
+                                         "achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"],
+                                         "frac": gbs / peaks["hbm_gbs"]}}
+        del snap, g_new
+        p2 = H.Plan(w.level, gamma=w.gamma, cfl=w.cfl, precision=args.precision,
+                    batching="persistent", grav_energy=1)
+        p2.set_tile_shape(shape)
+        l2 = H.Level(lev.state[0], lev.state[1], lev.grav, lev.cur)
+        p2.advance(l2, a1[:1], a1[1:], dtv)
+        torch.cuda.synchronize()
+        l2.cur = lev.cur
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        p2.profile(True)
+        p2.advance(l2, a1[:1], a1[1:], dtv)
+        pr2 = p2.counters(reset=True)
+        p2.profile(False)
+        torch.cuda.synchronize()
+        ms2 = pr2["advance_ms"] / max(1, pr2["timed_advances"])
+        tf2 = flops * cells / (ms2 / 1e3) / 1e12
+        variants["energy_option_ii"] = {"advance_ms": ms2, "achieved_tflops": tf2,
+                                        "frac": tf2 / peak_tf, "bound": "alu",
+                                        "vs_option_i_advance_ms": adv_ms}
+        p2.close()
+
     # FP64 forms on the same workload (one step each), for the FP32-vs-FP64 comparison
     side = {}
     if not args.no_fp64:
@@ -382,6 +449,7 @@ def run_ours(args, w):
                              "alg_bytes_per_zone": ALG_BYTES_PER_ZONE,
                              "peak_source": f"hbm_gbs {peak_src}"},
             "kernel_ms": {"advance": adv_ms, "ghost_fill": fill_ms},
+            "variants": variants,
             "fp64_comparison": side,
             "clocks": clk,
             "e2e": e2e,
@@ -655,6 +723,7 @@ def main(argv=None):
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--traffic-per-zone", type=float, default=0.0,
                     help="DRAM bytes per zone of the advance kernel from an ncu capture")
     ap.add_argument("--keep-fluxes", type=int, default=1,

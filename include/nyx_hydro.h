@@ -175,7 +175,8 @@ int nyx_hydro_predict(nyx_plan *plan, nyx_level *level, const double *a_old_dev,
  * grav_energy -- then the dual-energy sync, in place (FP64 for every plan);
  * cur flips.  Gravity fields are device fields of 3 components (valid cells
  * read; NULL = zero).  dt_next_dev (may be NULL) receives the CFL step of
- * the new state at a_new.  With grav_new = grav_old the pair gives the
+ * the new state at a_new (FP32 for mixed plans, as nyx_hydro_estdt).  With
+ * grav_new = grav_old the pair gives the
  * result of nyx_hydro_advance (bitwise for FP64 plans). */
 int nyx_hydro_correct(nyx_plan *plan, nyx_level *level, const double *a_old_dev,
                       const double *a_new_dev, const double *dt_dev, const double *grav_old_dev,

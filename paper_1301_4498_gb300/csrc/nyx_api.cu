@@ -403,7 +403,8 @@ int do_correct(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_n
   launch_step_setup(P->d_K, a_old, a_new, dt, P->d_SC, P->d_boxes, P->nbox, P->d_BS, P->stream);
   launch_correct(P->d_boxes, P->d_cell_pref, P->nbox, P->total_cells, P->d_K, P->d_SC,
                  L->state[L->cur], L->state[1 - L->cur], g_old, g_new,
-                 dt_next ? P->d_dtacc : nullptr, P->d_status, P->stream);
+                 dt_next ? P->d_dtacc : nullptr, P->d_status, P->prm.precision == NYX_MIXED,
+                 P->stream);
   P->launches += 2;
   if (dt_next) {
     launch_dt_finalize(P->d_K, P->d_dtacc, dt_next, P->stream);

@@ -71,11 +71,12 @@ int launch_fused_f64(int shape, const FusedArgs &a, int grid, cudaStream_t st);
 // Step 6 alone over every valid cell of a level (FP64): the predictor in
 // Sp (6 components) is corrected in place with the state at t^n in S, g^n in
 // Go and g^{n+1} in Gn (either may be null: zero), then synchronised; the CFL
-// minimum of the result goes to dtacc (may be null).
+// minimum of the result goes to dtacc (may be null), formed in FP32 when
+// f32_dt (mixed plans) and in FP64 otherwise.
 void launch_correct(const BoxDev *boxes, const long long *cell_pref, int nbox, long long total,
                     const SchemeConsts *K, const StepConsts *SC, const double *S, double *Sp,
                     const double *Go, const double *Gn, unsigned long long *dtacc,
-                    unsigned *status, cudaStream_t st);
+                    unsigned *status, bool f32_dt, cudaStream_t st);
 int launch_fused_mixed(int shape, const FusedArgs &a, int grid, cudaStream_t st);
 int max_grid_f64(int shape);
 int max_grid_mixed(int shape);

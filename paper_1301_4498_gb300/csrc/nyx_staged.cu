@@ -302,7 +302,10 @@ __global__ void k_update(BoxDev b, const SchemeConsts *K, const StepConsts *SC, 
 // The corrector with g^n and g^{n+1} and the dual-energy sync over every
 // valid cell of the level, in place on the predictor; one thread per cell,
 // cells of a box in x-fastest order (coalesced), the box found by a binary
-// search of the cell offsets.  CFL minimum of the result as in k_update.
+// search of the cell offsets.  CFL minimum of the result as in k_update (in
+// FP32 for mixed plans, as their CFL reduction is: FP64 division and square
+// root run at a small fraction of the FP32 rate on this part).
+template <bool F32DT>
 __global__ void k_correct(const BoxDev *boxes, const long long *cell_pref, int nbox,
                           long long total, const SchemeConsts *K, const StepConsts *SC,
                           const double *S, double *Sp, const double *Go, const double *Gn,
@@ -350,15 +353,28 @@ __global__ void k_correct(const BoxDev *boxes, const long long *cell_pref, int n
 #pragma unroll
     for (int c = 1; c < 6; ++c) Sp[c * bs + id] = o6[c];
     if (dtacc) {
-      double p = k.gm1 * o6[5];
-      if (p < k.small_pres) p = k.small_pres;
-      const double c = sqrt(k.gamma * p / rho_s);
-      double t0 = sc.a_new * b.dx[0] / (fabs(o6[1] / rho_s) + c);
-      double t1 = sc.a_new * b.dx[1] / (fabs(o6[2] / rho_s) + c);
-      double t2 = sc.a_new * b.dx[2] / (fabs(o6[3] / rho_s) + c);
-      if (t0 < local_min) local_min = t0;
-      if (t1 < local_min) local_min = t1;
-      if (t2 < local_min) local_min = t2;
+      if constexpr (F32DT) {
+        const float r = (float)rho_s, ir = 1.0f / r;
+        float p = (float)k.gm1 * (float)o6[5];
+        if (p < (float)k.small_pres) p = (float)k.small_pres;
+        const float c = sqrtf((float)k.gamma * p * ir);
+        const float an = (float)sc.a_new;
+        const float t0 = an * (float)b.dx[0] / (fabsf((float)o6[1] * ir) + c);
+        const float t1 = an * (float)b.dx[1] / (fabsf((float)o6[2] * ir) + c);
+        const float t2 = an * (float)b.dx[2] / (fabsf((float)o6[3] * ir) + c);
+        const double tm = (double)fminf(t0, fminf(t1, t2));
+        if (tm < local_min) local_min = tm;
+      } else {
+        double p = k.gm1 * o6[5];
+        if (p < k.small_pres) p = k.small_pres;
+        const double c = sqrt(k.gamma * p / rho_s);
+        double t0 = sc.a_new * b.dx[0] / (fabs(o6[1] / rho_s) + c);
+        double t1 = sc.a_new * b.dx[1] / (fabs(o6[2] / rho_s) + c);
+        double t2 = sc.a_new * b.dx[2] / (fabs(o6[3] / rho_s) + c);
+        if (t0 < local_min) local_min = t0;
+        if (t1 < local_min) local_min = t1;
+        if (t2 < local_min) local_min = t2;
+      }
     }
   }
   if (dtacc) {
@@ -500,10 +516,14 @@ void launch_estdt(const BoxDev *boxes, const long long *cell_pref, int nbox, lon
 void launch_correct(const BoxDev *boxes, const long long *cell_pref, int nbox, long long total,
                     const SchemeConsts *K, const StepConsts *SC, const double *S, double *Sp,
                     const double *Go, const double *Gn, unsigned long long *dtacc,
-                    unsigned *status, cudaStream_t st) {
+                    unsigned *status, bool f32_dt, cudaStream_t st) {
   if (total <= 0) return;
-  k_correct<<<grid_for(total, 256), 256, 0, st>>>(boxes, cell_pref, nbox, total, K, SC, S, Sp, Go,
-                                                   Gn, dtacc, status);
+  if (f32_dt)
+    k_correct<true><<<grid_for(total, 256), 256, 0, st>>>(boxes, cell_pref, nbox, total, K, SC, S,
+                                                           Sp, Go, Gn, dtacc, status);
+  else
+    k_correct<false><<<grid_for(total, 256), 256, 0, st>>>(boxes, cell_pref, nbox, total, K, SC, S,
+                                                            Sp, Go, Gn, dtacc, status);
 }
 
 void launch_dt_finalize(const SchemeConsts *K, unsigned long long *dtacc, double *dt_out,
