@@ -54,7 +54,8 @@ class _Params(C.Structure):
                 ("small_pres", C.c_double), ("eta_de", C.c_double),
                 ("riemann_max_iter", C.c_int), ("riemann_tol", C.c_double),
                 ("grav_corrector", C.c_int), ("dual_energy_sync", C.c_int),
-                ("grav_energy", C.c_int)]
+                ("grav_energy", C.c_int), ("reconstruction", C.c_int),
+                ("riemann_solver", C.c_int)]
 
 
 class _Level(C.Structure):
@@ -83,11 +84,14 @@ class OracleParams:
     grav_corrector: int = 1
     dual_energy_sync: int = 1
     grav_energy: int = 0       # Sec. 3.2: 0 rho U . g in the energy; 1 the kinetic-energy change
+    reconstruction: int = 0    # Sec. 3.2: 0 PPM, 1 PLM
+    riemann_solver: int = 0    # Sec. 3.2: 0 two-shock (iterative), 1 linearised
 
     def _c(self) -> _Params:
         return _Params(self.gamma, self.cfl, self.small_dens, self.small_pres, self.eta_de,
                        self.riemann_max_iter, self.riemann_tol, self.grav_corrector,
-                       self.dual_energy_sync, self.grav_energy)
+                       self.dual_energy_sync, self.grav_energy, self.reconstruction,
+                       self.riemann_solver)
 
 
 def load(path: str):

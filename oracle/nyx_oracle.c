@@ -35,6 +35,7 @@ static long long orc_rcount[ORC_MAX_THREADS * 8][2];
 typedef struct {
   double gamma, gm1, igm1, kshock, small_dens, small_pres, tol;
   int max_iter;
+  int plm, linear;  /* PLM profiles; linearised Riemann solver */
 } eos_t;
 
 static eos_t make_eos(const orc_params *p) {
@@ -47,6 +48,8 @@ static eos_t make_eos(const orc_params *p) {
   e.small_pres = p->small_pres;
   e.tol = p->riemann_tol;
   e.max_iter = p->riemann_max_iter;
+  e.plm = p->reconstruction == 1;
+  e.linear = p->riemann_solver == 1;
   return e;
 }
 
@@ -99,6 +102,18 @@ static void ppm_coeffs(const double s[5], double *sLo, double *sRo, double *s6o)
   *s6o = 6.0 * (si - 0.5 * (sL + sR));
 }
 
+/* PLM (Sec. 3.2, the piecewise linear option): the linear profile with the
+ * MC-limited slope d of the cell, written in the parabola's coefficients --
+ * edge values s_i -+ d/2 and no curvature -- so that the integrals below
+ * are the averages of the linear profile.  reading: the plain MC slope (the
+ * PPM slope of cell i), not a fourth-order slope. */
+static void plm_coeffs(const double s[5], double *sLo, double *sRo, double *s6o) {
+  double d = mc_slope(s[1], s[2], s[3]);
+  *sLo = s[2] - 0.5 * d;
+  *sRo = s[2] + 0.5 * d;
+  *s6o = 0.0;
+}
+
 /* Average of the parabola over the sigma-fraction of the cell next to the
  * right (Ip) or left (Im) edge. */
 static double ppm_ip(double sL, double sR, double s6, double sig) {
@@ -131,7 +146,12 @@ static void trace_cell(const eos_t *E, double s5[5][5], double c, const double g
                        double dtdx, const trace_src_t *src, int dir, double qm[5],
                        double qp[5], double bm_out[3], double bp_out[3]) {
   double sL[5], sR[5], s6[5];
-  for (int v = 0; v < 5; ++v) ppm_coeffs(s5[v], &sL[v], &sR[v], &s6[v]);
+  for (int v = 0; v < 5; ++v) {
+    if (E->plm)
+      plm_coeffs(s5[v], &sL[v], &sR[v], &s6[v]);
+    else
+      ppm_coeffs(s5[v], &sL[v], &sR[v], &s6[v]);
+  }
   const int nv = 1 + dir;
   const double rho = s5[0][2];
   const double un = s5[nv][2];
@@ -209,7 +229,10 @@ static double shock_w(const eos_t *E, double C, double ps, double p) {
 
 static void sample_side(const eos_t *E, const double *qo, double Wo, double co, double s,
                         double pstar, double ustar, double g[5]) {
-  double rhos = 1.0 / (1.0 / qo[0] - (pstar - qo[4]) / (Wo * Wo));
+  /* star density: across the shock curve (two-shock), or from the
+   * linearised relation dp = c^2 d rho (linearised solver) */
+  double rhos = E->linear ? qo[0] + (pstar - qo[4]) / (co * co)
+                          : 1.0 / (1.0 / qo[0] - (pstar - qo[4]) / (Wo * Wo));
   if (rhos < E->small_dens) rhos = E->small_dens;
   double cs = sqrt(E->gamma * pstar / rhos);
   int star;
@@ -256,7 +279,9 @@ static void riemann_solve(const eos_t *E, const double *qL, const double *qR, do
   double p = (CR * pL + CL * pR + CL * CR * (uL - uR)) / (CL + CR);
   if (p < E->small_pres) p = E->small_pres;
   long long nit = 0;
-  for (int it = 0; it < E->max_iter; ++it) {
+  /* the linearised solver stops at the acoustic estimate: p* above, the
+   * wave speeds the acoustic impedances C (no Newton iteration) */
+  for (int it = 0; it < (E->linear ? 0 : E->max_iter); ++it) {
     double WL = shock_w(E, CL, pL, p);
     double WR = shock_w(E, CR, pR, p);
     double usL = uL - (p - pL) / WL;
@@ -277,8 +302,8 @@ static void riemann_solve(const eos_t *E, const double *qL, const double *qR, do
       orc_rcount[t * 8][1] += nit;
     }
   }
-  const double WL = shock_w(E, CL, pL, p);
-  const double WR = shock_w(E, CR, pR, p);
+  const double WL = E->linear ? CL : shock_w(E, CL, pL, p);
+  const double WR = E->linear ? CR : shock_w(E, CR, pR, p);
   const double ustar = (pL - pR + WL * uL + WR * uR) / (WL + WR);
   const double pstar = p;
   double g[5];

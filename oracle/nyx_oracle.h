@@ -45,6 +45,10 @@ typedef struct {
   int grav_energy;       /* S_g in the total energy (Sec. 3.2): 0 the product of the
                             cell-centred momentum and g; 1 the change of the kinetic
                             energy that the momentum's gravity update makes */
+  int reconstruction;    /* edge-state profiles (Sec. 3.2): 0 PPM, 1 PLM; both with the
+                            reference-state tracing */
+  int riemann_solver;    /* 0 the iterative two-shock solver; 1 the linearised
+                            approximate solver (Sec. 3.2 names both) */
 } orc_params;
 
 typedef struct {

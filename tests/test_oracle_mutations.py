@@ -16,6 +16,7 @@ import test_oracle_ppm as tp
 import test_oracle_riemann as tr
 import test_oracle_step as ts
 import test_oracle_trace as tt
+import test_oracle_variants as tv
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(os.path.dirname(HERE), "oracle", "nyx_oracle.c")
@@ -78,6 +79,17 @@ MUTANTS = {
     "periodic wrap off by one": ("x = dlo[d] + ((x - dlo[d]) % len + len) % len;",
                                  "x = dlo[d] + ((x - dlo[d] + 1) % len + len) % len;",
                                  ts.test_ghost_fill_periodic_outflow_and_tiles, ()),
+    # PLM and the linearised solver
+    "PLM edge at a quarter slope": ("*sRo = s[2] + 0.5 * d;", "*sRo = s[2] + 0.25 * d;",
+                                    tv.test_plm_traced_density_closed_form, ()),
+    "PLM slope from the upwind cells": ("double d = mc_slope(s[1], s[2], s[3]);",
+                                        "double d = mc_slope(s[0], s[1], s[2]);",
+                                        tv.test_plm_traced_density_closed_form, ()),
+    "linearised star density sign": ("? qo[0] + (pstar - qo[4]) / (co * co)",
+                                     "? qo[0] - (pstar - qo[4]) / (co * co)",
+                                     tv.test_sod_with_the_linearised_solver, ()),
+    "linearised solver iterates anyway": ("(E->linear ? 0 : E->max_iter)", "(E->max_iter)",
+                                          tv.test_linearised_symmetric_collision_closed_form, ()),
     # gravity source variants
     "corrector uses g^n for the new density": ("(rho_s * gn[c] - rho * go[c])",
                                                 "(rho_s * go[c] - rho * go[c])",
