@@ -55,6 +55,11 @@ extern "C" {
 #define NYX_MIXED 1        /* FP32 reconstruction/tracing/Riemann; FP64 state,
                               flux-divergence accumulation and dual-energy sync */
 
+#define NYX_PPM 0          /* edge-state profiles: piecewise parabolic (Sec. 3.2) */
+#define NYX_PLM 1          /* piecewise linear, MC-limited slope (Sec. 3.2) */
+#define NYX_RS_TWO_SHOCK 0 /* iterative two-shock Riemann solver (Sec. 3.2) */
+#define NYX_RS_LINEAR 1    /* linearised approximate Riemann solver (Sec. 3.2) */
+
 #define NYX_PERSISTENT 0   /* one persistent fused launch over all (box, tile) items */
 #define NYX_PER_BOX 1      /* plain FP64 stage-by-stage kernels, one box at a time */
 
@@ -104,6 +109,11 @@ typedef struct {
                               product of the cell-centred momentum and g; 1 the change
                               of the kinetic energy that the momentum's gravity update
                               makes (leaves e = E - U^2/2 to the hydro update) */
+  int reconstruction;      /* NYX_PPM or NYX_PLM; both trace with the reference state of
+                              Sec. 3.2 (the average of the profile over the domain of
+                              dependence of the fastest wave toward the face) */
+  int riemann_solver;      /* NYX_RS_TWO_SHOCK or NYX_RS_LINEAR (acoustic p*, u* without
+                              iteration; star density from dp = c^2 d rho) */
 } nyx_hydro_params;
 
 typedef struct nyx_plan nyx_plan;
@@ -120,7 +130,7 @@ typedef struct {
 /* Fill *params with the defaults (gamma 5/3, cfl 0.5, small_dens 1e-10,
  * small_pres 1e-12, eta_de 1e-4, 12 iterations, tol 1e-10, FP64,
  * corrector on, persistent, autotune off, keep_fluxes off, coarse_fine off,
- * grav_energy 0). */
+ * grav_energy 0, PPM, two-shock solver). */
 void nyx_hydro_default_params(nyx_hydro_params *params);
 
 /* Validate the level (Sec. 4.1: even positive extents, ng == 4, boxes of a

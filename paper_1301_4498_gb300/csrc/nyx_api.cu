@@ -373,6 +373,7 @@ int do_advance(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_n
     a.flux_keep = P->d_flux;
     a.flux_off = P->d_flux_off;
     a.predict_only = predict_only ? 1 : 0;
+    a.variant = P->hK.plm | (P->hK.linear_rs << 1);
     if (P->prm.autotune && !P->tuned) {
       int rc = tune_shape(P, a);
       if (rc) return rc;
@@ -506,6 +507,7 @@ int plan_tune(nyx_plan *P, nyx_level *L, const double *a_dev, const double *dt_d
   a.G = L->grav;
   a.Sn = L->state[1 - L->cur];
   a.status = P->d_status_tune;
+  a.variant = P->hK.plm | (P->hK.linear_rs << 1);
   do_fill(P, L->state[L->cur], NCONS);
   launch_step_setup(P->d_K, a_dev, a_dev + 1, dt_dev, P->d_SC, P->d_boxes, P->nbox, P->d_BS,
                     P->stream);
@@ -557,6 +559,8 @@ void nyx_hydro_default_params(nyx_hydro_params *p) {
   p->keep_fluxes = 0;
   p->coarse_fine = 0;
   p->grav_energy = 0;
+  p->reconstruction = NYX_PPM;
+  p->riemann_solver = NYX_RS_TWO_SHOCK;
 }
 
 const char *nyx_last_error(void) { return g_err.c_str(); }
@@ -681,6 +685,8 @@ int nyx_hydro_plan(const nyx_level_desc *lev, const nyx_hydro_params *prm, void 
     K.max_iter = prm->riemann_max_iter;
     K.grav_corrector = prm->grav_corrector;
     K.grav_energy = prm->grav_energy;
+    K.plm = prm->reconstruction == NYX_PLM;
+    K.linear_rs = prm->riemann_solver == NYX_RS_LINEAR;
     TRYC(cudaMalloc(&P->d_K, sizeof(SchemeConsts)));
     TRYC(cudaMemcpy(P->d_K, &K, sizeof(SchemeConsts), cudaMemcpyHostToDevice));
     TRYC(cudaMalloc(&P->d_SC, sizeof(StepConsts)));
@@ -811,6 +817,7 @@ int nyx_hydro_run(nyx_plan *P, nyx_level *L, const double *a_dev, double *dt_dev
     a.G = L->grav;
     a.Sn = L->state[1 - L->cur];
     a.status = P->d_status_tune;
+    a.variant = P->hK.plm | (P->hK.linear_rs << 1);
     // time the shapes on the first step as it will run: its own dt
     if (compute_dt0) do_estdt(P, L->state[L->cur], a_dev, dt_dev);
     do_fill(P, L->state[L->cur], NCONS);

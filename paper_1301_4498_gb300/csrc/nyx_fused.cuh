@@ -51,6 +51,8 @@ __device__ __forceinline__ Eos<R> make_eos(const nyx::SchemeConsts &k, bool mixe
   e.small_pres = (R)k.small_pres;
   e.tol = (R)(mixed ? k.tol_mixed : k.tol);
   e.max_iter = k.max_iter;
+  e.plm = k.plm;
+  e.linear = k.linear_rs;
   return e;
 }
 

@@ -172,7 +172,7 @@ __device__ __forceinline__ void face_flux_dir(const Eos<float> &E, int dir, cons
   F[7] = o[7];
 }
 
-template <int TX, int TY, int MB>
+template <int TX, int TY, int MB, int VAR>
 __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a) {
   using G = G2<TX, TY>;
   constexpr int NC = G::NC, NCP = G::NCP, NE = G::NE, W = G::W, WE = G::WE, NT = G::NT;
@@ -183,7 +183,13 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
 
   const nyx::SchemeConsts KK = *a.K;
   const nyx::StepConsts sc = *a.SC;
-  const Eos<float> E = make_eos<float>(KK, true);
+  Eos<float> E = make_eos<float>(KK, true);
+  // VAR >= 0 fixes the scheme variant at compile time (bit 0 PLM, bit 1 the
+  // linearised solver), so the default instantiation carries no variant code
+  if constexpr (VAR >= 0) {
+    E.plm = VAR & 1;
+    E.linear = (VAR >> 1) & 1;
+  }
   TraceSrc<float> src;
   src.hdtp = d2f_rn(sc.hdtp);
   src.src_u = d2f_rn(sc.src_u);
@@ -581,25 +587,26 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
   if (flags) atomicOr(a.status, flags);
 }
 
-template <int TX, int TY, int MB>
+template <int TX, int TY, int MB, int VAR>
 int launch_two(const nyx::FusedArgs &a, int grid, cudaStream_t st) {
   using G = G2<TX, TY>;
   cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(int), st);
   if (e != cudaSuccess) return (int)e;
-  k_fused2<TX, TY, MB><<<grid, G::NT, G::SMEM, st>>>(a);
+  k_fused2<TX, TY, MB, VAR><<<grid, G::NT, G::SMEM, st>>>(a);
   return (int)cudaGetLastError();
 }
 
-template <int TX, int TY, int MB>
+template <int TX, int TY, int MB, int VAR>
 int max_grid_two() {
   using G = G2<TX, TY>;
-  cudaError_t e = cudaFuncSetAttribute(k_fused2<TX, TY, MB>,
+  cudaError_t e = cudaFuncSetAttribute(k_fused2<TX, TY, MB, VAR>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
   if (e != cudaSuccess) return 0;
   int per_sm = 0, dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused2<TX, TY, MB>, G::NT, G::SMEM);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused2<TX, TY, MB, VAR>, G::NT,
+                                                G::SMEM);
   if (per_sm < 1) return 0;
   return per_sm * nsm;
 }

@@ -3,6 +3,8 @@
 // state, flux-divergence accumulation, update and dual-energy sync.
 // Shapes 0-2: column-owning form (nyx_fused.cuh); 3-5: task form
 // (nyx_fused2.cuh).
+#include <algorithm>
+
 #define NYX_NS nyx_mixed
 #include "nyx_fused.cuh"
 #include "nyx_fused2.cuh"
@@ -14,9 +16,15 @@ int launch_fused_mixed(int shape, const FusedArgs &a, int grid, cudaStream_t st)
     case 0: return nyx_mixed::launch_one<float, 16, 16>(a, grid, st);
     case 1: return nyx_mixed::launch_one<float, 32, 8>(a, grid, st);
     case 2: return nyx_mixed::launch_one<float, 16, 8>(a, grid, st);
-    case 3: return nyx_mixed::launch_two<16, 8, 1>(a, grid, st);
-    case 4: return nyx_mixed::launch_two<8, 8, 2>(a, grid, st);
-    case 5: return nyx_mixed::launch_two<32, 4, 1>(a, grid, st);
+    case 3:  // the default shape: one instantiation per scheme variant
+      switch (a.variant) {
+        case 1: return nyx_mixed::launch_two<16, 8, 1, 1>(a, grid, st);
+        case 2: return nyx_mixed::launch_two<16, 8, 1, 2>(a, grid, st);
+        case 3: return nyx_mixed::launch_two<16, 8, 1, 3>(a, grid, st);
+        default: return nyx_mixed::launch_two<16, 8, 1, 0>(a, grid, st);
+      }
+    case 4: return nyx_mixed::launch_two<8, 8, 2, -1>(a, grid, st);
+    case 5: return nyx_mixed::launch_two<32, 4, 1, -1>(a, grid, st);
     default: return (int)cudaErrorInvalidValue;
   }
 }
@@ -26,9 +34,14 @@ int max_grid_mixed(int shape) {
     case 0: return nyx_mixed::max_grid_one<float, 16, 16>();
     case 1: return nyx_mixed::max_grid_one<float, 32, 8>();
     case 2: return nyx_mixed::max_grid_one<float, 16, 8>();
-    case 3: return nyx_mixed::max_grid_two<16, 8, 1>();
-    case 4: return nyx_mixed::max_grid_two<8, 8, 2>();
-    case 5: return nyx_mixed::max_grid_two<32, 4, 1>();
+    case 3: {  // every variant instantiation, the smallest grid
+      int g = nyx_mixed::max_grid_two<16, 8, 1, 0>();
+      g = std::min(g, nyx_mixed::max_grid_two<16, 8, 1, 1>());
+      g = std::min(g, nyx_mixed::max_grid_two<16, 8, 1, 2>());
+      return std::min(g, nyx_mixed::max_grid_two<16, 8, 1, 3>());
+    }
+    case 4: return nyx_mixed::max_grid_two<8, 8, 2, -1>();
+    case 5: return nyx_mixed::max_grid_two<32, 4, 1, -1>();
     default: return 1;
   }
 }

@@ -34,6 +34,8 @@ struct SchemeConsts {
   double tol_mixed;
   int max_iter, grav_corrector;
   int grav_energy;  // S_g in the total energy: 0 rho U . g, 1 kinetic-energy change (Sec. 3.2)
+  int plm;          // 1: PLM profiles (Sec. 3.2)
+  int linear_rs;    // 1: linearised Riemann solver (Sec. 3.2)
 };
 
 // Scalars of one step, derived on the device from a_old, a_new, dt so that

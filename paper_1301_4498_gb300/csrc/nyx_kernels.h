@@ -52,6 +52,7 @@ struct FusedArgs {
   double *flux_keep;              // final-flux store, or null
   const long long *flux_off;      // per-box offsets into flux_keep
   int predict_only;               // 1: Step 2 only (no corrector, no dual-energy sync, no dt)
+  int variant;                    // scheme variant: bit 0 PLM, bit 1 linearised solver
 };
 
 // Tile shapes of the fused kernel (columns per CTA in x and y).

@@ -22,6 +22,8 @@ template <class R>
 struct Eos {
   R gamma, gm1, igm1, kshock, small_dens, small_pres, tol;
   int max_iter;
+  int plm;     // PLM profiles instead of PPM (Sec. 3.2)
+  int linear;  // the linearised Riemann solver instead of the two-shock one (Sec. 3.2)
 };
 
 template <class R>
@@ -86,6 +88,17 @@ __device__ __forceinline__ void ppm_coeffs(R s0, R s1, R s2, R s3, R s4, R &sLo,
   s6o = R(6) * (si - R(0.5) * (sL + sR));
 }
 
+// PLM (Sec. 3.2): the linear profile with the cell's MC-limited slope d,
+// written as a parabola with edge values s_i -+ d/2 and no curvature, so that
+// ppm_ip / ppm_im below give the averages of the linear profile.
+template <class R>
+__device__ __forceinline__ void plm_coeffs(R s1, R s2, R s3, R &sLo, R &sRo, R &s6o) {
+  const R d = mc_slope(s1, s2, s3);
+  sLo = s2 - R(0.5) * d;
+  sRo = s2 + R(0.5) * d;
+  s6o = R(0);
+}
+
 template <class R>
 __device__ __forceinline__ R ppm_ip(R sL, R sR, R s6, R sig) {
   return sR - R(0.5) * sig * ((sR - sL) - (R(1) - R(2.0 / 3.0) * sig) * s6);
@@ -118,7 +131,14 @@ __device__ __forceinline__ void trace_cell(const Eos<R> &E, const R (&s)[5][5], 
   constexpr int NV = 1 + DIR;
   R sL[5], sR[5], s6[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) ppm_coeffs(s[v][0], s[v][1], s[v][2], s[v][3], s[v][4], sL[v], sR[v], s6[v]);
+  if (E.plm) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) plm_coeffs(s[v][1], s[v][2], s[v][3], sL[v], sR[v], s6[v]);
+  } else {
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+      ppm_coeffs(s[v][0], s[v][1], s[v][2], s[v][3], s[v][4], sL[v], sR[v], s6[v]);
+  }
   const R rho = s[0][2];
   const R un = s[NV][2];
   const R pr = s[4][2];
@@ -216,7 +236,9 @@ __device__ __forceinline__ R shock_w(const Eos<R> &E, R C, R ps, R p) {
 template <class R>
 __device__ __forceinline__ void sample_side(const Eos<R> &E, R ro, R uo, R t1o, R t2o, R po, R Wo,
                                             R co, R s, R pstar, R ustar, R (&g)[5]) {
-  R rhos = R(1) / (R(1) / ro - (pstar - po) / (Wo * Wo));
+  // star density across the shock curve, or from dp = c^2 d rho (linearised)
+  R rhos = E.linear ? ro + (pstar - po) / (co * co)
+                    : R(1) / (R(1) / ro - (pstar - po) / (Wo * Wo));
   if (rhos < E.small_dens) rhos = E.small_dens;
   R cs = sqrt_r(E.gamma * pstar / rhos);
   int star;
@@ -264,7 +286,8 @@ __device__ __forceinline__ void riemann(const Eos<R> &E, const R (&qL)[5], const
   const R pL = qL[4], pR = qR[4], uL = qL[1], uR = qR[1];
   R p = (CR * pL + CL * pR + CL * CR * (uL - uR)) / (CL + CR);
   if (p < E.small_pres) p = E.small_pres;
-  for (int it = 0; it < E.max_iter; ++it) {
+  // the linearised solver stops at this acoustic estimate (W = C)
+  for (int it = 0; it < (E.linear ? 0 : E.max_iter); ++it) {
     R WL = shock_w(E, CL, pL, p);
     R WR = shock_w(E, CR, pR, p);
     R usL = uL - (p - pL) / WL;
@@ -277,8 +300,8 @@ __device__ __forceinline__ void riemann(const Eos<R> &E, const R (&qL)[5], const
     p = pn;
     if (conv) break;
   }
-  const R WL = shock_w(E, CL, pL, p);
-  const R WR = shock_w(E, CR, pR, p);
+  const R WL = E.linear ? CL : shock_w(E, CL, pL, p);
+  const R WR = E.linear ? CR : shock_w(E, CR, pR, p);
   const R ustar = (pL - pR + WL * uL + WR * uR) / (WL + WR);
   const R pstar = p;
   R g[5];
@@ -317,7 +340,8 @@ __device__ __forceinline__ void sample_side_fast(const Eos<float> &E, float ro, 
                                                  float t1o, float t2o, float po, float Wo, float iWo,
                                                  float co, float s, float pstar, float ustar,
                                                  float (&g)[5]) {
-  float d = iro - (pstar - po) * (iWo * iWo);  // 1/rho*
+  // 1/rho*: across the shock curve, or from dp = c^2 d rho (linearised)
+  float d = E.linear ? 1.0f / (ro + (pstar - po) / (co * co)) : iro - (pstar - po) * (iWo * iWo);
   float rhos = 1.0f / d;
   float ird = d;
   if (!(rhos >= E.small_dens)) {
@@ -371,7 +395,7 @@ __device__ __forceinline__ void riemann_fast(const Eos<float> &E, const float (&
   const float kL = E.kshock / pL, kR = E.kshock / pR;
   float p = (CR * pL + CL * pR + CL * CR * (uL - uR)) / (CL + CR);
   if (p < E.small_pres) p = E.small_pres;
-  for (int it = 0; it < E.max_iter; ++it) {
+  for (int it = 0; it < (E.linear ? 0 : E.max_iter); ++it) {
     const float xL = fmaxf(1.0f + (p - pL) * kL, 1e-10f);
     const float xR = fmaxf(1.0f + (p - pR) * kR, 1e-10f);
     const float rL = rsqrtf(xL), rR = rsqrtf(xR);
@@ -385,9 +409,10 @@ __device__ __forceinline__ void riemann_fast(const Eos<float> &E, const float (&
     p = pn;
     if (conv) break;
   }
-  const float xL = fmaxf(1.0f + (p - pL) * kL, 1e-10f);
-  const float xR = fmaxf(1.0f + (p - pR) * kR, 1e-10f);
-  const float rL = rsqrtf(xL), rR = rsqrtf(xR);
+  // final wave speeds W = C sqrt(x), x = 1 for the linearised solver (W = C)
+  const float xL = E.linear ? 1.0f : fmaxf(1.0f + (p - pL) * kL, 1e-10f);
+  const float xR = E.linear ? 1.0f : fmaxf(1.0f + (p - pR) * kR, 1e-10f);
+  const float rL = E.linear ? 1.0f : rsqrtf(xL), rR = E.linear ? 1.0f : rsqrtf(xR);
   const float WL = CL * xL * rL, WR = CR * xR * rR;
   const float ustar = (pL - pR + WL * uL + WR * uR) / (WL + WR);
   const float pstar = p;

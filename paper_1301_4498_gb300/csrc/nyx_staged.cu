@@ -28,6 +28,8 @@ __device__ __forceinline__ Eos<double> eos64(const SchemeConsts &k) {
   e.small_pres = k.small_pres;
   e.tol = k.tol;
   e.max_iter = k.max_iter;
+  e.plm = k.plm;
+  e.linear = k.linear_rs;
   return e;
 }
 

@@ -25,6 +25,10 @@ NYX_ETIMEOUT = -5
 NYX_ENOMEM = -6
 NYX_FP64 = 0
 NYX_MIXED = 1
+NYX_PPM = 0
+NYX_PLM = 1
+NYX_RS_TWO_SHOCK = 0
+NYX_RS_LINEAR = 1
 NYX_PERSISTENT = 0
 NYX_PER_BOX = 1
 NOALLOC_MAX_BOXES = 4096  # NYX_NOALLOC_MAX_BOXES of include/nyx_hydro.h
@@ -60,7 +64,8 @@ class NyxParams(C.Structure):
                 ("riemann_max_iter", C.c_int), ("riemann_tol", C.c_double),
                 ("precision", C.c_int), ("grav_corrector", C.c_int), ("batching", C.c_int),
                 ("autotune", C.c_int), ("keep_fluxes", C.c_int), ("coarse_fine", C.c_int),
-                ("grav_energy", C.c_int)]
+                ("grav_energy", C.c_int), ("reconstruction", C.c_int),
+                ("riemann_solver", C.c_int)]
 
 
 class NyxLevel(C.Structure):
@@ -175,6 +180,12 @@ def make_params(**kw) -> NyxParams:
     prec = kw.pop("precision", None)
     if prec is not None:
         p.precision = {"fp64": NYX_FP64, "mixed": NYX_MIXED}.get(prec, prec)
+    rec = kw.pop("reconstruction", None)
+    if rec is not None:
+        p.reconstruction = {"ppm": NYX_PPM, "plm": NYX_PLM}.get(rec, rec)
+    rs = kw.pop("riemann_solver", None)
+    if rs is not None:
+        p.riemann_solver = {"two_shock": NYX_RS_TWO_SHOCK, "linear": NYX_RS_LINEAR}.get(rs, rs)
     bat = kw.pop("batching", None)
     if bat is not None:
         p.batching = {"persistent": NYX_PERSISTENT, "per_box": NYX_PER_BOX}.get(bat, bat)
