@@ -66,6 +66,15 @@ class _Level(C.Structure):
                 ("dom_bc", C.POINTER(C.c_int))]
 
 
+class _PoissonParams(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_cycles", C.c_int), ("pre", C.c_int), ("post", C.c_int),
+                ("coarse_sweeps", C.c_int), ("min_size", C.c_int), ("four_pi_G", C.c_double)]
+
+
+class _PoissonStats(C.Structure):
+    _fields_ = [("cycles", C.c_int), ("resid", C.c_double), ("rho_mean", C.c_double)]
+
+
 class _Stats(C.Structure):
     _fields_ = [("floor_rho", C.c_longlong), ("floor_e", C.c_longlong),
                 ("use_e", C.c_longlong), ("bad", C.c_longlong)]
@@ -118,6 +127,10 @@ def load(path: str):
                                   C.POINTER(dp), C.POINTER(dp), C.POINTER(dp), C.c_double,
                                   C.c_double, C.c_double, C.POINTER(_Stats)]
         L.orc_correct.restype = C.c_int
+        L.orc_poisson_solve.argtypes = [C.POINTER(_Level), C.POINTER(_PoissonParams),
+                                        C.POINTER(dp), C.c_double, dp, C.POINTER(dp),
+                                        C.POINTER(_PoissonStats)]
+        L.orc_poisson_solve.restype = C.c_int
         L.orc_amr_check.argtypes = [C.POINTER(_Level), C.POINTER(_Level)]
         L.orc_amr_check.restype = C.c_int
         L.orc_amr_interp.argtypes = [C.POINTER(_Level), C.c_int, C.POINTER(dp), C.POINTER(_Level),
@@ -419,3 +432,42 @@ def amr_step(coarse, fine, params: OracleParams, cstate, fstate, cgrav=None, fgr
     if average_down:
         cn = amr_average_down(coarse, cn, fine, fn)
     return cn, fn, stc, stf
+
+
+# ---------------------------------------------------------------------------
+# Self-gravity (Sec. 3.4): periodic 7-point Poisson equation by multigrid.
+
+@dataclass
+class PoissonParams:
+    tol: float = 1e-12
+    max_cycles: int = 50
+    pre: int = 2
+    post: int = 2
+    coarse_sweeps: int = 40
+    min_size: int = 2
+    four_pi_G: float = 1.0
+
+    def _c(self):
+        return _PoissonParams(self.tol, self.max_cycles, self.pre, self.post, self.coarse_sweeps,
+                              self.min_size, self.four_pi_G)
+
+
+def poisson_solve(lev, params: PoissonParams, states, a: float, phi=None):
+    """Solve L phi = four_pi_G / a (rho - mean rho) on the dense periodic grid
+    of the level's single domain by V-cycles (red-black Gauss-Seidel), from
+    the initial guess phi (dense, (nz, ny, nx); zero if None).  Returns
+    (phi, grav, stats): grav per box (3 components, valid cells filled, ghosts
+    zero), g = -grad phi by centred differences."""
+    cl, keep = _level(lev)
+    n = (lev.dom_hi[0] - lev.dom_lo[0] + 1).astype(int)
+    ph = np.zeros((n[2], n[1], n[0])) if phi is None else np.array(phi, dtype=np.float64,
+                                                                     order="C", copy=True)
+    sin = [np.ascontiguousarray(s, dtype=np.float64) for s in states]
+    grav = [np.zeros(lev.shape(b, 3)) for b in range(lev.nbox)]
+    st = _PoissonStats()
+    p = params._c()
+    rc = lib().orc_poisson_solve(C.byref(cl), C.byref(p), _ptrs(sin), a, _dp(ph), _ptrs(grav),
+                                 C.byref(st))
+    if rc == -1:
+        raise ValueError("oracle Poisson: the level must tile one periodic domain with equal cells")
+    return ph, grav, dict(cycles=st.cycles, resid=st.resid, rho_mean=st.rho_mean, rc=rc)

@@ -1255,3 +1255,223 @@ int orc_amr_average_down(const orc_level *C, int ncomp, double *const *cstate,
   }
   return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Self-gravity, Sec. 3.4: the 7-point Laplacian on the cell centres of the
+ * periodic domain, solved by geometric multigrid (V-cycles with red-black
+ * Gauss-Seidel), tolerance 1e-12 by default, warm start from the previous
+ * potential; g the centred difference of phi.  The paper uses BoxLib's
+ * cell-centred multigrid without stating its transfer operators; reading:
+ * restriction = mean of the 8 fine cells, prolongation = the coarse value
+ * (piecewise constant), as in standard cell-centred multigrid.
+ *
+ * All sums run in a fixed order (rows, then planes, then the domain) so
+ * that a parallel code can reproduce them exactly. */
+typedef struct {
+  int n[3];
+  double h2, ih2;   /* dx^2 and 1/dx^2 at this grid */
+  double *phi, *f;
+} mg_grid;
+
+static size_t mg_idx(const mg_grid *g, int i, int j, int k) {
+  return ((size_t)k * g->n[1] + j) * g->n[0] + i;
+}
+
+static int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+static double mg_nbsum(const mg_grid *g, int i, int j, int k) {
+  const double *u = g->phi;
+  double s = u[mg_idx(g, wrapi(i - 1, g->n[0]), j, k)];
+  s = s + u[mg_idx(g, wrapi(i + 1, g->n[0]), j, k)];
+  s = s + u[mg_idx(g, i, wrapi(j - 1, g->n[1]), k)];
+  s = s + u[mg_idx(g, i, wrapi(j + 1, g->n[1]), k)];
+  s = s + u[mg_idx(g, i, j, wrapi(k - 1, g->n[2]))];
+  s = s + u[mg_idx(g, i, j, wrapi(k + 1, g->n[2]))];
+  return s;
+}
+
+/* one red-black Gauss-Seidel sweep: red cells (i+j+k even), then black */
+static void mg_sweep(mg_grid *g) {
+  for (int color = 0; color < 2; ++color) {
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 0; k < g->n[2]; ++k)
+      for (int j = 0; j < g->n[1]; ++j)
+        for (int i = (j + k + color) & 1; i < g->n[0]; i += 2) {
+          const size_t id = mg_idx(g, i, j, k);
+          g->phi[id] = (mg_nbsum(g, i, j, k) - g->h2 * g->f[id]) * SIXTH;
+        }
+  }
+}
+
+static double mg_resid(const mg_grid *g, int i, int j, int k) {
+  const size_t id = mg_idx(g, i, j, k);
+  return g->f[id] - (mg_nbsum(g, i, j, k) - 6.0 * g->phi[id]) * g->ih2;
+}
+
+static double mg_resid_max(const mg_grid *g) {
+  double m = 0.0;
+#pragma omp parallel for collapse(2) schedule(static) reduction(max : m)
+  for (int k = 0; k < g->n[2]; ++k)
+    for (int j = 0; j < g->n[1]; ++j)
+      for (int i = 0; i < g->n[0]; ++i) {
+        const double r = fabs(mg_resid(g, i, j, k));
+        if (r > m) m = r;
+      }
+  return m;
+}
+
+/* coarse f = mean of the 8 fine residuals; coarse phi = 0 */
+static void mg_restrict(const mg_grid *fg, mg_grid *cg) {
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int k = 0; k < cg->n[2]; ++k)
+    for (int j = 0; j < cg->n[1]; ++j)
+      for (int i = 0; i < cg->n[0]; ++i) {
+        double s = 0.0;
+        for (int o = 0; o < 8; ++o) {
+          const double r = mg_resid(fg, 2 * i + (o & 1), 2 * j + ((o >> 1) & 1), 2 * k + (o >> 2));
+          s = (o == 0) ? r : s + r;
+        }
+        const size_t id = mg_idx(cg, i, j, k);
+        cg->f[id] = 0.125 * s;
+        cg->phi[id] = 0.0;
+      }
+}
+
+static void mg_prolong_add(const mg_grid *cg, mg_grid *fg) {
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int k = 0; k < fg->n[2]; ++k)
+    for (int j = 0; j < fg->n[1]; ++j)
+      for (int i = 0; i < fg->n[0]; ++i) {
+        const size_t id = mg_idx(fg, i, j, k);
+        fg->phi[id] = fg->phi[id] + cg->phi[mg_idx(cg, i / 2, j / 2, k / 2)];
+      }
+}
+
+static void mg_vcycle(mg_grid *G, int l, int nl, const orc_poisson_params *p) {
+  if (l == nl - 1) {
+    for (int s = 0; s < p->coarse_sweeps; ++s) mg_sweep(&G[l]);
+    return;
+  }
+  for (int s = 0; s < p->pre; ++s) mg_sweep(&G[l]);
+  mg_restrict(&G[l], &G[l + 1]);
+  mg_vcycle(G, l + 1, nl, p);
+  mg_prolong_add(&G[l + 1], &G[l]);
+  for (int s = 0; s < p->post; ++s) mg_sweep(&G[l]);
+}
+
+int orc_poisson_solve(const orc_level *L, const orc_poisson_params *p, double *const *state,
+                      double a, double *phi, double *const *grav_out, orc_poisson_stats *st) {
+  if (L->ndom != 1) return -1;
+  const int *dlo = L->dom_lo, *dhi = L->dom_hi;
+  int n[3];
+  long long cells = 0;
+  for (int d = 0; d < 3; ++d) {
+    n[d] = dhi[d] - dlo[d] + 1;
+    if (n[d] % 2) return -1;
+    if (L->dom_bc[d] != ORC_BC_PERIODIC || L->dom_bc[3 + d] != ORC_BC_PERIODIC) return -1;
+  }
+  const double dx = L->dx[0];
+  for (int b = 0; b < L->nbox; ++b) {
+    for (int d = 0; d < 3; ++d)
+      if (L->dx[3 * b + d] != dx) return -1;
+    long long v = 1;
+    for (int d = 0; d < 3; ++d) v *= (L->hi[3 * b + d] - L->lo[3 * b + d] + 1);
+    cells += v;
+  }
+  if (cells != (long long)n[0] * n[1] * n[2]) return -1;
+  /* grid hierarchy */
+  mg_grid G[32];
+  int nl = 0;
+  {
+    int m[3] = {n[0], n[1], n[2]};
+    double h = dx;
+    for (;;) {
+      G[nl].n[0] = m[0];
+      G[nl].n[1] = m[1];
+      G[nl].n[2] = m[2];
+      G[nl].h2 = h * h;
+      G[nl].ih2 = 1.0 / (h * h);
+      size_t v = (size_t)m[0] * m[1] * m[2];
+      G[nl].phi = nl ? (double *)calloc(v, sizeof(double)) : phi;
+      G[nl].f = (double *)calloc(v, sizeof(double));
+      ++nl;
+      /* coarsen while the coarse extents stay even (a periodic red-black
+       * colouring needs even extents) and no smaller than min_size */
+      int ok = nl < 32;
+      for (int d = 0; d < 3; ++d)
+        if (m[d] % 4 || m[d] < 2 * p->min_size) ok = 0;
+      if (!ok) break;
+      for (int d = 0; d < 3; ++d) m[d] /= 2;
+      h *= 2.0;
+    }
+  }
+  /* gather rho into the dense right-hand side */
+  double *f0 = G[0].f;
+  for (int b = 0; b < L->nbox; ++b) {
+    geom_t g = make_geom(L->lo + 3 * b, L->hi + 3 * b, L->ng);
+    for (int k = 0; k < g.n[2]; ++k)
+      for (int j = 0; j < g.n[1]; ++j)
+        for (int i = 0; i < g.n[0]; ++i)
+          f0[mg_idx(&G[0], L->lo[3 * b] - dlo[0] + i, L->lo[3 * b + 1] - dlo[1] + j,
+                    L->lo[3 * b + 2] - dlo[2] + k)] = state[b][gidx(&g, i, j, k)];
+  }
+  /* mean density: rows, then planes, then the domain, each in index order */
+  double tot = 0.0;
+  for (int k = 0; k < n[2]; ++k) {
+    double plane = 0.0;
+    for (int j = 0; j < n[1]; ++j) {
+      double row = 0.0;
+      for (int i = 0; i < n[0]; ++i) {
+        const double v = f0[mg_idx(&G[0], i, j, k)];
+        row = (i == 0) ? v : row + v;
+      }
+      plane = (j == 0) ? row : plane + row;
+    }
+    tot = (k == 0) ? plane : tot + plane;
+  }
+  const double mean = tot / ((double)n[0] * n[1] * n[2]);
+  const double c = p->four_pi_G / a;
+  double fmax = 0.0;
+  for (size_t q = 0; q < (size_t)n[0] * n[1] * n[2]; ++q) {
+    f0[q] = c * (f0[q] - mean);
+    if (fabs(f0[q]) > fmax) fmax = fabs(f0[q]);
+  }
+  /* V-cycles */
+  int cyc = 0;
+  double res = mg_resid_max(&G[0]);
+  const double target = p->tol * fmax;
+  while (res > target && cyc < p->max_cycles) {
+    mg_vcycle(G, 0, nl, p);
+    ++cyc;
+    res = mg_resid_max(&G[0]);
+  }
+  /* g = -grad phi, centred differences */
+  const double hdx = 0.5 / dx;
+  for (int b = 0; b < L->nbox; ++b) {
+    geom_t g = make_geom(L->lo + 3 * b, L->hi + 3 * b, L->ng);
+    for (int k = 0; k < g.n[2]; ++k)
+      for (int j = 0; j < g.n[1]; ++j)
+        for (int i = 0; i < g.n[0]; ++i) {
+          const int I = L->lo[3 * b] - dlo[0] + i, J = L->lo[3 * b + 1] - dlo[1] + j,
+                    K = L->lo[3 * b + 2] - dlo[2] + k;
+          const double *u = phi;
+          const size_t id = gidx(&g, i, j, k);
+          grav_out[b][id] = -((u[mg_idx(&G[0], wrapi(I + 1, n[0]), J, K)] -
+                               u[mg_idx(&G[0], wrapi(I - 1, n[0]), J, K)]) * hdx);
+          grav_out[b][g.vol + id] = -((u[mg_idx(&G[0], I, wrapi(J + 1, n[1]), K)] -
+                                       u[mg_idx(&G[0], I, wrapi(J - 1, n[1]), K)]) * hdx);
+          grav_out[b][2 * g.vol + id] = -((u[mg_idx(&G[0], I, J, wrapi(K + 1, n[2]))] -
+                                           u[mg_idx(&G[0], I, J, wrapi(K - 1, n[2]))]) * hdx);
+        }
+  }
+  for (int l = 0; l < nl; ++l) {
+    if (l) free(G[l].phi);
+    free(G[l].f);
+  }
+  if (st) {
+    st->cycles = cyc;
+    st->resid = fmax > 0.0 ? res / fmax : 0.0;
+    st->rho_mean = mean;
+  }
+  return res <= target ? 0 : -4;
+}

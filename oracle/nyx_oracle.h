@@ -128,6 +128,34 @@ int orc_amr_reflux(const orc_level *C, double *const *cstate, double *const *cfl
 int orc_amr_average_down(const orc_level *C, int ncomp, double *const *cstate,
                          const orc_level *F, double *const *fstate);
 
+/* ---- self-gravity (Sec. 3.4): periodic 7-point Poisson, multigrid ------
+ * The level's boxes must tile one periodic domain (even extents) with equal
+ * cubic cells;
+ * the solve runs on the dense grid of the domain (x fastest).  RHS f =
+ * four_pi_G / a * (rho - mean rho) (no dark matter).  V-cycles with
+ * red-black Gauss-Seidel (red: i+j+k even, first), average restriction,
+ * piecewise-constant prolongation, a fixed number of sweeps on the
+ * coarsest grid; stop when max|f - L phi| <= tol max|f|.  phi (dense,
+ * in/out) is the initial guess (warm start) and the result; grav_out (per
+ * box, valid cells) receives g = -grad phi by centred differences. */
+typedef struct {
+  double tol;             /* relative max-norm residual, 1e-12 */
+  int max_cycles;         /* V-cycle cap */
+  int pre, post;          /* red-black sweeps before / after the coarse correction */
+  int coarse_sweeps;      /* sweeps on the coarsest grid */
+  int min_size;           /* coarsen while every extent is a multiple of 4 and >= 2 min_size */
+  double four_pi_G;       /* 4 pi G in code units */
+} orc_poisson_params;
+
+typedef struct {
+  int cycles;             /* V-cycles taken */
+  double resid;           /* final max|f - L phi| / max|f| */
+  double rho_mean;        /* the mean density subtracted */
+} orc_poisson_stats;
+
+int orc_poisson_solve(const orc_level *lev, const orc_poisson_params *p, double *const *state,
+                      double a, double *phi, double *const *grav_out, orc_poisson_stats *st);
+
 /* Unit-level entry points used by the pin tests. */
 void orc_ppm_line(int n, const double *s, double *sL, double *sR, double *s6);
 void orc_ppm_integrals(double sL, double sR, double s6, double sigma, double *ip, double *im);

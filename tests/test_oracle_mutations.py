@@ -12,6 +12,7 @@ import pytest
 import oracle
 import test_oracle_amr as ta
 import test_oracle_gravity as tg
+import test_oracle_poisson as tps
 import test_oracle_ppm as tp
 import test_oracle_riemann as tr
 import test_oracle_step as ts
@@ -79,6 +80,18 @@ MUTANTS = {
     "periodic wrap off by one": ("x = dlo[d] + ((x - dlo[d]) % len + len) % len;",
                                  "x = dlo[d] + ((x - dlo[d] + 1) % len + len) % len;",
                                  ts.test_ghost_fill_periodic_outflow_and_tiles, ()),
+    # self-gravity
+    "smoother weight 1/7": ("g->phi[id] = (mg_nbsum(g, i, j, k) - g->h2 * g->f[id]) * SIXTH;",
+                            "g->phi[id] = (mg_nbsum(g, i, j, k) - g->h2 * g->f[id]) / 7.0;",
+                            tps.test_single_mode_closed_form, ()),
+    "residual stencil centre 5": ("(mg_nbsum(g, i, j, k) - 6.0 * g->phi[id]) * g->ih2",
+                                  "(mg_nbsum(g, i, j, k) - 5.0 * g->phi[id]) * g->ih2",
+                                  tps.test_single_mode_closed_form, ()),
+    "coarse grid spacing not doubled": ("      h *= 2.0;", "      h *= 1.0;",
+                                        tps.test_residual_tolerance_warm_start_and_convergence_rate,
+                                        ()),
+    "gravity without the 1/2": ("const double hdx = 0.5 / dx;", "const double hdx = 1.0 / dx;",
+                                tps.test_single_mode_closed_form, ()),
     # PLM and the linearised solver
     "PLM edge at a quarter slope": ("*sRo = s[2] + 0.5 * d;", "*sRo = s[2] + 0.25 * d;",
                                     tv.test_plm_traced_density_closed_form, ()),
