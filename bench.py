@@ -476,6 +476,11 @@ def run_ours(args, w):
 # reads and writes the coarse cell (336 B per coarse face); average down reads
 # 8 fine cells and writes one coarse cell (432 B per coarse cell).
 AMR_BYTES = {"interp": 54, "reflux": 336, "avgdown": 432}
+# One V-cycle of the self-gravity solve per fine cell: 4 red-black sweeps
+# (read phi and f, write phi: 24 B each), the residual restriction (16 B), the
+# prolongation (24 B) and the residual norm (16 B), times 8/7 for the coarser
+# grids: 174 B.
+VCYCLE_BYTES_PER_CELL = 174
 
 
 def oracle_amr_sample(w, budget_s=12.0):
@@ -639,6 +644,29 @@ def run_amr(args, aw):
         gbs = AMR_BYTES[name] * units / (ms_k / 1e3) / 1e9
         coupling[name] = {"ms": ms_k, "units": units, "alg_bytes_per_unit": AMR_BYTES[name],
                           "achieved_gbs": gbs, "frac_hbm": gbs / peaks["hbm_gbs"]}
+    # self-gravity of the coarse level (one periodic 512^3 domain): a cold
+    # solve and a warm re-solve; the V-cycle cost is their difference per cycle
+    gravity = None
+    if not args.no_variants:
+        ps = H.Poisson(cp, four_pi_G=1.0)
+        gtmp = cp.empty_field(3)
+        ps.solve(lc.current, float(a_host[0]), gtmp, warm_start=False)   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cyc, res = ps.solve(lc.current, float(a_host[0]), gtmp, warm_start=False)
+        t_cold = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        cyc0, _ = ps.solve(lc.current, float(a_host[0]), gtmp, warm_start=True)
+        t_warm = time.perf_counter() - t0
+        per_cycle = (t_cold - t_warm) / max(1, cyc)
+        gbs = VCYCLE_BYTES_PER_CELL * cells_c / per_cycle / 1e9
+        gravity = {"cells": cells_c, "cold_solve_ms": t_cold * 1e3, "cycles": cyc,
+                   "relative_residual": res, "warm_resolve_ms": t_warm * 1e3,
+                   "warm_cycles": cyc0, "vcycle_ms": per_cycle * 1e3,
+                   "vcycle_alg_bytes_per_cell": VCYCLE_BYTES_PER_CELL,
+                   "achieved_gbs": gbs, "frac_hbm": gbs / peaks["hbm_gbs"], "bound": "hbm"}
+        ps.close()
+        del gtmp
     adv_ms = adv_c + adv_f
     flops = ALG_FLOPS_PER_ZONE[args.precision]
     peak_tf = PEAK_FP32_TFLOPS if args.precision == "mixed" else PEAK_FP64_TFLOPS
@@ -704,6 +732,7 @@ def run_amr(args, aw):
                           "ghost_fill_coarse": pc["fill_ms"] / max(1, pc["timed_fills"]),
                           "ghost_fill_fine": pf["fill_ms"] / max(1, pf["timed_fills"])},
             "coupling": coupling,
+            "self_gravity": gravity,
             "clocks": clk,
             "e2e": e2e,
             "gpu_launches": launches,

@@ -276,6 +276,50 @@ int nyx_hydro_estdt_noalloc(const nyx_level_desc *level, const nyx_hydro_params 
 /* Release the plan's device and host resources (not the caller's buffers). */
 int nyx_plan_destroy(nyx_plan *plan);
 
+/* ---------------------------------------------------------------- self-gravity
+ * The Poisson equation of Sec. 3.4 on one level that tiles a single periodic
+ * domain (even extents, equal cubic cells):
+ *     L phi = four_pi_G / a (rho - mean rho),
+ * L the 7-point Laplacian on cell centres, solved by geometric multigrid
+ * (V-cycles with red-black Gauss-Seidel: red cells i+j+k even first; mean
+ * restriction of the residual, piecewise-constant prolongation; coarsening
+ * while every extent is a multiple of 4 and >= 2 min_size; coarse_sweeps
+ * sweeps on the coarsest grid) until max|f - L phi| <= tol max|f|, then
+ * g = -grad phi by centred differences between adjacent cell centres.  The
+ * solve runs on the dense grid of the domain (gathered from the boxes); the
+ * object keeps phi for a warm start.  Dark matter is not included
+ * (rho is the gas density, component 0 of the state). */
+typedef struct nyx_poisson nyx_poisson;
+typedef struct {
+  double tol;         /* relative max-norm residual (1e-12) */
+  int max_cycles;     /* V-cycle cap (50) */
+  int pre, post;      /* red-black sweeps before / after the coarse correction (2, 2) */
+  int coarse_sweeps;  /* sweeps on the coarsest grid (40) */
+  int min_size;       /* smallest coarse extent (2) */
+  double four_pi_G;   /* 4 pi G in code units (1) */
+} nyx_poisson_params;
+
+void nyx_poisson_default_params(nyx_poisson_params *params);
+
+/* Check the plan's level and allocate the grids (about 2.3 doubles per
+ * cell).  NYX_EINVAL if the level cannot be solved this way. */
+int nyx_poisson_create(nyx_plan *plan, const nyx_poisson_params *params, nyx_poisson **out);
+
+/* Solve for the state (device field, 6 components, rho first) at scale
+ * factor a (host scalar) and write g into grav_out (device field of 3
+ * components, ghosts filled by the plan's fill).  warm_start != 0 starts
+ * from the previous phi, else from zero.  Synchronous: it reads the
+ * residual after every V-cycle.  *cycles_out, *resid_out (may be NULL):
+ * V-cycles taken and the final relative residual.  NYX_ETIMEOUT if
+ * max_cycles did not reach the tolerance (g is still written). */
+int nyx_poisson_solve(nyx_poisson *ps, const double *state, double a, double *grav_out,
+                      int warm_start, int *cycles_out, double *resid_out);
+
+/* Copy phi (dense, x fastest, domain extents) to a device buffer. */
+int nyx_poisson_phi(nyx_poisson *ps, double *phi_out);
+
+int nyx_poisson_destroy(nyx_poisson *ps);
+
 /* ---------------------------------------------------------------- two levels
  * Coarse-fine coupling of Sec. 4.1-4.3 for a refinement ratio of 2 and no
  * subcycling (both levels take the same dt, Sec. 4.2).

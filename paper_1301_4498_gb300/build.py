@@ -31,6 +31,7 @@ UNITS = {
     "nyx_fused_mixed.cu": ["--fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
     "nyx_noalloc.cu": [],
     "nyx_amr.cu": ["--fmad=false"],
+    "nyx_poisson.cu": ["--fmad=false"],
 }
 
 

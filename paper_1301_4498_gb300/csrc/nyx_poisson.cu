@@ -1,0 +1,435 @@
+// nyx_poisson.cu -- self-gravity of one level (Sec. 3.4): the periodic
+// 7-point Poisson equation L phi = 4 pi G / a (rho - mean rho) solved by
+// geometric multigrid (V-cycles with red-black Gauss-Seidel relaxation,
+// tolerance 1e-12 by default, warm start from the previous potential), then
+// g = -grad phi by centred differences between adjacent cell centres.
+//
+// One GPU holds the whole level, so the solve runs on the dense periodic
+// grid of its domain (gathered from the boxes): no ghost exchange between
+// boxes at any multigrid level.  Transfer operators (reading): restriction
+// = mean of the 8 fine residuals, prolongation = the coarse correction
+// (piecewise constant).  Every sum runs in a fixed order (rows, planes,
+// domain; the 8 children in index order) and the residual norm is a max,
+// so the result does not depend on scheduling.  FP64 throughout; this unit
+// is built without FMA contraction.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "nyx_hydro.h"
+#include "nyx_internal.cuh"
+#include "nyx_kernels.h"
+#include "nyx_plan.h"
+
+using namespace nyx;
+using namespace nyx::host;
+
+namespace {
+
+struct Dims {
+  int n[3];
+};
+
+__device__ __forceinline__ long long didx(const Dims &d, int i, int j, int k) {
+  return ((long long)k * d.n[1] + j) * d.n[0] + i;
+}
+__device__ __forceinline__ int wrp(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+__device__ __forceinline__ double nbsum(const double *u, const Dims &d, int i, int j, int k) {
+  double s = u[didx(d, wrp(i - 1, d.n[0]), j, k)];
+  s = s + u[didx(d, wrp(i + 1, d.n[0]), j, k)];
+  s = s + u[didx(d, i, wrp(j - 1, d.n[1]), k)];
+  s = s + u[didx(d, i, wrp(j + 1, d.n[1]), k)];
+  s = s + u[didx(d, i, j, wrp(k - 1, d.n[2]))];
+  s = s + u[didx(d, i, j, wrp(k + 1, d.n[2]))];
+  return s;
+}
+
+__device__ __forceinline__ double resid_at(const double *phi, const double *f, const Dims &d,
+                                           double ih2, int i, int j, int k) {
+  const long long id = didx(d, i, j, k);
+  return f[id] - (nbsum(phi, d, i, j, k) - 6.0 * phi[id]) * ih2;
+}
+
+// valid cell t of the level (box by binary search of the cell offsets)
+__device__ __forceinline__ void level_cell(const BoxDev *boxes, const long long *cell_pref,
+                                           int nbox, long long t, int &b, int &i, int &j,
+                                           int &k) {
+  int lo = 0, hi = nbox - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cell_pref[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  b = lo;
+  const BoxDev &X = boxes[lo];
+  const long long f = t - cell_pref[lo];
+  i = (int)(f % X.n[0]);
+  const long long u = f / X.n[0];
+  j = (int)(u % X.n[1]);
+  k = (int)(u / X.n[1]);
+}
+
+__global__ void k_pg_gather(const double *state, const BoxDev *boxes, const long long *cell_pref,
+                            const int *box_lo, int nbox, long long total, Dims d, double *f) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int b, i, j, k;
+    level_cell(boxes, cell_pref, nbox, t, b, i, j, k);
+    const BoxDev X = boxes[b];
+    f[didx(d, box_lo[3 * b] + i, box_lo[3 * b + 1] + j, box_lo[3 * b + 2] + k)] =
+        state[NCONS * X.pref + cell_index(X, i, j, k)];
+  }
+}
+
+// row sums (one thread per row, in index order), then plane sums, then the total
+__global__ void k_pg_rows(const double *f, Dims d, double *rows) {
+  const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= (long long)d.n[1] * d.n[2]) return;
+  const double *p = f + r * d.n[0];
+  double s = p[0];
+  for (int i = 1; i < d.n[0]; ++i) s = s + p[i];
+  rows[r] = s;
+}
+__global__ void k_pg_planes(const double *rows, Dims d, double *planes) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.n[2]) return;
+  const double *p = rows + (long long)k * d.n[1];
+  double s = p[0];
+  for (int j = 1; j < d.n[1]; ++j) s = s + p[j];
+  planes[k] = s;
+}
+__global__ void k_pg_mean(const double *planes, Dims d, double *mean) {
+  double s = planes[0];
+  for (int k = 1; k < d.n[2]; ++k) s = s + planes[k];
+  *mean = s / ((double)d.n[0] * d.n[1] * d.n[2]);
+}
+
+__global__ void k_pg_rhs(double *f, long long n, const double *mean, double c,
+                         unsigned long long *fmax_bits) {
+  const double m = *mean;
+  double loc = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const double v = c * (f[q] - m);
+    f[q] = v;
+    loc = fmax(loc, fabs(v));
+  }
+  for (int o = 16; o > 0; o >>= 1) loc = fmax(loc, __shfl_xor_sync(0xffffffffu, loc, o));
+  if ((threadIdx.x & 31) == 0)
+    atomicMax(fmax_bits, (unsigned long long)__double_as_longlong(loc));
+}
+
+// one colour of a red-black sweep: cells with (i + j + k) % 2 == color
+__global__ void k_pg_sweep(double *phi, const double *f, Dims d, double h2, int color) {
+  const int hx = d.n[0] / 2;
+  const long long n = (long long)hx * d.n[1] * d.n[2];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i2 = (int)(t % hx);
+    const long long u = t / hx;
+    const int j = (int)(u % d.n[1]);
+    const int k = (int)(u / d.n[1]);
+    const int i = 2 * i2 + ((j + k + color) & 1);
+    const long long id = didx(d, i, j, k);
+    phi[id] = (nbsum(phi, d, i, j, k) - h2 * f[id]) * (1.0 / 6.0);
+  }
+}
+
+__global__ void k_pg_resid_max(const double *phi, const double *f, Dims d, double ih2,
+                               unsigned long long *out) {
+  const long long n = (long long)d.n[0] * d.n[1] * d.n[2];
+  double loc = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % d.n[0]);
+    const long long u = t / d.n[0];
+    const int j = (int)(u % d.n[1]);
+    const int k = (int)(u / d.n[1]);
+    loc = fmax(loc, fabs(resid_at(phi, f, d, ih2, i, j, k)));
+  }
+  for (int o = 16; o > 0; o >>= 1) loc = fmax(loc, __shfl_xor_sync(0xffffffffu, loc, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(loc));
+}
+
+// coarse f = mean of the 8 fine residuals (index order), coarse phi = 0
+__global__ void k_pg_restrict(const double *phi, const double *f, Dims d, double ih2,
+                              double *fc, double *phic, Dims dc) {
+  const long long n = (long long)dc.n[0] * dc.n[1] * dc.n[2];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % dc.n[0]);
+    const long long u = t / dc.n[0];
+    const int j = (int)(u % dc.n[1]);
+    const int k = (int)(u / dc.n[1]);
+    double s = 0.0;
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      const double r =
+          resid_at(phi, f, d, ih2, 2 * i + (o & 1), 2 * j + ((o >> 1) & 1), 2 * k + (o >> 2));
+      s = (o == 0) ? r : s + r;
+    }
+    fc[t] = 0.125 * s;
+    phic[t] = 0.0;
+  }
+}
+
+__global__ void k_pg_prolong(double *phi, Dims d, const double *phic, Dims dc) {
+  const long long n = (long long)d.n[0] * d.n[1] * d.n[2];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % d.n[0]);
+    const long long u = t / d.n[0];
+    const int j = (int)(u % d.n[1]);
+    const int k = (int)(u / d.n[1]);
+    phi[t] = phi[t] + phic[didx(dc, i / 2, j / 2, k / 2)];
+  }
+}
+
+// g = -grad phi (centred) into the level's gravity field, valid cells
+__global__ void k_pg_grav(const double *u, Dims d, double hdx, const BoxDev *boxes,
+                          const long long *cell_pref, const int *box_lo, int nbox,
+                          long long total, double *grav) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int b, i, j, k;
+    level_cell(boxes, cell_pref, nbox, t, b, i, j, k);
+    const BoxDev X = boxes[b];
+    const int I = box_lo[3 * b] + i, J = box_lo[3 * b + 1] + j, K = box_lo[3 * b + 2] + k;
+    double *G = grav + NGRAV * X.pref + cell_index(X, i, j, k);
+    G[0] = -((u[didx(d, wrp(I + 1, d.n[0]), J, K)] - u[didx(d, wrp(I - 1, d.n[0]), J, K)]) * hdx);
+    G[X.stride] =
+        -((u[didx(d, I, wrp(J + 1, d.n[1]), K)] - u[didx(d, I, wrp(J - 1, d.n[1]), K)]) * hdx);
+    G[2 * X.stride] =
+        -((u[didx(d, I, J, wrp(K + 1, d.n[2]))] - u[didx(d, I, J, wrp(K - 1, d.n[2]))]) * hdx);
+  }
+}
+
+int gridn(long long n, int block) {
+  long long g = (n + block - 1) / block;
+  return (int)std::max<long long>(1, std::min<long long>(g, 152 * 32));
+}
+
+struct Level {
+  Dims d;
+  double h2, ih2;
+  double *phi = nullptr, *f = nullptr;
+};
+
+}  // namespace
+
+struct nyx_poisson {
+  nyx_plan *P = nullptr;
+  nyx_poisson_params prm{};
+  std::vector<Level> L;
+  int *d_box_lo = nullptr;       // box lo relative to the domain origin
+  double *d_rows = nullptr, *d_planes = nullptr, *d_scal = nullptr;  // scal: mean
+  unsigned long long *d_max = nullptr;
+  double dx = 0.0;
+  long long launches = 0;
+};
+
+namespace {
+
+void free_poisson(nyx_poisson *S) {
+  if (!S) return;
+  for (auto &l : S->L) {
+    if (l.phi) cudaFree(l.phi);
+    if (l.f) cudaFree(l.f);
+  }
+  cudaFree(S->d_box_lo);
+  cudaFree(S->d_rows);
+  cudaFree(S->d_planes);
+  cudaFree(S->d_scal);
+  cudaFree(S->d_max);
+  delete S;
+}
+
+int read_max(nyx_poisson *S, double *out) {
+  unsigned long long v = 0;
+  CK(cudaMemcpyAsync(&v, S->d_max, sizeof(v), cudaMemcpyDeviceToHost, S->P->stream));
+  CK(cudaStreamSynchronize(S->P->stream));
+  std::memcpy(out, &v, sizeof(double));
+  return NYX_OK;
+}
+
+void sweep(nyx_poisson *S, Level &l) {
+  const long long n = (long long)(l.d.n[0] / 2) * l.d.n[1] * l.d.n[2];
+  for (int c = 0; c < 2; ++c)
+    k_pg_sweep<<<gridn(n, 256), 256, 0, S->P->stream>>>(l.phi, l.f, l.d, l.h2, c);
+  S->launches += 2;
+}
+
+void vcycle(nyx_poisson *S, size_t l) {
+  Level &g = S->L[l];
+  if (l + 1 == S->L.size()) {
+    for (int s = 0; s < S->prm.coarse_sweeps; ++s) sweep(S, g);
+    return;
+  }
+  for (int s = 0; s < S->prm.pre; ++s) sweep(S, g);
+  Level &c = S->L[l + 1];
+  const long long nc = (long long)c.d.n[0] * c.d.n[1] * c.d.n[2];
+  k_pg_restrict<<<gridn(nc, 256), 256, 0, S->P->stream>>>(g.phi, g.f, g.d, g.ih2, c.f, c.phi, c.d);
+  S->launches += 1;
+  vcycle(S, l + 1);
+  const long long nf = (long long)g.d.n[0] * g.d.n[1] * g.d.n[2];
+  k_pg_prolong<<<gridn(nf, 256), 256, 0, S->P->stream>>>(g.phi, g.d, c.phi, c.d);
+  S->launches += 1;
+  for (int s = 0; s < S->prm.post; ++s) sweep(S, g);
+}
+
+int resid_max(nyx_poisson *S, double *out) {
+  Level &g = S->L[0];
+  CK(cudaMemsetAsync(S->d_max, 0, sizeof(unsigned long long), S->P->stream));
+  const long long n = (long long)g.d.n[0] * g.d.n[1] * g.d.n[2];
+  k_pg_resid_max<<<gridn(n, 256), 256, 0, S->P->stream>>>(g.phi, g.f, g.d, g.ih2, S->d_max);
+  S->launches += 1;
+  return read_max(S, out);
+}
+
+}  // namespace
+
+extern "C" {
+
+void nyx_poisson_default_params(nyx_poisson_params *p) {
+  if (!p) return;
+  p->tol = 1e-12;
+  p->max_cycles = 50;
+  p->pre = 2;
+  p->post = 2;
+  p->coarse_sweeps = 40;
+  p->min_size = 2;
+  p->four_pi_G = 1.0;
+}
+
+int nyx_poisson_create(nyx_plan *P, const nyx_poisson_params *prm, nyx_poisson **out) {
+  if (!P || !prm || !out) return fail(NYX_EINVAL, "null argument");
+  *out = nullptr;
+  if (P->doms.size() != 1) return fail(NYX_EINVAL, "the Poisson solve needs a one-domain level");
+  const nyx_domain &D = P->doms[0];
+  int n[3];
+  for (int a = 0; a < 3; ++a) {
+    n[a] = D.hi[a] - D.lo[a] + 1;
+    if (n[a] % 2) return fail(NYX_EINVAL, "the Poisson solve needs even domain extents");
+    if (D.bc[a] != NYX_BC_PERIODIC || D.bc[3 + a] != NYX_BC_PERIODIC)
+      return fail(NYX_EINVAL, "the Poisson solve needs a periodic domain");
+  }
+  const double dx = P->boxes[0].dx[0];
+  for (const nyx_box &X : P->boxes)
+    for (int a = 0; a < 3; ++a)
+      if (X.dx[a] != dx) return fail(NYX_EINVAL, "the Poisson solve needs equal cubic cells");
+  if (P->total_cells != (long long)n[0] * n[1] * n[2])
+    return fail(NYX_EINVAL, "the level's boxes must tile its domain");
+  if (prm->pre < 0 || prm->post < 0 || prm->coarse_sweeps < 1 || prm->max_cycles < 0 ||
+      prm->min_size < 1 || !(prm->tol > 0.0))
+    return fail(NYX_EINVAL, "bad Poisson parameters");
+  nyx_poisson *S = new nyx_poisson;
+  S->P = P;
+  S->prm = *prm;
+  S->dx = dx;
+  int m[3] = {n[0], n[1], n[2]};
+  double h = dx;
+  int rc = NYX_OK;
+  for (;;) {
+    Level l;
+    for (int a = 0; a < 3; ++a) l.d.n[a] = m[a];
+    l.h2 = h * h;
+    l.ih2 = 1.0 / (h * h);
+    const size_t v = (size_t)m[0] * m[1] * m[2];
+    if (cudaMalloc(&l.phi, v * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&l.f, v * sizeof(double)) != cudaSuccess) {
+      S->L.push_back(l);
+      rc = fail(NYX_ENOMEM, "Poisson grid allocation failed");
+      break;
+    }
+    cudaMemset(l.phi, 0, v * sizeof(double));
+    S->L.push_back(l);
+    bool ok = S->L.size() < 32;
+    for (int a = 0; a < 3; ++a)
+      if (m[a] % 4 || m[a] < 2 * prm->min_size) ok = false;
+    if (!ok) break;
+    for (int a = 0; a < 3; ++a) m[a] /= 2;
+    h *= 2.0;
+  }
+  if (!rc) {
+    std::vector<int> lo(3 * P->nbox);
+    for (int b = 0; b < P->nbox; ++b)
+      for (int a = 0; a < 3; ++a) lo[3 * b + a] = P->boxes[b].lo[a] - D.lo[a];
+    if (cudaMalloc(&S->d_box_lo, lo.size() * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&S->d_rows, sizeof(double) * (size_t)n[1] * n[2]) != cudaSuccess ||
+        cudaMalloc(&S->d_planes, sizeof(double) * n[2]) != cudaSuccess ||
+        cudaMalloc(&S->d_scal, sizeof(double) * 2) != cudaSuccess ||
+        cudaMalloc(&S->d_max, sizeof(unsigned long long)) != cudaSuccess)
+      rc = fail(NYX_ENOMEM, "Poisson scratch allocation failed");
+    else if (cudaMemcpy(S->d_box_lo, lo.data(), lo.size() * sizeof(int), cudaMemcpyHostToDevice) !=
+             cudaSuccess)
+      rc = fail(NYX_ECUDA, "Poisson table upload failed");
+  }
+  if (rc) {
+    free_poisson(S);
+    return rc;
+  }
+  *out = S;
+  return NYX_OK;
+}
+
+int nyx_poisson_solve(nyx_poisson *S, const double *state, double a, double *grav_out,
+                      int warm_start, int *cycles_out, double *resid_out) {
+  if (!S || !state || !grav_out || !(a > 0.0)) return fail(NYX_EINVAL, "bad argument");
+  nyx_plan &P = *S->P;
+  Level &g0 = S->L[0];
+  const long long N = (long long)g0.d.n[0] * g0.d.n[1] * g0.d.n[2];
+  cudaStream_t st = P.stream;
+  if (!warm_start) CK(cudaMemsetAsync(g0.phi, 0, N * sizeof(double), st));
+  k_pg_gather<<<gridn(P.total_cells, 256), 256, 0, st>>>(state, P.d_boxes, P.d_cell_pref,
+                                                        S->d_box_lo, P.nbox, P.total_cells, g0.d,
+                                                        g0.f);
+  const long long nrow = (long long)g0.d.n[1] * g0.d.n[2];
+  k_pg_rows<<<gridn(nrow, 128), 128, 0, st>>>(g0.f, g0.d, S->d_rows);
+  k_pg_planes<<<gridn(g0.d.n[2], 128), 128, 0, st>>>(S->d_rows, g0.d, S->d_planes);
+  k_pg_mean<<<1, 1, 0, st>>>(S->d_planes, g0.d, S->d_scal);
+  CK(cudaMemsetAsync(S->d_max, 0, sizeof(unsigned long long), st));
+  k_pg_rhs<<<gridn(N, 256), 256, 0, st>>>(g0.f, N, S->d_scal, S->prm.four_pi_G / a, S->d_max);
+  S->launches += 5;
+  double fmax = 0.0, res = 0.0;
+  int rc = read_max(S, &fmax);
+  if (rc) return rc;
+  if ((rc = resid_max(S, &res))) return rc;
+  const double target = S->prm.tol * fmax;
+  int cyc = 0;
+  while (res > target && cyc < S->prm.max_cycles) {
+    vcycle(S, 0);
+    ++cyc;
+    if ((rc = resid_max(S, &res))) return rc;
+  }
+  k_pg_grav<<<gridn(P.total_cells, 256), 256, 0, st>>>(g0.phi, g0.d, 0.5 / S->dx, P.d_boxes,
+                                                      P.d_cell_pref, S->d_box_lo, P.nbox,
+                                                      P.total_cells, grav_out);
+  S->launches += 1;
+  plan_fill(&P, grav_out, NGRAV);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "Poisson launch");
+  P.launches += S->launches;
+  S->launches = 0;
+  if (cycles_out) *cycles_out = cyc;
+  if (resid_out) *resid_out = fmax > 0.0 ? res / fmax : 0.0;
+  if (res > target) return fail(NYX_ETIMEOUT, "Poisson solve did not reach the tolerance");
+  return NYX_OK;
+}
+
+int nyx_poisson_phi(nyx_poisson *S, double *phi_out) {
+  if (!S || !phi_out) return fail(NYX_EINVAL, "null argument");
+  Level &g0 = S->L[0];
+  const size_t N = (size_t)g0.d.n[0] * g0.d.n[1] * g0.d.n[2];
+  CK(cudaMemcpyAsync(phi_out, g0.phi, N * sizeof(double), cudaMemcpyDeviceToDevice, S->P->stream));
+  return NYX_OK;
+}
+
+int nyx_poisson_destroy(nyx_poisson *S) {
+  free_poisson(S);
+  return NYX_OK;
+}
+
+}  // extern "C"

@@ -130,7 +130,6 @@ __device__ __forceinline__ void trace_cell(const Eos<R> &E, const R (&s)[5][5], 
                                            R (&qm)[5], R (&qp)[5]) {
   constexpr int NV = 1 + DIR;
   R sL[5], sR[5], s6[5];
-#pragma unroll
   if (E.plm) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) plm_coeffs(s[v][1], s[v][2], s[v][3], sL[v], sR[v], s6[v]);

@@ -68,6 +68,11 @@ class NyxParams(C.Structure):
                 ("riemann_solver", C.c_int)]
 
 
+class NyxPoissonParams(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_cycles", C.c_int), ("pre", C.c_int), ("post", C.c_int),
+                ("coarse_sweeps", C.c_int), ("min_size", C.c_int), ("four_pi_G", C.c_double)]
+
+
 class NyxLevel(C.Structure):
     _fields_ = [("state", C.c_void_p * 2), ("grav", C.c_void_p), ("cur", C.c_int)]
 
@@ -118,6 +123,15 @@ def load_library(path: str | None = None):
     L.nyx_hydro_counters_read.argtypes = [vp, C.c_int, C.POINTER(NyxCounters)]
     L.nyx_hydro_estdt_noalloc.argtypes = [C.POINTER(NyxLevelDesc), C.POINTER(NyxParams), vp, vp,
                                           vp, vp]
+    L.nyx_poisson_default_params.argtypes = [C.POINTER(NyxPoissonParams)]
+    L.nyx_poisson_default_params.restype = None
+    L.nyx_poisson_create.argtypes = [vp, C.POINTER(NyxPoissonParams), C.POINTER(vp)]
+    L.nyx_poisson_solve.argtypes = [vp, vp, C.c_double, vp, C.c_int, ip, dp]
+    L.nyx_poisson_phi.argtypes = [vp, vp]
+    L.nyx_poisson_destroy.argtypes = [vp]
+    for name in ("nyx_poisson_create", "nyx_poisson_solve", "nyx_poisson_phi",
+                 "nyx_poisson_destroy"):
+        getattr(L, name).restype = C.c_int
     L.nyx_amr_create.argtypes = [vp, vp, C.POINTER(vp)]
     L.nyx_amr_interp.argtypes = [vp, vp, vp, C.c_int, C.c_int]
     L.nyx_amr_reflux.argtypes = [vp, vp]
@@ -411,6 +425,53 @@ def estdt_noalloc(spec, state, a_dev, dt_dev, stream=None, **params):
         stream = torch.cuda.current_stream().cuda_stream
     _check(load_library().nyx_hydro_estdt_noalloc(C.byref(desc), C.byref(p), _ptr(state),
                                                    _ptr(a_dev), _ptr(dt_dev), C.c_void_p(stream)))
+
+
+class Poisson:
+    """Self-gravity of a plan's level (nyx_poisson_*): periodic multigrid
+    Poisson solve on the dense grid of its domain, g = -grad phi."""
+
+    def __init__(self, plan: "Plan", **params):
+        self.lib = load_library()
+        self.plan = plan
+        p = NyxPoissonParams()
+        self.lib.nyx_poisson_default_params(C.byref(p))
+        for k, v in params.items():
+            setattr(p, k, v)
+        self.params = p
+        h = C.c_void_p()
+        _check(self.lib.nyx_poisson_create(plan.h, C.byref(p), C.byref(h)))
+        self.h = h
+        n = plan.spec.dom_hi[0] - plan.spec.dom_lo[0] + 1
+        self.shape = (int(n[2]), int(n[1]), int(n[0]))
+
+    def solve(self, state, a, grav_out, warm_start=True):
+        """Returns (cycles, relative residual)."""
+        cyc = C.c_int()
+        res = C.c_double()
+        with self.plan.ordered():
+            _check(self.lib.nyx_poisson_solve(self.h, _ptr(state), float(a), _ptr(grav_out),
+                                              1 if warm_start else 0, C.byref(cyc),
+                                              C.byref(res)))
+        return cyc.value, res.value
+
+    def phi(self):
+        import torch
+        out = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        with self.plan.ordered():
+            _check(self.lib.nyx_poisson_phi(self.h, _ptr(out)))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.nyx_poisson_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Amr:
