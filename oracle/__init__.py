@@ -128,9 +128,23 @@ def load(path: str):
                                   C.c_double, C.c_double, C.POINTER(_Stats)]
         L.orc_correct.restype = C.c_int
         L.orc_poisson_solve.argtypes = [C.POINTER(_Level), C.POINTER(_PoissonParams),
-                                        C.POINTER(dp), C.c_double, dp, C.POINTER(dp),
+                                        C.POINTER(dp), dp, C.c_double, dp, C.POINTER(dp), dp,
                                         C.POINTER(_PoissonStats)]
         L.orc_poisson_solve.restype = C.c_int
+        ip3 = C.POINTER(C.c_int)
+        L.orc_pm_deposit.argtypes = [ip3, C.c_double, dp, dp, C.c_longlong, dp]
+        L.orc_pm_deposit.restype = None
+        L.orc_pm_interp.argtypes = [ip3, C.c_double, dp, dp, C.c_longlong, dp]
+        L.orc_pm_interp.restype = None
+        L.orc_pm_kick_drift.argtypes = [ip3, C.c_double, dp, dp, dp, C.c_longlong, C.c_double,
+                                        C.c_double, C.c_double]
+        L.orc_pm_kick_drift.restype = None
+        L.orc_pm_kick.argtypes = [ip3, C.c_double, dp, dp, dp, C.c_longlong, C.c_double,
+                                  C.c_double, C.c_double]
+        L.orc_pm_kick.restype = None
+        L.orc_pm_estdt.argtypes = [ip3, C.c_double, dp, dp, dp, C.c_longlong, C.c_double,
+                                   C.c_double]
+        L.orc_pm_estdt.restype = C.c_double
         L.orc_amr_check.argtypes = [C.POINTER(_Level), C.POINTER(_Level)]
         L.orc_amr_check.restype = C.c_int
         L.orc_amr_interp.argtypes = [C.POINTER(_Level), C.c_int, C.POINTER(dp), C.POINTER(_Level),
@@ -452,22 +466,81 @@ class PoissonParams:
                               self.min_size, self.four_pi_G)
 
 
-def poisson_solve(lev, params: PoissonParams, states, a: float, phi=None):
-    """Solve L phi = four_pi_G / a (rho - mean rho) on the dense periodic grid
-    of the level's single domain by V-cycles (red-black Gauss-Seidel), from
-    the initial guess phi (dense, (nz, ny, nx); zero if None).  Returns
-    (phi, grav, stats): grav per box (3 components, valid cells filled, ghosts
-    zero), g = -grad phi by centred differences."""
+def poisson_solve(lev, params: PoissonParams, states, a: float, phi=None, rho_dm=None,
+                  want_dense_g=False):
+    """Solve L phi = four_pi_G / a (rho_b + rho_dm - mean) on the dense
+    periodic grid of the level's single domain by V-cycles (red-black
+    Gauss-Seidel), from the initial guess phi (dense, (nz, ny, nx); zero if
+    None).  rho_dm: dense dark-matter density or None.  Returns (phi, grav,
+    stats) -- grav per box (3 components, valid cells filled, ghosts zero),
+    g = -grad phi by centred differences -- plus the dense g (3, nz, ny, nx)
+    when want_dense_g."""
     cl, keep = _level(lev)
     n = (lev.dom_hi[0] - lev.dom_lo[0] + 1).astype(int)
     ph = np.zeros((n[2], n[1], n[0])) if phi is None else np.array(phi, dtype=np.float64,
                                                                      order="C", copy=True)
     sin = [np.ascontiguousarray(s, dtype=np.float64) for s in states]
     grav = [np.zeros(lev.shape(b, 3)) for b in range(lev.nbox)]
+    rd = None if rho_dm is None else np.ascontiguousarray(rho_dm, dtype=np.float64)
+    gd = np.zeros((3, n[2], n[1], n[0])) if want_dense_g else None
     st = _PoissonStats()
     p = params._c()
-    rc = lib().orc_poisson_solve(C.byref(cl), C.byref(p), _ptrs(sin), a, _dp(ph), _ptrs(grav),
-                                 C.byref(st))
+    rc = lib().orc_poisson_solve(C.byref(cl), C.byref(p), _ptrs(sin),
+                                 None if rd is None else _dp(rd), a, _dp(ph), _ptrs(grav),
+                                 None if gd is None else _dp(gd), C.byref(st))
     if rc == -1:
         raise ValueError("oracle Poisson: the level must tile one periodic domain with equal cells")
-    return ph, grav, dict(cycles=st.cycles, resid=st.resid, rho_mean=st.rho_mean, rc=rc)
+    out = (ph, grav, dict(cycles=st.cycles, resid=st.resid, rho_mean=st.rho_mean, rc=rc))
+    return out + (gd,) if want_dense_g else out
+
+
+# ---------------------------------------------------------------------------
+# Dark matter (Sec. 3.3-3.6): particles on a dense periodic grid of n cells of
+# width dx per axis (positions in [0, n dx)); x, u of shape (3, np), m (np,).
+
+def _n3(n):
+    return (C.c_int * 3)(int(n[0]), int(n[1]), int(n[2]))
+
+
+def pm_deposit(n, dx, x, m):
+    """Cloud-in-cell density (nz, ny, nx) of the particles (Sec. 3.4)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    rho = np.zeros((n[2], n[1], n[0]))
+    lib().orc_pm_deposit(_n3(n), dx, _dp(x), _dp(m), m.shape[0], _dp(rho))
+    return rho
+
+
+def pm_interp(n, dx, g, x):
+    """g (3, nz, ny, nx) at the particles by the cloud-in-cell weights."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    out = np.zeros_like(x)
+    lib().orc_pm_interp(_n3(n), dx, _dp(g), _dp(x), x.shape[1], _dp(out))
+    return out
+
+
+def pm_kick_drift(n, dx, g, x, u, *, a_old, a_half, dt):
+    """Step 3 on copies: returns (x^{n+1}, u^{n+1/2})."""
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    x = np.array(x, dtype=np.float64, order="C", copy=True)
+    u = np.array(u, dtype=np.float64, order="C", copy=True)
+    lib().orc_pm_kick_drift(_n3(n), dx, _dp(g), _dp(x), _dp(u), x.shape[1], a_old, a_half, dt)
+    return x, u
+
+
+def pm_kick(n, dx, g, x, u, *, a_half, a_new, dt):
+    """Step 5 on a copy: returns u^{n+1}."""
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    u = np.array(u, dtype=np.float64, order="C", copy=True)
+    lib().orc_pm_kick(_n3(n), dx, _dp(g), _dp(x), _dp(u), x.shape[1], a_half, a_new, dt)
+    return u
+
+
+def pm_estdt(n, dx, g, x, u, a, cfl_dm=0.5):
+    """Particle time step of Sec. 3.5."""
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    return float(lib().orc_pm_estdt(_n3(n), dx, _dp(g), _dp(x), _dp(u), x.shape[1], a, cfl_dm))

@@ -1360,7 +1360,8 @@ static void mg_vcycle(mg_grid *G, int l, int nl, const orc_poisson_params *p) {
 }
 
 int orc_poisson_solve(const orc_level *L, const orc_poisson_params *p, double *const *state,
-                      double a, double *phi, double *const *grav_out, orc_poisson_stats *st) {
+                      const double *rho_dm, double a, double *phi, double *const *grav_out,
+                      double *g_dense, orc_poisson_stats *st) {
   if (L->ndom != 1) return -1;
   const int *dlo = L->dom_lo, *dhi = L->dom_hi;
   int n[3];
@@ -1415,6 +1416,9 @@ int orc_poisson_solve(const orc_level *L, const orc_poisson_params *p, double *c
           f0[mg_idx(&G[0], L->lo[3 * b] - dlo[0] + i, L->lo[3 * b + 1] - dlo[1] + j,
                     L->lo[3 * b + 2] - dlo[2] + k)] = state[b][gidx(&g, i, j, k)];
   }
+  /* dark matter (Sec. 3.4): rho_b + rho_dm */
+  if (rho_dm)
+    for (size_t q = 0; q < (size_t)n[0] * n[1] * n[2]; ++q) f0[q] = f0[q] + rho_dm[q];
   /* mean density: rows, then planes, then the domain, each in index order */
   double tot = 0.0;
   for (int k = 0; k < n[2]; ++k) {
@@ -1447,7 +1451,22 @@ int orc_poisson_solve(const orc_level *L, const orc_poisson_params *p, double *c
   }
   /* g = -grad phi, centred differences */
   const double hdx = 0.5 / dx;
-  for (int b = 0; b < L->nbox; ++b) {
+  if (g_dense) {
+    const size_t N = (size_t)n[0] * n[1] * n[2];
+    for (int K = 0; K < n[2]; ++K)
+      for (int J = 0; J < n[1]; ++J)
+        for (int I = 0; I < n[0]; ++I) {
+          const double *u = phi;
+          const size_t id = mg_idx(&G[0], I, J, K);
+          g_dense[id] = -((u[mg_idx(&G[0], wrapi(I + 1, n[0]), J, K)] -
+                           u[mg_idx(&G[0], wrapi(I - 1, n[0]), J, K)]) * hdx);
+          g_dense[N + id] = -((u[mg_idx(&G[0], I, wrapi(J + 1, n[1]), K)] -
+                               u[mg_idx(&G[0], I, wrapi(J - 1, n[1]), K)]) * hdx);
+          g_dense[2 * N + id] = -((u[mg_idx(&G[0], I, J, wrapi(K + 1, n[2]))] -
+                                   u[mg_idx(&G[0], I, J, wrapi(K - 1, n[2]))]) * hdx);
+        }
+  }
+  for (int b = 0; grav_out && b < L->nbox; ++b) {
     geom_t g = make_geom(L->lo + 3 * b, L->hi + 3 * b, L->ng);
     for (int k = 0; k < g.n[2]; ++k)
       for (int j = 0; j < g.n[1]; ++j)
@@ -1474,4 +1493,123 @@ int orc_poisson_solve(const orc_level *L, const orc_poisson_params *p, double *c
     st->rho_mean = mean;
   }
   return res <= target ? 0 : -4;
+}
+
+
+/* ------------------------------------------------------------------ */
+/* Dark matter as particles (Sec. 3.3, 3.4, 3.5, 3.6 Steps 3 and 5) on the
+ * dense periodic grid of n[0] x n[1] x n[2] cells of width dx, positions in
+ * [0, n dx) per axis (cell I spans [I dx, (I+1) dx)).
+ *
+ * Cloud in cell: a particle is a cube of side dx centred on it; the cells it
+ * overlaps get its mass in proportion to the overlap, divided by dx^3.  The
+ * same weights interpolate g from the cell centres to the particle (Sec. 3.3:
+ * linear interpolation from cell centres), which with the centred-difference
+ * g makes the self-force vanish (Sec. 3.4). */
+static void cic_weights(double x, double dx, int n, int *i0, double *w0) {
+  const double s = x / dx - 0.5;
+  const double fl = floor(s);
+  *w0 = 1.0 - (s - fl);      /* weight of cell i0; i0 + 1 gets 1 - w0 */
+  int i = (int)fl;
+  *i0 = wrapi(i, n);
+}
+
+void orc_pm_deposit(const int n[3], double dx, const double *x, const double *m, long long np,
+                    double *rho) {
+  const size_t N = (size_t)n[0] * n[1] * n[2];
+  for (size_t q = 0; q < N; ++q) rho[q] = 0.0;
+  const double iv = 1.0 / (dx * dx * dx);
+  for (long long p = 0; p < np; ++p) {
+    int i0[3];
+    double w0[3];
+    for (int d = 0; d < 3; ++d) cic_weights(x[d * np + p], dx, n[d], &i0[d], &w0[d]);
+    for (int o = 0; o < 8; ++o) {
+      const int I = (o & 1) ? wrapi(i0[0] + 1, n[0]) : i0[0];
+      const int J = ((o >> 1) & 1) ? wrapi(i0[1] + 1, n[1]) : i0[1];
+      const int K = (o >> 2) ? wrapi(i0[2] + 1, n[2]) : i0[2];
+      const double w = ((o & 1) ? 1.0 - w0[0] : w0[0]) * (((o >> 1) & 1) ? 1.0 - w0[1] : w0[1]) *
+                       ((o >> 2) ? 1.0 - w0[2] : w0[2]);
+      const size_t id = ((size_t)K * n[1] + J) * n[0] + I;
+      rho[id] = rho[id] + m[p] * w * iv;
+    }
+  }
+}
+
+/* g at a particle: the cloud-in-cell weights of its position */
+static void pm_g_at(const int n[3], double dx, const double *g, const double xp[3], double out[3]) {
+  const size_t N = (size_t)n[0] * n[1] * n[2];
+  int i0[3];
+  double w0[3];
+  for (int d = 0; d < 3; ++d) cic_weights(xp[d], dx, n[d], &i0[d], &w0[d]);
+  for (int c = 0; c < 3; ++c) out[c] = 0.0;
+  for (int o = 0; o < 8; ++o) {
+    const int I = (o & 1) ? wrapi(i0[0] + 1, n[0]) : i0[0];
+    const int J = ((o >> 1) & 1) ? wrapi(i0[1] + 1, n[1]) : i0[1];
+    const int K = (o >> 2) ? wrapi(i0[2] + 1, n[2]) : i0[2];
+    const double w = ((o & 1) ? 1.0 - w0[0] : w0[0]) * (((o >> 1) & 1) ? 1.0 - w0[1] : w0[1]) *
+                     ((o >> 2) ? 1.0 - w0[2] : w0[2]);
+    const size_t id = ((size_t)K * n[1] + J) * n[0] + I;
+    for (int c = 0; c < 3; ++c) out[c] = out[c] + w * g[c * N + id];
+  }
+}
+
+void orc_pm_interp(const int n[3], double dx, const double *g, const double *x, long long np,
+                   double *gp) {
+  for (long long p = 0; p < np; ++p) {
+    double xp[3] = {x[p], x[np + p], x[2 * np + p]}, o[3];
+    pm_g_at(n, dx, g, xp, o);
+    for (int c = 0; c < 3; ++c) gp[c * np + p] = o[c];
+  }
+}
+
+/* Step 3: u^{n+1/2} = (a^n u^n + dt/2 g^n) / a^{n+1/2}; x^{n+1} = x^n +
+ * dt / a^{n+1/2} u^{n+1/2}, wrapped into the periodic domain. */
+void orc_pm_kick_drift(const int n[3], double dx, const double *g, double *x, double *u,
+                       long long np, double a_old, double a_half, double dt) {
+  const double L[3] = {n[0] * dx, n[1] * dx, n[2] * dx};
+  for (long long p = 0; p < np; ++p) {
+    double xp[3] = {x[p], x[np + p], x[2 * np + p]}, gp[3];
+    pm_g_at(n, dx, g, xp, gp);
+    for (int c = 0; c < 3; ++c) {
+      const double uh = (a_old * u[c * np + p] + 0.5 * dt * gp[c]) / a_half;
+      u[c * np + p] = uh;
+      double xn = xp[c] + dt / a_half * uh;
+      if (xn < 0.0) xn = xn + L[c];
+      if (xn >= L[c]) xn = xn - L[c];
+      x[c * np + p] = xn;
+    }
+  }
+}
+
+/* Step 5: u^{n+1} = (a^{n+1/2} u^{n+1/2} + dt/2 g^{n+1}) / a^{n+1}. */
+void orc_pm_kick(const int n[3], double dx, const double *g, const double *x, double *u,
+                 long long np, double a_half, double a_new, double dt) {
+  for (long long p = 0; p < np; ++p) {
+    double xp[3] = {x[p], x[np + p], x[2 * np + p]}, gp[3];
+    pm_g_at(n, dx, g, xp, gp);
+    for (int c = 0; c < 3; ++c) u[c * np + p] = (a_half * u[c * np + p] + 0.5 * dt * gp[c]) / a_new;
+  }
+}
+
+/* Sec. 3.5: dt_dm = cfl_dm min_d a dx / max_j |u_j,d|, and g_j dt^2 < dx:
+ * dt_dm <= sqrt(dx / max_j |g_j,d|) (reading: per component, g at the
+ * particle by cloud in cell).  Returns +inf for resting particles in no field. */
+double orc_pm_estdt(const int n[3], double dx, const double *g, const double *x, const double *u,
+                    long long np, double a, double cfl_dm) {
+  double umax = 0.0, gmax = 0.0;
+  for (long long p = 0; p < np; ++p) {
+    double xp[3] = {x[p], x[np + p], x[2 * np + p]}, gp[3];
+    pm_g_at(n, dx, g, xp, gp);
+    for (int c = 0; c < 3; ++c) {
+      if (fabs(u[c * np + p]) > umax) umax = fabs(u[c * np + p]);
+      if (fabs(gp[c]) > gmax) gmax = fabs(gp[c]);
+    }
+  }
+  double dt = INFINITY;
+  if (umax > 0.0) dt = cfl_dm * (a * dx / umax);
+  if (gmax > 0.0) {
+    const double dg = sqrt(dx / gmax);
+    if (dg < dt) dt = dg;
+  }
+  return dt;
 }

@@ -137,7 +137,8 @@ int orc_amr_average_down(const orc_level *C, int ncomp, double *const *cstate,
  * piecewise-constant prolongation, a fixed number of sweeps on the
  * coarsest grid; stop when max|f - L phi| <= tol max|f|.  phi (dense,
  * in/out) is the initial guess (warm start) and the result; grav_out (per
- * box, valid cells) receives g = -grad phi by centred differences. */
+ * box, valid cells; may be NULL) receives g = -grad phi by centred
+ * differences.  rho_dm (dense, may be NULL) is added to the gas density. */
 typedef struct {
   double tol;             /* relative max-norm residual, 1e-12 */
   int max_cycles;         /* V-cycle cap */
@@ -154,7 +155,25 @@ typedef struct {
 } orc_poisson_stats;
 
 int orc_poisson_solve(const orc_level *lev, const orc_poisson_params *p, double *const *state,
-                      double a, double *phi, double *const *grav_out, orc_poisson_stats *st);
+                      const double *rho_dm, double a, double *phi, double *const *grav_out,
+                      double *g_dense, orc_poisson_stats *st);
+
+/* ---- dark matter (Sec. 3.3-3.6): particles on the dense periodic grid --
+ * n cells of width dx per axis, positions in [0, n dx); SoA arrays x[3*np],
+ * u[3*np] (comoving position, peculiar proper velocity), m[np]; dense
+ * fields x fastest, g as 3 consecutive dense arrays.  rho_dm (optional in
+ * orc_poisson_solve) is added to rho_b on the right-hand side; g_dense
+ * (optional) receives g on the dense grid for the particles. */
+void orc_pm_deposit(const int n[3], double dx, const double *x, const double *m, long long np,
+                    double *rho);
+void orc_pm_interp(const int n[3], double dx, const double *g, const double *x, long long np,
+                   double *gp);
+void orc_pm_kick_drift(const int n[3], double dx, const double *g, double *x, double *u,
+                       long long np, double a_old, double a_half, double dt);
+void orc_pm_kick(const int n[3], double dx, const double *g, const double *x, double *u,
+                 long long np, double a_half, double a_new, double dt);
+double orc_pm_estdt(const int n[3], double dx, const double *g, const double *x, const double *u,
+                    long long np, double a, double cfl_dm);
 
 /* Unit-level entry points used by the pin tests. */
 void orc_ppm_line(int n, const double *s, double *sL, double *sR, double *s6);

@@ -518,3 +518,27 @@ def scale_valid(arrays, factors, ng: int = NG) -> list:
         valid(a, ng)[...] *= f[None]
         out.append(a)
     return out
+
+
+# ---------------------------------------------------------------------------
+# dark-matter particles (seeded; positions in [0, n dx) per axis)
+
+def dm_particles(n, dx, per_axis=None, seed=17, disp=0.3, vel_rms=0.05, mass_total=5.0):
+    """Particles on a lattice of per_axis^3 points (default: one per cell)
+    at the lattice cell centres, each displaced by a uniform random offset of
+    up to disp lattice spacings per axis, with Gaussian velocities of rms
+    vel_rms per component and equal masses summing to mass_total (times the
+    domain volume).  Returns (x (3, np), u (3, np), m (np,))."""
+    rng = np.random.default_rng(seed)
+    n = np.asarray(n, dtype=np.int64)
+    per = n if per_axis is None else np.asarray([per_axis] * 3, dtype=np.int64)
+    L = n * dx
+    sp = L / per
+    grids = np.meshgrid(*(np.arange(int(per[d])) for d in range(3)), indexing="ij")
+    base = np.stack([(grids[d].ravel() + 0.5) * sp[d] for d in range(3)])
+    x = base + disp * sp[:, None] * rng.uniform(-1.0, 1.0, size=base.shape)
+    x = np.mod(x, L[:, None])
+    u = vel_rms * rng.standard_normal(size=x.shape)
+    npart = x.shape[1]
+    m = np.full(npart, mass_total * float(np.prod(L)) / npart)
+    return np.ascontiguousarray(x), np.ascontiguousarray(u), m

@@ -12,6 +12,7 @@ import pytest
 import oracle
 import test_oracle_amr as ta
 import test_oracle_gravity as tg
+import test_oracle_pm as tpm
 import test_oracle_poisson as tps
 import test_oracle_ppm as tp
 import test_oracle_riemann as tr
@@ -80,6 +81,16 @@ MUTANTS = {
     "periodic wrap off by one": ("x = dlo[d] + ((x - dlo[d]) % len + len) % len;",
                                  "x = dlo[d] + ((x - dlo[d] + 1) % len + len) % len;",
                                  ts.test_ghost_fill_periodic_outflow_and_tiles, ()),
+    # dark matter
+    "cloud-in-cell weights swapped": ("  *w0 = 1.0 - (s - fl);", "  *w0 = s - fl;",
+                                      tpm.test_deposit_centre_and_corner, ()),
+    "deposit without 1/dx^3": ("      rho[id] = rho[id] + m[p] * w * iv;", "      rho[id] = rho[id] + m[p] * w;",
+                               tpm.test_deposit_conserves_mass, ()),
+    "kick with the whole dt": ("const double uh = (a_old * u[c * np + p] + 0.5 * dt * gp[c]) / a_half;",
+                               "const double uh = (a_old * u[c * np + p] + dt * gp[c]) / a_half;",
+                               tpm.test_kdk_uniform_field_at_unit_scale_factor, ()),
+    "drift divided by a_old": ("double xn = xp[c] + dt / a_half * uh;", "double xn = xp[c] + dt / a_old * uh;",
+                               tpm.test_free_streaming_under_expansion_and_periodic_wrap, ()),
     # self-gravity
     "smoother weight 1/7": ("g->phi[id] = (mg_nbsum(g, i, j, k) - g->h2 * g->f[id]) * SIXTH;",
                             "g->phi[id] = (mg_nbsum(g, i, j, k) - g->h2 * g->f[id]) / 7.0;",
