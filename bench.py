@@ -43,6 +43,9 @@ CORRECT_BYTES_PER_ZONE = 168
 # subtraction).  FP64 division and square root run at a small fraction of the
 # FP32 rate here; measured FP64 instruction rate: 0.506e12 per second.
 CORRECT_FP64_FLOPS_PER_ZONE = 44
+# 4 pi G of the self-gravity workloads in code units (mean density 1, sound
+# speed 1, box length 1): a free-fall time of order the sound crossing time.
+COSMO_FOUR_PI_G = 1.0
 FP64_INSTR_TPS = 0.506
 # Algorithmic floating-point operations per zone-update (+ - * / sqrt counted
 # once each, comparisons not counted): 3196 for primitives, PPM + tracing in 3
@@ -97,6 +100,10 @@ def make_workload(name: str, sample_only: bool = False):
         return W.amr_large(nsteps=100)
     if name == "amr128":  # the same structure on a 128^3 domain (profiling case)
         return W.amr_large(n=128, box=32, nfine=6, nsteps=100)
+    if name == "cosmo":  # gas + dark matter + self-gravity on the 512^3 level (Steps 1-6)
+        return W.cosmo_level(n=64 if sample_only else 512, box=32, nsteps=100)
+    if name == "cosmo128":
+        return W.cosmo_level(n=128, box=32, nsteps=100)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -744,6 +751,206 @@ def run_amr(args, aw):
     cp.close()
 
 
+# ---------------------------------------------------------------------- self-gravity + dark matter
+
+def oracle_cosmo_step(w, P, PP, cs, x, u, m, phi, a0, a1, gd0=None):
+    """One step of the single-level algorithm with gas, dark matter and
+    self-gravity on the oracle (Steps 1-6; Step 1 from scratch when gd0 is
+    None).  Returns (state, x, u, phi, dense g at t^{n+1})."""
+    import oracle
+    n = tuple(int(v) for v in (w.level.dom_hi[0] - w.level.dom_lo[0] + 1))
+    dx = float(w.level.dx[0][0])
+    ah = 0.5 * (a0 + a1)
+    rho0 = oracle.pm_deposit(n, dx, x, m)
+    phi, gl0, _, gd0 = oracle.poisson_solve(w.level, PP, cs, a0, phi, rho_dm=rho0,
+                                            want_dense_g=True)
+    oracle.fill_ghosts(w.level, gl0)
+    dt = min(oracle.estdt(w.level, P, cs, a0), oracle.pm_estdt(n, dx, gd0, x, u, a0))
+    pred, _ = oracle.predict(w.level, P, cs, gl0, a_old=a0, a_new=a1, dt=dt)
+    x1, uh = oracle.pm_kick_drift(n, dx, gd0, x, u, a_old=a0, a_half=ah, dt=dt)
+    rho1 = oracle.pm_deposit(n, dx, x1, m)
+    phi, gl1, _, gd1 = oracle.poisson_solve(w.level, PP, pred, a1, phi, rho_dm=rho1,
+                                            want_dense_g=True)
+    oracle.fill_ghosts(w.level, gl1)
+    u1 = oracle.pm_kick(n, dx, gd1, x1, uh, a_half=ah, a_new=a1, dt=dt)
+    new, _ = oracle.correct(w.level, P, cs, pred, gl0, gl1, a_old=a0, a_new=a1, dt=dt)
+    return new, x1, u1, phi, gd1
+
+
+def oracle_cosmo_sample(budget_s=12.0):
+    """The oracle's full step on a 64^3 sample (gas + 64^3 particles)."""
+    import oracle
+    w = make_workload("cosmo", sample_only=True)
+    x, u, m = w.level.meta["dm"]
+    P = oracle.OracleParams(gamma=w.gamma, cfl=w.cfl)
+    PP = oracle.PoissonParams(four_pi_G=COSMO_FOUR_PI_G)
+    cs, phi = w.state, None
+    a0, a1 = float(w.a_sched[0]), float(w.a_sched[1])
+    elapsed, steps = 0.0, 0
+    while elapsed < budget_s:
+        t0 = time.perf_counter()
+        cs, x, u, phi, _ = oracle_cosmo_step(w, P, PP, cs, x, u, m, phi, a0, a1)
+        elapsed += time.perf_counter() - t0
+        steps += 1
+    cells = w.level.valid_cells()
+    return {"value": cells * steps / elapsed, "unit": "zone-updates/s", "cores": os.cpu_count(),
+            "kind": "oracle", "elapsed_s": elapsed / steps,
+            "sample": f"{steps} step(s) of gas + dark matter + self-gravity on a 64^3 level "
+                      f"(8 boxes of 32^3, {m.size} particles), FP64 oracle, OpenMP on all host "
+                      f"cores; {elapsed:.1f} s"}
+
+
+def run_reference_cosmo(args, w):
+    ws, rank, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    per = []
+    info = None
+    for s in range(args.warmup + args.steps):
+        r = oracle_cosmo_sample(budget_s=args.ref_budget)
+        if s >= args.warmup:
+            per.append(r)
+        info = r
+    value = statistics.median(x["value"] for x in per)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "zone-updates/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": statistics.median(x["elapsed_s"] for x in per) * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": args.workload, "level": w.name, "sample": info["sample"]},
+           "cpu_baseline": {"value": value, "unit": "zone-updates/s", "cores": info["cores"],
+                            "kind": "oracle", "sample": info["sample"]},
+           "e2e": {"value": value, "unit": "zone-updates/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_cosmo(args, w):
+    """The single-level algorithm with gas, dark matter and self-gravity
+    (Sec. 3.6 Steps 1-6): per step the particle and gas time steps, the gas
+    predictor with g^n, kick-drift, deposit at x^{n+1}, the Poisson solve on
+    rho_b^{n+1,*} + rho_dm^{n+1} (warm start), kick, the gas corrector with
+    g^{n+1}; g^n of the next step is this step's g^{n+1} (Step 1 shortcut).
+    Host-driven: the solve reads its residual after every V-cycle."""
+    import torch
+    from paper_1301_4498_gb300 import hydro as H
+    ws, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    peaks, peak_src = load_peaks()
+    K, Wm = args.steps, args.warmup
+    cells = w.level.valid_cells()
+    x, u, m = w.level.meta["dm"]
+    npart = m.size
+    plan = H.Plan(w.level, gamma=w.gamma, cfl=w.cfl, precision=args.precision,
+                  batching="persistent", autotune=1 if args.autotune else 0)
+    if args.tile_shape >= 0:
+        plan.set_tile_shape(args.tile_shape)
+    lev = H.make_level(plan, w.state, None)
+    ps = H.Poisson(plan, four_pi_G=COSMO_FOUR_PI_G)
+    xd, ud, md = (torch.tensor(v, device="cuda") for v in (x, u, m))
+    rho = ps.dense(1)[0]
+    gd = ps.dense(3)
+    g_old, g_new = plan.empty_field(3), plan.empty_field(3)
+    a_host = a_schedule_for(w, Wm + K + 1)
+    a = torch.tensor(a_host, dtype=torch.float64, device="cuda")
+    dts = torch.zeros(3, dtype=torch.float64, device="cuda")
+    stream = plan.torch_stream
+    # Step 1 of the first step: g^0 from scratch
+    ps.pm_deposit(xd, md, rho)
+    ps.solve(lev.current, float(a_host[0]), g_old, warm_start=False, rho_dm=rho, g_dense=gd)
+    timing = {"gas_advance": 0.0, "particles": 0.0, "solve": 0.0, "corrector": 0.0}
+    cyc_total = 0
+
+    def step(s, record):
+        nonlocal g_old, g_new, cyc_total
+        a0, a1 = float(a_host[s]), float(a_host[s + 1])
+        ah = 0.5 * (a0 + a1)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        plan.estdt(lev, a[s:s + 1], dts[0:1])
+        ps.pm_estdt(xd, ud, gd, a0, dts[1:2])
+        torch.minimum(dts[0:1], dts[1:2], out=dts[2:3])
+        dt = float(dts[2].item())
+        ev[0].record(stream)
+        plan.predict(lev, a[s:s + 1], a[s + 1:s + 2], dts[2:3], g_old)
+        ev[1].record(stream)
+        ps.pm_kick_drift(xd, ud, gd, a0, ah, dt)
+        ps.pm_deposit(xd, md, rho)
+        ev[2].record(stream)
+        cyc, _ = ps.solve(lev.state[1 - lev.cur], a1, g_new, warm_start=True, rho_dm=rho,
+                          g_dense=gd)
+        ev[3].record(stream)
+        ps.pm_kick(xd, ud, gd, ah, a1, dt)
+        ev[4].record(stream)
+        plan.correct(lev, a[s:s + 1], a[s + 1:s + 2], dts[2:3], g_old, g_new)
+        ev[5].record(stream)
+        g_old, g_new = g_new, g_old
+        if record:
+            torch.cuda.synchronize()
+            timing["gas_advance"] += ev[0].elapsed_time(ev[1])
+            timing["particles"] += ev[1].elapsed_time(ev[2]) + ev[3].elapsed_time(ev[4])
+            timing["solve"] += ev[2].elapsed_time(ev[3])
+            timing["corrector"] += ev[4].elapsed_time(ev[5])
+            cyc_total += cyc
+
+    for s in range(Wm):
+        step(s, False)
+    torch.cuda.synchronize()
+    rc, flags = plan.status()
+    if rc != H.NYX_OK:
+        raise SystemExit(f"device status after warm-up: {rc} flags {flags}")
+    plan.counters(reset=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(Wm, Wm + K):
+        step(s, True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    launches = plan.counters(reset=True)["launches"]
+    ms_max = max_over_ranks(ms, ws)
+    value = ws * cells * K / (ms_max / 1e3)
+    adv_ms = timing["gas_advance"] / K
+    flops = ALG_FLOPS_PER_ZONE[args.precision]
+    peak_tf = PEAK_FP32_TFLOPS if args.precision == "mixed" else PEAK_FP64_TFLOPS
+    achieved_tf = flops * cells / (adv_ms / 1e3) / 1e12
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = oracle_cosmo_sample(budget_s=args.cpu_budget)
+        cpu.pop("elapsed_s", None)
+    shape, (tx, ty) = plan.tile_shape()
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "zone-updates/s", "n_gpus": ws,
+            "steps": K, "warmup": Wm, "ms_per_step": ms_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "level": w.name, "valid_cells": cells,
+                       "particles": npart, "boxes": w.level.nbox, "precision": args.precision,
+                       "step": "Sec. 3.6 Steps 1-6 (g^n from the previous Step 4)",
+                       "tile": [tx, ty], "l2": "inputs larger than L2",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+            "particle_updates_per_s": ws * npart * K / (ms_max / 1e3),
+            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf,
+                         "unit": "TFLOP/s", "frac": achieved_tf / peak_tf, "traffic": None,
+                         "kernel": "fused gas predictor (k_fused2)", "kernel_ms": adv_ms,
+                         "alg_flops_per_zone": flops, "peak_source": "unit counts x 2070 MHz"},
+            "breakdown_ms_per_step": {k: v / K for k, v in timing.items()},
+            "poisson_cycles_per_step": cyc_total / K,
+            "clocks": clk, "e2e": None, "gpu_launches": launches, "cpu_baseline": cpu,
+        }
+        print(json.dumps(out), flush=True)
+    ps.close()
+    plan.close()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -752,7 +959,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="large",
                     choices=["large", "large128", "comoving128", "uneven512", "uneven64", "mixed256",
-                             "sod", "amr", "amr128"])
+                             "sod", "amr", "amr128", "cosmo", "cosmo128"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--tile-shape", type=int, default=-1,
@@ -772,7 +979,12 @@ def main(argv=None):
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     w = make_workload(args.workload, sample_only=args.impl == "reference")
-    if isinstance(w, W.AmrWorkload):
+    if "dm" in w.level.meta if hasattr(w, "level") else False:
+        if args.impl == "reference":
+            run_reference_cosmo(args, w)
+        else:
+            run_cosmo(args, w)
+    elif isinstance(w, W.AmrWorkload):
         if args.impl == "reference":
             run_reference_amr(args, w)
         else:

@@ -305,15 +305,42 @@ void nyx_poisson_default_params(nyx_poisson_params *params);
  * cell).  NYX_EINVAL if the level cannot be solved this way. */
 int nyx_poisson_create(nyx_plan *plan, const nyx_poisson_params *params, nyx_poisson **out);
 
-/* Solve for the state (device field, 6 components, rho first) at scale
- * factor a (host scalar) and write g into grav_out (device field of 3
- * components, ghosts filled by the plan's fill).  warm_start != 0 starts
- * from the previous phi, else from zero.  Synchronous: it reads the
- * residual after every V-cycle.  *cycles_out, *resid_out (may be NULL):
- * V-cycles taken and the final relative residual.  NYX_ETIMEOUT if
- * max_cycles did not reach the tolerance (g is still written). */
-int nyx_poisson_solve(nyx_poisson *ps, const double *state, double a, double *grav_out,
-                      int warm_start, int *cycles_out, double *resid_out);
+/* Solve for the state (device field, 6 components, rho first) plus rho_dm
+ * (dense device grid of the domain, x fastest; NULL = no dark matter) at
+ * scale factor a (host scalar).  grav_out (may be NULL): device level field
+ * of 3 components receiving g, ghosts filled by the plan's fill.
+ * g_dense_out (may be NULL): 3 consecutive dense grids receiving g (for the
+ * particles).  warm_start != 0 starts from the previous phi, else from
+ * zero.  Synchronous: it reads the residual after every V-cycle.
+ * *cycles_out, *resid_out (may be NULL): V-cycles taken and the final
+ * relative residual.  NYX_ETIMEOUT if max_cycles did not reach the
+ * tolerance (g is still written). */
+int nyx_poisson_solve(nyx_poisson *ps, const double *state, const double *rho_dm, double a,
+                      double *grav_out, double *g_dense_out, int warm_start, int *cycles_out,
+                      double *resid_out);
+
+/* Dark matter as particles (Sec. 3.3-3.6) on the dense periodic grid of a
+ * nyx_poisson object (n cells of width dx per axis; positions in [0, n dx)).
+ * Device SoA arrays: x[3 np] (comoving positions), u[3 np] (peculiar proper
+ * velocities), m[np].  Cloud in cell: a particle is a cube of side dx; the
+ * 8 cells it overlaps get its mass in proportion to the overlap / dx^3, and
+ * the same weights interpolate g to it (no self-force with the centred g).
+ *  - deposit: rho_dm (dense) = the particles' density (zeroed first;
+ *    floating-point atomics, so the summation order is not fixed);
+ *  - kick_drift (Step 3): u = (a_old u + dt/2 g^n(x)) / a_half, then
+ *    x += dt u / a_half, wrapped into the domain (one period at most);
+ *  - kick (Step 5): u = (a_half u + dt/2 g^{n+1}(x)) / a_new;
+ *  - estdt (Sec. 3.5): *dt_dev = min(cfl_dm a dx / max |u_d|,
+ *    sqrt(dx / max |g_d|)) over the particles (+inf if both maxima are 0).
+ * Stream-ordered on the plan's stream; scalars are host doubles. */
+int nyx_pm_deposit(nyx_poisson *ps, const double *x, const double *m, long long np,
+                   double *rho_dm);
+int nyx_pm_kick_drift(nyx_poisson *ps, double *x, double *u, long long np, const double *g_dense,
+                      double a_old, double a_half, double dt);
+int nyx_pm_kick(nyx_poisson *ps, const double *x, double *u, long long np, const double *g_dense,
+                double a_half, double a_new, double dt);
+int nyx_pm_estdt(nyx_poisson *ps, const double *x, const double *u, long long np,
+                 const double *g_dense, double a, double cfl_dm, double *dt_dev);
 
 /* Copy phi (dense, x fastest, domain extents) to a device buffer. */
 int nyx_poisson_phi(nyx_poisson *ps, double *phi_out);

@@ -84,6 +84,153 @@ __global__ void k_pg_gather(const double *state, const BoxDev *boxes, const long
   }
 }
 
+__global__ void k_pg_add(double *f, const double *r, long long n) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x)
+    f[q] = f[q] + r[q];
+}
+
+// g = -grad phi on the dense grid (3 consecutive dense arrays)
+__global__ void k_pg_grav_dense(const double *u, Dims d, double hdx, double *g) {
+  const long long n = (long long)d.n[0] * d.n[1] * d.n[2];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int I = (int)(t % d.n[0]);
+    const long long v = t / d.n[0];
+    const int J = (int)(v % d.n[1]);
+    const int K = (int)(v / d.n[1]);
+    g[t] = -((u[didx(d, wrp(I + 1, d.n[0]), J, K)] - u[didx(d, wrp(I - 1, d.n[0]), J, K)]) * hdx);
+    g[n + t] =
+        -((u[didx(d, I, wrp(J + 1, d.n[1]), K)] - u[didx(d, I, wrp(J - 1, d.n[1]), K)]) * hdx);
+    g[2 * n + t] =
+        -((u[didx(d, I, J, wrp(K + 1, d.n[2]))] - u[didx(d, I, J, wrp(K - 1, d.n[2]))]) * hdx);
+  }
+}
+
+// ---------------------------------------------------------------- dark matter
+// Cloud in cell (Sec. 3.4): cell-centred coordinate s = x/dx - 1/2, the
+// particle's cube overlaps cells floor(s) (weight 1 - frac(s)) and floor(s)+1.
+__device__ __forceinline__ void cic(double x, double dx, int n, int &i0, double &w0) {
+  const double s = x / dx - 0.5;
+  const double fl = floor(s);
+  w0 = 1.0 - (s - fl);
+  i0 = wrp((int)fl, n);
+}
+
+__device__ __forceinline__ void g_at(const double *g, const Dims &d, double dx, double x0,
+                                     double x1, double x2, double (&out)[3]) {
+  const long long N = (long long)d.n[0] * d.n[1] * d.n[2];
+  int i0, j0, k0;
+  double wx, wy, wz;
+  cic(x0, dx, d.n[0], i0, wx);
+  cic(x1, dx, d.n[1], j0, wy);
+  cic(x2, dx, d.n[2], k0, wz);
+  out[0] = out[1] = out[2] = 0.0;
+#pragma unroll
+  for (int o = 0; o < 8; ++o) {
+    const int I = (o & 1) ? wrp(i0 + 1, d.n[0]) : i0;
+    const int J = ((o >> 1) & 1) ? wrp(j0 + 1, d.n[1]) : j0;
+    const int K = (o >> 2) ? wrp(k0 + 1, d.n[2]) : k0;
+    const double w = ((o & 1) ? 1.0 - wx : wx) * (((o >> 1) & 1) ? 1.0 - wy : wy) *
+                     ((o >> 2) ? 1.0 - wz : wz);
+    const long long id = didx(d, I, J, K);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out[c] = out[c] + w * g[c * N + id];
+  }
+}
+
+__global__ void k_pm_deposit(const double *x, const double *m, long long np, Dims d, double dx,
+                             double iv, double *rho) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np;
+       p += (long long)gridDim.x * blockDim.x) {
+    int i0, j0, k0;
+    double wx, wy, wz;
+    cic(x[p], dx, d.n[0], i0, wx);
+    cic(x[np + p], dx, d.n[1], j0, wy);
+    cic(x[2 * np + p], dx, d.n[2], k0, wz);
+    const double mp = m[p];
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      const int I = (o & 1) ? wrp(i0 + 1, d.n[0]) : i0;
+      const int J = ((o >> 1) & 1) ? wrp(j0 + 1, d.n[1]) : j0;
+      const int K = (o >> 2) ? wrp(k0 + 1, d.n[2]) : k0;
+      const double w = ((o & 1) ? 1.0 - wx : wx) * (((o >> 1) & 1) ? 1.0 - wy : wy) *
+                       ((o >> 2) ? 1.0 - wz : wz);
+      atomicAdd(&rho[didx(d, I, J, K)], mp * w * iv);
+    }
+  }
+}
+
+// Step 3: kick by dt/2 with g^n, drift by dt at a^{n+1/2}, periodic wrap
+__global__ void k_pm_kick_drift(double *x, double *u, long long np, const double *g, Dims d,
+                                double dx, double a_old, double a_half, double dt) {
+  const double L[3] = {d.n[0] * dx, d.n[1] * dx, d.n[2] * dx};
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np;
+       p += (long long)gridDim.x * blockDim.x) {
+    double gp[3];
+    const double xp[3] = {x[p], x[np + p], x[2 * np + p]};
+    g_at(g, d, dx, xp[0], xp[1], xp[2], gp);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double uh = (a_old * u[c * np + p] + 0.5 * dt * gp[c]) / a_half;
+      u[c * np + p] = uh;
+      double xn = xp[c] + dt / a_half * uh;
+      if (xn < 0.0) xn = xn + L[c];
+      if (xn >= L[c]) xn = xn - L[c];
+      x[c * np + p] = xn;
+    }
+  }
+}
+
+// Step 5: kick by dt/2 with g^{n+1}
+__global__ void k_pm_kick(const double *x, double *u, long long np, const double *g, Dims d,
+                          double dx, double a_half, double a_new, double dt) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np;
+       p += (long long)gridDim.x * blockDim.x) {
+    double gp[3];
+    g_at(g, d, dx, x[p], x[np + p], x[2 * np + p], gp);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u[c * np + p] = (a_half * u[c * np + p] + 0.5 * dt * gp[c]) / a_new;
+  }
+}
+
+// Sec. 3.5: maxima of |u_d| and |g_d| at the particles (ordered bits)
+__global__ void k_pm_maxes(const double *x, const double *u, long long np, const double *g,
+                           Dims d, double dx, unsigned long long *mx) {
+  double um = 0.0, gm = 0.0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np;
+       p += (long long)gridDim.x * blockDim.x) {
+    double gp[3];
+    g_at(g, d, dx, x[p], x[np + p], x[2 * np + p], gp);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      um = fmax(um, fabs(u[c * np + p]));
+      gm = fmax(gm, fabs(gp[c]));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    um = fmax(um, __shfl_xor_sync(0xffffffffu, um, o));
+    gm = fmax(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&mx[0], (unsigned long long)__double_as_longlong(um));
+    atomicMax(&mx[1], (unsigned long long)__double_as_longlong(gm));
+  }
+}
+
+__global__ void k_pm_dt(const unsigned long long *mx, double a, double dx, double cfl_dm,
+                        double *dt_out) {
+  const double um = __longlong_as_double((long long)mx[0]);
+  const double gm = __longlong_as_double((long long)mx[1]);
+  double dt = __longlong_as_double(0x7ff0000000000000LL);
+  if (um > 0.0) dt = cfl_dm * (a * dx / um);
+  if (gm > 0.0) {
+    const double dg = sqrt(dx / gm);
+    if (dg < dt) dt = dg;
+  }
+  *dt_out = dt;
+}
+
 // row sums (one thread per row, in index order), then plane sums, then the total
 __global__ void k_pg_rows(const double *f, Dims d, double *rows) {
   const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -361,7 +508,7 @@ int nyx_poisson_create(nyx_plan *P, const nyx_poisson_params *prm, nyx_poisson *
         cudaMalloc(&S->d_rows, sizeof(double) * (size_t)n[1] * n[2]) != cudaSuccess ||
         cudaMalloc(&S->d_planes, sizeof(double) * n[2]) != cudaSuccess ||
         cudaMalloc(&S->d_scal, sizeof(double) * 2) != cudaSuccess ||
-        cudaMalloc(&S->d_max, sizeof(unsigned long long)) != cudaSuccess)
+        cudaMalloc(&S->d_max, 2 * sizeof(unsigned long long)) != cudaSuccess)
       rc = fail(NYX_ENOMEM, "Poisson scratch allocation failed");
     else if (cudaMemcpy(S->d_box_lo, lo.data(), lo.size() * sizeof(int), cudaMemcpyHostToDevice) !=
              cudaSuccess)
@@ -375,9 +522,10 @@ int nyx_poisson_create(nyx_plan *P, const nyx_poisson_params *prm, nyx_poisson *
   return NYX_OK;
 }
 
-int nyx_poisson_solve(nyx_poisson *S, const double *state, double a, double *grav_out,
-                      int warm_start, int *cycles_out, double *resid_out) {
-  if (!S || !state || !grav_out || !(a > 0.0)) return fail(NYX_EINVAL, "bad argument");
+int nyx_poisson_solve(nyx_poisson *S, const double *state, const double *rho_dm, double a,
+                      double *grav_out, double *g_dense_out, int warm_start, int *cycles_out,
+                      double *resid_out) {
+  if (!S || !state || !(a > 0.0)) return fail(NYX_EINVAL, "bad argument");
   nyx_plan &P = *S->P;
   Level &g0 = S->L[0];
   const long long N = (long long)g0.d.n[0] * g0.d.n[1] * g0.d.n[2];
@@ -386,6 +534,10 @@ int nyx_poisson_solve(nyx_poisson *S, const double *state, double a, double *gra
   k_pg_gather<<<gridn(P.total_cells, 256), 256, 0, st>>>(state, P.d_boxes, P.d_cell_pref,
                                                         S->d_box_lo, P.nbox, P.total_cells, g0.d,
                                                         g0.f);
+  if (rho_dm) {
+    k_pg_add<<<gridn(N, 256), 256, 0, st>>>(g0.f, rho_dm, N);
+    S->launches += 1;
+  }
   const long long nrow = (long long)g0.d.n[1] * g0.d.n[2];
   k_pg_rows<<<gridn(nrow, 128), 128, 0, st>>>(g0.f, g0.d, S->d_rows);
   k_pg_planes<<<gridn(g0.d.n[2], 128), 128, 0, st>>>(S->d_rows, g0.d, S->d_planes);
@@ -404,11 +556,17 @@ int nyx_poisson_solve(nyx_poisson *S, const double *state, double a, double *gra
     ++cyc;
     if ((rc = resid_max(S, &res))) return rc;
   }
-  k_pg_grav<<<gridn(P.total_cells, 256), 256, 0, st>>>(g0.phi, g0.d, 0.5 / S->dx, P.d_boxes,
-                                                      P.d_cell_pref, S->d_box_lo, P.nbox,
-                                                      P.total_cells, grav_out);
-  S->launches += 1;
-  plan_fill(&P, grav_out, NGRAV);
+  if (grav_out) {
+    k_pg_grav<<<gridn(P.total_cells, 256), 256, 0, st>>>(g0.phi, g0.d, 0.5 / S->dx, P.d_boxes,
+                                                        P.d_cell_pref, S->d_box_lo, P.nbox,
+                                                        P.total_cells, grav_out);
+    S->launches += 1;
+    plan_fill(&P, grav_out, NGRAV);
+  }
+  if (g_dense_out) {
+    k_pg_grav_dense<<<gridn(N, 256), 256, 0, st>>>(g0.phi, g0.d, 0.5 / S->dx, g_dense_out);
+    S->launches += 1;
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "Poisson launch");
   P.launches += S->launches;
@@ -417,6 +575,59 @@ int nyx_poisson_solve(nyx_poisson *S, const double *state, double a, double *gra
   if (resid_out) *resid_out = fmax > 0.0 ? res / fmax : 0.0;
   if (res > target) return fail(NYX_ETIMEOUT, "Poisson solve did not reach the tolerance");
   return NYX_OK;
+}
+
+int nyx_pm_deposit(nyx_poisson *S, const double *x, const double *m, long long np,
+                   double *rho_dm) {
+  if (!S || !rho_dm || np < 0 || (np && (!x || !m))) return fail(NYX_EINVAL, "bad argument");
+  Level &g0 = S->L[0];
+  const long long N = (long long)g0.d.n[0] * g0.d.n[1] * g0.d.n[2];
+  CK(cudaMemsetAsync(rho_dm, 0, N * sizeof(double), S->P->stream));
+  if (np) {
+    const double iv = 1.0 / (S->dx * S->dx * S->dx);
+    k_pm_deposit<<<gridn(np, 256), 256, 0, S->P->stream>>>(x, m, np, g0.d, S->dx, iv, rho_dm);
+    S->P->launches += 1;
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? NYX_OK : cuda_fail(e, "deposit launch");
+}
+
+int nyx_pm_kick_drift(nyx_poisson *S, double *x, double *u, long long np, const double *g_dense,
+                      double a_old, double a_half, double dt) {
+  if (!S || !g_dense || np < 0 || (np && (!x || !u))) return fail(NYX_EINVAL, "bad argument");
+  if (np) {
+    k_pm_kick_drift<<<gridn(np, 256), 256, 0, S->P->stream>>>(x, u, np, g_dense, S->L[0].d,
+                                                              S->dx, a_old, a_half, dt);
+    S->P->launches += 1;
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? NYX_OK : cuda_fail(e, "kick-drift launch");
+}
+
+int nyx_pm_kick(nyx_poisson *S, const double *x, double *u, long long np, const double *g_dense,
+                double a_half, double a_new, double dt) {
+  if (!S || !g_dense || np < 0 || (np && (!x || !u))) return fail(NYX_EINVAL, "bad argument");
+  if (np) {
+    k_pm_kick<<<gridn(np, 256), 256, 0, S->P->stream>>>(x, u, np, g_dense, S->L[0].d, S->dx,
+                                                        a_half, a_new, dt);
+    S->P->launches += 1;
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? NYX_OK : cuda_fail(e, "kick launch");
+}
+
+int nyx_pm_estdt(nyx_poisson *S, const double *x, const double *u, long long np,
+                 const double *g_dense, double a, double cfl_dm, double *dt_dev) {
+  if (!S || !g_dense || !dt_dev || np < 0 || (np && (!x || !u)))
+    return fail(NYX_EINVAL, "bad argument");
+  CK(cudaMemsetAsync(S->d_max, 0, 2 * sizeof(unsigned long long), S->P->stream));
+  if (np)
+    k_pm_maxes<<<gridn(np, 256), 256, 0, S->P->stream>>>(x, u, np, g_dense, S->L[0].d, S->dx,
+                                                         S->d_max);
+  k_pm_dt<<<1, 1, 0, S->P->stream>>>(S->d_max, a, S->dx, cfl_dm, dt_dev);
+  S->P->launches += np ? 2 : 1;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? NYX_OK : cuda_fail(e, "particle dt launch");
 }
 
 int nyx_poisson_phi(nyx_poisson *S, double *phi_out) {

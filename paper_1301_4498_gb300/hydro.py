@@ -126,7 +126,14 @@ def load_library(path: str | None = None):
     L.nyx_poisson_default_params.argtypes = [C.POINTER(NyxPoissonParams)]
     L.nyx_poisson_default_params.restype = None
     L.nyx_poisson_create.argtypes = [vp, C.POINTER(NyxPoissonParams), C.POINTER(vp)]
-    L.nyx_poisson_solve.argtypes = [vp, vp, C.c_double, vp, C.c_int, ip, dp]
+    L.nyx_poisson_solve.argtypes = [vp, vp, vp, C.c_double, vp, vp, C.c_int, ip, dp]
+    L.nyx_pm_deposit.argtypes = [vp, vp, vp, C.c_longlong, vp]
+    L.nyx_pm_kick_drift.argtypes = [vp, vp, vp, C.c_longlong, vp, C.c_double, C.c_double,
+                                    C.c_double]
+    L.nyx_pm_kick.argtypes = [vp, vp, vp, C.c_longlong, vp, C.c_double, C.c_double, C.c_double]
+    L.nyx_pm_estdt.argtypes = [vp, vp, vp, C.c_longlong, vp, C.c_double, C.c_double, vp]
+    for name in ("nyx_pm_deposit", "nyx_pm_kick_drift", "nyx_pm_kick", "nyx_pm_estdt"):
+        getattr(L, name).restype = C.c_int
     L.nyx_poisson_phi.argtypes = [vp, vp]
     L.nyx_poisson_destroy.argtypes = [vp]
     for name in ("nyx_poisson_create", "nyx_poisson_solve", "nyx_poisson_phi",
@@ -445,15 +452,40 @@ class Poisson:
         n = plan.spec.dom_hi[0] - plan.spec.dom_lo[0] + 1
         self.shape = (int(n[2]), int(n[1]), int(n[0]))
 
-    def solve(self, state, a, grav_out, warm_start=True):
+    def solve(self, state, a, grav_out=None, warm_start=True, rho_dm=None, g_dense=None):
         """Returns (cycles, relative residual)."""
         cyc = C.c_int()
         res = C.c_double()
         with self.plan.ordered():
-            _check(self.lib.nyx_poisson_solve(self.h, _ptr(state), float(a), _ptr(grav_out),
+            _check(self.lib.nyx_poisson_solve(self.h, _ptr(state), _ptr(rho_dm), float(a),
+                                              _ptr(grav_out), _ptr(g_dense),
                                               1 if warm_start else 0, C.byref(cyc),
                                               C.byref(res)))
         return cyc.value, res.value
+
+    def dense(self, ncomp=1):
+        import torch
+        return torch.zeros((ncomp,) + self.shape, dtype=torch.float64, device="cuda")
+
+    # dark matter: x, u (3, np), m (np,) device tensors; g a (3, nz, ny, nx) dense tensor
+    def pm_deposit(self, x, m, rho_dm):
+        with self.plan.ordered():
+            _check(self.lib.nyx_pm_deposit(self.h, _ptr(x), _ptr(m), m.numel(), _ptr(rho_dm)))
+
+    def pm_kick_drift(self, x, u, g, a_old, a_half, dt):
+        with self.plan.ordered():
+            _check(self.lib.nyx_pm_kick_drift(self.h, _ptr(x), _ptr(u), x.shape[1], _ptr(g),
+                                              float(a_old), float(a_half), float(dt)))
+
+    def pm_kick(self, x, u, g, a_half, a_new, dt):
+        with self.plan.ordered():
+            _check(self.lib.nyx_pm_kick(self.h, _ptr(x), _ptr(u), x.shape[1], _ptr(g),
+                                        float(a_half), float(a_new), float(dt)))
+
+    def pm_estdt(self, x, u, g, a, dt_dev, cfl_dm=0.5):
+        with self.plan.ordered():
+            _check(self.lib.nyx_pm_estdt(self.h, _ptr(x), _ptr(u), x.shape[1], _ptr(g), float(a),
+                                         float(cfl_dm), _ptr(dt_dev)))
 
     def phi(self):
         import torch

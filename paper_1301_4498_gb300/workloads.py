@@ -542,3 +542,20 @@ def dm_particles(n, dx, per_axis=None, seed=17, disp=0.3, vel_rms=0.05, mass_tot
     npart = x.shape[1]
     m = np.full(npart, mass_total * float(np.prod(L)) / npart)
     return np.ascontiguousarray(x), np.ascontiguousarray(u), m
+
+
+def cosmo_level(n=512, box=32, sigma=1.0, seed=5, nsteps=100, part_seed=17, dm_mass=5.0,
+                dm_vel_rms=0.1, a0=1.0 / 51, aN=1.0 / 31) -> Workload:
+    """Gas on a periodic n^3 level cut into box^3 boxes (the comoving
+    generator) plus one dark-matter particle per cell (dm_particles, total
+    mass dm_mass times the mean gas mass), for the single-level algorithm
+    with self-gravity.  The particles are in level.meta["dm"] = (x, u, m);
+    the gravity field is left to the Poisson solve (grav = None)."""
+    w = tiled_box(n=n, box=box, sigma=sigma, seed=seed, nsteps=nsteps, a0=a0, aN=aN)
+    dx = 1.0 / n
+    w.level.meta["dm"] = dm_particles((n, n, n), dx, seed=part_seed, vel_rms=dm_vel_rms,
+                                      mass_total=dm_mass)
+    w.grav = None
+    w.name = f"{w.name} + {n}^3 dark-matter particles"
+    w.mixed = True
+    return w
