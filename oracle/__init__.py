@@ -55,7 +55,7 @@ class _Params(C.Structure):
                 ("riemann_max_iter", C.c_int), ("riemann_tol", C.c_double),
                 ("grav_corrector", C.c_int), ("dual_energy_sync", C.c_int),
                 ("grav_energy", C.c_int), ("reconstruction", C.c_int),
-                ("riemann_solver", C.c_int)]
+                ("riemann_solver", C.c_int), ("flattening", C.c_int)]
 
 
 class _Level(C.Structure):
@@ -95,12 +95,13 @@ class OracleParams:
     grav_energy: int = 0       # Sec. 3.2: 0 rho U . g in the energy; 1 the kinetic-energy change
     reconstruction: int = 0    # Sec. 3.2: 0 PPM, 1 PLM
     riemann_solver: int = 0    # Sec. 3.2: 0 two-shock (iterative), 1 linearised
+    flattening: int = 0        # 1: Colella-Woodward shock flattening of the profiles
 
     def _c(self) -> _Params:
         return _Params(self.gamma, self.cfl, self.small_dens, self.small_pres, self.eta_de,
                        self.riemann_max_iter, self.riemann_tol, self.grav_corrector,
                        self.dual_energy_sync, self.grav_energy, self.reconstruction,
-                       self.riemann_solver)
+                       self.riemann_solver, self.flattening)
 
 
 def load(path: str):
@@ -121,8 +122,13 @@ def load(path: str):
         L.orc_riemann.argtypes = [C.POINTER(_Params), dp, dp, dp, dp, dp]
         L.orc_riemann_counts.argtypes = [C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.c_int]
         L.orc_riemann_counts.restype = None
-        L.orc_trace_line.argtypes = [C.POINTER(_Params), C.c_int, dp, dp, C.c_double,
+        L.orc_trace_line.argtypes = [C.POINTER(_Params), C.c_int, dp, dp, dp, C.c_double,
                                      C.c_double, C.c_double, C.c_int, dp, dp, dp, dp]
+        L.orc_flatten_line.argtypes = [C.POINTER(_Params), C.c_int, dp, dp, dp]
+        L.orc_flatten_line.restype = None
+        L.orc_flatten_field.argtypes = [C.POINTER(_Level), C.POINTER(_Params), C.POINTER(dp),
+                                        C.POINTER(dp)]
+        L.orc_flatten_field.restype = C.c_int
         L.orc_correct.argtypes = [C.POINTER(_Level), C.POINTER(_Params), C.POINTER(dp),
                                   C.POINTER(dp), C.POINTER(dp), C.POINTER(dp), C.c_double,
                                   C.c_double, C.c_double, C.POINTER(_Stats)]
@@ -318,6 +324,31 @@ def riemann_counts(reset: bool = True):
     return c.value, n.value
 
 
+def flatten_line(pr, u, params: OracleParams = None):
+    """Shock-flattening coefficients along a line of pressures ``pr`` and
+    velocities ``u`` along it: cells 3..n-4 (1 at the others)."""
+    params = params or OracleParams()
+    pr = np.ascontiguousarray(pr, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.zeros(len(pr))
+    p = params._c()
+    lib().orc_flatten_line(C.byref(p), len(pr), _dp(pr), _dp(u), _dp(out))
+    return out
+
+
+def flatten_field(lev, params: OracleParams, states):
+    """Shock-flattening coefficient of every cell of every box (copies of
+    ``states`` with their ghost cells filled): a list of (nz+2g, ny+2g,
+    nx+2g) arrays, 1 outside [-1, n] in each direction."""
+    S = [np.array(s, dtype=np.float64, copy=True) for s in states]
+    fill_ghosts(lev, S)
+    out = [np.zeros(s.shape[1:]) for s in S]
+    cl, keep = _level(lev)
+    p = params._c()
+    lib().orc_flatten_field(C.byref(cl), C.byref(p), _ptrs(S), _ptrs(out))
+    return out
+
+
 def ppm_line(s: np.ndarray):
     """PPM edge values and curvature (sL, sR, s6) for cells 2..n-3 of a line."""
     s = np.ascontiguousarray(s, dtype=np.float64)
@@ -346,18 +377,21 @@ def riemann(params: OracleParams, qL, qR):
     return out, float(ps[0]), float(us[0])
 
 
-def trace_line(params: OracleParams, q5, g=None, *, dtp, dx, adot=0.0, direction=0):
+def trace_line(params: OracleParams, q5, g=None, *, dtp, dx, adot=0.0, direction=0, fl=None):
     """Trace a line of primitives (5 x n, rho,u_x,u_y,u_z,p) along
     ``direction``.  Returns (qm, qp, beta_m, beta_p) for cells 2..n-3: the
     low- and high-face edge states and the wave amplitudes (beta_-, beta_0,
-    beta_+) of each side."""
+    beta_+) of each side.  ``fl`` (n values, default 1) is each cell's
+    shock-flattening coefficient."""
     q5 = np.ascontiguousarray(q5, dtype=np.float64)
     n = q5.shape[1]
     gl = None if g is None else np.ascontiguousarray(g, dtype=np.float64)
+    fla = None if fl is None else np.ascontiguousarray(np.broadcast_to(fl, (n,)), dtype=np.float64)
     qm, qp = np.zeros((5, n)), np.zeros((5, n))
     bm, bp = np.zeros((3, n)), np.zeros((3, n))
     p = params._c()
-    lib().orc_trace_line(C.byref(p), n, _dp(q5), None if gl is None else _dp(gl), dtp, dx, adot,
+    lib().orc_trace_line(C.byref(p), n, _dp(q5), None if gl is None else _dp(gl),
+                         None if fla is None else _dp(fla), dtp, dx, adot,
                          direction, _dp(qm), _dp(qp), _dp(bm), _dp(bp))
     return qm, qp, bm, bp
 

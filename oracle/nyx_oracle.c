@@ -19,6 +19,7 @@
 
 #include <math.h>
 #include <omp.h>
+#include <stddef.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -124,6 +125,50 @@ static double ppm_im(double sL, double sR, double s6, double sig) {
 }
 
 /* ------------------------------------------------------------------ */
+/* Shock flattening (Colella & Woodward 1984; the PPM that Sec. 3.2 cites).
+ * reading: along each direction d, a cell is inside a shock when the
+ * pressure differs across it (cells i-1, i+1) by more than eps times the
+ * smaller of the two pressures and the flow converges there
+ * (u_d(i-1) > u_d(i+1)).  The shock's steepness is the ratio z of that
+ * pressure difference to the one across cells i-2, i+2 (the latter not
+ * below the pressure floor): a jump spread over one cell gives z near 1,
+ * smooth data z near 1/2.  chi = clamp(omega2 (z - omega1), 0, 1) inside
+ * a shock, 0 outside.  A cell's flattening along d is the larger chi of
+ * itself and its neighbour on the low-pressure side (the side the shock
+ * moves into; the right-hand one when both pressures are equal).  The
+ * cell's coefficient is 1 minus its largest flattening over the three
+ * directions; each profile of the cell is pulled toward the cell value by
+ * it (edge values s_c + f (s_edge - s_c), curvature f s6).  Constants of
+ * CW84: eps = 0.33, omega1 = 0.75, omega2 = 10. */
+#define FLAT_EPS 0.33
+#define FLAT_OMEGA1 0.75
+#define FLAT_OMEGA2 10.0
+
+/* chi of the cell at pr[0], u[0]; neighbours at multiples of stride s */
+static double shock_chi(const double *pr, const double *u, ptrdiff_t s, double small_pres) {
+  double dp1 = pr[s] - pr[-s];
+  double dp2 = pr[2 * s] - pr[-2 * s];
+  double lo = (pr[s] < pr[-s]) ? pr[s] : pr[-s];
+  if (!(fabs(dp1) > FLAT_EPS * lo)) return 0.0;
+  if (!(u[-s] - u[s] > 0.0)) return 0.0;
+  double den = fabs(dp2);
+  if (den < small_pres) den = small_pres;
+  double z = fabs(dp1) / den;
+  double w = FLAT_OMEGA2 * (z - FLAT_OMEGA1);
+  if (w < 0.0) w = 0.0;
+  if (w > 1.0) w = 1.0;
+  return w;
+}
+
+/* flattening along one direction (needs pr at -3..3, u at -2..2) */
+static double flat_dir(const double *pr, const double *u, ptrdiff_t s, double small_pres) {
+  double chi0 = shock_chi(pr, u, s, small_pres);
+  ptrdiff_t t = (pr[s] - pr[-s] > 0.0) ? -s : s;
+  double chin = shock_chi(pr + t, u + t, s, small_pres);
+  return (chi0 > chin) ? chi0 : chin;
+}
+
+/* ------------------------------------------------------------------ */
 /* Characteristic tracing with a reference state (Sec. 3.2): the reference
  * is the average of the parabola over the domain of dependence of the
  * fastest wave moving toward the face (the edge value if it moves away);
@@ -143,7 +188,7 @@ typedef struct {
 } trace_src_t;
 
 static void trace_cell(const eos_t *E, double s5[5][5], double c, const double g3[3],
-                       double dtdx, const trace_src_t *src, int dir, double qm[5],
+                       double dtdx, const trace_src_t *src, double fl, int dir, double qm[5],
                        double qp[5], double bm_out[3], double bp_out[3]) {
   double sL[5], sR[5], s6[5];
   for (int v = 0; v < 5; ++v) {
@@ -152,6 +197,14 @@ static void trace_cell(const eos_t *E, double s5[5][5], double c, const double g
     else
       ppm_coeffs(s5[v], &sL[v], &sR[v], &s6[v]);
   }
+  /* shock flattening: fl = 1 leaves the profiles as they are */
+  if (fl < 1.0)
+    for (int v = 0; v < 5; ++v) {
+      double si = s5[v][2];
+      sL[v] = fl * sL[v] + (1.0 - fl) * si;
+      sR[v] = fl * sR[v] + (1.0 - fl) * si;
+      s6[v] = fl * s6[v];
+    }
   const int nv = 1 + dir;
   const double rho = s5[0][2];
   const double un = s5[nv][2];
@@ -598,6 +651,26 @@ static int advance_box(const eos_t *E, const orc_params *P, const int lo_[3], co
     for (int v = 0; v < 6; ++v) q[v * V + id] = q6[v];
   })
 
+  /* O1b shock-flattening coefficients on [-1, n] in every direction (the
+   * cells whose edge states the valid faces use; their +-3 stencil is
+   * inside the 4 ghost cells); 1 on the other cells */
+  double *fl = NULL;
+  if (P->flattening) {
+    fl = alloc_arr(V);
+    for (size_t t = 0; t < V; ++t) fl[t] = 1.0;
+    int lo[3] = {-1, -1, -1}, hi[3] = {g.n[0], g.n[1], g.n[2]};
+    RANGE_LOOP(lo, hi, {
+      size_t id = gidx(&g, i, j, k);
+      double f = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        double fd = flat_dir(q + 4 * V + id, q + (size_t)(1 + d) * V + id, (ptrdiff_t)g.st[d],
+                             E->small_pres);
+        if (fd > f) f = fd;
+      }
+      fl[id] = 1.0 - f;
+    })
+  }
+
   /* O2+O3 PPM and tracing, direction d, where +-2 neighbours exist */
   double *qm[3], *qp[3];
   for (int d = 0; d < 3; ++d) {
@@ -618,7 +691,8 @@ static int advance_box(const eos_t *E, const orc_params *P, const int lo_[3], co
       if (G)
         for (int c = 0; c < 3; ++c) g3[c] = G[c * V + id];
       double a5[5], b5[5];
-      trace_cell(E, s5, q[5 * V + id], g3, dtdx, &src, d, a5, b5, NULL, NULL);
+      trace_cell(E, s5, q[5 * V + id], g3, dtdx, &src, fl ? fl[id] : 1.0, d, a5, b5, NULL,
+                 NULL);
       for (int v = 0; v < 5; ++v) {
         qmd[v * V + id] = a5[v];
         qpd[v * V + id] = b5[v];
@@ -762,6 +836,7 @@ static int advance_box(const eos_t *E, const orc_params *P, const int lo_[3], co
     free(qp[d]);
   }
   free(q);
+  free(fl);
 
   /* O6-O9 conservative update with comoving weights, gravity predictor
    * (Step 2) and corrector (Step 6), dual-energy sync (Step 6). */
@@ -965,6 +1040,41 @@ void orc_riemann_counts(long long *calls, long long *iters, int reset) {
 
 /* ------------------------------------------------------------------ */
 /* Unit-level entry points for the pin tests. */
+void orc_flatten_line(const orc_params *p, int n, const double *pr, const double *u, double *fl) {
+  for (int i = 0; i < n; ++i) fl[i] = 1.0;
+  for (int i = 3; i < n - 3; ++i) fl[i] = 1.0 - flat_dir(pr + i, u + i, 1, p->small_pres);
+}
+
+int orc_flatten_field(const orc_level *L, const orc_params *p, double *const *S,
+                      double *const *fl) {
+  eos_t E = make_eos(p);
+  for (int b = 0; b < L->nbox; ++b) {
+    geom_t g = make_geom(L->lo + 3 * b, L->hi + 3 * b, L->ng);
+    const size_t V = g.vol;
+    double *q = alloc_arr(6 * V);
+    for (size_t id = 0; id < V; ++id) {
+      double q6[6];
+      primitives(&E, S[b], V, id, q6);
+      for (int v = 0; v < 6; ++v) q[v * V + id] = q6[v];
+    }
+    for (size_t id = 0; id < V; ++id) fl[b][id] = 1.0;
+    for (int k = -1; k <= g.n[2]; ++k)
+      for (int j = -1; j <= g.n[1]; ++j)
+        for (int i = -1; i <= g.n[0]; ++i) {
+          size_t id = gidx(&g, i, j, k);
+          double f = 0.0;
+          for (int d = 0; d < 3; ++d) {
+            double fd = flat_dir(q + 4 * V + id, q + (size_t)(1 + d) * V + id, (ptrdiff_t)g.st[d],
+                                 E.small_pres);
+            if (fd > f) f = fd;
+          }
+          fl[b][id] = 1.0 - f;
+        }
+    free(q);
+  }
+  return 0;
+}
+
 void orc_ppm_line(int n, const double *s, double *sL, double *sR, double *s6) {
   for (int i = 2; i < n - 2; ++i) ppm_coeffs(s + i - 2, &sL[i], &sR[i], &s6[i]);
 }
@@ -985,8 +1095,8 @@ int orc_riemann(const orc_params *p, const double *qL, const double *qR, double 
  * gline: 3 x n gravity.  Fills qm, qp (5 x n) and the wave amplitudes
  * (3 x n, may be NULL) for cells 2..n-3. */
 void orc_trace_line(const orc_params *p, int n, const double *q5, const double *gline,
-                    double dtp, double dx, double adot, int dir, double *qm, double *qp,
-                    double *beta_m, double *beta_p) {
+                    const double *fl, double dtp, double dx, double adot, int dir, double *qm,
+                    double *qp, double *beta_m, double *beta_p) {
   eos_t E = make_eos(p);
   trace_src_t src;
   src.hdtp = 0.5 * dtp;
@@ -1001,7 +1111,7 @@ void orc_trace_line(const orc_params *p, int n, const double *q5, const double *
     if (gline)
       for (int d = 0; d < 3; ++d) g3[d] = gline[d * n + i];
     double a5[5], b5[5], bm[3], bp[3];
-    trace_cell(&E, s5, c, g3, dtp / dx, &src, dir, a5, b5, bm, bp);
+    trace_cell(&E, s5, c, g3, dtp / dx, &src, fl ? fl[i] : 1.0, dir, a5, b5, bm, bp);
     for (int v = 0; v < 5; ++v) {
       qm[v * n + i] = a5[v];
       qp[v * n + i] = b5[v];

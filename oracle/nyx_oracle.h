@@ -49,6 +49,8 @@ typedef struct {
                             reference-state tracing */
   int riemann_solver;    /* 0 the iterative two-shock solver; 1 the linearised
                             approximate solver (Sec. 3.2 names both) */
+  int flattening;        /* 1: Colella-Woodward shock flattening of the profiles
+                            (the PPM the scheme of Sec. 3.2 cites); 0 off */
 } orc_params;
 
 typedef struct {
@@ -181,8 +183,15 @@ void orc_ppm_integrals(double sL, double sR, double s6, double sigma, double *ip
 int orc_riemann(const orc_params *p, const double *qL, const double *qR, double *flux8,
                 double *pstar, double *ustar);
 void orc_trace_line(const orc_params *p, int n, const double *q5, const double *gline,
-                    double dtp, double dx, double adot, int dir, double *qm, double *qp,
-                    double *beta_m, double *beta_p);
+                    const double *fl, double dtp, double dx, double adot, int dir, double *qm,
+                    double *qp, double *beta_m, double *beta_p);
+/* Shock-flattening coefficients of cells 3..n-4 of a line (pressure pr,
+ * velocity along the line u); the other entries are set to 1. */
+void orc_flatten_line(const orc_params *p, int n, const double *pr, const double *u, double *fl);
+/* Shock-flattening coefficient of every cell of every box (fl[b]: the
+ * box's volume with ghosts) from the state S with its ghosts filled. */
+int orc_flatten_field(const orc_level *L, const orc_params *p, double *const *S,
+                      double *const *fl);
 
 #ifdef __cplusplus
 }

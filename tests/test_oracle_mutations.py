@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 import test_oracle_amr as ta
+import test_oracle_flattening as tf
 import test_oracle_gravity as tg
 import test_oracle_pm as tpm
 import test_oracle_poisson as tps
@@ -149,6 +150,25 @@ MUTANTS = {
     "fine ghosts never copied from fine neighbours": ("          if (region == 1) {\n            const int sb",
                                                       "          if (region == 2) {\n            const int sb",
                                                       ta.test_fine_ghosts_take_fine_neighbours_first, ()),
+    "flattening takes the high-pressure neighbour": (
+        "ptrdiff_t t = (pr[s] - pr[-s] > 0.0) ? -s : s;", "ptrdiff_t t = (pr[s] - pr[-s] > 0.0) ? s : -s;",
+        tf.test_two_cell_shock_flattens_the_shock_and_the_cell_behind_it, ()),
+    "shock test at half the lower pressure": ("fabs(dp1) > FLAT_EPS * lo", "fabs(dp1) > 0.5 * lo",
+                                              tf.test_pressure_jump_threshold_is_a_third,
+                                              (0.34, True)),
+    "shock test on diverging flow": ("if (!(u[-s] - u[s] > 0.0)) return 0.0;",
+                                     "if (!(u[-s] - u[s] < 0.0)) return 0.0;",
+                                     tf.test_two_cell_shock_flattens_the_shock_and_the_cell_behind_it,
+                                     ()),
+    "steepness ramp slope 5": ("double w = FLAT_OMEGA2 * (z - FLAT_OMEGA1);",
+                               "double w = 5.0 * (z - FLAT_OMEGA1);",
+                               tf.test_partial_flattening_closed_form, ()),
+    "curvature not flattened": ("s6[v] = fl * s6[v];", "s6[v] = s6[v];",
+                                tf.test_traced_deviation_scales_with_the_coefficient, (0, 0)),
+    "flattening from the z direction only": ("if (fd > f) f = fd;", "if (d == 2) f = fd;",
+                                             tf.test_each_direction_uses_its_own_line, (0,)),
+    "flattening reads u_x in every direction": ("q + (size_t)(1 + d) * V + id", "q + (size_t)1 * V + id",
+                                                tf.test_each_direction_uses_its_own_line, (1,)),
 }
 
 
