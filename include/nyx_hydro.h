@@ -114,6 +114,12 @@ typedef struct {
                               dependence of the fastest wave toward the face) */
   int riemann_solver;      /* NYX_RS_TWO_SHOCK or NYX_RS_LINEAR (acoustic p*, u* without
                               iteration; star density from dp = c^2 d rho) */
+  int flattening;          /* 1: Colella-Woodward shock flattening of the profiles (the
+                              PPM that Sec. 3.2 cites): a cell in a steep, converging
+                              pressure jump (or next to one, on its low-pressure side)
+                              has its profiles pulled toward the cell value.  Costs one
+                              extra pass over the level per advance and, per plan, one
+                              value per cell (FP64 plans double, mixed plans float). */
 } nyx_hydro_params;
 
 typedef struct nyx_plan nyx_plan;
@@ -130,7 +136,7 @@ typedef struct {
 /* Fill *params with the defaults (gamma 5/3, cfl 0.5, small_dens 1e-10,
  * small_pres 1e-12, eta_de 1e-4, 12 iterations, tol 1e-10, FP64,
  * corrector on, persistent, autotune off, keep_fluxes off, coarse_fine off,
- * grav_energy 0, PPM, two-shock solver). */
+ * grav_energy 0, PPM, two-shock solver, no flattening). */
 void nyx_hydro_default_params(nyx_hydro_params *params);
 
 /* Validate the level (Sec. 4.1: even positive extents, ng == 4, boxes of a
@@ -237,6 +243,8 @@ typedef struct {
   long long launches;
   long long timed_fills, timed_advances;
   double fill_ms, advance_ms;
+  long long timed_flattens;  /* shock-flattening passes (flattening plans) */
+  double flatten_ms;
 } nyx_hydro_counters;
 int nyx_hydro_profile(nyx_plan *plan, int enable);
 int nyx_hydro_counters_read(nyx_plan *plan, int reset, nyx_hydro_counters *out);

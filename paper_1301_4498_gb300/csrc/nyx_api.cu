@@ -265,6 +265,10 @@ void free_plan(nyx_plan *P) {
     cudaEventDestroy(e.first);
     cudaEventDestroy(e.second);
   }
+  for (auto &e : P->ev_flat) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
   cudaFree(P->d_boxes);
   cudaFree(P->d_cell_pref);
   cudaFree(P->d_K);
@@ -279,6 +283,8 @@ void free_plan(nyx_plan *P) {
     cudaFree(p.d_pref);
   }
   cudaFree(P->d_scratch);
+  cudaFree(P->d_flat);
+  cudaFree(P->d_flat_tiles);
   cudaFree(P->d_flux);
   cudaFree(P->d_flux_off);
   for (auto &it : P->d_items) cudaFree(it);
@@ -337,12 +343,29 @@ int do_estdt(nyx_plan *P, const double *state, const double *a_dev, double *dt_d
 
 int tune_shape(nyx_plan *P, const FusedArgs &base);
 
+// Shock-flattening coefficients of state S (ghosts filled), when the plan
+// flattens.
+int do_flatten(nyx_plan *P, const double *S) {
+  if (!P->d_flat) return NYX_OK;
+  Span sp(P, &P->ev_flat);
+  int e = launch_flatten(P->prm.precision, P->d_boxes, P->d_flat_tiles, P->flat_ntiles, S,
+                         P->d_K, P->d_flat, P->stream);
+  if (e) return cuda_fail((cudaError_t)e, "flattening launch");
+  P->launches += 1;
+  return NYX_OK;
+}
+
+int variant_bits(const nyx_plan *P) {
+  return P->hK.plm | (P->hK.linear_rs << 1) | (P->hK.flat << 2);
+}
+
 int do_advance(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_new,
                const double *dt, const double *grav, double *dt_next, bool predict_only = false) {
   double *S = L->state[L->cur];
   double *Sn = L->state[1 - L->cur];
   const double *G = grav ? grav : L->grav;
   do_fill(P, S, NCONS);
+  if (int rc = do_flatten(P, S)) return rc;
   launch_step_setup(P->d_K, a_old, a_new, dt, P->d_SC, P->d_boxes, P->nbox, P->d_BS, P->stream);
   P->launches += 1;
   unsigned long long *acc = dt_next ? P->d_dtacc : nullptr;
@@ -352,7 +375,9 @@ int do_advance(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_n
     for (int b = 0; b < P->nbox; ++b) {
       const BoxDev &X = P->hbox[b];
       launch_staged_box(X, P->d_boxes + b, P->d_K, P->d_SC, P->d_BS + b, S + NCONS * X.pref,
-                        G ? G + NGRAV * X.pref : nullptr, Sn + NCONS * X.pref, P->d_scratch,
+                        G ? G + NGRAV * X.pref : nullptr,
+                        P->d_flat ? static_cast<const double *>(P->d_flat) + X.pref : nullptr,
+                        Sn + NCONS * X.pref, P->d_scratch,
                         P->Vmax, acc, P->d_status,
                         P->d_flux ? P->d_flux + P->flux_off[b] : nullptr, predict_only ? 1 : 0,
                         P->stream);
@@ -373,7 +398,8 @@ int do_advance(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_n
     a.flux_keep = P->d_flux;
     a.flux_off = P->d_flux_off;
     a.predict_only = predict_only ? 1 : 0;
-    a.variant = P->hK.plm | (P->hK.linear_rs << 1);
+    a.variant = variant_bits(P);
+    a.flat = P->d_flat;
     if (P->prm.autotune && !P->tuned) {
       int rc = tune_shape(P, a);
       if (rc) return rc;
@@ -507,8 +533,10 @@ int plan_tune(nyx_plan *P, nyx_level *L, const double *a_dev, const double *dt_d
   a.G = L->grav;
   a.Sn = L->state[1 - L->cur];
   a.status = P->d_status_tune;
-  a.variant = P->hK.plm | (P->hK.linear_rs << 1);
+  a.variant = variant_bits(P);
+  a.flat = P->d_flat;
   do_fill(P, L->state[L->cur], NCONS);
+  if (int rc = do_flatten(P, L->state[L->cur])) return rc;
   launch_step_setup(P->d_K, a_dev, a_dev + 1, dt_dev, P->d_SC, P->d_boxes, P->nbox, P->d_BS,
                     P->stream);
   return tune_shape(P, a);
@@ -532,6 +560,20 @@ int launch_fused(int precision, int shape, const FusedArgs &a, int grid, cudaStr
   if (grid < 1) grid = 1;
   return precision == NYX_MIXED ? launch_fused_mixed(shape, a, grid, st)
                                 : launch_fused_f64(shape, a, grid, st);
+}
+
+int launch_flatten(int precision, const BoxDev *boxes, const FlatTile *tiles, int ntiles,
+                   const double *S, const SchemeConsts *K, void *fl, cudaStream_t st) {
+  return precision == NYX_MIXED ? launch_flatten_mixed(boxes, tiles, ntiles, S, K, fl, st)
+                                : launch_flatten_f64(boxes, tiles, ntiles, S, K, fl, st);
+}
+
+int flatten_init(int precision) {
+  return precision == NYX_MIXED ? flatten_init_mixed() : flatten_init_f64();
+}
+
+int launch_flat_ones(int precision, void *fl, long long n, cudaStream_t st) {
+  return precision == NYX_MIXED ? flat_ones_mixed(fl, n, st) : flat_ones_f64(fl, n, st);
 }
 
 int fused_max_grid(int precision, int shape) {
@@ -561,6 +603,7 @@ void nyx_hydro_default_params(nyx_hydro_params *p) {
   p->grav_energy = 0;
   p->reconstruction = NYX_PPM;
   p->riemann_solver = NYX_RS_TWO_SHOCK;
+  p->flattening = 0;
 }
 
 const char *nyx_last_error(void) { return g_err.c_str(); }
@@ -687,6 +730,7 @@ int nyx_hydro_plan(const nyx_level_desc *lev, const nyx_hydro_params *prm, void 
     K.grav_energy = prm->grav_energy;
     K.plm = prm->reconstruction == NYX_PLM;
     K.linear_rs = prm->riemann_solver == NYX_RS_LINEAR;
+    K.flat = prm->flattening ? 1 : 0;
     TRYC(cudaMalloc(&P->d_K, sizeof(SchemeConsts)));
     TRYC(cudaMemcpy(P->d_K, &K, sizeof(SchemeConsts), cudaMemcpyHostToDevice));
     TRYC(cudaMalloc(&P->d_SC, sizeof(StepConsts)));
@@ -699,6 +743,33 @@ int nyx_hydro_plan(const nyx_level_desc *lev, const nyx_hydro_params *prm, void 
     TRYC(cudaMalloc(&P->d_status_tune, sizeof(unsigned)));
     TRYC(cudaMemset(P->d_status_tune, 0, sizeof(unsigned)));
     TRYC(cudaMalloc(&P->d_scal, 4 * sizeof(double)));
+    if (K.flat) {
+      const size_t esz = prm->precision == NYX_MIXED ? sizeof(float) : sizeof(double);
+      TRYC(cudaMalloc(&P->d_flat, esz * (size_t)P->total_stride));
+      // the [-1, n]^2 columns of each box in near-equal tiles of <= 34 x 17
+      std::vector<FlatTile> ft;
+      for (int b = 0; b < P->nbox; ++b) {
+        const int L0 = P->hbox[b].n[0] + 2, L1 = P->hbox[b].n[1] + 2;
+        const int tx = (L0 + 33) / 34, ty = (L1 + 16) / 17;
+        for (int v = 0; v < ty; ++v)
+          for (int u = 0; u < tx; ++u) {
+            FlatTile T;
+            T.box = b;
+            T.x0 = -1 + (int)((long long)L0 * u / tx);
+            T.nx = -1 + (int)((long long)L0 * (u + 1) / tx) - T.x0;
+            T.y0 = -1 + (int)((long long)L1 * v / ty);
+            T.ny = -1 + (int)((long long)L1 * (v + 1) / ty) - T.y0;
+            ft.push_back(T);
+          }
+      }
+      P->flat_ntiles = (int)ft.size();
+      TRYC(cudaMalloc(&P->d_flat_tiles, sizeof(FlatTile) * ft.size()));
+      TRYC(cudaMemcpy(P->d_flat_tiles, ft.data(), sizeof(FlatTile) * ft.size(),
+                      cudaMemcpyHostToDevice));
+      TRYC((cudaError_t)flatten_init(prm->precision));
+      TRYC((cudaError_t)launch_flat_ones(prm->precision, P->d_flat, P->total_stride, P->stream));
+      TRYC(cudaStreamSynchronize(P->stream));
+    }
     if (prm->batching == NYX_PER_BOX) {
       TRYC(cudaMalloc(&P->d_scratch, sizeof(double) * staged_scratch_doubles(P->Vmax)));
     } else {
@@ -817,10 +888,12 @@ int nyx_hydro_run(nyx_plan *P, nyx_level *L, const double *a_dev, double *dt_dev
     a.G = L->grav;
     a.Sn = L->state[1 - L->cur];
     a.status = P->d_status_tune;
-    a.variant = P->hK.plm | (P->hK.linear_rs << 1);
+    a.variant = variant_bits(P);
+    a.flat = P->d_flat;
     // time the shapes on the first step as it will run: its own dt
     if (compute_dt0) do_estdt(P, L->state[L->cur], a_dev, dt_dev);
     do_fill(P, L->state[L->cur], NCONS);
+    if (int rc = do_flatten(P, L->state[L->cur])) return rc;
     launch_step_setup(P->d_K, a_dev, a_dev + 1, dt_dev, P->d_SC, P->d_boxes, P->nbox, P->d_BS,
                       P->stream);
     int rc = tune_shape(P, a);
@@ -931,6 +1004,7 @@ int nyx_hydro_counters_read(nyx_plan *P, int reset, nyx_hydro_counters *out) {
   };
   sum(P->ev_fill, out->fill_ms, out->timed_fills);
   sum(P->ev_adv, out->advance_ms, out->timed_advances);
+  sum(P->ev_flat, out->flatten_ms, out->timed_flattens);
   out->launches = P->launches;
   if (reset) {
     for (auto &e : P->ev_fill) {
@@ -941,8 +1015,13 @@ int nyx_hydro_counters_read(nyx_plan *P, int reset, nyx_hydro_counters *out) {
       cudaEventDestroy(e.first);
       cudaEventDestroy(e.second);
     }
+    for (auto &e : P->ev_flat) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
     P->ev_fill.clear();
     P->ev_adv.clear();
+    P->ev_flat.clear();
     P->launches = 0;
   }
   return NYX_OK;

@@ -53,6 +53,7 @@ __device__ __forceinline__ Eos<R> make_eos(const nyx::SchemeConsts &k, bool mixe
   e.max_iter = k.max_iter;
   e.plm = k.plm;
   e.linear = k.linear_rs;
+  e.flat = k.flat;
   return e;
 }
 
@@ -390,6 +391,7 @@ __global__ void __launch_bounds__(FusedGeom<R, TX, TY>::NT, 1) k_fused(nyx::Fuse
     const long long ps = (long long)b.N[0] * b.N[1];
     const double *S = a.S + nyx::NCONS * b.pref;
     const double *G = a.G ? a.G + nyx::NGRAV * b.pref : nullptr;
+    const R *FL = E.flat ? static_cast<const R *>(a.flat) + b.pref : nullptr;
     double *Sn = a.Sn + nyx::NCONS * b.pref;
     const bool act = in_r1 && i <= nxt && j <= nyt;
     const bool inX = i >= 0 && i < nxt, inY = j >= 0 && j < nyt;
@@ -471,22 +473,23 @@ __global__ void __launch_bounds__(FusedGeom<R, TX, TY>::NT, 1) k_fused(nyx::Fuse
           g3[1] = to_r<R>(G[bs + id]);
           g3[2] = to_r<R>(G[2 * bs + id]);
         }
+        const R fl = FL ? FL[col + (long long)(c + 4) * ps] : R(1);
         R s[5][5];
 #pragma unroll
         for (int v = 0; v < 5; ++v)
 #pragma unroll
           for (int o = 0; o < 5; ++o) s[v][o] = Ps[v * NE + me_e + (o - 2)];
-        trace_cell<R, 0>(E, s, cs, g3, dtdx0, src, qx_m, qx_p);
+        trace_cell<R, 0>(E, s, cs, g3, dtdx0, src, fl, qx_m, qx_p);
 #pragma unroll
         for (int v = 0; v < 5; ++v)
 #pragma unroll
           for (int o = 0; o < 5; ++o) s[v][o] = Ps[v * NE + me_e + (o - 2) * WE];
-        trace_cell<R, 1>(E, s, cs, g3, dtdx1, src, qy_m, qy_p);
+        trace_cell<R, 1>(E, s, cs, g3, dtdx1, src, fl, qy_m, qy_p);
 #pragma unroll
         for (int v = 0; v < 5; ++v)
 #pragma unroll
           for (int o = 0; o < 5; ++o) s[v][o] = win[o][v];
-        trace_cell<R, 2>(E, s, cs, g3, dtdx2, src, qz_m, qz_p);
+        trace_cell<R, 2>(E, s, cs, g3, dtdx2, src, fl, qz_m, qz_p);
         put5(A, NC, 0, me, qx_p);
         put5(A, NC, 5, me, qy_p);
       }
@@ -710,6 +713,121 @@ __global__ void __launch_bounds__(FusedGeom<R, TX, TY>::NT, 1) k_fused(nyx::Fuse
 
 // The dynamic shared-memory attribute is set by max_grid_one, which every
 // plan calls for its shapes when it is created (outside any graph capture).
+// ---------------------------------------------------------------- shock flattening
+// Coefficient 1 - max_d flat_d of every cell of [-1, n]^3 of every box (the
+// cells the advance traces; the +-3 stencil fits in the 4 ghost cells), from
+// the primitives exactly as the advance forms them in type R.  One block per
+// tile of output columns (nyx::FlatTile) walks the planes c = -1 .. n_z: it
+// keeps p and u_z of planes c-3 .. c+3 at the output columns in a ring, and
+// p, u_x, u_y of plane c on the tile's frame (+-3 in x and y), so that each
+// cell's primitives are formed about once per tile instead of once per
+// stencil point.  The other cells keep the 1 they were set to when the
+// buffer was made.
+constexpr int FLAT_TX = 34, FLAT_TY = 17;  // largest output tile
+constexpr int FLAT_NO = FLAT_TX * FLAT_TY;
+constexpr int FLAT_NF = (FLAT_TX + 6) * (FLAT_TY + 6);
+constexpr int FLAT_THREADS = 512;
+
+template <class R>
+constexpr size_t flat_smem() {
+  return sizeof(R) * (size_t)(14 * FLAT_NO + 3 * FLAT_NF);
+}
+
+__device__ __forceinline__ int flat_slot(int k) { return (k + 7) % 7; }  // k >= -7
+
+template <class R>
+__global__ void __launch_bounds__(FLAT_THREADS) k_flatten(const nyx::BoxDev *boxes,
+                                                          const nyx::FlatTile *tiles,
+                                                          const double *Sall,
+                                                          const nyx::SchemeConsts *K, R *FLall) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R *ringp = reinterpret_cast<R *>(smem_raw);  // [7][FLAT_NO] p at the output columns
+  R *ringw = ringp + 7 * FLAT_NO;               // [7][FLAT_NO] u_z at the output columns
+  R *fp = ringw + 7 * FLAT_NO;                  // [FLAT_NF] p of plane c on the frame
+  R *fu = fp + FLAT_NF;                         // [FLAT_NF] u_x
+  R *fv = fu + FLAT_NF;                         // [FLAT_NF] u_y
+  const nyx::FlatTile T = tiles[blockIdx.x];
+  const nyx::BoxDev b = boxes[T.box];
+  const Eos<R> E = make_eos<R>(*K, sizeof(R) == 4);
+  const double *S = Sall + nyx::NCONS * b.pref;
+  R *FL = FLall + b.pref;
+  const long long bs = b.stride;
+  const int N0 = b.N[0], N1 = b.N[1];
+  const int NO = T.nx * T.ny, FW = T.nx + 6, NF = FW * (T.ny + 6);
+  auto cell = [&](int i, int j, int k) {
+    return ((long long)(k + 4) * N1 + (j + 4)) * N0 + (i + 4);
+  };
+  auto ring_plane = [&](int k) {
+    R *P = ringp + flat_slot(k) * FLAT_NO, *U = ringw + flat_slot(k) * FLAT_NO;
+    for (int o = threadIdx.x; o < NO; o += blockDim.x) {
+      R q[5];
+      prims_of<R>(S, bs, cell(T.x0 + o % T.nx, T.y0 + o / T.nx, k), E, q);
+      P[o] = q[4];
+      U[o] = q[3];
+    }
+  };
+  for (int k = -4; k <= 1; ++k) ring_plane(k);
+  for (int c = -1; c <= b.n[2]; ++c) {
+    ring_plane(c + 3);
+    for (int e = threadIdx.x; e < NF; e += blockDim.x) {
+      R q[5];
+      prims_of<R>(S, bs, cell(T.x0 - 3 + e % FW, T.y0 - 3 + e / FW, c), E, q);
+      fp[e] = q[4];
+      fu[e] = q[1];
+      fv[e] = q[2];
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < NO; o += blockDim.x) {
+      const int ox = o % T.nx, oy = o / T.nx;
+      const int fe = (oy + 3) * FW + (ox + 3);
+      R p[7], u[5];
+      R fmax;
+#pragma unroll
+      for (int s = 0; s < 7; ++s) p[s] = fp[fe + s - 3];
+#pragma unroll
+      for (int s = 0; s < 5; ++s) u[s] = fu[fe + s - 2];
+      fmax = flat_dir(p, u, E.small_pres);
+#pragma unroll
+      for (int s = 0; s < 7; ++s) p[s] = fp[fe + (s - 3) * FW];
+#pragma unroll
+      for (int s = 0; s < 5; ++s) u[s] = fv[fe + (s - 2) * FW];
+      R f = flat_dir(p, u, E.small_pres);
+      if (f > fmax) fmax = f;
+#pragma unroll
+      for (int s = 0; s < 7; ++s) p[s] = ringp[flat_slot(c + s - 3) * FLAT_NO + o];
+#pragma unroll
+      for (int s = 0; s < 5; ++s) u[s] = ringw[flat_slot(c + s - 2) * FLAT_NO + o];
+      f = flat_dir(p, u, E.small_pres);
+      if (f > fmax) fmax = f;
+      FL[cell(T.x0 + ox, T.y0 + oy, c)] = R(1) - fmax;
+    }
+    __syncthreads();
+  }
+}
+
+template <class R>
+int launch_flatten_t(const nyx::BoxDev *boxes, const nyx::FlatTile *tiles, int ntiles,
+                     const double *S, const nyx::SchemeConsts *K, void *fl, cudaStream_t st) {
+  if (ntiles < 1) return 0;
+  k_flatten<R><<<ntiles, FLAT_THREADS, flat_smem<R>(), st>>>(boxes, tiles, S, K,
+                                                              static_cast<R *>(fl));
+  return (int)cudaGetLastError();
+}
+
+template <class R>
+int flatten_init_t() {
+  return (int)cudaFuncSetAttribute(k_flatten<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)flat_smem<R>());
+}
+
+// Set every value of a coefficient buffer to 1 (no flattening).
+template <class R>
+__global__ void k_flat_ones(R *fl, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    fl[t] = R(1);
+}
+
 template <class R, int TX, int TY>
 int launch_one(const nyx::FusedArgs &a, int grid, cudaStream_t st) {
   using FG = FusedGeom<R, TX, TY>;

@@ -51,8 +51,8 @@ struct G2 {
   static constexpr int QZFP = QZFM + 5 * NC;         // [2 planes][5][NC] final z, high side
   static constexpr int P1 = QZFP + 10 * NC;          // [28][NC] pool: FX,FY | Fxy,Fyx,Fxz,Fyz
   static constexpr int P2 = P1 + 28 * NC;            // [40][NC] pool: qxy,qyx,qxz,qyz | qxf,qyf
-  static constexpr int GR = P2 + 40 * NC;            // [3][NC] gravity of plane c
-  static constexpr int UF = GR + 3 * NC;             // [8][NUF] final x, y fluxes of plane c-1
+  static constexpr int GR = P2 + 40 * NC;            // [4][NC] gravity and flattening, plane c
+  static constexpr int UF = GR + 4 * NC;             // [8][NUF] final x, y fluxes of plane c-1
   static constexpr int FFZ = UF + 8 * NUF;           // [2 faces][8][NZF] final z fluxes
   static constexpr int TOTAL = FFZ + 16 * NZF;
   static constexpr size_t SMEM = sizeof(float) * (size_t)TOTAL;
@@ -189,6 +189,7 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
   if constexpr (VAR >= 0) {
     E.plm = VAR & 1;
     E.linear = (VAR >> 1) & 1;
+    E.flat = 0;
   }
   TraceSrc<float> src;
   src.hdtp = d2f_rn(sc.hdtp);
@@ -267,6 +268,9 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
             sm[G::GR + me] = g0;
             sm[G::GR + NC + me] = g1;
             sm[G::GR + 2 * NC + me] = g2;
+            if (E.flat)
+              sm[G::GR + 3 * NC + me] =
+                  static_cast<const float *>(a.flat)[b.pref + mycol + (long long)(c + 4) * ps];
             // plane c of the own column into the framed buffer
             const float *rc = ring(c);
 #pragma unroll
@@ -319,7 +323,8 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
           }
           const float dtdx = (dir == 0) ? dtdx0 : ((dir == 1) ? dtdx1 : dtdx2);
           float qmn[5], qpn[5], qm[5], qp[5];
-          trace_cell<float, 0>(E, s5, cs, gn, dtdx, src, qmn, qpn);
+          const float fl = E.flat ? sm[G::GR + 3 * NC + me] : 1.0f;
+          trace_cell<float, 0>(E, s5, cs, gn, dtdx, src, fl, qmn, qpn);
           to_lab(dir, qmn, qm);
           to_lab(dir, qpn, qp);
           float *dst = (dir == 2) ? sm + G::QZ + pc * 10 * NC : sm + G::QXY + (pc * 2 + dir) * 10 * NC;

@@ -14,6 +14,18 @@ int launch_fused_f64(int shape, const FusedArgs &a, int grid, cudaStream_t st) {
   }
 }
 
+int launch_flatten_f64(const BoxDev *boxes, const FlatTile *tiles, int ntiles, const double *S,
+                       const SchemeConsts *K, void *fl, cudaStream_t st) {
+  return nyx_fused64::launch_flatten_t<double>(boxes, tiles, ntiles, S, K, fl, st);
+}
+
+int flatten_init_f64() { return nyx_fused64::flatten_init_t<double>(); }
+
+int flat_ones_f64(void *fl, long long n, cudaStream_t st) {
+  nyx_fused64::k_flat_ones<double><<<1216, 256, 0, st>>>(static_cast<double *>(fl), n);
+  return (int)cudaGetLastError();
+}
+
 int max_grid_f64(int shape) {
   switch (shape) {
     case 0: return nyx_fused64::max_grid_one<double, 16, 16>();

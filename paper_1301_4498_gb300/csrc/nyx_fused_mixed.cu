@@ -16,7 +16,9 @@ int launch_fused_mixed(int shape, const FusedArgs &a, int grid, cudaStream_t st)
     case 0: return nyx_mixed::launch_one<float, 16, 16>(a, grid, st);
     case 1: return nyx_mixed::launch_one<float, 32, 8>(a, grid, st);
     case 2: return nyx_mixed::launch_one<float, 16, 8>(a, grid, st);
-    case 3:  // the default shape: one instantiation per scheme variant
+    case 3:  // the default shape: one instantiation per scheme variant (flattening: the
+             // instantiation with run-time variant flags)
+      if (a.variant & 4) return nyx_mixed::launch_two<16, 8, 1, -1>(a, grid, st);
       switch (a.variant) {
         case 1: return nyx_mixed::launch_two<16, 8, 1, 1>(a, grid, st);
         case 2: return nyx_mixed::launch_two<16, 8, 1, 2>(a, grid, st);
@@ -38,12 +40,25 @@ int max_grid_mixed(int shape) {
       int g = nyx_mixed::max_grid_two<16, 8, 1, 0>();
       g = std::min(g, nyx_mixed::max_grid_two<16, 8, 1, 1>());
       g = std::min(g, nyx_mixed::max_grid_two<16, 8, 1, 2>());
+      g = std::min(g, nyx_mixed::max_grid_two<16, 8, 1, -1>());
       return std::min(g, nyx_mixed::max_grid_two<16, 8, 1, 3>());
     }
     case 4: return nyx_mixed::max_grid_two<8, 8, 2, -1>();
     case 5: return nyx_mixed::max_grid_two<32, 4, 1, -1>();
     default: return 1;
   }
+}
+
+int launch_flatten_mixed(const BoxDev *boxes, const FlatTile *tiles, int ntiles, const double *S,
+                         const SchemeConsts *K, void *fl, cudaStream_t st) {
+  return nyx_mixed::launch_flatten_t<float>(boxes, tiles, ntiles, S, K, fl, st);
+}
+
+int flatten_init_mixed() { return nyx_mixed::flatten_init_t<float>(); }
+
+int flat_ones_mixed(void *fl, long long n, cudaStream_t st) {
+  nyx_mixed::k_flat_ones<float><<<1216, 256, 0, st>>>(static_cast<float *>(fl), n);
+  return (int)cudaGetLastError();
 }
 
 }  // namespace nyx

@@ -36,6 +36,7 @@ struct SchemeConsts {
   int grav_energy;  // S_g in the total energy: 0 rho U . g, 1 kinetic-energy change (Sec. 3.2)
   int plm;          // 1: PLM profiles (Sec. 3.2)
   int linear_rs;    // 1: linearised Riemann solver (Sec. 3.2)
+  int flat;         // 1: Colella-Woodward shock flattening (per-cell coefficients)
 };
 
 // Scalars of one step, derived on the device from a_old, a_new, dt so that
@@ -60,6 +61,13 @@ struct FillRect {
 };
 
 // Work item of the fused persistent kernel: a TX x TY column tile of a box.
+// Output tile of the shock-flattening pass: columns [x0, x0+nx) x [y0, y0+ny)
+// of one box, local coordinates (-1 and n are the one-cell halo); nx <= 34,
+// ny <= 17.
+struct FlatTile {
+  int box, x0, y0, nx, ny;
+};
+
 struct WorkItem {
   int box;
   int x0, y0;

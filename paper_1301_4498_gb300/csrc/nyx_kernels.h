@@ -31,9 +31,9 @@ size_t staged_scratch_doubles(long long V);
 
 void launch_staged_box(const BoxDev &b, const BoxDev *b_dev, const SchemeConsts *K,
                        const StepConsts *SC, const BoxStep *BSb, const double *Sbox,
-                       const double *Gbox, double *Snbox, double *scratch, long long V,
-                       unsigned long long *dtacc, unsigned *status, double *flux_keep,
-                       int predict_only, cudaStream_t st);
+                       const double *Gbox, const double *FLbox, double *Snbox, double *scratch,
+                       long long V, unsigned long long *dtacc, unsigned *status,
+                       double *flux_keep, int predict_only, cudaStream_t st);
 
 // Arguments of one launch of the fused persistent advance.
 struct FusedArgs {
@@ -52,7 +52,10 @@ struct FusedArgs {
   double *flux_keep;              // final-flux store, or null
   const long long *flux_off;      // per-box offsets into flux_keep
   int predict_only;               // 1: Step 2 only (no corrector, no dual-energy sync, no dt)
-  int variant;                    // scheme variant: bit 0 PLM, bit 1 linearised solver
+  int variant;                    // scheme variant: bit 0 PLM, bit 1 linearised solver,
+                                  // bit 2 shock flattening
+  const void *flat;               // shock-flattening coefficients (double for FP64 plans,
+                                  // float for mixed ones; one per cell, state layout) or null
 };
 
 // Tile shapes of the fused kernel (columns per CTA in x and y).
@@ -81,5 +84,24 @@ void launch_correct(const BoxDev *boxes, const long long *cell_pref, int nbox, l
 int launch_fused_mixed(int shape, const FusedArgs &a, int grid, cudaStream_t st);
 int max_grid_f64(int shape);
 int max_grid_mixed(int shape);
+int launch_flatten_f64(const BoxDev *boxes, const FlatTile *tiles, int ntiles, const double *S,
+                       const SchemeConsts *K, void *fl, cudaStream_t st);
+int launch_flatten_mixed(const BoxDev *boxes, const FlatTile *tiles, int ntiles, const double *S,
+                         const SchemeConsts *K, void *fl, cudaStream_t st);
+int flatten_init_f64();
+int flatten_init_mixed();
+int flat_ones_f64(void *fl, long long n, cudaStream_t st);
+int flat_ones_mixed(void *fl, long long n, cudaStream_t st);
+
+// Shock-flattening coefficients of the cells [-1, n]^3 of every box from the
+// state S (ghosts filled), in the plan's arithmetic: fl is double for FP64
+// plans, float for mixed ones.  tiles: the boxes' [-1, n]^2 columns cut into
+// tiles of at most 34 x 17 (one block each).  Return a cudaError_t.
+int launch_flatten(int precision, const BoxDev *boxes, const FlatTile *tiles, int ntiles,
+                   const double *S, const SchemeConsts *K, void *fl, cudaStream_t st);
+// Shared-memory attribute of the flattening kernel (once per process).
+int flatten_init(int precision);
+// Set the n coefficients of fl to 1.
+int launch_flat_ones(int precision, void *fl, long long n, cudaStream_t st);
 
 }  // namespace nyx

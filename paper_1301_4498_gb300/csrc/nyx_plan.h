@@ -59,6 +59,12 @@ struct nyx_plan {
   unsigned *d_status_tune = nullptr;  // status of autotuner launches (never reported)
   double *d_scal = nullptr;  // host-call scalars: a_old, a_new, dt, dt_next
   nyx::host::FillPass pass[4];
+  // shock flattening: one coefficient per cell (double for FP64 plans, float
+  // for mixed ones), set per advance on the boxes' [-1, n]^3 by one block
+  // per tile of output columns
+  void *d_flat = nullptr;
+  nyx::FlatTile *d_flat_tiles = nullptr;
+  int flat_ntiles = 0;
   // per-box FP64 form
   double *d_scratch = nullptr;
   long long Vmax = 0;
@@ -78,7 +84,7 @@ struct nyx_plan {
   // counters and profiling
   long long launches = 0;
   bool profiling = false;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_fill, ev_adv;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_fill, ev_adv, ev_flat;
 };
 
 

@@ -24,6 +24,7 @@ struct Eos {
   int max_iter;
   int plm;     // PLM profiles instead of PPM (Sec. 3.2)
   int linear;  // the linearised Riemann solver instead of the two-shock one (Sec. 3.2)
+  int flat;    // Colella-Woodward shock flattening (coefficients from k_flatten)
 };
 
 template <class R>
@@ -115,6 +116,39 @@ __device__ __forceinline__ R ppm_im(R sL, R sR, R s6, R sig) {
 // waves moving toward the face are projected with the primitive-system
 // eigenvectors at the cell centre.  Half-step comoving sources (Sec. 2.2 in
 // primitive form) are added to both edge states.
+// ---------------------------------------------------------------- shock flattening
+// Colella & Woodward (1984), the PPM that Sec. 3.2 cites.  Along one
+// direction, a cell is in a shock when the pressure across it (cells -1,
+// +1) differs by more than 0.33 of the smaller of the two and the flow
+// converges (u(-1) > u(+1)); its steepness chi = clamp(10 (z - 0.75), 0, 1),
+// z = |p(+1) - p(-1)| / max(|p(+2) - p(-2)|, small_pres), is 0 outside a
+// shock.  The cell's flattening is the larger chi of itself and of its
+// neighbour on the low-pressure side (the +1 one when p(+1) = p(-1)).
+template <class R>
+__device__ __forceinline__ R shock_chi(R pm2, R pm1, R pp1, R pp2, R um1, R up1, R small_pres) {
+  const R dp1 = pp1 - pm1;
+  const R lo = (pp1 < pm1) ? pp1 : pm1;
+  if (!(rabs(dp1) > R(0.33) * lo)) return R(0);
+  if (!(um1 - up1 > R(0))) return R(0);
+  R den = rabs(pp2 - pm2);
+  if (den < small_pres) den = small_pres;
+  const R z = rabs(dp1) / den;
+  R w = R(10) * (z - R(0.75));
+  if (w < R(0)) w = R(0);
+  if (w > R(1)) w = R(1);
+  return w;
+}
+
+// Flattening along one direction: p[o] at offsets o - 3 (o = 0..6), u[o] the
+// velocity along it at offsets o - 2 (o = 0..4).
+template <class R>
+__device__ __forceinline__ R flat_dir(const R (&p)[7], const R (&u)[5], R small_pres) {
+  const R c0 = shock_chi(p[1], p[2], p[4], p[5], u[1], u[3], small_pres);
+  const R cn = (p[4] - p[2] > R(0)) ? shock_chi(p[0], p[1], p[3], p[4], u[0], u[2], small_pres)
+                                    : shock_chi(p[2], p[3], p[5], p[6], u[2], u[4], small_pres);
+  return (c0 > cn) ? c0 : cn;
+}
+
 template <class R>
 struct TraceSrc {
   R hdtp;   // dt'/2
@@ -123,11 +157,12 @@ struct TraceSrc {
 };
 
 // s[v][o]: variable v of (rho, u_x, u_y, u_z, p) at cells i-2..i+2 along DIR.
+// fl: the cell's shock-flattening coefficient (1: none).
 // Outputs qm (low face i-1/2) and qp (high face i+1/2), lab frame.
 template <class R, int DIR>
 __device__ __forceinline__ void trace_cell(const Eos<R> &E, const R (&s)[5][5], R c,
                                            const R (&g3)[3], R dtdx, const TraceSrc<R> &src,
-                                           R (&qm)[5], R (&qp)[5]) {
+                                           R fl, R (&qm)[5], R (&qp)[5]) {
   constexpr int NV = 1 + DIR;
   R sL[5], sR[5], s6[5];
   if (E.plm) {
@@ -137,6 +172,16 @@ __device__ __forceinline__ void trace_cell(const Eos<R> &E, const R (&s)[5][5], 
 #pragma unroll
     for (int v = 0; v < 5; ++v)
       ppm_coeffs(s[v][0], s[v][1], s[v][2], s[v][3], s[v][4], sL[v], sR[v], s6[v]);
+  }
+  // shock flattening: each profile pulled toward the cell value
+  if (fl < R(1)) {
+    const R gl = R(1) - fl;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      sL[v] = fl * sL[v] + gl * s[v][2];
+      sR[v] = fl * sR[v] + gl * s[v][2];
+      s6[v] = fl * s6[v];
+    }
   }
   const R rho = s[0][2];
   const R un = s[NV][2];

@@ -30,6 +30,7 @@ __device__ __forceinline__ Eos<double> eos64(const SchemeConsts &k) {
   e.max_iter = k.max_iter;
   e.plm = k.plm;
   e.linear = k.linear_rs;
+  e.flat = k.flat;
   return e;
 }
 
@@ -88,8 +89,8 @@ __global__ void k_prims(BoxDev b, const SchemeConsts *K, const double *S, double
 // ------------------------------------------------------------ O2+O3 PPM and tracing
 template <int DIR>
 __global__ void k_trace(BoxDev b, const SchemeConsts *K, const StepConsts *SC, const BoxStep *BS,
-                        const double *q, const double *G, double *qm, double *qp, long long V,
-                        Range r) {
+                        const double *q, const double *G, const double *FL, double *qm,
+                        double *qp, long long V, Range r) {
   const Eos<double> E = eos64(*K);
   TraceSrc<double> src;
   src.hdtp = SC->hdtp;
@@ -113,7 +114,8 @@ __global__ void k_trace(BoxDev b, const SchemeConsts *K, const StepConsts *SC, c
       g3[2] = G[2 * b.stride + id];
     }
     double a5[5], b5[5];
-    nyx_f64::trace_cell<double, DIR>(E, sv, q[5 * V + id], g3, dtdx, src, a5, b5);
+    const double fl = FL ? FL[id] : 1.0;
+    nyx_f64::trace_cell<double, DIR>(E, sv, q[5 * V + id], g3, dtdx, src, fl, a5, b5);
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       qm[v * V + id] = a5[v];
@@ -538,9 +540,9 @@ size_t staged_scratch_doubles(long long V) { return (size_t)222 * (size_t)V; }
 // One box, all stages.  Sbox/Snbox/Gbox point at the box's blocks.
 void launch_staged_box(const BoxDev &b, const BoxDev *b_dev, const SchemeConsts *K,
                        const StepConsts *SC, const BoxStep *BSb, const double *Sbox,
-                       const double *Gbox, double *Snbox, double *scratch, long long V,
-                       unsigned long long *dtacc, unsigned *status, double *flux_keep,
-                       int predict_only, cudaStream_t st) {
+                       const double *Gbox, const double *FLbox, double *Snbox, double *scratch,
+                       long long V, unsigned long long *dtacc, unsigned *status,
+                       double *flux_keep, int predict_only, cudaStream_t st) {
   (void)b_dev;
   const int BLK = 256;
   double *q = scratch;
@@ -574,17 +576,20 @@ void launch_staged_box(const BoxDev &b, const BoxDev *b_dev, const SchemeConsts 
   {
     int lo[3] = {L[0] + 2, L[1], L[2]}, hi[3] = {H[0] - 2, H[1], H[2]};
     Range r = make_range(lo, hi);
-    k_trace<0><<<grid_for(r.count, BLK), BLK, 0, st>>>(b, K, SC, BSb, q, Gbox, qm[0], qp[0], V, r);
+    k_trace<0><<<grid_for(r.count, BLK), BLK, 0, st>>>(b, K, SC, BSb, q, Gbox, FLbox, qm[0],
+                                                        qp[0], V, r);
   }
   {
     int lo[3] = {L[0], L[1] + 2, L[2]}, hi[3] = {H[0], H[1] - 2, H[2]};
     Range r = make_range(lo, hi);
-    k_trace<1><<<grid_for(r.count, BLK), BLK, 0, st>>>(b, K, SC, BSb, q, Gbox, qm[1], qp[1], V, r);
+    k_trace<1><<<grid_for(r.count, BLK), BLK, 0, st>>>(b, K, SC, BSb, q, Gbox, FLbox, qm[1],
+                                                        qp[1], V, r);
   }
   {
     int lo[3] = {L[0], L[1], L[2] + 2}, hi[3] = {H[0], H[1], H[2] - 2};
     Range r = make_range(lo, hi);
-    k_trace<2><<<grid_for(r.count, BLK), BLK, 0, st>>>(b, K, SC, BSb, q, Gbox, qm[2], qp[2], V, r);
+    k_trace<2><<<grid_for(r.count, BLK), BLK, 0, st>>>(b, K, SC, BSb, q, Gbox, FLbox, qm[2],
+                                                        qp[2], V, r);
   }
   // normal solves
 #define NORMAL(D)                                                                                \

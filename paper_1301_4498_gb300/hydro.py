@@ -65,7 +65,7 @@ class NyxParams(C.Structure):
                 ("precision", C.c_int), ("grav_corrector", C.c_int), ("batching", C.c_int),
                 ("autotune", C.c_int), ("keep_fluxes", C.c_int), ("coarse_fine", C.c_int),
                 ("grav_energy", C.c_int), ("reconstruction", C.c_int),
-                ("riemann_solver", C.c_int)]
+                ("riemann_solver", C.c_int), ("flattening", C.c_int)]
 
 
 class NyxPoissonParams(C.Structure):
@@ -80,7 +80,8 @@ class NyxLevel(C.Structure):
 class NyxCounters(C.Structure):
     _fields_ = [("launches", C.c_longlong), ("timed_fills", C.c_longlong),
                 ("timed_advances", C.c_longlong), ("fill_ms", C.c_double),
-                ("advance_ms", C.c_double)]
+                ("advance_ms", C.c_double), ("timed_flattens", C.c_longlong),
+                ("flatten_ms", C.c_double)]
 
 
 def header_functions():
@@ -207,6 +208,8 @@ def make_params(**kw) -> NyxParams:
     rs = kw.pop("riemann_solver", None)
     if rs is not None:
         p.riemann_solver = {"two_shock": NYX_RS_TWO_SHOCK, "linear": NYX_RS_LINEAR}.get(rs, rs)
+    if "flattening" in kw:
+        p.flattening = int(bool(kw.pop("flattening")))
     bat = kw.pop("batching", None)
     if bat is not None:
         p.batching = {"persistent": NYX_PERSISTENT, "per_box": NYX_PER_BOX}.get(bat, bat)
@@ -390,7 +393,8 @@ class Plan:
         c = NyxCounters()
         _check(self.lib.nyx_hydro_counters_read(self.h, 1 if reset else 0, C.byref(c)))
         return dict(launches=c.launches, timed_fills=c.timed_fills,
-                    timed_advances=c.timed_advances, fill_ms=c.fill_ms, advance_ms=c.advance_ms)
+                    timed_advances=c.timed_advances, fill_ms=c.fill_ms, advance_ms=c.advance_ms,
+                    timed_flattens=c.timed_flattens, flatten_ms=c.flatten_ms)
 
     def step_host(self, level, host_in, host_out, a_old, a_new, dt=0.0):
         """End-to-end step through host buffers (torch CPU tensors, ideally
