@@ -518,11 +518,14 @@ def run_ours(args, w):
 # reads and writes the coarse cell (336 B per coarse face); average down reads
 # 8 fine cells and writes one coarse cell (432 B per coarse cell).
 AMR_BYTES = {"interp": 54, "reflux": 336, "avgdown": 432}
-# One V-cycle of the self-gravity solve per fine cell: 4 red-black sweeps
-# (read phi and f, write phi: 24 B each), the residual restriction (16 B), the
-# prolongation (24 B) and the residual norm (16 B), times 8/7 for the coarser
-# grids: 174 B.
-VCYCLE_BYTES_PER_CELL = 174
+# One cycle of the self-gravity solve per fine cell.  FP64: 4 red-black
+# sweeps (read phi and f, write phi: 24 B each), the residual restriction
+# (16 B), the prolongation (24 B) and the residual norm (16 B), times 8/7 for
+# the coarser grids: 174 B.  Mixed (iterative refinement): the FP32 V-cycle
+# (4 sweeps of 12 B, restriction 8 B, prolongation 12 B, times 8/7: 78 B),
+# the FP64 residual with its float copy and e = 0 (24 B), the FP64 update of
+# phi (20 B): 122 B.
+VCYCLE_BYTES_PER_CELL = {"fp64": 174, "mixed": 122}
 
 
 def oracle_amr_sample(w, budget_s=12.0):
@@ -690,7 +693,7 @@ def run_amr(args, aw):
     # solve and a warm re-solve; the V-cycle cost is their difference per cycle
     gravity = None
     if not args.no_variants:
-        ps = H.Poisson(cp, four_pi_G=1.0)
+        ps = H.Poisson(cp, four_pi_G=1.0, precision=args.precision)
         gtmp = cp.empty_field(3)
         ps.solve(lc.current, float(a_host[0]), gtmp, warm_start=False)   # warm-up
         torch.cuda.synchronize()
@@ -701,11 +704,12 @@ def run_amr(args, aw):
         cyc0, _ = ps.solve(lc.current, float(a_host[0]), gtmp, warm_start=True)
         t_warm = time.perf_counter() - t0
         per_cycle = (t_cold - t_warm) / max(1, cyc)
-        gbs = VCYCLE_BYTES_PER_CELL * cells_c / per_cycle / 1e9
+        vb = VCYCLE_BYTES_PER_CELL[args.precision]
+        gbs = vb * cells_c / per_cycle / 1e9
         gravity = {"cells": cells_c, "cold_solve_ms": t_cold * 1e3, "cycles": cyc,
                    "relative_residual": res, "warm_resolve_ms": t_warm * 1e3,
                    "warm_cycles": cyc0, "vcycle_ms": per_cycle * 1e3,
-                   "vcycle_alg_bytes_per_cell": VCYCLE_BYTES_PER_CELL,
+                   "vcycle_alg_bytes_per_cell": vb, "precision": args.precision,
                    "achieved_gbs": gbs, "frac_hbm": gbs / peaks["hbm_gbs"], "bound": "hbm"}
         ps.close()
         del gtmp
@@ -881,7 +885,9 @@ def run_cosmo(args, w):
     if args.tile_shape >= 0:
         plan.set_tile_shape(args.tile_shape)
     lev = H.make_level(plan, w.state, None)
-    ps = H.Poisson(plan, four_pi_G=COSMO_FOUR_PI_G)
+    # mixed plans solve by iterative refinement (FP64 residual and update
+    # around FP32 V-cycles), to the same FP64 stopping test
+    ps = H.Poisson(plan, four_pi_G=COSMO_FOUR_PI_G, precision=args.precision)
     xd, ud, md = (torch.tensor(v, device="cuda") for v in (x, u, m))
     rho = ps.dense(1)[0]
     gd = ps.dense(3)
@@ -896,13 +902,16 @@ def run_cosmo(args, w):
     timing = {"gas_advance": 0.0, "particles": 0.0, "solve": 0.0, "corrector": 0.0}
     cyc_total = 0
 
+    pdt_ready = [False]   # dts[1] holds this step's particle dt (from the last kick)
+
     def step(s, record):
         nonlocal g_old, g_new, cyc_total
         a0, a1 = float(a_host[s]), float(a_host[s + 1])
         ah = 0.5 * (a0 + a1)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
         plan.estdt(lev, a[s:s + 1], dts[0:1])
-        ps.pm_estdt(xd, ud, gd, a0, dts[1:2])
+        if not pdt_ready[0]:
+            ps.pm_estdt(xd, ud, gd, a0, dts[1:2])
         torch.minimum(dts[0:1], dts[1:2], out=dts[2:3])
         dt = float(dts[2].item())
         ev[0].record(stream)
@@ -914,7 +923,9 @@ def run_cosmo(args, w):
         cyc, _ = ps.solve(lev.state[1 - lev.cur], a1, g_new, warm_start=True, rho_dm=rho,
                           g_dense=gd)
         ev[3].record(stream)
-        ps.pm_kick(xd, ud, gd, ah, a1, dt)
+        # Step 5 with the next step's particle dt from the kicked particles
+        ps.pm_kick_estdt(xd, ud, gd, ah, a1, dt, dts[1:2])
+        pdt_ready[0] = True
         ev[4].record(stream)
         plan.correct(lev, a[s:s + 1], a[s + 1:s + 2], dts[2:3], g_old, g_new)
         ev[5].record(stream)
@@ -970,6 +981,9 @@ def run_cosmo(args, w):
             "config": {"workload": args.workload, "level": w.name, "valid_cells": cells,
                        "particles": npart, "boxes": w.level.nbox, "precision": args.precision,
                        "step": "Sec. 3.6 Steps 1-6 (g^n from the previous Step 4)",
+                       "poisson": ("iterative refinement: FP64 residual and update, FP32 "
+                                   "V-cycles" if args.precision == "mixed"
+                                   else "FP64 V-cycles"),
                        "tile": [tx, ty], "l2": "inputs larger than L2",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
             "particle_updates_per_s": ws * npart * K / (ms_max / 1e3),

@@ -295,8 +295,8 @@ int nyx_plan_destroy(nyx_plan *plan);
  * sweeps on the coarsest grid) until max|f - L phi| <= tol max|f|, then
  * g = -grad phi by centred differences between adjacent cell centres.  The
  * solve runs on the dense grid of the domain (gathered from the boxes); the
- * object keeps phi for a warm start.  Dark matter is not included
- * (rho is the gas density, component 0 of the state). */
+ * object keeps phi for a warm start.  rho is the gas density (component 0
+ * of the state) plus the dark matter's dense density when one is given. */
 typedef struct nyx_poisson nyx_poisson;
 typedef struct {
   double tol;         /* relative max-norm residual (1e-12) */
@@ -305,6 +305,10 @@ typedef struct {
   int coarse_sweeps;  /* sweeps on the coarsest grid (40) */
   int min_size;       /* smallest coarse extent (2) */
   double four_pi_G;   /* 4 pi G in code units (1) */
+  int precision;      /* NYX_FP64 (default): every operation in FP64.  NYX_MIXED:
+                         iterative refinement, each cycle an FP64 residual, one
+                         FP32 V-cycle on the correction equation from zero, and
+                         an FP64 update of phi; the same FP64 stopping test */
 } nyx_poisson_params;
 
 void nyx_poisson_default_params(nyx_poisson_params *params);
@@ -339,7 +343,11 @@ int nyx_poisson_solve(nyx_poisson *ps, const double *state, const double *rho_dm
  *    x += dt u / a_half, wrapped into the domain (one period at most);
  *  - kick (Step 5): u = (a_half u + dt/2 g^{n+1}(x)) / a_new;
  *  - estdt (Sec. 3.5): *dt_dev = min(cfl_dm a dx / max |u_d|,
- *    sqrt(dx / max |g_d|)) over the particles (+inf if both maxima are 0).
+ *    sqrt(dx / max |g_d|)) over the particles (+inf if both maxima are 0);
+ *  - kick_estdt: kick, then estdt of the kicked particles at a = a_new with
+ *    the g^{n+1} the kick used (the next step's particle dt), in one pass.
+ * The kernels multiply by reciprocals and use fused multiply-adds, so they
+ * match a plain evaluation of these formulas to round-off.
  * Stream-ordered on the plan's stream; scalars are host doubles. */
 int nyx_pm_deposit(nyx_poisson *ps, const double *x, const double *m, long long np,
                    double *rho_dm);
@@ -349,6 +357,9 @@ int nyx_pm_kick(nyx_poisson *ps, const double *x, double *u, long long np, const
                 double a_half, double a_new, double dt);
 int nyx_pm_estdt(nyx_poisson *ps, const double *x, const double *u, long long np,
                  const double *g_dense, double a, double cfl_dm, double *dt_dev);
+int nyx_pm_kick_estdt(nyx_poisson *ps, const double *x, double *u, long long np,
+                      const double *g_dense, double a_half, double a_new, double dt,
+                      double cfl_dm, double *dt_dev);
 
 /* Copy phi (dense, x fastest, domain extents) to a device buffer. */
 int nyx_poisson_phi(nyx_poisson *ps, double *phi_out);

@@ -10,8 +10,11 @@
 // = mean of the 8 fine residuals, prolongation = the coarse correction
 // (piecewise constant).  Every sum runs in a fixed order (rows, planes,
 // domain; the 8 children in index order) and the residual norm is a max,
-// so the result does not depend on scheduling.  FP64 throughout; this unit
-// is built without FMA contraction.
+// so the result does not depend on scheduling.  FP64 throughout by default;
+// this unit is built without FMA contraction.  Mixed precision (on request):
+// iterative refinement, each cycle an FP64 residual r = f - L phi, one FP32
+// V-cycle of the same multigrid on L e = r from e = 0, and phi += e in FP64;
+// the stopping test is the same FP64 max-norm residual.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,8 +41,9 @@ __device__ __forceinline__ long long didx(const Dims &d, int i, int j, int k) {
 }
 __device__ __forceinline__ int wrp(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
-__device__ __forceinline__ double nbsum(const double *u, const Dims &d, int i, int j, int k) {
-  double s = u[didx(d, wrp(i - 1, d.n[0]), j, k)];
+template <class T>
+__device__ __forceinline__ T nbsum(const T *u, const Dims &d, int i, int j, int k) {
+  T s = u[didx(d, wrp(i - 1, d.n[0]), j, k)];
   s = s + u[didx(d, wrp(i + 1, d.n[0]), j, k)];
   s = s + u[didx(d, i, wrp(j - 1, d.n[1]), k)];
   s = s + u[didx(d, i, wrp(j + 1, d.n[1]), k)];
@@ -48,10 +52,11 @@ __device__ __forceinline__ double nbsum(const double *u, const Dims &d, int i, i
   return s;
 }
 
-__device__ __forceinline__ double resid_at(const double *phi, const double *f, const Dims &d,
-                                           double ih2, int i, int j, int k) {
+template <class T>
+__device__ __forceinline__ T resid_at(const T *phi, const T *f, const Dims &d, T ih2, int i, int j,
+                                      int k) {
   const long long id = didx(d, i, j, k);
-  return f[id] - (nbsum(phi, d, i, j, k) - 6.0 * phi[id]) * ih2;
+  return f[id] - (nbsum(phi, d, i, j, k) - T(6) * phi[id]) * ih2;
 }
 
 // valid cell t of the level (box by binary search of the cell offsets)
@@ -110,71 +115,79 @@ __global__ void k_pg_grav_dense(const double *u, Dims d, double hdx, double *g) 
 // ---------------------------------------------------------------- dark matter
 // Cloud in cell (Sec. 3.4): cell-centred coordinate s = x/dx - 1/2, the
 // particle's cube overlaps cells floor(s) (weight 1 - frac(s)) and floor(s)+1.
-__device__ __forceinline__ void cic(double x, double dx, int n, int &i0, double &w0) {
-  const double s = x / dx - 0.5;
+// The particle kernels compare with the oracle within round-off (the deposit
+// adds with atomics), so they multiply by host reciprocals instead of
+// dividing and accumulate with fused multiply-adds: the FP64 pipe is their
+// bound.
+__device__ __forceinline__ void cic(double x, double idx, int n, int &i0, double &w0) {
+  const double s = x * idx - 0.5;
   const double fl = floor(s);
   w0 = 1.0 - (s - fl);
   i0 = wrp((int)fl, n);
 }
 
-__device__ __forceinline__ void g_at(const double *g, const Dims &d, double dx, double x0,
+__device__ __forceinline__ void g_at(const double *g, const Dims &d, double idx, double x0,
                                      double x1, double x2, double (&out)[3]) {
   const long long N = (long long)d.n[0] * d.n[1] * d.n[2];
   int i0, j0, k0;
   double wx, wy, wz;
-  cic(x0, dx, d.n[0], i0, wx);
-  cic(x1, dx, d.n[1], j0, wy);
-  cic(x2, dx, d.n[2], k0, wz);
+  cic(x0, idx, d.n[0], i0, wx);
+  cic(x1, idx, d.n[1], j0, wy);
+  cic(x2, idx, d.n[2], k0, wz);
+  const int i1 = wrp(i0 + 1, d.n[0]), j1 = wrp(j0 + 1, d.n[1]), k1 = wrp(k0 + 1, d.n[2]);
+  const double vx = 1.0 - wx, vy = 1.0 - wy, vz = 1.0 - wz;
   out[0] = out[1] = out[2] = 0.0;
 #pragma unroll
   for (int o = 0; o < 8; ++o) {
-    const int I = (o & 1) ? wrp(i0 + 1, d.n[0]) : i0;
-    const int J = ((o >> 1) & 1) ? wrp(j0 + 1, d.n[1]) : j0;
-    const int K = (o >> 2) ? wrp(k0 + 1, d.n[2]) : k0;
-    const double w = ((o & 1) ? 1.0 - wx : wx) * (((o >> 1) & 1) ? 1.0 - wy : wy) *
-                     ((o >> 2) ? 1.0 - wz : wz);
+    const int I = (o & 1) ? i1 : i0;
+    const int J = ((o >> 1) & 1) ? j1 : j0;
+    const int K = (o >> 2) ? k1 : k0;
+    const double w = ((o & 1) ? vx : wx) * (((o >> 1) & 1) ? vy : wy) * ((o >> 2) ? vz : wz);
     const long long id = didx(d, I, J, K);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) out[c] = out[c] + w * g[c * N + id];
+    for (int c = 0; c < 3; ++c) out[c] = fma(w, g[c * N + id], out[c]);
   }
 }
 
-__global__ void k_pm_deposit(const double *x, const double *m, long long np, Dims d, double dx,
+__global__ void k_pm_deposit(const double *x, const double *m, long long np, Dims d, double idx,
                              double iv, double *rho) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np;
        p += (long long)gridDim.x * blockDim.x) {
     int i0, j0, k0;
     double wx, wy, wz;
-    cic(x[p], dx, d.n[0], i0, wx);
-    cic(x[np + p], dx, d.n[1], j0, wy);
-    cic(x[2 * np + p], dx, d.n[2], k0, wz);
-    const double mp = m[p];
+    cic(x[p], idx, d.n[0], i0, wx);
+    cic(x[np + p], idx, d.n[1], j0, wy);
+    cic(x[2 * np + p], idx, d.n[2], k0, wz);
+    const int i1 = wrp(i0 + 1, d.n[0]), j1 = wrp(j0 + 1, d.n[1]), k1 = wrp(k0 + 1, d.n[2]);
+    const double vx = 1.0 - wx, vy = 1.0 - wy, vz = 1.0 - wz;
+    const double mp = m[p] * iv;
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
-      const int I = (o & 1) ? wrp(i0 + 1, d.n[0]) : i0;
-      const int J = ((o >> 1) & 1) ? wrp(j0 + 1, d.n[1]) : j0;
-      const int K = (o >> 2) ? wrp(k0 + 1, d.n[2]) : k0;
-      const double w = ((o & 1) ? 1.0 - wx : wx) * (((o >> 1) & 1) ? 1.0 - wy : wy) *
-                       ((o >> 2) ? 1.0 - wz : wz);
-      atomicAdd(&rho[didx(d, I, J, K)], mp * w * iv);
+      const int I = (o & 1) ? i1 : i0;
+      const int J = ((o >> 1) & 1) ? j1 : j0;
+      const int K = (o >> 2) ? k1 : k0;
+      const double w = ((o & 1) ? vx : wx) * (((o >> 1) & 1) ? vy : wy) * ((o >> 2) ? vz : wz);
+      atomicAdd(&rho[didx(d, I, J, K)], mp * w);
     }
   }
 }
 
-// Step 3: kick by dt/2 with g^n, drift by dt at a^{n+1/2}, periodic wrap
+// Step 3: kick by dt/2 with g^n, drift by dt at a^{n+1/2}, periodic wrap.
+// ia_half = 1/a_half, dta = dt/a_half.
 __global__ void k_pm_kick_drift(double *x, double *u, long long np, const double *g, Dims d,
-                                double dx, double a_old, double a_half, double dt) {
+                                double dx, double idx, double a_old, double ia_half, double hdt,
+                                double dta) {
   const double L[3] = {d.n[0] * dx, d.n[1] * dx, d.n[2] * dx};
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np;
        p += (long long)gridDim.x * blockDim.x) {
     double gp[3];
     const double xp[3] = {x[p], x[np + p], x[2 * np + p]};
-    g_at(g, d, dx, xp[0], xp[1], xp[2], gp);
+    g_at(g, d, idx, xp[0], xp[1], xp[2], gp);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const double uh = (a_old * u[c * np + p] + 0.5 * dt * gp[c]) / a_half;
+      const double uh = fma(a_old, u[c * np + p], hdt * gp[c]) * ia_half;
       u[c * np + p] = uh;
-      double xn = xp[c] + dt / a_half * uh;
+      double xn = fma(dta, uh, xp[c]);
       if (xn < 0.0) xn = xn + L[c];
       if (xn >= L[c]) xn = xn - L[c];
       x[c * np + p] = xn;
@@ -182,26 +195,44 @@ __global__ void k_pm_kick_drift(double *x, double *u, long long np, const double
   }
 }
 
-// Step 5: kick by dt/2 with g^{n+1}
+// Step 5: kick by dt/2 with g^{n+1} (ia_new = 1/a_new).  With mx, also the
+// maxima of |u_d| and |g_d| of the kicked particles (Sec. 3.5), for the
+// particle time step of the next step: the same values k_pm_maxes forms.
 __global__ void k_pm_kick(const double *x, double *u, long long np, const double *g, Dims d,
-                          double dx, double a_half, double a_new, double dt) {
+                          double idx, double a_half, double ia_new, double hdt,
+                          unsigned long long *mx) {
+  double um = 0.0, gm = 0.0;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np;
        p += (long long)gridDim.x * blockDim.x) {
     double gp[3];
-    g_at(g, d, dx, x[p], x[np + p], x[2 * np + p], gp);
+    g_at(g, d, idx, x[p], x[np + p], x[2 * np + p], gp);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) u[c * np + p] = (a_half * u[c * np + p] + 0.5 * dt * gp[c]) / a_new;
+    for (int c = 0; c < 3; ++c) {
+      const double un = fma(a_half, u[c * np + p], hdt * gp[c]) * ia_new;
+      u[c * np + p] = un;
+      um = fmax(um, fabs(un));
+      gm = fmax(gm, fabs(gp[c]));
+    }
+  }
+  if (!mx) return;
+  for (int o = 16; o > 0; o >>= 1) {
+    um = fmax(um, __shfl_xor_sync(0xffffffffu, um, o));
+    gm = fmax(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&mx[0], (unsigned long long)__double_as_longlong(um));
+    atomicMax(&mx[1], (unsigned long long)__double_as_longlong(gm));
   }
 }
 
 // Sec. 3.5: maxima of |u_d| and |g_d| at the particles (ordered bits)
 __global__ void k_pm_maxes(const double *x, const double *u, long long np, const double *g,
-                           Dims d, double dx, unsigned long long *mx) {
+                           Dims d, double idx, unsigned long long *mx) {
   double um = 0.0, gm = 0.0;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np;
        p += (long long)gridDim.x * blockDim.x) {
     double gp[3];
-    g_at(g, d, dx, x[p], x[np + p], x[2 * np + p], gp);
+    g_at(g, d, idx, x[p], x[np + p], x[2 * np + p], gp);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       um = fmax(um, fabs(u[c * np + p]));
@@ -270,69 +301,82 @@ __global__ void k_pg_rhs(double *f, long long n, const double *mean, double c,
 }
 
 // one colour of a red-black sweep: cells with (i + j + k) % 2 == color
-__global__ void k_pg_sweep(double *phi, const double *f, Dims d, double h2, int color) {
-  const int hx = d.n[0] / 2;
-  const long long n = (long long)hx * d.n[1] * d.n[2];
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i2 = (int)(t % hx);
-    const long long u = t / hx;
-    const int j = (int)(u % d.n[1]);
-    const int k = (int)(u / d.n[1]);
-    const int i = 2 * i2 + ((j + k + color) & 1);
-    const long long id = didx(d, i, j, k);
-    phi[id] = (nbsum(phi, d, i, j, k) - h2 * f[id]) * (1.0 / 6.0);
-  }
+// (launched on a grid3 of (n_x / 2, n_y, n_z): no index division)
+template <class T>
+__global__ void k_pg_sweep(T *phi, const T *f, Dims d, T h2, int color) {
+  const int i2 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i2 >= d.n[0] / 2) return;
+  const int j = blockIdx.y, k = blockIdx.z;
+  const int i = 2 * i2 + ((j + k + color) & 1);
+  const long long id = didx(d, i, j, k);
+  phi[id] = (nbsum(phi, d, i, j, k) - h2 * f[id]) * (T(1) / T(6));
 }
 
+// (grid3 of (n_x, n_y, n_z))
 __global__ void k_pg_resid_max(const double *phi, const double *f, Dims d, double ih2,
                                unsigned long long *out) {
-  const long long n = (long long)d.n[0] * d.n[1] * d.n[2];
   double loc = 0.0;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % d.n[0]);
-    const long long u = t / d.n[0];
-    const int j = (int)(u % d.n[1]);
-    const int k = (int)(u / d.n[1]);
-    loc = fmax(loc, fabs(resid_at(phi, f, d, ih2, i, j, k)));
-  }
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < d.n[0]) loc = fabs(resid_at(phi, f, d, ih2, i, (int)blockIdx.y, (int)blockIdx.z));
   for (int o = 16; o > 0; o >>= 1) loc = fmax(loc, __shfl_xor_sync(0xffffffffu, loc, o));
   if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(loc));
 }
 
 // coarse f = mean of the 8 fine residuals (index order), coarse phi = 0
-__global__ void k_pg_restrict(const double *phi, const double *f, Dims d, double ih2,
-                              double *fc, double *phic, Dims dc) {
-  const long long n = (long long)dc.n[0] * dc.n[1] * dc.n[2];
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % dc.n[0]);
-    const long long u = t / dc.n[0];
-    const int j = (int)(u % dc.n[1]);
-    const int k = (int)(u / dc.n[1]);
-    double s = 0.0;
+// (grid3 of the coarse grid)
+template <class T>
+__global__ void k_pg_restrict(const T *phi, const T *f, Dims d, T ih2, T *fc, T *phic, Dims dc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < dc.n[0]) {
+    const int j = blockIdx.y, k = blockIdx.z;
+    const long long t = didx(dc, i, j, k);
+    T s = T(0);
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
-      const double r =
+      const T r =
           resid_at(phi, f, d, ih2, 2 * i + (o & 1), 2 * j + ((o >> 1) & 1), 2 * k + (o >> 2));
       s = (o == 0) ? r : s + r;
     }
-    fc[t] = 0.125 * s;
-    phic[t] = 0.0;
+    fc[t] = T(0.125) * s;
+    phic[t] = T(0);
   }
 }
 
-__global__ void k_pg_prolong(double *phi, Dims d, const double *phic, Dims dc) {
-  const long long n = (long long)d.n[0] * d.n[1] * d.n[2];
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % d.n[0]);
-    const long long u = t / d.n[0];
-    const int j = (int)(u % d.n[1]);
-    const int k = (int)(u / d.n[1]);
-    phi[t] = phi[t] + phic[didx(dc, i / 2, j / 2, k / 2)];
+// (grid3 of the fine grid)
+template <class T>
+__global__ void k_pg_prolong(T *phi, Dims d, const T *phic, Dims dc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n[0]) return;
+  const int j = blockIdx.y, k = blockIdx.z;
+  const long long t = didx(d, i, j, k);
+  phi[t] = phi[t] + phic[didx(dc, i / 2, j / 2, k / 2)];
+}
+
+// Mixed precision: the FP64 residual r = f - L phi of the finest grid as
+// float (the right-hand side of the FP32 correction solve), its FP64 max
+// norm, and the correction's start e = 0.
+// (grid3 of (n_x, n_y, n_z))
+__global__ void k_pg_resid32(const double *phi, const double *f, Dims d, double ih2, float *r,
+                             float *e, unsigned long long *out) {
+  double loc = 0.0;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < d.n[0]) {
+    const int j = blockIdx.y, k = blockIdx.z;
+    const double v = resid_at(phi, f, d, ih2, i, j, k);
+    const long long t = didx(d, i, j, k);
+    r[t] = __double2float_rn(v);
+    e[t] = 0.0f;
+    loc = fabs(v);
   }
+  for (int o = 16; o > 0; o >>= 1) loc = fmax(loc, __shfl_xor_sync(0xffffffffu, loc, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(loc));
+}
+
+// phi += e (the FP32 correction), in FP64
+__global__ void k_pg_correct(double *phi, const float *e, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    phi[t] = phi[t] + (double)e[t];
 }
 
 // g = -grad phi (centred) into the level's gravity field, valid cells
@@ -359,11 +403,26 @@ int gridn(long long n, int block) {
   return (int)std::max<long long>(1, std::min<long long>(g, 152 * 32));
 }
 
-struct Level {
-  Dims d;
-  double h2, ih2;
-  double *phi = nullptr, *f = nullptr;
+// Launch shape covering an (nx, ny, nz) index box: x in blocks of up to 128
+// threads, y and z one block row each (extents are at most 65535).
+struct Grid3 {
+  dim3 g, b;
 };
+Grid3 grid3(int nx, int ny, int nz) {
+  Grid3 r;
+  const int bx = std::min(128, (nx + 31) / 32 * 32);
+  r.b = dim3(bx, 1, 1);
+  r.g = dim3((nx + bx - 1) / bx, ny, nz);
+  return r;
+}
+
+template <class T>
+struct LevelT {
+  Dims d;
+  T h2, ih2;
+  T *phi = nullptr, *f = nullptr;
+};
+using Level = LevelT<double>;
 
 }  // namespace
 
@@ -371,6 +430,7 @@ struct nyx_poisson {
   nyx_plan *P = nullptr;
   nyx_poisson_params prm{};
   std::vector<Level> L;
+  std::vector<LevelT<float>> L32;  // mixed precision: the FP32 correction grids
   int *d_box_lo = nullptr;       // box lo relative to the domain origin
   double *d_rows = nullptr, *d_planes = nullptr, *d_scal = nullptr;  // scal: mean
   unsigned long long *d_max = nullptr;
@@ -383,6 +443,10 @@ namespace {
 void free_poisson(nyx_poisson *S) {
   if (!S) return;
   for (auto &l : S->L) {
+    if (l.phi) cudaFree(l.phi);
+    if (l.f) cudaFree(l.f);
+  }
+  for (auto &l : S->L32) {
     if (l.phi) cudaFree(l.phi);
     if (l.f) cudaFree(l.f);
   }
@@ -402,27 +466,29 @@ int read_max(nyx_poisson *S, double *out) {
   return NYX_OK;
 }
 
-void sweep(nyx_poisson *S, Level &l) {
-  const long long n = (long long)(l.d.n[0] / 2) * l.d.n[1] * l.d.n[2];
+template <class T>
+void sweep(nyx_poisson *S, LevelT<T> &l) {
+  const Grid3 G = grid3(l.d.n[0] / 2, l.d.n[1], l.d.n[2]);
   for (int c = 0; c < 2; ++c)
-    k_pg_sweep<<<gridn(n, 256), 256, 0, S->P->stream>>>(l.phi, l.f, l.d, l.h2, c);
+    k_pg_sweep<T><<<G.g, G.b, 0, S->P->stream>>>(l.phi, l.f, l.d, l.h2, c);
   S->launches += 2;
 }
 
-void vcycle(nyx_poisson *S, size_t l) {
-  Level &g = S->L[l];
-  if (l + 1 == S->L.size()) {
+template <class T>
+void vcycle(nyx_poisson *S, std::vector<LevelT<T>> &L, size_t l) {
+  LevelT<T> &g = L[l];
+  if (l + 1 == L.size()) {
     for (int s = 0; s < S->prm.coarse_sweeps; ++s) sweep(S, g);
     return;
   }
   for (int s = 0; s < S->prm.pre; ++s) sweep(S, g);
-  Level &c = S->L[l + 1];
-  const long long nc = (long long)c.d.n[0] * c.d.n[1] * c.d.n[2];
-  k_pg_restrict<<<gridn(nc, 256), 256, 0, S->P->stream>>>(g.phi, g.f, g.d, g.ih2, c.f, c.phi, c.d);
+  LevelT<T> &c = L[l + 1];
+  const Grid3 Gc = grid3(c.d.n[0], c.d.n[1], c.d.n[2]);
+  k_pg_restrict<T><<<Gc.g, Gc.b, 0, S->P->stream>>>(g.phi, g.f, g.d, g.ih2, c.f, c.phi, c.d);
   S->launches += 1;
-  vcycle(S, l + 1);
-  const long long nf = (long long)g.d.n[0] * g.d.n[1] * g.d.n[2];
-  k_pg_prolong<<<gridn(nf, 256), 256, 0, S->P->stream>>>(g.phi, g.d, c.phi, c.d);
+  vcycle(S, L, l + 1);
+  const Grid3 Gf = grid3(g.d.n[0], g.d.n[1], g.d.n[2]);
+  k_pg_prolong<T><<<Gf.g, Gf.b, 0, S->P->stream>>>(g.phi, g.d, c.phi, c.d);
   S->launches += 1;
   for (int s = 0; s < S->prm.post; ++s) sweep(S, g);
 }
@@ -430,10 +496,30 @@ void vcycle(nyx_poisson *S, size_t l) {
 int resid_max(nyx_poisson *S, double *out) {
   Level &g = S->L[0];
   CK(cudaMemsetAsync(S->d_max, 0, sizeof(unsigned long long), S->P->stream));
-  const long long n = (long long)g.d.n[0] * g.d.n[1] * g.d.n[2];
-  k_pg_resid_max<<<gridn(n, 256), 256, 0, S->P->stream>>>(g.phi, g.f, g.d, g.ih2, S->d_max);
+  const Grid3 G = grid3(g.d.n[0], g.d.n[1], g.d.n[2]);
+  if (S->L32.empty()) {
+    k_pg_resid_max<<<G.g, G.b, 0, S->P->stream>>>(g.phi, g.f, g.d, g.ih2, S->d_max);
+  } else {  // also the FP32 right-hand side of the next correction, and e = 0
+    LevelT<float> &g32 = S->L32[0];
+    k_pg_resid32<<<G.g, G.b, 0, S->P->stream>>>(g.phi, g.f, g.d, g.ih2, g32.f, g32.phi, S->d_max);
+  }
   S->launches += 1;
   return read_max(S, out);
+}
+
+// One cycle: a V-cycle on phi (FP64), or a refinement step (FP32 V-cycle on
+// the correction equation whose right-hand side resid_max left, then phi +=
+// e in FP64).
+void cycle(nyx_poisson *S) {
+  if (S->L32.empty()) {
+    vcycle(S, S->L, 0);
+    return;
+  }
+  vcycle(S, S->L32, 0);
+  Level &g = S->L[0];
+  const long long n = (long long)g.d.n[0] * g.d.n[1] * g.d.n[2];
+  k_pg_correct<<<gridn(n, 256), 256, 0, S->P->stream>>>(g.phi, S->L32[0].phi, n);
+  S->launches += 1;
 }
 
 }  // namespace
@@ -449,6 +535,7 @@ void nyx_poisson_default_params(nyx_poisson_params *p) {
   p->coarse_sweeps = 40;
   p->min_size = 2;
   p->four_pi_G = 1.0;
+  p->precision = NYX_FP64;
 }
 
 int nyx_poisson_create(nyx_plan *P, const nyx_poisson_params *prm, nyx_poisson **out) {
@@ -470,7 +557,8 @@ int nyx_poisson_create(nyx_plan *P, const nyx_poisson_params *prm, nyx_poisson *
   if (P->total_cells != (long long)n[0] * n[1] * n[2])
     return fail(NYX_EINVAL, "the level's boxes must tile its domain");
   if (prm->pre < 0 || prm->post < 0 || prm->coarse_sweeps < 1 || prm->max_cycles < 0 ||
-      prm->min_size < 1 || !(prm->tol > 0.0))
+      prm->min_size < 1 || !(prm->tol > 0.0) ||
+      (prm->precision != NYX_FP64 && prm->precision != NYX_MIXED))
     return fail(NYX_EINVAL, "bad Poisson parameters");
   nyx_poisson *S = new nyx_poisson;
   S->P = P;
@@ -493,6 +581,19 @@ int nyx_poisson_create(nyx_plan *P, const nyx_poisson_params *prm, nyx_poisson *
     }
     cudaMemset(l.phi, 0, v * sizeof(double));
     S->L.push_back(l);
+    if (prm->precision == NYX_MIXED) {
+      LevelT<float> l32;
+      l32.d = l.d;
+      l32.h2 = (float)l.h2;
+      l32.ih2 = (float)l.ih2;
+      if (cudaMalloc(&l32.phi, v * sizeof(float)) != cudaSuccess ||
+          cudaMalloc(&l32.f, v * sizeof(float)) != cudaSuccess) {
+        S->L32.push_back(l32);
+        rc = fail(NYX_ENOMEM, "Poisson grid allocation failed");
+        break;
+      }
+      S->L32.push_back(l32);
+    }
     bool ok = S->L.size() < 32;
     for (int a = 0; a < 3; ++a)
       if (m[a] % 4 || m[a] < 2 * prm->min_size) ok = false;
@@ -552,7 +653,7 @@ int nyx_poisson_solve(nyx_poisson *S, const double *state, const double *rho_dm,
   const double target = S->prm.tol * fmax;
   int cyc = 0;
   while (res > target && cyc < S->prm.max_cycles) {
-    vcycle(S, 0);
+    cycle(S);
     ++cyc;
     if ((rc = resid_max(S, &res))) return rc;
   }
@@ -585,7 +686,8 @@ int nyx_pm_deposit(nyx_poisson *S, const double *x, const double *m, long long n
   CK(cudaMemsetAsync(rho_dm, 0, N * sizeof(double), S->P->stream));
   if (np) {
     const double iv = 1.0 / (S->dx * S->dx * S->dx);
-    k_pm_deposit<<<gridn(np, 256), 256, 0, S->P->stream>>>(x, m, np, g0.d, S->dx, iv, rho_dm);
+    k_pm_deposit<<<gridn(np, 256), 256, 0, S->P->stream>>>(x, m, np, g0.d, 1.0 / S->dx, iv,
+                                                           rho_dm);
     S->P->launches += 1;
   }
   cudaError_t e = cudaGetLastError();
@@ -594,26 +696,49 @@ int nyx_pm_deposit(nyx_poisson *S, const double *x, const double *m, long long n
 
 int nyx_pm_kick_drift(nyx_poisson *S, double *x, double *u, long long np, const double *g_dense,
                       double a_old, double a_half, double dt) {
-  if (!S || !g_dense || np < 0 || (np && (!x || !u))) return fail(NYX_EINVAL, "bad argument");
+  if (!S || !g_dense || np < 0 || (np && (!x || !u)) || !(a_half > 0.0))
+    return fail(NYX_EINVAL, "bad argument");
   if (np) {
-    k_pm_kick_drift<<<gridn(np, 256), 256, 0, S->P->stream>>>(x, u, np, g_dense, S->L[0].d,
-                                                              S->dx, a_old, a_half, dt);
+    k_pm_kick_drift<<<gridn(np, 256), 256, 0, S->P->stream>>>(
+        x, u, np, g_dense, S->L[0].d, S->dx, 1.0 / S->dx, a_old, 1.0 / a_half, 0.5 * dt,
+        dt / a_half);
     S->P->launches += 1;
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? NYX_OK : cuda_fail(e, "kick-drift launch");
 }
 
-int nyx_pm_kick(nyx_poisson *S, const double *x, double *u, long long np, const double *g_dense,
-                double a_half, double a_new, double dt) {
-  if (!S || !g_dense || np < 0 || (np && (!x || !u))) return fail(NYX_EINVAL, "bad argument");
+static int pm_kick_impl(nyx_poisson *S, const double *x, double *u, long long np,
+                        const double *g_dense, double a_half, double a_new, double dt,
+                        unsigned long long *mx) {
+  if (!S || !g_dense || np < 0 || (np && (!x || !u)) || !(a_new > 0.0))
+    return fail(NYX_EINVAL, "bad argument");
   if (np) {
-    k_pm_kick<<<gridn(np, 256), 256, 0, S->P->stream>>>(x, u, np, g_dense, S->L[0].d, S->dx,
-                                                        a_half, a_new, dt);
+    k_pm_kick<<<gridn(np, 256), 256, 0, S->P->stream>>>(x, u, np, g_dense, S->L[0].d,
+                                                        1.0 / S->dx, a_half, 1.0 / a_new,
+                                                        0.5 * dt, mx);
     S->P->launches += 1;
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? NYX_OK : cuda_fail(e, "kick launch");
+}
+
+int nyx_pm_kick(nyx_poisson *S, const double *x, double *u, long long np, const double *g_dense,
+                double a_half, double a_new, double dt) {
+  return pm_kick_impl(S, x, u, np, g_dense, a_half, a_new, dt, nullptr);
+}
+
+int nyx_pm_kick_estdt(nyx_poisson *S, const double *x, double *u, long long np,
+                      const double *g_dense, double a_half, double a_new, double dt,
+                      double cfl_dm, double *dt_dev) {
+  if (!S || !dt_dev) return fail(NYX_EINVAL, "bad argument");
+  CK(cudaMemsetAsync(S->d_max, 0, 2 * sizeof(unsigned long long), S->P->stream));
+  int rc = pm_kick_impl(S, x, u, np, g_dense, a_half, a_new, dt, S->d_max);
+  if (rc) return rc;
+  k_pm_dt<<<1, 1, 0, S->P->stream>>>(S->d_max, a_new, S->dx, cfl_dm, dt_dev);
+  S->P->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? NYX_OK : cuda_fail(e, "particle dt launch");
 }
 
 int nyx_pm_estdt(nyx_poisson *S, const double *x, const double *u, long long np,
@@ -622,8 +747,8 @@ int nyx_pm_estdt(nyx_poisson *S, const double *x, const double *u, long long np,
     return fail(NYX_EINVAL, "bad argument");
   CK(cudaMemsetAsync(S->d_max, 0, 2 * sizeof(unsigned long long), S->P->stream));
   if (np)
-    k_pm_maxes<<<gridn(np, 256), 256, 0, S->P->stream>>>(x, u, np, g_dense, S->L[0].d, S->dx,
-                                                         S->d_max);
+    k_pm_maxes<<<gridn(np, 256), 256, 0, S->P->stream>>>(x, u, np, g_dense, S->L[0].d,
+                                                         1.0 / S->dx, S->d_max);
   k_pm_dt<<<1, 1, 0, S->P->stream>>>(S->d_max, a, S->dx, cfl_dm, dt_dev);
   S->P->launches += np ? 2 : 1;
   cudaError_t e = cudaGetLastError();

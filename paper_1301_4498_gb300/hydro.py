@@ -70,7 +70,8 @@ class NyxParams(C.Structure):
 
 class NyxPoissonParams(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_cycles", C.c_int), ("pre", C.c_int), ("post", C.c_int),
-                ("coarse_sweeps", C.c_int), ("min_size", C.c_int), ("four_pi_G", C.c_double)]
+                ("coarse_sweeps", C.c_int), ("min_size", C.c_int), ("four_pi_G", C.c_double),
+                ("precision", C.c_int)]
 
 
 class NyxLevel(C.Structure):
@@ -133,7 +134,10 @@ def load_library(path: str | None = None):
                                     C.c_double]
     L.nyx_pm_kick.argtypes = [vp, vp, vp, C.c_longlong, vp, C.c_double, C.c_double, C.c_double]
     L.nyx_pm_estdt.argtypes = [vp, vp, vp, C.c_longlong, vp, C.c_double, C.c_double, vp]
-    for name in ("nyx_pm_deposit", "nyx_pm_kick_drift", "nyx_pm_kick", "nyx_pm_estdt"):
+    L.nyx_pm_kick_estdt.argtypes = [vp, vp, vp, C.c_longlong, vp, C.c_double, C.c_double,
+                                    C.c_double, C.c_double, vp]
+    for name in ("nyx_pm_deposit", "nyx_pm_kick_drift", "nyx_pm_kick", "nyx_pm_estdt",
+                 "nyx_pm_kick_estdt"):
         getattr(L, name).restype = C.c_int
     L.nyx_poisson_phi.argtypes = [vp, vp]
     L.nyx_poisson_destroy.argtypes = [vp]
@@ -447,6 +451,9 @@ class Poisson:
         self.plan = plan
         p = NyxPoissonParams()
         self.lib.nyx_poisson_default_params(C.byref(p))
+        prec = params.pop("precision", None)
+        if prec is not None:
+            p.precision = {"fp64": NYX_FP64, "mixed": NYX_MIXED}.get(prec, prec)
         for k, v in params.items():
             setattr(p, k, v)
         self.params = p
@@ -485,6 +492,13 @@ class Poisson:
         with self.plan.ordered():
             _check(self.lib.nyx_pm_kick(self.h, _ptr(x), _ptr(u), x.shape[1], _ptr(g),
                                         float(a_half), float(a_new), float(dt)))
+
+    def pm_kick_estdt(self, x, u, g, a_half, a_new, dt, dt_dev, cfl_dm=0.5):
+        """Kick (Step 5), then the particle dt of the kicked particles at a_new."""
+        with self.plan.ordered():
+            _check(self.lib.nyx_pm_kick_estdt(self.h, _ptr(x), _ptr(u), x.shape[1], _ptr(g),
+                                              float(a_half), float(a_new), float(dt),
+                                              float(cfl_dm), _ptr(dt_dev)))
 
     def pm_estdt(self, x, u, g, a, dt_dev, cfl_dm=0.5):
         with self.plan.ordered():

@@ -116,3 +116,32 @@ def test_cosmological_step_matches_the_oracle():
         assert num <= 1e-12 * den, c
     ps.close()
     plan.close()
+
+
+def test_fused_kick_and_time_step():
+    """nyx_pm_kick_estdt: the kick of nyx_pm_kick and the particle dt that
+    nyx_pm_estdt gives for the kicked particles, from one pass (bitwise)."""
+    w, n, dx, x, u, m = _case()
+    plan = H.Plan(w.level, gamma=w.gamma, cfl=w.cfl, precision="fp64")
+    lev = H.make_level(plan, w.state, None)
+    ps = H.Poisson(plan, four_pi_G=FOUR_PI_G)
+    xd = torch.tensor(x, device="cuda")
+    md = torch.tensor(m, device="cuda")
+    rho = ps.dense(1)[0]
+    g = ps.dense(3)
+    ps.pm_deposit(xd, md, rho)
+    ps.solve(lev.current, 0.5, None, warm_start=False, rho_dm=rho, g_dense=g)
+    u1 = torch.tensor(u, device="cuda")
+    u2 = u1.clone()
+    d1 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    d2 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ps.pm_kick(xd, u1, g, 0.45, 0.5, 0.01)
+    ps.pm_estdt(xd, u1, g, 0.5, d1)
+    ps.pm_kick_estdt(xd, u2, g, 0.45, 0.5, 0.01, d2)
+    torch.cuda.synchronize()
+    assert torch.equal(u1, u2)
+    assert d1.item() == d2.item() and 0.0 < d1.item() < float("inf")
+    un = oracle.pm_kick(n, dx, g.cpu().numpy(), x, u, a_half=0.45, a_new=0.5, dt=0.01)
+    assert _rel(u1.cpu().numpy(), un) <= 1e-13
+    ps.close()
+    plan.close()
