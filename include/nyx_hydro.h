@@ -308,7 +308,8 @@ typedef struct {
   int precision;      /* NYX_FP64 (default): every operation in FP64.  NYX_MIXED:
                          iterative refinement, each cycle an FP64 residual, one
                          FP32 V-cycle on the correction equation from zero, and
-                         an FP64 update of phi; the same FP64 stopping test */
+                         an FP64 update of phi; the stopping test on that
+                         FP64 residual, rounded to float */
 } nyx_poisson_params;
 
 void nyx_poisson_default_params(nyx_poisson_params *params);
