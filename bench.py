@@ -463,8 +463,14 @@ def run_ours(args, w):
             p64.run(l64, a, dt, 1, compute_dt0=True, use_graph=False)
             f1.record(p64.torch_stream)
             torch.cuda.synchronize()
-            side[label] = {"value": cells / (f0.elapsed_time(f1) / 1e3), "unit": "zone-updates/s",
-                           "steps": 1}
+            zps = cells / (f0.elapsed_time(f1) / 1e3)
+            tf = ALG_FLOPS_PER_ZONE["fp64"] * zps / 1e12
+            side[label] = {"value": zps, "unit": "zone-updates/s", "steps": 1,
+                           "roofline": {"bound": "fp64", "achieved": tf,
+                                        "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
+                                        "frac": tf / PEAK_FP64_TFLOPS,
+                                        "alg_flops_per_zone": ALG_FLOPS_PER_ZONE["fp64"],
+                                        "note": "whole step (fill, advance, dt) timed"}}
             p64.close()
 
     cpu = None
