@@ -352,23 +352,26 @@ def run_ours(args, w):
     achieved_tf = flops * cells / (adv_ms / 1e3) / 1e12
     shape, (tx, ty) = plan.tile_shape()
 
-    # end to end through the C ABI with pinned host buffers
+    # end to end through the C ABI with pinned host buffers: the level's valid
+    # cells in, the new valid cells and dt out, every step
     e2e = None
     if not args.no_e2e:
-        host_in = torch.from_numpy(plan.pack_host(w.state, 6)).pin_memory()
+        restore()
+        host_in = torch.from_numpy(plan.pack_valid(w.state)).pin_memory()
         host_out = torch.empty_like(host_in).pin_memory()
         e2e_steps = max(1, min(3, K))
-        d = plan.step_host(lev, host_in, host_out, float(a_host[0]), float(a_host[1]), 0.0)
+        d = plan.step_host_valid(lev, host_in, host_out, float(a_host[0]), float(a_host[1]), 0.0)
         torch.cuda.synchronize()
         barrier(ws)
         t0 = time.perf_counter()
         for s in range(e2e_steps):
-            d = plan.step_host(lev, host_in, host_out, float(a_host[s]), float(a_host[s + 1]), d)
+            d = plan.step_host_valid(lev, host_in, host_out, float(a_host[s]), float(a_host[s + 1]),
+                                     d)
         t_e2e = max_over_ranks(time.perf_counter() - t0, ws)
         state_bytes = host_in.numel() * 8
         e2e = {"value": ws * cells * e2e_steps / t_e2e, "unit": "zone-updates/s",
                "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes + 8,
-               "steps": e2e_steps}
+               "steps": e2e_steps, "call": "nyx_hydro_step_host_valid (valid cells only)"}
         del host_in, host_out
 
     # scheme variants on the same level: the standalone corrector with a second

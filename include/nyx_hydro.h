@@ -223,6 +223,17 @@ int nyx_hydro_fluxes(nyx_plan *plan, const nyx_level *level, int box, int dir, d
 int nyx_hydro_step_host(nyx_plan *plan, nyx_level *level, const double *host_state_in,
                         double *host_state_out, double a_old, double a_new, double *dt_inout);
 
+/* The same end-to-end step with the level's VALID cells only on the host
+ * (ghost cells are derived data, about 40 % of a field with 4-cell ghosts
+ * on 32^3 boxes): host_in and host_out hold, box after box, the 6 components
+ * of the box's n_x n_y n_z valid cells (component-major, x fastest; box b
+ * starts at 6 times the number of valid cells of the boxes before it).  One
+ * copy each way through a device staging buffer of the same size, made on
+ * the first call (NYX_ENOMEM if it cannot be); the copies to and from the
+ * level's state run on the device.  Synchronous. */
+int nyx_hydro_step_host_valid(nyx_plan *plan, nyx_level *level, const double *host_in,
+                              double *host_out, double a_old, double a_new, double *dt_inout);
+
 /* Tile shapes of the fused persistent kernel: shape index -> columns per
  * work item (tx, ty).  Shapes 0-2 are the column-owning form (FP64 and
  * mixed), 3-5 the task form (mixed only).  nyx_hydro_tile_shape returns

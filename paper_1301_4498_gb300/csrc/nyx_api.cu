@@ -285,6 +285,8 @@ void free_plan(nyx_plan *P) {
   cudaFree(P->d_scratch);
   cudaFree(P->d_flat);
   cudaFree(P->d_flat_tiles);
+  cudaFree(P->d_packed);
+  cudaFree(P->d_plane_pref);
   cudaFree(P->d_flux);
   cudaFree(P->d_flux_off);
   for (auto &it : P->d_items) cudaFree(it);
@@ -957,6 +959,52 @@ int nyx_hydro_step_host(nyx_plan *P, nyx_level *L, const double *host_in, double
   int rc = do_advance(P, L, P->d_scal, P->d_scal + 1, P->d_scal + 2, nullptr, P->d_scal + 3);
   if (rc) return rc;
   CK(cudaMemcpyAsync(host_out, L->state[L->cur], bytes, cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaMemcpyAsync(dt_inout, P->d_scal + 3, sizeof(double), cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  return NYX_OK;
+}
+
+int nyx_hydro_step_host_valid(nyx_plan *P, nyx_level *L, const double *host_in, double *host_out,
+                              double a_old, double a_new, double *dt_inout) {
+  if (!P || !L || !host_in || !host_out || !dt_inout) return fail(NYX_EINVAL, "null argument");
+  if ((L->cur != 0 && L->cur != 1) || !L->state[0] || !L->state[1] || L->state[0] == L->state[1])
+    return fail(NYX_EINVAL, "level needs two distinct state buffers and cur in {0,1}");
+  if (!P->d_packed) {
+    std::vector<int> pp(P->nbox);
+    long long nb = 0;
+    for (int b = 0; b < P->nbox; ++b) {
+      pp[b] = (int)nb;
+      nb += P->hbox[b].n[2];
+    }
+    if (nb > 0x7fffffffLL) return fail(NYX_EINVAL, "too many box planes for one launch");
+    cudaError_t e = cudaMalloc(&P->d_packed, sizeof(double) * NCONS * (size_t)P->total_cells);
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_plane_pref, sizeof(int) * P->nbox);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(P->d_plane_pref, pp.data(), sizeof(int) * P->nbox, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(P->d_packed);
+      cudaFree(P->d_plane_pref);
+      P->d_packed = nullptr;
+      P->d_plane_pref = nullptr;
+      return e == cudaErrorMemoryAllocation ? fail(NYX_ENOMEM, "packed state allocation failed")
+                                            : cuda_fail(e, "packed state set-up");
+    }
+    P->plane_blocks = (int)nb;
+  }
+  const size_t bytes = sizeof(double) * NCONS * (size_t)P->total_cells;
+  double h[3] = {a_old, a_new, *dt_inout};
+  CK(cudaMemcpyAsync(P->d_packed, host_in, bytes, cudaMemcpyHostToDevice, P->stream));
+  CK(cudaMemcpyAsync(P->d_scal, h, 3 * sizeof(double), cudaMemcpyHostToDevice, P->stream));
+  launch_valid_copy(L->state[L->cur], P->d_packed, P->d_boxes, P->d_cell_pref, P->d_plane_pref,
+                    P->nbox, P->plane_blocks, 1, P->stream);
+  P->launches += 1;
+  if (!(*dt_inout > 0.0)) do_estdt(P, L->state[L->cur], P->d_scal, P->d_scal + 2);
+  int rc = do_advance(P, L, P->d_scal, P->d_scal + 1, P->d_scal + 2, nullptr, P->d_scal + 3);
+  if (rc) return rc;
+  launch_valid_copy(L->state[L->cur], P->d_packed, P->d_boxes, P->d_cell_pref, P->d_plane_pref,
+                    P->nbox, P->plane_blocks, 0, P->stream);
+  P->launches += 1;
+  CK(cudaMemcpyAsync(host_out, P->d_packed, bytes, cudaMemcpyDeviceToHost, P->stream));
   CK(cudaMemcpyAsync(dt_inout, P->d_scal + 3, sizeof(double), cudaMemcpyDeviceToHost, P->stream));
   CK(cudaStreamSynchronize(P->stream));
   return NYX_OK;

@@ -33,7 +33,48 @@ __global__ void k_fill_rects(double *field, int ncomp, const BoxDev *boxes, cons
   }
 }
 
+// Copy between a level field (6 components, with ghosts) and its valid cells
+// packed box by box (box b at 6 cell_pref[b], component-major, x fastest).
+// One block per plane of each box (plane_pref[b]: the first block of box
+// b); consecutive threads take consecutive x cells on both sides.
+__global__ void k_valid_copy(double *field, double *packed, const BoxDev *boxes,
+                             const long long *cell_pref, const int *plane_pref, int nbox,
+                             int to_field) {
+  const int blk = blockIdx.x;
+  int lo = 0, hi = nbox - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (plane_pref[mid] <= blk) lo = mid;
+    else hi = mid - 1;
+  }
+  const BoxDev X = boxes[lo];
+  const int k = blk - plane_pref[lo];
+  const int nxy = X.n[0] * X.n[1];
+  const long long vol = (long long)nxy * X.n[2];
+  double *F = field + NCONS * X.pref;
+  double *Pk = packed + NCONS * cell_pref[lo] + (long long)k * nxy;
+  for (int t = threadIdx.x; t < nxy; t += blockDim.x) {
+    const int i = t % X.n[0], j = t / X.n[0];
+    const long long id = cell_index(X, i, j, k);
+    if (to_field) {
+#pragma unroll
+      for (int c = 0; c < NCONS; ++c) F[c * X.stride + id] = Pk[c * vol + t];
+    } else {
+#pragma unroll
+      for (int c = 0; c < NCONS; ++c) Pk[c * vol + t] = F[c * X.stride + id];
+    }
+  }
+}
+
 }  // namespace
+
+void launch_valid_copy(double *field, double *packed, const BoxDev *boxes,
+                       const long long *cell_pref, const int *plane_pref, int nbox, int nblocks,
+                       int to_field, cudaStream_t st) {
+  if (nblocks < 1) return;
+  k_valid_copy<<<nblocks, 256, 0, st>>>(field, packed, boxes, cell_pref, plane_pref, nbox,
+                                       to_field);
+}
 
 void launch_fill(double *field, int ncomp, const BoxDev *boxes, const FillRect *rects,
                  const long long *rect_pref, int nrect, long long total, cudaStream_t st) {

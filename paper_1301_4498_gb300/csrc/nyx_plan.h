@@ -65,6 +65,11 @@ struct nyx_plan {
   void *d_flat = nullptr;
   nyx::FlatTile *d_flat_tiles = nullptr;
   int flat_ntiles = 0;
+  // packed valid cells of a state (nyx_hydro_step_host_valid), made on
+  // first use: 6 doubles per valid cell, one copy block per box plane
+  double *d_packed = nullptr;
+  int *d_plane_pref = nullptr;
+  int plane_blocks = 0;
   // per-box FP64 form
   double *d_scratch = nullptr;
   long long Vmax = 0;

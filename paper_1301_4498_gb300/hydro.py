@@ -116,6 +116,8 @@ def load_library(path: str | None = None):
     L.nyx_hydro_fluxes.argtypes = [vp, C.POINTER(NyxLevel), C.c_int, C.c_int, vp]
     L.nyx_hydro_step_host.argtypes = [vp, C.POINTER(NyxLevel), vp, vp, C.c_double, C.c_double,
                                       dp]
+    L.nyx_hydro_step_host_valid.argtypes = [vp, C.POINTER(NyxLevel), vp, vp, C.c_double,
+                                            C.c_double, dp]
     L.nyx_hydro_status.argtypes = [vp, ip]
     L.nyx_plan_destroy.argtypes = [vp]
     L.nyx_hydro_tile_shape.argtypes = [C.c_int, ip, ip]
@@ -158,6 +160,7 @@ def load_library(path: str | None = None):
         getattr(L, name).restype = C.c_int
     for name in ("nyx_hydro_plan", "nyx_hydro_layout", "nyx_hydro_fill", "nyx_hydro_estdt",
                  "nyx_hydro_advance", "nyx_hydro_run", "nyx_hydro_fluxes", "nyx_hydro_step_host",
+                 "nyx_hydro_step_host_valid",
                  "nyx_hydro_status", "nyx_plan_destroy", "nyx_hydro_tile_shape",
                  "nyx_hydro_set_tile_shape", "nyx_hydro_get_tile_shape", "nyx_hydro_profile",
                  "nyx_hydro_counters_read", "nyx_hydro_estdt_noalloc", "nyx_hydro_predict",
@@ -412,6 +415,38 @@ class Plan:
                                             C.byref(d)))
         level.sync_from_c()
         return d.value
+
+    def step_host_valid(self, level, host_in, host_out, a_old, a_new, dt=0.0):
+        """End-to-end step with only the valid cells on the host (pack_valid
+        layout; torch CPU tensors, ideally pinned).  Returns the next step's
+        CFL dt."""
+        d = C.c_double(dt)
+        cl = level.c()
+        import torch
+        self.torch_stream.wait_stream(torch.cuda.current_stream())
+        _check(self.lib.nyx_hydro_step_host_valid(self.h, C.byref(cl),
+                                                  C.c_void_p(host_in.data_ptr()),
+                                                  C.c_void_p(host_out.data_ptr()), a_old, a_new,
+                                                  C.byref(d)))
+        level.sync_from_c()
+        return d.value
+
+    def pack_valid(self, arrays):
+        """Valid cells of per-box state arrays (6, Nz, Ny, Nx) packed box by
+        box, component-major, x fastest (the step_host_valid layout)."""
+        g = self.spec.ng
+        return np.concatenate([np.ascontiguousarray(a[:, g:-g, g:-g, g:-g]).ravel()
+                               for a in arrays])
+
+    def unpack_valid(self, flat):
+        """Inverse of pack_valid: per-box arrays of the valid cells (6, nz, ny, nx)."""
+        res, o = [], 0
+        for b in range(self.nbox):
+            n = self.spec.extent(b)
+            v = 6 * n[0] * n[1] * n[2]
+            res.append(np.asarray(flat[o:o + v]).reshape(6, n[2], n[1], n[0]).copy())
+            o += v
+        return res
 
     def status(self):
         f = C.c_int()

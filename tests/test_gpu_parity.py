@@ -318,3 +318,26 @@ def test_autotuned_graph_run_reports_clean_status():
     ref = plan2.from_device(lev2.current, 6)
     for x, y in zip(got, ref):
         assert np.array_equal(W.valid(x), W.valid(y))
+
+
+def test_step_host_valid_matches_device_path():
+    """nyx_hydro_step_host_valid: only the valid cells cross the host link;
+    the step is the device path's, bitwise, and so is the next dt."""
+    w = W.tiled_box(n=64, box=32, nsteps=1)
+    plan = H.Plan(w.level, gamma=w.gamma, cfl=w.cfl, precision="mixed")
+    lev = H.make_level(plan, w.state, w.grav)
+    host_in = torch.from_numpy(plan.pack_valid(w.state)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    dt_next = plan.step_host_valid(lev, host_in, host_out, float(w.a_sched[0]),
+                                   float(w.a_sched[1]))
+    got = plan.unpack_valid(host_out.numpy())
+    S_dev, dts, _, _ = gpu_run(w, 1, precision="mixed")
+    for a, b in zip(got, S_dev):
+        assert np.array_equal(a, W.valid(b))
+    assert dt_next == dts[1]
+    # a second call reuses the staging buffer and continues from host_out
+    host_in.copy_(host_out)
+    plan.step_host_valid(lev, host_in, host_out, float(w.a_sched[0]), float(w.a_sched[1]),
+                         dt_next)
+    assert np.isfinite(host_out.numpy()).all()
+    plan.close()
