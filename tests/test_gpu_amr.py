@@ -197,3 +197,26 @@ def test_create_rejects_bad_pairs():
     with pytest.raises(H.NyxError):
         H.Plan(fine, precision="fp64", keep_fluxes=1)      # holes without coarse_fine
     fp_nokeep.close(); fp_other_stream.close(); cp.close()
+
+
+def test_two_level_step_with_flattening_fp64():
+    """The two-level step with shock flattening on both levels (the fine
+    level's coefficients see its interpolated ghost cells) against the
+    oracle's, FP64, within 1e-12."""
+    w, fine = TA._hierarchy()
+    cp, fp, amr, lc, lf = _setup(w, fine, flattening=True)
+    cs, fs, cg, fg = _oracle_setup(w, fine)
+    P = oracle.OracleParams(gamma=w.gamma, cfl=w.cfl, flattening=1)
+    f = oracle.flatten_field(w.level, P, cs)
+    assert min(float(x.min()) for x in f) < 1.0
+    a0, a1 = float(w.a_sched[0]), float(w.a_sched[1])
+    dtv = oracle.amr_estdt(w.level, fine, P, cs, fs, a0)
+    a = torch.tensor([a0, a1], dtype=torch.float64, device="cuda")
+    dt = torch.tensor([dtv], dtype=torch.float64, device="cuda")
+    amr.step(lc, lf, a[:1], a[1:], dt)
+    torch.cuda.synchronize()
+    assert cp.status() == (0, 0) and fp.status() == (0, 0)
+    cn, fn, _, _ = oracle.amr_step(w.level, fine, P, cs, fs, cg, fg, a_old=a0, a_new=a1, dt=dtv)
+    assert _norm_rel(cp.from_device(lc.current, 6), cn) <= 1e-12
+    assert _norm_rel(fp.from_device(lf.current, 6), fn) <= 1e-12
+    amr.close(); fp.close(); cp.close()
