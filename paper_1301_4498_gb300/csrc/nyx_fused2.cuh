@@ -18,6 +18,15 @@
 // stored, so the x/y flux buffer is single and the z-face buffer holds two
 // faces.
 //
+// The update warps also load each plane's inputs, which the column threads
+// used to load in a stage of their own (stage 0): primitive plane c+2 into
+// the ring, plane c into the framed buffer with its 3-cell frame, and plane
+// c's gravity and flattening rows.  Their FP64 update leaves the integer
+// pipe, which does the conversions, idle.  Two more named barriers hand the
+// inputs over: LOADED once they are written, CONSUMED once the column
+// threads have traced plane c (the last read of ring plane c-2 and of the
+// framed plane), before the update warps overwrite them.
+//
 // Rings over planes: slot = (plane + 2) & 1 for the two-plane rings, and
 // (plane + 8) % 5 for the five-plane primitive ring.
 #pragma once
@@ -60,8 +69,9 @@ struct G2 {
 };
 
 // Named barriers: 0 is __syncthreads (all threads, item fetch and tile end);
-// the column threads' stage barrier; the update hand-over pair.
-constexpr int BAR_COL = 1, BAR_READY = 2, BAR_FREE = 3;
+// the column threads' stage barrier; the flux hand-over pair; the input
+// hand-over pair.
+constexpr int BAR_COL = 1, BAR_READY = 2, BAR_FREE = 3, BAR_LOADED = 4, BAR_CONSUMED = 5;
 __device__ __forceinline__ void bar_sync_n(int id, int n) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
@@ -222,80 +232,19 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
 
     if (colthr) {
       const nyx::BoxStep bst = a.BS[w.box];
-      const double *Gv = a.G ? a.G + nyx::NGRAV * b.pref : nullptr;
       const float dtdx0 = d2f_rn(bst.dtdx[0]), dtdx1 = d2f_rn(bst.dtdx[1]), dtdx2 = d2f_rn(bst.dtdx[2]);
       const float c30 = d2f_rn(bst.cdt3[0]), c31 = d2f_rn(bst.cdt3[1]), c32 = d2f_rn(bst.cdt3[2]);
       const float ch0 = d2f_rn(bst.chalf[0]), ch1 = d2f_rn(bst.chalf[1]), ch2 = d2f_rn(bst.chalf[2]);
-      const int nstrip = 4 * (nxt + 2) + 4 * (nyt + 2);
       // geometry of this thread's column for this tile
       const bool act = me < NC && mi <= nxt && mj <= nyt;
       const bool inX = mi >= 0 && mi < nxt, inY = mj >= 0 && mj < nyt;
-      const long long mycol = (long long)(w.y0 + mj + 4) * b.N[0] + (w.x0 + mi + 4);
-
-      auto load_prims = [&](long long id, float *dst, int stride) {
-        float q[5];
-        prims_of<float>(S, bs, id, E, q);
-#pragma unroll
-        for (int v = 0; v < 5; ++v) dst[v * stride] = q[v];
-      };
       auto ring = [&](int plane) { return sm + G::PR + ring5(plane) * 5 * NC + me; };
-
-      // prologue: planes -1 and 0 by kind 0 (which copies plane c into the
-      // framed buffer), planes -3 and -2 by kinds 1 and 2
-      if (act) {
-        if (kq == 0) {
-          load_prims(mycol + (long long)(-1 + 4) * ps, ring(-1), NC);
-          load_prims(mycol + (long long)(0 + 4) * ps, ring(0), NC);
-        } else {
-          load_prims(mycol + (long long)(kq - 4 + 4) * ps, ring(kq - 4), NC);
-        }
-      }
 
       for (int c = -1; c <= nz; ++c) {
         const int pc = par2(c), pm = par2(c - 1);
         const bool zc = c >= 1;
-        // ---------------------------------------------- S0: primitives (+ gravity of plane c)
-        if (tid < NCP) {
-          if (act) {
-            load_prims(mycol + (long long)(c + 2 + 4) * ps, ring(c + 2), NC);
-            float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-            if (Gv) {
-              const long long id = mycol + (long long)(c + 4) * ps;
-              g0 = d2f_rn(Gv[id]);
-              g1 = d2f_rn(Gv[bs + id]);
-              g2 = d2f_rn(Gv[2 * bs + id]);
-            }
-            sm[G::GR + me] = g0;
-            sm[G::GR + NC + me] = g1;
-            sm[G::GR + 2 * NC + me] = g2;
-            if (E.flat)
-              sm[G::GR + 3 * NC + me] =
-                  static_cast<const float *>(a.flat)[b.pref + mycol + (long long)(c + 4) * ps];
-            // plane c of the own column into the framed buffer
-            const float *rc = ring(c);
-#pragma unroll
-            for (int v = 0; v < 5; ++v) sm[G::PE + v * NE + mee] = rc[v * NC];
-          }
-        } else {
-          // the frame strips of plane c: column threads of kinds 1 and 2
-          for (int u = tid - NCP; u < nstrip; u += NTC - NCP) {
-            int x, y;
-            if (u < 4 * (nyt + 2)) {
-              const int r = u % (nyt + 2), s2 = u / (nyt + 2);
-              y = r - 1;
-              x = (s2 < 2) ? (-3 + s2) : (nxt + 1 + (s2 - 2));
-            } else {
-              const int v = u - 4 * (nyt + 2);
-              const int r = v % (nxt + 2), s2 = v / (nxt + 2);
-              x = r - 1;
-              y = (s2 < 2) ? (-3 + s2) : (nyt + 1 + (s2 - 2));
-            }
-            const long long id =
-                ((long long)(c + 4) * b.N[1] + (w.y0 + y + 4)) * b.N[0] + (w.x0 + x + 4);
-            load_prims(id, sm + G::PE + (y + 3) * WE + (x + 3), NE);
-          }
-        }
-        bar_sync_n(BAR_COL, NTC);
+        // ---------------------------------------------- S0: plane c's inputs (update warps)
+        bar_sync_n(BAR_LOADED, NT);
 
         // ---------------------------------------------- S1: tracing at plane c
         if (act) {
@@ -332,6 +281,8 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
           st5(dst + 5 * NC, NC, me, qp);
         }
         bar_sync_n(BAR_COL, NTC);
+        // ring plane c-2 and the framed plane c are no longer read
+        if (c < nz) bar_arrive_n(BAR_CONSUMED, NT);
 
         // ---------------------------------------------- S2: normal solves
         if (act) {
@@ -541,7 +492,7 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
             bar_arrive_n(BAR_READY, NT);
           }
         }
-        // no barrier here: the next plane's S0 touches nothing S6 reads or writes
+        // no barrier here: the next plane's inputs touch nothing S2-S6 read or write
       }
     } else {
       // ------------------------------------------------ update warps (stage 7)
@@ -554,32 +505,109 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
       double *Sn = a.Sn + nyx::NCONS * b.pref;
       const MixK mk = make_mixk(KK, sc, b);
       const int ux = uj * (TX + 1) + ui, uy = NXF + uj * TX + ui, uz = uj * TX + ui;
-      for (int p = 0; p < nz; ++p) {
-        // the final fluxes of plane p (x, y faces; z faces p-1/2 and p+1/2)
-        bar_sync_n(BAR_READY, NT);
-        if (upd) {
-          float Fxm[8], Fxp[8], Fym[8], Fyp[8], Fzm[8], Fzp[8];
-          const float *U = sm + G::UF;
-          const float *Zm = sm + G::FFZ + (p & 1) * 8 * NZF, *Zp = sm + G::FFZ + ((p + 1) & 1) * 8 * NZF;
+      const int nstrip = 4 * (nxt + 2) + 4 * (nyt + 2);
+
+      auto load_prims = [&](long long id, float *dst, int stride) {
+        float q[5];
+        prims_of<float>(S, bs, id, E, q);
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            Fxm[k] = U[k * NUF + ux];
-            Fxp[k] = U[k * NUF + ux + 1];
-            Fym[k] = U[k * NUF + uy];
-            Fyp[k] = U[k * NUF + uy + TX];
-            Fzm[k] = Zm[k * NZF + uz];
-            Fzp[k] = Zp[k * NZF + uz];
+        for (int v = 0; v < 5; ++v) dst[v * stride] = q[v];
+      };
+      auto ring_at = [&](int plane) { return sm + G::PR + ring5(plane) * 5 * NC; };
+      // the tile's columns: e = (j+1) W + (i+1), i in [-1, nxt], j in [-1, nyt]
+      auto column = [&](int e, long long &col) {
+        const int ci = e % W - 1, cj = e / W - 1;
+        col = (long long)(w.y0 + cj + 4) * b.N[0] + (w.x0 + ci + 4);
+        return ci <= nxt && cj <= nyt;
+      };
+      // inputs of plane c: ring plane c+2; plane c's gravity, flattening and
+      // framed copy (its own columns from the ring, the frame strips loaded)
+      auto inputs = [&](int c) {
+        for (int e = uthr; e < NC; e += G::NU) {
+          long long col;
+          if (!column(e, col)) continue;
+          load_prims(col + (long long)(c + 2 + 4) * ps, ring_at(c + 2) + e, NC);
+          const long long id = col + (long long)(c + 4) * ps;
+          float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+          if (Gv) {
+            g0 = d2f_rn(Gv[id]);
+            g1 = d2f_rn(Gv[bs + id]);
+            g2 = d2f_rn(Gv[2 * bs + id]);
           }
-          const long long id = ucol + (long long)(p + 4) * ps;
-          update_cell_mixed(KK, sc, b, mk, S, Gv, Sn, id, Fxm, Fxp, Fym, Fyp, Fzm, Fzp, dtmin,
-                            flags, a.dtacc != nullptr, !a.predict_only);
-          if (a.flux_keep)
-            keep_fluxes(a.flux_keep + a.flux_off[w.box], b.n[0], b.n[1], nz, w.x0 + ui,
-                        w.y0 + uj, p, Fxm, Fxp, Fym, Fyp, Fzm, Fzp);
+          sm[G::GR + e] = g0;
+          sm[G::GR + NC + e] = g1;
+          sm[G::GR + 2 * NC + e] = g2;
+          if (E.flat) sm[G::GR + 3 * NC + e] = static_cast<const float *>(a.flat)[b.pref + id];
+          const float *rc = ring_at(c) + e;
+          const int ee = (e / W + 2) * WE + (e % W + 2);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) sm[G::PE + v * NE + ee] = rc[v * NC];
         }
-        // plane p's buffers may be overwritten (by the fluxes of plane p+1)
-        if (p + 2 <= nz) bar_arrive_n(BAR_FREE, NT);
+        for (int u = uthr; u < nstrip; u += G::NU) {
+          int x, y;
+          if (u < 4 * (nyt + 2)) {
+            const int r = u % (nyt + 2), s2 = u / (nyt + 2);
+            y = r - 1;
+            x = (s2 < 2) ? (-3 + s2) : (nxt + 1 + (s2 - 2));
+          } else {
+            const int v = u - 4 * (nyt + 2);
+            const int r = v % (nxt + 2), s2 = v / (nxt + 2);
+            x = r - 1;
+            y = (s2 < 2) ? (-3 + s2) : (nyt + 1 + (s2 - 2));
+          }
+          const long long id =
+              ((long long)(c + 4) * b.N[1] + (w.y0 + y + 4)) * b.N[0] + (w.x0 + x + 4);
+          load_prims(id, sm + G::PE + (y + 3) * WE + (x + 3), NE);
+        }
+      };
+      auto update_plane = [&](int p) {
+        if (!upd) return;
+        float Fxm[8], Fxp[8], Fym[8], Fyp[8], Fzm[8], Fzp[8];
+        const float *U = sm + G::UF;
+        const float *Zm = sm + G::FFZ + (p & 1) * 8 * NZF, *Zp = sm + G::FFZ + ((p + 1) & 1) * 8 * NZF;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          Fxm[k] = U[k * NUF + ux];
+          Fxp[k] = U[k * NUF + ux + 1];
+          Fym[k] = U[k * NUF + uy];
+          Fyp[k] = U[k * NUF + uy + TX];
+          Fzm[k] = Zm[k * NZF + uz];
+          Fzp[k] = Zp[k * NZF + uz];
+        }
+        const long long id = ucol + (long long)(p + 4) * ps;
+        update_cell_mixed(KK, sc, b, mk, S, Gv, Sn, id, Fxm, Fxp, Fym, Fyp, Fzm, Fzp, dtmin, flags,
+                          a.dtacc != nullptr, !a.predict_only);
+        if (a.flux_keep)
+          keep_fluxes(a.flux_keep + a.flux_off[w.box], b.n[0], b.n[1], nz, w.x0 + ui, w.y0 + uj, p,
+                      Fxm, Fxp, Fym, Fyp, Fzm, Fzp);
+      };
+
+      // prologue: ring planes -3 .. 0, then the inputs of plane -1
+      for (int e = uthr; e < NC; e += G::NU) {
+        long long col;
+        if (!column(e, col)) continue;
+#pragma unroll 1
+        for (int k = -3; k <= 0; ++k) load_prims(col + (long long)(k + 4) * ps, ring_at(k) + e, NC);
       }
+      inputs(-1);
+      __threadfence_block();
+      bar_arrive_n(BAR_LOADED, NT);
+      for (int c = 0; c <= nz; ++c) {
+        // plane c-1 traced: its ring plane c-3 slot and the framed plane are free
+        bar_sync_n(BAR_CONSUMED, NT);
+        inputs(c);
+        __threadfence_block();
+        bar_arrive_n(BAR_LOADED, NT);
+        if (c >= 2) {
+          // the final fluxes of plane c-2 (x, y faces; z faces c-5/2 and c-3/2)
+          bar_sync_n(BAR_READY, NT);
+          update_plane(c - 2);
+          // plane c-2's buffers may be overwritten (by the fluxes of plane c-1)
+          bar_arrive_n(BAR_FREE, NT);
+        }
+      }
+      bar_sync_n(BAR_READY, NT);
+      update_plane(nz - 1);
     }
     __syncthreads();
   }

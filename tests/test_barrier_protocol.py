@@ -1,14 +1,20 @@
-"""Host-side check of the flux hand-over between the column threads and the
+"""Host-side check of the hand-overs between the column threads and the
 update warps of the task-form kernel (nyx_fused2.cuh).
 
-The kernel's column threads (producer) and update threads (consumer) meet on
-two named barriers per box tile:
-  * producer, plane step c = -1 .. nz: after its stage barriers it computes the
-    final fluxes, waits on FREE when c >= 2, stores the fluxes of plane c-1
-    (x/y buffer) and of z face c (slot c & 1), and arrives on READY when
-    c >= 1;
-  * consumer, p = 0 .. nz-1: waits on READY, updates plane p (x/y buffer, z
-    faces p and p+1), and arrives on FREE when p + 2 <= nz;
+The kernel's column threads (producer of fluxes) and update threads
+(consumer of fluxes, and producer of each plane's inputs) meet on four named
+barriers per box tile:
+  * the update warps write the primitive ring's planes -3 .. 1 and plane -1's
+    frame, gravity and flattening rows, and arrive on LOADED; then for
+    c = 0 .. nz they wait on CONSUMED, write ring plane c+2 and plane c's
+    frame, arrive on LOADED, and (c >= 2) wait on READY, update plane c-2
+    and arrive on FREE when c <= nz; finally they wait on READY and update
+    plane nz-1;
+  * the column threads, plane step c = -1 .. nz: wait on LOADED, trace plane
+    c (ring planes c-2 .. c+2, the frame of plane c), pass their stage
+    barrier, arrive on CONSUMED when c < nz, run their other stages, wait on
+    FREE when c >= 2, store the fluxes of plane c-1 (x/y buffer) and of z
+    face c (slot c & 1), and arrive on READY when c >= 1;
   * both then meet on the CTA-wide barrier before the next tile.
 This test models bar.sync / bar.arrive phase counting (a phase completes when
 the arrivals reach the barrier's thread count) and runs the two sequences
@@ -23,13 +29,18 @@ import pytest
 
 NTC, NU = 576, 128          # 16x8 tile: 3 x 192 column threads, 4 update warps
 NT = NTC + NU
-BAR_ALL, BAR_COL, BAR_READY, BAR_FREE = 0, 1, 2, 3
+BAR_ALL, BAR_COL, BAR_READY, BAR_FREE, BAR_LOADED, BAR_CONSUMED = 0, 1, 2, 3, 4, 5
 
 
 def producer_ops(nz):
     ops = []
     for c in range(-1, nz + 1):
-        ops += [("sync", BAR_COL, NTC)] * 6          # stage barriers S0..S5
+        ops.append(("sync", BAR_LOADED, NT))
+        ops.append(("trace", c))
+        ops.append(("sync", BAR_COL, NTC))           # end of the trace stage
+        if c < nz:
+            ops.append(("arrive", BAR_CONSUMED, NT))
+        ops += [("sync", BAR_COL, NTC)] * 4          # stage barriers S2..S5
         if c >= 2:
             ops.append(("sync", BAR_FREE, NT))
         ops.append(("store", c))
@@ -40,12 +51,18 @@ def producer_ops(nz):
 
 
 def consumer_ops(nz):
-    ops = []
-    for p in range(nz):
-        ops.append(("sync", BAR_READY, NT))
-        ops.append(("load", p))
-        if p + 2 <= nz:
-            ops.append(("arrive", BAR_FREE, NT))
+    ops = [("prologue",), ("write", -1), ("arrive", BAR_LOADED, NT)]
+    for c in range(0, nz + 1):
+        ops.append(("sync", BAR_CONSUMED, NT))
+        ops.append(("write", c))
+        ops.append(("arrive", BAR_LOADED, NT))
+        if c >= 2:
+            ops.append(("sync", BAR_READY, NT))
+            ops.append(("load", c - 2))
+            if c <= nz:
+                ops.append(("arrive", BAR_FREE, NT))
+    ops.append(("sync", BAR_READY, NT))
+    ops.append(("load", nz - 1))
     ops.append(("sync", BAR_ALL, NT))
     return ops
 
@@ -60,6 +77,9 @@ def simulate(depths, rng):
     blocked = {}
     xy = {}        # the single x/y buffer: (tile, plane, live)
     zf = {}        # z-face slots: slot -> (tile, face, live)
+    ring = {}      # primitive ring: slot (plane + 8) % 5 -> (tile, plane)
+    frame = {}     # the framed plane (with gravity and flattening rows): (tile, plane)
+    traced = set()  # (tile, plane) traced by the column threads
     steps = 0
     while True:
         steps += 1
@@ -89,6 +109,29 @@ def simulate(depths, rng):
                 if bid == BAR_ALL:
                     tile["P"] += 1
                     tile["C"] += 1
+        elif op[0] == "prologue":
+            t = tile["C"]
+            for k in range(-3, 1):
+                ring[(k + 8) % 5] = (t, k)
+        elif op[0] == "write":
+            c, t = op[1], tile["C"]
+            nz = depths[t]
+            k = c + 2                                 # ring plane written
+            old = ring.get((k + 8) % 5)
+            if old is not None and old[0] == t:
+                q = old[1]
+                for cc in range(max(-1, q - 2), min(nz, q + 2) + 1):
+                    assert (t, cc) in traced, f"ring plane {q} overwritten before trace {cc}"
+            ring[(k + 8) % 5] = (t, k)
+            if frame and frame["tile"] == t:
+                assert (t, frame["plane"]) in traced, f"frame {frame['plane']} overwritten"
+            frame.update(tile=t, plane=c)
+        elif op[0] == "trace":
+            c, t = op[1], tile["P"]
+            for k in range(c - 2, c + 3):
+                assert ring.get((k + 8) % 5) == (t, k), f"trace {c}: ring plane {k} missing"
+            assert frame.get("tile") == t and frame.get("plane") == c, f"trace {c}: frame"
+            traced.add((t, c))
         elif op[0] == "store":
             c, t = op[1], tile["P"]
             if c >= 1:
@@ -116,6 +159,32 @@ def simulate(depths, rng):
 def test_flux_handover_protocol(depths):
     for seed in range(200):
         simulate(depths, random.Random(seed))
+
+
+def test_planted_input_mistake_is_caught():
+    """Update warps that write the next plane's inputs without waiting for
+    the trace of the previous plane must fail."""
+    global consumer_ops
+    saved = consumer_ops
+
+    def eager(nz):
+        ops = saved(nz)
+        for i in range(len(ops) - 1):       # write before the wait, counts unchanged
+            if ops[i][:2] == ("sync", BAR_CONSUMED) and ops[i + 1][0] == "write":
+                ops[i], ops[i + 1] = ops[i + 1], ops[i]
+        return ops
+
+    consumer_ops = eager
+    try:
+        caught = 0
+        for seed in range(200):
+            try:
+                simulate([8], random.Random(seed))
+            except AssertionError:
+                caught += 1
+        assert caught > 0
+    finally:
+        consumer_ops = saved
 
 
 def test_planted_protocol_mistake_is_caught():
