@@ -34,13 +34,14 @@
 
 namespace NYX_NS {
 
-template <int TX, int TY>
+template <int TX, int TY, int XU>
 struct G2 {
   static constexpr int W = TX + 2, H = TY + 2, NC = W * H;
   static constexpr int NCP = (NC + 31) / 32 * 32;  // task stride of one kind
   static constexpr int WE = TX + 6, HE = TY + 6, NE = WE * HE;
   static constexpr int NTC = 3 * NCP;                     // column-task threads
-  static constexpr int NU = (TX * TY + 31) / 32 * 32;     // update threads
+  // update threads: one per output cell, plus XU that only load inputs
+  static constexpr int NU = (TX * TY + 31) / 32 * 32 + XU;
   static constexpr int NT = NTC + NU;
   // final fluxes of one plane, compact over the output cells: x faces
   // [(TX+1) x TY], then y faces [TX x (TY+1)]; z faces [TX x TY]
@@ -67,6 +68,11 @@ struct G2 {
   static constexpr size_t SMEM = sizeof(float) * (size_t)TOTAL;
   static_assert(SMEM <= 227 * 1024, "task-form tile does not fit in shared memory");
 };
+
+// Extra loading-only update threads: two warps when one CTA holds the SM
+// (24 warps at 80 registers fit the per-scheduler register files), none
+// when two CTAs share it.
+#define XU_OF(MB) ((MB) == 1 ? 64 : 0)
 
 // Named barriers: 0 is __syncthreads (all threads, item fetch and tile end);
 // the column threads' stage barrier; the flux hand-over pair; the input
@@ -183,8 +189,8 @@ __device__ __forceinline__ void face_flux_dir(const Eos<float> &E, int dir, cons
 }
 
 template <int TX, int TY, int MB, int VAR>
-__global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a) {
-  using G = G2<TX, TY>;
+__global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::FusedArgs a) {
+  using G = G2<TX, TY, XU_OF(MB)>;
   constexpr int NC = G::NC, NCP = G::NCP, NE = G::NE, W = G::W, WE = G::WE, NT = G::NT;
   constexpr int NTC = G::NTC, NUF = G::NUF, NXF = G::NXF, NZF = G::NZF;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -622,7 +628,7 @@ __global__ void __launch_bounds__(G2<TX, TY>::NT, MB) k_fused2(nyx::FusedArgs a)
 
 template <int TX, int TY, int MB, int VAR>
 int launch_two(const nyx::FusedArgs &a, int grid, cudaStream_t st) {
-  using G = G2<TX, TY>;
+  using G = G2<TX, TY, XU_OF(MB)>;
   cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(int), st);
   if (e != cudaSuccess) return (int)e;
   k_fused2<TX, TY, MB, VAR><<<grid, G::NT, G::SMEM, st>>>(a);
@@ -631,7 +637,7 @@ int launch_two(const nyx::FusedArgs &a, int grid, cudaStream_t st) {
 
 template <int TX, int TY, int MB, int VAR>
 int max_grid_two() {
-  using G = G2<TX, TY>;
+  using G = G2<TX, TY, XU_OF(MB)>;
   cudaError_t e = cudaFuncSetAttribute(k_fused2<TX, TY, MB, VAR>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
   if (e != cudaSuccess) return 0;
