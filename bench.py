@@ -211,11 +211,13 @@ def max_over_ranks(x: float, ws: int) -> float:
 
 # ---------------------------------------------------------------------- CPU oracle timing
 
-def oracle_sample(workload_name, w, budget_s=12.0, max_boxes=None):
+def oracle_sample(workload_name, w, budget_s=12.0, max_boxes=None, threads=0):
     """Time the FP64 CPU oracle on a bounded sample of the workload: whole
     independent boxes (periodic domains of their own) advanced one step,
-    added one at a time until ``budget_s`` of CPU time is spent."""
+    added one at a time until ``budget_s`` of CPU time is spent.  threads:
+    OpenMP threads (0: all host cores)."""
     import oracle
+    oracle.set_threads(threads)
     P = oracle.OracleParams(gamma=w.gamma, cfl=w.cfl)
     lev = w.level
     # boxes that are their own domain (all of them for single-box levels)
@@ -239,10 +241,13 @@ def oracle_sample(workload_name, w, budget_s=12.0, max_boxes=None):
         used += 1
         if elapsed >= budget_s or (max_boxes and used >= max_boxes):
             break
-    return {"value": cells / elapsed, "unit": "zone-updates/s", "cores": os.cpu_count(),
+    oracle.set_threads(0)
+    where = f"{threads} host thread(s)" if threads > 0 else "OpenMP on all host cores"
+    return {"value": cells / elapsed, "unit": "zone-updates/s",
+            "cores": threads if threads > 0 else os.cpu_count(),
             "kind": "oracle", "elapsed_s": elapsed,
             "sample": f"{used} whole box(es) of the '{workload_name}' workload ({cells} cells), "
-                      f"1 step each, FP64 oracle, OpenMP on all host cores; {elapsed:.1f} s"}
+                      f"1 step each, FP64 oracle, {where}; {elapsed:.1f} s"}
 
 
 def run_reference(args, w):
@@ -479,6 +484,9 @@ def run_ours(args, w):
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = oracle_sample(args.workload, w, budget_s=args.cpu_budget)
+        one = oracle_sample(args.workload, w, budget_s=0.5 * args.cpu_budget, threads=1)
+        cpu["single_thread"] = {"value": one["value"], "unit": one["unit"], "cores": 1,
+                                "sample": one["sample"]}
 
     if rank == 0:
         out = {

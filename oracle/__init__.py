@@ -124,6 +124,8 @@ def load(path: str):
         L.orc_riemann_counts.restype = None
         L.orc_trace_line.argtypes = [C.POINTER(_Params), C.c_int, dp, dp, dp, C.c_double,
                                      C.c_double, C.c_double, C.c_int, dp, dp, dp, dp]
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_set_threads.restype = None
         L.orc_flatten_line.argtypes = [C.POINTER(_Params), C.c_int, dp, dp, dp]
         L.orc_flatten_line.restype = None
         L.orc_flatten_field.argtypes = [C.POINTER(_Level), C.POINTER(_Params), C.POINTER(dp),
@@ -322,6 +324,11 @@ def riemann_counts(reset: bool = True):
     c, n = C.c_longlong(), C.c_longlong()
     lib().orc_riemann_counts(C.byref(c), C.byref(n), 1 if reset else 0)
     return c.value, n.value
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads of the oracle's loops (n <= 0: all host processors)."""
+    lib().orc_set_threads(int(n))
 
 
 def flatten_line(pr, u, params: OracleParams = None):

@@ -1040,6 +1040,8 @@ void orc_riemann_counts(long long *calls, long long *iters, int reset) {
 
 /* ------------------------------------------------------------------ */
 /* Unit-level entry points for the pin tests. */
+void orc_set_threads(int n) { omp_set_num_threads(n > 0 ? n : omp_get_num_procs()); }
+
 void orc_flatten_line(const orc_params *p, int n, const double *pr, const double *u, double *fl) {
   for (int i = 0; i < n; ++i) fl[i] = 1.0;
   for (int i = 3; i < n - 3; ++i) fl[i] = 1.0 - flat_dir(pr + i, u + i, 1, p->small_pres);

@@ -177,6 +177,9 @@ void orc_pm_kick(const int n[3], double dx, const double *g, const double *x, do
 double orc_pm_estdt(const int n[3], double dx, const double *g, const double *x, const double *u,
                     long long np, double a, double cfl_dm);
 
+/* OpenMP threads of the oracle's loops (n <= 0: all host processors). */
+void orc_set_threads(int n);
+
 /* Unit-level entry points used by the pin tests. */
 void orc_ppm_line(int n, const double *s, double *sL, double *sR, double *s6);
 void orc_ppm_integrals(double sL, double sR, double s6, double sigma, double *ip, double *im);
