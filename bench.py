@@ -279,6 +279,42 @@ def run_reference(args, w):
 
 # ---------------------------------------------------------------------- GPU path
 
+def field_errors(plan, spec, got, ref):
+    """Per conserved field, normwise relative L-inf and L1 differences of two
+    level states over the valid cells, taken on strided views of runs of
+    equally shaped, consecutive boxes."""
+    off, st = plan.layout(6)
+    runs, b0 = [], 0
+    for b in range(1, spec.nbox + 1):
+        if b == spec.nbox or spec.extent(b) != spec.extent(b0) or st[b] != st[b0]:
+            runs.append((b0, b))
+            b0 = b
+    g_ng = spec.ng
+    ninf, dinf, n1, d1 = [0.0] * 6, [0.0] * 6, [0.0] * 6, [0.0] * 6
+    for r0, r1 in runs:
+        nx, ny, nz = spec.extent(r0)
+        shp = (nz + 2 * g_ng, ny + 2 * g_ng, nx + 2 * g_ng)
+        vol = shp[0] * shp[1] * shp[2]
+        s = int(st[r0])
+        v = slice(g_ng, -g_ng)
+
+        def view(x):
+            return x[int(off[r0]):int(off[r1])].view(r1 - r0, 6, s)[:, :, :vol] \
+                .reshape(r1 - r0, 6, *shp)[:, :, v, v, v]
+        G, R = view(got), view(ref)
+        for c in range(6):
+            d = (G[:, c] - R[:, c]).abs()
+            ra = R[:, c].abs()
+            ninf[c] = max(ninf[c], float(d.max()))
+            dinf[c] = max(dinf[c], float(ra.max()))
+            n1[c] += float(d.sum())
+            d1[c] += float(ra.sum())
+            del d, ra
+    names = ["rho", "m_x", "m_y", "m_z", "rhoE", "rhoe"]
+    return {n: {"linf": ninf[c] / max(dinf[c], 1e-300), "l1": n1[c] / max(d1[c], 1e-300)}
+            for c, n in enumerate(names)}
+
+
 def run_ours(args, w):
     import torch
     from paper_1301_4498_gb300 import hydro as H
@@ -456,15 +492,32 @@ def run_ours(args, w):
         # shock flattening: the coefficient pass, then the advance reading it
         variants["flattening"] = one_advance(flattening=True)
 
-    # FP64 forms on the same workload (one step each), for the FP32-vs-FP64 comparison
+    # FP64 forms on the same workload (one step each), for the FP32-vs-FP64
+    # comparison; the mixed step's per-field error against the FP64 step from
+    # the same state with the same dt
     side = {}
+    errors = None
     if not args.no_fp64:
         restore()
+        lm = H.Level(lev.state[0], lev.state[1], lev.grav, lev.cur)
+        plan.run(lm, a, dt, 1, compute_dt0=True, use_graph=False)
+        torch.cuda.synchronize()
+        mixed_new = lm.state[lm.cur].clone()
+        dt0 = dt[:1].clone()
         for label, batching in (("fp64_persistent", "persistent"), ("fp64_per_box", "per_box")):
+            restore()
             p64 = H.Plan(w.level, gamma=w.gamma, cfl=w.cfl, precision="fp64", batching=batching)
             l64 = H.Level(lev.state[0], lev.state[1], lev.grav, lev.cur)
-            p64.run(l64, a, dt, 1, compute_dt0=True, use_graph=False)
+            dt[:1].copy_(dt0)
+            p64.run(l64, a, dt, 1, compute_dt0=False, use_graph=False)
             torch.cuda.synchronize()
+            if label == "fp64_persistent":
+                errors = {"reference": "the FP64 persistent form, one step from the same state "
+                                       "and dt (bit for bit the FP64 oracle's arithmetic)",
+                          "metric": "normwise relative over the valid cells: max|d|/max|ref| "
+                                    "and sum|d|/sum|ref|",
+                          "fields": field_errors(plan, w.level, mixed_new, l64.state[l64.cur])}
+                del mixed_new
             f0 = torch.cuda.Event(enable_timing=True)
             f1 = torch.cuda.Event(enable_timing=True)
             f0.record(p64.torch_stream)
@@ -518,6 +571,7 @@ def run_ours(args, w):
             "kernel_ms": {"advance": adv_ms, "ghost_fill": fill_ms},
             "variants": variants,
             "fp64_comparison": side,
+            "mixed_vs_fp64": errors,
             "clocks": clk,
             "e2e": e2e,
             "gpu_launches": launches,
