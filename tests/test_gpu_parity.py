@@ -97,11 +97,33 @@ def test_estdt_matches_oracle_bitwise():
 
 # ------------------------------------------------------------------ FP64 parity
 
+def _thin_slabs(nsteps=2):
+    """A periodic 16 x 8 x 8 comoving field cut into four 16 x 8 x 2 slabs:
+    every box has n_z = 2, so its z ghost cells come from boxes up to two
+    slabs away, and the task form's plane pipeline (ring, input and flux
+    hand-overs) runs at its shortest."""
+    dx = 1.0 / 16
+    lo = [[0, 0, 2 * k] for k in range(4)]
+    hi = [[15, 7, 2 * k + 1] for k in range(4)]
+    lev = W._mk(lo, hi, [0] * 4, [[dx] * 3] * 4, [0, 0, 0], [15, 7, 7], [0] * 6, "thin")
+    f = W.comoving_fields((8, 8, 16), 0.5, 7, dx)
+    S, G = [], []
+    for b in range(4):
+        sl = (slice(2 * b, 2 * b + 2), slice(0, 8), slice(0, 16))
+        fb = W.Fields(f.rho[sl], f.u[(slice(None),) + sl], f.g[(slice(None),) + sl])
+        s, g = W._patch_state(lev, b, fb)
+        S.append(s)
+        G.append(g)
+    return W.Workload("thin slabs 16x8x2", lev, S, G, W.a_schedule(1 / 51, 1 / 49, nsteps),
+                      5.0 / 3.0, 0.5, nsteps, False)
+
+
 SMALL_CASES = {
     "sod": (lambda: W.sod(), 20),
     "comoving32": (lambda: W.comoving_box(n=32, nsteps=3), 3),
     "tiled64x8": (lambda: W.tiled_box(n=64, box=32, nsteps=2), 2),
     "uneven6": (lambda: W.uneven_boxes(nbox=512, boxes=[0, 1, 2, 3, 4, 5], nsteps=2), 2),
+    "thin": (lambda: _thin_slabs(2), 2),
 }
 
 
@@ -192,7 +214,7 @@ def test_mixed_within_gates(oracle_results, name):
 
 
 @pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5])
-@pytest.mark.parametrize("name", ["sod", "tiled64x8", "uneven6"])
+@pytest.mark.parametrize("name", ["sod", "tiled64x8", "uneven6", "thin"])
 def test_mixed_every_tile_shape_within_gates(oracle_results, name, shape):
     """Both forms of the mixed kernel (column-owning shapes 0-2, task form
     3-5), including ragged tiles of the uneven boxes."""
