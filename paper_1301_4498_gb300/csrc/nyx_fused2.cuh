@@ -201,11 +201,12 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
   const nyx::StepConsts sc = *a.SC;
   Eos<float> E = make_eos<float>(KK, true);
   // VAR >= 0 fixes the scheme variant at compile time (bit 0 PLM, bit 1 the
-  // linearised solver), so the default instantiation carries no variant code
+  // linearised solver, bit 2 shock flattening), so the default instantiation
+  // carries no variant code
   if constexpr (VAR >= 0) {
     E.plm = VAR & 1;
     E.linear = (VAR >> 1) & 1;
-    E.flat = 0;
+    E.flat = (VAR >> 2) & 1;
   }
   TraceSrc<float> src;
   src.hdtp = d2f_rn(sc.hdtp);

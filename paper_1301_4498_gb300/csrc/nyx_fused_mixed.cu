@@ -16,8 +16,9 @@ int launch_fused_mixed(int shape, const FusedArgs &a, int grid, cudaStream_t st)
     case 0: return nyx_mixed::launch_one<float, 16, 16>(a, grid, st);
     case 1: return nyx_mixed::launch_one<float, 32, 8>(a, grid, st);
     case 2: return nyx_mixed::launch_one<float, 16, 8>(a, grid, st);
-    case 3:  // the default shape: one instantiation per scheme variant (flattening: the
-             // instantiation with run-time variant flags)
+    case 3:  // the default shape: one instantiation per scheme variant (flattening with
+             // PLM or the linearised solver: the one with run-time variant flags)
+      if (a.variant == 4) return nyx_mixed::launch_two<16, 8, 1, 4>(a, grid, st);
       if (a.variant & 4) return nyx_mixed::launch_two<16, 8, 1, -1>(a, grid, st);
       switch (a.variant) {
         case 1: return nyx_mixed::launch_two<16, 8, 1, 1>(a, grid, st);
@@ -41,6 +42,7 @@ int max_grid_mixed(int shape) {
       g = std::min(g, nyx_mixed::max_grid_two<16, 8, 1, 1>());
       g = std::min(g, nyx_mixed::max_grid_two<16, 8, 1, 2>());
       g = std::min(g, nyx_mixed::max_grid_two<16, 8, 1, -1>());
+      g = std::min(g, nyx_mixed::max_grid_two<16, 8, 1, 4>());
       return std::min(g, nyx_mixed::max_grid_two<16, 8, 1, 3>());
     }
     case 4: return nyx_mixed::max_grid_two<8, 8, 2, -1>();
