@@ -120,6 +120,9 @@ typedef struct {
                               has its profiles pulled toward the cell value.  Costs one
                               extra pass over the level per advance and, per plan, one
                               value per cell (FP64 plans double, mixed plans float). */
+  int z_chunks;            /* 1: the task-form tile shapes may cut columns into chunks of
+                              planes to even out the CTAs' loads (nyx_task_items); 0 keeps
+                              whole columns.  Either gives the same result, bit for bit. */
 } nyx_hydro_params;
 
 typedef struct nyx_plan nyx_plan;
@@ -136,7 +139,7 @@ typedef struct {
 /* Fill *params with the defaults (gamma 5/3, cfl 0.5, small_dens 1e-10,
  * small_pres 1e-12, eta_de 1e-4, 12 iterations, tol 1e-10, FP64,
  * corrector on, persistent, autotune off, keep_fluxes off, coarse_fine off,
- * grav_energy 0, PPM, two-shock solver, no flattening). */
+ * grav_energy 0, PPM, two-shock solver, no flattening, z_chunks 1). */
 void nyx_hydro_default_params(nyx_hydro_params *params);
 
 /* Validate the level (Sec. 4.1: even positive extents, ng == 4, boxes of a
@@ -244,6 +247,21 @@ int nyx_hydro_step_host_valid(nyx_plan *plan, nyx_level *level, const double *ho
 int nyx_hydro_tile_shape(int shape, int *tx, int *ty);
 int nyx_hydro_set_tile_shape(nyx_plan *plan, int shape);
 int nyx_hydro_get_tile_shape(const nyx_plan *plan, int *shape);
+
+/* Work list of the fused persistent kernel for a level of nbox boxes with
+ * interior extents n[3b], n[3b+1], n[3b+2] (x, y, z) and column tiles of
+ * tx x ty, run on `slots` resident CTAs that take items from one queue.
+ * Host only: it needs no GPU and no plan, and is the list a plan builds.
+ * Each item is 7 ints (box, x0, y0, nx, ny, z0, nz): cells [x0, x0+nx) x
+ * [y0, y0+ny) x [z0, z0+nz) of the box; the items tile every box once.
+ * chunk = 0 keeps every column whole (the column-owning shapes); chunk != 0
+ * (the task-form shapes) lets the list cut columns along z into chunks
+ * when that evens out the CTAs' loads.  Items come in queue order, the
+ * largest first.  Writes min(cap, *count) items to `items` (caller-owned,
+ * 7 * cap ints) and the full count to *count.  NYX_EINVAL for a negative
+ * size, an empty box, tx, ty or slots below 1, or a null pointer. */
+int nyx_task_items(int nbox, const int *n, int tx, int ty, int slots, int chunk, int *items,
+                   int cap, int *count);
 
 /* Counters of the plan: kernel launches it enqueued (graph replays count
  * the kernels of the graph), and, while profiling is on, the summed CUDA

@@ -5,11 +5,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <queue>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -228,30 +230,124 @@ int upload_pass(FillPass &p, const std::vector<FillRect> &rects) {
   return NYX_OK;
 }
 
-// Work list of the fused kernel for one tile shape: every box cut into
-// tx x ty column tiles, ordered largest work first (LPT).
-std::vector<WorkItem> build_items(const nyx_plan &P, int tx, int ty) {
-  std::vector<WorkItem> items;
-  for (int b = 0; b < P.nbox; ++b) {
-    const BoxDev &X = P.hbox[b];
-    for (int y0 = 0; y0 < X.n[1]; y0 += ty)
-      for (int x0 = 0; x0 < X.n[0]; x0 += tx) {
-        WorkItem w;
-        w.box = b;
-        w.x0 = x0;
-        w.y0 = y0;
-        w.nx = std::min(tx, X.n[0] - x0);
-        w.ny = std::min(ty, X.n[1] - y0);
-        w.pad = 0;
-        items.push_back(w);
-      }
+// ---------------------------------------------------------------- work lists
+// Relative cost of a work item: its columns times the plane steps it takes.
+// An item of nz planes runs nz + 2 column steps (the first plane's traces
+// and the last z face are extra) plus its ring prologue, about one more.
+double item_cost(const WorkItem &w) { return double(w.nx + 2) * (w.ny + 2) * (w.nz + 3); }
+
+void lpt_sort(std::vector<WorkItem> &it) {
+  std::stable_sort(it.begin(), it.end(),
+                   [](const WorkItem &a, const WorkItem &b) { return item_cost(a) > item_cost(b); });
+}
+
+// Finish time of the last of `slots` resident CTAs that each take the next
+// item of the list when they are free (the work queue of the persistent
+// kernels), with item_cost as the duration.
+double queue_makespan(const std::vector<WorkItem> &it, int slots) {
+  std::priority_queue<double, std::vector<double>, std::greater<double>> q;
+  for (int i = 0; i < slots; ++i) q.push(0.0);
+  double m = 0.0;
+  for (const WorkItem &w : it) {
+    const double t = q.top() + item_cost(w);
+    q.pop();
+    q.push(t);
+    m = std::max(m, t);
   }
-  std::stable_sort(items.begin(), items.end(), [&](const WorkItem &a, const WorkItem &b) {
-    long long wa = (long long)(a.nx + 2) * (a.ny + 2) * (P.hbox[a.box].n[2] + 2);
-    long long wb = (long long)(b.nx + 2) * (b.ny + 2) * (P.hbox[b.box].n[2] + 2);
-    return wa > wb;
-  });
+  return m;
+}
+
+constexpr int kWhole = 1 << 30;
+constexpr int kRestChunk = 16;  // planes of the chunks a long column's rest is cut into
+
+// Every box cut into tx x ty column tiles, every column of n planes cut by
+// the rule (L, M): n > M gives a main chunk of M planes and the rest in
+// chunks of at most kRestChunk; otherwise ceil(n / L) chunks as even as
+// possible.  (kWhole, kWhole) keeps the columns whole.
+std::vector<WorkItem> tile_items(const std::vector<std::array<int, 3>> &n, int tx, int ty, int L,
+                                 int M) {
+  std::vector<WorkItem> items;
+  std::vector<std::pair<int, int>> cuts;
+  for (int b = 0; b < (int)n.size(); ++b) {
+    const int nz = n[b][2];
+    cuts.clear();
+    if (nz > M) {
+      cuts.push_back({0, M});
+      const int r = nz - M, k = (r + kRestChunk - 1) / kRestChunk;
+      for (int i = 0; i < k; ++i) cuts.push_back({M + r * i / k, r * (i + 1) / k - r * i / k});
+    } else {
+      const int k = std::max(1, (int)(((long long)nz + L - 1) / L));
+      for (int i = 0; i < k; ++i)
+        cuts.push_back({(int)((long long)nz * i / k), (int)((long long)nz * (i + 1) / k - (long long)nz * i / k)});
+    }
+    for (const auto &c : cuts)
+      for (int y0 = 0; y0 < n[b][1]; y0 += ty)
+        for (int x0 = 0; x0 < n[b][0]; x0 += tx) {
+          WorkItem w;
+          w.box = b;
+          w.x0 = x0;
+          w.y0 = y0;
+          w.nx = std::min(tx, n[b][0] - x0);
+          w.ny = std::min(ty, n[b][1] - y0);
+          w.z0 = c.first;
+          w.nz = c.second;
+          w.pad = 0;
+          items.push_back(w);
+        }
+  }
+  lpt_sort(items);
   return items;
+}
+
+// Work list of the fused kernel for one tile shape, in the order the queue
+// hands it out (largest first).  The column-owning form takes whole columns.
+// The task form streams any range of planes, so when whole columns leave
+// the `slots` resident CTAs unevenly loaded (fewer tiles than CTAs, or a
+// last partial wave), the columns are cut along z: among even cuts into
+// chunks of at least 16 planes and cuts into one main chunk plus short
+// rest chunks that fill the queue's tail, the one with the earliest
+// simulated finish is taken, if it beats whole columns by 2 %.
+std::vector<WorkItem> task_items(const std::vector<std::array<int, 3>> &n, int tx, int ty,
+                                 int slots, bool chunk) {
+  std::vector<WorkItem> best = tile_items(n, tx, ty, kWhole, kWhole);
+  if (!chunk || slots < 1 || best.empty()) return best;
+  const double whole = queue_makespan(best, slots);
+  double total = 0.0;
+  for (const WorkItem &w : best) total += item_cost(w);
+  if (whole <= 1.02 * total / slots) return best;
+
+  std::vector<std::pair<int, int>> rules;
+  int nmax = 0;
+  for (const auto &e : n) {
+    nmax = std::max(nmax, e[2]);
+    for (int k = 2; k <= e[2] / 16; ++k) rules.push_back({(e[2] + k - 1) / k, kWhole});
+  }
+  const double plane_lb = total / slots / ((tx + 2) * (ty + 2));
+  for (int i = 0; i <= 24; ++i) {
+    const int M = (int)std::floor(plane_lb * (1.0 + 0.01 * i)) - 3;
+    if (M >= 16 && M < nmax) rules.push_back({kWhole, M});
+  }
+  std::sort(rules.begin(), rules.end());
+  rules.erase(std::unique(rules.begin(), rules.end()), rules.end());
+
+  const size_t cap = (size_t)64 * slots;
+  double bm = 0.98 * whole;
+  for (const auto &r : rules) {
+    std::vector<WorkItem> it = tile_items(n, tx, ty, r.first, r.second);
+    if (it.size() > std::max(cap, best.size())) continue;
+    const double m = queue_makespan(it, slots);
+    if (m < bm) {
+      bm = m;
+      best.swap(it);
+    }
+  }
+  return best;
+}
+
+std::vector<WorkItem> build_items(const nyx_plan &P, int tx, int ty, int slots, bool chunk) {
+  std::vector<std::array<int, 3>> n(P.nbox);
+  for (int b = 0; b < P.nbox; ++b) n[b] = {P.hbox[b].n[0], P.hbox[b].n[1], P.hbox[b].n[2]};
+  return task_items(n, tx, ty, slots, chunk);
 }
 
 void free_plan(nyx_plan *P) {
@@ -553,7 +649,8 @@ namespace nyx {
 void record_error(const char *msg) { g_err = msg ? msg : ""; }
 
 // 0-2: column-owning form (FP64 and mixed); 3-5: task form (mixed only)
-static const TileShape kShapes[] = {{16, 16}, {32, 8}, {16, 8}, {16, 8}, {8, 8}, {32, 4}};
+static const TileShape kShapes[] = {{16, 16, 0}, {32, 8, 0}, {16, 8, 0},
+                                    {16, 8, 1},  {8, 8, 1},  {32, 4, 1}};
 
 int fused_num_shapes(int precision) { return precision == NYX_MIXED ? 6 : 3; }
 TileShape fused_shape(int idx) { return kShapes[idx]; }
@@ -606,6 +703,7 @@ void nyx_hydro_default_params(nyx_hydro_params *p) {
   p->reconstruction = NYX_PPM;
   p->riemann_solver = NYX_RS_TWO_SHOCK;
   p->flattening = 0;
+  p->z_chunks = 1;
 }
 
 const char *nyx_last_error(void) { return g_err.c_str(); }
@@ -775,16 +873,6 @@ int nyx_hydro_plan(const nyx_level_desc *lev, const nyx_hydro_params *prm, void 
     if (prm->batching == NYX_PER_BOX) {
       TRYC(cudaMalloc(&P->d_scratch, sizeof(double) * staged_scratch_doubles(P->Vmax)));
     } else {
-      for (int s = 0; s < fused_num_shapes(prm->precision); ++s) {
-        TileShape ts = fused_shape(s);
-        std::vector<WorkItem> it = build_items(*P, ts.tx, ts.ty);
-        P->nitems[s] = (int)it.size();
-        TRYC(cudaMalloc(&P->d_items[s], sizeof(WorkItem) * it.size()));
-        TRYC(cudaMemcpy(P->d_items[s], it.data(), sizeof(WorkItem) * it.size(),
-                        cudaMemcpyHostToDevice));
-      }
-      TRYC(cudaMalloc(&P->d_queue, sizeof(int)));
-      TRYC(cudaMemset(P->d_queue, 0, sizeof(int)));
       for (int sh = 0; sh < fused_num_shapes(prm->precision); ++sh) {
         P->max_grid[sh] = fused_max_grid(prm->precision, sh);
         if (P->max_grid[sh] < 1) {
@@ -792,6 +880,17 @@ int nyx_hydro_plan(const nyx_level_desc *lev, const nyx_hydro_params *prm, void 
           goto fail_out;
         }
       }
+      for (int s = 0; s < fused_num_shapes(prm->precision); ++s) {
+        TileShape ts = fused_shape(s);
+        std::vector<WorkItem> it = build_items(*P, ts.tx, ts.ty, P->max_grid[s],
+                                                ts.task && prm->z_chunks);
+        P->nitems[s] = (int)it.size();
+        TRYC(cudaMalloc(&P->d_items[s], sizeof(WorkItem) * it.size()));
+        TRYC(cudaMemcpy(P->d_items[s], it.data(), sizeof(WorkItem) * it.size(),
+                        cudaMemcpyHostToDevice));
+      }
+      TRYC(cudaMalloc(&P->d_queue, sizeof(int)));
+      TRYC(cudaMemset(P->d_queue, 0, sizeof(int)));
       TRYC(cudaGetLastError());
     }
     if (prm->keep_fluxes) {
@@ -1015,6 +1114,26 @@ int nyx_hydro_tile_shape(int shape, int *tx, int *ty) {
   TileShape t = fused_shape(shape);
   if (tx) *tx = t.tx;
   if (ty) *ty = t.ty;
+  return NYX_OK;
+}
+
+int nyx_task_items(int nbox, const int *n, int tx, int ty, int slots, int chunk, int *items,
+                   int cap, int *count) {
+  if (nbox < 0 || (nbox > 0 && !n) || tx < 1 || ty < 1 || slots < 1 || cap < 0 ||
+      (cap > 0 && !items) || !count)
+    return fail(NYX_EINVAL, "bad arguments to nyx_task_items");
+  std::vector<std::array<int, 3>> e(nbox);
+  for (int b = 0; b < nbox; ++b) {
+    e[b] = {n[3 * b], n[3 * b + 1], n[3 * b + 2]};
+    if (e[b][0] < 1 || e[b][1] < 1 || e[b][2] < 1) return fail(NYX_EINVAL, "empty box");
+  }
+  std::vector<WorkItem> it = task_items(e, tx, ty, slots, chunk != 0);
+  *count = (int)it.size();
+  for (int i = 0; i < std::min(cap, (int)it.size()); ++i) {
+    const WorkItem &w = it[i];
+    const int v[7] = {w.box, w.x0, w.y0, w.nx, w.ny, w.z0, w.nz};
+    std::memcpy(items + 7 * i, v, sizeof v);
+  }
   return NYX_OK;
 }
 

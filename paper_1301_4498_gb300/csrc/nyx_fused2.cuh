@@ -233,6 +233,7 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
     const nyx::WorkItem w = a.items[item];
     const nyx::BoxDev b = a.boxes[w.box];
     const int nxt = w.nx, nyt = w.ny, nz = b.n[2];
+    const int zb = w.z0, ze = w.z0 + w.nz;  // this item's planes [zb, ze)
     const long long bs = b.stride;
     const long long ps = (long long)b.N[0] * b.N[1];
     const double *S = a.S + nyx::NCONS * b.pref;
@@ -247,9 +248,9 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
       const bool inX = mi >= 0 && mi < nxt, inY = mj >= 0 && mj < nyt;
       auto ring = [&](int plane) { return sm + G::PR + ring5(plane) * 5 * NC + me; };
 
-      for (int c = -1; c <= nz; ++c) {
+      for (int c = zb - 1; c <= ze; ++c) {
         const int pc = par2(c), pm = par2(c - 1);
-        const bool zc = c >= 1;
+        const bool zc = c >= zb + 1;
         // ---------------------------------------------- S0: plane c's inputs (update warps)
         bar_sync_n(BAR_LOADED, NT);
 
@@ -289,7 +290,7 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
         }
         bar_sync_n(BAR_COL, NTC);
         // ring plane c-2 and the framed plane c are no longer read
-        if (c < nz) bar_arrive_n(BAR_CONSUMED, NT);
+        if (c < ze) bar_arrive_n(BAR_CONSUMED, NT);
 
         // ---------------------------------------------- S2: normal solves
         if (act) {
@@ -310,7 +311,7 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
             Rr = sm + G::QXY + (pc * 2 + 1) * 10 * NC;
             O = sm + G::P1 + 7 * NC;
           } else {
-            go = c >= 0;
+            go = c >= zb;
             L = sm + G::QZ + pm * 10 * NC + 5 * NC;
             lc = me;
             Rr = sm + G::QZ + pc * 10 * NC;
@@ -405,11 +406,11 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
                 Rr = sm + G::P2 + 30 * NC; O = sm + G::P1 + 21 * NC;
                 break;
               case 4:  // F^{z|x} at face c-1/2
-                go = c >= 0 && inX; dir = 2; L = sm + G::QZXP + pm * 5 * NC; lc = me;
+                go = c >= zb && inX; dir = 2; L = sm + G::QZXP + pm * 5 * NC; lc = me;
                 Rr = sm + G::QZXM; O = sm + G::FZXY + (pc * 2 + 0) * 7 * NC;
                 break;
               default:  // F^{z|y} at face c-1/2
-                go = c >= 0 && inY; dir = 2; L = sm + G::QZYP + pm * 5 * NC; lc = me;
+                go = c >= zb && inY; dir = 2; L = sm + G::QZYP + pm * 5 * NC; lc = me;
                 Rr = sm + G::QZYM; O = sm + G::FZXY + (pc * 2 + 1) * 7 * NC;
                 break;
             }
@@ -478,7 +479,7 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
             } else if (kq == 1) {
               go = zc && mj >= 0 && inX; L = sm + G::P2 + 15 * NC; lc = me - W; Rr = sm + G::P2 + 10 * NC;
             } else {
-              go = c >= 0 && inX && inY; L = sm + G::QZFP + pm * 5 * NC; lc = me; Rr = sm + G::QZFM;
+              go = c >= zb && inX && inY; L = sm + G::QZFP + pm * 5 * NC; lc = me; Rr = sm + G::QZFM;
             }
             if (go) {
               float l[5], r[5];
@@ -487,14 +488,14 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
               face_flux_dir(E, kq, l, r, F);
             }
           }
-          if (c >= 2) bar_sync_n(BAR_FREE, NT);
+          if (c >= zb + 2) bar_sync_n(BAR_FREE, NT);
           if (go) {
             float *O = (kq == 0)   ? sm + G::UF + mj * (TX + 1) + mi
                        : (kq == 1) ? sm + G::UF + NXF + mj * TX + mi
                                    : sm + G::FFZ + (c & 1) * 8 * NZF + mj * TX + mi;
             st8(O, (kq == 2) ? NZF : NUF, 0, F);
           }
-          if (c >= 1) {
+          if (c >= zb + 1) {
             __threadfence_block();
             bar_arrive_n(BAR_READY, NT);
           }
@@ -594,18 +595,19 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
         long long col;
         if (!column(e, col)) continue;
 #pragma unroll 1
-        for (int k = -3; k <= 0; ++k) load_prims(col + (long long)(k + 4) * ps, ring_at(k) + e, NC);
+        for (int k = zb - 3; k <= zb; ++k)
+          load_prims(col + (long long)(k + 4) * ps, ring_at(k) + e, NC);
       }
-      inputs(-1);
+      inputs(zb - 1);
       __threadfence_block();
       bar_arrive_n(BAR_LOADED, NT);
-      for (int c = 0; c <= nz; ++c) {
+      for (int c = zb; c <= ze; ++c) {
         // plane c-1 traced: its ring plane c-3 slot and the framed plane are free
         bar_sync_n(BAR_CONSUMED, NT);
         inputs(c);
         __threadfence_block();
         bar_arrive_n(BAR_LOADED, NT);
-        if (c >= 2) {
+        if (c >= zb + 2) {
           // the final fluxes of plane c-2 (x, y faces; z faces c-5/2 and c-3/2)
           bar_sync_n(BAR_READY, NT);
           update_plane(c - 2);
@@ -614,7 +616,7 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
         }
       }
       bar_sync_n(BAR_READY, NT);
-      update_plane(nz - 1);
+      update_plane(ze - 1);
     }
     __syncthreads();
   }

@@ -72,6 +72,7 @@ struct WorkItem {
   int box;
   int x0, y0;
   int nx, ny;     // tile extent (<= TX, TY at the box edge)
+  int z0, nz;     // planes [z0, z0 + nz) of the box (the task form; whole columns otherwise)
   int pad;
 };
 

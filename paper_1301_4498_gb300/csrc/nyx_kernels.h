@@ -67,6 +67,7 @@ struct FusedArgs {
 // Tile shapes of the fused kernel (columns per CTA in x and y).
 struct TileShape {
   int tx, ty;
+  int task;  // the task form (streams any range of planes) rather than column-owning
 };
 int fused_num_shapes(int precision);
 TileShape fused_shape(int idx);

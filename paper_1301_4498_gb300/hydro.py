@@ -65,7 +65,8 @@ class NyxParams(C.Structure):
                 ("precision", C.c_int), ("grav_corrector", C.c_int), ("batching", C.c_int),
                 ("autotune", C.c_int), ("keep_fluxes", C.c_int), ("coarse_fine", C.c_int),
                 ("grav_energy", C.c_int), ("reconstruction", C.c_int),
-                ("riemann_solver", C.c_int), ("flattening", C.c_int)]
+                ("riemann_solver", C.c_int), ("flattening", C.c_int),
+                ("z_chunks", C.c_int)]
 
 
 class NyxPoissonParams(C.Structure):
@@ -121,6 +122,7 @@ def load_library(path: str | None = None):
     L.nyx_hydro_status.argtypes = [vp, ip]
     L.nyx_plan_destroy.argtypes = [vp]
     L.nyx_hydro_tile_shape.argtypes = [C.c_int, ip, ip]
+    L.nyx_task_items.argtypes = [C.c_int, ip, C.c_int, C.c_int, C.c_int, C.c_int, ip, C.c_int, ip]
     L.nyx_hydro_set_tile_shape.argtypes = [vp, C.c_int]
     L.nyx_hydro_get_tile_shape.argtypes = [vp, ip]
     L.nyx_hydro_profile.argtypes = [vp, C.c_int]
@@ -463,6 +465,28 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def tile_shape_of(shape):
+    """Columns (tx, ty) of a tile shape of the fused kernel."""
+    tx, ty = C.c_int(), C.c_int()
+    _check(load_library().nyx_hydro_tile_shape(shape, C.byref(tx), C.byref(ty)))
+    return tx.value, ty.value
+
+
+def task_items(extents, tx, ty, slots, chunk=True):
+    """The fused kernel's work list for boxes of interior extents [(nx, ny,
+    nz), ...], tiles tx x ty on `slots` resident CTAs: an (items, 7) int
+    array of (box, x0, y0, nx, ny, z0, nz) in queue order.  Host only."""
+    lib = load_library()
+    n = (C.c_int * max(1, 3 * len(extents)))(*[int(v) for e in extents for v in e])
+    count = C.c_int()
+    _check(lib.nyx_task_items(len(extents), n, tx, ty, slots, int(bool(chunk)), None, 0,
+                              C.byref(count)))
+    out = (C.c_int * max(1, 7 * count.value))()
+    _check(lib.nyx_task_items(len(extents), n, tx, ty, slots, int(bool(chunk)), out, count.value,
+                              C.byref(count)))
+    return np.array(out[:7 * count.value], dtype=np.int64).reshape(count.value, 7)
 
 
 def estdt_noalloc(spec, state, a_dev, dt_dev, stream=None, **params):

@@ -4,18 +4,19 @@ update warps of the task-form kernel (nyx_fused2.cuh).
 The kernel's column threads (producer of fluxes) and update threads
 (consumer of fluxes, and producer of each plane's inputs) meet on four named
 barriers per box tile:
-  * the update warps write the primitive ring's planes -3 .. 1 and plane -1's
-    frame, gravity and flattening rows, and arrive on LOADED; then for
-    c = 0 .. nz they wait on CONSUMED, write ring plane c+2 and plane c's
-    frame, arrive on LOADED, and (c >= 2) wait on READY, update plane c-2
-    and arrive on FREE when c <= nz; finally they wait on READY and update
-    plane nz-1;
-  * the column threads, plane step c = -1 .. nz: wait on LOADED, trace plane
-    c (ring planes c-2 .. c+2, the frame of plane c), pass their stage
-    barrier, arrive on CONSUMED when c < nz, run their other stages, wait on
-    FREE when c >= 2, store the fluxes of plane c-1 (x/y buffer) and of z
-    face c (slot c & 1), and arrive on READY when c >= 1;
-  * both then meet on the CTA-wide barrier before the next tile.
+  * a work item is a tile's planes [zb, ze) (the whole column, zb = 0 and
+    ze = nz, or a chunk of it);
+  * the update warps write the primitive ring's planes zb-3 .. zb+1 and plane
+    zb-1's frame, gravity and flattening rows, and arrive on LOADED; then for
+    c = zb .. ze they wait on CONSUMED, write ring plane c+2 and plane c's
+    frame, arrive on LOADED, and (c >= zb+2) wait on READY, update plane c-2
+    and arrive on FREE; finally they wait on READY and update plane ze-1;
+  * the column threads, plane step c = zb-1 .. ze: wait on LOADED, trace
+    plane c (ring planes c-2 .. c+2, the frame of plane c), pass their stage
+    barrier, arrive on CONSUMED when c < ze, run their other stages, wait on
+    FREE when c >= zb+2, store the fluxes of plane c-1 (x/y buffer) and of z
+    face c (slot c & 1), and arrive on READY when c >= zb+1;
+  * both then meet on the CTA-wide barrier before the next item.
 This test models bar.sync / bar.arrive phase counting (a phase completes when
 the arrivals reach the barrier's thread count) and runs the two sequences
 under random interleavings.  It checks that every phase completes with exactly
@@ -32,45 +33,51 @@ NT = NTC + NU
 BAR_ALL, BAR_COL, BAR_READY, BAR_FREE, BAR_LOADED, BAR_CONSUMED = 0, 1, 2, 3, 4, 5
 
 
-def producer_ops(nz):
+def producer_ops(zb, ze):
     ops = []
-    for c in range(-1, nz + 1):
+    for c in range(zb - 1, ze + 1):
         ops.append(("sync", BAR_LOADED, NT))
         ops.append(("trace", c))
         ops.append(("sync", BAR_COL, NTC))           # end of the trace stage
-        if c < nz:
+        if c < ze:
             ops.append(("arrive", BAR_CONSUMED, NT))
         ops += [("sync", BAR_COL, NTC)] * 4          # stage barriers S2..S5
-        if c >= 2:
+        if c >= zb + 2:
             ops.append(("sync", BAR_FREE, NT))
         ops.append(("store", c))
-        if c >= 1:
+        if c >= zb + 1:
             ops.append(("arrive", BAR_READY, NT))
     ops.append(("sync", BAR_ALL, NT))
     return ops
 
 
-def consumer_ops(nz):
-    ops = [("prologue",), ("write", -1), ("arrive", BAR_LOADED, NT)]
-    for c in range(0, nz + 1):
+def consumer_ops(zb, ze):
+    ops = [("prologue",), ("write", zb - 1), ("arrive", BAR_LOADED, NT)]
+    for c in range(zb, ze + 1):
         ops.append(("sync", BAR_CONSUMED, NT))
         ops.append(("write", c))
         ops.append(("arrive", BAR_LOADED, NT))
-        if c >= 2:
+        if c >= zb + 2:
             ops.append(("sync", BAR_READY, NT))
             ops.append(("load", c - 2))
-            if c <= nz:
-                ops.append(("arrive", BAR_FREE, NT))
+            ops.append(("arrive", BAR_FREE, NT))
     ops.append(("sync", BAR_READY, NT))
-    ops.append(("load", nz - 1))
+    ops.append(("load", ze - 1))
     ops.append(("sync", BAR_ALL, NT))
     return ops
 
 
+def _items(depths):
+    """Work items (zb, ze): an int is a whole column of that depth, a pair
+    a chunk of planes."""
+    return [(0, d) if isinstance(d, int) else tuple(d) for d in depths]
+
+
 def simulate(depths, rng):
     weight = {"P": NTC, "C": NU}
-    prog = {"P": [op for nz in depths for op in producer_ops(nz)],
-            "C": [op for nz in depths for op in consumer_ops(nz)]}
+    items = _items(depths)
+    prog = {"P": [op for zb, ze in items for op in producer_ops(zb, ze)],
+            "C": [op for zb, ze in items for op in consumer_ops(zb, ze)]}
     pos = {"P": 0, "C": 0}
     tile = {"P": 0, "C": 0}
     bars = {}
@@ -111,16 +118,17 @@ def simulate(depths, rng):
                     tile["C"] += 1
         elif op[0] == "prologue":
             t = tile["C"]
-            for k in range(-3, 1):
+            zb = items[t][0]
+            for k in range(zb - 3, zb + 1):
                 ring[(k + 8) % 5] = (t, k)
         elif op[0] == "write":
             c, t = op[1], tile["C"]
-            nz = depths[t]
+            zb, ze = items[t]
             k = c + 2                                 # ring plane written
             old = ring.get((k + 8) % 5)
             if old is not None and old[0] == t:
                 q = old[1]
-                for cc in range(max(-1, q - 2), min(nz, q + 2) + 1):
+                for cc in range(max(zb - 1, q - 2), min(ze, q + 2) + 1):
                     assert (t, cc) in traced, f"ring plane {q} overwritten before trace {cc}"
             ring[(k + 8) % 5] = (t, k)
             if frame and frame["tile"] == t:
@@ -134,10 +142,11 @@ def simulate(depths, rng):
             traced.add((t, c))
         elif op[0] == "store":
             c, t = op[1], tile["P"]
-            if c >= 1:
+            zb = items[t][0]
+            if c >= zb + 1:
                 assert not xy.get("live"), f"x/y fluxes of plane {xy.get('plane')} overwritten"
                 xy.update(tile=t, plane=c - 1, live=True)
-            if c >= 0:
+            if c >= zb:
                 old = zf.get(c & 1)
                 assert not (old and old["live"]), f"z face {old and old['face']} overwritten"
                 zf[c & 1] = {"tile": t, "face": c, "live": True}
@@ -149,13 +158,15 @@ def simulate(depths, rng):
                 assert s and s["live"] and (s["tile"], s["face"]) == (t, f)
             xy["live"] = False
             zf[p & 1]["live"] = False           # face p is needed by plane p only from now on
-            nz = depths[t]
-            if p == nz - 1:
+            if p == items[t][1] - 1:
                 zf[(p + 1) & 1]["live"] = False  # the tile's last face
 
 
 @pytest.mark.parametrize("depths", [[1], [2], [3], [4], [5], [8], [32], [64],
-                                    [1, 2, 3, 4, 5, 6, 7, 8], [32, 64, 32, 1, 3]])
+                                    [1, 2, 3, 4, 5, 6, 7, 8], [32, 64, 32, 1, 3],
+                                    [(0, 112), (112, 128), (0, 16)],
+                                    [(5, 6), (6, 8), (0, 5), (3, 4), (40, 43)],
+                                    [(64, 128), 16, (17, 33), (1, 2)]])
 def test_flux_handover_protocol(depths):
     for seed in range(200):
         simulate(depths, random.Random(seed))
@@ -167,8 +178,8 @@ def test_planted_input_mistake_is_caught():
     global consumer_ops
     saved = consumer_ops
 
-    def eager(nz):
-        ops = saved(nz)
+    def eager(zb, ze):
+        ops = saved(zb, ze)
         for i in range(len(ops) - 1):       # write before the wait, counts unchanged
             if ops[i][:2] == ("sync", BAR_CONSUMED) and ops[i + 1][0] == "write":
                 ops[i], ops[i + 1] = ops[i + 1], ops[i]
@@ -192,8 +203,8 @@ def test_planted_protocol_mistake_is_caught():
     global consumer_ops
     saved = consumer_ops
 
-    def early(nz):
-        ops = saved(nz)
+    def early(zb, ze):
+        ops = saved(zb, ze)
         out = []
         for op in ops:
             if op[0] == "load":

@@ -4,6 +4,7 @@ needed: validation runs before any CUDA call)."""
 import ctypes as C
 import os
 
+import numpy as np
 import pytest
 
 from paper_1301_4498_gb300 import build as B
@@ -85,3 +86,73 @@ def test_null_arguments_rejected(lib):
     assert lib.nyx_hydro_status(None, None) == H.NYX_EINVAL
     assert lib.nyx_plan_destroy(None) == H.NYX_EINVAL
     assert lib.nyx_hydro_fill(None, None, 6) == H.NYX_EINVAL
+
+
+# ------------------------------------------------------------ work lists
+def _cost(it):
+    """The scheduler's duration model: columns x (planes + 3)."""
+    return ((it[:, 3] + 2) * (it[:, 4] + 2) * (it[:, 6] + 3)).astype(float)
+
+
+def _queue_finish(it, slots):
+    import heapq
+    q = [0.0] * slots
+    end = 0.0
+    for c in _cost(it):
+        t = heapq.heappop(q) + c
+        heapq.heappush(q, t)
+        end = max(end, t)
+    return end
+
+
+LEVELS = {"one128": [(128, 128, 128)], "one256": [(256, 256, 256)],
+          "mix": [(32, 32, 32)] * 8 + [(64, 64, 64)] * 2,
+          "ragged": [(40, 24, 50), (17, 9, 33), (5, 3, 1)]}
+
+
+@pytest.mark.parametrize("level", sorted(LEVELS))
+@pytest.mark.parametrize("tile", [(16, 8), (8, 8), (32, 4)])
+@pytest.mark.parametrize("slots", [7, 152, 304])
+@pytest.mark.parametrize("chunk", [False, True])
+def test_task_items_tile_every_cell_once(lib, level, tile, slots, chunk):
+    ext = LEVELS[level]
+    it = H.task_items(ext, tile[0], tile[1], slots, chunk)
+    seen = [np.zeros((n[2], n[1], n[0]), np.int32) for n in ext]
+    for b, x0, y0, nx, ny, z0, nz in it:
+        assert 1 <= nx <= tile[0] and 1 <= ny <= tile[1] and nz >= 1
+        assert x0 % tile[0] == 0 and y0 % tile[1] == 0
+        seen[b][z0:z0 + nz, y0:y0 + ny, x0:x0 + nx] += 1
+    assert all(np.all(s == 1) for s in seen)
+    c = _cost(it)
+    assert np.all(np.diff(c) <= 0)                  # queue order: largest first
+    if not chunk:
+        assert np.all(it[:, 5] == 0) and np.all(it[:, 6] == [ext[b][2] for b in it[:, 0]])
+
+
+def test_task_items_even_out_a_single_box(lib):
+    """128^3 in 16 x 8 tiles: 128 columns for 152 CTAs leave 24 idle with
+    whole columns; the chunked list finishes within 6 % of the even share
+    and 10 % before whole columns, in the duration model checked here."""
+    ext = [(128, 128, 128)]
+    whole = H.task_items(ext, 16, 8, 152, False)
+    cut = H.task_items(ext, 16, 8, 152, True)
+    lb = _cost(whole).sum() / 152
+    assert len(whole) == 128 and _queue_finish(whole, 152) == pytest.approx(131 * 180)
+    assert len(cut) > 152
+    assert _queue_finish(cut, 152) <= 1.06 * lb
+    assert _queue_finish(cut, 152) <= 0.9 * _queue_finish(whole, 152)
+
+
+def test_task_items_keep_columns_of_a_many_box_level(lib):
+    """A level with many more tiles than CTAs keeps whole columns."""
+    ext = [(32, 32, 32)] * 64 + [(64, 64, 64)] * 6
+    assert np.array_equal(H.task_items(ext, 16, 8, 152, True),
+                          H.task_items(ext, 16, 8, 152, False))
+
+
+@pytest.mark.parametrize("bad", [dict(ext=[(4, 4, 0)]), dict(slots=0), dict(tx=0)])
+def test_task_items_reject_bad_arguments(lib, bad):
+    kw = dict(ext=[(8, 8, 8)], tx=16, ty=8, slots=152)
+    kw.update(bad)
+    with pytest.raises(H.NyxError):
+        H.task_items(kw["ext"], kw["tx"], kw["ty"], kw["slots"])

@@ -363,3 +363,60 @@ def test_step_host_valid_matches_device_path():
                          dt_next)
     assert np.isfinite(host_out.numpy()).all()
     plan.close()
+
+
+def _tall_box(nsteps=2):
+    """A periodic 32 x 16 x 94 comoving box: 4 tiles of 16 x 8, far fewer
+    than CTAs, over tall columns that the work list cuts into chunks of 18
+    and 19 planes."""
+    dx = 1.0 / 94
+    lev = W.single_box_level(32, 16, 94, dx, name="tall")
+    f = W.comoving_fields((94, 16, 32), 0.5, 5, dx)
+    S, G = W._patch_state(lev, 0, f)
+    return W.Workload("tall 32x16x94", lev, [S], [G], W.a_schedule(1 / 51, 1 / 49, nsteps),
+                      5.0 / 3.0, 0.5, nsteps, False)
+
+
+def _chunk_run(w, n, shape, z_chunks, **kw):
+    plan = H.Plan(w.level, gamma=w.gamma, cfl=w.cfl, precision="mixed", z_chunks=z_chunks, **kw)
+    plan.set_tile_shape(shape)
+    lev = H.make_level(plan, w.state, w.grav)
+    a = torch.tensor(np.asarray(w.a_sched[:n + 1], dtype=np.float64), device="cuda")
+    dt = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+    plan.run(lev, a, dt, n, compute_dt0=True, use_graph=False)
+    torch.cuda.synchronize()
+    assert plan.status()[0] == H.NYX_OK
+    return plan, lev, dt.cpu().numpy()
+
+
+@pytest.mark.parametrize("shape", [3, 4, 5])
+@pytest.mark.parametrize("name", ["comoving32", "tiled64x8", "thin", "tall"])
+def test_task_form_chunks_equal_whole_columns_bitwise(oracle_results, name, shape):
+    """The task form with its columns cut into plane chunks (what the work
+    list does where tiles are fewer than CTAs) gives the whole-column result
+    bit for bit: each face flux comes from the same stencil in the same
+    order, whichever item computes it.  Also with flattening and with the
+    fluxes kept for reflux."""
+    if name == "tall":
+        w, n = _tall_box(2), 2
+    else:
+        w, _, _, n = oracle_results(name)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    tx, ty = H.tile_shape_of(shape)
+    ext = [w.level.extent(b) for b in range(w.level.nbox)]
+    slots = sms * (2 if shape == 4 else 1)
+    chunked = H.task_items(ext, tx, ty, slots, True)
+    if name != "thin":       # the 2-plane slabs stay whole; the others are cut
+        assert len(chunked) > len(H.task_items(ext, tx, ty, slots, False))
+    for kw in (dict(), dict(flattening=True, keep_fluxes=1)):
+        p1, l1, d1 = _chunk_run(w, n, shape, 1, **kw)
+        p0, l0, d0 = _chunk_run(w, n, shape, 0, **kw)
+        assert np.array_equal(d0, d1)
+        for x, y in zip(p1.from_device(l1.current, 6), p0.from_device(l0.current, 6)):
+            assert np.array_equal(W.valid(x), W.valid(y))
+        if kw:
+            for b in range(w.level.nbox):
+                for di in range(3):
+                    assert torch.equal(p1.fluxes(l1, b, di), p0.fluxes(l0, b, di)), (b, di)
+        p1.close()
+        p0.close()
