@@ -66,7 +66,7 @@ ALG_FLOPS_PER_ZONE = {"mixed": 3196 + 480 * 3.14, "fp64": 3196 + 480 * 3.83}
 # level's box sizes (ncu capture of the large128 workload, profiles/
 # k_fused2_mixed_large128.md); traffic scales with the cells of boxes of the
 # same sizes.  Reported only for that kernel, workload and shape.
-TRAFFIC_BYTES_PER_ZONE = {("large", 3): 150.9, ("large128", 3): 150.9}
+TRAFFIC_BYTES_PER_ZONE = {("large", 3): 151.2, ("large128", 3): 151.2}
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 

@@ -230,10 +230,16 @@ int nyx_hydro_step_host(nyx_plan *plan, nyx_level *level, const double *host_sta
  * (ghost cells are derived data, about 40 % of a field with 4-cell ghosts
  * on 32^3 boxes): host_in and host_out hold, box after box, the 6 components
  * of the box's n_x n_y n_z valid cells (component-major, x fastest; box b
- * starts at 6 times the number of valid cells of the boxes before it).  One
- * copy each way through a device staging buffer of the same size, made on
- * the first call (NYX_ENOMEM if it cannot be); the copies to and from the
- * level's state run on the device.  Synchronous. */
+ * starts at 6 times the number of valid cells of the boxes before it).  The
+ * copies go through a device staging buffer of the same size, made on the
+ * first call (NYX_ENOMEM if it cannot be); the scatter into and the gather
+ * from the level's state run on the device.  On a persistent plan whose
+ * level has enough work items, the boxes are cut into up to 8 groups: each
+ * group's new cells are copied out while later groups advance, and, when
+ * *dt_inout > 0 and the plan does not flatten, each group's cells are
+ * copied in while earlier groups fill and advance.  The library's own
+ * streams for this wait on the plan's stream first.  The result is the same
+ * either way.  Synchronous: every copy has ended when the call returns. */
 int nyx_hydro_step_host_valid(nyx_plan *plan, nyx_level *level, const double *host_in,
                               double *host_out, double a_old, double a_new, double *dt_inout);
 

@@ -223,6 +223,7 @@ int upload_pass(FillPass &p, const std::vector<FillRect> &rects) {
     acc += (long long)rects[i].ext[0] * rects[i].ext[1] * rects[i].ext[2];
   }
   p.total = acc;
+  p.h = rects;
   CK(cudaMalloc(&p.d_rects, sizeof(FillRect) * p.n));
   CK(cudaMalloc(&p.d_pref, sizeof(long long) * p.n));
   CK(cudaMemcpy(p.d_rects, rects.data(), sizeof(FillRect) * p.n, cudaMemcpyHostToDevice));
@@ -386,6 +387,13 @@ void free_plan(nyx_plan *P) {
   cudaFree(P->d_flux);
   cudaFree(P->d_flux_off);
   for (auto &it : P->d_items) cudaFree(it);
+  for (auto &it : P->d_items_grp) cudaFree(it);
+  for (auto &e : P->ev_grp) cudaEventDestroy(e);
+  if (P->copy_stream) cudaStreamDestroy(P->copy_stream);
+  for (auto &r : P->d_rects_grp) cudaFree(r);
+  for (auto &e : P->ev_in) cudaEventDestroy(e);
+  if (P->ev_start) cudaEventDestroy(P->ev_start);
+  if (P->h2d_stream) cudaStreamDestroy(P->h2d_stream);
   cudaFree(P->d_queue);
   delete P;
 }
@@ -457,8 +465,35 @@ int variant_bits(const nyx_plan *P) {
   return P->hK.plm | (P->hK.linear_rs << 1) | (P->hK.flat << 2);
 }
 
+int read_back_group(nyx_plan *P, const double *Sn, int g, double *host_out);
+
+FusedArgs fused_args(nyx_plan *P, const double *S, const double *G, double *Sn,
+                     unsigned long long *acc, bool predict_only) {
+  FusedArgs a;
+  a.boxes = P->d_boxes;
+  a.queue = P->d_queue;
+  a.K = P->d_K;
+  a.SC = P->d_SC;
+  a.BS = P->d_BS;
+  a.S = S;
+  a.G = G;
+  a.Sn = Sn;
+  a.dtacc = acc;
+  a.status = P->d_status;
+  a.flux_keep = P->d_flux;
+  a.flux_off = P->d_flux_off;
+  a.predict_only = predict_only ? 1 : 0;
+  a.variant = variant_bits(P);
+  a.flat = P->d_flat;
+  return a;
+}
+
+// One advance of state[cur] into state[1-cur].  With host_out (a fused plan
+// whose read-back groups are set up), the advance runs one launch per box
+// group, each followed by the group's read-back into host_out.
 int do_advance(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_new,
-               const double *dt, const double *grav, double *dt_next, bool predict_only = false) {
+               const double *dt, const double *grav, double *dt_next, bool predict_only = false,
+               double *host_out = nullptr) {
   double *S = L->state[L->cur];
   double *Sn = L->state[1 - L->cur];
   const double *G = grav ? grav : L->grav;
@@ -482,32 +517,31 @@ int do_advance(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_n
       P->launches += P->d_flux ? 29 : 26;
     }
   } else {
-    FusedArgs a;
-    a.boxes = P->d_boxes;
-    a.queue = P->d_queue;
-    a.K = P->d_K;
-    a.SC = P->d_SC;
-    a.BS = P->d_BS;
-    a.S = S;
-    a.G = G;
-    a.Sn = Sn;
-    a.dtacc = acc;
-    a.status = P->d_status;
-    a.flux_keep = P->d_flux;
-    a.flux_off = P->d_flux_off;
-    a.predict_only = predict_only ? 1 : 0;
-    a.variant = variant_bits(P);
-    a.flat = P->d_flat;
+    FusedArgs a = fused_args(P, S, G, Sn, acc, predict_only);
     if (P->prm.autotune && !P->tuned) {
       int rc = tune_shape(P, a);
       if (rc) return rc;
     }
-    a.items = P->d_items[P->shape];
-    a.nitems = P->nitems[P->shape];
-    int grid = std::min(P->max_grid[P->shape], a.nitems);
-    int e = launch_fused(P->prm.precision, P->shape, a, grid, P->stream);
-    if (e) return cuda_fail((cudaError_t)e, "fused advance launch");
-    P->launches += 1;
+    const int s = P->shape;
+    if (host_out && P->ngrp > 1) {
+      for (int g = 0; g < P->ngrp; ++g) {
+        a.items = P->d_items_grp[s] + P->grp_off[s][g];
+        a.nitems = P->grp_off[s][g + 1] - P->grp_off[s][g];
+        if (a.nitems > 0) {
+          int e = launch_fused(P->prm.precision, s, a, std::min(P->max_grid[s], a.nitems),
+                               P->stream);
+          if (e) return cuda_fail((cudaError_t)e, "fused advance launch");
+          P->launches += 1;
+        }
+        if (int rc = read_back_group(P, Sn, g, host_out)) return rc;
+      }
+    } else {
+      a.items = P->d_items[s];
+      a.nitems = P->nitems[s];
+      int e = launch_fused(P->prm.precision, s, a, std::min(P->max_grid[s], a.nitems), P->stream);
+      if (e) return cuda_fail((cudaError_t)e, "fused advance launch");
+      P->launches += 1;
+    }
   }
   }
   if (dt_next) {
@@ -518,6 +552,166 @@ int do_advance(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_n
   if (e != cudaSuccess) return cuda_fail(e, "advance launch");
   P->flux_valid = P->d_flux != nullptr;
   if (!predict_only) L->cur = 1 - L->cur;
+  return NYX_OK;
+}
+
+// Read-back groups of nyx_hydro_step_host_valid (fused plans): up to 8
+// ranges of whole boxes with about equal cells, as long as each group keeps
+// 4 waves of items or more in the plan's tile shape, so that the tail of
+// each group's launch stays short against the copy it hides.  One group (no
+// overlap) otherwise.  Every shape gets the same groups.
+int setup_readback(nyx_plan *P) {
+  const int nsh = fused_num_shapes(P->prm.precision);
+  const int waves = P->nitems[P->shape] / std::max(1, P->max_grid[P->shape]);
+  const int G = std::min(std::min(8, P->nbox), waves / 4);
+  std::vector<int> gb(1, 0);
+  for (int g = 1; g < G; ++g) {
+    const long long want = P->total_cells * g / G;
+    int b = gb.back() + 1;
+    while (b < P->nbox && P->cell_pref[b] < want) ++b;
+    if (b >= P->nbox) break;
+    gb.push_back(b);
+  }
+  gb.push_back(P->nbox);
+  const int ng = (int)gb.size() - 1;
+  if (ng < 2) {
+    P->ngrp = 1;
+    return NYX_OK;
+  }
+  for (int s = 0; s < nsh; ++s) {
+    std::vector<WorkItem> it;
+    it.reserve(P->h_items[s].size());
+    P->grp_off[s].assign(1, 0);
+    for (int g = 0; g < ng; ++g) {
+      for (const WorkItem &w : P->h_items[s])
+        if (w.box >= gb[g] && w.box < gb[g + 1]) it.push_back(w);
+      P->grp_off[s].push_back((int)it.size());
+    }
+    CK(cudaMalloc(&P->d_items_grp[s], sizeof(WorkItem) * it.size()));
+    CK(cudaMemcpy(P->d_items_grp[s], it.data(), sizeof(WorkItem) * it.size(),
+                  cudaMemcpyHostToDevice));
+  }
+  // input side: each group's fill rects, the groups they read, and an
+  // input order that brings in the groups the first advances need first
+  std::vector<int> gof(P->nbox);
+  for (int g = 0; g < ng; ++g)
+    for (int b = gb[g]; b < gb[g + 1]; ++b) gof[b] = g;
+  std::vector<unsigned> src(ng, 0u);
+  for (int p = 0; p < 4; ++p) {
+    std::vector<FillRect> r;
+    r.reserve(P->pass[p].h.size());
+    P->rect_off[p].assign(1, 0);
+    for (int g = 0; g < ng; ++g) {
+      for (const FillRect &R : P->pass[p].h) {
+        if (gof[R.dst_box] != g) continue;
+        r.push_back(R);
+        src[g] |= 1u << gof[R.src_box];
+      }
+      P->rect_off[p].push_back((int)r.size());
+    }
+    if (!r.empty()) {
+      CK(cudaMalloc(&P->d_rects_grp[p], sizeof(FillRect) * r.size()));
+      CK(cudaMemcpy(P->d_rects_grp[p], r.data(), sizeof(FillRect) * r.size(),
+                    cudaMemcpyHostToDevice));
+    }
+  }
+  std::vector<int> order;
+  std::vector<char> sent(ng, 0);
+  for (int g = 0; g < ng; ++g) {
+    const unsigned need = src[g] | (1u << g);
+    for (int q = 0; q < ng; ++q)
+      if (((need >> q) & 1u) && !sent[q]) {
+        sent[q] = 1;
+        order.push_back(q);
+      }
+  }
+  CK(cudaStreamCreateWithFlags(&P->copy_stream, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&P->h2d_stream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&P->ev_start, cudaEventDisableTiming));
+  P->ev_grp.assign(ng, nullptr);
+  for (auto &e : P->ev_grp) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  P->ev_in.assign(ng, nullptr);
+  for (auto &e : P->ev_in) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  P->grp_src = src;
+  P->in_order = order;
+  P->grp_box = gb;
+  P->ngrp = ng;
+  return NYX_OK;
+}
+
+// nyx_hydro_step_host_valid with its input, advance and read-back overlapped
+// per box group: the groups' valid cells are copied in and scattered on the
+// input stream in in_order; group g's ghost fill and advance wait only for
+// the groups the fill reads; its new cells go back while later groups
+// advance.  Needs the step scalars in d_scal[0..2] (dt given).
+int step_pipelined(nyx_plan *P, nyx_level *L, const double *host_in, double *host_out) {
+  double *S = L->state[L->cur];
+  double *Sn = L->state[1 - L->cur];
+  CK(cudaEventRecord(P->ev_start, P->stream));
+  CK(cudaStreamWaitEvent(P->h2d_stream, P->ev_start, 0));
+  for (int q : P->in_order) {
+    const int b0 = P->grp_box[q], b1 = P->grp_box[q + 1];
+    const long long c0 = P->cell_pref[b0], c1 = b1 < P->nbox ? P->cell_pref[b1] : P->total_cells;
+    const int k0 = P->plane_pref[b0], k1 = b1 < P->nbox ? P->plane_pref[b1] : P->plane_blocks;
+    CK(cudaMemcpyAsync(P->d_packed + NCONS * c0, host_in + NCONS * c0,
+                       sizeof(double) * NCONS * (size_t)(c1 - c0), cudaMemcpyHostToDevice,
+                       P->h2d_stream));
+    launch_valid_copy(S, P->d_packed, P->d_boxes, P->d_cell_pref, P->d_plane_pref, P->nbox,
+                      k1 - k0, k0, 1, P->h2d_stream);
+    P->launches += 1;
+    CK(cudaEventRecord(P->ev_in[q], P->h2d_stream));
+  }
+  launch_step_setup(P->d_K, P->d_scal, P->d_scal + 1, P->d_scal + 2, P->d_SC, P->d_boxes, P->nbox,
+                    P->d_BS, P->stream);
+  P->launches += 1;
+  FusedArgs a = fused_args(P, S, L->grav, Sn, P->d_dtacc, false);
+  const int s = P->shape;
+  unsigned waited = 0;
+  for (int g = 0; g < P->ngrp; ++g) {
+    const unsigned need = (P->grp_src[g] | (1u << g)) & ~waited;
+    for (int q = 0; q < P->ngrp; ++q)
+      if ((need >> q) & 1u) CK(cudaStreamWaitEvent(P->stream, P->ev_in[q], 0));
+    waited |= need;
+    for (int p = 0; p < 4; ++p) {
+      const int r0 = P->rect_off[p][g], nr = P->rect_off[p][g + 1] - r0;
+      if (nr > 0) {
+        launch_fill(S, NCONS, P->d_boxes, P->d_rects_grp[p] + r0, nullptr, nr, P->pass[p].total,
+                    P->stream);
+        P->launches += 1;
+      }
+    }
+    a.items = P->d_items_grp[s] + P->grp_off[s][g];
+    a.nitems = P->grp_off[s][g + 1] - P->grp_off[s][g];
+    if (a.nitems > 0) {
+      int e = launch_fused(P->prm.precision, s, a, std::min(P->max_grid[s], a.nitems), P->stream);
+      if (e) return cuda_fail((cudaError_t)e, "fused advance launch");
+      P->launches += 1;
+    }
+    if (int rc = read_back_group(P, Sn, g, host_out)) return rc;
+  }
+  launch_dt_finalize(P->d_K, P->d_dtacc, P->d_scal + 3, P->stream);
+  P->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "pipelined step launch");
+  P->flux_valid = P->d_flux != nullptr;
+  L->cur = 1 - L->cur;
+  return NYX_OK;
+}
+
+// The new valid cells of group g's boxes: gathered into the packed buffer
+// on the plan's stream, then copied to host_out on the copy stream.
+int read_back_group(nyx_plan *P, const double *Sn, int g, double *host_out) {
+  const int b0 = P->grp_box[g], b1 = P->grp_box[g + 1];
+  const int k0 = P->plane_pref[b0], k1 = b1 < P->nbox ? P->plane_pref[b1] : P->plane_blocks;
+  launch_valid_copy(const_cast<double *>(Sn), P->d_packed, P->d_boxes, P->d_cell_pref,
+                    P->d_plane_pref, P->nbox, k1 - k0, k0, 0, P->stream);
+  P->launches += 1;
+  const long long c0 = P->cell_pref[b0], c1 = b1 < P->nbox ? P->cell_pref[b1] : P->total_cells;
+  CK(cudaEventRecord(P->ev_grp[g], P->stream));
+  CK(cudaStreamWaitEvent(P->copy_stream, P->ev_grp[g], 0));
+  CK(cudaMemcpyAsync(host_out + NCONS * c0, P->d_packed + NCONS * c0,
+                     sizeof(double) * NCONS * (size_t)(c1 - c0), cudaMemcpyDeviceToHost,
+                     P->copy_stream));
   return NYX_OK;
 }
 
@@ -888,6 +1082,7 @@ int nyx_hydro_plan(const nyx_level_desc *lev, const nyx_hydro_params *prm, void 
         TRYC(cudaMalloc(&P->d_items[s], sizeof(WorkItem) * it.size()));
         TRYC(cudaMemcpy(P->d_items[s], it.data(), sizeof(WorkItem) * it.size(),
                         cudaMemcpyHostToDevice));
+        P->h_items[s] = std::move(it);
       }
       TRYC(cudaMalloc(&P->d_queue, sizeof(int)));
       TRYC(cudaMemset(P->d_queue, 0, sizeof(int)));
@@ -1089,19 +1284,51 @@ int nyx_hydro_step_host_valid(nyx_plan *P, nyx_level *L, const double *host_in, 
                                             : cuda_fail(e, "packed state set-up");
     }
     P->plane_blocks = (int)nb;
+    P->plane_pref = pp;
   }
+  if (P->prm.batching != NYX_PER_BOX && P->ngrp == 0)
+    if (int rc = setup_readback(P)) return rc;
   const size_t bytes = sizeof(double) * NCONS * (size_t)P->total_cells;
   double h[3] = {a_old, a_new, *dt_inout};
-  CK(cudaMemcpyAsync(P->d_packed, host_in, bytes, cudaMemcpyHostToDevice, P->stream));
   CK(cudaMemcpyAsync(P->d_scal, h, 3 * sizeof(double), cudaMemcpyHostToDevice, P->stream));
+  if (P->ngrp > 1 && *dt_inout > 0.0 && !P->d_flat && !(P->prm.autotune && !P->tuned)) {
+    // input, advance and read-back overlapped per box group
+    int rc = step_pipelined(P, L, host_in, host_out);
+    if (rc) {
+      cudaStreamSynchronize(P->h2d_stream);
+      cudaStreamSynchronize(P->copy_stream);
+      return rc;
+    }
+    CK(cudaMemcpyAsync(dt_inout, P->d_scal + 3, sizeof(double), cudaMemcpyDeviceToHost,
+                       P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    CK(cudaStreamSynchronize(P->h2d_stream));
+    CK(cudaStreamSynchronize(P->copy_stream));
+    return NYX_OK;
+  }
+  CK(cudaMemcpyAsync(P->d_packed, host_in, bytes, cudaMemcpyHostToDevice, P->stream));
   launch_valid_copy(L->state[L->cur], P->d_packed, P->d_boxes, P->d_cell_pref, P->d_plane_pref,
-                    P->nbox, P->plane_blocks, 1, P->stream);
+                    P->nbox, P->plane_blocks, 0, 1, P->stream);
   P->launches += 1;
   if (!(*dt_inout > 0.0)) do_estdt(P, L->state[L->cur], P->d_scal, P->d_scal + 2);
+  if (P->ngrp > 1) {
+    // the read-back of each box group overlaps the advance of the next ones
+    int rc = do_advance(P, L, P->d_scal, P->d_scal + 1, P->d_scal + 2, nullptr, P->d_scal + 3,
+                        false, host_out);
+    if (rc) {
+      cudaStreamSynchronize(P->copy_stream);
+      return rc;
+    }
+    CK(cudaMemcpyAsync(dt_inout, P->d_scal + 3, sizeof(double), cudaMemcpyDeviceToHost,
+                       P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    CK(cudaStreamSynchronize(P->copy_stream));
+    return NYX_OK;
+  }
   int rc = do_advance(P, L, P->d_scal, P->d_scal + 1, P->d_scal + 2, nullptr, P->d_scal + 3);
   if (rc) return rc;
   launch_valid_copy(L->state[L->cur], P->d_packed, P->d_boxes, P->d_cell_pref, P->d_plane_pref,
-                    P->nbox, P->plane_blocks, 0, P->stream);
+                    P->nbox, P->plane_blocks, 0, 0, P->stream);
   P->launches += 1;
   CK(cudaMemcpyAsync(host_out, P->d_packed, bytes, cudaMemcpyDeviceToHost, P->stream));
   CK(cudaMemcpyAsync(dt_inout, P->d_scal + 3, sizeof(double), cudaMemcpyDeviceToHost, P->stream));

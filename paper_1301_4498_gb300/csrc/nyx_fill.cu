@@ -53,8 +53,8 @@ __global__ void k_fill_rects(double *field, int ncomp, const BoxDev *boxes, cons
 // b); consecutive threads take consecutive x cells on both sides.
 __global__ void k_valid_copy(double *field, double *packed, const BoxDev *boxes,
                              const long long *cell_pref, const int *plane_pref, int nbox,
-                             int to_field) {
-  const int blk = blockIdx.x;
+                             int blk0, int to_field) {
+  const int blk = blk0 + (int)blockIdx.x;
   int lo = 0, hi = nbox - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -84,9 +84,9 @@ __global__ void k_valid_copy(double *field, double *packed, const BoxDev *boxes,
 
 void launch_valid_copy(double *field, double *packed, const BoxDev *boxes,
                        const long long *cell_pref, const int *plane_pref, int nbox, int nblocks,
-                       int to_field, cudaStream_t st) {
+                       int blk0, int to_field, cudaStream_t st) {
   if (nblocks < 1) return;
-  k_valid_copy<<<nblocks, 256, 0, st>>>(field, packed, boxes, cell_pref, plane_pref, nbox,
+  k_valid_copy<<<nblocks, 256, 0, st>>>(field, packed, boxes, cell_pref, plane_pref, nbox, blk0,
                                        to_field);
 }
 

@@ -11,10 +11,11 @@ void record_error(const char *msg);
 
 // Valid cells of a level field (6 components) to or from their packed form
 // (box b at 6 cell_pref[b], component-major, x fastest); one block per plane
-// of each box, plane_pref[b] the first block of box b, nblocks the total.
+// of each box, plane_pref[b] the first block of box b.  Copies the nblocks
+// box planes from block blk0 on (a range of whole boxes, or all of them).
 void launch_valid_copy(double *field, double *packed, const BoxDev *boxes,
                        const long long *cell_pref, const int *plane_pref, int nbox, int nblocks,
-                       int to_field, cudaStream_t st);
+                       int blk0, int to_field, cudaStream_t st);
 void launch_fill(double *field, int ncomp, const BoxDev *boxes, const FillRect *rects,
                  const long long *rect_pref, int nrect, long long total, cudaStream_t st);
 

@@ -20,6 +20,7 @@ struct FillPass {
   long long *d_pref = nullptr;
   int n = 0;
   long long total = 0;
+  std::vector<FillRect> h;  // host copy (regrouped for the pipelined host step)
 };
 
 using GraphKey = std::tuple<const void *, const void *, const void *, int, const void *, const void *,
@@ -69,7 +70,30 @@ struct nyx_plan {
   // first use: 6 doubles per valid cell, one copy block per box plane
   double *d_packed = nullptr;
   int *d_plane_pref = nullptr;
+  std::vector<int> plane_pref;
   int plane_blocks = 0;
+  // ... and its read-back overlapped with the advance: the fused form's
+  // items regrouped by box ranges [grp_box[g], grp_box[g+1]) (each group in
+  // queue order), one launch per group; a group's cells are gathered and
+  // copied to the host on copy_stream while the next group advances
+  int ngrp = 0;
+  std::vector<int> grp_box;
+  std::vector<int> grp_off[8];  // per shape: first item of each group, ngrp + 1 entries
+  nyx::WorkItem *d_items_grp[8] = {nullptr};
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> ev_grp;
+  // ... and its input overlapped too: each group's cells copied in and
+  // scattered on h2d_stream (in in_order), each group's ghost fill (the
+  // rects of pass p whose destination is in group g: d_rects_grp[p] from
+  // rect_off[p][g]) launched once the groups it reads (grp_src[g], a bit
+  // mask) are in
+  cudaStream_t h2d_stream = nullptr;
+  std::vector<cudaEvent_t> ev_in;
+  cudaEvent_t ev_start = nullptr;
+  nyx::FillRect *d_rects_grp[4] = {nullptr};
+  std::vector<int> rect_off[4];
+  std::vector<unsigned> grp_src;
+  std::vector<int> in_order;
   // per-box FP64 form
   double *d_scratch = nullptr;
   long long Vmax = 0;
@@ -80,6 +104,7 @@ struct nyx_plan {
   bool flux_valid = false;
   // fused persistent form
   nyx::WorkItem *d_items[8] = {nullptr};
+  std::vector<nyx::WorkItem> h_items[8];
   int nitems[8] = {0};
   int *d_queue = nullptr;
   int shape = 0;

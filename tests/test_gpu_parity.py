@@ -365,6 +365,54 @@ def test_step_host_valid_matches_device_path():
     plan.close()
 
 
+@pytest.mark.parametrize("shape", [3, 5])
+def test_step_host_valid_overlapped_read_back_matches_device_path(shape):
+    """A level of 1000 boxes of 16^3 (13 or more waves of work items): the
+    advance of nyx_hydro_step_host_valid runs one launch per group of boxes,
+    and each group's new cells are copied to the host while the next groups
+    advance.  The result and the next dt are the device path's, bit for bit;
+    the plan's launch counter shows the groups (one advance launch and one
+    gather per group, against one of each).  With dt given, the groups'
+    input copies overlap the fills and advances of earlier groups as well,
+    for the same result."""
+    w = W.tiled_box(n=160, box=16, nsteps=1)
+    plan = H.Plan(w.level, gamma=w.gamma, cfl=w.cfl, precision="mixed")
+    plan.set_tile_shape(shape)
+    lev = H.make_level(plan, w.state, w.grav)
+    host_in = torch.from_numpy(plan.pack_valid(w.state)).pin_memory()
+    host_out = torch.full_like(host_in, float("nan")).pin_memory()
+    plan.counters(reset=True)
+    dt_next = plan.step_host_valid(lev, host_in, host_out, float(w.a_sched[0]),
+                                   float(w.a_sched[1]))
+    n_host = plan.counters(reset=True)["launches"]
+    got = plan.unpack_valid(host_out.numpy())
+    ref = H.Plan(w.level, gamma=w.gamma, cfl=w.cfl, precision="mixed")
+    ref.set_tile_shape(shape)
+    rlev = H.make_level(ref, w.state, w.grav)
+    a = torch.tensor(np.asarray(w.a_sched[:2], dtype=np.float64), device="cuda")
+    dt = torch.zeros(2, dtype=torch.float64, device="cuda")
+    ref.counters(reset=True)
+    ref.run(rlev, a, dt, 1, compute_dt0=True, use_graph=False)
+    torch.cuda.synchronize()
+    n_dev = ref.counters(reset=True)["launches"]
+    assert ref.status()[0] == H.NYX_OK and plan.status()[0] == H.NYX_OK
+    for x, y in zip(got, ref.from_device(rlev.current, 6)):
+        assert np.array_equal(x, W.valid(y))
+    assert dt_next == dt.cpu().numpy()[1]
+    groups = (n_host - n_dev) // 2          # scatter + G gathers + G advances vs 1 advance
+    assert n_host - n_dev == 2 * groups and groups >= 2, (n_host, n_dev)
+    # with dt given, the input is pipelined too: each group's cells are
+    # copied in and scattered while earlier groups fill and advance
+    out2 = torch.full_like(host_in, float("nan")).pin_memory()
+    dt0 = float(dt.cpu().numpy()[0])
+    dt_next2 = plan.step_host_valid(lev, host_in, out2, float(w.a_sched[0]),
+                                    float(w.a_sched[1]), dt0)
+    assert plan.status()[0] == H.NYX_OK
+    assert torch.equal(out2, host_out) and dt_next2 == dt_next
+    plan.close()
+    ref.close()
+
+
 def _tall_box(nsteps=2):
     """A periodic 32 x 16 x 94 comoving box: 4 tiles of 16 x 8, far fewer
     than CTAs, over tall columns that the work list cuts into chunks of 18
