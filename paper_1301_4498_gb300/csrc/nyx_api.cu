@@ -394,6 +394,10 @@ void free_plan(nyx_plan *P) {
   for (auto &e : P->ev_in) cudaEventDestroy(e);
   if (P->ev_start) cudaEventDestroy(P->ev_start);
   if (P->h2d_stream) cudaStreamDestroy(P->h2d_stream);
+  if (P->ev_setup) cudaEventDestroy(P->ev_setup);
+  if (P->ev_side) cudaEventDestroy(P->ev_side);
+  if (P->stream2) cudaStreamDestroy(P->stream2);
+  cudaFree(P->d_queue_grp);
   cudaFree(P->d_queue);
   delete P;
 }
@@ -465,7 +469,7 @@ int variant_bits(const nyx_plan *P) {
   return P->hK.plm | (P->hK.linear_rs << 1) | (P->hK.flat << 2);
 }
 
-int read_back_group(nyx_plan *P, const double *Sn, int g, double *host_out);
+int read_back_group(nyx_plan *P, const double *Sn, int g, double *host_out, cudaStream_t st);
 
 FusedArgs fused_args(nyx_plan *P, const double *S, const double *G, double *Sn,
                      unsigned long long *acc, bool predict_only) {
@@ -533,7 +537,7 @@ int do_advance(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_n
           if (e) return cuda_fail((cudaError_t)e, "fused advance launch");
           P->launches += 1;
         }
-        if (int rc = read_back_group(P, Sn, g, host_out)) return rc;
+        if (int rc = read_back_group(P, Sn, g, host_out, P->stream)) return rc;
       }
     } else {
       a.items = P->d_items[s];
@@ -555,15 +559,14 @@ int do_advance(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_n
   return NYX_OK;
 }
 
-// Read-back groups of nyx_hydro_step_host_valid (fused plans): up to 8
+// Read-back groups of nyx_hydro_step_host_valid (fused plans): up to 16
 // ranges of whole boxes with about equal cells, as long as each group keeps
-// 4 waves of items or more in the plan's tile shape, so that the tail of
-// each group's launch stays short against the copy it hides.  One group (no
+// 4 waves of items or more in the plan's tile shape.  One group (no
 // overlap) otherwise.  Every shape gets the same groups.
 int setup_readback(nyx_plan *P) {
   const int nsh = fused_num_shapes(P->prm.precision);
   const int waves = P->nitems[P->shape] / std::max(1, P->max_grid[P->shape]);
-  const int G = std::min(std::min(8, P->nbox), waves / 4);
+  const int G = std::min(std::min(16, P->nbox), waves / 4);
   std::vector<int> gb(1, 0);
   for (int g = 1; g < G; ++g) {
     const long long want = P->total_cells * g / G;
@@ -627,7 +630,11 @@ int setup_readback(nyx_plan *P) {
   }
   CK(cudaStreamCreateWithFlags(&P->copy_stream, cudaStreamNonBlocking));
   CK(cudaStreamCreateWithFlags(&P->h2d_stream, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&P->stream2, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&P->ev_start, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&P->ev_setup, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&P->ev_side, cudaEventDisableTiming));
+  CK(cudaMalloc(&P->d_queue_grp, sizeof(int) * ng));
   P->ev_grp.assign(ng, nullptr);
   for (auto &e : P->ev_grp) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   P->ev_in.assign(ng, nullptr);
@@ -641,9 +648,10 @@ int setup_readback(nyx_plan *P) {
 
 // nyx_hydro_step_host_valid with its input, advance and read-back overlapped
 // per box group: the groups' valid cells are copied in and scattered on the
-// input stream in in_order; group g's ghost fill and advance wait only for
-// the groups the fill reads; its new cells go back while later groups
-// advance.  Needs the step scalars in d_scal[0..2] (dt given).
+// input stream in in_order; group g's ghost fill and advance, on the plan's
+// stream or stream2 in turn, wait only for the groups the fill reads; its
+// new cells go back while later groups advance.  Needs the step scalars in
+// d_scal[0..2] (dt given).
 int step_pipelined(nyx_plan *P, nyx_level *L, const double *host_in, double *host_out) {
   double *S = L->state[L->cur];
   double *Sn = L->state[1 - L->cur];
@@ -664,31 +672,38 @@ int step_pipelined(nyx_plan *P, nyx_level *L, const double *host_in, double *hos
   launch_step_setup(P->d_K, P->d_scal, P->d_scal + 1, P->d_scal + 2, P->d_SC, P->d_boxes, P->nbox,
                     P->d_BS, P->stream);
   P->launches += 1;
+  CK(cudaEventRecord(P->ev_setup, P->stream));
+  CK(cudaStreamWaitEvent(P->stream2, P->ev_setup, 0));
   FusedArgs a = fused_args(P, S, L->grav, Sn, P->d_dtacc, false);
   const int s = P->shape;
-  unsigned waited = 0;
+  const cudaStream_t cs[2] = {P->stream, P->stream2};
+  unsigned waited[2] = {0u, 0u};
   for (int g = 0; g < P->ngrp; ++g) {
-    const unsigned need = (P->grp_src[g] | (1u << g)) & ~waited;
+    const cudaStream_t st = cs[g & 1];
+    const unsigned need = (P->grp_src[g] | (1u << g)) & ~waited[g & 1];
     for (int q = 0; q < P->ngrp; ++q)
-      if ((need >> q) & 1u) CK(cudaStreamWaitEvent(P->stream, P->ev_in[q], 0));
-    waited |= need;
+      if ((need >> q) & 1u) CK(cudaStreamWaitEvent(st, P->ev_in[q], 0));
+    waited[g & 1] |= need;
     for (int p = 0; p < 4; ++p) {
       const int r0 = P->rect_off[p][g], nr = P->rect_off[p][g + 1] - r0;
       if (nr > 0) {
         launch_fill(S, NCONS, P->d_boxes, P->d_rects_grp[p] + r0, nullptr, nr, P->pass[p].total,
-                    P->stream);
+                    st);
         P->launches += 1;
       }
     }
     a.items = P->d_items_grp[s] + P->grp_off[s][g];
     a.nitems = P->grp_off[s][g + 1] - P->grp_off[s][g];
+    a.queue = P->d_queue_grp + g;
     if (a.nitems > 0) {
-      int e = launch_fused(P->prm.precision, s, a, std::min(P->max_grid[s], a.nitems), P->stream);
+      int e = launch_fused(P->prm.precision, s, a, std::min(P->max_grid[s], a.nitems), st);
       if (e) return cuda_fail((cudaError_t)e, "fused advance launch");
       P->launches += 1;
     }
-    if (int rc = read_back_group(P, Sn, g, host_out)) return rc;
+    if (int rc = read_back_group(P, Sn, g, host_out, st)) return rc;
   }
+  CK(cudaEventRecord(P->ev_side, P->stream2));
+  CK(cudaStreamWaitEvent(P->stream, P->ev_side, 0));
   launch_dt_finalize(P->d_K, P->d_dtacc, P->d_scal + 3, P->stream);
   P->launches += 1;
   cudaError_t e = cudaGetLastError();
@@ -699,15 +714,16 @@ int step_pipelined(nyx_plan *P, nyx_level *L, const double *host_in, double *hos
 }
 
 // The new valid cells of group g's boxes: gathered into the packed buffer
-// on the plan's stream, then copied to host_out on the copy stream.
-int read_back_group(nyx_plan *P, const double *Sn, int g, double *host_out) {
+// on stream st (where the group advanced), then copied to host_out on the
+// copy stream.
+int read_back_group(nyx_plan *P, const double *Sn, int g, double *host_out, cudaStream_t st) {
   const int b0 = P->grp_box[g], b1 = P->grp_box[g + 1];
   const int k0 = P->plane_pref[b0], k1 = b1 < P->nbox ? P->plane_pref[b1] : P->plane_blocks;
   launch_valid_copy(const_cast<double *>(Sn), P->d_packed, P->d_boxes, P->d_cell_pref,
-                    P->d_plane_pref, P->nbox, k1 - k0, k0, 0, P->stream);
+                    P->d_plane_pref, P->nbox, k1 - k0, k0, 0, st);
   P->launches += 1;
   const long long c0 = P->cell_pref[b0], c1 = b1 < P->nbox ? P->cell_pref[b1] : P->total_cells;
-  CK(cudaEventRecord(P->ev_grp[g], P->stream));
+  CK(cudaEventRecord(P->ev_grp[g], st));
   CK(cudaStreamWaitEvent(P->copy_stream, P->ev_grp[g], 0));
   CK(cudaMemcpyAsync(host_out + NCONS * c0, P->d_packed + NCONS * c0,
                      sizeof(double) * NCONS * (size_t)(c1 - c0), cudaMemcpyDeviceToHost,
@@ -1296,6 +1312,7 @@ int nyx_hydro_step_host_valid(nyx_plan *P, nyx_level *L, const double *host_in, 
     int rc = step_pipelined(P, L, host_in, host_out);
     if (rc) {
       cudaStreamSynchronize(P->h2d_stream);
+      cudaStreamSynchronize(P->stream2);
       cudaStreamSynchronize(P->copy_stream);
       return rc;
     }
@@ -1303,6 +1320,7 @@ int nyx_hydro_step_host_valid(nyx_plan *P, nyx_level *L, const double *host_in, 
                        P->stream));
     CK(cudaStreamSynchronize(P->stream));
     CK(cudaStreamSynchronize(P->h2d_stream));
+    CK(cudaStreamSynchronize(P->stream2));
     CK(cudaStreamSynchronize(P->copy_stream));
     return NYX_OK;
   }

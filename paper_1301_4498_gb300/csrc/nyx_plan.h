@@ -90,6 +90,12 @@ struct nyx_plan {
   cudaStream_t h2d_stream = nullptr;
   std::vector<cudaEvent_t> ev_in;
   cudaEvent_t ev_start = nullptr;
+  // groups advance on the plan's stream and stream2 in turn (a group's
+  // launch takes the SMs its predecessor's tail frees), each with its own
+  // work-queue counter
+  cudaStream_t stream2 = nullptr;
+  cudaEvent_t ev_setup = nullptr, ev_side = nullptr;
+  int *d_queue_grp = nullptr;
   nyx::FillRect *d_rects_grp[4] = {nullptr};
   std::vector<int> rect_off[4];
   std::vector<unsigned> grp_src;
