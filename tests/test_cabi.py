@@ -156,3 +156,19 @@ def test_task_items_reject_bad_arguments(lib, bad):
     kw.update(bad)
     with pytest.raises(H.NyxError):
         H.task_items(kw["ext"], kw["tx"], kw["ty"], kw["slots"])
+
+
+def test_task_items_count_query_and_short_buffer(lib):
+    """cap = 0 only counts; a short buffer gets the first cap items of the
+    same list and the full count."""
+    ext = [(40, 24, 50), (17, 9, 33)]
+    n = (C.c_int * 6)(*[v for e in ext for v in e])
+    count = C.c_int()
+    assert lib.nyx_task_items(2, n, 16, 8, 152, 1, None, 0, C.byref(count)) == H.NYX_OK
+    full = H.task_items(ext, 16, 8, 152, True)
+    assert count.value == len(full) > 5
+    buf = (C.c_int * (7 * 6))(*([-7] * 42))
+    assert lib.nyx_task_items(2, n, 16, 8, 152, 1, buf, 5, C.byref(count)) == H.NYX_OK
+    assert count.value == len(full)
+    got = np.array(buf[:], dtype=np.int64).reshape(6, 7)
+    assert np.array_equal(got[:5], full[:5]) and np.all(got[5] == -7)
