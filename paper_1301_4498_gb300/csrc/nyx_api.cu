@@ -577,10 +577,11 @@ int setup_readback(nyx_plan *P) {
   }
   gb.push_back(P->nbox);
   const int ng = (int)gb.size() - 1;
-  if (ng < 2) {
-    P->ngrp = 1;
-    return NYX_OK;
-  }
+  // one group until every buffer below is in place: a set-up that fails
+  // part way leaves the plan on the ungrouped path (free_plan releases what
+  // was made)
+  P->ngrp = 1;
+  if (ng < 2) return NYX_OK;
   for (int s = 0; s < nsh; ++s) {
     std::vector<WorkItem> it;
     it.reserve(P->h_items[s].size());
