@@ -66,6 +66,7 @@ ALG_FLOPS_PER_ZONE = {"mixed": 3196 + 480 * 3.14, "fp64": 3196 + 480 * 3.83}
 # level's box sizes (ncu capture of the large128 workload, profiles/
 # k_fused2_mixed_large128.md); traffic scales with the cells of boxes of the
 # same sizes.  Reported only for that kernel, workload and shape.
+NOMINAL_HBM_GBS = 7900.0   # HBM3e nominal rate of the part, beside the measured copy rate
 TRAFFIC_BYTES_PER_ZONE = {("large", 3): 151.2, ("large128", 3): 151.2}
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
@@ -568,7 +569,9 @@ def run_ours(args, w):
             "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"],
                              "unit": "GB/s", "frac": achieved_gbs / peaks["hbm_gbs"],
                              "alg_bytes_per_zone": ALG_BYTES_PER_ZONE,
-                             "peak_source": f"hbm_gbs {peak_src}"},
+                             "peak_source": f"hbm_gbs {peak_src}",
+                             "nominal_peak": NOMINAL_HBM_GBS,
+                             "frac_of_nominal": achieved_gbs / NOMINAL_HBM_GBS},
             "kernel_ms": {"advance": adv_ms, "ghost_fill": fill_ms},
             "variants": variants,
             "fp64_comparison": side,
@@ -845,7 +848,9 @@ def run_amr(args, aw):
             "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"],
                              "unit": "GB/s", "frac": achieved_gbs / peaks["hbm_gbs"],
                              "alg_bytes_per_zone": ALG_BYTES_PER_ZONE,
-                             "peak_source": f"hbm_gbs {peak_src}"},
+                             "peak_source": f"hbm_gbs {peak_src}",
+                             "nominal_peak": NOMINAL_HBM_GBS,
+                             "frac_of_nominal": achieved_gbs / NOMINAL_HBM_GBS},
             "kernel_ms": {"advance_coarse": adv_c, "advance_fine": adv_f,
                           "ghost_fill_coarse": pc["fill_ms"] / max(1, pc["timed_fills"]),
                           "ghost_fill_fine": pf["fill_ms"] / max(1, pf["timed_fills"])},
