@@ -236,8 +236,8 @@ int nyx_hydro_step_host(nyx_plan *plan, nyx_level *level, const double *host_sta
  * from the level's state run on the device.  On a persistent plan whose
  * level has enough work items, the boxes are cut into up to 16 groups: each
  * group's new cells are copied out while later groups advance, and, when
- * *dt_inout > 0 and the plan does not flatten, each group's cells are
- * copied in while earlier groups fill and advance.  The library's own
+ * *dt_inout > 0, each group's cells are copied in while earlier groups
+ * fill, flatten (flattening plans) and advance.  The library's own
  * streams for this wait on the plan's stream first.  The result is the same
  * either way.  Synchronous: every copy has ended when the call returns. */
 int nyx_hydro_step_host_valid(nyx_plan *plan, nyx_level *level, const double *host_in,

@@ -693,6 +693,16 @@ int step_pipelined(nyx_plan *P, nyx_level *L, const double *host_in, double *hos
         P->launches += 1;
       }
     }
+    if (P->d_flat) {
+      // the group's flattening coefficients read only its own boxes, ghosts included
+      const int t0 = P->flat_tile_pref[P->grp_box[g]], t1 = P->flat_tile_pref[P->grp_box[g + 1]];
+      if (t1 > t0) {
+        int e = launch_flatten(P->prm.precision, P->d_boxes, P->d_flat_tiles + t0, t1 - t0, S,
+                               P->d_K, P->d_flat, st);
+        if (e) return cuda_fail((cudaError_t)e, "flattening launch");
+        P->launches += 1;
+      }
+    }
     a.items = P->d_items_grp[s] + P->grp_off[s][g];
     a.nitems = P->grp_off[s][g + 1] - P->grp_off[s][g];
     a.queue = P->d_queue_grp + g;
@@ -1059,6 +1069,7 @@ int nyx_hydro_plan(const nyx_level_desc *lev, const nyx_hydro_params *prm, void 
       TRYC(cudaMalloc(&P->d_flat, esz * (size_t)P->total_stride));
       // the [-1, n]^2 columns of each box in near-equal tiles of <= 34 x 17
       std::vector<FlatTile> ft;
+      P->flat_tile_pref.assign(1, 0);
       for (int b = 0; b < P->nbox; ++b) {
         const int L0 = P->hbox[b].n[0] + 2, L1 = P->hbox[b].n[1] + 2;
         const int tx = (L0 + 33) / 34, ty = (L1 + 16) / 17;
@@ -1072,6 +1083,7 @@ int nyx_hydro_plan(const nyx_level_desc *lev, const nyx_hydro_params *prm, void 
             T.ny = -1 + (int)((long long)L1 * (v + 1) / ty) - T.y0;
             ft.push_back(T);
           }
+        P->flat_tile_pref.push_back((int)ft.size());
       }
       P->flat_ntiles = (int)ft.size();
       TRYC(cudaMalloc(&P->d_flat_tiles, sizeof(FlatTile) * ft.size()));
@@ -1308,7 +1320,7 @@ int nyx_hydro_step_host_valid(nyx_plan *P, nyx_level *L, const double *host_in, 
   const size_t bytes = sizeof(double) * NCONS * (size_t)P->total_cells;
   double h[3] = {a_old, a_new, *dt_inout};
   CK(cudaMemcpyAsync(P->d_scal, h, 3 * sizeof(double), cudaMemcpyHostToDevice, P->stream));
-  if (P->ngrp > 1 && *dt_inout > 0.0 && !P->d_flat && !(P->prm.autotune && !P->tuned)) {
+  if (P->ngrp > 1 && *dt_inout > 0.0 && !(P->prm.autotune && !P->tuned)) {
     // input, advance and read-back overlapped per box group
     int rc = step_pipelined(P, L, host_in, host_out);
     if (rc) {

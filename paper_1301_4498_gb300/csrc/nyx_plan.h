@@ -66,6 +66,7 @@ struct nyx_plan {
   void *d_flat = nullptr;
   nyx::FlatTile *d_flat_tiles = nullptr;
   int flat_ntiles = 0;
+  std::vector<int> flat_tile_pref;  // first tile of each box (tiles come box by box), nbox + 1
   // packed valid cells of a state (nyx_hydro_step_host_valid), made on
   // first use: 6 doubles per valid cell, one copy block per box plane
   double *d_packed = nullptr;

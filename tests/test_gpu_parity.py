@@ -413,6 +413,38 @@ def test_step_host_valid_overlapped_read_back_matches_device_path(shape):
     ref.close()
 
 
+def test_step_host_valid_overlapped_with_flattening_matches_device_path():
+    """The overlapped host step of a flattening plan (each group's
+    coefficient pass after its own fill) equals the device path bit for bit,
+    with dt given and with dt computed."""
+    w = W.tiled_box(n=160, box=16, sigma=0.6, seed=3, nsteps=1)
+    kw = dict(gamma=w.gamma, cfl=w.cfl, precision="mixed", flattening=True)
+    ref = H.Plan(w.level, **kw)
+    ref.set_tile_shape(3)
+    rlev = H.make_level(ref, w.state, w.grav)
+    a = torch.tensor(np.asarray(w.a_sched[:2], dtype=np.float64), device="cuda")
+    dt = torch.zeros(2, dtype=torch.float64, device="cuda")
+    ref.run(rlev, a, dt, 1, compute_dt0=True, use_graph=False)
+    torch.cuda.synchronize()
+    assert ref.status()[0] == H.NYX_OK
+    want = [W.valid(x) for x in ref.from_device(rlev.current, 6)]
+    d = dt.cpu().numpy()
+    plan = H.Plan(w.level, **kw)
+    plan.set_tile_shape(3)
+    lev = H.make_level(plan, w.state, w.grav)
+    host_in = torch.from_numpy(plan.pack_valid(w.state)).pin_memory()
+    for dt_in in (0.0, float(d[0])):
+        out = torch.full_like(host_in, float("nan")).pin_memory()
+        dt_next = plan.step_host_valid(lev, host_in, out, float(w.a_sched[0]),
+                                       float(w.a_sched[1]), dt_in)
+        assert plan.status()[0] == H.NYX_OK
+        for x, y in zip(plan.unpack_valid(out.numpy()), want):
+            assert np.array_equal(x, y), dt_in
+        assert dt_next == d[1]
+    plan.close()
+    ref.close()
+
+
 def _tall_box(nsteps=2):
     """A periodic 32 x 16 x 94 comoving box: 4 tiles of 16 x 8, far fewer
     than CTAs, over tall columns that the work list cuts into chunks of 18
