@@ -239,7 +239,10 @@ int nyx_hydro_step_host(nyx_plan *plan, nyx_level *level, const double *host_sta
  * *dt_inout > 0, each group's cells are copied in while earlier groups
  * fill, flatten (flattening plans) and advance.  The library's own
  * streams for this wait on the plan's stream first.  The result is the same
- * either way.  Synchronous: every copy has ended when the call returns. */
+ * either way.  The overlap needs pinned host buffers (pageable ones are
+ * copied correctly, but each copy then holds the calling thread).  host_in
+ * may equal host_out.  Synchronous: every copy has ended when the call
+ * returns. */
 int nyx_hydro_step_host_valid(nyx_plan *plan, nyx_level *level, const double *host_in,
                               double *host_out, double a_old, double a_new, double *dt_inout);
 
