@@ -120,6 +120,7 @@ def load(path: str):
         L.orc_ppm_line.argtypes = [C.c_int, dp, dp, dp, dp]
         L.orc_ppm_integrals.argtypes = [C.c_double] * 4 + [dp, dp]
         L.orc_riemann.argtypes = [C.POINTER(_Params), dp, dp, dp, dp, dp]
+        L.orc_riemann_state.argtypes = [C.POINTER(_Params), dp, dp, dp]
         L.orc_riemann_counts.argtypes = [C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.c_int]
         L.orc_riemann_counts.restype = None
         L.orc_trace_line.argtypes = [C.POINTER(_Params), C.c_int, dp, dp, dp, C.c_double,
@@ -382,6 +383,17 @@ def riemann(params: OracleParams, qL, qR):
     p = params._c()
     lib().orc_riemann(C.byref(p), _dp(qL), _dp(qR), _dp(out), _dp(ps), _dp(us))
     return out, float(ps[0]), float(us[0])
+
+
+def riemann_state(params: OracleParams, qL, qR):
+    """The Godunov state (rho, u_n, u_t1, u_t2, p) sampled at x/t = 0 by the
+    two-shock solve (Sec. 3.2), from which ``riemann`` forms its fluxes."""
+    qL = np.ascontiguousarray(qL, dtype=np.float64)
+    qR = np.ascontiguousarray(qR, dtype=np.float64)
+    g = np.zeros(5)
+    p = params._c()
+    lib().orc_riemann_state(C.byref(p), _dp(qL), _dp(qR), _dp(g))
+    return g
 
 
 def trace_line(params: OracleParams, q5, g=None, *, dtp, dx, adot=0.0, direction=0, fl=None):

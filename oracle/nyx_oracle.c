@@ -323,7 +323,7 @@ static void sample_side(const eos_t *E, const double *qo, double Wo, double co, 
 }
 
 static void riemann_solve(const eos_t *E, const double *qL, const double *qR, double out[8],
-                          double *pstar_o, double *ustar_o) {
+                          double *pstar_o, double *ustar_o, double *g_o) {
   const double cL = sqrt(E->gamma * qL[4] / qL[0]);
   const double cR = sqrt(E->gamma * qR[4] / qR[0]);
   const double CL = qL[0] * cL;
@@ -386,6 +386,8 @@ static void riemann_solve(const eos_t *E, const double *qL, const double *qR, do
   out[7] = pg;
   if (pstar_o) *pstar_o = pstar;
   if (ustar_o) *ustar_o = ustar;
+  if (g_o)
+    for (int v = 0; v < 5; ++v) g_o[v] = g[v];
 }
 
 /* Tangential axes of a face direction, in increasing order. */
@@ -403,7 +405,7 @@ static void face_flux(const eos_t *E, int dir, const double *qLl, const double *
   double qL[5] = {qLl[0], qLl[1 + dir], qLl[1 + t1], qLl[1 + t2], qLl[4]};
   double qR[5] = {qRl[0], qRl[1 + dir], qRl[1 + t1], qRl[1 + t2], qRl[4]};
   double out[8];
-  riemann_solve(E, qL, qR, out, NULL, NULL);
+  riemann_solve(E, qL, qR, out, NULL, NULL, NULL);
   F8[0] = out[0];
   F8[1 + dir] = out[1];
   F8[1 + t1] = out[2];
@@ -1089,7 +1091,14 @@ void orc_ppm_integrals(double sL, double sR, double s6, double sigma, double *ip
 int orc_riemann(const orc_params *p, const double *qL, const double *qR, double *flux8,
                 double *pstar, double *ustar) {
   eos_t E = make_eos(p);
-  riemann_solve(&E, qL, qR, flux8, pstar, ustar);
+  riemann_solve(&E, qL, qR, flux8, pstar, ustar, NULL);
+  return 0;
+}
+
+int orc_riemann_state(const orc_params *p, const double *qL, const double *qR, double *g5) {
+  eos_t E = make_eos(p);
+  double flux8[8];
+  riemann_solve(&E, qL, qR, flux8, NULL, NULL, g5);
   return 0;
 }
 

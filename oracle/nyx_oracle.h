@@ -185,6 +185,9 @@ void orc_ppm_line(int n, const double *s, double *sL, double *sR, double *s6);
 void orc_ppm_integrals(double sL, double sR, double s6, double sigma, double *ip, double *im);
 int orc_riemann(const orc_params *p, const double *qL, const double *qR, double *flux8,
                 double *pstar, double *ustar);
+/* The Godunov state (rho, u_n, u_t1, u_t2, p) at x/t = 0 that the fluxes of
+ * orc_riemann are formed from, floors applied. */
+int orc_riemann_state(const orc_params *p, const double *qL, const double *qR, double *g5);
 void orc_trace_line(const orc_params *p, int n, const double *q5, const double *gline,
                     const double *fl, double dtp, double dx, double adot, int dir, double *qm,
                     double *qp, double *beta_m, double *beta_p);

@@ -45,6 +45,13 @@ MUTANTS = {
                                                 tr.test_contact_only, ()),
     "energy flux without p u": ("out[4] = ug * (rhoeg + ke + pg);", "out[4] = ug * (rhoeg + ke);",
                                 tr.test_supersonic_upwinding, ()),
+    "rarefaction fan weight from the wrong edge (w <-> 1 - w)": (
+        "w = (0.0 - H) / (T - H);", "w = (0.0 - T) / (H - T);",
+        tr.test_transonic_rarefaction_fan_is_continuous_and_linear, ()),
+    "u* = 0 takes the left side instead of the mean": (
+        "for (int v = 0; v < 5; ++v) g[v] = 0.5 * (gl[v] + gr[v]);",
+        "for (int v = 0; v < 5; ++v) g[v] = gl[v];",
+        tr.test_stationary_contact_face_takes_the_mean_of_both_sides, ()),
     "Newton step sign": ("double pn = p - ZL * ZR", "double pn = p + ZL * ZR",
                          tr.test_symmetric_collision_closed_form, (1.4, 1.0)),
     "shock curve constant (gamma+1 -> gamma-1)": (

@@ -183,3 +183,74 @@ def test_rarefaction_fan_interpolation_brackets():
     ug, pg = F[6], F[7]
     assert min(qL[1], us) - 1e-14 <= ug <= max(qL[1], us) + 1e-14
     assert min(qL[4], ps) - 1e-14 <= pg <= max(qL[4], ps) + 1e-14
+
+
+def _fan_scan(P, qL, qR, xi):
+    """Godunov state at x/t = xi of the problem (qL, qR): the problem seen
+    from a frame moving at xi (both normal velocities shifted by -xi),
+    sampled at x/t = 0, with the frame velocity added back."""
+    out = []
+    for x in xi:
+        g = oracle.riemann_state(P, [qL[0], qL[1] - x] + list(qL[2:]), [qR[0], qR[1] - x] + list(qR[2:]))
+        out.append([g[0], g[1] + x, g[4]])
+    return np.array(out)
+
+
+def test_transonic_rarefaction_fan_is_continuous_and_linear():
+    """Sec. 3.2's two-shock solver samples a rarefaction with a linear fan
+    (Colella & Glaz 1985): between the head (speed u_o - c_o) and the tail
+    (u* - c*) the sampled state is linear in x/t, and it meets the side state
+    at the head and the star state at the tail, so the whole self-similar
+    profile is continuous across both edges of the fan.  Scanning the
+    profile through Galilean shifts tests exactly that; a weight measured
+    from the wrong edge (w <-> 1 - w) puts a jump of the whole wave strength
+    at both edges."""
+    g = 1.4
+    P = _params(g)
+    qL = [1.0, 0.0, 0.0, 0.0, 1.0]
+    qR = [0.125, 0.0, 0.0, 0.0, 0.1]
+    _, ps, us = oracle.riemann(P, qL, qR)
+    cL = math.sqrt(g * qL[4] / qL[0])
+    head = qL[1] - cL
+    # from left of the head to just left of the contact (left side sampled)
+    d = 2.0 ** -12
+    xi = head - 0.25 + d * np.arange(int((us - 0.05 - (head - 0.25)) / d))
+    prof = _fan_scan(P, qL, qR, xi)
+    # the left state before the head, the star state (p*, u*) before the contact
+    assert np.all(prof[xi < head - d] == np.array([qL[0], qL[1], qL[4]]))
+    assert prof[-1][2] == pytest.approx(ps, rel=1e-14)
+    assert prof[-1][1] == pytest.approx(us, rel=1e-14)
+    # continuity: no step larger than the fan's slope allows
+    span = np.abs(prof[-1] - prof[0])
+    assert np.all(np.abs(np.diff(prof, axis=0)) <= 2e-3 * span)
+    # inside the fan (strictly between both edge states, with both neighbours)
+    # the profile is linear in x/t: vanishing second differences
+    tail = float(xi[np.argmax(np.all(np.abs(prof - prof[-1]) <= 1e-13 * span, axis=1))])
+    assert head < tail < us
+    inner = (xi > head + 2 * d) & (xi < tail - 2 * d)
+    assert inner.sum() > 100
+    dd = np.abs(prof[2:] - 2 * prof[1:-1] + prof[:-2])[inner[1:-1]]
+    assert np.all(dd <= 1e-12 * span)
+    # the slopes are the wave strengths over the fan's width (tail - head)
+    slope = (prof[-1] - prof[0]) / (tail - head)
+    mid = np.flatnonzero(inner)[len(np.flatnonzero(inner)) // 2]
+    assert (prof[mid + 1] - prof[mid]) / d == pytest.approx(slope, rel=2e-2)
+
+
+def test_stationary_contact_face_takes_the_mean_of_both_sides():
+    """u* = 0 exactly (a contact at rest, equal pressures, different
+    densities and tangential velocities): the face sits on the contact, and
+    the reading of Sec. 3.2's solver takes the arithmetic mean of the two
+    sides' samples.  Every value here is exact in binary.  The choice enters
+    no flux, because each flux but F_mn = p* carries a factor u_g = 0."""
+    P = _params(5.0 / 3.0)
+    qL = [2.0, 0.0, 0.25, -0.5, 1.0]
+    qR = [0.5, 0.0, 0.75, 0.5, 1.0]
+    F, ps, us = oracle.riemann(P, qL, qR)
+    assert us == 0.0 and ps == 1.0
+    g = oracle.riemann_state(P, qL, qR)
+    assert list(g) == [1.25, 0.0, 0.5, 0.0, 1.0]
+    assert list(F) == [0.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0]
+    # mirrored problem: the same mean
+    gm = oracle.riemann_state(P, [qR[0], -0.0] + qR[2:], [qL[0], -0.0] + qL[2:])
+    assert list(gm) == [1.25, 0.0, 0.5, 0.0, 1.0]
