@@ -41,7 +41,7 @@ CORRECT_BYTES_PER_ZONE = 168
 # corrector 16 (two dot products and the weighted difference), dual-energy
 # sync 10 (kinetic energy with its division, the switch test, the
 # subtraction).  FP64 division and square root run at a small fraction of the
-# FP32 rate here; measured FP64 instruction rate: 0.506e12 per second.
+# FP32 rate here.
 CORRECT_FP64_FLOPS_PER_ZONE = 44
 # The shock-flattening pass reads five state components of every cell (rho,
 # the three momenta, rho e; 40 B, the +-3 stencil's reuse coming from the
@@ -51,25 +51,33 @@ FLATTEN_BYTES_PER_ZONE = {"mixed": 44, "fp64": 48}
 # 4 pi G of the self-gravity workloads in code units (mean density 1, sound
 # speed 1, box length 1): a free-fall time of order the sound crossing time.
 COSMO_FOUR_PI_G = 1.0
-FP64_INSTR_TPS = 0.506
 # Algorithmic floating-point operations per zone-update (+ - * / sqrt counted
 # once each, comparisons not counted): 3196 for primitives, PPM + tracing in 3
 # directions, 12 Riemann set-ups/samplings, 18 corner-coupling corrections and
-# the update, plus 480 per mean Newton iteration of the 12 two-shock solves.
-# The FP64 oracle on the large level's 64^3 boxes, in the initial state every
-# timed phase starts from, averages 3.14 iterations at the mixed path's
-# tolerance (1e-6) and 3.83 at the FP64 one (1e-10).
+# the FP64 update (165 in the FP64 forms), plus 480 per mean Newton iteration
+# of the 12 two-shock solves.  The FP64 oracle on the large level's 64^3
+# boxes, in the initial state every timed phase starts from, averages 3.14
+# iterations at the mixed path's tolerance (1e-6) and 3.83 at the FP64 one
+# (1e-10).
 ALG_FLOPS_PER_ZONE = {"mixed": 3196 + 480 * 3.14, "fp64": 3196 + 480 * 3.83}
-# Peaks from unit counts and the maximum SM clock (2070 MHz): 152 SMs x 128
-# FP32 lanes x 2 (FMA) = 80.5 TFLOP/s; 152 SMs x 2 FP64 FMA/clk x 2 = 1.26 TFLOP/s.
+# The mixed path splits them over two pipes.  FP64: the update as written
+# (flux differences and divergence 48, predictor 2 + 1 + 18, reciprocal of
+# the density 3, m.g 5, total energy 8, internal energy 7, gravity corrector
+# 20, dual-energy sync with the kinetic energy 10): 122.  FP32: the rest
+# (the FP64 forms' update of 165 taken out).
+ALG_FP64_FLOPS_MIXED = 122
+ALG_FP32_FLOPS_MIXED = ALG_FLOPS_PER_ZONE["mixed"] - 165
 # DRAM bytes per zone of the task-form kernel at 16 x 8 tiles on the large
-# level's box sizes (ncu capture of the large128 workload, profiles/
-# k_fused2_mixed_large128.md); traffic scales with the cells of boxes of the
-# same sizes.  Reported only for that kernel, workload and shape.
+# level's box sizes, from one ncu capture of the large128 workload (the same
+# box sizes on a 128^3 domain); traffic scales with the cells of boxes of the
+# same sizes.  Reported only for that kernel, workload and shape, and only
+# while the kernel is the one captured.
 NOMINAL_HBM_GBS = 7900.0   # HBM3e nominal rate of the part, beside the measured copy rate
 TRAFFIC_BYTES_PER_ZONE = {("large", 3): 151.2, ("large128", 3): 151.2}
-PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# Unit-count peaks (152 SMs at the 2070 MHz maximum clock; 128 FP32 and 2
+# FP64 FMA lanes per SM per clock), reported beside the measured ones.
+NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+NOMINAL_FP64_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 
 def load_peaks():
@@ -80,6 +88,49 @@ def load_peaks():
         return d, "measured"
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def measure_alu(stream=None):
+    """FP32 and FP64 multiply-add peaks of this GPU, measured by the
+    library's own throughput probe (nyx_alu_peak), in TFLOP/s (FMA = 2)."""
+    from paper_1301_4498_gb300 import hydro as H
+    f32 = H.alu_peak("fp32", 0.25, stream)
+    f64 = H.alu_peak("fp64", 0.25, stream)
+    return {"fp32_tflops": 2 * f32 / 1e12, "fp64_tflops": 2 * f64 / 1e12,
+            "fp32_fma_per_s": f32, "fp64_fma_per_s": f64,
+            "nominal_fp32_tflops": NOMINAL_FP32_TFLOPS, "nominal_fp64_tflops": NOMINAL_FP64_TFLOPS,
+            "how": "nyx_alu_peak: 8 independent FMA chains per thread, 8 x 256 threads per SM, "
+                   "best of 5 timed launches (CUDA events)"}
+
+
+def roofline_of(kernel_ms, cells, precision, peaks, peak_src, alu, kernel, traffic=None):
+    """Roofline of one launch of the advance over `cells` zones: the time
+    each roof (HBM at the measured copy rate, the FP32 and the FP64 pipe at
+    their measured FMA rates) allows for the algorithmic work, and the
+    achieved fraction of the binding (slowest) one."""
+    sec = kernel_ms / 1e3
+    if precision == "mixed":
+        work = {"fp32": ALG_FP32_FLOPS_MIXED, "fp64": ALG_FP64_FLOPS_MIXED}
+    else:
+        work = {"fp64": ALG_FLOPS_PER_ZONE["fp64"]}
+    roofs = {"hbm": {"bound": "hbm", "alg_per_zone": ALG_BYTES_PER_ZONE, "unit": "GB/s",
+                     "achieved": ALG_BYTES_PER_ZONE * cells / sec / 1e9,
+                     "peak": peaks["hbm_gbs"], "peak_source": f"hbm_gbs {peak_src}"}}
+    for pipe, fz in work.items():
+        roofs[pipe] = {"bound": pipe, "alg_per_zone": fz, "unit": "TFLOP/s",
+                       "achieved": fz * cells / sec / 1e12,
+                       "peak": alu[f"{pipe}_tflops"], "peak_source": "measured (nyx_alu_peak)"}
+    for r in roofs.values():
+        r["frac"] = r["achieved"] / r["peak"]
+        r["roof_ms"] = kernel_ms * r["frac"]
+    bind = max(roofs, key=lambda k: roofs[k]["roof_ms"])
+    b = roofs[bind]
+    out = {"bound": b["bound"], "achieved": b["achieved"], "peak": b["peak"], "unit": b["unit"],
+           "frac": b["frac"], "traffic": traffic, "traffic_unit": "bytes per launch",
+           "kernel": kernel, "kernel_ms": kernel_ms, "peak_source": b["peak_source"],
+           "binding": "the roof allowing the longest time for the algorithmic work",
+           "roofs": roofs}
+    return out
 
 
 def make_workload(name: str, sample_only: bool = False):
@@ -343,6 +394,8 @@ def run_ours(args, w):
     def restore():
         lev.state[lev.cur].copy_(snap)
 
+    # measured ALU peaks of this GPU (the roofline's FP32 and FP64 denominators)
+    alu = measure_alu(stream.cuda_stream)
     # warm-up: W eager steps (the first one also runs the tile autotuner)
     plan.run(lev, a, dt, Wm, compute_dt0=True, use_graph=False)
     restore()
@@ -389,10 +442,7 @@ def run_ours(args, w):
     restore()
     adv_ms = prof["advance_ms"] / max(1, prof["timed_advances"])
     fill_ms = prof["fill_ms"] / max(1, prof["timed_fills"])
-    achieved_gbs = ALG_BYTES_PER_ZONE * cells / (adv_ms / 1e3) / 1e9
     flops = ALG_FLOPS_PER_ZONE[args.precision]
-    peak_tf = PEAK_FP32_TFLOPS if args.precision == "mixed" else PEAK_FP64_TFLOPS
-    achieved_tf = flops * cells / (adv_ms / 1e3) / 1e12
     shape, (tx, ty) = plan.tile_shape()
 
     # end to end through the C ABI with pinned host buffers: the level's valid
@@ -446,10 +496,10 @@ def run_ours(args, w):
         f64 = CORRECT_FP64_FLOPS_PER_ZONE * cells / (c_ms / 1e3) / 1e12
         variants["corrector"] = {"ms": c_ms, "bound": "fp64",
                                  "alg_fp64_flops_per_zone": CORRECT_FP64_FLOPS_PER_ZONE,
-                                 "achieved": f64, "peak": FP64_INSTR_TPS, "unit": "TFLOP/s",
-                                 "frac": f64 / FP64_INSTR_TPS,
-                                 "peak_source": "measured FP64 instruction rate (one flop per "
-                                                "non-FMA instruction)",
+                                 "achieved": f64, "peak": alu["fp64_fma_per_s"] / 1e12,
+                                 "unit": "TFLOP/s", "frac": f64 / (alu["fp64_fma_per_s"] / 1e12),
+                                 "peak_source": "measured FP64 instruction rate (nyx_alu_peak; "
+                                                "one flop per non-FMA instruction)",
                                  "hbm": {"alg_bytes_per_zone": CORRECT_BYTES_PER_ZONE,
                                          "achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"],
                                          "frac": gbs / peaks["hbm_gbs"]}}
@@ -483,9 +533,10 @@ def run_ours(args, w):
             return out
 
         r2 = one_advance(grav_energy=1)
-        r2["achieved_tflops"] = flops * cells / (r2["advance_ms"] / 1e3) / 1e12
-        r2["frac"] = r2["achieved_tflops"] / peak_tf
-        r2["bound"] = "alu"
+        rf2 = roofline_of(r2["advance_ms"], cells, args.precision, peaks, peak_src, alu,
+                          "fused advance, energy option (ii)")
+        r2.update(bound=rf2["bound"], achieved=rf2["achieved"], peak=rf2["peak"],
+                  unit=rf2["unit"], frac=rf2["frac"])
         variants["energy_option_ii"] = r2
         # PLM and the linearised solver do fewer operations than the
         # algorithmic count above, so only their times and rates are reported
@@ -530,8 +581,9 @@ def run_ours(args, w):
             tf = ALG_FLOPS_PER_ZONE["fp64"] * zps / 1e12
             side[label] = {"value": zps, "unit": "zone-updates/s", "steps": 1,
                            "roofline": {"bound": "fp64", "achieved": tf,
-                                        "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
-                                        "frac": tf / PEAK_FP64_TFLOPS,
+                                        "peak": alu["fp64_tflops"], "unit": "TFLOP/s",
+                                        "frac": tf / alu["fp64_tflops"],
+                                        "peak_source": "measured (nyx_alu_peak)",
                                         "alg_flops_per_zone": ALG_FLOPS_PER_ZONE["fp64"],
                                         "note": "whole step (fill, advance, dt) timed"}}
             p64.close()
@@ -554,24 +606,18 @@ def run_ours(args, w):
                        "batching": "persistent + CUDA graph", "tile": [tx, ty],
                        "l2": "inputs larger than L2 (state + gravity > 20 GB)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
-            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf,
-                         "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
-                         "traffic": (args.traffic_per_zone * cells if args.traffic_per_zone else
-                                     (TRAFFIC_BYTES_PER_ZONE[(args.workload, shape)] * cells
-                                      if args.precision == "mixed" and
-                                      (args.workload, shape) in TRAFFIC_BYTES_PER_ZONE else None)),
-                         "traffic_unit": "bytes per launch",
-                         "kernel": ("k_fused2 (task form)" if shape >= 3 else
-                                    f"k_fused<{'float' if args.precision == 'mixed' else 'double'}>"),
-                         "kernel_ms": adv_ms, "alg_flops_per_zone": flops,
-                         "pipe": "fp32" if args.precision == "mixed" else "fp64",
-                         "peak_source": "unit counts x 2070 MHz"},
-            "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"],
-                             "unit": "GB/s", "frac": achieved_gbs / peaks["hbm_gbs"],
-                             "alg_bytes_per_zone": ALG_BYTES_PER_ZONE,
-                             "peak_source": f"hbm_gbs {peak_src}",
-                             "nominal_peak": NOMINAL_HBM_GBS,
-                             "frac_of_nominal": achieved_gbs / NOMINAL_HBM_GBS},
+            "roofline": roofline_of(
+                adv_ms, cells, args.precision, peaks, peak_src, alu,
+                ("k_fused2 (task form)" if shape >= 3 else
+                 f"k_fused<{'float' if args.precision == 'mixed' else 'double'}>"),
+                traffic=(args.traffic_per_zone * cells if args.traffic_per_zone else
+                         (TRAFFIC_BYTES_PER_ZONE[(args.workload, shape)] * cells
+                          if args.precision == "mixed" and
+                          (args.workload, shape) in TRAFFIC_BYTES_PER_ZONE else None))),
+            "alu_peaks": alu,
+            "hbm_nominal": {"peak": NOMINAL_HBM_GBS,
+                            "frac": ALG_BYTES_PER_ZONE * cells / (adv_ms / 1e3) / 1e9 /
+                            NOMINAL_HBM_GBS},
             "kernel_ms": {"advance": adv_ms, "ghost_fill": fill_ms},
             "variants": variants,
             "fp64_comparison": side,
@@ -789,10 +835,7 @@ def run_amr(args, aw):
         ps.close()
         del gtmp
     adv_ms = adv_c + adv_f
-    flops = ALG_FLOPS_PER_ZONE[args.precision]
-    peak_tf = PEAK_FP32_TFLOPS if args.precision == "mixed" else PEAK_FP64_TFLOPS
-    achieved_tf = flops * cells / (adv_ms / 1e3) / 1e12
-    achieved_gbs = ALG_BYTES_PER_ZONE * cells / (adv_ms / 1e3) / 1e9
+    alu = measure_alu(stream.cuda_stream)
     shape, (tx, ty) = cp.tile_shape()
 
     e2e = None
@@ -838,19 +881,9 @@ def run_amr(args, aw):
                        "keep_fluxes": args.keep_fluxes, "tile": [tx, ty],
                        "l2": "inputs larger than L2 (state + gravity > 20 GB)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
-            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf,
-                         "unit": "TFLOP/s", "frac": achieved_tf / peak_tf, "traffic": None,
-                         "traffic_unit": "bytes per launch",
-                         "kernel": "fused advance of both levels", "kernel_ms": adv_ms,
-                         "alg_flops_per_zone": flops,
-                         "pipe": "fp32" if args.precision == "mixed" else "fp64",
-                         "peak_source": "unit counts x 2070 MHz"},
-            "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"],
-                             "unit": "GB/s", "frac": achieved_gbs / peaks["hbm_gbs"],
-                             "alg_bytes_per_zone": ALG_BYTES_PER_ZONE,
-                             "peak_source": f"hbm_gbs {peak_src}",
-                             "nominal_peak": NOMINAL_HBM_GBS,
-                             "frac_of_nominal": achieved_gbs / NOMINAL_HBM_GBS},
+            "roofline": roofline_of(adv_ms, cells, args.precision, peaks, peak_src, alu,
+                                    "fused advance of both levels"),
+            "alu_peaks": alu,
             "kernel_ms": {"advance_coarse": adv_c, "advance_fine": adv_f,
                           "ghost_fill_coarse": pc["fill_ms"] / max(1, pc["timed_fills"]),
                           "ghost_fill_fine": pf["fill_ms"] / max(1, pf["timed_fills"])},
@@ -1041,9 +1074,7 @@ def run_cosmo(args, w):
     ms_max = max_over_ranks(ms, ws)
     value = ws * cells * K / (ms_max / 1e3)
     adv_ms = timing["gas_advance"] / K
-    flops = ALG_FLOPS_PER_ZONE[args.precision]
-    peak_tf = PEAK_FP32_TFLOPS if args.precision == "mixed" else PEAK_FP64_TFLOPS
-    achieved_tf = flops * cells / (adv_ms / 1e3) / 1e12
+    alu = measure_alu(plan.torch_stream.cuda_stream)
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = oracle_cosmo_sample(budget_s=args.cpu_budget)
@@ -1064,10 +1095,9 @@ def run_cosmo(args, w):
                        "tile": [tx, ty], "l2": "inputs larger than L2",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
             "particle_updates_per_s": ws * npart * K / (ms_max / 1e3),
-            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf,
-                         "unit": "TFLOP/s", "frac": achieved_tf / peak_tf, "traffic": None,
-                         "kernel": "fused gas predictor (k_fused2)", "kernel_ms": adv_ms,
-                         "alg_flops_per_zone": flops, "peak_source": "unit counts x 2070 MHz"},
+            "roofline": roofline_of(adv_ms, cells, args.precision, peaks, peak_src, alu,
+                                    "fused gas predictor (k_fused2)"),
+            "alu_peaks": alu,
             "breakdown_ms_per_step": {k: v / K for k, v in timing.items()},
             "poisson_cycles_per_step": cyc_total / K,
             "clocks": clk, "e2e": None, "gpu_launches": launches, "cpu_baseline": cpu,

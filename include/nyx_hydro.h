@@ -307,9 +307,13 @@ int nyx_hydro_status(nyx_plan *plan, int *flags);
  *    with NYX_EINVAL.
  *  - The first call on a device looks up the array's device address (with
  *    that device current); make that first call before any stream capture.
+ *    Every call copies its tables from host memory, and a call whose stream
+ *    is capturing is rejected with NYX_EINVAL.
  *  - Every call shares the array and leaves its contents behind; each call
  *    rewrites the tables and resets the accumulator before use.  Calls that
  *    overlap on the GPU (other streams, other host threads) race.
+ *  - A non-finite or non-positive dx, gamma <= 1, or a non-finite gamma, cfl
+ *    or small_pres is rejected with NYX_EINVAL, as nyx_hydro_plan does.
  *  - level, params: host descriptors as for nyx_hydro_plan (ng must be 4).
  *    state: device field of 6 components.  a_dev, dt_dev: device scalars.
  *    stream: a cudaStream_t (NULL = legacy default stream).  Asynchronous
@@ -321,6 +325,16 @@ int nyx_hydro_estdt_noalloc(const nyx_level_desc *level, const nyx_hydro_params 
 
 /* Release the plan's device and host resources (not the caller's buffers). */
 int nyx_plan_destroy(nyx_plan *plan);
+
+/* Measured fused multiply-add throughput of the current device (no
+ * counterpart in the paper: it gives the ALU denominators of the roofline
+ * against which the advance is reported).  pipe 0: FP32, 1: FP64.  Runs
+ * independent multiply-add chains on every SM for about `seconds` in total
+ * (0 < seconds <= 10) on `stream`, synchronising with it, and stores the best
+ * rate of five timed launches in *fma_per_s (lane operations per second; one
+ * FMA is two floating-point operations).  Allocates nothing on the device.
+ * NYX_EINVAL for a bad argument, NYX_ECUDA if a launch or event fails. */
+int nyx_alu_peak(int pipe, double seconds, void *stream, double *fma_per_s);
 
 /* ---------------------------------------------------------------- self-gravity
  * The Poisson equation of Sec. 3.4 on one level that tiles a single periodic

@@ -30,6 +30,7 @@ UNITS = {
     "nyx_fused_f64.cu": ["--fmad=false"],
     "nyx_fused_mixed.cu": ["--fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
     "nyx_noalloc.cu": [],
+    "nyx_probe.cu": [],
     "nyx_amr.cu": ["--fmad=false"],
     "nyx_poisson.cu": ["--fmad=false"],
 }

@@ -11,6 +11,7 @@
 // host threads) therefore race; calls on one stream are ordered and safe.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <mutex>
 #include <string>
 
@@ -64,13 +65,23 @@ extern "C" int nyx_hydro_estdt_noalloc(const nyx_level_desc *level, const nyx_hy
                                 " boxes; the allocation-free CFL reduction takes at most " +
                                 std::to_string(kMaxBoxes));
   if (level->ng != 4) return fail(NYX_EINVAL, "ghost width must be 4");
-  if (!(params->gamma > 1.0) || !(params->cfl > 0.0) || !(params->small_pres > 0.0))
+  if (!(params->gamma > 1.0) || !std::isfinite(params->gamma) || !(params->cfl > 0.0) ||
+      !std::isfinite(params->cfl) || !(params->small_pres > 0.0) ||
+      !std::isfinite(params->small_pres))
     return fail(NYX_EINVAL, "invalid scheme parameters");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(NYX_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= 64) return fail(NYX_EINVAL, "device index out of range");
   cudaStream_t st = (cudaStream_t)stream;
+  // The tables are copied from host memory on every call, which a stream
+  // that is being captured into a graph cannot take.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess)
+    return fail(NYX_ECUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
+  if (cap != cudaStreamCaptureStatusNone)
+    return fail(NYX_EINVAL, "the stream is capturing; call nyx_hydro_estdt_noalloc outside stream capture");
 
   Staging &S = staging();
   std::lock_guard<std::mutex> lock(S.mu);
@@ -91,7 +102,7 @@ extern "C" int nyx_hydro_estdt_noalloc(const nyx_level_desc *level, const nyx_hy
     BoxDev &D = S.boxes[b];
     for (int a = 0; a < 3; ++a) {
       const int n = X.hi[a] - X.lo[a] + 1;
-      if (n <= 0 || (n & 1) || !(X.dx[a] > 0.0))
+      if (n <= 0 || (n & 1) || !(X.dx[a] > 0.0) || !std::isfinite(X.dx[a]))
         return fail(NYX_EINVAL, "box " + std::to_string(b) + " has a bad extent or dx");
       D.n[a] = n;
       D.N[a] = n + 8;

@@ -129,6 +129,8 @@ def load_library(path: str | None = None):
     L.nyx_hydro_counters_read.argtypes = [vp, C.c_int, C.POINTER(NyxCounters)]
     L.nyx_hydro_estdt_noalloc.argtypes = [C.POINTER(NyxLevelDesc), C.POINTER(NyxParams), vp, vp,
                                           vp, vp]
+    L.nyx_alu_peak.argtypes = [C.c_int, C.c_double, vp, dp]
+    L.nyx_alu_peak.restype = C.c_int
     L.nyx_poisson_default_params.argtypes = [C.POINTER(NyxPoissonParams)]
     L.nyx_poisson_default_params.restype = None
     L.nyx_poisson_create.argtypes = [vp, C.POINTER(NyxPoissonParams), C.POINTER(vp)]
@@ -499,6 +501,19 @@ def estdt_noalloc(spec, state, a_dev, dt_dev, stream=None, **params):
         stream = torch.cuda.current_stream().cuda_stream
     _check(load_library().nyx_hydro_estdt_noalloc(C.byref(desc), C.byref(p), _ptr(state),
                                                    _ptr(a_dev), _ptr(dt_dev), C.c_void_p(stream)))
+
+
+def alu_peak(pipe: str, seconds: float = 0.25, stream=None) -> float:
+    """nyx_alu_peak: measured fused multiply-add rate of the current device
+    (lane operations per second) on the FP32 (``"fp32"``) or FP64
+    (``"fp64"``) pipe."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    out = C.c_double()
+    _check(load_library().nyx_alu_peak({"fp32": 0, "fp64": 1}[pipe], seconds, C.c_void_p(stream),
+                                       C.byref(out)))
+    return out.value
 
 
 class Poisson:

@@ -172,3 +172,12 @@ def test_task_items_count_query_and_short_buffer(lib):
     assert count.value == len(full)
     got = np.array(buf[:], dtype=np.int64).reshape(6, 7)
     assert np.array_equal(got[:5], full[:5]) and np.all(got[5] == -7)
+
+
+def test_alu_peak_rejects_bad_arguments(lib):
+    out = C.c_double(-1.0)
+    assert lib.nyx_alu_peak(2, 0.25, None, C.byref(out)) == H.NYX_EINVAL
+    assert lib.nyx_alu_peak(0, 0.0, None, C.byref(out)) == H.NYX_EINVAL
+    assert lib.nyx_alu_peak(1, 11.0, None, C.byref(out)) == H.NYX_EINVAL
+    assert lib.nyx_alu_peak(0, 0.25, None, None) == H.NYX_EINVAL
+    assert out.value == -1.0

@@ -40,13 +40,29 @@ def test_noalloc_estdt_matches_plan_estdt_twice():
     plan2, lev2, ref2 = _reference(w2, 1.0 / 50)
     out = torch.full((2,), -1.0, dtype=torch.float64, device="cuda")
     a = torch.tensor([1.0 / 51, 1.0 / 50], dtype=torch.float64, device="cuda")
+    warm = torch.zeros(1, dtype=torch.float64, device="cuda")
+    # a warm-up call loads the kernels, then the two calls under test must
+    # leave every allocator untouched
+    H.estdt_noalloc(w2.level, lev2.current, a[1:2], warm, gamma=w2.gamma, cfl=w2.cfl)
+    torch.cuda.synchronize()
+    used0, free0 = torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0]
     H.estdt_noalloc(w1.level, lev1.current, a[0:1], out[0:1], gamma=w1.gamma, cfl=w1.cfl)
     H.estdt_noalloc(w2.level, lev2.current, a[1:2], out[1:2], gamma=w2.gamma, cfl=w2.cfl)
     torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == used0
+    assert torch.cuda.mem_get_info()[0] == free0
     got = out.cpu().numpy()
     assert abs(got[0] - ref1) <= TOL * ref1, (got[0], ref1)
     assert abs(got[1] - ref2) <= TOL * ref2, (got[1], ref2)
     assert got[0] != got[1]
+
+
+def test_noalloc_estdt_rejects_non_finite_cell_width():
+    spec = W.independent_boxes_level([(2, 2, 2)], float("inf"))
+    x = torch.zeros(8, dtype=torch.float64, device="cuda")
+    with pytest.raises(H.NyxError) as e:
+        H.estdt_noalloc(spec, x, x[0:1], x[1:2])
+    assert e.value.code == H.NYX_EINVAL
 
 
 def test_noalloc_estdt_rejects_too_many_boxes():
