@@ -64,7 +64,15 @@ struct G2 {
   static constexpr int GR = P2 + 40 * NC;            // [4][NC] gravity and flattening, plane c
   static constexpr int UF = GR + 4 * NC;             // [8][NUF] final x, y fluxes of plane c-1
   static constexpr int FFZ = UF + 8 * NUF;           // [2 faces][8][NZF] final z fluxes
-  static constexpr int TOTAL = FFZ + 16 * NZF;
+  // task lists of stages S2-S6 for the full tile (ushort entries)
+  static constexpr int T2 = (TX + 1) * H + W * (TY + 1) + NC;
+  static constexpr int T3 = 2 * W * TY + 2 * TX * H + 2 * NC;
+  static constexpr int T4 = (TX + 1) * TY + TX * (TY + 1) + (TX + 1) * H + W * (TY + 1) + TX * H + W * TY;
+  static constexpr int T5 = TX * TY + W * TY + TX * H;
+  static constexpr int T6 = (TX + 1) * TY + TX * (TY + 1) + TX * TY;
+  static constexpr int TT = T2 + T3 + T4 + T5 + T6;
+  static constexpr int TAB = FFZ + 16 * NZF;         // [TT] ushort task lists
+  static constexpr int TOTAL = TAB + (TT + 1) / 2;
   static constexpr size_t SMEM = sizeof(float) * (size_t)TOTAL;
   static_assert(SMEM <= 227 * 1024, "task-form tile does not fit in shared memory");
 };
@@ -188,6 +196,88 @@ __device__ __forceinline__ void face_flux_dir(const Eos<float> &E, int dir, cons
   F[7] = o[7];
 }
 
+// Task lists of stages S2-S6.  Each kind of task covers a rectangle of the
+// tile's columns (local i in [i0, nx-1+di1], j in [j0, ny-1+dj1]; -1 and n
+// are the one-cell halo): the faces or states that the tile's corner-coupled
+// fluxes need.  Kinds, in list order: S2 normal x, y, z; S3 q_{x|y}, q_{y|x},
+// q_{z|x}, q_{z|y}, q_{x|z}, q_{y|z}; S4 F^{x|y}, F^{y|x}, F^{x|z}, F^{y|z},
+// F^{z|x}, F^{z|y}; S5 final z, x, y states; S6 final x, y, z solves.
+struct KRect {
+  int i0, di1, j0, dj1;
+};
+__device__ __forceinline__ KRect krect(int k) {
+  switch (k) {
+    case 0: return {0, 1, -1, 1};    // S2 x faces
+    case 1: return {-1, 1, 0, 1};    // S2 y faces
+    case 2: return {-1, 1, -1, 1};   // S2 z faces
+    case 3: return {-1, 1, 0, 0};    // S3 q_{x|y}
+    case 4: return {0, 0, -1, 1};    // S3 q_{y|x}
+    case 5: return {0, 0, -1, 1};    // S3 q_{z|x}
+    case 6: return {-1, 1, 0, 0};    // S3 q_{z|y}
+    case 7: return {-1, 1, -1, 1};   // S3 q_{x|z}
+    case 8: return {-1, 1, -1, 1};   // S3 q_{y|z}
+    case 9: return {0, 1, 0, 0};     // S4 F^{x|y}
+    case 10: return {0, 0, 0, 1};    // S4 F^{y|x}
+    case 11: return {0, 1, -1, 1};   // S4 F^{x|z}
+    case 12: return {-1, 1, 0, 1};   // S4 F^{y|z}
+    case 13: return {0, 0, -1, 1};   // S4 F^{z|x}
+    case 14: return {-1, 1, 0, 0};   // S4 F^{z|y}
+    case 15: return {0, 0, 0, 0};    // S5 final z state
+    case 16: return {-1, 1, 0, 0};   // S5 final x state
+    case 17: return {0, 0, -1, 1};   // S5 final y state
+    case 18: return {0, 1, 0, 0};    // S6 x faces
+    case 19: return {0, 0, 0, 1};    // S6 y faces
+    default: return {0, 0, 0, 0};    // S6 z faces
+  }
+}
+__device__ __forceinline__ int kind0_of(int st) { return st == 0 ? 0 : (st == 1 ? 3 : (st == 2 ? 9 : (st == 3 ? 15 : 18))); }
+__device__ __forceinline__ int nkind_of(int st) { return (st == 1 || st == 2) ? 6 : 3; }
+
+// tn[0..4]: the number of tasks of S2..S6 for an nx x ny tile; tn[5..8]: the
+// list offsets of S3..S6 (S2 starts at 0).
+__device__ __forceinline__ void task_counts(int nx, int ny, int (&tn)[9]) {
+  int off = 0;
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    int n = 0;
+    for (int k = kind0_of(st); k < kind0_of(st) + nkind_of(st); ++k) {
+      const KRect r = krect(k);
+      n += (nx + r.di1 - r.i0) * (ny + r.dj1 - r.j0);
+    }
+    tn[st] = n;
+    if (st > 0) tn[4 + st] = off;
+    off += n;
+  }
+}
+
+// Entries (kind within its stage << 12 | owned column) of every list, in
+// kind order, written by threads [0, nthr).
+template <int W>
+__device__ void build_tasks(unsigned short *tab, int nx, int ny, const int (&tn)[9], int tid,
+                            int nthr) {
+  const int total = tn[5] + tn[1] + tn[2] + tn[3] + tn[4];
+  for (int t = tid; t < total; t += nthr) {
+    int st = 0, l = t;
+    if (t >= tn[8]) { st = 4; l = t - tn[8]; }
+    else if (t >= tn[7]) { st = 3; l = t - tn[7]; }
+    else if (t >= tn[6]) { st = 2; l = t - tn[6]; }
+    else if (t >= tn[5]) { st = 1; l = t - tn[5]; }
+    const int k0 = kind0_of(st);
+    unsigned short e = 0;
+    for (int k = 0; k < nkind_of(st); ++k) {
+      const KRect r = krect(k0 + k);
+      const int w = nx + r.di1 - r.i0, h = ny + r.dj1 - r.j0;
+      if (l < w * h) {
+        const int i = r.i0 + l % w, j = r.j0 + l / w;
+        e = (unsigned short)((k << 12) | ((j + 1) * W + (i + 1)));
+        break;
+      }
+      l -= w * h;
+    }
+    tab[t] = e;
+  }
+}
+
 template <int TX, int TY, int MB, int VAR>
 __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::FusedArgs a) {
   using G = G2<TX, TY, XU_OF(MB)>;
@@ -224,6 +314,8 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
   const int mee = (mj + 3) * WE + (mi + 3);
   float dtmin = __int_as_float(0x7f800000);
   unsigned flags = 0;
+  unsigned short *ttab = reinterpret_cast<unsigned short *>(sm + G::TAB);
+  int tab_nx = -1, tab_ny = -1;  // the tile extent the lists were built for
 
   for (;;) {
     if (tid == 0) s_item = atomicAdd(a.queue, 1);
@@ -243,6 +335,15 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
       const float dtdx0 = d2f_rn(bst.dtdx[0]), dtdx1 = d2f_rn(bst.dtdx[1]), dtdx2 = d2f_rn(bst.dtdx[2]);
       const float c30 = d2f_rn(bst.cdt3[0]), c31 = d2f_rn(bst.cdt3[1]), c32 = d2f_rn(bst.cdt3[2]);
       const float ch0 = d2f_rn(bst.chalf[0]), ch1 = d2f_rn(bst.chalf[1]), ch2 = d2f_rn(bst.chalf[2]);
+      int tn[9];
+      task_counts(nxt, nyt, tn);
+      if (nxt != tab_nx || nyt != tab_ny) {
+        // the previous item's lists are no longer read (item-end barrier)
+        build_tasks<W>(ttab, nxt, nyt, tn, tid, NTC);
+        tab_nx = nxt;
+        tab_ny = nyt;
+        bar_sync_n(BAR_COL, NTC);
+      }
       // geometry of this thread's column for this tile
       const bool act = me < NC && mi <= nxt && mj <= nyt;
       const bool inX = mi >= 0 && mi < nxt, inY = mj >= 0 && mj < nyt;
@@ -293,173 +394,158 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
         if (c < ze) bar_arrive_n(BAR_CONSUMED, NT);
 
         // ---------------------------------------------- S2: normal solves
-        if (act) {
+        // Stages S2-S6 run the tile's task lists (built for its extent when the
+        // item starts): only the tasks whose faces or states the tile needs, in
+        // kind order, dealt to the column threads in turn.
+        for (int t = tid; t < tn[0]; t += NTC) {
+          const int e = ttab[t], kind = e >> 12, cm = e & 0xfff;
           const float *L, *Rr;
           float *O;
           int lc;
-          bool go;
-          if (kq == 0) {
-            go = mi >= 0;
-            L = sm + G::QXY + (pc * 2 + 0) * 10 * NC + 5 * NC;
-            lc = me - 1;
-            Rr = sm + G::QXY + (pc * 2 + 0) * 10 * NC;
-            O = sm + G::P1;
-          } else if (kq == 1) {
-            go = mj >= 0;
-            L = sm + G::QXY + (pc * 2 + 1) * 10 * NC + 5 * NC;
-            lc = me - W;
-            Rr = sm + G::QXY + (pc * 2 + 1) * 10 * NC;
-            O = sm + G::P1 + 7 * NC;
+          if (kind == 0) {
+            L = sm + G::QXY + (pc * 2 + 0) * 10 * NC + 5 * NC; lc = cm - 1;
+            Rr = sm + G::QXY + (pc * 2 + 0) * 10 * NC; O = sm + G::P1;
+          } else if (kind == 1) {
+            L = sm + G::QXY + (pc * 2 + 1) * 10 * NC + 5 * NC; lc = cm - W;
+            Rr = sm + G::QXY + (pc * 2 + 1) * 10 * NC; O = sm + G::P1 + 7 * NC;
           } else {
-            go = c >= zb;
-            L = sm + G::QZ + pm * 10 * NC + 5 * NC;
-            lc = me;
-            Rr = sm + G::QZ + pc * 10 * NC;
-            O = sm + G::FZ + pc * 7 * NC;
+            L = sm + G::QZ + pm * 10 * NC + 5 * NC; lc = cm;
+            Rr = sm + G::QZ + pc * 10 * NC; O = sm + G::FZ + pc * 7 * NC;
           }
-          if (go) {
+          if (kind < 2 || c >= zb) {
             float l[5], r[5], F[8];
             ld5(L, NC, lc, l);
-            ld5(Rr, NC, me, r);
-            face_flux_dir(E, kq, l, r, F);
-            st7(O, NC, me, F);
+            ld5(Rr, NC, cm, r);
+            face_flux_dir(E, kind, l, r, F);
+            st7(O, NC, cm, F);
           }
         }
         bar_sync_n(BAR_COL, NTC);
 
         // ---------------------------------------------- S3: corner coupling, theta = 1/3
-        if (act) {
-  #pragma unroll 1
-          for (int rep = 0; rep < 2; ++rep) {
-            const int kind = kq + 3 * rep;
-            const float *Q, *Fmb, *Fpb;
-            float *Om, *Op;
-            int fpc;
-            float coef;
-            bool go;
-            switch (kind) {
-              case 0:  // q_{x|y} at c
-                go = inY; Q = sm + G::QXY + (pc * 2 + 0) * 10 * NC; Fmb = Fpb = sm + G::P1 + 7 * NC;
-                fpc = me + W; coef = c31; Om = sm + G::P2; Op = sm + G::P2 + 5 * NC;
-                break;
-              case 1:  // q_{y|x} at c
-                go = inX; Q = sm + G::QXY + (pc * 2 + 1) * 10 * NC; Fmb = Fpb = sm + G::P1;
-                fpc = me + 1; coef = c30; Om = sm + G::P2 + 10 * NC; Op = sm + G::P2 + 15 * NC;
-                break;
-              case 2:  // q_{z|x} at c
-                go = inX; Q = sm + G::QZ + pc * 10 * NC; Fmb = Fpb = sm + G::P1;
-                fpc = me + 1; coef = c30; Om = sm + G::QZXM; Op = sm + G::QZXP + pc * 5 * NC;
-                break;
-              case 3:  // q_{z|y} at c
-                go = inY; Q = sm + G::QZ + pc * 10 * NC; Fmb = Fpb = sm + G::P1 + 7 * NC;
-                fpc = me + W; coef = c31; Om = sm + G::QZYM; Op = sm + G::QZYP + pc * 5 * NC;
-                break;
-              case 4:  // q_{x|z} at c-1
-                go = zc; Q = sm + G::QXY + (pm * 2 + 0) * 10 * NC; Fmb = sm + G::FZ + pm * 7 * NC;
-                Fpb = sm + G::FZ + pc * 7 * NC; fpc = me; coef = c32;
-                Om = sm + G::P2 + 20 * NC; Op = sm + G::P2 + 25 * NC;
-                break;
-              default:  // q_{y|z} at c-1
-                go = zc; Q = sm + G::QXY + (pm * 2 + 1) * 10 * NC; Fmb = sm + G::FZ + pm * 7 * NC;
-                Fpb = sm + G::FZ + pc * 7 * NC; fpc = me; coef = c32;
-                Om = sm + G::P2 + 30 * NC; Op = sm + G::P2 + 35 * NC;
-                break;
-            }
-            if (go) {
-              const TFlux<float> Fm = ld7(Fmb, NC, me), Fp = ld7(Fpb, NC, fpc);
-              float qa[5], qb[5], oa[5], ob[5];
-              ld5(Q, NC, me, qa);
-              ld5(Q + 5 * NC, NC, me, qb);
-              transverse1(E, qa, coef, Fp, Fm, oa);
-              transverse1(E, qb, coef, Fp, Fm, ob);
-              st5(Om, NC, me, oa);
-              st5(Op, NC, me, ob);
-            }
+        for (int t = tid; t < tn[1]; t += NTC) {
+          const int e = ttab[tn[5] + t], kind = e >> 12, cm = e & 0xfff;
+          const float *Q, *Fmb, *Fpb;
+          float *Om, *Op;
+          int fpc;
+          float coef;
+          switch (kind) {
+            case 0:  // q_{x|y} at c
+              Q = sm + G::QXY + (pc * 2 + 0) * 10 * NC; Fmb = Fpb = sm + G::P1 + 7 * NC;
+              fpc = cm + W; coef = c31; Om = sm + G::P2; Op = sm + G::P2 + 5 * NC;
+              break;
+            case 1:  // q_{y|x} at c
+              Q = sm + G::QXY + (pc * 2 + 1) * 10 * NC; Fmb = Fpb = sm + G::P1;
+              fpc = cm + 1; coef = c30; Om = sm + G::P2 + 10 * NC; Op = sm + G::P2 + 15 * NC;
+              break;
+            case 2:  // q_{z|x} at c
+              Q = sm + G::QZ + pc * 10 * NC; Fmb = Fpb = sm + G::P1;
+              fpc = cm + 1; coef = c30; Om = sm + G::QZXM; Op = sm + G::QZXP + pc * 5 * NC;
+              break;
+            case 3:  // q_{z|y} at c
+              Q = sm + G::QZ + pc * 10 * NC; Fmb = Fpb = sm + G::P1 + 7 * NC;
+              fpc = cm + W; coef = c31; Om = sm + G::QZYM; Op = sm + G::QZYP + pc * 5 * NC;
+              break;
+            case 4:  // q_{x|z} at c-1
+              Q = sm + G::QXY + (pm * 2 + 0) * 10 * NC; Fmb = sm + G::FZ + pm * 7 * NC;
+              Fpb = sm + G::FZ + pc * 7 * NC; fpc = cm; coef = c32;
+              Om = sm + G::P2 + 20 * NC; Op = sm + G::P2 + 25 * NC;
+              break;
+            default:  // q_{y|z} at c-1
+              Q = sm + G::QXY + (pm * 2 + 1) * 10 * NC; Fmb = sm + G::FZ + pm * 7 * NC;
+              Fpb = sm + G::FZ + pc * 7 * NC; fpc = cm; coef = c32;
+              Om = sm + G::P2 + 30 * NC; Op = sm + G::P2 + 35 * NC;
+              break;
+          }
+          if (kind < 4 || zc) {
+            const TFlux<float> Fm = ld7(Fmb, NC, cm), Fp = ld7(Fpb, NC, fpc);
+            float qa[5], qb[5], oa[5], ob[5];
+            ld5(Q, NC, cm, qa);
+            ld5(Q + 5 * NC, NC, cm, qb);
+            transverse1(E, qa, coef, Fp, Fm, oa);
+            transverse1(E, qb, coef, Fp, Fm, ob);
+            st5(Om, NC, cm, oa);
+            st5(Op, NC, cm, ob);
           }
         }
         bar_sync_n(BAR_COL, NTC);
 
         // ---------------------------------------------- S4: intermediate solves
-        if (act) {
-  #pragma unroll 1
-          for (int rep = 0; rep < 2; ++rep) {
-            const int kind = kq + 3 * rep;
-            const float *L, *Rr;
-            float *O;
-            int lc, dir;
-            bool go;
-            switch (kind) {
-              case 0:  // F^{x|y} at c
-                go = mi >= 0 && inY; dir = 0; L = sm + G::P2 + 5 * NC; lc = me - 1; Rr = sm + G::P2;
-                O = sm + G::P1;
-                break;
-              case 1:  // F^{y|x} at c
-                go = mj >= 0 && inX; dir = 1; L = sm + G::P2 + 15 * NC; lc = me - W;
-                Rr = sm + G::P2 + 10 * NC; O = sm + G::P1 + 7 * NC;
-                break;
-              case 2:  // F^{x|z} at c-1
-                go = zc && mi >= 0; dir = 0; L = sm + G::P2 + 25 * NC; lc = me - 1;
-                Rr = sm + G::P2 + 20 * NC; O = sm + G::P1 + 14 * NC;
-                break;
-              case 3:  // F^{y|z} at c-1
-                go = zc && mj >= 0; dir = 1; L = sm + G::P2 + 35 * NC; lc = me - W;
-                Rr = sm + G::P2 + 30 * NC; O = sm + G::P1 + 21 * NC;
-                break;
-              case 4:  // F^{z|x} at face c-1/2
-                go = c >= zb && inX; dir = 2; L = sm + G::QZXP + pm * 5 * NC; lc = me;
-                Rr = sm + G::QZXM; O = sm + G::FZXY + (pc * 2 + 0) * 7 * NC;
-                break;
-              default:  // F^{z|y} at face c-1/2
-                go = c >= zb && inY; dir = 2; L = sm + G::QZYP + pm * 5 * NC; lc = me;
-                Rr = sm + G::QZYM; O = sm + G::FZXY + (pc * 2 + 1) * 7 * NC;
-                break;
-            }
-            if (go) {
-              float l[5], r[5], F[8];
-              ld5(L, NC, lc, l);
-              ld5(Rr, NC, me, r);
-              face_flux_dir(E, dir, l, r, F);
-              st7(O, NC, me, F);
-            }
+        for (int t = tid; t < tn[2]; t += NTC) {
+          const int e = ttab[tn[6] + t], kind = e >> 12, cm = e & 0xfff;
+          const float *L, *Rr;
+          float *O;
+          int lc, dir;
+          switch (kind) {
+            case 0:  // F^{x|y} at c
+              dir = 0; L = sm + G::P2 + 5 * NC; lc = cm - 1; Rr = sm + G::P2; O = sm + G::P1;
+              break;
+            case 1:  // F^{y|x} at c
+              dir = 1; L = sm + G::P2 + 15 * NC; lc = cm - W; Rr = sm + G::P2 + 10 * NC;
+              O = sm + G::P1 + 7 * NC;
+              break;
+            case 2:  // F^{x|z} at c-1
+              dir = 0; L = sm + G::P2 + 25 * NC; lc = cm - 1; Rr = sm + G::P2 + 20 * NC;
+              O = sm + G::P1 + 14 * NC;
+              break;
+            case 3:  // F^{y|z} at c-1
+              dir = 1; L = sm + G::P2 + 35 * NC; lc = cm - W; Rr = sm + G::P2 + 30 * NC;
+              O = sm + G::P1 + 21 * NC;
+              break;
+            case 4:  // F^{z|x} at face c-1/2
+              dir = 2; L = sm + G::QZXP + pm * 5 * NC; lc = cm; Rr = sm + G::QZXM;
+              O = sm + G::FZXY + (pc * 2 + 0) * 7 * NC;
+              break;
+            default:  // F^{z|y} at face c-1/2
+              dir = 2; L = sm + G::QZYP + pm * 5 * NC; lc = cm; Rr = sm + G::QZYM;
+              O = sm + G::FZXY + (pc * 2 + 1) * 7 * NC;
+              break;
+          }
+          if (kind < 2 || (kind < 4 ? zc : c >= zb)) {
+            float l[5], r[5], F[8];
+            ld5(L, NC, lc, l);
+            ld5(Rr, NC, cm, r);
+            face_flux_dir(E, dir, l, r, F);
+            st7(O, NC, cm, F);
           }
         }
         bar_sync_n(BAR_COL, NTC);
 
         // ---------------------------------------------- S5: final states, theta = 1/2
-        if (act) {
+        for (int t = tid; t < tn[3]; t += NTC) {
+          const int e = ttab[tn[7] + t], kind = e >> 12, cm = e & 0xfff;
           const float *Q, *Ab, *Bmb, *Bpb;
           float *Om, *Op;
           int apc, bpc;
           float k1c, k2c;
-          bool go;
-          if (kq == 0) {  // z at plane c: F^{x|y} in x, F^{y|x} in y
-            go = inX && inY; Q = sm + G::QZ + pc * 10 * NC;
-            Ab = sm + G::P1; apc = me + 1; k1c = ch0;
-            Bmb = Bpb = sm + G::P1 + 7 * NC; bpc = me + W; k2c = ch1;
+          if (kind == 0) {  // z at plane c: F^{x|y} in x, F^{y|x} in y
+            Q = sm + G::QZ + pc * 10 * NC;
+            Ab = sm + G::P1; apc = cm + 1; k1c = ch0;
+            Bmb = Bpb = sm + G::P1 + 7 * NC; bpc = cm + W; k2c = ch1;
             Om = sm + G::QZFM; Op = sm + G::QZFP + pc * 5 * NC;
-          } else if (kq == 1) {  // x at plane c-1: F^{y|z} in y, F^{z|y} in z
-            go = zc && inY; Q = sm + G::QXY + (pm * 2 + 0) * 10 * NC;
-            Ab = sm + G::P1 + 21 * NC; apc = me + W; k1c = ch1;
+          } else if (kind == 1) {  // x at plane c-1: F^{y|z} in y, F^{z|y} in z
+            Q = sm + G::QXY + (pm * 2 + 0) * 10 * NC;
+            Ab = sm + G::P1 + 21 * NC; apc = cm + W; k1c = ch1;
             Bmb = sm + G::FZXY + (pm * 2 + 1) * 7 * NC; Bpb = sm + G::FZXY + (pc * 2 + 1) * 7 * NC;
-            bpc = me; k2c = ch2;
+            bpc = cm; k2c = ch2;
             Om = sm + G::P2; Op = sm + G::P2 + 5 * NC;
           } else {  // y at plane c-1: F^{x|z} in x, F^{z|x} in z
-            go = zc && inX; Q = sm + G::QXY + (pm * 2 + 1) * 10 * NC;
-            Ab = sm + G::P1 + 14 * NC; apc = me + 1; k1c = ch0;
+            Q = sm + G::QXY + (pm * 2 + 1) * 10 * NC;
+            Ab = sm + G::P1 + 14 * NC; apc = cm + 1; k1c = ch0;
             Bmb = sm + G::FZXY + (pm * 2 + 0) * 7 * NC; Bpb = sm + G::FZXY + (pc * 2 + 0) * 7 * NC;
-            bpc = me; k2c = ch2;
+            bpc = cm; k2c = ch2;
             Om = sm + G::P2 + 10 * NC; Op = sm + G::P2 + 15 * NC;
           }
-          if (go) {
-            const TFlux<float> Am = ld7(Ab, NC, me), Ap = ld7(Ab, NC, apc);
-            const TFlux<float> Bm = ld7(Bmb, NC, me), Bp = ld7(Bpb, NC, bpc);
+          if (kind == 0 || zc) {
+            const TFlux<float> Am = ld7(Ab, NC, cm), Ap = ld7(Ab, NC, apc);
+            const TFlux<float> Bm = ld7(Bmb, NC, cm), Bp = ld7(Bpb, NC, bpc);
             float qa[5], qb[5], oa[5], ob[5];
-            ld5(Q, NC, me, qa);
-            ld5(Q + 5 * NC, NC, me, qb);
+            ld5(Q, NC, cm, qa);
+            ld5(Q + 5 * NC, NC, cm, qb);
             transverse2(E, qa, k1c, Ap, Am, k2c, Bp, Bm, oa);
             transverse2(E, qb, k1c, Ap, Am, k2c, Bp, Bm, ob);
-            st5(Om, NC, me, oa);
-            st5(Op, NC, me, ob);
+            st5(Om, NC, cm, oa);
+            st5(Op, NC, cm, ob);
           }
         }
         bar_sync_n(BAR_COL, NTC);
@@ -468,32 +554,38 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
         // The fluxes go to the update warps' buffers: x and y faces of plane
         // c-1, z face c-1/2 (slot c & 1).  The buffers are written once the
         // update of plane c-2 has released them, and handed over after.
+        // The list holds at most one task per column thread.
         {
           bool go = false;
           float F[8];
-          if (act) {
+          int kind = 0, cm = 0;
+          if (tid < tn[4]) {
+            const int e = ttab[tn[8] + tid];
+            kind = e >> 12;
+            cm = e & 0xfff;
             const float *L, *Rr;
             int lc;
-            if (kq == 0) {
-              go = zc && mi >= 0 && inY; L = sm + G::P2 + 5 * NC; lc = me - 1; Rr = sm + G::P2;
-            } else if (kq == 1) {
-              go = zc && mj >= 0 && inX; L = sm + G::P2 + 15 * NC; lc = me - W; Rr = sm + G::P2 + 10 * NC;
+            if (kind == 0) {
+              go = zc; L = sm + G::P2 + 5 * NC; lc = cm - 1; Rr = sm + G::P2;
+            } else if (kind == 1) {
+              go = zc; L = sm + G::P2 + 15 * NC; lc = cm - W; Rr = sm + G::P2 + 10 * NC;
             } else {
-              go = c >= zb && inX && inY; L = sm + G::QZFP + pm * 5 * NC; lc = me; Rr = sm + G::QZFM;
+              go = c >= zb; L = sm + G::QZFP + pm * 5 * NC; lc = cm; Rr = sm + G::QZFM;
             }
             if (go) {
               float l[5], r[5];
               ld5(L, NC, lc, l);
-              ld5(Rr, NC, me, r);
-              face_flux_dir(E, kq, l, r, F);
+              ld5(Rr, NC, cm, r);
+              face_flux_dir(E, kind, l, r, F);
             }
           }
           if (c >= zb + 2) bar_sync_n(BAR_FREE, NT);
           if (go) {
-            float *O = (kq == 0)   ? sm + G::UF + mj * (TX + 1) + mi
-                       : (kq == 1) ? sm + G::UF + NXF + mj * TX + mi
-                                   : sm + G::FFZ + (c & 1) * 8 * NZF + mj * TX + mi;
-            st8(O, (kq == 2) ? NZF : NUF, 0, F);
+            const int ci = cm % W - 1, cj = cm / W - 1;
+            float *O = (kind == 0)   ? sm + G::UF + cj * (TX + 1) + ci
+                       : (kind == 1) ? sm + G::UF + NXF + cj * TX + ci
+                                     : sm + G::FFZ + (c & 1) * 8 * NZF + cj * TX + ci;
+            st8(O, (kind == 2) ? NZF : NUF, 0, F);
           }
           if (c >= zb + 1) {
             __threadfence_block();

@@ -41,9 +41,18 @@ __device__ __forceinline__ R rcopysign(R m, R s) { return copysign(m, s); }
 
 // ---------------------------------------------------------------- PPM
 // MC-limited slope, fourth-order interface value, CW84 parabola limiter
-// (Colella & Woodward 1984, named in Sec. 3.2).
+// (Colella & Woodward 1984, named in Sec. 3.2).  Here and in the corner
+// coupling below, the FP32 instantiation takes the same values in select form
+// (every lane computes both outcomes, so lanes that take different limiter
+// branches do not split their warp); the FP64 one keeps the branch form, the
+// oracle's expressions one for one.
 template <class R>
 __device__ __forceinline__ R mc_slope(R sm, R s0, R sp) {
+  if constexpr (sizeof(R) == 4) {
+    const float dc = 0.5f * (sp - sm), dl = s0 - sm, dr = sp - s0;
+    const float m = fminf(fabsf(dc), fminf(2.0f * fabsf(dl), 2.0f * fabsf(dr)));
+    return (dl * dr > 0.0f) ? copysignf(m, dc) : 0.0f;
+  }
   R dc = R(0.5) * (sp - sm);
   R dl = s0 - sm;
   R dr = sp - s0;
@@ -72,6 +81,18 @@ __device__ __forceinline__ void ppm_coeffs(R s0, R s1, R s2, R s3, R s4, R &sLo,
   R sL = interface_value(s1, s2, dm, d0);
   R sR = interface_value(s2, s3, d0, dp);
   R si = s2;
+  if constexpr (sizeof(R) == 4) {
+    const bool flat = (sR - si) * (si - sL) <= 0.0f;
+    const float D = sR - sL, M = si - 0.5f * (sL + sR);
+    const float DM = D * M, D26 = D * D * (1.0f / 6.0f);
+    const bool cl = DM > D26, cr = !cl && (-D26 > DM);
+    const float nL = flat ? si : (cl ? 3.0f * si - 2.0f * sR : sL);
+    const float nR = flat ? si : (cr ? 3.0f * si - 2.0f * sL : sR);
+    sLo = nL;
+    sRo = nR;
+    s6o = 6.0f * (si - 0.5f * (nL + nR));
+    return;
+  }
   if ((sR - si) * (si - sL) <= R(0)) {
     sL = si;
     sR = si;
@@ -212,6 +233,18 @@ __device__ __forceinline__ void trace_cell(const Eos<R> &E, const R (&s)[5][5], 
       d0p = ref[4] - ppm_ip(sL[4], sR[4], s6[4], sig0);
       d0n = ref[NV] - ppm_ip(sL[NV], sR[NV], s6[NV], sig0);
     }
+    if constexpr (sizeof(R) == 4) {
+      // the entropy/shear wave's direction varies from lane to lane: selects
+      const bool w1 = lam1 > R(0);
+      const R e0 = ref[0] - ppm_ip(sL[0], sR[0], s6[0], sig1);
+      const R e4 = ref[4] - ppm_ip(sL[4], sR[4], s6[4], sig1);
+      const R ea = ref[TV1] - ppm_ip(sL[TV1], sR[TV1], s6[TV1], sig1);
+      const R eb = ref[TV2] - ppm_ip(sL[TV2], sR[TV2], s6[TV2], sig1);
+      d1r = w1 ? e0 : R(0);
+      d1p = w1 ? e4 : R(0);
+      d1a = w1 ? ea : R(0);
+      d1b = w1 ? eb : R(0);
+    } else
     if (lam1 > R(0)) {
       d1r = ref[0] - ppm_ip(sL[0], sR[0], s6[0], sig1);
       d1p = ref[4] - ppm_ip(sL[4], sR[4], s6[4], sig1);
@@ -236,6 +269,17 @@ __device__ __forceinline__ void trace_cell(const Eos<R> &E, const R (&s)[5][5], 
       d2p = ref[4] - ppm_im(sL[4], sR[4], s6[4], sig2);
       d2n = ref[NV] - ppm_im(sL[NV], sR[NV], s6[NV], sig2);
     }
+    if constexpr (sizeof(R) == 4) {
+      const bool w1 = lam1 < R(0);
+      const R e0 = ref[0] - ppm_im(sL[0], sR[0], s6[0], sig1);
+      const R e4 = ref[4] - ppm_im(sL[4], sR[4], s6[4], sig1);
+      const R ea = ref[TV1] - ppm_im(sL[TV1], sR[TV1], s6[TV1], sig1);
+      const R eb = ref[TV2] - ppm_im(sL[TV2], sR[TV2], s6[TV2], sig1);
+      d1r = w1 ? e0 : R(0);
+      d1p = w1 ? e4 : R(0);
+      d1a = w1 ? ea : R(0);
+      d1b = w1 ? eb : R(0);
+    } else
     if (lam1 < R(0)) {
       d1r = ref[0] - ppm_im(sL[0], sR[0], s6[0], sig1);
       d1p = ref[4] - ppm_im(sL[4], sR[4], s6[4], sig1);
@@ -376,58 +420,47 @@ __device__ __forceinline__ void riemann(const Eos<R> &E, const R (&qL)[5], const
   out[7] = pg;
 }
 
-// The same two-shock solve for the FP32 path, written with reciprocals and
-// reciprocal square roots (MUFU) instead of divisions and square roots.  With
-// x = max(1 + K (p - p_s)/p_s, 1e-10) and r = x^{-1/2}: W = C x r, 1/W = r/C,
-// and the Newton slope 1/Z = (W^2 + C^2)/(2 W^3) = (x + 1) r^3 / (2 C).
+// FP32 Godunov state sampled from side o (sign s = +1 for the left side, -1
+// for the right one), written with selects instead of branches: every lane
+// forms the shock and the rarefaction quantities and picks its case, so a
+// warp whose faces meet different wave patterns does not split.
 __device__ __forceinline__ void sample_side_fast(const Eos<float> &E, float ro, float iro, float uo,
                                                  float t1o, float t2o, float po, float Wo, float iWo,
                                                  float co, float s, float pstar, float ustar,
                                                  float (&g)[5]) {
-  // 1/rho*: across the shock curve, or from dp = c^2 d rho (linearised)
-  float d = E.linear ? 1.0f / (ro + (pstar - po) / (co * co)) : iro - (pstar - po) * (iWo * iWo);
-  float rhos = 1.0f / d;
-  float ird = d;
-  if (!(rhos >= E.small_dens)) {
-    rhos = E.small_dens;
-    ird = 1.0f / E.small_dens;
-  }
+  const float d = E.linear ? 1.0f / (ro + (pstar - po) / (co * co)) : iro - (pstar - po) * (iWo * iWo);
+  const float rq = 1.0f / d;
+  const bool low = !(rq >= E.small_dens);
+  const float rhos = low ? E.small_dens : rq;
+  const float ird = low ? 1.0f / E.small_dens : d;
   const float cs2 = E.gamma * pstar * ird;
   const float cs = cs2 * rsqrtf(cs2);
-  int star;
-  float w = -1.0f;
-  if (pstar > po) {
-    const float S = uo - s * (Wo * iro);
-    star = (s * S < 0.0f) ? 1 : 0;
-  } else {
-    const float H = uo - s * co;
-    const float T = ustar - s * cs;
-    if (s * H >= 0.0f) {
-      star = 0;
-    } else if (s * T < 0.0f) {
-      star = 1;
-    } else {
-      star = 2;
-      w = H / (H - T);
-    }
-  }
-  if (star == 0) {
-    g[0] = ro;
-    g[1] = uo;
-    g[4] = po;
-  } else if (star == 1) {
-    g[0] = rhos;
-    g[1] = ustar;
-    g[4] = pstar;
-  } else {
-    g[0] = (1.0f - w) * ro + w * rhos;
-    g[1] = (1.0f - w) * uo + w * ustar;
-    g[4] = (1.0f - w) * po + w * pstar;
-  }
+  const bool shock = pstar > po;
+  const float S = uo - s * (Wo * iro);
+  const float H = uo - s * co;
+  const float T = ustar - s * cs;
+  const bool side_r = s * H >= 0.0f;     // rarefaction: head moving away
+  const bool star_r = s * T < 0.0f;      // rarefaction: tail moving away
+  const bool star = shock ? (s * S < 0.0f) : (!side_r && star_r);
+  const bool fan = !shock && !side_r && !star_r;
+  const float w = H / (H - T);
+  const float lr = (1.0f - w) * ro + w * rhos;
+  const float lu = (1.0f - w) * uo + w * ustar;
+  const float lp = (1.0f - w) * po + w * pstar;
+  g[0] = fan ? lr : (star ? rhos : ro);
+  g[1] = fan ? lu : (star ? ustar : uo);
+  g[4] = fan ? lp : (star ? pstar : po);
   g[2] = t1o;
   g[3] = t2o;
 }
 
+// The same two-shock solve for the FP32 path, written with reciprocals and
+// reciprocal square roots (MUFU) instead of divisions and square roots.  With
+// x = max(1 + K (p - p_s)/p_s, 1e-10) and r = x^{-1/2}: W = C x r, 1/W = r/C,
+// and the Newton slope 1/Z = (W^2 + C^2)/(2 W^3) = (x + 1) r^3 / (2 C).  Each
+// lane leaves the Newton loop when it has converged: the lanes that are done
+// go on to sample while the others iterate, which hides the loop's latency
+// better than holding the whole warp to its slowest lane.
 __device__ __forceinline__ void riemann_fast(const Eos<float> &E, const float (&qL)[5],
                                              const float (&qR)[5], float (&out)[8]) {
   const float iRL = 1.0f / qL[0], iRR = 1.0f / qR[0];
@@ -461,20 +494,19 @@ __device__ __forceinline__ void riemann_fast(const Eos<float> &E, const float (&
   const float ustar = (pL - pR + WL * uL + WR * uR) / (WL + WR);
   const float pstar = p;
   float g[5];
-  if (ustar > 0.0f) {
-    sample_side_fast(E, qL[0], iRL, qL[1], qL[2], qL[3], qL[4], WL, rL * iCL, cL, 1.0f, pstar,
-                     ustar, g);
-  } else if (ustar < 0.0f) {
-    sample_side_fast(E, qR[0], iRR, qR[1], qR[2], qR[3], qR[4], WR, rR * iCR, cR, -1.0f, pstar,
-                     ustar, g);
-  } else {
-    float gl[5], gr[5];
-    sample_side_fast(E, qL[0], iRL, qL[1], qL[2], qL[3], qL[4], WL, rL * iCL, cL, 1.0f, pstar,
-                     ustar, gl);
-    sample_side_fast(E, qR[0], iRR, qR[1], qR[2], qR[3], qR[4], WR, rR * iCR, cR, -1.0f, pstar,
-                     ustar, gr);
+  {
+    // upwind side: left for u* >= 0 (u* = 0 also samples the right side below)
+    const bool rs = ustar < 0.0f;
+    sample_side_fast(E, rs ? qR[0] : qL[0], rs ? iRR : iRL, rs ? qR[1] : qL[1],
+                     rs ? qR[2] : qL[2], rs ? qR[3] : qL[3], rs ? qR[4] : qL[4], rs ? WR : WL,
+                     rs ? rR * iCR : rL * iCL, rs ? cR : cL, rs ? -1.0f : 1.0f, pstar, ustar, g);
+    if (ustar == 0.0f) {
+      float gr[5];
+      sample_side_fast(E, qR[0], iRR, qR[1], qR[2], qR[3], qR[4], WR, rR * iCR, cR, -1.0f,
+                       pstar, ustar, gr);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) g[v] = 0.5f * (gl[v] + gr[v]);
+      for (int v = 0; v < 5; ++v) g[v] = 0.5f * (g[v] + gr[v]);
+    }
   }
   if (g[0] < E.small_dens) g[0] = E.small_dens;
   if (g[4] < E.small_pres) g[4] = E.small_pres;
@@ -561,6 +593,18 @@ __device__ __forceinline__ void transverse1(const Eos<R> &E, const R (&q)[5], R 
   m1 = m1 - cdt * (Fp.f[2] - Fm.f[2]);
   m2 = m2 - cdt * (Fp.f[3] - Fm.f[3]);
   R en = rhoe - cdt * rhoe_flux_diff(Fp, Fm);
+  if constexpr (sizeof(R) == 4) {
+    const bool bad = rn < E.small_dens;
+    const R irn = R(1) / rn;
+    R p = E.gm1 * en;
+    if (p < E.small_pres) p = E.small_pres;
+    out[0] = bad ? q[0] : rn;
+    out[1] = bad ? q[1] : m0 * irn;
+    out[2] = bad ? q[2] : m1 * irn;
+    out[3] = bad ? q[3] : m2 * irn;
+    out[4] = bad ? q[4] : p;
+    return;
+  }
   if (rn < E.small_dens) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) out[v] = q[v];
@@ -599,6 +643,18 @@ __device__ __forceinline__ void transverse2(const Eos<R> &E, const R (&q)[5], R 
   m1 = m1 - c2 * (Bp.f[2] - Bm.f[2]);
   m2 = m2 - c2 * (Bp.f[3] - Bm.f[3]);
   en = en - c2 * rhoe_flux_diff(Bp, Bm);
+  if constexpr (sizeof(R) == 4) {
+    const bool bad = rn < E.small_dens;
+    const R irn = R(1) / rn;
+    R p = E.gm1 * en;
+    if (p < E.small_pres) p = E.small_pres;
+    out[0] = bad ? q[0] : rn;
+    out[1] = bad ? q[1] : m0 * irn;
+    out[2] = bad ? q[2] : m1 * irn;
+    out[3] = bad ? q[3] : m2 * irn;
+    out[4] = bad ? q[4] : p;
+    return;
+  }
   if (rn < E.small_dens) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) out[v] = q[v];
