@@ -368,6 +368,47 @@ def field_errors(plan, spec, got, ref):
             for c, n in enumerate(names)}
 
 
+def mixed256_errors(H, torch):
+    """256^3 periodic box, sigma = 1.0, a 1/51 -> 1/49 over 50 steps: the mixed
+    and the FP64 persistent forms from the same initial state, each with its
+    own CFL steps; per conserved field the normwise relative L-inf and L1
+    difference after step 50, and each form's rate over the 50 steps."""
+    w = make_workload("mixed256")
+    cells = w.level.valid_cells()
+    out = {"workload": w.name, "steps": w.nsteps, "cells": cells}
+    states = {}
+    for prec in ("mixed", "fp64"):
+        plan = H.Plan(w.level, gamma=w.gamma, cfl=w.cfl, precision=prec, batching="persistent",
+                      autotune=1)
+        lev = H.make_level(plan, w.state, w.grav)
+        snap = lev.state[0].clone()
+        a = torch.tensor(a_schedule_for(w, w.nsteps), dtype=torch.float64, device="cuda")
+        dt = torch.zeros(w.nsteps + 1, dtype=torch.float64, device="cuda")
+        plan.run(lev, a, dt, w.nsteps, compute_dt0=True, use_graph=True)
+        torch.cuda.synchronize()
+        lev.state[0].copy_(snap)
+        lev.cur = 0
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(plan.torch_stream)
+        plan.run(lev, a, dt, w.nsteps, compute_dt0=True, use_graph=True)
+        e1.record(plan.torch_stream)
+        torch.cuda.synchronize()
+        rc, flags = plan.status()
+        out[prec] = {"status": rc, "value": cells * w.nsteps / (e0.elapsed_time(e1) / 1e3),
+                     "unit": "zone-updates/s", "dt_last": float(dt[w.nsteps - 1])}
+        states[prec] = lev.state[lev.cur].clone()
+        keep = plan
+        del lev, snap
+        if prec == "fp64":
+            out["fields"] = field_errors(keep, w.level, states["mixed"], states["fp64"])
+        keep.close()
+    out["metric"] = "normwise relative over the valid cells: max|d|/max|ref| and sum|d|/sum|ref|"
+    del states
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, w):
     import torch
     from paper_1301_4498_gb300 import hydro as H
@@ -444,6 +485,38 @@ def run_ours(args, w):
     fill_ms = prof["fill_ms"] / max(1, prof["timed_fills"])
     flops = ALG_FLOPS_PER_ZONE[args.precision]
     shape, (tx, ty) = plan.tile_shape()
+
+    # the workload's whole prescribed run (the large level: 100 steps, a from
+    # 1/51 to 1/31) in one CUDA-graph replay from the initial state, with the
+    # device status read at its end
+    prescribed = None
+    if not args.no_prescribed and w.nsteps > K:
+        restore()
+        nps = w.nsteps
+        a_all = torch.tensor(a_schedule_for(w, nps), dtype=torch.float64, device="cuda")
+        dt_all = torch.zeros(nps + 1, dtype=torch.float64, device="cuda")
+        plan.run(lev, a_all, dt_all, nps, compute_dt0=True, use_graph=True)  # capture + first run
+        torch.cuda.synchronize()
+        restore()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        plan.run(lev, a_all, dt_all, nps, compute_dt0=True, use_graph=True)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        pms = p0.elapsed_time(p1)
+        prc, pflags = plan.status()
+        prescribed = {"steps": nps, "a_first": float(a_all[0]), "a_last": float(a_all[nps]),
+                      "status": prc, "status_flags": pflags,
+                      "value": cells * nps / (pms / 1e3), "unit": "zone-updates/s",
+                      "ms_per_step": pms / nps, "dt_first": float(dt_all[0]),
+                      "dt_last": float(dt_all[nps - 1]),
+                      "how": "one CUDA-graph replay of every step (ghost fill, fused advance, CFL "
+                             "dt) from the initial state, timed with CUDA events"}
+        if prc != H.NYX_OK:
+            raise SystemExit(f"device status after the prescribed run: {prc} flags {pflags}")
+        del a_all, dt_all
+        restore()
 
     # end to end through the C ABI with pinned host buffers: the level's valid
     # cells in, the new valid cells and dt out, every step
@@ -588,6 +661,13 @@ def run_ours(args, w):
                                         "note": "whole step (fill, advance, dt) timed"}}
             p64.close()
 
+    # the 256^3 sigma = 1 box over its 50 prescribed steps: the mixed path's
+    # per-field error against the FP64 path (itself the oracle's arithmetic,
+    # bit for bit), both persistent and graph-captured
+    m256 = None
+    if not args.no_mixed256 and args.workload == "large" and args.precision == "mixed":
+        m256 = mixed256_errors(H, torch)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = oracle_sample(args.workload, w, budget_s=args.cpu_budget)
@@ -622,6 +702,8 @@ def run_ours(args, w):
             "variants": variants,
             "fp64_comparison": side,
             "mixed_vs_fp64": errors,
+            "prescribed_run": prescribed,
+            "mixed256_50_steps": m256,
             "clocks": clk,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -1124,6 +1206,10 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-prescribed", action="store_true",
+                    help="skip the workload's whole prescribed run (100 steps on the large level)")
+    ap.add_argument("--no-mixed256", action="store_true",
+                    help="skip the 256^3 sigma = 1 box's 50-step mixed-vs-FP64 error leg")
     ap.add_argument("--traffic-per-zone", type=float, default=0.0,
                     help="DRAM bytes per zone of the advance kernel from an ncu capture")
     ap.add_argument("--keep-fluxes", type=int, default=1,

@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
+from gates import MIXED_GATES
 from paper_1301_4498_gb300 import workloads as W
 
 import test_oracle_amr as TA
@@ -139,8 +140,12 @@ def test_two_level_step_mixed_within_the_mixed_gates():
     torch.cuda.synchronize()
     assert cp.status() == (0, 0) and fp.status() == (0, 0)
     cn, fn, _, _ = oracle.amr_step(w.level, fine, P, cs, fs, cg, fg, a_old=a0, a_new=a1, dt=dtv)
-    assert _norm_rel(cp.from_device(lc.current, 6), cn) <= 2e-3
-    assert _norm_rel(fp.from_device(lf.current, 6), fn) <= 2e-3
+    e_mixed = _norm_rel(cp.from_device(lc.current, 6), cn)
+    print('mixed vs oracle, worst field L-inf:', e_mixed)
+    assert e_mixed <= MIXED_GATES["linf"]
+    e_mixed = _norm_rel(fp.from_device(lf.current, 6), fn)
+    print('mixed vs oracle, worst field L-inf:', e_mixed)
+    assert e_mixed <= MIXED_GATES["linf"]
     amr.close(); fp.close(); cp.close()
 
 

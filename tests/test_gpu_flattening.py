@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
+from gates import MIXED_GATES
 from paper_1301_4498_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -73,7 +74,9 @@ def test_mixed_within_the_gate(shape):
     w = _case()
     got = _run_gpu(w, 2, shape=shape, precision="mixed", flattening=True)
     ref = _ref(w)
-    assert _norm_rel(got, ref) <= 2e-3
+    e_mixed = _norm_rel(got, ref)
+    print('mixed vs oracle, worst field L-inf:', e_mixed)
+    assert e_mixed <= MIXED_GATES["linf"]
     # flattening changes the answer by much more than the gate's round-off
     plain, _, _ = oracle.run(w.level, oracle.OracleParams(gamma=w.gamma, cfl=w.cfl), w.state,
                              w.grav, w.a_sched, 2)

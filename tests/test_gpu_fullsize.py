@@ -91,6 +91,17 @@ def test_uneven_512_boxes():
         check(err, precision)
 
 
+# Per field (L-inf, L1) gates of the mixed path against the FP64 path after
+# the 50 steps of the 256^3 sigma = 1 box: twice the measured errors (L-inf
+# 2.6e-3, 4.1e-3, 5.8e-3, 1.6e-3, 1.2e-3, 1.1e-3; L1 6.4e-7, 2.9e-6, 2.9e-6,
+# 2.9e-6, 6.2e-7, 6.2e-7 for rho, m_x, m_y, m_z, rhoE, rhoe), so a doubling of
+# the error fails.  The L-inf peaks sit at shocks of the sigma = 1 field, where
+# a limiter or sampling branch taken differently in FP32 moves a jump by a
+# fraction of a cell.
+GATES_50 = {"rho": (5.3e-3, 1.3e-6), "m_x": (8.2e-3, 5.8e-6), "m_y": (1.2e-2, 5.9e-6),
+            "m_z": (3.3e-3, 5.8e-6), "rhoE": (2.5e-3, 1.3e-6), "rhoe": (2.2e-3, 1.3e-6)}
+
+
 def test_mixed_256_sigma1():
     w = W.comoving_box(n=256, sigma=1.0, seed=4, nsteps=50, mixed=True)
     ref2, _, _ = oracle.run(w.level, oracle.OracleParams(gamma=w.gamma, cfl=w.cfl), w.state,
@@ -104,7 +115,7 @@ def test_mixed_256_sigma1():
     err50 = field_errors(S32, S64)
     print("mixed256 50 steps mixed vs FP64 GPU (L-inf, L1):", err50)
     for k, (linf, l1) in err50.items():
-        assert l1 <= 1e-3 and linf <= 0.1, (k, err50)
+        assert linf <= GATES_50[k][0] and l1 <= GATES_50[k][1], (k, err50)
 
 
 def test_large_level_sampled_boxes():

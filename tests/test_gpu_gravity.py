@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
+from gates import MIXED_GATES
 from paper_1301_4498_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -119,5 +120,7 @@ def test_predict_then_correct_mixed_within_the_gate():
     plan.correct(lev, a[:1], a[1:], d[:1], lev.grav, gn)
     torch.cuda.synchronize()
     assert plan.status() == (0, 0)
-    assert _norm_rel(plan.from_device(lev.current, 6), ref) <= 2e-3
+    e_mixed = _norm_rel(plan.from_device(lev.current, 6), ref)
+    print('mixed vs oracle, worst field L-inf:', e_mixed)
+    assert e_mixed <= MIXED_GATES["linf"]
     plan.close()

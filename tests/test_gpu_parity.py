@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
+from gates import FP64_TOL, MIXED_GATES  # noqa: F401  (re-exported to the other GPU tests)
 from paper_1301_4498_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -21,10 +22,7 @@ if not torch.cuda.is_available():
 
 from paper_1301_4498_gb300 import hydro as H  # noqa: E402
 
-FP64_TOL = 1e-12
 FIELDS = ("rho", "m_x", "m_y", "m_z", "rhoE", "rhoe")
-# mixed path vs FP64 oracle after the stated number of steps (normwise relative)
-MIXED_GATES = {"linf": 2e-3, "l1": 2e-5}
 
 
 def oracle_params(w, **kw):

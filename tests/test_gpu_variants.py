@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
+from gates import MIXED_GATES
 from paper_1301_4498_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -66,7 +67,9 @@ def test_variant_mixed_within_the_gate(rec, rs, shape):
     plan.run(lev, a, dt, 2, compute_dt0=True, use_graph=False)
     torch.cuda.synchronize()
     assert plan.status() == (0, 0)
-    assert _norm_rel(plan.from_device(lev.current, 6), ref) <= 2e-3
+    e_mixed = _norm_rel(plan.from_device(lev.current, 6), ref)
+    print('mixed vs oracle, worst field L-inf:', e_mixed)
+    assert e_mixed <= MIXED_GATES["linf"]
     plan.close()
 
 
