@@ -485,6 +485,12 @@ def run_ours(args, w):
     fill_ms = prof["fill_ms"] / max(1, prof["timed_fills"])
     flops = ALG_FLOPS_PER_ZONE[args.precision]
     shape, (tx, ty) = plan.tile_shape()
+    tcls, ttrials, tlaunches = plan.tune_info()
+    tuning = {"box_size_classes": tcls, "trial_launches": ttrials,
+              "fused_launches_per_advance": tlaunches,
+              "how": "per box-size class, one wave of work items per candidate (tile shape x "
+                     "resident CTAs per SM); choices cached in a JSON file keyed by GPU, SM count, "
+                     "precision, scheme variant and box extent (0 trials: all from the cache)"}
 
     # the workload's whole prescribed run (the large level: 100 steps, a from
     # 1/51 to 1/31) in one CUDA-graph replay from the initial state, with the
@@ -703,6 +709,7 @@ def run_ours(args, w):
             "fp64_comparison": side,
             "mixed_vs_fp64": errors,
             "prescribed_run": prescribed,
+            "autotune": tuning,
             "mixed256_50_steps": m256,
             "clocks": clk,
             "e2e": e2e,

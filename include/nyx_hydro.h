@@ -99,7 +99,7 @@ typedef struct {
   int precision;           /* NYX_FP64 or NYX_MIXED */
   int grav_corrector;      /* 1: Step 6 gravity corrector */
   int batching;            /* NYX_PERSISTENT or NYX_PER_BOX */
-  int autotune;            /* 1: time the tile shapes once and keep the fastest */
+  int autotune;            /* 1: tune the tile shape per box-size class (nyx_hydro_tune_info) */
   int keep_fluxes;         /* 1: keep the final fluxes of the last advance */
   int coarse_fine;         /* 1: the level is the fine level of a nyx_amr pair: ghost
                               cells that no box of the level covers are left to
@@ -256,6 +256,23 @@ int nyx_hydro_step_host_valid(nyx_plan *plan, nyx_level *level, const double *ho
 int nyx_hydro_tile_shape(int shape, int *tx, int *ty);
 int nyx_hydro_set_tile_shape(nyx_plan *plan, int shape);
 int nyx_hydro_get_tile_shape(const nyx_plan *plan, int *shape);
+
+/* The autotuner of a persistent plan (params.autotune = 1; runs before the
+ * first advance, outside any stream capture).  Analogue of the paper's
+ * knapsack / space-filling-curve distribution of grids over processors
+ * (Sec. 5.1), which balances work by box size: the level's boxes are grouped
+ * into box-size classes (equal extents), and each class gets the tile shape
+ * and resident CTAs per SM that run one full wave of its work items in the
+ * least time per zone.  Classes with the same choice share one launch; the
+ * advance makes one launch per distinct choice.  Choices are kept in a JSON
+ * file keyed by GPU name, SM count, precision, scheme variant and box extent
+ * -- $NYX_TUNE_CACHE if set (empty: no file), else _tune_cache.json beside
+ * libnyxhydro.so -- and a class found there is not timed again.  After the
+ * tuning, *classes receives the number of box-size classes, *trials the
+ * trial launches it made (0: every class came from the file) and *launches
+ * the fused launches of one advance.  Any output pointer may be NULL.
+ * NYX_EINVAL for a null plan. */
+int nyx_hydro_tune_info(const nyx_plan *plan, int *classes, int *trials, int *launches);
 
 /* Work list of the fused persistent kernel for a level of nbox boxes with
  * interior extents n[3b], n[3b+1], n[3b+2] (x, y, z) and column tiles of

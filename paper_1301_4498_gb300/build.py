@@ -78,7 +78,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if relink:
         objs = [os.path.join(BUILD, u.replace(".cu", ".o")) for u in UNITS]
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
+        cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{r.stderr}")

@@ -3,13 +3,17 @@
 // balance of the paper's Sec. 5.1 distribution), CUDA-graph capture, status
 // and the C ABI of include/nyx_hydro.h.
 #include <cuda_runtime.h>
+#include <dlfcn.h>
 
 #include <algorithm>
 #include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <sstream>
 #include <map>
 #include <queue>
 #include <string>
@@ -388,6 +392,10 @@ void free_plan(nyx_plan *P) {
   cudaFree(P->d_flux_off);
   for (auto &it : P->d_items) cudaFree(it);
   for (auto &it : P->d_items_grp) cudaFree(it);
+  for (auto &pt : P->parts) {
+    cudaFree(pt.d_items);
+    cudaFree(pt.d_items_grp);
+  }
   for (auto &e : P->ev_grp) cudaEventDestroy(e);
   if (P->copy_stream) cudaStreamDestroy(P->copy_stream);
   for (auto &r : P->d_rects_grp) cudaFree(r);
@@ -492,6 +500,43 @@ FusedArgs fused_args(nyx_plan *P, const double *S, const double *G, double *Sn,
   return a;
 }
 
+// The fused advance over the whole level (g < 0) or over read-back group g:
+// one launch of the plan's shape, or one per part of the autotuner's
+// per-class choice.
+int launch_level(nyx_plan *P, FusedArgs a, int g, cudaStream_t st) {
+  if (P->parts.empty()) {
+    const int s = P->shape;
+    if (g < 0) {
+      a.items = P->d_items[s];
+      a.nitems = P->nitems[s];
+    } else {
+      a.items = P->d_items_grp[s] + P->grp_off[s][g];
+      a.nitems = P->grp_off[s][g + 1] - P->grp_off[s][g];
+    }
+    if (a.nitems > 0) {
+      int e = launch_fused(P->prm.precision, s, a, std::min(P->max_grid[s], a.nitems), st);
+      if (e) return cuda_fail((cudaError_t)e, "fused advance launch");
+      P->launches += 1;
+    }
+    return NYX_OK;
+  }
+  for (const auto &pt : P->parts) {
+    if (g < 0) {
+      a.items = pt.d_items;
+      a.nitems = pt.nitems;
+    } else {
+      a.items = pt.d_items_grp + pt.grp_off[g];
+      a.nitems = pt.grp_off[g + 1] - pt.grp_off[g];
+    }
+    if (a.nitems > 0) {
+      int e = launch_fused(P->prm.precision, pt.shape, a, std::min(pt.grid, a.nitems), st);
+      if (e) return cuda_fail((cudaError_t)e, "fused advance launch");
+      P->launches += 1;
+    }
+  }
+  return NYX_OK;
+}
+
 // One advance of state[cur] into state[1-cur].  With host_out (a fused plan
 // whose read-back groups are set up), the advance runs one launch per box
 // group, each followed by the group's read-back into host_out.
@@ -526,25 +571,13 @@ int do_advance(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_n
       int rc = tune_shape(P, a);
       if (rc) return rc;
     }
-    const int s = P->shape;
     if (host_out && P->ngrp > 1) {
       for (int g = 0; g < P->ngrp; ++g) {
-        a.items = P->d_items_grp[s] + P->grp_off[s][g];
-        a.nitems = P->grp_off[s][g + 1] - P->grp_off[s][g];
-        if (a.nitems > 0) {
-          int e = launch_fused(P->prm.precision, s, a, std::min(P->max_grid[s], a.nitems),
-                               P->stream);
-          if (e) return cuda_fail((cudaError_t)e, "fused advance launch");
-          P->launches += 1;
-        }
+        if (int rc = launch_level(P, a, g, P->stream)) return rc;
         if (int rc = read_back_group(P, Sn, g, host_out, P->stream)) return rc;
       }
     } else {
-      a.items = P->d_items[s];
-      a.nitems = P->nitems[s];
-      int e = launch_fused(P->prm.precision, s, a, std::min(P->max_grid[s], a.nitems), P->stream);
-      if (e) return cuda_fail((cudaError_t)e, "fused advance launch");
-      P->launches += 1;
+      if (int rc = launch_level(P, a, -1, P->stream)) return rc;
     }
   }
   }
@@ -559,13 +592,35 @@ int do_advance(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_n
   return NYX_OK;
 }
 
+// A part's items regrouped by the read-back groups [gb[g], gb[g+1]) of boxes.
+int part_groups(nyx_plan::RunPart &pt, const std::vector<int> &gb) {
+  const int ng = (int)gb.size() - 1;
+  std::vector<WorkItem> it;
+  it.reserve(pt.h_items.size());
+  pt.grp_off.assign(1, 0);
+  for (int g = 0; g < ng; ++g) {
+    for (const WorkItem &w : pt.h_items)
+      if (w.box >= gb[g] && w.box < gb[g + 1]) it.push_back(w);
+    pt.grp_off.push_back((int)it.size());
+  }
+  cudaFree(pt.d_items_grp);
+  pt.d_items_grp = nullptr;
+  CK(cudaMalloc(&pt.d_items_grp, sizeof(WorkItem) * std::max<size_t>(1, it.size())));
+  CK(cudaMemcpy(pt.d_items_grp, it.data(), sizeof(WorkItem) * it.size(), cudaMemcpyHostToDevice));
+  return NYX_OK;
+}
+
 // Read-back groups of nyx_hydro_step_host_valid (fused plans): up to 16
 // ranges of whole boxes with about equal cells, as long as each group keeps
 // 4 waves of items or more in the plan's tile shape.  One group (no
 // overlap) otherwise.  Every shape gets the same groups.
 int setup_readback(nyx_plan *P) {
   const int nsh = fused_num_shapes(P->prm.precision);
-  const int waves = P->nitems[P->shape] / std::max(1, P->max_grid[P->shape]);
+  int waves = P->nitems[P->shape] / std::max(1, P->max_grid[P->shape]);
+  if (!P->parts.empty()) {
+    waves = 0;
+    for (const auto &pt : P->parts) waves += pt.nitems / std::max(1, pt.grid);
+  }
   const int G = std::min(std::min(16, P->nbox), waves / 4);
   std::vector<int> gb(1, 0);
   for (int g = 1; g < G; ++g) {
@@ -595,6 +650,8 @@ int setup_readback(nyx_plan *P) {
     CK(cudaMemcpy(P->d_items_grp[s], it.data(), sizeof(WorkItem) * it.size(),
                   cudaMemcpyHostToDevice));
   }
+  for (auto &pt : P->parts)
+    if (int rc = part_groups(pt, gb)) return rc;
   // input side: each group's fill rects, the groups they read, and an
   // input order that brings in the groups the first advances need first
   std::vector<int> gof(P->nbox);
@@ -676,7 +733,6 @@ int step_pipelined(nyx_plan *P, nyx_level *L, const double *host_in, double *hos
   CK(cudaEventRecord(P->ev_setup, P->stream));
   CK(cudaStreamWaitEvent(P->stream2, P->ev_setup, 0));
   FusedArgs a = fused_args(P, S, L->grav, Sn, P->d_dtacc, false);
-  const int s = P->shape;
   const cudaStream_t cs[2] = {P->stream, P->stream2};
   unsigned waited[2] = {0u, 0u};
   for (int g = 0; g < P->ngrp; ++g) {
@@ -703,14 +759,8 @@ int step_pipelined(nyx_plan *P, nyx_level *L, const double *host_in, double *hos
         P->launches += 1;
       }
     }
-    a.items = P->d_items_grp[s] + P->grp_off[s][g];
-    a.nitems = P->grp_off[s][g + 1] - P->grp_off[s][g];
     a.queue = P->d_queue_grp + g;
-    if (a.nitems > 0) {
-      int e = launch_fused(P->prm.precision, s, a, std::min(P->max_grid[s], a.nitems), st);
-      if (e) return cuda_fail((cudaError_t)e, "fused advance launch");
-      P->launches += 1;
-    }
+    if (int rc = launch_level(P, a, g, st)) return rc;
     if (int rc = read_back_group(P, Sn, g, host_out, st)) return rc;
   }
   CK(cudaEventRecord(P->ev_side, P->stream2));
@@ -762,46 +812,237 @@ int do_correct(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_n
   return NYX_OK;
 }
 
-// Time every tile shape on the plan's level once (state is only read;
-// the output buffer is overwritten) and keep the fastest.
+// ---------------------------------------------------------------- autotuner
+// The level's boxes fall into box-size classes (boxes of equal extent), and
+// each class is tuned on its own.  Every candidate -- a tile shape with a
+// number of resident CTAs per SM (all that fit, or one) -- runs one wave of
+// the class's work items (as many items as the candidate keeps resident; a
+// class with fewer items has them repeated, so that the timing is of a full
+// machine), and the candidate with the least time per zone wins.  Choices are
+// kept in a JSON file keyed by GPU name, SM count, precision, scheme variant
+// and box extent, so a later plan whose classes are all there makes no trial
+// launch.  Classes that settle on the same candidate share one launch; the
+// level's launch is one per distinct candidate (nyx_plan::parts), or the
+// single level-wide list when every class agrees on a shape at full
+// residency.  The staging depth of the kernels is fixed by their ring
+// structure; the plane chunks of the task form come from the queue model of
+// task_items, not from timing.
+
+struct TuneChoice {
+  int shape = -1, per_sm = 0;
+  double ns_per_zone = 0.0;
+};
+
+std::string tune_cache_path() {
+  if (const char *env = std::getenv("NYX_TUNE_CACHE")) return std::string(env);  // "": no cache
+  Dl_info info;
+  if (dladdr((void *)&tune_cache_path, &info) && info.dli_fname) {
+    const std::string f = info.dli_fname;
+    const size_t k = f.rfind('/');
+    return (k == std::string::npos ? std::string(".") : f.substr(0, k)) + "/_tune_cache.json";
+  }
+  return "";
+}
+
+// One entry per line: "key": {"shape": S, "ctas_per_sm": K, "ns_per_zone": T}
+std::map<std::string, TuneChoice> tune_cache_load(const std::string &path) {
+  std::map<std::string, TuneChoice> m;
+  if (path.empty()) return m;
+  std::ifstream in(path);
+  std::string line;
+  while (std::getline(in, line)) {
+    const size_t a = line.find('"');
+    if (a == std::string::npos) continue;
+    const size_t b = line.find('"', a + 1);
+    if (b == std::string::npos) continue;
+    TuneChoice c;
+    if (std::sscanf(line.c_str() + b + 1, ": {\"shape\": %d, \"ctas_per_sm\": %d, \"ns_per_zone\": %lf",
+                    &c.shape, &c.per_sm, &c.ns_per_zone) == 3 &&
+        c.shape >= 0 && c.per_sm > 0)
+      m[line.substr(a + 1, b - a - 1)] = c;
+  }
+  return m;
+}
+
+void tune_cache_save(const std::string &path, const std::map<std::string, TuneChoice> &m) {
+  if (path.empty()) return;
+  const std::string tmp = path + ".tmp" + std::to_string((long long)std::rand());
+  {
+    std::ofstream out(tmp);
+    if (!out) return;
+    out << "{\n";
+    size_t n = 0;
+    for (const auto &kv : m) {
+      char buf[160];
+      std::snprintf(buf, sizeof(buf), "{\"shape\": %d, \"ctas_per_sm\": %d, \"ns_per_zone\": %.6g}",
+                    kv.second.shape, kv.second.per_sm, kv.second.ns_per_zone);
+      out << " \"" << kv.first << "\": " << buf << (++n < m.size() ? ",\n" : "\n");
+    }
+    out << "}\n";
+  }
+  std::rename(tmp.c_str(), path.c_str());  // whole file or none: readers never see a partial one
+}
+
+// Items of the boxes `sel` (indices into the plan's box list) for one tile
+// shape, with the box indices of the plan.
+std::vector<WorkItem> subset_items(const nyx_plan &P, const std::vector<int> &sel, int tx, int ty,
+                                   int slots, bool chunk) {
+  std::vector<std::array<int, 3>> n(sel.size());
+  for (size_t k = 0; k < sel.size(); ++k) {
+    const BoxDev &X = P.hbox[sel[k]];
+    n[k] = {X.n[0], X.n[1], X.n[2]};
+  }
+  std::vector<WorkItem> it = task_items(n, tx, ty, slots, chunk);
+  for (WorkItem &w : it) w.box = sel[w.box];
+  return it;
+}
+
 int tune_shape(nyx_plan *P, const FusedArgs &base) {
   P->tuned = true;
   cudaStreamCaptureStatus cs;
   CK(cudaStreamIsCapturing(P->stream, &cs));
   if (cs != cudaStreamCaptureStatusNone) return NYX_OK;  // keep the current shape under capture
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
-  float best = 1e30f;
-  int best_s = P->shape;
-  for (int s = 0; s < fused_num_shapes(P->prm.precision); ++s) {
-    FusedArgs a = base;
-    a.items = P->d_items[s];
-    a.nitems = P->nitems[s];
-    a.dtacc = nullptr;
-    a.flux_keep = nullptr;
-    a.status = P->d_status_tune;
-    int grid = std::min(P->max_grid[s], a.nitems);
-    float tot = 0.f;
-    for (int rep = 0; rep < 3; ++rep) {
-      CK(cudaEventRecord(e0, P->stream));
-      int e = launch_fused(P->prm.precision, s, a, grid, P->stream);
-      if (e) return cuda_fail((cudaError_t)e, "autotune launch");
-      P->launches += 1;
-      CK(cudaEventRecord(e1, P->stream));
-      CK(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, e0, e1));
-      if (rep > 0) tot += ms;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, dev));
+  const int nsm = prop.multiProcessorCount;
+  const int nsh = fused_num_shapes(P->prm.precision);
+  // classes: boxes of equal extent, in order of first appearance
+  std::map<std::array<int, 3>, int> cls_of;
+  std::vector<std::array<int, 3>> cls_n;
+  std::vector<std::vector<int>> cls_boxes;
+  for (int b = 0; b < P->nbox; ++b) {
+    const std::array<int, 3> e = {P->hbox[b].n[0], P->hbox[b].n[1], P->hbox[b].n[2]};
+    auto f = cls_of.find(e);
+    if (f == cls_of.end()) {
+      f = cls_of.emplace(e, (int)cls_n.size()).first;
+      cls_n.push_back(e);
+      cls_boxes.emplace_back();
     }
-    if (tot < best) {
-      best = tot;
-      best_s = s;
-    }
+    cls_boxes[f->second].push_back(b);
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  P->shape = best_s;
+  const int nc = (int)cls_n.size();
+  P->tune_classes = nc;
+  P->tune_trials = 0;
+  const std::string path = tune_cache_path();
+  std::map<std::string, TuneChoice> cache = tune_cache_load(path);
+  const std::string prefix = std::string(prop.name) + "|sm" + std::to_string(nsm) + "|" +
+                             (P->prm.precision == NYX_MIXED ? "mixed" : "fp64") + "|v" +
+                             std::to_string(variant_bits(P)) + "|";
+  std::vector<TuneChoice> pick(nc);
+  bool fresh = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  WorkItem *d_wave = nullptr;
+  size_t wave_cap = 0;
+  int rc = NYX_OK;
+  for (int c = 0; c < nc && rc == NYX_OK; ++c) {
+    const std::string key = prefix + std::to_string(cls_n[c][0]) + "x" + std::to_string(cls_n[c][1]) +
+                            "x" + std::to_string(cls_n[c][2]);
+    auto hit = cache.find(key);
+    if (hit != cache.end() && hit->second.shape < nsh &&
+        hit->second.per_sm * nsm <= P->max_grid[hit->second.shape]) {
+      pick[c] = hit->second;
+      continue;
+    }
+    if (!e0) {
+      CK(cudaEventCreate(&e0));
+      CK(cudaEventCreate(&e1));
+    }
+    TuneChoice best;
+    for (int sh = 0; sh < nsh && rc == NYX_OK; ++sh) {
+      const TileShape ts = fused_shape(sh);
+      const int full = std::max(1, P->max_grid[sh] / nsm);
+      std::vector<WorkItem> all = subset_items(*P, cls_boxes[c], ts.tx, ts.ty, kWhole, false);
+      std::vector<int> occ(1, full);  // resident CTAs per SM: all that fit, and one
+      if (full > 1) occ.push_back(1);
+      for (int per_sm : occ) {
+        const int grid = per_sm * nsm;
+        std::vector<WorkItem> wave(grid);
+        double zones = 0.0;
+        for (int k = 0; k < grid; ++k) {
+          wave[k] = all[k % all.size()];
+          zones += double(wave[k].nx) * wave[k].ny * wave[k].nz;
+        }
+        if (wave.size() > wave_cap) {
+          cudaFree(d_wave);
+          d_wave = nullptr;
+          if (cudaMalloc(&d_wave, sizeof(WorkItem) * wave.size()) != cudaSuccess) {
+            rc = fail(NYX_ENOMEM, "autotune item buffer");
+            break;
+          }
+          wave_cap = wave.size();
+        }
+        CK(cudaMemcpy(d_wave, wave.data(), sizeof(WorkItem) * wave.size(), cudaMemcpyHostToDevice));
+        FusedArgs a = base;
+        a.items = d_wave;
+        a.nitems = grid;
+        a.dtacc = nullptr;
+        a.flux_keep = nullptr;
+        a.status = P->d_status_tune;
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {  // the first launch warms up
+          CK(cudaEventRecord(e0, P->stream));
+          int e = launch_fused(P->prm.precision, sh, a, grid, P->stream);
+          if (e) return cuda_fail((cudaError_t)e, "autotune launch");
+          P->launches += 1;
+          P->tune_trials += 1;
+          CK(cudaEventRecord(e1, P->stream));
+          CK(cudaEventSynchronize(e1));
+          CK(cudaEventElapsedTime(&ms, e0, e1));
+        }
+        const double t = ms * 1e6 / zones;
+        if (best.shape < 0 || t < best.ns_per_zone) {
+          best.shape = sh;
+          best.per_sm = per_sm;
+          best.ns_per_zone = t;
+        }
+      }
+    }
+    pick[c] = best;
+    cache[key] = best;
+    fresh = true;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(d_wave);
+  if (rc) return rc;
+  if (fresh) tune_cache_save(path, cache);
+
+  // one part per distinct choice, its classes' boxes together
+  std::map<std::pair<int, int>, std::vector<int>> groups;
+  std::map<std::pair<int, int>, long long> gcells;
+  for (int c = 0; c < nc; ++c) {
+    auto &v = groups[{pick[c].shape, pick[c].per_sm}];
+    v.insert(v.end(), cls_boxes[c].begin(), cls_boxes[c].end());
+    gcells[{pick[c].shape, pick[c].per_sm}] +=
+        (long long)cls_boxes[c].size() * cls_n[c][0] * cls_n[c][1] * cls_n[c][2];
+  }
+  for (auto &pt : P->parts) {
+    cudaFree(pt.d_items);
+    cudaFree(pt.d_items_grp);
+  }
+  P->parts.clear();
+  auto biggest = gcells.begin();
+  for (auto it = gcells.begin(); it != gcells.end(); ++it)
+    if (it->second > biggest->second) biggest = it;
+  P->shape = biggest->first.first;
+  if (groups.size() == 1 && biggest->first.second * nsm >= P->max_grid[P->shape]) return NYX_OK;
+  for (auto &kv : groups) {
+    nyx_plan::RunPart pt;
+    pt.shape = kv.first.first;
+    pt.grid = std::min(P->max_grid[pt.shape], kv.first.second * nsm);
+    std::sort(kv.second.begin(), kv.second.end());
+    const TileShape ts = fused_shape(pt.shape);
+    pt.h_items = subset_items(*P, kv.second, ts.tx, ts.ty, pt.grid, ts.task && P->prm.z_chunks);
+    pt.nitems = (int)pt.h_items.size();
+    CK(cudaMalloc(&pt.d_items, sizeof(WorkItem) * std::max(1, pt.nitems)));
+    CK(cudaMemcpy(pt.d_items, pt.h_items.data(), sizeof(WorkItem) * pt.nitems,
+                  cudaMemcpyHostToDevice));
+    P->parts.push_back(std::move(pt));
+    if (P->ngrp > 1)
+      if (int r2 = part_groups(P->parts.back(), P->grp_box)) return r2;
+  }
   return NYX_OK;
 }
 
@@ -1399,8 +1640,21 @@ int nyx_hydro_set_tile_shape(nyx_plan *P, int shape) {
   if (!P) return fail(NYX_EINVAL, "null plan");
   if (P->prm.batching != NYX_PERSISTENT) return fail(NYX_EINVAL, "plan is not persistent");
   if (shape < 0 || shape >= fused_num_shapes(P->prm.precision)) return fail(NYX_EINVAL, "tile shape out of range");
+  for (auto &pt : P->parts) {
+    cudaFree(pt.d_items);
+    cudaFree(pt.d_items_grp);
+  }
+  P->parts.clear();
   P->shape = shape;
   P->tuned = true;
+  return NYX_OK;
+}
+
+int nyx_hydro_tune_info(const nyx_plan *P, int *classes, int *trials, int *launches) {
+  if (!P) return fail(NYX_EINVAL, "null plan");
+  if (classes) *classes = P->tune_classes;
+  if (trials) *trials = P->tune_trials;
+  if (launches) *launches = P->parts.empty() ? 1 : (int)P->parts.size();
   return NYX_OK;
 }
 

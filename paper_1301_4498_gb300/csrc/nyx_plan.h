@@ -109,7 +109,21 @@ struct nyx_plan {
   std::vector<long long> flux_off;
   long long *d_flux_off = nullptr;
   bool flux_valid = false;
-  // fused persistent form
+  // fused persistent form.  parts: the autotuner's per-class choice when the
+  // box-size classes settle on different (shape, grid) pairs, one launch per
+  // part over the boxes of its classes; empty: one launch of `shape` over
+  // the level-wide list d_items[shape]
+  struct RunPart {
+    int shape = 0, grid = 0;
+    nyx::WorkItem *d_items = nullptr;
+    int nitems = 0;
+    std::vector<nyx::WorkItem> h_items;
+    nyx::WorkItem *d_items_grp = nullptr;
+    std::vector<int> grp_off;  // first item of each read-back group, ngrp + 1 entries
+  };
+  std::vector<RunPart> parts;
+  int tune_trials = 0;       // trial launches of the last tuning (0: every class from the cache)
+  int tune_classes = 0;      // box-size classes of the level
   nyx::WorkItem *d_items[8] = {nullptr};
   std::vector<nyx::WorkItem> h_items[8];
   int nitems[8] = {0};

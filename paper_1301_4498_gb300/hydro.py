@@ -124,6 +124,8 @@ def load_library(path: str | None = None):
     L.nyx_hydro_tile_shape.argtypes = [C.c_int, ip, ip]
     L.nyx_task_items.argtypes = [C.c_int, ip, C.c_int, C.c_int, C.c_int, C.c_int, ip, C.c_int, ip]
     L.nyx_hydro_set_tile_shape.argtypes = [vp, C.c_int]
+    L.nyx_hydro_tune_info.argtypes = [vp, ip, ip, ip]
+    L.nyx_hydro_tune_info.restype = C.c_int
     L.nyx_hydro_get_tile_shape.argtypes = [vp, ip]
     L.nyx_hydro_profile.argtypes = [vp, C.c_int]
     L.nyx_hydro_counters_read.argtypes = [vp, C.c_int, C.POINTER(NyxCounters)]
@@ -396,6 +398,13 @@ class Plan:
         tx, ty = C.c_int(), C.c_int()
         _check(self.lib.nyx_hydro_tile_shape(s.value, C.byref(tx), C.byref(ty)))
         return s.value, (tx.value, ty.value)
+
+    def tune_info(self):
+        """(box-size classes, trial launches of the last tuning, fused launches
+        per advance) of the plan's autotuner (nyx_hydro_tune_info)."""
+        c, t, n = C.c_int(), C.c_int(), C.c_int()
+        _check(self.lib.nyx_hydro_tune_info(self.h, C.byref(c), C.byref(t), C.byref(n)))
+        return c.value, t.value, n.value
 
     def profile(self, enable=True):
         _check(self.lib.nyx_hydro_profile(self.h, 1 if enable else 0))
