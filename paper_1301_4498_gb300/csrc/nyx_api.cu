@@ -2,6 +2,8 @@
 // copy list, the batched work list (largest boxes first, as a knapsack-style
 // balance of the paper's Sec. 5.1 distribution), CUDA-graph capture, status
 // and the C ABI of include/nyx_hydro.h.
+#include <cuda.h>  // CUtensorMap and its enums (the encoder comes through the runtime)
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <dlfcn.h>
 
@@ -397,6 +399,7 @@ void free_plan(nyx_plan *P) {
     cudaFree(pt.d_items_grp);
   }
   for (auto &e : P->ev_grp) cudaEventDestroy(e);
+  for (auto &kv : P->tmaps) cudaFree(kv.second);
   if (P->copy_stream) cudaStreamDestroy(P->copy_stream);
   for (auto &r : P->d_rects_grp) cudaFree(r);
   for (auto &e : P->ev_in) cudaEventDestroy(e);
@@ -497,7 +500,101 @@ FusedArgs fused_args(nyx_plan *P, const double *S, const double *G, double *Sn,
   a.predict_only = predict_only ? 1 : 0;
   a.variant = variant_bits(P);
   a.flat = P->d_flat;
+  a.tmS = nullptr;
+  a.tmG = nullptr;
   return a;
+}
+
+// ---------------------------------------------------------------- TMA descriptors
+// The task form at 16 x 8 tiles stages each plane's state and gravity with
+// tensor copies.  Its descriptors: per box, a 4-D tiled map over the box's
+// component arrays (x, y, z with ghosts, component), box (tx + 4) x (ty + 2)
+// x 1 x ncomp of FP64, out-of-range elements filled with zeros.  The encoder
+// is the driver's cuTensorMapEncodeTiled, reached through the runtime; any
+// failure leaves the plan on plain loads.
+bool shape_stages_with_tma(const nyx_plan *P, int shape) {
+  const TileShape ts = fused_shape(shape);
+  return P->prm.precision == NYX_MIXED && ts.task && ts.tx == 16 && ts.ty == 8;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+
+// Descriptors of `field` (ncomp components) for `shape`, built on first use
+// (not while the plan's stream is being captured: then null, plain loads).
+const void *plan_tmaps(nyx_plan *P, const double *field, int ncomp, int shape) {
+  if (!field || !shape_stages_with_tma(P, shape)) return nullptr;
+  const auto key = std::make_tuple((const void *)field, ncomp, shape);
+  auto it = P->tmaps.find(key);
+  if (it != P->tmaps.end()) return it->second;
+  if (capturing(P)) return nullptr;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+  void *d = nullptr;
+  if (enc) {
+    const TileShape ts = fused_shape(shape);
+    std::vector<CUtensorMap> h(P->nbox);
+    bool ok = true;
+    for (int b = 0; b < P->nbox && ok; ++b) {
+      const BoxDev &X = P->hbox[b];
+      void *base = const_cast<double *>(field) + (size_t)ncomp * X.pref;
+      const cuuint64_t gdim[4] = {(cuuint64_t)X.N[0], (cuuint64_t)X.N[1], (cuuint64_t)X.N[2],
+                                  (cuuint64_t)ncomp};
+      const cuuint64_t gstr[3] = {8ull * X.N[0], 8ull * X.N[0] * X.N[1], 8ull * X.stride};
+      const cuuint32_t box[4] = {(cuuint32_t)(ts.tx + 4), (cuuint32_t)(ts.ty + 2), 1u,
+                                 (cuuint32_t)ncomp};
+      const cuuint32_t es[4] = {1u, 1u, 1u, 1u};
+      ok = enc(&h[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, base, gdim, gstr, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    if (ok && cudaMalloc(&d, sizeof(CUtensorMap) * h.size()) == cudaSuccess) {
+      if (cudaMemcpy(d, h.data(), sizeof(CUtensorMap) * h.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+        cudaFree(d);
+        d = nullptr;
+      }
+    } else {
+      d = nullptr;
+    }
+    cudaGetLastError();
+  }
+  P->tmaps[key] = d;
+  return d;
+}
+
+// Descriptors of the level's state versions and gravity for the shapes in
+// use (called before a graph capture, which cannot build them).
+void prepare_tmaps(nyx_plan *P, const nyx_level *L) {
+  std::vector<int> shapes;
+  if (P->parts.empty())
+    shapes.push_back(P->shape);
+  else
+    for (const auto &pt : P->parts) shapes.push_back(pt.shape);
+  for (int s : shapes) {
+    plan_tmaps(P, L->state[0], NCONS, s);
+    plan_tmaps(P, L->state[1], NCONS, s);
+    plan_tmaps(P, L->grav, NGRAV, s);
+  }
+}
+
+void set_tmaps(nyx_plan *P, FusedArgs &a, int shape) {
+  a.tmS = plan_tmaps(P, a.S, NCONS, shape);
+  a.tmG = a.G ? plan_tmaps(P, a.G, NGRAV, shape) : nullptr;
+  if (!a.tmS || (a.G && !a.tmG)) a.tmS = a.tmG = nullptr;
 }
 
 // The fused advance over the whole level (g < 0) or over read-back group g:
@@ -514,6 +611,7 @@ int launch_level(nyx_plan *P, FusedArgs a, int g, cudaStream_t st) {
       a.nitems = P->grp_off[s][g + 1] - P->grp_off[s][g];
     }
     if (a.nitems > 0) {
+      set_tmaps(P, a, s);
       int e = launch_fused(P->prm.precision, s, a, std::min(P->max_grid[s], a.nitems), st);
       if (e) return cuda_fail((cudaError_t)e, "fused advance launch");
       P->launches += 1;
@@ -529,6 +627,7 @@ int launch_level(nyx_plan *P, FusedArgs a, int g, cudaStream_t st) {
       a.nitems = pt.grp_off[g + 1] - pt.grp_off[g];
     }
     if (a.nitems > 0) {
+      set_tmaps(P, a, pt.shape);
       int e = launch_fused(P->prm.precision, pt.shape, a, std::min(pt.grid, a.nitems), st);
       if (e) return cuda_fail((cudaError_t)e, "fused advance launch");
       P->launches += 1;
@@ -1465,6 +1564,7 @@ int nyx_hydro_run(nyx_plan *P, nyx_level *L, const double *a_dev, double *dt_dev
     int rc = tune_shape(P, a);
     if (rc) return rc;
   }
+  if (P->prm.batching == NYX_PERSISTENT) prepare_tmaps(P, L);
   GraphKey key(L->state[0], L->state[1], L->grav, L->cur, a_dev, dt_dev, nsteps, compute_dt0);
   auto it = P->graphs.find(key);
   if (it == P->graphs.end()) {

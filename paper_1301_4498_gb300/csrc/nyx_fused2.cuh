@@ -27,6 +27,13 @@
 // threads have traced plane c (the last read of ring plane c-2 and of the
 // framed plane), before the update warps overwrite them.
 //
+// At 16 x 8 tiles (one CTA per SM) the update warps take each plane's state
+// (at plane c+2, for the ring) and gravity (at plane c) from staging buffers
+// that tensor copies (TMA, cp.async.bulk.tensor with per-box descriptors)
+// fill one plane ahead: the copies of the next plane's inputs go once every
+// update thread has read the buffers, and complete on an mbarrier whose wait
+// is bounded.  The frame strips and the update's own reads stay plain loads.
+//
 // Rings over planes: slot = (plane + 2) & 1 for the two-plane rings, and
 // (plane + 8) % 5 for the five-plane primitive ring.
 #pragma once
@@ -72,10 +79,72 @@ struct G2 {
   static constexpr int T6 = (TX + 1) * TY + TX * (TY + 1) + TX * TY;
   static constexpr int TT = T2 + T3 + T4 + T5 + T6;
   static constexpr int TAB = FFZ + 16 * NZF;         // [TT] ushort task lists
-  static constexpr int TOTAL = TAB + (TT + 1) / 2;
+  static constexpr int TOTAL0 = TAB + (TT + 1) / 2;
+  // TMA staging (16 x 8 tiles at one CTA per SM; the other shapes have no
+  // room): one plane of the state (6 components) and of gravity (3) over
+  // the tile's columns, x from x0 + 2 (an even coordinate: 16-byte aligned)
+  // for SX doubles, y from y0 + 3 for H rows, as FP64, and the mbarrier the
+  // copies complete on
+  static constexpr bool TMA = (TX == 16 && TY == 8 && XU > 0);
+  static constexpr int SX = TX + 4;
+  static constexpr int STG = (TOTAL0 + 255) / 256 * 256;  // 1024-byte aligned
+  static constexpr int STGS = STG;                        // [6][H][SX] doubles
+  static constexpr int STGG = STGS + 2 * 6 * H * SX;      // [3][H][SX] doubles
+  static constexpr int MBAR = STGG + 2 * 3 * H * SX;      // one 8-byte mbarrier
+  static constexpr unsigned STG_BYTES_S = 8u * 6 * H * SX, STG_BYTES_G = 8u * 3 * H * SX;
+  // + 32 floats: the staging area is aligned to 128 bytes at run time
+  static constexpr int TOTAL = TMA ? MBAR + 2 + 32 : TOTAL0;
   static constexpr size_t SMEM = sizeof(float) * (size_t)TOTAL;
   static_assert(SMEM <= 227 * 1024, "task-form tile does not fit in shared memory");
 };
+
+// ---------------------------------------------------------------- TMA staging
+// A CTA's tensor copies (cp.async.bulk.tensor) land in shared memory and
+// complete on an mbarrier; waits are bounded and a wait that gives up raises
+// ST_TIMEOUT and switches the CTA to plain loads.
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(void *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(void *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(void *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+// bounded wait for phase `parity`; false if it gave up
+__device__ __forceinline__ bool mbar_wait(void *bar, unsigned parity) {
+  for (unsigned it = 0; it < (1u << 20); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_load_4d(void *dst, const void *tmap, int x, int y, int z, int c,
+                                            void *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(c), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tmap_acquire(const void *tmap) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap) : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 
 // Extra loading-only update threads: two warps when one CTA holds the SM
 // (24 warps at 80 registers fit the per-scheduler register files), none
@@ -86,6 +155,7 @@ struct G2 {
 // the column threads' stage barrier; the flux hand-over pair; the input
 // hand-over pair.
 constexpr int BAR_COL = 1, BAR_READY = 2, BAR_FREE = 3, BAR_LOADED = 4, BAR_CONSUMED = 5;
+constexpr int BAR_UPD = 6;  // the update warps among themselves (TMA staging)
 __device__ __forceinline__ void bar_sync_n(int id, int n) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
@@ -283,9 +353,10 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
   using G = G2<TX, TY, XU_OF(MB)>;
   constexpr int NC = G::NC, NCP = G::NCP, NE = G::NE, W = G::W, WE = G::WE, NT = G::NT;
   constexpr int NTC = G::NTC, NUF = G::NUF, NXF = G::NXF, NZF = G::NZF;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
   float *sm = reinterpret_cast<float *>(smem_raw);
   __shared__ int s_item;
+  __shared__ int s_tma_fail;
 
   const nyx::SchemeConsts KK = *a.K;
   const nyx::StepConsts sc = *a.SC;
@@ -316,6 +387,21 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
   unsigned flags = 0;
   unsigned short *ttab = reinterpret_cast<unsigned short *>(sm + G::TAB);
   int tab_nx = -1, tab_ny = -1;  // the tile extent the lists were built for
+  // TMA staging of the update warps' plane inputs (16 x 8 tiles with tensor
+  // maps given): phase parity of the mbarrier, and whether copies are used
+  // the staging area, moved up to the next 128-byte boundary (tensor copies
+  // need a 128-byte aligned destination); offsets below are relative to it
+  float *stg = sm + G::STG;
+  if constexpr (G::TMA) stg += ((128u - (smem_addr(stg) & 127u)) & 127u) / 4u;
+  void *tbar = G::TMA ? static_cast<void *>(stg + (G::MBAR - G::STG)) : nullptr;
+  unsigned tph = 0;
+  bool use_tma = G::TMA && a.tmS != nullptr && (a.G == nullptr || a.tmG != nullptr);
+  if constexpr (G::TMA) {
+    if (tid == 0) {
+      s_tma_fail = 0;
+      mbar_init(tbar, 1);
+    }
+  }
 
   for (;;) {
     if (tid == 0) s_item = atomicAdd(a.queue, 1);
@@ -620,19 +706,69 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
         col = (long long)(w.y0 + cj + 4) * b.N[0] + (w.x0 + ci + 4);
         return ci <= nxt && cj <= nyt;
       };
+      // tensor copies of inputs(c)'s planes into the staging buffers: the
+      // state at plane c+2 (the ring's new plane) and gravity at plane c,
+      // over x in [x0+2, x0+2+SX), y in [y0+3, y0+3+H) of the box with ghosts
+      // (the tile's columns and their halo; past the box edge the copy fills
+      // zeros, which no column reads)
+      if (s_tma_fail) use_tma = false;  // a wait gave up in an earlier item: plain loads
+      const char *tmS_b = use_tma ? static_cast<const char *>(a.tmS) + 128 * (size_t)w.box : nullptr;
+      const char *tmG_b = (use_tma && a.G) ? static_cast<const char *>(a.tmG) + 128 * (size_t)w.box
+                                           : nullptr;
+      if (G::TMA && use_tma && uthr == 0) {
+        tmap_acquire(tmS_b);
+        if (tmG_b) tmap_acquire(tmG_b);
+      }
+      auto issue = [&](int c) {
+        if constexpr (G::TMA) {
+          if (uthr == 0) {
+            fence_async_smem();  // earlier reads of the buffers precede the copies
+            mbar_expect_tx(tbar, G::STG_BYTES_S + (tmG_b ? G::STG_BYTES_G : 0u));
+            tma_load_4d(stg + (G::STGS - G::STG), tmS_b, w.x0 + 2, w.y0 + 3, c + 2 + 4, 0, tbar);
+            if (tmG_b)
+              tma_load_4d(stg + (G::STGG - G::STG), tmG_b, w.x0 + 2, w.y0 + 3, c + 4, 0, tbar);
+          }
+        }
+      };
+      bool staged = false;  // the copies of the next inputs() are in flight
       // inputs of plane c: ring plane c+2; plane c's gravity, flattening and
       // framed copy (its own columns from the ring, the frame strips loaded)
       auto inputs = [&](int c) {
+        if (G::TMA && staged) {
+          if (mbar_wait(tbar, tph)) {
+            tph ^= 1u;
+          } else {  // gave up: flag it; the phase stays the one still owed
+            flags |= nyx::ST_TIMEOUT;
+            s_tma_fail = 1;
+          }
+        }
         for (int e = uthr; e < NC; e += G::NU) {
           long long col;
           if (!column(e, col)) continue;
-          load_prims(col + (long long)(c + 2 + 4) * ps, ring_at(c + 2) + e, NC);
           const long long id = col + (long long)(c + 4) * ps;
           float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-          if (Gv) {
-            g0 = d2f_rn(Gv[id]);
-            g1 = d2f_rn(Gv[bs + id]);
-            g2 = d2f_rn(Gv[2 * bs + id]);
+          if (G::TMA && staged) {
+            // the column's values from the staging buffers
+            const int sidx = (e / W) * G::SX + (e % W + 1);
+            const double *stS = reinterpret_cast<const double *>(stg + (G::STGS - G::STG));
+            float q[5];
+            prims_of<float>(stS, G::H * G::SX, sidx, E, q);
+            float *dst = ring_at(c + 2) + e;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) dst[v * NC] = q[v];
+            if (tmG_b) {
+              const double *stG = reinterpret_cast<const double *>(stg + (G::STGG - G::STG));
+              g0 = d2f_rn(stG[sidx]);
+              g1 = d2f_rn(stG[G::H * G::SX + sidx]);
+              g2 = d2f_rn(stG[2 * G::H * G::SX + sidx]);
+            }
+          } else {
+            load_prims(col + (long long)(c + 2 + 4) * ps, ring_at(c + 2) + e, NC);
+            if (Gv) {
+              g0 = d2f_rn(Gv[id]);
+              g1 = d2f_rn(Gv[bs + id]);
+              g2 = d2f_rn(Gv[2 * bs + id]);
+            }
           }
           sm[G::GR + e] = g0;
           sm[G::GR + NC + e] = g1;
@@ -642,6 +778,17 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
           const int ee = (e / W + 2) * WE + (e % W + 2);
 #pragma unroll
           for (int v = 0; v < 5; ++v) sm[G::PE + v * NE + ee] = rc[v * NC];
+        }
+        if constexpr (G::TMA) {
+          // the staging buffers are read: the first update warp waits until
+          // every update thread is past this point (the others only arrive)
+          // and its first thread sends the copies of the next inputs
+          if (uthr < 32)
+            bar_sync_n(BAR_UPD, G::NU);
+          else
+            bar_arrive_n(BAR_UPD, G::NU);
+          staged = use_tma && c + 1 <= ze;
+          if (staged) issue(c + 1);
         }
         for (int u = uthr; u < nstrip; u += G::NU) {
           int x, y;
@@ -690,7 +837,7 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
         for (int k = zb - 3; k <= zb; ++k)
           load_prims(col + (long long)(k + 4) * ps, ring_at(k) + e, NC);
       }
-      inputs(zb - 1);
+      inputs(zb - 1);  // plain loads; it issues the copies of plane zb's inputs
       __threadfence_block();
       bar_arrive_n(BAR_LOADED, NT);
       for (int c = zb; c <= ze; ++c) {
@@ -711,6 +858,11 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
       update_plane(ze - 1);
     }
     __syncthreads();
+  }
+  if constexpr (G::TMA) {
+    // a wait that gave up may have left copies in flight: wait once more
+    // (bounded) before the CTA's shared memory goes
+    if (s_tma_fail && tid == NTC) mbar_wait(tbar, tph);
   }
 
   if (a.dtacc) {

@@ -63,6 +63,11 @@ struct FusedArgs {
                                   // bit 2 shock flattening
   const void *flat;               // shock-flattening coefficients (double for FP64 plans,
                                   // float for mixed ones; one per cell, state layout) or null
+  // TMA descriptors (CUtensorMap, one per box, in device memory) of S and G
+  // for the tile shape being launched, or null: the kernels that stage
+  // their plane inputs with tensor copies fall back to plain loads
+  const void *tmS;
+  const void *tmG;
 };
 
 // Tile shapes of the fused kernel (columns per CTA in x and y).

@@ -122,6 +122,10 @@ struct nyx_plan {
     std::vector<int> grp_off;  // first item of each read-back group, ngrp + 1 entries
   };
   std::vector<RunPart> parts;
+  // TMA descriptors of level fields for the shapes that stage with tensor
+  // copies: one CUtensorMap per box, in device memory, keyed by (field
+  // address, components, shape); null marks a field that cannot be mapped
+  std::map<std::tuple<const void *, int, int>, void *> tmaps;
   int tune_trials = 0;       // trial launches of the last tuning (0: every class from the cache)
   int tune_classes = 0;      // box-size classes of the level
   nyx::WorkItem *d_items[8] = {nullptr};
