@@ -670,6 +670,9 @@ int do_advance(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_n
       int rc = tune_shape(P, a);
       if (rc) return rc;
     }
+    // the TMA descriptors of both state versions at once (a level alternates
+    // between them), so that no later step stops to build them
+    prepare_tmaps(P, L);
     if (host_out && P->ngrp > 1) {
       for (int g = 0; g < P->ngrp; ++g) {
         if (int rc = launch_level(P, a, g, P->stream)) return rc;
@@ -775,9 +778,17 @@ int setup_readback(nyx_plan *P) {
                     cudaMemcpyHostToDevice));
     }
   }
+  // groups advance in this order: first those whose fill reads only
+  // themselves (independent boxes, which need no other group's input), then
+  // the others in box order; the inputs come in the order these need them
+  std::vector<int> proc;
+  for (int g = 0; g < ng; ++g)
+    if ((src[g] & ~(1u << g)) == 0u) proc.push_back(g);
+  for (int g = 0; g < ng; ++g)
+    if ((src[g] & ~(1u << g)) != 0u) proc.push_back(g);
   std::vector<int> order;
   std::vector<char> sent(ng, 0);
-  for (int g = 0; g < ng; ++g) {
+  for (int g : proc) {
     const unsigned need = src[g] | (1u << g);
     for (int q = 0; q < ng; ++q)
       if (((need >> q) & 1u) && !sent[q]) {
@@ -785,6 +796,7 @@ int setup_readback(nyx_plan *P) {
         order.push_back(q);
       }
   }
+  CK((cudaError_t)preload_copy_kernels());
   CK(cudaStreamCreateWithFlags(&P->copy_stream, cudaStreamNonBlocking));
   CK(cudaStreamCreateWithFlags(&P->h2d_stream, cudaStreamNonBlocking));
   CK(cudaStreamCreateWithFlags(&P->stream2, cudaStreamNonBlocking));
@@ -798,6 +810,7 @@ int setup_readback(nyx_plan *P) {
   for (auto &e : P->ev_in) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   P->grp_src = src;
   P->in_order = order;
+  P->proc_order = proc;
   P->grp_box = gb;
   P->ngrp = ng;
   return NYX_OK;
@@ -834,17 +847,18 @@ int step_pipelined(nyx_plan *P, nyx_level *L, const double *host_in, double *hos
   FusedArgs a = fused_args(P, S, L->grav, Sn, P->d_dtacc, false);
   const cudaStream_t cs[2] = {P->stream, P->stream2};
   unsigned waited[2] = {0u, 0u};
-  for (int g = 0; g < P->ngrp; ++g) {
-    const cudaStream_t st = cs[g & 1];
-    const unsigned need = (P->grp_src[g] | (1u << g)) & ~waited[g & 1];
+  for (int gi = 0; gi < P->ngrp; ++gi) {
+    const int g = P->proc_order[gi];
+    const cudaStream_t st = cs[gi & 1];
+    const unsigned need = (P->grp_src[g] | (1u << g)) & ~waited[gi & 1];
     for (int q = 0; q < P->ngrp; ++q)
       if ((need >> q) & 1u) CK(cudaStreamWaitEvent(st, P->ev_in[q], 0));
-    waited[g & 1] |= need;
+    waited[gi & 1] |= need;
     for (int p = 0; p < 4; ++p) {
       const int r0 = P->rect_off[p][g], nr = P->rect_off[p][g + 1] - r0;
       if (nr > 0) {
         launch_fill(S, NCONS, P->d_boxes, P->d_rects_grp[p] + r0, nullptr, nr, P->pass[p].total,
-                    st);
+                    st, true);
         P->launches += 1;
       }
     }
@@ -1658,6 +1672,7 @@ int nyx_hydro_step_host_valid(nyx_plan *P, nyx_level *L, const double *host_in, 
   }
   if (P->prm.batching != NYX_PER_BOX && P->ngrp == 0)
     if (int rc = setup_readback(P)) return rc;
+  if (P->prm.batching != NYX_PER_BOX && !(P->prm.autotune && !P->tuned)) prepare_tmaps(P, L);
   const size_t bytes = sizeof(double) * NCONS * (size_t)P->total_cells;
   double h[3] = {a_old, a_new, *dt_inout};
   CK(cudaMemcpyAsync(P->d_scal, h, 3 * sizeof(double), cudaMemcpyHostToDevice, P->stream));

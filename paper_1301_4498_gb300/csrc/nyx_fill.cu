@@ -16,32 +16,47 @@ namespace {
 // component of its cell before storing any (NC > 0: that many components;
 // 0: ncomp at run time, one at a time), instead of one dependent load and
 // store per component.
-template <int NC>
-__global__ void k_fill_rects(double *field, int ncomp, const BoxDev *boxes, const FillRect *rects,
-                             int nrect) {
+//
+// Launch shapes: the ghost fill of a whole level runs alone, 256 threads per
+// block.  The copies of the overlapped host step (scatter, per-group fill,
+// gather) run 128 threads per block at no more than 32 registers per
+// thread: the fused advance holds 80 registers x 768 threads of every SM
+// (61,440 of 65,536), which leaves room for exactly one such block beside
+// it, so one box group's copies run on the SMs while another group advances
+// instead of waiting for its end.
+constexpr int COPY_THREADS = 128;
+
+template <int NC, int BESIDE>
+__global__ void __launch_bounds__(BESIDE ? COPY_THREADS : 256, BESIDE ? 16 : 1)
+    k_fill_rects(double *field, int ncomp, const BoxDev *boxes, const FillRect *rects, int nrect) {
   for (int r = blockIdx.x; r < nrect; r += gridDim.x) {
-    const FillRect R = rects[r];
-    const BoxDev bd = boxes[R.dst_box];
-    const BoxDev bs = boxes[R.src_box];
+    const FillRect &R = rects[r];
+    const BoxDev &bd = boxes[R.dst_box];
+    const BoxDev &bs = boxes[R.src_box];
+    // only what the copy needs, so that it fits in 32 registers
+    const long long dstr = bd.stride, sstr = bs.stride;
     double *D = field + (long long)ncomp * bd.pref;
     const double *S = field + (long long)ncomp * bs.pref;
-    const int n = R.ext[0] * R.ext[1] * R.ext[2];
+    const int dN0 = bd.N[0], dN1 = bd.N[1], sN0 = bs.N[0], sN1 = bs.N[1];
+    const int e0 = R.ext[0], e1 = R.ext[1], n = R.ext[0] * R.ext[1] * R.ext[2];
+    const int d0 = R.dlo[0] + 4, d1 = R.dlo[1] + 4, d2 = R.dlo[2] + 4;
+    const int s0 = R.slo[0] + 4, s1 = R.slo[1] + 4, s2 = R.slo[2] + 4;
+    const int t0 = R.sstep[0], t1 = R.sstep[1], t2 = R.sstep[2];
     for (int f = threadIdx.x; f < n; f += blockDim.x) {
-      const int i = f % R.ext[0];
-      const int u = f / R.ext[0];
-      const int j = u % R.ext[1];
-      const int k = u / R.ext[1];
-      const long long di = cell_index(bd, R.dlo[0] + i, R.dlo[1] + j, R.dlo[2] + k);
-      const long long si = cell_index(bs, R.slo[0] + R.sstep[0] * i, R.slo[1] + R.sstep[1] * j,
-                                      R.slo[2] + R.sstep[2] * k);
+      const int i = f % e0;
+      const int u = f / e0;
+      const int j = u % e1;
+      const int k = u / e1;
+      const long long di = ((long long)(d2 + k) * dN1 + (d1 + j)) * dN0 + (d0 + i);
+      const long long si = ((long long)(s2 + t2 * k) * sN1 + (s1 + t1 * j)) * sN0 + (s0 + t0 * i);
       if constexpr (NC > 0) {
         double v[NC];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) v[c] = __ldg(S + c * bs.stride + si);
+        for (int c = 0; c < NC; ++c) v[c] = __ldg(S + c * sstr + si);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) D[c * bd.stride + di] = v[c];
+        for (int c = 0; c < NC; ++c) D[c * dstr + di] = v[c];
       } else {
-        for (int c = 0; c < ncomp; ++c) D[c * bd.stride + di] = S[c * bs.stride + si];
+        for (int c = 0; c < ncomp; ++c) D[c * dstr + di] = S[c * sstr + si];
       }
     }
   }
@@ -51,9 +66,9 @@ __global__ void k_fill_rects(double *field, int ncomp, const BoxDev *boxes, cons
 // packed box by box (box b at 6 cell_pref[b], component-major, x fastest).
 // One block per plane of each box (plane_pref[b]: the first block of box
 // b); consecutive threads take consecutive x cells on both sides.
-__global__ void k_valid_copy(double *field, double *packed, const BoxDev *boxes,
-                             const long long *cell_pref, const int *plane_pref, int nbox,
-                             int blk0, int to_field) {
+__global__ void __launch_bounds__(COPY_THREADS, 16)
+    k_valid_copy(double *field, double *packed, const BoxDev *boxes, const long long *cell_pref,
+                 const int *plane_pref, int nbox, int blk0, int to_field) {
   const int blk = blk0 + (int)blockIdx.x;
   int lo = 0, hi = nbox - 1;
   while (lo < hi) {
@@ -82,25 +97,47 @@ __global__ void k_valid_copy(double *field, double *packed, const BoxDev *boxes,
 
 }  // namespace
 
+// Load the copy kernels of the overlapped host step (with lazy module
+// loading, a kernel's first launch may wait for every kernel and copy in
+// flight, which would stall the first overlapped step behind its inputs).
+int preload_copy_kernels() {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, k_fill_rects<NCONS, 1>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_valid_copy);
+  return (int)e;
+}
+
 void launch_valid_copy(double *field, double *packed, const BoxDev *boxes,
                        const long long *cell_pref, const int *plane_pref, int nbox, int nblocks,
                        int blk0, int to_field, cudaStream_t st) {
   if (nblocks < 1) return;
-  k_valid_copy<<<nblocks, 256, 0, st>>>(field, packed, boxes, cell_pref, plane_pref, nbox, blk0,
-                                       to_field);
+  k_valid_copy<<<nblocks, COPY_THREADS, 0, st>>>(field, packed, boxes, cell_pref, plane_pref,
+                                                 nbox, blk0, to_field);
+}
+
+template <int BESIDE>
+void fill_launch(double *field, int ncomp, const BoxDev *boxes, const FillRect *rects, int nrect,
+                 cudaStream_t st) {
+  const int threads = BESIDE ? COPY_THREADS : 256;
+  const int cap = BESIDE ? 152 * 32 : 152 * 16;
+  const int grid = nrect < cap ? nrect : cap;
+  if (ncomp == NCONS)
+    k_fill_rects<NCONS, BESIDE><<<grid, threads, 0, st>>>(field, ncomp, boxes, rects, nrect);
+  else if (ncomp == NGRAV)
+    k_fill_rects<NGRAV, BESIDE><<<grid, threads, 0, st>>>(field, ncomp, boxes, rects, nrect);
+  else
+    k_fill_rects<0, BESIDE><<<grid, threads, 0, st>>>(field, ncomp, boxes, rects, nrect);
 }
 
 void launch_fill(double *field, int ncomp, const BoxDev *boxes, const FillRect *rects,
-                 const long long *rect_pref, int nrect, long long total, cudaStream_t st) {
+                 const long long *rect_pref, int nrect, long long total, cudaStream_t st,
+                 bool beside) {
   (void)rect_pref;
   if (nrect <= 0 || total <= 0) return;
-  const int grid = nrect < 152 * 16 ? nrect : 152 * 16;
-  if (ncomp == NCONS)
-    k_fill_rects<NCONS><<<grid, 256, 0, st>>>(field, ncomp, boxes, rects, nrect);
-  else if (ncomp == NGRAV)
-    k_fill_rects<NGRAV><<<grid, 256, 0, st>>>(field, ncomp, boxes, rects, nrect);
+  if (beside)
+    fill_launch<1>(field, ncomp, boxes, rects, nrect, st);
   else
-    k_fill_rects<0><<<grid, 256, 0, st>>>(field, ncomp, boxes, rects, nrect);
+    fill_launch<0>(field, ncomp, boxes, rects, nrect, st);
 }
 
 }  // namespace nyx

@@ -16,8 +16,10 @@ void record_error(const char *msg);
 void launch_valid_copy(double *field, double *packed, const BoxDev *boxes,
                        const long long *cell_pref, const int *plane_pref, int nbox, int nblocks,
                        int blk0, int to_field, cudaStream_t st);
+int preload_copy_kernels();  // cudaError_t of loading the overlapped host step's copy kernels
 void launch_fill(double *field, int ncomp, const BoxDev *boxes, const FillRect *rects,
-                 const long long *rect_pref, int nrect, long long total, cudaStream_t st);
+                 const long long *rect_pref, int nrect, long long total, cudaStream_t st,
+                 bool beside = false);
 
 void launch_step_setup(const SchemeConsts *K, const double *a_old, const double *a_new,
                        const double *dt, StepConsts *SC, const BoxDev *boxes, int nbox,

@@ -101,6 +101,7 @@ struct nyx_plan {
   std::vector<int> rect_off[4];
   std::vector<unsigned> grp_src;
   std::vector<int> in_order;
+  std::vector<int> proc_order;  // the order in which the groups advance
   // per-box FP64 form
   double *d_scratch = nullptr;
   long long Vmax = 0;
