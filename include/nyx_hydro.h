@@ -120,8 +120,9 @@ typedef struct {
                               has its profiles pulled toward the cell value.  Costs one
                               extra pass over the level per advance and, per plan, one
                               value per cell (FP64 plans double, mixed plans float). */
-  int z_chunks;            /* 1: the task-form tile shapes may cut columns into chunks of
-                              planes to even out the CTAs' loads (nyx_task_items); 0 keeps
+  int z_chunks;            /* 1: the fused kernel may cut columns into chunks of planes to
+                              even out the CTAs' loads (nyx_task_items), for example when a
+                              single box has fewer column tiles than the GPU has SMs; 0 keeps
                               whole columns.  Either gives the same result, bit for bit. */
 } nyx_hydro_params;
 
@@ -280,9 +281,9 @@ int nyx_hydro_tune_info(const nyx_plan *plan, int *classes, int *trials, int *la
  * Host only: it needs no GPU and no plan, and is the list a plan builds.
  * Each item is 7 ints (box, x0, y0, nx, ny, z0, nz): cells [x0, x0+nx) x
  * [y0, y0+ny) x [z0, z0+nz) of the box; the items tile every box once.
- * chunk = 0 keeps every column whole (the column-owning shapes); chunk != 0
- * (the task-form shapes) lets the list cut columns along z into chunks
- * when that evens out the CTAs' loads.  Items come in queue order, the
+ * chunk = 0 keeps every column whole; chunk != 0 lets the list cut columns
+ * along z into chunks when that evens out the CTAs' loads (the plans' lists,
+ * for every tile shape, with z_chunks = 1).  Items come in queue order, the
  * largest first.  Writes min(cap, *count) items to `items` (caller-owned,
  * 7 * cap ints) and the full count to *count.  NYX_EINVAL for a negative
  * size, an empty box, tx, ty or slots below 1, or a null pointer. */

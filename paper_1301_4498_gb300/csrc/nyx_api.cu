@@ -307,8 +307,8 @@ std::vector<WorkItem> tile_items(const std::vector<std::array<int, 3>> &n, int t
 }
 
 // Work list of the fused kernel for one tile shape, in the order the queue
-// hands it out (largest first).  The column-owning form takes whole columns.
-// The task form streams any range of planes, so when whole columns leave
+// hands it out (largest first).  Both forms stream any range of planes of a
+// column (a chunk starts with its own ring prologue), so when whole columns leave
 // the `slots` resident CTAs unevenly loaded (fewer tiles than CTAs, or a
 // last partial wave), the columns are cut along z: among even cuts into
 // chunks of at least 16 planes and cuts into one main chunk plus short
@@ -1147,7 +1147,7 @@ int tune_shape(nyx_plan *P, const FusedArgs &base) {
     pt.grid = std::min(P->max_grid[pt.shape], kv.first.second * nsm);
     std::sort(kv.second.begin(), kv.second.end());
     const TileShape ts = fused_shape(pt.shape);
-    pt.h_items = subset_items(*P, kv.second, ts.tx, ts.ty, pt.grid, ts.task && P->prm.z_chunks);
+    pt.h_items = subset_items(*P, kv.second, ts.tx, ts.ty, pt.grid, P->prm.z_chunks != 0);
     pt.nitems = (int)pt.h_items.size();
     CK(cudaMalloc(&pt.d_items, sizeof(WorkItem) * std::max(1, pt.nitems)));
     CK(cudaMemcpy(pt.d_items, pt.h_items.data(), sizeof(WorkItem) * pt.nitems,
@@ -1459,8 +1459,7 @@ int nyx_hydro_plan(const nyx_level_desc *lev, const nyx_hydro_params *prm, void 
       }
       for (int s = 0; s < fused_num_shapes(prm->precision); ++s) {
         TileShape ts = fused_shape(s);
-        std::vector<WorkItem> it = build_items(*P, ts.tx, ts.ty, P->max_grid[s],
-                                                ts.task && prm->z_chunks);
+        std::vector<WorkItem> it = build_items(*P, ts.tx, ts.ty, P->max_grid[s], prm->z_chunks);
         P->nitems[s] = (int)it.size();
         TRYC(cudaMalloc(&P->d_items[s], sizeof(WorkItem) * it.size()));
         TRYC(cudaMemcpy(P->d_items[s], it.data(), sizeof(WorkItem) * it.size(),

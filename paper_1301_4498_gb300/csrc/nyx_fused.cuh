@@ -387,6 +387,7 @@ __global__ void __launch_bounds__(FusedGeom<R, TX, TY>::NT, 1) k_fused(nyx::Fuse
     const nyx::BoxDev b = a.boxes[w.box];
     const nyx::BoxStep bst = a.BS[w.box];
     const int nxt = w.nx, nyt = w.ny, nz = b.n[2];
+    const int zb = w.z0, ze = w.z0 + w.nz;  // this item's planes [zb, ze)
     const long long bs = b.stride;
     const long long ps = (long long)b.N[0] * b.N[1];
     const double *S = a.S + nyx::NCONS * b.pref;
@@ -408,7 +409,7 @@ __global__ void __launch_bounds__(FusedGeom<R, TX, TY>::NT, 1) k_fused(nyx::Fuse
 #pragma unroll
       for (int o = 0; o < 4; ++o) {
         R q[5];
-        prims_of<R>(S, bs, col + (long long)(o - 3 + 4) * ps, E, q);
+        prims_of<R>(S, bs, col + (long long)(zb + o - 3 + 4) * ps, E, q);
 #pragma unroll
         for (int v = 0; v < 5; ++v) win[o][v] = q[v];
       }
@@ -430,7 +431,7 @@ __global__ void __launch_bounds__(FusedGeom<R, TX, TY>::NT, 1) k_fused(nyx::Fuse
 
     const int nstrip = 4 * (nxt + 2) + 4 * (nyt + 2);
 
-    for (int c = -1; c <= nz; ++c) {
+    for (int c = zb - 1; c <= ze; ++c) {
       // ---------------- stage 0: primitives
       if (act) {
         R q[5];
@@ -509,7 +510,7 @@ __global__ void __launch_bounds__(FusedGeom<R, TX, TY>::NT, 1) k_fused(nyx::Fuse
           face_flux<R, 1>(E, l, qy_m, F8);
           put7(B, NC, 7, me, tflux_of(F8));
         }
-        if (c >= 0) {
+        if (c >= zb) {
           face_flux<R, 2>(E, qzp_prev, qz_m, F8);
           Fz = tflux_of(F8);
         }
@@ -519,7 +520,7 @@ __global__ void __launch_bounds__(FusedGeom<R, TX, TY>::NT, 1) k_fused(nyx::Fuse
       // ---------------- stage 3: corner coupling, theta = 1/3
       R qxy_m[5], qxy_p[5], qyx_m[5], qyx_p[5], qzx_m[5], qzx_p[5], qzy_m[5], qzy_p[5];
       R qxz_m[5], qxz_p[5], qyz_m[5], qyz_p[5];
-      const bool zc = (c >= 1);  // plane c-1 is a valid plane
+      const bool zc = (c >= zb + 1);  // plane c-1 is one of the item's planes
       if (act) {
         if (inY) {
           TFlux<R> Fm = get7(B, NC, 7, me), Fp = get7(B, NC, 7, me + W);
@@ -572,11 +573,11 @@ __global__ void __launch_bounds__(FusedGeom<R, TX, TY>::NT, 1) k_fused(nyx::Fuse
           face_flux<R, 1>(E, l, qyz_m, F8);
           put7(B, NC, 21, me, tflux_of(F8));
         }
-        if (c >= 0 && inX) {  // F^{z|x} at face c-1/2
+        if (c >= zb && inX) {  // F^{z|x} at face c-1/2
           face_flux<R, 2>(E, qzx_prev, qzx_m, F8);
           Fzx = tflux_of(F8);
         }
-        if (c >= 0 && inY) {  // F^{z|y} at face c-1/2
+        if (c >= zb && inY) {  // F^{z|y} at face c-1/2
           face_flux<R, 2>(E, qzy_prev, qzy_m, F8);
           Fzy = tflux_of(F8);
         }
@@ -623,7 +624,7 @@ __global__ void __launch_bounds__(FusedGeom<R, TX, TY>::NT, 1) k_fused(nyx::Fuse
 #pragma unroll
           for (int k = 0; k < 8; ++k) B[(8 + k) * NC + me] = F8[k];
         }
-        if (c >= 0 && inX && inY) face_flux<R, 2>(E, qzf_prev, qzf_m, Ffz);
+        if (c >= zb && inX && inY) face_flux<R, 2>(E, qzf_prev, qzf_m, Ffz);
       }
       __syncthreads();
 
@@ -688,13 +689,13 @@ __global__ void __launch_bounds__(FusedGeom<R, TX, TY>::NT, 1) k_fused(nyx::Fuse
         copy5(qx_prev_p, qx_p);
         copy5(qy_prev_m, qy_m);
         copy5(qy_prev_p, qy_p);
-        if (c >= 0) Fz_prev = Fz;
+        if (c >= zb) Fz_prev = Fz;
         if (inX) copy5(qzx_prev, qzx_p);
         if (inY) copy5(qzy_prev, qzy_p);
-        if (c >= 0 && inX) Fzx_prev = Fzx;
-        if (c >= 0 && inY) Fzy_prev = Fzy;
+        if (c >= zb && inX) Fzx_prev = Fzx;
+        if (c >= zb && inY) Fzy_prev = Fzy;
         if (inX && inY) copy5(qzf_prev, qzf_p);
-        if (c >= 0 && inX && inY) copy8(Ffz_prev, Ffz);
+        if (c >= zb && inX && inY) copy8(Ffz_prev, Ffz);
       }
     }
     __syncthreads();

@@ -455,8 +455,8 @@ def _tall_box(nsteps=2):
                       5.0 / 3.0, 0.5, nsteps, False)
 
 
-def _chunk_run(w, n, shape, z_chunks, **kw):
-    plan = H.Plan(w.level, gamma=w.gamma, cfl=w.cfl, precision="mixed", z_chunks=z_chunks, **kw)
+def _chunk_run(w, n, shape, z_chunks, precision="mixed", **kw):
+    plan = H.Plan(w.level, gamma=w.gamma, cfl=w.cfl, precision=precision, z_chunks=z_chunks, **kw)
     plan.set_tile_shape(shape)
     lev = H.make_level(plan, w.state, w.grav)
     a = torch.tensor(np.asarray(w.a_sched[:n + 1], dtype=np.float64), device="cuda")
@@ -498,3 +498,28 @@ def test_task_form_chunks_equal_whole_columns_bitwise(oracle_results, name, shap
                     assert torch.equal(p1.fluxes(l1, b, di), p0.fluxes(l0, b, di)), (b, di)
         p1.close()
         p0.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("shape", [0, 1, 2])
+@pytest.mark.parametrize("name", ["comoving32", "tall"])
+def test_column_form_chunks_equal_whole_columns_bitwise(oracle_results, name, shape, precision):
+    """The column-owning form (the FP64 path's fused kernel) with its columns
+    cut into plane chunks gives the whole-column result bit for bit, and the
+    chunked list is longer where a box has fewer tiles than the GPU has
+    SMs."""
+    if name == "tall":
+        w, n = _tall_box(2), 2
+    else:
+        w, _, _, n = oracle_results(name)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    tx, ty = H.tile_shape_of(shape)
+    ext = [w.level.extent(b) for b in range(w.level.nbox)]
+    assert len(H.task_items(ext, tx, ty, sms, True)) > len(H.task_items(ext, tx, ty, sms, False))
+    p1, l1, d1 = _chunk_run(w, n, shape, 1, precision)
+    p0, l0, d0 = _chunk_run(w, n, shape, 0, precision)
+    assert np.array_equal(d0, d1)
+    for x, y in zip(p1.from_device(l1.current, 6), p0.from_device(l0.current, 6)):
+        assert np.array_equal(W.valid(x), W.valid(y))
+    p1.close()
+    p0.close()
