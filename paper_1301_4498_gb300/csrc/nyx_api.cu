@@ -928,10 +928,10 @@ int do_correct(nyx_plan *P, nyx_level *L, const double *a_old, const double *a_n
 // ---------------------------------------------------------------- autotuner
 // The level's boxes fall into box-size classes (boxes of equal extent), and
 // each class is tuned on its own.  Every candidate -- a tile shape with a
-// number of resident CTAs per SM (all that fit, or one) -- runs one wave of
-// the class's work items (as many items as the candidate keeps resident; a
-// class with fewer items has them repeated, so that the timing is of a full
-// machine), and the candidate with the least time per zone wins.  Choices are
+// number of resident CTAs per SM (all that fit, or one) -- runs two waves of
+// the class's work items (twice as many items as the candidate keeps
+// resident; a class with fewer items has them repeated, so that the timing
+// is of a full machine), and the candidate with the least time per zone wins.  Choices are
 // kept in a JSON file keyed by GPU name, SM count, precision, scheme variant
 // and box extent, so a later plan whose classes are all there makes no trial
 // launch.  Classes that settle on the same candidate share one launch; the
@@ -1071,9 +1071,9 @@ int tune_shape(nyx_plan *P, const FusedArgs &base) {
       if (full > 1) occ.push_back(1);
       for (int per_sm : occ) {
         const int grid = per_sm * nsm;
-        std::vector<WorkItem> wave(grid);
+        std::vector<WorkItem> wave(2 * grid);  // two waves: per-launch overhead weighs less
         double zones = 0.0;
-        for (int k = 0; k < grid; ++k) {
+        for (int k = 0; k < 2 * grid; ++k) {
           wave[k] = all[k % all.size()];
           zones += double(wave[k].nx) * wave[k].ny * wave[k].nz;
         }
@@ -1089,7 +1089,7 @@ int tune_shape(nyx_plan *P, const FusedArgs &base) {
         CK(cudaMemcpy(d_wave, wave.data(), sizeof(WorkItem) * wave.size(), cudaMemcpyHostToDevice));
         FusedArgs a = base;
         a.items = d_wave;
-        a.nitems = grid;
+        a.nitems = 2 * grid;
         a.dtacc = nullptr;
         a.flux_keep = nullptr;
         a.status = P->d_status_tune;
