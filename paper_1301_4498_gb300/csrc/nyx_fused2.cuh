@@ -37,6 +37,8 @@
 // Rings over planes: slot = (plane + 2) & 1 for the two-plane rings, and
 // (plane + 8) % 5 for the five-plane primitive ring.
 #pragma once
+#include <type_traits>
+
 #include "nyx_fused.cuh"
 
 namespace NYX_NS {
@@ -442,38 +444,40 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
         bar_sync_n(BAR_LOADED, NT);
 
         // ---------------------------------------------- S1: tracing at plane c
+        // The direction is uniform over a warp (kq = tid / NCP), so each
+        // direction runs its own instantiation: lab-frame stencil loads with
+        // compile-time strides, no frame permutations.
         if (act) {
-          const int dir = kq;
           const float *P0 = sm + G::PE;
           const float rho = P0[mee], p = P0[4 * NE + mee];
           const float cs2 = E.gamma * p / rho;
           const float cs = cs2 * rsqrtf(cs2);
-          const float gl0 = sm[G::GR + me], gl1 = sm[G::GR + NC + me], gl2 = sm[G::GR + 2 * NC + me];
-          float gn[3];
-          gn[0] = (dir == 0) ? gl0 : ((dir == 1) ? gl1 : gl2);
-          gn[1] = (dir == 0) ? gl1 : gl0;
-          gn[2] = (dir == 2) ? gl1 : gl2;
-          float s5[5][5];
-#pragma unroll
-          for (int o = 0; o < 5; ++o) {
-            const float *Po = (dir == 2) ? ring(c - 2 + o) : P0 + ((dir == 0) ? mee + (o - 2) : mee + (o - 2) * WE);
-            const int st = (dir == 2) ? NC : NE;
-            float ql[5], qn[5];
-#pragma unroll
-            for (int v = 0; v < 5; ++v) ql[v] = Po[v * st];
-            to_normal(dir, ql, qn);
-#pragma unroll
-            for (int v = 0; v < 5; ++v) s5[v][o] = qn[v];
-          }
-          const float dtdx = (dir == 0) ? dtdx0 : ((dir == 1) ? dtdx1 : dtdx2);
-          float qmn[5], qpn[5], qm[5], qp[5];
+          const float g3[3] = {sm[G::GR + me], sm[G::GR + NC + me], sm[G::GR + 2 * NC + me]};
           const float fl = E.flat ? sm[G::GR + 3 * NC + me] : 1.0f;
-          trace_cell<float, 0>(E, s5, cs, gn, dtdx, src, fl, qmn, qpn);
-          to_lab(dir, qmn, qm);
-          to_lab(dir, qpn, qp);
-          float *dst = (dir == 2) ? sm + G::QZ + pc * 10 * NC : sm + G::QXY + (pc * 2 + dir) * 10 * NC;
-          st5(dst, NC, me, qm);
-          st5(dst + 5 * NC, NC, me, qp);
+          auto trace_dir = [&](auto dirc) {
+            constexpr int DIR = decltype(dirc)::value;
+            float s5[5][5];
+#pragma unroll
+            for (int o = 0; o < 5; ++o) {
+              const float *Po = (DIR == 2) ? ring(c - 2 + o)
+                                           : P0 + ((DIR == 0) ? mee + (o - 2) : mee + (o - 2) * WE);
+              constexpr int st = (DIR == 2) ? NC : NE;
+#pragma unroll
+              for (int v = 0; v < 5; ++v) s5[v][o] = Po[v * st];
+            }
+            const float dtdx = (DIR == 0) ? dtdx0 : ((DIR == 1) ? dtdx1 : dtdx2);
+            float qm[5], qp[5];
+            trace_cell<float, DIR>(E, s5, cs, g3, dtdx, src, fl, qm, qp);
+            float *dst = (DIR == 2) ? sm + G::QZ + pc * 10 * NC : sm + G::QXY + (pc * 2 + DIR) * 10 * NC;
+            st5(dst, NC, me, qm);
+            st5(dst + 5 * NC, NC, me, qp);
+          };
+          if (kq == 0)
+            trace_dir(std::integral_constant<int, 0>{});
+          else if (kq == 1)
+            trace_dir(std::integral_constant<int, 1>{});
+          else
+            trace_dir(std::integral_constant<int, 2>{});
         }
         bar_sync_n(BAR_COL, NTC);
         // ring plane c-2 and the framed plane c are no longer read
