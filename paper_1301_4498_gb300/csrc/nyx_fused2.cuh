@@ -1,12 +1,25 @@
 // nyx_fused2.cuh -- the mixed-precision fused advance, task form.
 //
-// Same algorithm and stage order as nyx_fused.cuh (see its header), with a
-// different mapping onto the SM: every per-column value lives in shared
-// memory (structure-of-arrays, [field][column]) and each stage is a list of
-// independent tasks -- one trace direction of one column, one Riemann
-// problem on one face, one corner-coupling correction -- that the column
-// threads take in order (three threads per column).  Tasks of one kind are
-// padded to a whole number of warps, so a warp runs one kind at a time.
+// Same algorithm as nyx_fused.cuh (see its header), with a different
+// mapping onto the SM: every per-column value lives in shared memory
+// (structure-of-arrays, [field][column]) and each stage is a list of
+// independent tasks that the column threads take in order (three threads
+// per column).  Per plane c the column threads run four stages:
+//
+//   S1 tracing at plane c, one direction per thread (x, y, z)
+//   S2 normal solves: x, y faces of plane c, z face c-1/2
+//   S3 intermediate solves, each task first correcting its face's two
+//      states by the transverse normal fluxes (theta = 1/3): F^{x|y}, F^{y|x}
+//      at c; F^{x|z}, F^{y|z} at c-1; F^{z|x}, F^{z|y} at face c-1/2
+//   S4 final solves, each task first correcting its face's two states by
+//      the intermediate fluxes (theta = 1/2): x, y faces of plane c-1, z
+//      face c-1/2
+//
+// Each corrected state feeds exactly one face, so correcting it inside that
+// face's task does the same arithmetic as a separate correction stage,
+// without storing the states or a barrier between the two.  The z tasks
+// also correct the high side of plane c, kept in a two-plane ring for the
+// next plane's face.  S2-S4 take per-tile lists of the faces the tile needs.
 //
 // The FP64 update (stage 7) runs on its own warps, one output cell per
 // thread, decoupled from the column threads' stage barriers: the column
@@ -61,25 +74,20 @@ struct G2 {
   static constexpr int QXY = PE + 5 * NE;            // [2 planes][2 dirs x,y][10][NC] traced x, y
   static constexpr int QZ = QXY + 40 * NC;           // [2 planes][10][NC] traced z
   static constexpr int FZ = QZ + 20 * NC;            // [2 faces][7][NC] normal z fluxes
-  static constexpr int QZXM = FZ + 14 * NC;          // [5][NC] q_{z|x} low side, plane c
-  static constexpr int QZXP = QZXM + 5 * NC;         // [2 planes][5][NC] q_{z|x} high side
-  static constexpr int QZYM = QZXP + 10 * NC;        // [5][NC]
-  static constexpr int QZYP = QZYM + 5 * NC;         // [2][5][NC]
+  static constexpr int QZXP = FZ + 14 * NC;          // [2 planes][5][NC] q_{z|x} high side
+  static constexpr int QZYP = QZXP + 10 * NC;        // [2][5][NC] q_{z|y} high side
   static constexpr int FZXY = QZYP + 10 * NC;        // [2 faces][2 kinds z|x, z|y][7][NC]
-  static constexpr int QZFM = FZXY + 28 * NC;        // [5][NC] final z state, low side
-  static constexpr int QZFP = QZFM + 5 * NC;         // [2 planes][5][NC] final z, high side
-  static constexpr int P1 = QZFP + 10 * NC;          // [28][NC] pool: FX,FY | Fxy,Fyx,Fxz,Fyz
-  static constexpr int P2 = P1 + 28 * NC;            // [40][NC] pool: qxy,qyx,qxz,qyz | qxf,qyf
-  static constexpr int GR = P2 + 40 * NC;            // [4][NC] gravity and flattening, plane c
+  static constexpr int QZFP = FZXY + 28 * NC;        // [2 planes][5][NC] final z, high side
+  static constexpr int FN = QZFP + 10 * NC;          // [14][NC] normal x, y fluxes, plane c
+  static constexpr int P1 = FN + 14 * NC;            // [28][NC] Fxy, Fyx (c) | Fxz, Fyz (c-1)
+  static constexpr int GR = P1 + 28 * NC;            // [4][NC] gravity and flattening, plane c
   static constexpr int UF = GR + 4 * NC;             // [8][NUF] final x, y fluxes of plane c-1
   static constexpr int FFZ = UF + 8 * NUF;           // [2 faces][8][NZF] final z fluxes
-  // task lists of stages S2-S6 for the full tile (ushort entries)
+  // task lists of stages S2-S4 for the full tile (ushort entries)
   static constexpr int T2 = (TX + 1) * H + W * (TY + 1) + NC;
-  static constexpr int T3 = 2 * W * TY + 2 * TX * H + 2 * NC;
-  static constexpr int T4 = (TX + 1) * TY + TX * (TY + 1) + (TX + 1) * H + W * (TY + 1) + TX * H + W * TY;
-  static constexpr int T5 = TX * TY + W * TY + TX * H;
-  static constexpr int T6 = (TX + 1) * TY + TX * (TY + 1) + TX * TY;
-  static constexpr int TT = T2 + T3 + T4 + T5 + T6;
+  static constexpr int T3 = (TX + 1) * TY + TX * (TY + 1) + (TX + 1) * H + W * (TY + 1) + TX * H + W * TY;
+  static constexpr int T4 = (TX + 1) * TY + TX * (TY + 1) + TX * TY;
+  static constexpr int TT = T2 + T3 + T4;
   static constexpr int TAB = FFZ + 16 * NZF;         // [TT] ushort task lists
   static constexpr int TOTAL0 = TAB + (TT + 1) / 2;
   // TMA staging (16 x 8 tiles at one CTA per SM; the other shapes have no
@@ -268,12 +276,11 @@ __device__ __forceinline__ void face_flux_dir(const Eos<float> &E, int dir, cons
   F[7] = o[7];
 }
 
-// Task lists of stages S2-S6.  Each kind of task covers a rectangle of the
+// Task lists of stages S2-S4.  Each kind of task covers a rectangle of the
 // tile's columns (local i in [i0, nx-1+di1], j in [j0, ny-1+dj1]; -1 and n
-// are the one-cell halo): the faces or states that the tile's corner-coupled
-// fluxes need.  Kinds, in list order: S2 normal x, y, z; S3 q_{x|y}, q_{y|x},
-// q_{z|x}, q_{z|y}, q_{x|z}, q_{y|z}; S4 F^{x|y}, F^{y|x}, F^{x|z}, F^{y|z},
-// F^{z|x}, F^{z|y}; S5 final z, x, y states; S6 final x, y, z solves.
+// are the one-cell halo): the faces that the tile's corner-coupled fluxes
+// need.  Kinds, in list order: S2 normal x, y, z faces; S3 F^{x|y}, F^{y|x},
+// F^{x|z}, F^{y|z}, F^{z|x}, F^{z|y}; S4 final x, y, z faces.
 struct KRect {
   int i0, di1, j0, dj1;
 };
@@ -282,42 +289,33 @@ __device__ __forceinline__ KRect krect(int k) {
     case 0: return {0, 1, -1, 1};    // S2 x faces
     case 1: return {-1, 1, 0, 1};    // S2 y faces
     case 2: return {-1, 1, -1, 1};   // S2 z faces
-    case 3: return {-1, 1, 0, 0};    // S3 q_{x|y}
-    case 4: return {0, 0, -1, 1};    // S3 q_{y|x}
-    case 5: return {0, 0, -1, 1};    // S3 q_{z|x}
-    case 6: return {-1, 1, 0, 0};    // S3 q_{z|y}
-    case 7: return {-1, 1, -1, 1};   // S3 q_{x|z}
-    case 8: return {-1, 1, -1, 1};   // S3 q_{y|z}
-    case 9: return {0, 1, 0, 0};     // S4 F^{x|y}
-    case 10: return {0, 0, 0, 1};    // S4 F^{y|x}
-    case 11: return {0, 1, -1, 1};   // S4 F^{x|z}
-    case 12: return {-1, 1, 0, 1};   // S4 F^{y|z}
-    case 13: return {0, 0, -1, 1};   // S4 F^{z|x}
-    case 14: return {-1, 1, 0, 0};   // S4 F^{z|y}
-    case 15: return {0, 0, 0, 0};    // S5 final z state
-    case 16: return {-1, 1, 0, 0};   // S5 final x state
-    case 17: return {0, 0, -1, 1};   // S5 final y state
-    case 18: return {0, 1, 0, 0};    // S6 x faces
-    case 19: return {0, 0, 0, 1};    // S6 y faces
-    default: return {0, 0, 0, 0};    // S6 z faces
+    case 3: return {0, 1, 0, 0};     // S3 F^{x|y}
+    case 4: return {0, 0, 0, 1};     // S3 F^{y|x}
+    case 5: return {0, 1, -1, 1};    // S3 F^{x|z}
+    case 6: return {-1, 1, 0, 1};    // S3 F^{y|z}
+    case 7: return {0, 0, -1, 1};    // S3 F^{z|x}
+    case 8: return {-1, 1, 0, 0};    // S3 F^{z|y}
+    case 9: return {0, 1, 0, 0};     // S4 x faces
+    case 10: return {0, 0, 0, 1};    // S4 y faces
+    default: return {0, 0, 0, 0};    // S4 z faces
   }
 }
-__device__ __forceinline__ int kind0_of(int st) { return st == 0 ? 0 : (st == 1 ? 3 : (st == 2 ? 9 : (st == 3 ? 15 : 18))); }
-__device__ __forceinline__ int nkind_of(int st) { return (st == 1 || st == 2) ? 6 : 3; }
+__device__ __forceinline__ int kind0_of(int st) { return st == 0 ? 0 : (st == 1 ? 3 : 9); }
+__device__ __forceinline__ int nkind_of(int st) { return st == 1 ? 6 : 3; }
 
-// tn[0..4]: the number of tasks of S2..S6 for an nx x ny tile; tn[5..8]: the
-// list offsets of S3..S6 (S2 starts at 0).
-__device__ __forceinline__ void task_counts(int nx, int ny, int (&tn)[9]) {
+// tn[0..2]: the number of tasks of S2..S4 for an nx x ny tile; tn[3], tn[4]:
+// the list offsets of S3 and S4 (S2 starts at 0).
+__device__ __forceinline__ void task_counts(int nx, int ny, int (&tn)[5]) {
   int off = 0;
 #pragma unroll
-  for (int st = 0; st < 5; ++st) {
+  for (int st = 0; st < 3; ++st) {
     int n = 0;
     for (int k = kind0_of(st); k < kind0_of(st) + nkind_of(st); ++k) {
       const KRect r = krect(k);
       n += (nx + r.di1 - r.i0) * (ny + r.dj1 - r.j0);
     }
     tn[st] = n;
-    if (st > 0) tn[4 + st] = off;
+    if (st > 0) tn[2 + st] = off;
     off += n;
   }
 }
@@ -325,15 +323,13 @@ __device__ __forceinline__ void task_counts(int nx, int ny, int (&tn)[9]) {
 // Entries (kind within its stage << 12 | owned column) of every list, in
 // kind order, written by threads [0, nthr).
 template <int W>
-__device__ void build_tasks(unsigned short *tab, int nx, int ny, const int (&tn)[9], int tid,
+__device__ void build_tasks(unsigned short *tab, int nx, int ny, const int (&tn)[5], int tid,
                             int nthr) {
-  const int total = tn[5] + tn[1] + tn[2] + tn[3] + tn[4];
+  const int total = tn[0] + tn[1] + tn[2];
   for (int t = tid; t < total; t += nthr) {
     int st = 0, l = t;
-    if (t >= tn[8]) { st = 4; l = t - tn[8]; }
-    else if (t >= tn[7]) { st = 3; l = t - tn[7]; }
-    else if (t >= tn[6]) { st = 2; l = t - tn[6]; }
-    else if (t >= tn[5]) { st = 1; l = t - tn[5]; }
+    if (t >= tn[4]) { st = 2; l = t - tn[4]; }
+    else if (t >= tn[3]) { st = 1; l = t - tn[3]; }
     const int k0 = kind0_of(st);
     unsigned short e = 0;
     for (int k = 0; k < nkind_of(st); ++k) {
@@ -423,7 +419,7 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
       const float dtdx0 = d2f_rn(bst.dtdx[0]), dtdx1 = d2f_rn(bst.dtdx[1]), dtdx2 = d2f_rn(bst.dtdx[2]);
       const float c30 = d2f_rn(bst.cdt3[0]), c31 = d2f_rn(bst.cdt3[1]), c32 = d2f_rn(bst.cdt3[2]);
       const float ch0 = d2f_rn(bst.chalf[0]), ch1 = d2f_rn(bst.chalf[1]), ch2 = d2f_rn(bst.chalf[2]);
-      int tn[9];
+      int tn[5];
       task_counts(nxt, nyt, tn);
       if (nxt != tab_nx || nyt != tab_ny) {
         // the previous item's lists are no longer read (item-end barrier)
@@ -484,9 +480,9 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
         if (c < ze) bar_arrive_n(BAR_CONSUMED, NT);
 
         // ---------------------------------------------- S2: normal solves
-        // Stages S2-S6 run the tile's task lists (built for its extent when the
-        // item starts): only the tasks whose faces or states the tile needs, in
-        // kind order, dealt to the column threads in turn.
+        // Stages S2-S4 run the tile's task lists (built for its extent when the
+        // item starts): only the tasks whose faces the tile needs, in kind
+        // order, dealt to the column threads in turn.
         for (int t = tid; t < tn[0]; t += NTC) {
           const int e = ttab[t], kind = e >> 12, cm = e & 0xfff;
           const float *L, *Rr;
@@ -494,10 +490,10 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
           int lc;
           if (kind == 0) {
             L = sm + G::QXY + (pc * 2 + 0) * 10 * NC + 5 * NC; lc = cm - 1;
-            Rr = sm + G::QXY + (pc * 2 + 0) * 10 * NC; O = sm + G::P1;
+            Rr = sm + G::QXY + (pc * 2 + 0) * 10 * NC; O = sm + G::FN;
           } else if (kind == 1) {
             L = sm + G::QXY + (pc * 2 + 1) * 10 * NC + 5 * NC; lc = cm - W;
-            Rr = sm + G::QXY + (pc * 2 + 1) * 10 * NC; O = sm + G::P1 + 7 * NC;
+            Rr = sm + G::QXY + (pc * 2 + 1) * 10 * NC; O = sm + G::FN + 7 * NC;
           } else {
             L = sm + G::QZ + pm * 10 * NC + 5 * NC; lc = cm;
             Rr = sm + G::QZ + pc * 10 * NC; O = sm + G::FZ + pc * 7 * NC;
@@ -512,162 +508,133 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
         }
         bar_sync_n(BAR_COL, NTC);
 
-        // ---------------------------------------------- S3: corner coupling, theta = 1/3
+        // ---------------------------------------------- S3: intermediate solves
+        // Each task corrects its face's two states by the normal fluxes of the
+        // transverse direction (theta = 1/3) and solves: F^{x|y}, F^{y|x} at
+        // plane c; F^{x|z}, F^{y|z} at plane c-1; F^{z|x}, F^{z|y} at face
+        // c-1/2, whose tasks also correct the high side of plane c for the
+        // next plane's face (at plane zb-1 only that).
         for (int t = tid; t < tn[1]; t += NTC) {
-          const int e = ttab[tn[5] + t], kind = e >> 12, cm = e & 0xfff;
+          const int e = ttab[tn[3] + t], kind = e >> 12, cm = e & 0xfff;
           const float *Q, *Fmb, *Fpb;
-          float *Om, *Op;
-          int fpc;
+          float *O;
+          int foff, lstep, dir;
           float coef;
           switch (kind) {
-            case 0:  // q_{x|y} at c
-              Q = sm + G::QXY + (pc * 2 + 0) * 10 * NC; Fmb = Fpb = sm + G::P1 + 7 * NC;
-              fpc = cm + W; coef = c31; Om = sm + G::P2; Op = sm + G::P2 + 5 * NC;
-              break;
-            case 1:  // q_{y|x} at c
-              Q = sm + G::QXY + (pc * 2 + 1) * 10 * NC; Fmb = Fpb = sm + G::P1;
-              fpc = cm + 1; coef = c30; Om = sm + G::P2 + 10 * NC; Op = sm + G::P2 + 15 * NC;
-              break;
-            case 2:  // q_{z|x} at c
-              Q = sm + G::QZ + pc * 10 * NC; Fmb = Fpb = sm + G::P1;
-              fpc = cm + 1; coef = c30; Om = sm + G::QZXM; Op = sm + G::QZXP + pc * 5 * NC;
-              break;
-            case 3:  // q_{z|y} at c
-              Q = sm + G::QZ + pc * 10 * NC; Fmb = Fpb = sm + G::P1 + 7 * NC;
-              fpc = cm + W; coef = c31; Om = sm + G::QZYM; Op = sm + G::QZYP + pc * 5 * NC;
-              break;
-            case 4:  // q_{x|z} at c-1
-              Q = sm + G::QXY + (pm * 2 + 0) * 10 * NC; Fmb = sm + G::FZ + pm * 7 * NC;
-              Fpb = sm + G::FZ + pc * 7 * NC; fpc = cm; coef = c32;
-              Om = sm + G::P2 + 20 * NC; Op = sm + G::P2 + 25 * NC;
-              break;
-            default:  // q_{y|z} at c-1
-              Q = sm + G::QXY + (pm * 2 + 1) * 10 * NC; Fmb = sm + G::FZ + pm * 7 * NC;
-              Fpb = sm + G::FZ + pc * 7 * NC; fpc = cm; coef = c32;
-              Om = sm + G::P2 + 30 * NC; Op = sm + G::P2 + 35 * NC;
-              break;
-          }
-          if (kind < 4 || zc) {
-            const TFlux<float> Fm = ld7(Fmb, NC, cm), Fp = ld7(Fpb, NC, fpc);
-            float qa[5], qb[5], oa[5], ob[5];
-            ld5(Q, NC, cm, qa);
-            ld5(Q + 5 * NC, NC, cm, qb);
-            transverse1(E, qa, coef, Fp, Fm, oa);
-            transverse1(E, qb, coef, Fp, Fm, ob);
-            st5(Om, NC, cm, oa);
-            st5(Op, NC, cm, ob);
-          }
-        }
-        bar_sync_n(BAR_COL, NTC);
-
-        // ---------------------------------------------- S4: intermediate solves
-        for (int t = tid; t < tn[2]; t += NTC) {
-          const int e = ttab[tn[6] + t], kind = e >> 12, cm = e & 0xfff;
-          const float *L, *Rr;
-          float *O;
-          int lc, dir;
-          switch (kind) {
-            case 0:  // F^{x|y} at c
-              dir = 0; L = sm + G::P2 + 5 * NC; lc = cm - 1; Rr = sm + G::P2; O = sm + G::P1;
+            case 0:  // F^{x|y} at c: x states corrected by the y fluxes
+              Q = sm + G::QXY + (pc * 2 + 0) * 10 * NC; Fmb = Fpb = sm + G::FN + 7 * NC;
+              foff = W; coef = c31; lstep = 1; dir = 0; O = sm + G::P1;
               break;
             case 1:  // F^{y|x} at c
-              dir = 1; L = sm + G::P2 + 15 * NC; lc = cm - W; Rr = sm + G::P2 + 10 * NC;
-              O = sm + G::P1 + 7 * NC;
+              Q = sm + G::QXY + (pc * 2 + 1) * 10 * NC; Fmb = Fpb = sm + G::FN;
+              foff = 1; coef = c30; lstep = W; dir = 1; O = sm + G::P1 + 7 * NC;
               break;
-            case 2:  // F^{x|z} at c-1
-              dir = 0; L = sm + G::P2 + 25 * NC; lc = cm - 1; Rr = sm + G::P2 + 20 * NC;
+            case 2:  // F^{x|z} at c-1: z fluxes of faces c-3/2 and c-1/2
+              Q = sm + G::QXY + (pm * 2 + 0) * 10 * NC; Fmb = sm + G::FZ + pm * 7 * NC;
+              Fpb = sm + G::FZ + pc * 7 * NC; foff = 0; coef = c32; lstep = 1; dir = 0;
               O = sm + G::P1 + 14 * NC;
               break;
             case 3:  // F^{y|z} at c-1
-              dir = 1; L = sm + G::P2 + 35 * NC; lc = cm - W; Rr = sm + G::P2 + 30 * NC;
+              Q = sm + G::QXY + (pm * 2 + 1) * 10 * NC; Fmb = sm + G::FZ + pm * 7 * NC;
+              Fpb = sm + G::FZ + pc * 7 * NC; foff = 0; coef = c32; lstep = W; dir = 1;
               O = sm + G::P1 + 21 * NC;
               break;
             case 4:  // F^{z|x} at face c-1/2
-              dir = 2; L = sm + G::QZXP + pm * 5 * NC; lc = cm; Rr = sm + G::QZXM;
-              O = sm + G::FZXY + (pc * 2 + 0) * 7 * NC;
+              Q = sm + G::QZ + pc * 10 * NC; Fmb = Fpb = sm + G::FN;
+              foff = 1; coef = c30; lstep = 0; dir = 2; O = sm + G::FZXY + (pc * 2 + 0) * 7 * NC;
               break;
             default:  // F^{z|y} at face c-1/2
-              dir = 2; L = sm + G::QZYP + pm * 5 * NC; lc = cm; Rr = sm + G::QZYM;
-              O = sm + G::FZXY + (pc * 2 + 1) * 7 * NC;
+              Q = sm + G::QZ + pc * 10 * NC; Fmb = Fpb = sm + G::FN + 7 * NC;
+              foff = W; coef = c31; lstep = 0; dir = 2; O = sm + G::FZXY + (pc * 2 + 1) * 7 * NC;
               break;
           }
-          if (kind < 2 || (kind < 4 ? zc : c >= zb)) {
-            float l[5], r[5], F[8];
-            ld5(L, NC, lc, l);
-            ld5(Rr, NC, cm, r);
+          float l[5], r[5];
+          bool go;
+          if (kind < 4) {
+            go = kind < 2 || zc;
+            if (go) {
+              const int lcl = cm - lstep;  // the cell left of the face: its high side
+              float q[5];
+              ld5(Q + 5 * NC, NC, lcl, q);
+              transverse1(E, q, coef, ld7(Fpb, NC, lcl + foff), ld7(Fmb, NC, lcl), l);
+              ld5(Q, NC, cm, q);
+              transverse1(E, q, coef, ld7(Fpb, NC, cm + foff), ld7(Fmb, NC, cm), r);
+            }
+          } else {
+            // the cell of plane c: its high side for face c+1/2, its low side here
+            float *ring_z = sm + ((kind == 4) ? G::QZXP : G::QZYP);
+            const TFlux<float> Fm = ld7(Fmb, NC, cm), Fp = ld7(Fpb, NC, cm + foff);
+            float q[5], h[5];
+            ld5(Q + 5 * NC, NC, cm, q);
+            transverse1(E, q, coef, Fp, Fm, h);
+            st5(ring_z + pc * 5 * NC, NC, cm, h);
+            go = c >= zb;
+            if (go) {
+              ld5(Q, NC, cm, q);
+              transverse1(E, q, coef, Fp, Fm, r);
+              ld5(ring_z + pm * 5 * NC, NC, cm, l);
+            }
+          }
+          if (go) {
+            float F[8];
             face_flux_dir(E, dir, l, r, F);
             st7(O, NC, cm, F);
           }
         }
         bar_sync_n(BAR_COL, NTC);
 
-        // ---------------------------------------------- S5: final states, theta = 1/2
-        for (int t = tid; t < tn[3]; t += NTC) {
-          const int e = ttab[tn[7] + t], kind = e >> 12, cm = e & 0xfff;
-          const float *Q, *Ab, *Bmb, *Bpb;
-          float *Om, *Op;
-          int apc, bpc;
-          float k1c, k2c;
-          if (kind == 0) {  // z at plane c: F^{x|y} in x, F^{y|x} in y
-            Q = sm + G::QZ + pc * 10 * NC;
-            Ab = sm + G::P1; apc = cm + 1; k1c = ch0;
-            Bmb = Bpb = sm + G::P1 + 7 * NC; bpc = cm + W; k2c = ch1;
-            Om = sm + G::QZFM; Op = sm + G::QZFP + pc * 5 * NC;
-          } else if (kind == 1) {  // x at plane c-1: F^{y|z} in y, F^{z|y} in z
-            Q = sm + G::QXY + (pm * 2 + 0) * 10 * NC;
-            Ab = sm + G::P1 + 21 * NC; apc = cm + W; k1c = ch1;
-            Bmb = sm + G::FZXY + (pm * 2 + 1) * 7 * NC; Bpb = sm + G::FZXY + (pc * 2 + 1) * 7 * NC;
-            bpc = cm; k2c = ch2;
-            Om = sm + G::P2; Op = sm + G::P2 + 5 * NC;
-          } else {  // y at plane c-1: F^{x|z} in x, F^{z|x} in z
-            Q = sm + G::QXY + (pm * 2 + 1) * 10 * NC;
-            Ab = sm + G::P1 + 14 * NC; apc = cm + 1; k1c = ch0;
-            Bmb = sm + G::FZXY + (pm * 2 + 0) * 7 * NC; Bpb = sm + G::FZXY + (pc * 2 + 0) * 7 * NC;
-            bpc = cm; k2c = ch2;
-            Om = sm + G::P2 + 10 * NC; Op = sm + G::P2 + 15 * NC;
-          }
-          if (kind == 0 || zc) {
-            const TFlux<float> Am = ld7(Ab, NC, cm), Ap = ld7(Ab, NC, apc);
-            const TFlux<float> Bm = ld7(Bmb, NC, cm), Bp = ld7(Bpb, NC, bpc);
-            float qa[5], qb[5], oa[5], ob[5];
-            ld5(Q, NC, cm, qa);
-            ld5(Q + 5 * NC, NC, cm, qb);
-            transverse2(E, qa, k1c, Ap, Am, k2c, Bp, Bm, oa);
-            transverse2(E, qb, k1c, Ap, Am, k2c, Bp, Bm, ob);
-            st5(Om, NC, cm, oa);
-            st5(Op, NC, cm, ob);
-          }
-        }
-        bar_sync_n(BAR_COL, NTC);
-
-        // ---------------------------------------------- S6: final solves
-        // The fluxes go to the update warps' buffers: x and y faces of plane
-        // c-1, z face c-1/2 (slot c & 1).  The buffers are written once the
-        // update of plane c-2 has released them, and handed over after.
-        // The list holds at most one task per column thread.
+        // ---------------------------------------------- S4: final solves
+        // Each task corrects its face's two states by the intermediate fluxes
+        // of both transverse directions (theta = 1/2) and solves: x and y faces
+        // of plane c-1, z face c-1/2 (whose tasks also correct the high side of
+        // plane c for the next face).  The fluxes go to the update warps'
+        // buffers, written once the update of plane c-2 has released them and
+        // handed over after.  The list holds at most one task per column thread.
         {
           bool go = false;
           float F[8];
           int kind = 0, cm = 0;
-          if (tid < tn[4]) {
-            const int e = ttab[tn[8] + tid];
+          if (tid < tn[2]) {
+            const int e = ttab[tn[4] + tid];
             kind = e >> 12;
             cm = e & 0xfff;
-            const float *L, *Rr;
-            int lc;
-            if (kind == 0) {
-              go = zc; L = sm + G::P2 + 5 * NC; lc = cm - 1; Rr = sm + G::P2;
-            } else if (kind == 1) {
-              go = zc; L = sm + G::P2 + 15 * NC; lc = cm - W; Rr = sm + G::P2 + 10 * NC;
+            float l[5], r[5], q[5];
+            if (kind < 2) {
+              go = zc;
+              if (go) {
+                // x: F^{y|z} in y, F^{z|y} in z; y: F^{x|z} in x, F^{z|x} in z
+                const float *Q = sm + G::QXY + (pm * 2 + kind) * 10 * NC;
+                const float *Ab = sm + G::P1 + (kind == 0 ? 21 : 14) * NC;
+                const int aoff = (kind == 0) ? W : 1;
+                const float k1c = (kind == 0) ? ch1 : ch0;
+                const float *Bmb = sm + G::FZXY + (pm * 2 + (kind == 0 ? 1 : 0)) * 7 * NC;
+                const float *Bpb = sm + G::FZXY + (pc * 2 + (kind == 0 ? 1 : 0)) * 7 * NC;
+                const int lcl = cm - ((kind == 0) ? 1 : W);
+                ld5(Q + 5 * NC, NC, lcl, q);
+                transverse2(E, q, k1c, ld7(Ab, NC, lcl + aoff), ld7(Ab, NC, lcl), ch2,
+                            ld7(Bpb, NC, lcl), ld7(Bmb, NC, lcl), l);
+                ld5(Q, NC, cm, q);
+                transverse2(E, q, k1c, ld7(Ab, NC, cm + aoff), ld7(Ab, NC, cm), ch2,
+                            ld7(Bpb, NC, cm), ld7(Bmb, NC, cm), r);
+              }
             } else {
-              go = c >= zb; L = sm + G::QZFP + pm * 5 * NC; lc = cm; Rr = sm + G::QZFM;
+              // z at plane c: F^{x|y} in x, F^{y|x} in y
+              const float *Q = sm + G::QZ + pc * 10 * NC;
+              const TFlux<float> Am = ld7(sm + G::P1, NC, cm), Ap = ld7(sm + G::P1, NC, cm + 1);
+              const TFlux<float> Bm = ld7(sm + G::P1 + 7 * NC, NC, cm);
+              const TFlux<float> Bp = ld7(sm + G::P1 + 7 * NC, NC, cm + W);
+              float h[5];
+              ld5(Q + 5 * NC, NC, cm, q);
+              transverse2(E, q, ch0, Ap, Am, ch1, Bp, Bm, h);
+              st5(sm + G::QZFP + pc * 5 * NC, NC, cm, h);
+              go = c >= zb;
+              if (go) {
+                ld5(Q, NC, cm, q);
+                transverse2(E, q, ch0, Ap, Am, ch1, Bp, Bm, r);
+                ld5(sm + G::QZFP + pm * 5 * NC, NC, cm, l);
+              }
             }
-            if (go) {
-              float l[5], r[5];
-              ld5(L, NC, lc, l);
-              ld5(Rr, NC, cm, r);
-              face_flux_dir(E, kind, l, r, F);
-            }
+            if (go) face_flux_dir(E, kind, l, r, F);
           }
           if (c >= zb + 2) bar_sync_n(BAR_FREE, NT);
           if (go) {
@@ -682,7 +649,7 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
             bar_arrive_n(BAR_READY, NT);
           }
         }
-        // no barrier here: the next plane's inputs touch nothing S2-S6 read or write
+        // no barrier here: the next plane's inputs touch nothing S2-S4 read or write
       }
     } else {
       // ------------------------------------------------ update warps (stage 7)
