@@ -43,9 +43,10 @@
 // At 16 x 8 tiles (one CTA per SM) the update warps take each plane's state
 // (at plane c+2, for the ring) and gravity (at plane c) from staging buffers
 // that tensor copies (TMA, cp.async.bulk.tensor with per-box descriptors)
-// fill one plane ahead: the copies of the next plane's inputs go once every
-// update thread has read the buffers, and complete on an mbarrier whose wait
-// is bounded.  The frame strips and the update's own reads stay plain loads.
+// fill one plane ahead: two buffers for alternate planes, the next plane's
+// copies sent as soon as every update thread is past the plane that last
+// read that buffer, each buffer completing on its own mbarrier whose wait is
+// bounded.  The frame strips and the update's own reads stay plain loads.
 //
 // Rings over planes: slot = (plane + 2) & 1 for the two-plane rings, and
 // (plane + 8) % 5 for the five-plane primitive ring.
@@ -90,20 +91,25 @@ struct G2 {
   static constexpr int TT = T2 + T3 + T4;
   static constexpr int TAB = FFZ + 16 * NZF;         // [TT] ushort task lists
   static constexpr int TOTAL0 = TAB + (TT + 1) / 2;
-  // TMA staging (16 x 8 tiles at one CTA per SM; the other shapes have no
-  // room): one plane of the state (6 components) and of gravity (3) over
-  // the tile's columns, x from x0 + 2 (an even coordinate: 16-byte aligned)
-  // for SX doubles, y from y0 + 3 for H rows, as FP64, and the mbarrier the
+  // TMA staging (16 x 8 tiles at one CTA per SM): one plane of the state
+  // (6 components) and of gravity (3) over the tile's columns, x from x0 + 2
+  // (an even coordinate: 16-byte aligned) for SX doubles, y from y0 + 3 for H
+  // rows, as FP64, in two buffers for alternate planes, and the mbarriers the
   // copies complete on
   static constexpr bool TMA = (TX == 16 && TY == 8 && XU > 0);
   static constexpr int SX = TX + 4;
   static constexpr int STG = (TOTAL0 + 255) / 256 * 256;  // 1024-byte aligned
-  static constexpr int STGS = STG;                        // [6][H][SX] doubles
-  static constexpr int STGG = STGS + 2 * 6 * H * SX;      // [3][H][SX] doubles
-  static constexpr int MBAR = STGG + 2 * 3 * H * SX;      // one 8-byte mbarrier
+  // two buffers, used by alternate planes: [6][H][SX] + [3][H][SX] doubles each
+  // one buffer, in floats, rounded up to 128 bytes (a tensor copy's
+  // destination must be 128-byte aligned)
+  static constexpr int STGB = (2 * 9 * H * SX + 31) / 32 * 32;
+  static constexpr int STGS = STG;                        // state part of buffer 0
+  static constexpr int STGG = STGS + 2 * 6 * H * SX;      // gravity part of buffer 0
+  static constexpr int MBAR = STG + 2 * STGB;             // two 8-byte mbarriers
+  static_assert((STGG - STGS) % 32 == 0, "gravity staging must start on a 128-byte boundary");
   static constexpr unsigned STG_BYTES_S = 8u * 6 * H * SX, STG_BYTES_G = 8u * 3 * H * SX;
   // + 32 floats: the staging area is aligned to 128 bytes at run time
-  static constexpr int TOTAL = TMA ? MBAR + 2 + 32 : TOTAL0;
+  static constexpr int TOTAL = TMA ? MBAR + 4 + 32 : TOTAL0;
   static constexpr size_t SMEM = sizeof(float) * (size_t)TOTAL;
   static_assert(SMEM <= 227 * 1024, "task-form tile does not fit in shared memory");
 };
@@ -165,7 +171,6 @@ __device__ __forceinline__ void fence_async_smem() {
 // the column threads' stage barrier; the flux hand-over pair; the input
 // hand-over pair.
 constexpr int BAR_COL = 1, BAR_READY = 2, BAR_FREE = 3, BAR_LOADED = 4, BAR_CONSUMED = 5;
-constexpr int BAR_UPD = 6;  // the update warps among themselves (TMA staging)
 __device__ __forceinline__ void bar_sync_n(int id, int n) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
@@ -391,13 +396,15 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
   // need a 128-byte aligned destination); offsets below are relative to it
   float *stg = sm + G::STG;
   if constexpr (G::TMA) stg += ((128u - (smem_addr(stg) & 127u)) & 127u) / 4u;
-  void *tbar = G::TMA ? static_cast<void *>(stg + (G::MBAR - G::STG)) : nullptr;
-  unsigned tph = 0;
+  // buffer k's mbarrier, and the phase parity each update thread waits for
+  auto tbar = [&](int k) { return static_cast<void *>(stg + (G::MBAR - G::STG) + 2 * k); };
+  unsigned tph0 = 0, tph1 = 0;
   bool use_tma = G::TMA && a.tmS != nullptr && (a.G == nullptr || a.tmG != nullptr);
   if constexpr (G::TMA) {
     if (tid == 0) {
       s_tma_fail = 0;
-      mbar_init(tbar, 1);
+      mbar_init(tbar(0), 1);
+      mbar_init(tbar(1), 1);
     }
   }
 
@@ -690,24 +697,28 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
         tmap_acquire(tmS_b);
         if (tmG_b) tmap_acquire(tmG_b);
       }
+      // the copies of inputs(c) go to buffer c & 1
       auto issue = [&](int c) {
         if constexpr (G::TMA) {
           if (uthr == 0) {
-            fence_async_smem();  // earlier reads of the buffers precede the copies
-            mbar_expect_tx(tbar, G::STG_BYTES_S + (tmG_b ? G::STG_BYTES_G : 0u));
-            tma_load_4d(stg + (G::STGS - G::STG), tmS_b, w.x0 + 2, w.y0 + 3, c + 2 + 4, 0, tbar);
+            const int k = c & 1;
+            float *buf = stg + k * G::STGB;
+            fence_async_smem();  // earlier reads of the buffer precede the copies
+            mbar_expect_tx(tbar(k), G::STG_BYTES_S + (tmG_b ? G::STG_BYTES_G : 0u));
+            tma_load_4d(buf, tmS_b, w.x0 + 2, w.y0 + 3, c + 2 + 4, 0, tbar(k));
             if (tmG_b)
-              tma_load_4d(stg + (G::STGG - G::STG), tmG_b, w.x0 + 2, w.y0 + 3, c + 4, 0, tbar);
+              tma_load_4d(buf + (G::STGG - G::STGS), tmG_b, w.x0 + 2, w.y0 + 3, c + 4, 0, tbar(k));
           }
         }
       };
-      bool staged = false;  // the copies of the next inputs() are in flight
       // inputs of plane c: ring plane c+2; plane c's gravity, flattening and
       // framed copy (its own columns from the ring, the frame strips loaded)
-      auto inputs = [&](int c) {
+      auto inputs = [&](int c, bool staged) {
+        const float *buf = stg + (c & 1) * G::STGB;
         if (G::TMA && staged) {
-          if (mbar_wait(tbar, tph)) {
-            tph ^= 1u;
+          unsigned &ph = (c & 1) ? tph1 : tph0;
+          if (mbar_wait(tbar(c & 1), ph)) {
+            ph ^= 1u;
           } else {  // gave up: flag it; the phase stays the one still owed
             flags |= nyx::ST_TIMEOUT;
             s_tma_fail = 1;
@@ -721,14 +732,14 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
           if (G::TMA && staged) {
             // the column's values from the staging buffers
             const int sidx = (e / W) * G::SX + (e % W + 1);
-            const double *stS = reinterpret_cast<const double *>(stg + (G::STGS - G::STG));
+            const double *stS = reinterpret_cast<const double *>(buf);
             float q[5];
             prims_of<float>(stS, G::H * G::SX, sidx, E, q);
             float *dst = ring_at(c + 2) + e;
 #pragma unroll
             for (int v = 0; v < 5; ++v) dst[v * NC] = q[v];
             if (tmG_b) {
-              const double *stG = reinterpret_cast<const double *>(stg + (G::STGG - G::STG));
+              const double *stG = reinterpret_cast<const double *>(buf + (G::STGG - G::STGS));
               g0 = d2f_rn(stG[sidx]);
               g1 = d2f_rn(stG[G::H * G::SX + sidx]);
               g2 = d2f_rn(stG[2 * G::H * G::SX + sidx]);
@@ -749,17 +760,6 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
           const int ee = (e / W + 2) * WE + (e % W + 2);
 #pragma unroll
           for (int v = 0; v < 5; ++v) sm[G::PE + v * NE + ee] = rc[v * NC];
-        }
-        if constexpr (G::TMA) {
-          // the staging buffers are read: the first update warp waits until
-          // every update thread is past this point (the others only arrive)
-          // and its first thread sends the copies of the next inputs
-          if (uthr < 32)
-            bar_sync_n(BAR_UPD, G::NU);
-          else
-            bar_arrive_n(BAR_UPD, G::NU);
-          staged = use_tma && c + 1 <= ze;
-          if (staged) issue(c + 1);
         }
         for (int u = uthr; u < nstrip; u += G::NU) {
           int x, y;
@@ -808,13 +808,17 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
         for (int k = zb - 3; k <= zb; ++k)
           load_prims(col + (long long)(k + 4) * ps, ring_at(k) + e, NC);
       }
-      inputs(zb - 1);  // plain loads; it issues the copies of plane zb's inputs
+      inputs(zb - 1, false);  // plain loads
+      if (use_tma) issue(zb);
       __threadfence_block();
       bar_arrive_n(BAR_LOADED, NT);
       for (int c = zb; c <= ze; ++c) {
-        // plane c-1 traced: its ring plane c-3 slot and the framed plane are free
+        // plane c-1 traced: its ring plane c-3 slot and the framed plane are
+        // free, and every update thread is past inputs(c-1), so buffer
+        // (c+1) & 1 is free for the copies of the next plane's inputs
         bar_sync_n(BAR_CONSUMED, NT);
-        inputs(c);
+        if (use_tma && c + 1 <= ze) issue(c + 1);
+        inputs(c, use_tma);
         __threadfence_block();
         bar_arrive_n(BAR_LOADED, NT);
         if (c >= zb + 2) {
@@ -833,7 +837,10 @@ __global__ void __launch_bounds__(G2<TX, TY, XU_OF(MB)>::NT, MB) k_fused2(nyx::F
   if constexpr (G::TMA) {
     // a wait that gave up may have left copies in flight: wait once more
     // (bounded) before the CTA's shared memory goes
-    if (s_tma_fail && tid == NTC) mbar_wait(tbar, tph);
+    if (s_tma_fail && tid == NTC) {
+      mbar_wait(tbar(0), tph0);
+      mbar_wait(tbar(1), tph1);
+    }
   }
 
   if (a.dtacc) {
