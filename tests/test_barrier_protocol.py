@@ -8,9 +8,11 @@ barriers per box tile:
     ze = nz, or a chunk of it);
   * the update warps write the primitive ring's planes zb-3 .. zb+1 and plane
     zb-1's frame, gravity and flattening rows, and arrive on LOADED; then for
-    c = zb .. ze they wait on CONSUMED, write ring plane c+2 and plane c's
-    frame, arrive on LOADED, and (c >= zb+2) wait on READY, update plane c-2
-    and arrive on FREE; finally they wait on READY and update plane ze-1;
+    c = zb .. ze they wait on CONSUMED (and send the tensor copies of plane
+    c+1's inputs into the staging buffer that plane c-1 used), write ring
+    plane c+2 and plane c's frame, arrive on LOADED, and (c >= zb+2) wait on
+    READY, update plane c-2 and arrive on FREE; finally they wait on READY
+    and update plane ze-1;
   * the column threads, plane step c = zb-1 .. ze: wait on LOADED, trace
     plane c (ring planes c-2 .. c+2, the frame of plane c), pass their stage
     barrier, arrive on CONSUMED when c < ze, run their other stages, wait on
@@ -41,7 +43,7 @@ def producer_ops(zb, ze):
         ops.append(("sync", BAR_COL, NTC))           # end of the trace stage
         if c < ze:
             ops.append(("arrive", BAR_CONSUMED, NT))
-        ops += [("sync", BAR_COL, NTC)] * 4          # stage barriers S2..S5
+        ops += [("sync", BAR_COL, NTC)] * 2          # stage barriers after S2 and S3
         if c >= zb + 2:
             ops.append(("sync", BAR_FREE, NT))
         ops.append(("store", c))
