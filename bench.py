@@ -73,7 +73,7 @@ ALG_FP32_FLOPS_MIXED = ALG_FLOPS_PER_ZONE["mixed"] - 165
 # same sizes.  Reported only for that kernel, workload and shape, and only
 # while the kernel is the one captured.
 NOMINAL_HBM_GBS = 7900.0   # HBM3e nominal rate of the part, beside the measured copy rate
-TRAFFIC_BYTES_PER_ZONE = {("large", 3): 154.6, ("large128", 3): 154.6}
+TRAFFIC_BYTES_PER_ZONE = {("large", 3): 154.3, ("large128", 3): 154.3}
 # Unit-count peaks (152 SMs at the 2070 MHz maximum clock; 128 FP32 and 2
 # FP64 FMA lanes per SM per clock), reported beside the measured ones.
 NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
