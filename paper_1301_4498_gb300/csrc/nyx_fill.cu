@@ -27,7 +27,7 @@ namespace {
 constexpr int COPY_THREADS = 128;
 
 template <int NC, int BESIDE>
-__global__ void __launch_bounds__(BESIDE ? COPY_THREADS : 256, BESIDE ? 16 : 1)
+__global__ void __launch_bounds__(BESIDE ? COPY_THREADS : 256, BESIDE ? 16 : 4)
     k_fill_rects(double *field, int ncomp, const BoxDev *boxes, const FillRect *rects, int nrect) {
   for (int r = blockIdx.x; r < nrect; r += gridDim.x) {
     const FillRect &R = rects[r];
@@ -42,6 +42,33 @@ __global__ void __launch_bounds__(BESIDE ? COPY_THREADS : 256, BESIDE ? 16 : 1)
     const int d0 = R.dlo[0] + 4, d1 = R.dlo[1] + 4, d2 = R.dlo[2] + 4;
     const int s0 = R.slo[0] + 4, s1 = R.slo[1] + 4, s2 = R.slo[2] + 4;
     const int t0 = R.sstep[0], t1 = R.sstep[1], t2 = R.sstep[2];
+    if constexpr (NC > 0 && !BESIDE) {
+      // 16-byte copies (two x cells per thread, double2 loads and stores)
+      // when both sides' rows start and stay on 16-byte boundaries: an even
+      // x extent copied forward, even row starts (box offset + first x),
+      // row lengths and component strides, a 16-byte aligned field
+      const long long dref = (long long)ncomp * bd.pref + d0, sref = (long long)ncomp * bs.pref + s0;
+      const bool vec = t0 == 1 && !(e0 & 1) && !(dref & 1) && !(sref & 1) && !(dN0 & 1) &&
+                       !(sN0 & 1) && !(dstr & 1) && !(sstr & 1) &&
+                       !(reinterpret_cast<unsigned long long>(field) & 15ull);
+      if (vec) {
+        const int h0 = e0 >> 1, nv = n >> 1;
+        for (int f = threadIdx.x; f < nv; f += blockDim.x) {
+          const int i = 2 * (f % h0);
+          const int u = f / h0;
+          const int j = u % e1;
+          const int k = u / e1;
+          const long long di = ((long long)(d2 + k) * dN1 + (d1 + j)) * dN0 + (d0 + i);
+          const long long si = ((long long)(s2 + t2 * k) * sN1 + (s1 + t1 * j)) * sN0 + (s0 + i);
+          double2 v[NC];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) v[c] = __ldg(reinterpret_cast<const double2 *>(S + c * sstr + si));
+#pragma unroll
+          for (int c = 0; c < NC; ++c) *reinterpret_cast<double2 *>(D + c * dstr + di) = v[c];
+        }
+        continue;
+      }
+    }
     for (int f = threadIdx.x; f < n; f += blockDim.x) {
       const int i = f % e0;
       const int u = f / e0;
