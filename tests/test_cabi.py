@@ -42,7 +42,7 @@ def _plan_rc(lib, spec, **kw):
 
 
 @pytest.mark.parametrize("case", ["odd", "ng", "overlap", "gap", "outside", "domain", "dx",
-                                  "bc"])
+                                  "bc", "empty"])
 def test_invalid_levels_rejected(lib, case):
     spec = W.tiled_level(32, 16)
     if case == "odd":
@@ -61,6 +61,8 @@ def test_invalid_levels_rejected(lib, case):
         spec.dx[2][1] = 0.0
     elif case == "bc":
         spec.dom_bc[0][0] = 7
+    elif case == "empty":
+        spec = W.tiled_level(32, 16).subset([])  # a level with no boxes
     rc, msg, h = _plan_rc(lib, spec)
     assert rc == H.NYX_EINVAL, (rc, msg)
     assert msg

@@ -523,3 +523,51 @@ def test_column_form_chunks_equal_whole_columns_bitwise(oracle_results, name, sh
         assert np.array_equal(W.valid(x), W.valid(y))
     p1.close()
     p0.close()
+
+
+# ------------------------------------------------------------------ degenerate input
+
+def _uniform_moving(n=48, box=24, nsteps=2):
+    """A uniform state moving obliquely under a uniform gravity, on a periodic
+    n^3 level of box^3 boxes (24 = 16 + 8: ragged 16 x 8 tiles)."""
+    lev = W.tiled_level(n, box)
+    shape = (box, box, box)
+    rho = np.full(shape, 1.3)
+    u = np.stack([np.full(shape, v) for v in (0.2, -0.1, 0.05)])
+    g = np.stack([np.full(shape, v) for v in (0.01, 0.02, -0.03)])
+    S, G = [], []
+    for b in range(lev.nbox):
+        s, gg = W._patch_state(lev, b, W.Fields(rho, u, g))
+        S.append(s)
+        G.append(gg)
+    return W.Workload("uniform", lev, S, G, W.a_schedule(1.0 / 51, 1.0 / 49, nsteps), 5.0 / 3.0,
+                      0.5, nsteps)
+
+
+@pytest.mark.parametrize("precision,shape", [("fp64", 1), ("mixed", 0), ("mixed", 3)])
+def test_uniform_state_stays_uniform_and_matches_oracle(precision, shape):
+    """Every face of a uniform state carries the same flux, so the flux
+    divergence vanishes exactly and every cell of every box takes the same
+    update: the result is uniform bit for bit, in both precisions and on
+    ragged tiles; its value is the oracle's (FP64 tolerance, mixed gates)."""
+    w = _uniform_moving()
+    n = 2
+    plan = H.Plan(w.level, gamma=w.gamma, cfl=w.cfl, precision=precision)
+    plan.set_tile_shape(shape)
+    lev = H.make_level(plan, w.state, w.grav)
+    a = torch.tensor(np.asarray(w.a_sched[:n + 1], dtype=np.float64), device="cuda")
+    dt = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+    plan.run(lev, a, dt, n, compute_dt0=True, use_graph=False)
+    torch.cuda.synchronize()
+    assert plan.status()[0] == H.NYX_OK
+    got = plan.from_device(lev.current, 6)
+    first = W.valid(got[0])[:, :1, :1, :1]
+    for g in got:
+        assert np.array_equal(W.valid(g), np.broadcast_to(first, W.valid(g).shape))
+    ref, _, _ = oracle.run(w.level, oracle_params(w), w.state, w.grav, w.a_sched, n)
+    err = field_errors(got, ref)
+    for k, (linf, l1) in err.items():
+        if precision == "fp64":
+            assert linf <= FP64_TOL, (k, err)
+        else:
+            assert linf <= MIXED_GATES["linf"] and l1 <= MIXED_GATES["l1"], (k, err)
