@@ -235,7 +235,7 @@ int nyx_hydro_step_host(nyx_plan *plan, nyx_level *level, const double *host_sta
  * copies go through a device staging buffer of the same size, made on the
  * first call (NYX_ENOMEM if it cannot be); the scatter into and the gather
  * from the level's state run on the device.  On a persistent plan whose
- * level has enough work items, the boxes are cut into up to 16 groups: each
+ * level has enough work items, the boxes are cut into up to 32 groups: each
  * group's new cells are copied out while later groups advance, and, when
  * *dt_inout > 0, each group's cells are copied in while earlier groups
  * fill, flatten (flattening plans) and advance.  The library's own
