@@ -206,7 +206,14 @@ int nyx_hydro_correct(nyx_plan *plan, nyx_level *level, const double *a_old_dev,
  * nsteps+1 scalars: dt_dev[0] is the first step's dt (computed here by
  * nyx_hydro_estdt if compute_dt0 != 0) and step s writes dt_dev[s+1].
  * use_graph != 0 captures the sequence once into a CUDA graph (kept in the
- * plan, keyed by the pointers and nsteps) and replays it. */
+ * plan, keyed by the pointers and nsteps) and replays it.  On a persistent
+ * plan whose level has enough work items (4 waves or more) the boxes are cut
+ * into the groups of nyx_hydro_step_host_valid (made on the first call):
+ * every step runs one advance launch per group, and each group's ghost fill
+ * (and flattening pass) of the next step starts as soon as the groups it
+ * reads have advanced, beside the other groups' advances.  The result is
+ * that of nsteps calls of nyx_hydro_advance, bit for bit (a plan with
+ * profiling on keeps one fill and one advance launch per step). */
 int nyx_hydro_run(nyx_plan *plan, nyx_level *level, const double *a_dev, double *dt_dev,
                   int nsteps, int compute_dt0, int use_graph);
 

@@ -408,6 +408,12 @@ void free_plan(nyx_plan *P) {
   if (P->ev_setup) cudaEventDestroy(P->ev_setup);
   if (P->ev_side) cudaEventDestroy(P->ev_side);
   if (P->stream2) cudaStreamDestroy(P->stream2);
+  for (int k = 0; k < 2; ++k) {
+    if (P->fill_stream[k]) cudaStreamDestroy(P->fill_stream[k]);
+    if (P->ev_fjoin[k]) cudaEventDestroy(P->ev_fjoin[k]);
+  }
+  for (auto &e : P->ev_gfill) cudaEventDestroy(e);
+  for (auto &e : P->ev_gadv) cudaEventDestroy(e);
   cudaFree(P->d_queue_grp);
   cudaFree(P->d_queue);
   delete P;
@@ -810,6 +816,14 @@ int setup_readback(nyx_plan *P) {
   for (auto &e : P->ev_grp) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   P->ev_in.assign(ng, nullptr);
   for (auto &e : P->ev_in) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  for (int k = 0; k < 2; ++k) {
+    CK(cudaStreamCreateWithFlags(&P->fill_stream[k], cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&P->ev_fjoin[k], cudaEventDisableTiming));
+  }
+  P->ev_gfill.assign(ng, nullptr);
+  for (auto &e : P->ev_gfill) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  P->ev_gadv.assign(ng, nullptr);
+  for (auto &e : P->ev_gadv) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   P->grp_src = src;
   P->in_order = order;
   P->proc_order = proc;
@@ -1161,9 +1175,95 @@ int tune_shape(nyx_plan *P, const FusedArgs &base) {
   return NYX_OK;
 }
 
+// nsteps steps of a fused plan with box groups, the ghost fill overlapped
+// with the advance.  Per step s, S = state[cur], Sn = state[1-cur]:
+//   * group g's fill (and flattening coefficients) of S, on fill stream
+//     gi & 1, waits only for the advances of step s-1 of the groups it reads
+//     (itself included; at s = 0 for the start of the run), so it runs
+//     beside the advances of the other groups.  It writes the ghost cells of
+//     g's boxes in S, which no advance of step s-1 reads (they read the other
+//     buffer) and none writes (advances write valid cells);
+//   * the step set-up waits for step s-1's dt (plan stream); then group g
+//     advances on the plan stream or stream2 in turn once its fill is done;
+//   * the dt of step s+1 is finalised once every group has advanced.
+// Every cell takes the same arithmetic as in the one-launch form, so the
+// result is the same bit for bit.
+int run_grouped(nyx_plan *P, nyx_level *L, const double *a_dev, double *dt_dev, int nsteps) {
+  CK(cudaEventRecord(P->ev_start, P->stream));
+  for (int k = 0; k < 2; ++k) CK(cudaStreamWaitEvent(P->fill_stream[k], P->ev_start, 0));
+  const cudaStream_t cs[2] = {P->stream, P->stream2};
+  for (int s = 0; s < nsteps; ++s) {
+    double *S = L->state[L->cur];
+    double *Sn = L->state[1 - L->cur];
+    for (int gi = 0; gi < P->ngrp; ++gi) {
+      const int g = P->proc_order[gi];
+      const cudaStream_t fs = P->fill_stream[gi & 1];
+      if (s > 0) {
+        const unsigned need = P->grp_src[g] | (1u << g);
+        for (int q = 0; q < P->ngrp; ++q)
+          if ((need >> q) & 1u) CK(cudaStreamWaitEvent(fs, P->ev_gadv[q], 0));
+      }
+      for (int p = 0; p < 4; ++p) {
+        const int r0 = P->rect_off[p][g], nr = P->rect_off[p][g + 1] - r0;
+        if (nr > 0) {
+          launch_fill(S, NCONS, P->d_boxes, P->d_rects_grp[p] + r0, nullptr, nr,
+                      P->pass[p].total, fs, true);
+          P->launches += 1;
+        }
+      }
+      if (P->d_flat) {
+        const int t0 = P->flat_tile_pref[P->grp_box[g]], t1 = P->flat_tile_pref[P->grp_box[g + 1]];
+        if (t1 > t0) {
+          int e = launch_flatten(P->prm.precision, P->d_boxes, P->d_flat_tiles + t0, t1 - t0, S,
+                                 P->d_K, P->d_flat, fs);
+          if (e) return cuda_fail((cudaError_t)e, "flattening launch");
+          P->launches += 1;
+        }
+      }
+      CK(cudaEventRecord(P->ev_gfill[g], fs));
+    }
+    launch_step_setup(P->d_K, a_dev + s, a_dev + s + 1, dt_dev + s, P->d_SC, P->d_boxes, P->nbox,
+                      P->d_BS, P->stream);
+    P->launches += 1;
+    CK(cudaEventRecord(P->ev_setup, P->stream));
+    CK(cudaStreamWaitEvent(P->stream2, P->ev_setup, 0));
+    FusedArgs a = fused_args(P, S, L->grav, Sn, P->d_dtacc, false);
+    for (int gi = 0; gi < P->ngrp; ++gi) {
+      const int g = P->proc_order[gi];
+      const cudaStream_t st = cs[gi & 1];
+      CK(cudaStreamWaitEvent(st, P->ev_gfill[g], 0));
+      a.queue = P->d_queue_grp + g;
+      if (int rc = launch_level(P, a, g, st)) return rc;
+      CK(cudaEventRecord(P->ev_gadv[g], st));
+    }
+    CK(cudaEventRecord(P->ev_side, P->stream2));
+    CK(cudaStreamWaitEvent(P->stream, P->ev_side, 0));
+    launch_dt_finalize(P->d_K, P->d_dtacc, dt_dev + s + 1, P->stream);
+    P->launches += 1;
+    L->cur = 1 - L->cur;
+  }
+  // every stream of the run ends joined to the plan stream
+  for (int k = 0; k < 2; ++k) {
+    CK(cudaEventRecord(P->ev_fjoin[k], P->fill_stream[k]));
+    CK(cudaStreamWaitEvent(P->stream, P->ev_fjoin[k], 0));
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "grouped run launch");
+  P->flux_valid = P->d_flux != nullptr;
+  return NYX_OK;
+}
+
 int enqueue_run(nyx_plan *P, nyx_level *L, const double *a_dev, double *dt_dev, int nsteps,
                 int compute_dt0) {
   if (compute_dt0) do_estdt(P, L->state[L->cur], a_dev, dt_dev);
+  // fused plans with box groups overlap each step's ghost fill with the
+  // advance; profiled runs keep one fill and one advance launch per step so
+  // that each is timed on its own
+  if (P->prm.batching != NYX_PER_BOX && P->ngrp > 1 && !(P->prm.autotune && !P->tuned) &&
+      !P->profiling && nsteps > 0) {
+    prepare_tmaps(P, L);
+    return run_grouped(P, L, a_dev, dt_dev, nsteps);
+  }
   for (int s = 0; s < nsteps; ++s) {
     int rc = do_advance(P, L, a_dev + s, a_dev + s + 1, dt_dev + s, nullptr, dt_dev + s + 1);
     if (rc) return rc;
@@ -1553,6 +1653,10 @@ int nyx_hydro_run(nyx_plan *P, nyx_level *L, const double *a_dev, double *dt_dev
   if (!P || !L || !a_dev || !dt_dev || nsteps < 0) return fail(NYX_EINVAL, "null argument");
   if ((L->cur != 0 && L->cur != 1) || !L->state[0] || !L->state[1] || L->state[0] == L->state[1])
     return fail(NYX_EINVAL, "level needs two distinct state buffers and cur in {0,1}");
+  // box groups (made once, outside any capture): a run overlaps each group's
+  // ghost fill with the other groups' advances
+  if (P->prm.batching != NYX_PER_BOX && P->ngrp == 0)
+    if (int rc = setup_readback(P)) return rc;
   if (!use_graph) return enqueue_run(P, L, a_dev, dt_dev, nsteps, compute_dt0);
   if (P->prm.batching == NYX_PERSISTENT && P->prm.autotune && !P->tuned) {
     // tune outside the capture: one eager step on scratch copies is not

@@ -102,6 +102,12 @@ struct nyx_plan {
   std::vector<unsigned> grp_src;
   std::vector<int> in_order;
   std::vector<int> proc_order;  // the order in which the groups advance
+  // multi-step runs on the device (nyx_hydro_run): each group's ghost fill
+  // of step s+1 runs on one of two fill streams as soon as the groups it
+  // reads have advanced in step s, beside the other groups' advances
+  cudaStream_t fill_stream[2] = {nullptr, nullptr};
+  std::vector<cudaEvent_t> ev_gfill, ev_gadv;
+  cudaEvent_t ev_fjoin[2] = {nullptr, nullptr};
   // per-box FP64 form
   double *d_scratch = nullptr;
   long long Vmax = 0;

@@ -390,7 +390,8 @@ def test_step_host_valid_overlapped_read_back_matches_device_path(shape):
     a = torch.tensor(np.asarray(w.a_sched[:2], dtype=np.float64), device="cuda")
     dt = torch.zeros(2, dtype=torch.float64, device="cuda")
     ref.counters(reset=True)
-    ref.run(rlev, a, dt, 1, compute_dt0=True, use_graph=False)
+    ref.estdt(rlev, a[0:1], dt[0:1])          # the one-launch device path: estdt, then
+    ref.advance(rlev, a[0:1], a[1:2], dt[0:1], dt_next=dt[1:2])  # fill + one advance launch
     torch.cuda.synchronize()
     n_dev = ref.counters(reset=True)["launches"]
     assert ref.status()[0] == H.NYX_OK and plan.status()[0] == H.NYX_OK
@@ -422,7 +423,8 @@ def test_step_host_valid_overlapped_with_flattening_matches_device_path():
     rlev = H.make_level(ref, w.state, w.grav)
     a = torch.tensor(np.asarray(w.a_sched[:2], dtype=np.float64), device="cuda")
     dt = torch.zeros(2, dtype=torch.float64, device="cuda")
-    ref.run(rlev, a, dt, 1, compute_dt0=True, use_graph=False)
+    ref.estdt(rlev, a[0:1], dt[0:1])
+    ref.advance(rlev, a[0:1], a[1:2], dt[0:1], dt_next=dt[1:2])
     torch.cuda.synchronize()
     assert ref.status()[0] == H.NYX_OK
     want = [W.valid(x) for x in ref.from_device(rlev.current, 6)]
@@ -440,6 +442,48 @@ def test_step_host_valid_overlapped_with_flattening_matches_device_path():
             assert np.array_equal(x, y), dt_in
         assert dt_next == d[1]
     plan.close()
+    ref.close()
+
+
+@pytest.mark.parametrize("precision,shape,flat", [("mixed", 3, False), ("mixed", 3, True),
+                                                   ("fp64", 1, False)])
+def test_grouped_run_equals_one_launch_steps(precision, shape, flat):
+    """nyx_hydro_run on a level with box groups (1000 boxes of 16^3) runs
+    each step as one launch per group, with each group's ghost fill (and
+    flattening pass) on a fill stream beside the other groups' advances.
+    Eager and graph-captured, the states and every dt equal, bit for bit,
+    those of one fill and one advance launch per step (nyx_hydro_advance)."""
+    n = 3
+    w = W.tiled_box(n=160, box=16, nsteps=n)
+    kw = dict(gamma=w.gamma, cfl=w.cfl, precision=precision, flattening=flat)
+    a = torch.tensor(np.asarray(w.a_sched[:n + 1], dtype=np.float64), device="cuda")
+    ref = H.Plan(w.level, **kw)
+    ref.set_tile_shape(shape)
+    rlev = H.make_level(ref, w.state, w.grav)
+    dt_ref = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+    ref.counters(reset=True)
+    ref.estdt(rlev, a[0:1], dt_ref[0:1])
+    for s in range(n):
+        ref.advance(rlev, a[s:s + 1], a[s + 1:s + 2], dt_ref[s:s + 1], dt_next=dt_ref[s + 1:s + 2])
+    torch.cuda.synchronize()
+    n_ref = ref.counters(reset=True)["launches"]
+    assert ref.status()[0] == H.NYX_OK
+    want = [W.valid(x) for x in ref.from_device(rlev.current, 6)]
+    for use_graph in (False, True):
+        plan = H.Plan(w.level, **kw)
+        plan.set_tile_shape(shape)
+        lev = H.make_level(plan, w.state, w.grav)
+        dt = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+        plan.counters(reset=True)
+        plan.run(lev, a, dt, n, compute_dt0=True, use_graph=use_graph)
+        torch.cuda.synchronize()
+        n_run = plan.counters(reset=True)["launches"]
+        assert plan.status()[0] == H.NYX_OK
+        assert torch.equal(dt, dt_ref), use_graph
+        for x, y in zip(plan.from_device(lev.current, 6), want):
+            assert np.array_equal(W.valid(x), y), use_graph
+        assert n_run > n_ref + 2 * n, (n_run, n_ref)  # one advance launch per group and step
+        plan.close()
     ref.close()
 
 
