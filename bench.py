@@ -689,7 +689,9 @@ def run_ours(args, w):
             "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "level": w.name, "valid_cells": cells,
                        "boxes": w.level.nbox, "precision": args.precision,
-                       "batching": "persistent + CUDA graph", "tile": [tx, ty],
+                       "batching": "persistent + CUDA graph; box groups, each group's ghost "
+                                   "fill beside the other groups' advances",
+                       "tile": [tx, ty],
                        "l2": "inputs larger than L2 (state + gravity > 20 GB)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
             "roofline": roofline_of(
