@@ -210,8 +210,9 @@ int nyx_hydro_correct(nyx_plan *plan, nyx_level *level, const double *a_old_dev,
  * plan whose level has enough work items (4 waves or more) the boxes are cut
  * into the groups of nyx_hydro_step_host_valid (made on the first call):
  * every step runs one advance launch per group, and each group's ghost fill
- * (and flattening pass) of the next step starts as soon as the groups it
- * reads have advanced, beside the other groups' advances.  The result is
+ * of the next step starts as soon as the groups it reads have advanced,
+ * beside the other groups' advances (a flattening plan's coefficient pass
+ * then runs over the whole level before the step's advances).  The result is
  * that of nsteps calls of nyx_hydro_advance, bit for bit (a plan with
  * profiling on keeps one fill and one advance launch per step). */
 int nyx_hydro_run(nyx_plan *plan, nyx_level *level, const double *a_dev, double *dt_dev,

@@ -1177,12 +1177,15 @@ int tune_shape(nyx_plan *P, const FusedArgs &base) {
 
 // nsteps steps of a fused plan with box groups, the ghost fill overlapped
 // with the advance.  Per step s, S = state[cur], Sn = state[1-cur]:
-//   * group g's fill (and flattening coefficients) of S, on fill stream
-//     gi & 1, waits only for the advances of step s-1 of the groups it reads
+//   * group g's fill of S, on fill stream gi & 1, waits only for the
+//     advances of step s-1 of the groups it reads
 //     (itself included; at s = 0 for the start of the run), so it runs
 //     beside the advances of the other groups.  It writes the ghost cells of
 //     g's boxes in S, which no advance of step s-1 reads (they read the other
 //     buffer) and none writes (advances write valid cells);
+//   * a flattening plan's coefficient pass runs over the whole level on the
+//     plan stream once every group is filled (it does not fit beside an
+//     advance);
 //   * the step set-up waits for step s-1's dt (plan stream); then group g
 //     advances on the plan stream or stream2 in turn once its fill is done;
 //   * the dt of step s+1 is finalised once every group has advanced.
@@ -1211,16 +1214,17 @@ int run_grouped(nyx_plan *P, nyx_level *L, const double *a_dev, double *dt_dev, 
           P->launches += 1;
         }
       }
-      if (P->d_flat) {
-        const int t0 = P->flat_tile_pref[P->grp_box[g]], t1 = P->flat_tile_pref[P->grp_box[g + 1]];
-        if (t1 > t0) {
-          int e = launch_flatten(P->prm.precision, P->d_boxes, P->d_flat_tiles + t0, t1 - t0, S,
-                                 P->d_K, P->d_flat, fs);
-          if (e) return cuda_fail((cudaError_t)e, "flattening launch");
-          P->launches += 1;
-        }
-      }
       CK(cudaEventRecord(P->ev_gfill[g], fs));
+    }
+    if (P->d_flat) {
+      // the coefficient pass (512 threads, 43 KB of shared memory per block)
+      // does not fit beside the advance: it runs over the whole level once
+      // every group is filled, before the step's advances
+      for (int k = 0; k < 2; ++k) {
+        CK(cudaEventRecord(P->ev_fjoin[k], P->fill_stream[k]));
+        CK(cudaStreamWaitEvent(P->stream, P->ev_fjoin[k], 0));
+      }
+      if (int rc = do_flatten(P, S)) return rc;
     }
     launch_step_setup(P->d_K, a_dev + s, a_dev + s + 1, dt_dev + s, P->d_SC, P->d_boxes, P->nbox,
                       P->d_BS, P->stream);
