@@ -718,11 +718,12 @@ int part_groups(nyx_plan::RunPart &pt, const std::vector<int> &gb) {
   return NYX_OK;
 }
 
-// Read-back groups of nyx_hydro_step_host_valid (fused plans): up to 32
-// ranges of whole boxes with about equal cells (the groups' bit masks are 32
-// bits), as long as each group keeps 2 waves of items or more in the plan's
-// tile shape.  One group (no overlap) otherwise.  Every shape gets the same
-// groups.  (On the 512^3 large level: 32 groups 1.74e9 zone-updates/s end
+// Box groups of a fused plan, used by nyx_hydro_step_host_valid (input,
+// advance and read-back overlapped per group) and by nyx_hydro_run (each
+// group's ghost fill beside the other groups' advances): up to 32 ranges of
+// whole boxes with about equal cells (the groups' bit masks are 32 bits), as
+// long as each group keeps 2 waves of items or more in the plan's tile shape.
+// One group (no overlap) otherwise.  Every shape gets the same groups.  (On the 512^3 large level: 32 groups 1.74e9 zone-updates/s end
 // to end, 16 groups 1.72e9, 8 groups 1.59e9.)
 int setup_readback(nyx_plan *P) {
   const int nsh = fused_num_shapes(P->prm.precision);
