@@ -1,5 +1,6 @@
-"""Host-side check of the stream schedule of a grouped multi-step run
-(run_grouped in nyx_api.cu), by a model of its enqueue order.
+"""Host-side check of the stream schedules of the box groups, by models of
+their enqueue order: a grouped multi-step run (run_grouped in nyx_api.cu)
+and, further below, the overlapped host step (step_pipelined).
 
 The run issues, on four streams (the plan stream P, a second advance stream
 S2, two fill streams F0, F1):
@@ -162,6 +163,89 @@ def test_planted_schedule_mistakes_are_caught(mistake, flat):
         src, proc = grouping(rng, ngrp)
         src[proc[0]] = set()          # a group whose fill reads no other group
         m = run_model(ngrp, src, proc, nsteps=4, flat=flat, mistake=mistake)
+        if m.check():
+            caught = True
+            break
+    assert caught, mistake
+
+
+# ---------------------------------------------------------------------------
+# The overlapped host step (step_pipelined in nyx_api.cu, dt given): the
+# plan stream P, a second advance stream S2, the input stream IN and the
+# read-back stream OUT.  The host buffers may be one buffer (host_in ==
+# host_out), and the device staging buffer (packed) serves both directions.
+
+def host_step_model(ngrp, src, proc, in_order, flat, same_host, mistake=None):
+    m = Model()
+    hin = "host" if same_host else "host_in"
+    hout = "host" if same_host else "host_out"
+    X, Y = 0, 1
+    m.op("P", "scalars", writes={("scal",)})
+    m.record("start", "P")
+    m.wait("IN", "start")
+    for q in in_order:
+        m.op("IN", f"copy_in{q}", reads={(hin, q)}, writes={("packed", q)})
+        m.op("IN", f"scatter{q}", reads={("packed", q)}, writes={("V", X, q)})
+        m.record(("in", q), "IN")
+    m.op("P", "setup", reads={("scal",)}, writes={("SC",)})
+    m.record("setup", "P")
+    m.wait("S2", "setup")
+    waited = [set(), set()]
+    for gi, g in enumerate(proc):
+        st = ("P", "S2")[gi & 1]
+        need = (set(src[g]) | {g}) - waited[gi & 1]
+        if mistake == "no_own_input":
+            need -= {g}
+        for q in sorted(need):
+            m.wait(st, ("in", q))
+        waited[gi & 1] |= need
+        m.op(st, f"fill{g}", reads={("V", X, q) for q in src[g]}, writes={("H", X, g)})
+        if flat:
+            m.op(st, f"flat{g}", reads={("V", X, g), ("H", X, g)}, writes={("C", g)})
+        reads = {("V", X, g), ("H", X, g), ("SC",)} | ({("C", g)} if flat else set())
+        m.op(st, f"adv{g}", reads=reads, writes={("V", Y, g)}, atomic={("acc",)})
+        m.op(st, f"gather{g}", reads={("V", Y, g)}, writes={("packed", g)})
+        m.record(("grp", g), st)
+        if mistake != "no_out_wait":
+            m.wait("OUT", ("grp", g))
+        m.op("OUT", f"copy_out{g}", reads={("packed", g)}, writes={(hout, g)})
+    m.record("side", "S2")
+    m.wait("P", "side")
+    m.op("P", "dtfin", reads={("acc",)}, writes={("acc",), ("scal_dt",)})
+    return m
+
+
+def host_step_grouping(rng, ngrp):
+    src, proc = grouping(rng, ngrp)
+    order, sent = [], set()
+    for g in proc:                     # inputs in the order the advances need them
+        for q in sorted(set(src[g]) | {g}):
+            if q not in sent:
+                sent.add(q)
+                order.append(q)
+    return src, proc, order
+
+
+@pytest.mark.parametrize("flat,same_host", [(False, False), (True, False), (False, True)])
+@pytest.mark.parametrize("seed", range(8))
+def test_host_step_schedule_orders_every_conflict(seed, flat, same_host):
+    rng = random.Random(500 + seed)
+    ngrp = rng.randint(2, 9)
+    src, proc, order = host_step_grouping(rng, ngrp)
+    assert sorted(order) == list(range(ngrp))
+    m = host_step_model(ngrp, src, proc, order, flat, same_host)
+    assert m.check() == []
+
+
+@pytest.mark.parametrize("mistake", ["no_own_input", "no_out_wait"])
+def test_planted_host_step_mistakes_are_caught(mistake):
+    caught = False
+    for seed in range(40):
+        rng = random.Random(2000 + seed)
+        ngrp = rng.randint(2, 9)
+        src, proc, order = host_step_grouping(rng, ngrp)
+        src[proc[0]] = set()
+        m = host_step_model(ngrp, src, proc, order, False, True, mistake=mistake)
         if m.check():
             caught = True
             break
